@@ -1,0 +1,287 @@
+/*
+ * Oracle for RAK label propagation and Newman-Girvan modularity.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is a plain, single-threaded, slow CPU
+ * restatement of what the paper's method computes.  Only the test suite, the
+ * package smoke check and the CPU-baseline leg of the benchmark may load it.
+ * The CUDA library never includes, links or calls anything here, and nothing
+ * here is shared with it.
+ *
+ * Paper: S. Sahu, "Selecting a suitable Parallel Label-propagation based
+ * algorithm for Disjoint Community Detection" (arXiv 2301.09125).
+ *
+ *   RAK (Sec. 3.2): every vertex starts with a unique label; at every step each
+ *   vertex adopts the label with the most interconnecting edge weight among its
+ *   neighbours.  Ties between maximum-weight labels are broken either by taking
+ *   the first of them ("strict") or a random one ("non-strict").  The run has
+ *   converged when at least (100 - n)% of the vertices kept their label during
+ *   a step, where n is the tolerance.
+ *   Asynchronous update (Sec. 3.3, stated for COPRA): a vertex may see labels
+ *   its neighbours took earlier in the same iteration.
+ *   Modularity (Sec. 1): Newman-Girvan quality of a disjoint partition.
+ *
+ * Readings where the paper is silent (each one is also listed in the design
+ * notes of the repository):
+ *   - "first" (strict) = the label whose first occurrence in the vertex's
+ *     adjacency list (CSR order) is earliest.
+ *   - "random" (non-strict) = among the maximum-weight labels, the one with the
+ *     smallest 64-bit counter-based hash of (seed, iteration, vertex, label);
+ *     equal hashes fall back to the strict rule.  The hash is SplitMix64's
+ *     output function (Steele, Lea & Flood, "Fast splittable pseudorandom
+ *     number generators", OOPSLA 2014) applied in counter mode.
+ *   - a vertex without edges keeps its label and never counts as changed, but
+ *     it is counted in N for the convergence test.
+ *   - converged iff changed <= tolerance * N, evaluated in double; the
+ *     iteration that meets the test is counted.
+ *   - synchronous = every vertex reads the labels of the previous iteration
+ *     (double buffer); asynchronous = in place, vertices in ascending order.
+ *   - the CSR is taken as given: a stored entry (v,u,w) is A_vu = w, a stored
+ *     self-loop counts the vertex's own current label, duplicate entries add.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------- */
+/* SplitMix64 output function (Steele et al. 2014): the 64-bit finaliser     */
+/* applied to state + k * golden-gamma.                                       */
+/* ------------------------------------------------------------------------- */
+#define ORACLE_GOLDEN_GAMMA 0x9E3779B97F4A7C15ULL
+
+uint64_t oracle_mix64(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+/* Counter-mode draw: the k-th (k >= 1) output of a SplitMix64 stream whose
+ * state starts at `key`. */
+static uint64_t oracle_draw(uint64_t key, uint64_t k)
+{
+    return oracle_mix64(key + k * ORACLE_GOLDEN_GAMMA);
+}
+
+/* Non-strict tie key of `label` at vertex v in global iteration t.
+ * Three nested counter-mode draws: stream(seed) -> t -> v -> label. */
+uint64_t oracle_tie_hash(uint64_t seed, int64_t t, int64_t v, int64_t label)
+{
+    uint64_t k_t = oracle_draw(seed, (uint64_t)t + 1);
+    uint64_t k_tv = oracle_draw(k_t, (uint64_t)v + 1);
+    return oracle_draw(k_tv, (uint64_t)label + 1);
+}
+
+/* ------------------------------------------------------------------------- */
+/* One RAK step for one vertex (Sec. 3.2).                                    */
+/* ------------------------------------------------------------------------- */
+
+/* Scratch for the insertion-ordered label -> (weight, first position) map. */
+typedef struct {
+    int32_t *slot_of; /* [n] label -> index into the lists below, -1 if absent */
+    int32_t *label;   /* [max_deg] labels in order of first appearance */
+    int64_t *weight;  /* [max_deg] summed edge weight per label */
+    int32_t *first;   /* [max_deg] first position in the adjacency list */
+} oracle_map;
+
+static int oracle_map_init(oracle_map *m, int32_t n, int64_t max_deg)
+{
+    m->slot_of = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    m->label = (int32_t *)malloc(sizeof(int32_t) * (size_t)(max_deg > 0 ? max_deg : 1));
+    m->weight = (int64_t *)malloc(sizeof(int64_t) * (size_t)(max_deg > 0 ? max_deg : 1));
+    m->first = (int32_t *)malloc(sizeof(int32_t) * (size_t)(max_deg > 0 ? max_deg : 1));
+    if (!m->slot_of || !m->label || !m->weight || !m->first) return -1;
+    for (int32_t i = 0; i < n; ++i) m->slot_of[i] = -1;
+    return 0;
+}
+
+static void oracle_map_free(oracle_map *m)
+{
+    free(m->slot_of);
+    free(m->label);
+    free(m->weight);
+    free(m->first);
+}
+
+/* The label vertex v adopts when it reads `cur` (Sec. 3.2):
+ *   1. sum, per neighbour label, the weights of the edges leading to it;
+ *   2. take the largest summed weight;
+ *   3. among the labels that reach it, strict picks the first one seen in the
+ *      adjacency list, non-strict the one with the smallest tie hash.
+ * A vertex without edges keeps cur[v]. */
+static int32_t oracle_choose_with(oracle_map *m, int32_t v, const int32_t *offsets,
+                                  const int32_t *indices, const int32_t *weights,
+                                  const int32_t *cur, int strict, uint64_t seed, int64_t t)
+{
+    int32_t begin = offsets[v], end = offsets[v + 1];
+    if (begin == end) return cur[v];
+
+    /* step 1: accumulate */
+    int32_t count = 0;
+    for (int32_t e = begin; e < end; ++e) {
+        int32_t l = cur[indices[e]];
+        int64_t w = weights ? (int64_t)weights[e] : 1;
+        int32_t s = m->slot_of[l];
+        if (s < 0) {
+            s = count++;
+            m->slot_of[l] = s;
+            m->label[s] = l;
+            m->weight[s] = 0;
+            m->first[s] = e - begin;
+        }
+        m->weight[s] += w;
+    }
+
+    /* step 2: maximum weight */
+    int64_t wmax = m->weight[0];
+    for (int32_t s = 1; s < count; ++s)
+        if (m->weight[s] > wmax) wmax = m->weight[s];
+
+    /* step 3: tie rule.  Slots are in order of first appearance, so the first
+     * maximum-weight slot is the strict choice. */
+    int32_t best = -1;
+    uint64_t best_hash = 0;
+    for (int32_t s = 0; s < count; ++s) {
+        if (m->weight[s] != wmax) continue;
+        if (strict) {
+            best = s;
+            break;
+        }
+        uint64_t h = oracle_tie_hash(seed, t, v, m->label[s]);
+        if (best < 0 || h < best_hash) { /* equal hash: keep the earlier slot */
+            best = s;
+            best_hash = h;
+        }
+    }
+    int32_t chosen = m->label[best];
+
+    for (int32_t s = 0; s < count; ++s) m->slot_of[m->label[s]] = -1;
+    return chosen;
+}
+
+static int64_t oracle_max_degree(int32_t n, const int32_t *offsets)
+{
+    int64_t d = 0;
+    for (int32_t v = 0; v < n; ++v)
+        if (offsets[v + 1] - offsets[v] > d) d = offsets[v + 1] - offsets[v];
+    return d;
+}
+
+/* The label each vertex in verts[0..count) adopts when reading `cur` in global
+ * iteration t.  Used to check single outputs of a sweep at sizes where a whole
+ * oracle run would be too slow.  Returns 0, or -1 on allocation failure. */
+int oracle_choose_many(int32_t n, const int32_t *offsets, const int32_t *indices,
+                       const int32_t *weights, const int32_t *cur, int strict, uint64_t seed,
+                       int64_t t, int64_t count, const int32_t *verts, int32_t *out)
+{
+    oracle_map m;
+    if (oracle_map_init(&m, n, oracle_max_degree(n, offsets)) != 0) {
+        oracle_map_free(&m);
+        return -1;
+    }
+    for (int64_t i = 0; i < count; ++i)
+        out[i] = oracle_choose_with(&m, verts[i], offsets, indices, weights, cur, strict, seed, t);
+    oracle_map_free(&m);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* The RAK iteration (Sec. 3.2, with Sec. 3.3's asynchronous update).         */
+/* ------------------------------------------------------------------------- */
+
+/* labels: in = initial labels (NULL = unique labels, label[v] = v); out = final.
+ * changed_hist[i] receives the number of vertices that changed in iteration i
+ * (capacity max_iter, may be NULL).
+ * iter_offset shifts the iteration index seen by the tie hash (resume).
+ * Returns 0, or -1 on bad arguments / allocation failure. */
+int oracle_rak(int32_t n, const int32_t *offsets, const int32_t *indices,
+               const int32_t *weights, double tolerance, int32_t max_iter, int async_mode,
+               int strict, uint64_t seed, int32_t iter_offset, const int32_t *init_labels,
+               int32_t *labels, int32_t *out_iterations, int32_t *out_converged,
+               int64_t *changed_hist)
+{
+    if (n < 0 || max_iter < 1 || !(tolerance >= 0.0 && tolerance <= 1.0)) return -1;
+    for (int32_t v = 0; v < n; ++v) labels[v] = init_labels ? init_labels[v] : v;
+    *out_iterations = 0;
+    *out_converged = 0;
+
+    oracle_map m;
+    int32_t *next = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    if (!next || oracle_map_init(&m, n, oracle_max_degree(n, offsets)) != 0) {
+        free(next);
+        return -1;
+    }
+
+    for (int32_t it = 0; it < max_iter; ++it) {
+        int64_t t = (int64_t)it + iter_offset;
+        int64_t changed = 0;
+        if (async_mode) {
+            /* in place, ascending vertex order: later vertices read new labels */
+            for (int32_t v = 0; v < n; ++v) {
+                int32_t c = oracle_choose_with(&m, v, offsets, indices, weights, labels,
+                                               strict, seed, t);
+                if (c != labels[v]) ++changed;
+                labels[v] = c;
+            }
+        } else {
+            /* every vertex reads the previous iteration's labels */
+            for (int32_t v = 0; v < n; ++v) {
+                next[v] = oracle_choose_with(&m, v, offsets, indices, weights, labels, strict,
+                                             seed, t);
+                if (next[v] != labels[v]) ++changed;
+            }
+            memcpy(labels, next, sizeof(int32_t) * (size_t)n);
+        }
+        if (changed_hist) changed_hist[it] = changed;
+        *out_iterations = it + 1;
+        if ((double)changed <= tolerance * (double)n) {
+            *out_converged = 1;
+            break;
+        }
+    }
+    free(next);
+    oracle_map_free(&m);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Modularity (Sec. 1; Newman & Girvan).                                      */
+/* ------------------------------------------------------------------------- */
+
+/* Q = (1/2m) sum_{v,u} [A_vu - k_v k_u / 2m] delta(c_v, c_u), where the stored
+ * CSR is the matrix A (entry (v,u,w) is A_vu = w), k_v = sum_u A_vu and
+ * 2m = sum_v k_v.  Grouping the double sum by community c gives
+ * Q = sum_c [ L_c / 2m - (K_c / 2m)^2 ], with L_c the weight of stored entries
+ * inside c and K_c the summed k_v of c's vertices.  L = sum_c L_c, K_c and 2m
+ * are exact 64-bit integers and S = sum_c K_c^2 an exact 128-bit one; Q is then
+ * L/2m - S/(2m)^2 in double.  Labels must lie in [0, n).  A graph without
+ * edges has Q = 0.  The three exact integers are also returned (may be NULL). */
+double oracle_modularity(int32_t n, const int32_t *offsets, const int32_t *indices,
+                         const int32_t *weights, const int32_t *labels, int64_t *out_l,
+                         int64_t *out_2m, uint64_t *out_s_hi_lo)
+{
+    int64_t two_m = 0, l_in = 0;
+    int64_t *k_c = (int64_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int64_t));
+    if (!k_c) return 0.0 / 0.0;
+    for (int32_t v = 0; v < n; ++v) {
+        int64_t k_v = 0;
+        for (int32_t e = offsets[v]; e < offsets[v + 1]; ++e) {
+            int64_t w = weights ? (int64_t)weights[e] : 1;
+            k_v += w;
+            if (labels[indices[e]] == labels[v]) l_in += w;
+        }
+        two_m += k_v;
+        k_c[labels[v]] += k_v;
+    }
+    unsigned __int128 s = 0;
+    for (int32_t c = 0; c < n; ++c) s += (unsigned __int128)((uint64_t)k_c[c]) * (uint64_t)k_c[c];
+    free(k_c);
+    if (out_l) *out_l = l_in;
+    if (out_2m) *out_2m = two_m;
+    if (out_s_hi_lo) {
+        out_s_hi_lo[0] = (uint64_t)(s >> 64);
+        out_s_hi_lo[1] = (uint64_t)s;
+    }
+    if (two_m == 0) return 0.0;
+    double dm = (double)two_m;
+    return (double)l_in / dm - (double)s / (dm * dm);
+}
