@@ -1,0 +1,250 @@
+/*
+ * lp.h - C ABI of the GB300 (sm_103a) RAK label-propagation library.
+ *
+ * Method: RAK / LPA label propagation as used by Sahu, "Selecting a suitable
+ * Parallel Label-propagation based algorithm for Disjoint Community
+ * Detection" (arXiv 2301.09125).
+ *   Sec. 3.2  every vertex starts with a unique label; in each iteration every
+ *             vertex adopts the label carrying the most interconnecting edge
+ *             weight among its neighbours; maximum-weight ties are broken by
+ *             taking the first of them (strict) or a random one (non-strict);
+ *             the run converges once at most a `tolerance` fraction of the
+ *             vertices changed label in an iteration (0.05 recommended).
+ *   Sec. 3.3  asynchronous update: a vertex may read labels its neighbours
+ *             took earlier in the same iteration.
+ *   Sec. 1    modularity (Newman-Girvan) scores the resulting partition.
+ *   Sec. 3.1  graphs are undirected (every edge stored in both directions)
+ *             and weighted.
+ *
+ * Conventions for every entry point:
+ *   - Every call returns an lp_status and never aborts the process.  On
+ *     failure lp_last_error() returns a message for the calling thread.
+ *   - Graphs are CSR with int32 row offsets (n+1 entries, offsets[0] = 0,
+ *     non-decreasing, offsets[n] = m), int32 column indices in [0, n) and
+ *     int32 weights >= 1 (NULL = every weight is 1).  The CSR is used exactly
+ *     as given: a stored entry (v,u,w) is A_vu = w; a stored self-loop counts
+ *     the vertex's own label; duplicate entries add up.  The library does not
+ *     symmetrise (LP_FLAG_CHECK_SYMMETRIC only checks).
+ *   - The order of entries inside a row is significant: the strict tie rule
+ *     picks, among the maximum-weight labels, the one whose first occurrence
+ *     in the row comes first.
+ *   - Non-strict ties: among the maximum-weight labels, the one with the
+ *     smallest 64-bit key mix(mix(mix(seed + (t+1)G) + (v+1)G) + (l+1)G),
+ *     where mix is the SplitMix64 output function (Steele, Lea & Flood 2014),
+ *     G = 0x9E3779B97F4A7C15, t = iteration + iter_offset, v the vertex and l
+ *     the label, both local to the graph; equal keys fall back to the strict
+ *     rule.
+ *   - Converged iff changed <= tolerance * n in double precision, where n
+ *     counts every vertex (isolated ones keep their label and never count as
+ *     changed).  Reaching max_iter first is not an error (converged = 0).
+ *   - All device work is ordered on the CUDA stream given at creation time.
+ *     Calls on one object are not thread-safe; distinct objects may be used
+ *     from distinct threads.
+ */
+#ifndef LP_H
+#define LP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LP_OK = 0,
+    LP_EINVAL = 1,   /* bad argument or invalid CSR / labels */
+    LP_ENOMEM = 2,   /* device or pinned host allocation failed */
+    LP_ECUDA = 3,    /* a CUDA runtime call failed */
+    LP_ETIMEOUT = 4, /* a bounded device-side wait ran out */
+    LP_ENOTREADY = 5 /* no result yet (serving poll) */
+} lp_status;
+
+enum { LP_SYNC = 0, LP_ASYNC = 1 };
+
+enum {
+    LP_FLAG_DEVICE_PTRS = 1,     /* offsets/indices/weights are device pointers */
+    LP_FLAG_CHECK_SYMMETRIC = 2, /* also reject a CSR whose pattern/weights are not symmetric */
+    LP_FLAG_BORROW = 4           /* with DEVICE_PTRS: keep the caller's indices/weights
+                                    instead of copying them (caller keeps them alive and
+                                    unchanged until lp_graph_destroy) */
+};
+
+/* Parameters of one RAK run (Sec. 3.2). */
+typedef struct {
+    double tolerance;           /* in [0, 1]; converged iff changed <= tolerance*n (default 0.05) */
+    int32_t max_iter;           /* >= 1 (default 20) */
+    int32_t mode;               /* LP_SYNC: every vertex reads the previous iteration's labels
+                                   (double buffer).  LP_ASYNC: a vertex also reads labels
+                                   written earlier in the same iteration (Sec. 3.3), in the
+                                   wave order given by `waves`. */
+    int32_t strict;             /* 1 = strict "first" tie rule, 0 = non-strict "random" */
+    int32_t iter_offset;        /* added to the iteration index seen by the non-strict key
+                                   (resume a run without changing its random stream) */
+    uint64_t seed;              /* non-strict key seed */
+    const int32_t *init_labels; /* NULL = unique labels label[v] = v (Sec. 3.2); else n
+                                   labels in [0, n) (resume from lp_labels_get) */
+    int32_t init_labels_on_device; /* 1 if init_labels is a device pointer */
+    int32_t waves;              /* LP_ASYNC only: the order of in-place updates (Sec. 3.3
+                                   leaves it open) is W >= 1 waves, wave(v) = v mod W (v local);
+                                   waves run in order 0..W-1 and store their labels when the
+                                   whole wave has chosen, so a vertex reads this iteration's
+                                   label of a neighbour in an earlier wave and the previous
+                                   iteration's label of any other.  W = 1 equals LP_SYNC;
+                                   W >= n is plain in-place updating in ascending vertex order.
+                                   Deterministic for every W.  Default 31; after clamping to
+                                   the largest graph's n, W must be <= 4096. */
+} lp_rak_params;
+
+/* Outcome of one run. */
+typedef struct {
+    int32_t iterations;   /* iterations executed, including the one that met the test */
+    int32_t converged;    /* 1 if the tolerance test was met, 0 if max_iter stopped it */
+    int64_t last_changed; /* vertices that changed label in the last iteration */
+    float gpu_ms;         /* device time of the iteration loop (CUDA events) */
+} lp_rak_result;
+
+typedef struct lp_graph lp_graph;
+
+/* Fill *p with the defaults: tolerance 0.05 (Sec. 3.2), max_iter 20,
+ * LP_SYNC, strict, iter_offset 0, seed 0, init_labels NULL, waves 31.
+ * Errors: LP_EINVAL if p is NULL. */
+lp_status lp_rak_params_default(lp_rak_params *p);
+
+/* Ingest one graph (Sec. 3.1: undirected, weighted): validate the CSR, copy it
+ * to the device (unless borrowed) and sort its vertices into degree buckets.
+ *   n, m      vertex and stored-entry counts; 0 <= n, 0 <= m < 2^31.
+ *   offsets   int32[n+1]; indices int32[m]; weights int32[m] or NULL.
+ *             Host pointers unless flags has LP_FLAG_DEVICE_PTRS.  The caller
+ *             keeps ownership; nothing is retained after return unless
+ *             LP_FLAG_BORROW is given.
+ *   flags     LP_FLAG_* bits.
+ *   cuda_stream  cudaStream_t used for all work on this graph (NULL = the
+ *             legacy default stream).
+ *   out       receives the new graph handle.
+ * Errors: LP_EINVAL for a NULL argument, n < 0, m out of range, offsets not a
+ * row pointer, an index outside [0, n), a weight < 1, a vertex whose summed
+ * weight is >= 2^31, or (with LP_FLAG_CHECK_SYMMETRIC) an asymmetric CSR;
+ * LP_ENOMEM; LP_ECUDA.  On error *out is left NULL and nothing leaks. */
+lp_status lp_graph_create(int32_t n, int64_t m, const int32_t *offsets, const int32_t *indices,
+                          const int32_t *weights, uint32_t flags, void *cuda_stream,
+                          lp_graph **out);
+
+/* Free the graph and every device buffer it owns (NULL is a no-op). */
+lp_status lp_graph_destroy(lp_graph *g);
+
+/* Vertex and entry counts of a graph.  Errors: LP_EINVAL on NULL. */
+lp_status lp_graph_info(const lp_graph *g, int32_t *n, int64_t *m);
+
+/* Run RAK to convergence (Sec. 3.2; asynchronous variant Sec. 3.3).
+ * The result labels stay on the device (lp_labels_get, lp_modularity).
+ * Returns after the run has finished on the device.
+ * Errors: LP_EINVAL for NULL arguments, tolerance outside [0, 1],
+ * max_iter < 1, mode not LP_SYNC/LP_ASYNC, waves < 1 or too large (LP_ASYNC),
+ * init_labels outside [0, n);
+ * LP_ENOMEM; LP_ECUDA. */
+lp_status lp_rak_run(lp_graph *g, const lp_rak_params *p, lp_rak_result *out);
+
+/* Number of vertices that changed label in each iteration of the last run.
+ * Writes min(capacity, iterations) values to changed and the iteration count
+ * to *count.  Errors: LP_EINVAL on NULL g or count, or changed NULL with
+ * capacity > 0. */
+lp_status lp_rak_history(const lp_graph *g, int64_t *changed, int32_t capacity, int32_t *count);
+
+/* Copy the current labels (n int32 vertex ids) to dst, a host pointer unless
+ * dst_on_device is 1.  Before any run the labels are the unique labels.
+ * Errors: LP_EINVAL on NULL; LP_ECUDA. */
+lp_status lp_labels_get(lp_graph *g, int32_t *dst, int32_t dst_on_device);
+
+/* Modularity (Sec. 1) of a partition of the graph:
+ *   Q = sum_c [ L_c / 2m - (K_c / 2m)^2 ]
+ * with A the stored CSR, k_v = sum_u A_vu, 2m = sum_v k_v, L_c = sum of A_vu
+ * over stored entries with both ends in c, K_c = sum of k_v over c.  L, K_c
+ * and 2m are summed exactly in 64-bit integers and sum_c K_c^2 exactly in 128
+ * bits; Q = L/2m - (sum_c K_c^2)/(2m)^2 is formed in double.  Q = 0 when the
+ * graph has no entries.
+ *   labels  n labels in [0, n) (host pointer unless labels_on_device), or NULL
+ *           for the graph's current labels.
+ * Errors: LP_EINVAL on NULL g/q or a label outside [0, n); LP_ENOMEM; LP_ECUDA. */
+lp_status lp_modularity(lp_graph *g, const int32_t *labels, int32_t labels_on_device, double *q);
+
+/* ---------------------------------------------------------------------------
+ * Batches: many independent graphs in one device arena, iterated together.
+ * Each graph keeps its own convergence test and iteration count; a graph that
+ * has converged stops changing while the others continue.  Labels and vertex
+ * ids are local to each graph.
+ * ------------------------------------------------------------------------- */
+typedef struct lp_batch lp_batch;
+
+typedef struct {
+    int32_t n;
+    int64_t m;
+    const int32_t *offsets; /* host int32[n+1] */
+    const int32_t *indices; /* host int32[m] */
+    const int32_t *weights; /* host int32[m] or NULL (unit) */
+} lp_graph_desc;
+
+/* Ingest `count` graphs (host CSR, validated as in lp_graph_create) into one
+ * device arena.  flags: LP_FLAG_CHECK_SYMMETRIC only.
+ * Errors: LP_EINVAL (bad count or any invalid graph; the message names its
+ * index), LP_ENOMEM, LP_ECUDA. */
+lp_status lp_batch_create(int32_t count, const lp_graph_desc *graphs, uint32_t flags,
+                          void *cuda_stream, lp_batch **out);
+
+/* Free a batch (NULL is a no-op). */
+lp_status lp_batch_destroy(lp_batch *b);
+
+/* Run RAK on every graph of the batch with the same parameters
+ * (init_labels must be NULL).  per_graph[i] receives graph i's outcome
+ * (array of `count` results, may be NULL).
+ * Errors: as lp_rak_run. */
+lp_status lp_batch_run(lp_batch *b, const lp_rak_params *p, lp_rak_result *per_graph);
+
+/* Labels of graph `index` after the last lp_batch_run (n_index int32).
+ * Errors: LP_EINVAL on NULL or index out of range; LP_ECUDA. */
+lp_status lp_batch_labels_get(lp_batch *b, int32_t index, int32_t *dst, int32_t dst_on_device);
+
+/* Modularity of graph `index` under its current labels (see lp_modularity).
+ * Errors: LP_EINVAL; LP_ENOMEM; LP_ECUDA. */
+lp_status lp_batch_modularity(lp_batch *b, int32_t index, double *q);
+
+/* ---------------------------------------------------------------------------
+ * Diagnostics
+ * ------------------------------------------------------------------------- */
+
+/* Device time of sweep launches, per kernel.  While profiling is enabled,
+ * every sweep launch is bracketed by two CUDA events on the graph's stream
+ * (a small overhead); the statistics accumulate across runs and graphs until
+ * lp_profile_reset. */
+typedef struct {
+    char name[32];    /* "sweep_small", "sweep_warp", "sweep_cta", "sweep_hub" */
+    int64_t launches; /* profiled launches */
+    double total_ms;  /* summed event time */
+    double vertices;  /* vertices scheduled (summed over launches) */
+    double entries;   /* CSR entries scheduled (summed over launches) */
+    double bytes;     /* algorithmic HBM bytes: 12 per vertex (row pointer, own
+                         label read, label write) + 4 per entry (column index)
+                         + 4 per entry for weighted graphs */
+} lp_kernel_stat;
+
+/* Turn per-kernel profiling on (1) or off (0).  Always LP_OK. */
+lp_status lp_profile_enable(int32_t on);
+
+/* Clear the accumulated statistics.  Always LP_OK. */
+lp_status lp_profile_reset(void);
+
+/* Copy up to `capacity` kernel statistics to out; *count receives how many
+ * kernels exist (4).  Errors: LP_EINVAL on NULL count, or NULL out with
+ * capacity > 0. */
+lp_status lp_profile_read(lp_kernel_stat *out, int32_t capacity, int32_t *count);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *lp_last_error(void);
+
+/* Number of kernels this library has launched in this process. */
+int64_t lp_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LP_H */

@@ -57,7 +57,8 @@ def _load():
         lib.oracle_rak.restype = ctypes.c_int
         lib.oracle_rak.argtypes = [ctypes.c_int32, _i32p, _i32p, _i32p, ctypes.c_double,
                                    ctypes.c_int32, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
-                                   ctypes.c_int32, _i32p, _i32p, _i32p, _i32p, _i64p]
+                                   ctypes.c_int32, _i32p, ctypes.c_int32, _i32p, _i32p, _i32p,
+                                   _i64p]
         lib.oracle_modularity.restype = ctypes.c_double
         lib.oracle_modularity.argtypes = [ctypes.c_int32, _i32p, _i32p, _i32p, _i32p, _i64p,
                                           _i64p, _u64p]
@@ -98,12 +99,13 @@ def tie_hash(seed: int, t: int, v: int, label: int) -> int:
 
 
 def rak(offsets, indices, weights=None, tolerance=0.05, max_iter=20, mode="sync",
-        strict=True, seed=0, iter_offset=0, init_labels=None):
+        strict=True, seed=0, iter_offset=0, init_labels=None, waves=0):
     """Run RAK to convergence (Sec. 3.2).
 
     Returns ``(labels, iterations, converged, changed_per_iteration)``.
-    ``mode`` is ``"sync"`` (double buffer) or ``"async"`` (in place, ascending
-    vertex order).
+    ``mode`` is ``"sync"`` (double buffer) or ``"async"`` (in place, Sec. 3.3,
+    in ``waves`` waves of vertices v mod W; 0 = every vertex its own wave,
+    i.e. ascending vertex order).
     """
     offsets = _arr(offsets)
     indices = _arr(indices)
@@ -121,7 +123,7 @@ def rak(offsets, indices, weights=None, tolerance=0.05, max_iter=20, mode="sync"
     rc = _load().oracle_rak(n, _ptr(offsets), _ptr(indices), _ptr(weights), float(tolerance),
                             int(max_iter), 1 if mode == "async" else 0, 1 if strict else 0,
                             ctypes.c_uint64(seed & (2**64 - 1)), int(iter_offset), _ptr(init),
-                            _ptr(labels), ctypes.byref(iters), ctypes.byref(conv),
+                            int(waves), _ptr(labels), ctypes.byref(iters), ctypes.byref(conv),
                             _ptr(hist, _i64p))
     if rc != 0:
         raise ValueError("oracle_rak rejected its arguments")

@@ -34,7 +34,13 @@
  *   - converged iff changed <= tolerance * N, evaluated in double; the
  *     iteration that meets the test is counted.
  *   - synchronous = every vertex reads the labels of the previous iteration
- *     (double buffer); asynchronous = in place, vertices in ascending order.
+ *     (double buffer).
+ *   - asynchronous = in place, in W waves: wave(v) = v mod W, waves run in
+ *     order 0..W-1 and a wave's new labels are stored once the whole wave has
+ *     chosen, so a vertex sees this iteration's labels of neighbours in earlier
+ *     waves and the previous iteration's labels of the others.  W >= n (the
+ *     default, W = 0) puts every vertex in its own wave: plain in-place
+ *     updates in ascending vertex order.  W = 1 is the synchronous rule.
  *   - the CSR is taken as given: a stored entry (v,u,w) is A_vu = w, a stored
  *     self-loop counts the vertex's own current label, duplicate entries add.
  */
@@ -192,14 +198,16 @@ int oracle_choose_many(int32_t n, const int32_t *offsets, const int32_t *indices
  * changed_hist[i] receives the number of vertices that changed in iteration i
  * (capacity max_iter, may be NULL).
  * iter_offset shifts the iteration index seen by the tie hash (resume).
+ * waves: asynchronous wave count W (0 = every vertex its own wave).
  * Returns 0, or -1 on bad arguments / allocation failure. */
 int oracle_rak(int32_t n, const int32_t *offsets, const int32_t *indices,
                const int32_t *weights, double tolerance, int32_t max_iter, int async_mode,
                int strict, uint64_t seed, int32_t iter_offset, const int32_t *init_labels,
-               int32_t *labels, int32_t *out_iterations, int32_t *out_converged,
+               int32_t waves, int32_t *labels, int32_t *out_iterations, int32_t *out_converged,
                int64_t *changed_hist)
 {
-    if (n < 0 || max_iter < 1 || !(tolerance >= 0.0 && tolerance <= 1.0)) return -1;
+    if (n < 0 || max_iter < 1 || waves < 0 || !(tolerance >= 0.0 && tolerance <= 1.0)) return -1;
+    int32_t w_count = (waves == 0 || waves > n) ? (n > 0 ? n : 1) : waves;
     for (int32_t v = 0; v < n; ++v) labels[v] = init_labels ? init_labels[v] : v;
     *out_iterations = 0;
     *out_converged = 0;
@@ -215,12 +223,16 @@ int oracle_rak(int32_t n, const int32_t *offsets, const int32_t *indices,
         int64_t t = (int64_t)it + iter_offset;
         int64_t changed = 0;
         if (async_mode) {
-            /* in place, ascending vertex order: later vertices read new labels */
-            for (int32_t v = 0; v < n; ++v) {
-                int32_t c = oracle_choose_with(&m, v, offsets, indices, weights, labels,
-                                               strict, seed, t);
-                if (c != labels[v]) ++changed;
-                labels[v] = c;
+            /* waves in order; a wave chooses from `labels`, which already holds
+             * the new labels of the earlier waves, then stores its own */
+            for (int32_t k = 0; k < w_count; ++k) {
+                for (int32_t v = k; v < n; v += w_count)
+                    next[v] = oracle_choose_with(&m, v, offsets, indices, weights, labels, strict,
+                                                 seed, t);
+                for (int32_t v = k; v < n; v += w_count) {
+                    if (next[v] != labels[v]) ++changed;
+                    labels[v] = next[v];
+                }
             }
         } else {
             /* every vertex reads the previous iteration's labels */

@@ -1,0 +1,371 @@
+"""ctypes binding of ``liblp.so`` (declared in ``include/lp.h``).
+
+Argument marshalling only: every step of label propagation and modularity
+runs in the library's CUDA kernels.  Arrays may be numpy arrays (host) or
+torch tensors (host or CUDA); CUDA tensors are passed as device pointers
+together with the current torch stream.  There is no fallback: if the library
+is missing or cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "liblp.so")
+
+LP_OK, LP_EINVAL, LP_ENOMEM, LP_ECUDA, LP_ETIMEOUT, LP_ENOTREADY = range(6)
+LP_SYNC, LP_ASYNC = 0, 1
+LP_FLAG_DEVICE_PTRS, LP_FLAG_CHECK_SYMMETRIC, LP_FLAG_BORROW = 1, 2, 4
+
+_STATUS = {LP_EINVAL: "LP_EINVAL", LP_ENOMEM: "LP_ENOMEM", LP_ECUDA: "LP_ECUDA",
+           LP_ETIMEOUT: "LP_ETIMEOUT", LP_ENOTREADY: "LP_ENOTREADY"}
+
+
+class LPError(RuntimeError):
+    """A library call returned a status other than LP_OK."""
+
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class lp_rak_params(ctypes.Structure):
+    _fields_ = [("tolerance", ctypes.c_double), ("max_iter", ctypes.c_int32),
+                ("mode", ctypes.c_int32), ("strict", ctypes.c_int32),
+                ("iter_offset", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("init_labels", ctypes.c_void_p), ("init_labels_on_device", ctypes.c_int32),
+                ("waves", ctypes.c_int32)]
+
+
+class lp_rak_result(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("last_changed", ctypes.c_int64), ("gpu_ms", ctypes.c_float)]
+
+    def as_dict(self):
+        return {"iterations": self.iterations, "converged": bool(self.converged),
+                "last_changed": self.last_changed, "gpu_ms": self.gpu_ms}
+
+
+class lp_graph_desc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("m", ctypes.c_int64), ("offsets", ctypes.c_void_p),
+                ("indices", ctypes.c_void_p), ("weights", ctypes.c_void_p)]
+
+
+class lp_kernel_stat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64),
+                ("total_ms", ctypes.c_double), ("vertices", ctypes.c_double),
+                ("entries", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
+_lib = None
+
+# Every symbol include/lp.h declares, with its ctypes signature.
+_P = ctypes.c_void_p
+SIGNATURES = {
+    "lp_rak_params_default": (ctypes.c_int, [ctypes.POINTER(lp_rak_params)]),
+    "lp_graph_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, _P, _P, _P,
+                                       ctypes.c_uint32, _P, ctypes.POINTER(_P)]),
+    "lp_graph_destroy": (ctypes.c_int, [_P]),
+    "lp_graph_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32),
+                                     ctypes.POINTER(ctypes.c_int64)]),
+    "lp_rak_run": (ctypes.c_int, [_P, ctypes.POINTER(lp_rak_params),
+                                  ctypes.POINTER(lp_rak_result)]),
+    "lp_rak_history": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32,
+                                      ctypes.POINTER(ctypes.c_int32)]),
+    "lp_labels_get": (ctypes.c_int, [_P, _P, ctypes.c_int32]),
+    "lp_modularity": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]),
+    "lp_batch_create": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(lp_graph_desc),
+                                       ctypes.c_uint32, _P, ctypes.POINTER(_P)]),
+    "lp_batch_destroy": (ctypes.c_int, [_P]),
+    "lp_batch_run": (ctypes.c_int, [_P, ctypes.POINTER(lp_rak_params),
+                                    ctypes.POINTER(lp_rak_result)]),
+    "lp_batch_labels_get": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int32]),
+    "lp_batch_modularity": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]),
+    "lp_profile_enable": (ctypes.c_int, [ctypes.c_int32]),
+    "lp_profile_reset": (ctypes.c_int, []),
+    "lp_profile_read": (ctypes.c_int, [ctypes.POINTER(lp_kernel_stat), ctypes.c_int32,
+                                       ctypes.POINTER(ctypes.c_int32)]),
+    "lp_last_error": (ctypes.c_char_p, []),
+    "lp_launch_count": (ctypes.c_int64, []),
+}
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load ``liblp.so`` (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(
+                f"{path} is missing: build it with paper_2301_09125_gb300.build.build() "
+                "(nvcc, sm_103a); there is no CPU fallback")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(status: int):
+    if status != LP_OK:
+        raise LPError(status, load().lp_last_error().decode(errors="replace"))
+
+
+# ---------------------------------------------------------------- marshalling
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _int32_buffer(x, name):
+    """(pointer, on_device, keepalive) of an int32 array-like."""
+    if x is None:
+        return None, False, None
+    if _is_torch(x):
+        import torch
+        if x.dtype != torch.int32:
+            raise TypeError(f"{name} must be int32")
+        if not x.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        return x.data_ptr(), bool(x.is_cuda), x
+    a = np.ascontiguousarray(x, dtype=np.int32)
+    return a.ctypes.data, False, a
+
+
+def _stream_of(*tensors):
+    for t in tensors:
+        if t is not None and _is_torch(t) and t.is_cuda:
+            import torch
+            return torch.cuda.current_stream(t.device).cuda_stream
+    return None
+
+
+def lp_rak_params_default() -> lp_rak_params:
+    p = lp_rak_params()
+    _check(load().lp_rak_params_default(ctypes.byref(p)))
+    return p
+
+
+def make_params(tolerance=0.05, max_iter=20, mode="sync", strict=True, seed=0, iter_offset=0,
+                init_labels=None, waves=None) -> tuple:
+    """(lp_rak_params, keepalive) from Python values."""
+    p = lp_rak_params_default()
+    p.tolerance = float(tolerance)
+    p.max_iter = int(max_iter)
+    p.mode = {"sync": LP_SYNC, "async": LP_ASYNC}[mode] if isinstance(mode, str) else int(mode)
+    p.strict = 1 if strict else 0
+    p.seed = int(seed) & (2**64 - 1)
+    p.iter_offset = int(iter_offset)
+    if waves is not None:
+        p.waves = int(waves)
+    ptr, on_dev, keep = _int32_buffer(init_labels, "init_labels")
+    p.init_labels = ptr
+    p.init_labels_on_device = 1 if on_dev else 0
+    return p, keep
+
+
+# ---------------------------------------------------------------- graphs
+def lp_graph_create(offsets, indices, weights=None, check_symmetric=False, borrow=False,
+                    stream=None) -> int:
+    """Create a graph from a CSR; returns the opaque handle.
+
+    All three arrays must live on the same side (host numpy/torch-CPU, or CUDA
+    tensors).  ``borrow=True`` (CUDA tensors only) keeps references to the
+    caller's memory instead of copying; the caller must keep the tensors alive
+    and unchanged until ``lp_graph_destroy``.
+    """
+    po, do, ko = _int32_buffer(offsets, "offsets")
+    pi, di, ki = _int32_buffer(indices, "indices")
+    pw, dw, kw = _int32_buffer(weights, "weights")
+    sides = {do, di} | ({dw} if weights is not None else set())
+    if len(sides) != 1:
+        raise ValueError("offsets, indices and weights must all be host or all be device arrays")
+    on_dev = do
+    n = (ko.shape[0] if hasattr(ko, "shape") else len(ko)) - 1
+    m = ki.shape[0] if hasattr(ki, "shape") else len(ki)
+    flags = (LP_FLAG_DEVICE_PTRS if on_dev else 0) | (LP_FLAG_CHECK_SYMMETRIC if check_symmetric else 0)
+    if borrow:
+        if not on_dev:
+            raise ValueError("borrow needs CUDA tensors")
+        flags |= LP_FLAG_BORROW
+    if stream is None:
+        stream = _stream_of(offsets, indices, weights)
+    h = ctypes.c_void_p()
+    _check(load().lp_graph_create(int(n), int(m), po, pi, pw, flags, stream, ctypes.byref(h)))
+    return h.value
+
+
+def lp_graph_destroy(handle: Optional[int]) -> None:
+    if handle:
+        _check(load().lp_graph_destroy(handle))
+
+
+def lp_graph_info(handle: int):
+    n = ctypes.c_int32()
+    m = ctypes.c_int64()
+    _check(load().lp_graph_info(handle, ctypes.byref(n), ctypes.byref(m)))
+    return n.value, m.value
+
+
+def lp_rak_run(handle: int, params: Optional[lp_rak_params] = None, **kw) -> lp_rak_result:
+    """Run RAK on a graph.  Pass an ``lp_rak_params`` or keyword arguments of
+    ``make_params``."""
+    keep = None
+    if params is None:
+        params, keep = make_params(**kw)
+    r = lp_rak_result()
+    _check(load().lp_rak_run(handle, ctypes.byref(params), ctypes.byref(r)))
+    del keep
+    return r
+
+
+def lp_rak_history(handle: int) -> np.ndarray:
+    cnt = ctypes.c_int32()
+    _check(load().lp_rak_history(handle, None, 0, ctypes.byref(cnt)))
+    out = np.zeros(cnt.value, dtype=np.int64)
+    _check(load().lp_rak_history(handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                 cnt.value, ctypes.byref(cnt)))
+    return out
+
+
+def lp_labels_get(handle: int, out=None):
+    """Current labels: into ``out`` (numpy or torch, host or CUDA) or a new
+    numpy array."""
+    n, _ = lp_graph_info(handle)
+    if out is None:
+        out = np.empty(n, dtype=np.int32)
+    ptr, on_dev, keep = _int32_buffer(out, "out")
+    if keep is not out:
+        raise ValueError("out must be a contiguous int32 array")
+    _check(load().lp_labels_get(handle, ptr, 1 if on_dev else 0))
+    return out
+
+
+def lp_modularity(handle: int, labels=None) -> float:
+    """Modularity of ``labels`` (or of the graph's current labels)."""
+    ptr, on_dev, keep = _int32_buffer(labels, "labels")
+    q = ctypes.c_double()
+    _check(load().lp_modularity(handle, ptr, 1 if on_dev else 0, ctypes.byref(q)))
+    del keep
+    return q.value
+
+
+# ---------------------------------------------------------------- batches
+def lp_batch_create(graphs: Sequence, check_symmetric=False, stream=None) -> int:
+    """Create a batch from host CSR triples ``(offsets, indices, weights|None)``."""
+    descs = (lp_graph_desc * len(graphs))()
+    keep = []
+    for i, g in enumerate(graphs):
+        off, idx, w = g[0], g[1], (g[2] if len(g) > 2 else None)
+        off = np.ascontiguousarray(off, dtype=np.int32)
+        idx = np.ascontiguousarray(idx, dtype=np.int32)
+        w = None if w is None else np.ascontiguousarray(w, dtype=np.int32)
+        keep += [off, idx, w]
+        descs[i].n = off.shape[0] - 1
+        descs[i].m = idx.shape[0]
+        descs[i].offsets = off.ctypes.data
+        descs[i].indices = idx.ctypes.data
+        descs[i].weights = None if w is None else w.ctypes.data
+    h = ctypes.c_void_p()
+    _check(load().lp_batch_create(len(graphs), descs,
+                                  LP_FLAG_CHECK_SYMMETRIC if check_symmetric else 0, stream,
+                                  ctypes.byref(h)))
+    return h.value
+
+
+def lp_batch_destroy(handle: Optional[int]) -> None:
+    if handle:
+        _check(load().lp_batch_destroy(handle))
+
+
+def lp_batch_run(handle: int, count: int, params: Optional[lp_rak_params] = None, **kw):
+    """Run every graph of a batch; returns the per-graph results."""
+    if params is None:
+        params, _ = make_params(**kw)
+    res = (lp_rak_result * count)()
+    _check(load().lp_batch_run(handle, ctypes.byref(params), res))
+    return list(res)
+
+
+def lp_batch_labels_get(handle: int, index: int, n: int, out=None):
+    if out is None:
+        out = np.empty(n, dtype=np.int32)
+    ptr, on_dev, keep = _int32_buffer(out, "out")
+    _check(load().lp_batch_labels_get(handle, index, ptr, 1 if on_dev else 0))
+    return out
+
+
+def lp_batch_modularity(handle: int, index: int) -> float:
+    q = ctypes.c_double()
+    _check(load().lp_batch_modularity(handle, index, ctypes.byref(q)))
+    return q.value
+
+
+def lp_profile_enable(on: bool = True) -> None:
+    _check(load().lp_profile_enable(1 if on else 0))
+
+
+def lp_profile_reset() -> None:
+    _check(load().lp_profile_reset())
+
+
+def lp_profile_read() -> dict:
+    """Per-kernel sweep statistics: name -> dict(launches, total_ms, vertices,
+    entries, bytes)."""
+    stats = (lp_kernel_stat * 8)()
+    cnt = ctypes.c_int32()
+    _check(load().lp_profile_read(stats, 8, ctypes.byref(cnt)))
+    return {st.name.decode(): {"launches": st.launches, "total_ms": st.total_ms,
+                               "vertices": st.vertices, "entries": st.entries, "bytes": st.bytes}
+            for st in stats[:cnt.value]}
+
+
+def lp_last_error() -> str:
+    return load().lp_last_error().decode(errors="replace")
+
+
+def lp_launch_count() -> int:
+    return int(load().lp_launch_count())
+
+
+# ---------------------------------------------------------------- convenience
+class Graph:
+    """Owning wrapper of an ``lp_graph`` handle (destroyed on close / GC)."""
+
+    def __init__(self, offsets, indices, weights=None, **kw):
+        self._keep = (offsets, indices, weights) if kw.get("borrow") else None
+        self.handle = lp_graph_create(offsets, indices, weights, **kw)
+        self.n, self.m = lp_graph_info(self.handle)
+
+    def rak(self, **kw) -> lp_rak_result:
+        return lp_rak_run(self.handle, **kw)
+
+    def labels(self, out=None):
+        return lp_labels_get(self.handle, out)
+
+    def history(self) -> np.ndarray:
+        return lp_rak_history(self.handle)
+
+    def modularity(self, labels=None) -> float:
+        return lp_modularity(self.handle, labels)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lp_graph_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

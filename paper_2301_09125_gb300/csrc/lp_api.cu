@@ -1,0 +1,1056 @@
+// C ABI of the library (declared in include/lp.h).
+//
+// A graph (lp_graph) and a batch (lp_batch) share one device representation,
+// GraphSet: an arena of G >= 1 graphs with concatenated CSR arrays, two label
+// buffers, degree-bucketed vertex lists and per-iteration changed counters.
+// lp_rak_run / lp_batch_run drive the iteration of Sec. 3.2: per iteration one
+// launch per non-empty degree bucket, then a read of the changed counters and
+// the tolerance test (changed <= tolerance * n, in double) on the host.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "lp.h"
+#include "lp_internal.cuh"
+
+namespace {
+
+thread_local std::string g_err;
+std::atomic<int64_t> g_launches{0};
+
+// Per-kernel sweep statistics (lp_profile_*): while enabled, every sweep
+// launch is bracketed by CUDA events on the graph's stream.
+const char *const KERNEL_NAMES[4] = {"sweep_small", "sweep_warp", "sweep_cta", "sweep_hub"};
+struct KernelStat {
+    int64_t launches = 0;
+    double ms = 0, vertices = 0, entries = 0, bytes = 0;
+};
+std::mutex g_prof_mu;
+std::atomic<bool> g_prof_on{false};
+KernelStat g_prof[4];
+
+lp_status fail(lp_status s, const std::string &msg)
+{
+    g_err = msg;
+    return s;
+}
+
+std::string cuda_msg(const char *what, cudaError_t e)
+{
+    return std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+}
+
+#define LP_CU(call)                                                  \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
+        if (e_ != cudaSuccess) return fail(LP_ECUDA, cuda_msg(#call, e_)); \
+    } while (0)
+
+#define LP_TRY(call)                          \
+    do {                                      \
+        lp_status s_ = (call);                \
+        if (s_ != LP_OK) return s_;           \
+    } while (0)
+
+// Adds the kernels launched in a scope to the process-wide counter.
+struct Launches {
+    int64_t n = 0;
+    ~Launches() { g_launches += n; }
+};
+
+// Switches to a device for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int now = -1;
+        if (prev >= 0 && cudaGetDevice(&now) == cudaSuccess && now != prev) cudaSetDevice(prev);
+    }
+};
+
+// Device memory comes from one stream-ordered pool per device that keeps
+// freed blocks for reuse (release threshold = all), so creating and
+// destroying graphs in a loop does not pay cudaMalloc / cudaFree each time.
+cudaMemPool_t device_pool(int dev)
+{
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {};
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev < 0 || dev >= 64) return nullptr;
+    if (!pools[dev]) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        pools[dev] = pool;
+    }
+    return pools[dev];
+}
+
+template <typename T>
+lp_status dev_alloc(T **p, int64_t count, const char *what, cudaStream_t st, int dev)
+{
+    *p = nullptr;
+    if (count <= 0) count = 1;
+    cudaMemPool_t pool = device_pool(dev);
+    cudaError_t e = pool ? cudaMallocFromPoolAsync((void **)p, (size_t)count * sizeof(T), pool, st)
+                         : cudaMalloc((void **)p, (size_t)count * sizeof(T));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? LP_ENOMEM : LP_ECUDA,
+                    std::string("device allocation of ") + what + " failed: " +
+                        cudaGetErrorString(e));
+    }
+    return LP_OK;
+}
+
+template <typename T>
+lp_status host_alloc(T **p, int64_t count, const char *what)
+{
+    *p = nullptr;
+    if (count <= 0) count = 1;
+    cudaError_t e = cudaMallocHost((void **)p, (size_t)count * sizeof(T));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return fail(LP_ENOMEM, std::string("pinned host allocation of ") + what + " failed");
+    }
+    return LP_OK;
+}
+
+uint64_t next_pow2(uint64_t x)
+{
+    uint64_t p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+const char *ingest_what(int32_t code)
+{
+    switch (code) {
+    case lp::ING_OFF_FIRST: return "offsets[0] must be 0";
+    case lp::ING_OFF_ORDER: return "offsets must be non-decreasing (first bad vertex)";
+    case lp::ING_OFF_LAST: return "offsets[n] must equal m";
+    case lp::ING_INDEX: return "column index outside [0, n) (entry)";
+    case lp::ING_WEIGHT: return "weight < 1 (entry)";
+    case lp::ING_WDEG: return "summed weight of a vertex reaches 2^31 (vertex)";
+    case lp::ING_ASYM: return "CSR is not symmetric";
+    case lp::ING_LABEL: return "label outside [0, n) (vertex)";
+    default: return "invalid input";
+    }
+}
+
+// Sorted (v, u, summed w) triples of a CSR, duplicates merged.
+struct Entry {
+    int32_t v, u;
+    int64_t w;
+};
+
+bool host_symmetric(int32_t n, const int32_t *off, const int32_t *idx, const int32_t *wts)
+{
+    std::vector<Entry> a, b;
+    const int64_t m = off[n];
+    a.reserve((size_t)m);
+    b.reserve((size_t)m);
+    for (int32_t v = 0; v < n; ++v)
+        for (int32_t e = off[v]; e < off[v + 1]; ++e) {
+            const int64_t w = wts ? wts[e] : 1;
+            a.push_back({v, idx[e], w});
+            b.push_back({idx[e], v, w});
+        }
+    auto less = [](const Entry &x, const Entry &y) { return x.v != y.v ? x.v < y.v : x.u < y.u; };
+    auto merge = [&](std::vector<Entry> &x) {
+        std::sort(x.begin(), x.end(), less);
+        size_t k = 0;
+        for (size_t i = 0; i < x.size(); ++i) {
+            if (k > 0 && x[k - 1].v == x[i].v && x[k - 1].u == x[i].u)
+                x[k - 1].w += x[i].w;
+            else
+                x[k++] = x[i];
+        }
+        x.resize(k);
+    };
+    merge(a);
+    merge(b);
+    if (a.size() != b.size()) return false;
+    for (size_t i = 0; i < a.size(); ++i)
+        if (a[i].v != b[i].v || a[i].u != b[i].u || a[i].w != b[i].w) return false;
+    return true;
+}
+
+
+}  // namespace
+
+// ----------------------------------------------------------------------------
+// Device representation shared by graphs and batches
+// ----------------------------------------------------------------------------
+namespace lp {
+
+struct GraphSet {
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t st = nullptr;
+    int32_t G = 0;
+    int32_t nv = 0;  // total vertices
+    int64_t ne = 0;  // total entries
+    int32_t *off = nullptr, *idx = nullptr, *wts = nullptr;
+    bool own_off = true, own_idx = true, own_wts = true;
+    int32_t *lab[2] = {nullptr, nullptr};
+    int32_t *list = nullptr;
+    int64_t bb[NUM_BUCKETS] = {0, 0, 0, 0}, bl[NUM_BUCKETS] = {0, 0, 0, 0};
+    int64_t be[NUM_BUCKETS] = {0, 0, 0, 0};  // summed degree of each bucket
+    // wave-partitioned bucket lists for asynchronous runs (built per wave count)
+    int32_t *wlist = nullptr;
+    int64_t *d_wtot = nullptr;
+    int32_t wl_waves = 0;
+    std::vector<int64_t> wstart, wcount;  // per class b * waves + k
+    int32_t max_n = 0;
+    int32_t hub_max_deg = 0;
+    // multi-graph bookkeeping (device copies are null for a single graph)
+    int32_t *vgraph = nullptr, *g_vbase = nullptr, *g_active = nullptr, *g_n = nullptr;
+    int64_t *g_ebase = nullptr;
+    std::vector<int32_t> h_n, h_vbase;
+    std::vector<int64_t> h_m, h_ebase;
+    // iteration state
+    int32_t *changed = nullptr, *h_changed = nullptr, *h_active = nullptr;
+    int64_t changed_cap = 0;
+    std::vector<int> final_buf;
+    std::vector<lp_rak_result> results;
+    std::vector<int64_t> history;  // graph 0
+    // hub overflow tables
+    int32_t *gt_key = nullptr, *gt_sum = nullptr;
+    uint32_t *gt_np = nullptr;
+    int64_t gt_slots = 0;
+    // modularity and label staging scratch
+    unsigned long long *kc = nullptr, *macc = nullptr, *mpart = nullptr, *h_macc = nullptr;
+    int64_t kc_cap = 0;
+    int mpart_blocks = 0;
+    int32_t *lab_tmp = nullptr;
+    IngestOut *d_ing = nullptr, *h_ing = nullptr;
+    int64_t *d_counts = nullptr, *h_counts = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::vector<cudaEvent_t> prof_ev;  // start/stop pairs of profiled launches
+
+    ~GraphSet() { release(); }
+
+    void release()
+    {
+        if (st) cudaStreamSynchronize(st);
+        cudaStream_t s0 = st;
+        auto f = [s0](void *p) {
+            if (p) cudaFreeAsync(p, s0);
+        };
+        auto fh = [](void *p) {
+            if (p) cudaFreeHost(p);
+        };
+        if (own_off) f(off);
+        if (own_idx) f(idx);
+        if (own_wts) f(wts);
+        off = idx = wts = nullptr;
+        f(lab[0]);
+        f(lab[1]);
+        f(list);
+        f(wlist);
+        f(d_wtot);
+        f(vgraph);
+        f(g_vbase);
+        f(g_active);
+        f(g_n);
+        f(g_ebase);
+        f(changed);
+        fh(h_changed);
+        fh(h_active);
+        f(gt_key);
+        f(gt_sum);
+        f(gt_np);
+        f(kc);
+        f(macc);
+        f(mpart);
+        fh(h_macc);
+        f(lab_tmp);
+        f(d_ing);
+        fh(h_ing);
+        f(d_counts);
+        fh(h_counts);
+        if (ev0) cudaEventDestroy(ev0);
+        if (ev1) cudaEventDestroy(ev1);
+        lab[0] = lab[1] = list = wlist = vgraph = g_vbase = g_active = g_n = nullptr;
+        d_wtot = nullptr;
+        g_ebase = nullptr;
+        changed = h_changed = h_active = nullptr;
+        gt_key = gt_sum = nullptr;
+        gt_np = nullptr;
+        kc = macc = mpart = h_macc = nullptr;
+        lab_tmp = nullptr;
+        d_ing = h_ing = nullptr;
+        d_counts = h_counts = nullptr;
+        ev0 = ev1 = nullptr;
+        for (cudaEvent_t e : prof_ev) cudaEventDestroy(e);
+        prof_ev.clear();
+        cudaStreamSynchronize(st);
+    }
+
+    lp_status begin(void *stream)
+    {
+        LP_CU(cudaGetDevice(&device));
+        LP_CU(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, device));
+        st = (cudaStream_t)stream;
+        static std::atomic<uint64_t> prepared{0};
+        if (device < 64 && !(prepared.load() & (1ull << device))) {
+            if (sweep_prepare() != 0 || wave_prepare() != 0)
+                return fail(LP_ECUDA, "setting kernel attributes failed");
+            prepared |= (1ull << device);
+        }
+        LP_TRY(dev_alloc(&d_ing, 1, "ingest status", st, device));
+        LP_TRY(host_alloc(&h_ing, 1, "ingest status"));
+        LP_TRY(dev_alloc(&d_counts, 3 * NUM_BUCKETS, "bucket counts", st, device));
+        LP_TRY(host_alloc(&h_counts, 3 * NUM_BUCKETS, "bucket counts"));
+        LP_TRY(dev_alloc(&macc, 2, "modularity accumulators", st, device));
+        LP_TRY(host_alloc(&h_macc, 2, "modularity accumulators"));
+        LP_CU(cudaEventCreate(&ev0));
+        LP_CU(cudaEventCreate(&ev1));
+        return LP_OK;
+    }
+
+    lp_status read_ingest(int graph_index)
+    {
+        LP_CU(cudaMemcpyAsync(h_ing, d_ing, sizeof(IngestOut), cudaMemcpyDeviceToHost, st));
+        LP_CU(cudaStreamSynchronize(st));
+        if (h_ing->err != ING_OK) {
+            char buf[256];
+            if (graph_index >= 0)
+                snprintf(buf, sizeof buf, "graph %d: %s %d", graph_index, ingest_what(h_ing->err),
+                         h_ing->err_at);
+            else
+                snprintf(buf, sizeof buf, "%s %d", ingest_what(h_ing->err), h_ing->err_at);
+            return fail(LP_EINVAL, buf);
+        }
+        return LP_OK;
+    }
+
+    // validate graph g's device CSR (already in place)
+    lp_status validate(int32_t g, const int32_t *o, const int32_t *ix, const int32_t *w, int32_t n,
+                       int64_t m, int graph_index)
+    {
+        Launches L;
+        if (ingest_validate(o, ix, w, n, m, d_ing, st, &L.n) != 0)
+            return fail(LP_ECUDA, cuda_msg("validation launch", cudaGetLastError()));
+        LP_TRY(read_ingest(graph_index));
+        if ((int64_t)h_ing->max_deg * (int64_t)h_ing->max_w >= 2147483648LL) {
+            if (ingest_check_wdeg(o, w, n, d_ing, st, &L.n) != 0)
+                return fail(LP_ECUDA, cuda_msg("weight-sum launch", cudaGetLastError()));
+            LP_TRY(read_ingest(graph_index));
+        }
+        (void)g;
+        return LP_OK;
+    }
+
+    lp_status bucket()
+    {
+        Launches L;
+        int32_t *blk = nullptr;
+        LP_TRY(dev_alloc(&blk, (int64_t)(ingest_bucket_scratch_bytes(nv) / sizeof(int32_t)),
+                         "bucket scratch", st, device));
+        lp_status s = LP_OK;
+        if (dev_alloc(&list, nv, "bucket list", st, device) != LP_OK) {
+            cudaFreeAsync(blk, st);
+            return LP_ENOMEM;
+        }
+        if (ingest_bucket(off, nv, vgraph, g_vbase, list, blk, d_counts, st, &L.n) != 0)
+            s = fail(LP_ECUDA, cuda_msg("bucketing launch", cudaGetLastError()));
+        if (s == LP_OK) {
+            cudaError_t e = cudaMemcpyAsync(h_counts, d_counts, 3 * NUM_BUCKETS * sizeof(int64_t),
+                                            cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) s = fail(LP_ECUDA, cuda_msg("bucket counts", e));
+        }
+        cudaFreeAsync(blk, st);
+        if (s != LP_OK) return s;
+        for (int c = 0; c < NUM_BUCKETS; ++c) {
+            bl[c] = h_counts[c];
+            bb[c] = h_counts[NUM_BUCKETS + c];
+            be[c] = h_counts[2 * NUM_BUCKETS + c];
+        }
+        // hub vertices: largest degree first, so the static CTA assignment of
+        // the hub kernel balances
+        if (bl[3] > 0) {
+            int32_t *deg = nullptr;
+            LP_TRY(dev_alloc(&deg, bl[3], "hub degrees", st, device));
+            std::vector<int32_t> hv((size_t)bl[3]), hd((size_t)bl[3]);
+            cudaError_t e = cudaSuccess;
+            if (degrees_of(off, vgraph, list + bb[3], bl[3], deg, st, &L.n) != 0)
+                e = cudaGetLastError();
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(hv.data(), list + bb[3], bl[3] * sizeof(int32_t),
+                                    cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(hd.data(), deg, bl[3] * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                    st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            cudaFreeAsync(deg, st);
+            if (e != cudaSuccess) return fail(LP_ECUDA, cuda_msg("hub degrees", e));
+            std::vector<int64_t> order((size_t)bl[3]);
+            for (size_t i = 0; i < order.size(); ++i) order[i] = (int64_t)i;
+            std::stable_sort(order.begin(), order.end(),
+                             [&](int64_t x, int64_t y) { return hd[x] > hd[y]; });
+            std::vector<int32_t> sorted(order.size());
+            for (size_t i = 0; i < order.size(); ++i) sorted[i] = hv[order[i]];
+            hub_max_deg = hd[order[0]];
+            LP_CU(cudaMemcpyAsync(list + bb[3], sorted.data(), bl[3] * sizeof(int32_t),
+                                  cudaMemcpyHostToDevice, st));
+            // one overflow table per hub CTA, sized for the largest hub
+            gt_slots = (int64_t)next_pow2(2ull * (uint64_t)hub_max_deg);
+            const int64_t total = gt_slots * hub_grid(bl[3], num_sms);
+            LP_TRY(dev_alloc(&gt_key, total, "hub overflow keys", st, device));
+            LP_TRY(dev_alloc(&gt_sum, total, "hub overflow sums", st, device));
+            LP_TRY(dev_alloc(&gt_np, total, "hub overflow positions", st, device));
+            LP_CU(cudaMemsetAsync(gt_key, 0xFF, total * sizeof(int32_t), st));
+            LP_CU(cudaMemsetAsync(gt_sum, 0, total * sizeof(int32_t), st));
+            LP_CU(cudaMemsetAsync(gt_np, 0, total * sizeof(uint32_t), st));
+            LP_CU(cudaStreamSynchronize(st));
+        }
+        return LP_OK;
+    }
+
+    lp_status alloc_labels()
+    {
+        LP_TRY(dev_alloc(&lab[0], nv, "labels", st, device));
+        LP_TRY(dev_alloc(&lab[1], nv, "labels", st, device));
+        Launches L;
+        if (fill_iota(lab[0], nv, vgraph, g_vbase, st, &L.n) != 0)
+            return fail(LP_ECUDA, cuda_msg("label init", cudaGetLastError()));
+        final_buf.assign((size_t)G, 0);
+        results.assign((size_t)G, lp_rak_result{0, 0, 0, 0.0f});
+        return LP_OK;
+    }
+
+    // Partition the bucket lists by wave (local id mod waves), once per wave count.
+    lp_status ensure_waves(int32_t waves)
+    {
+        if (waves == wl_waves) return LP_OK;
+        const int64_t len = bb[NUM_BUCKETS - 1] + bl[NUM_BUCKETS - 1];
+        if (!wlist) LP_TRY(dev_alloc(&wlist, nv, "wave lists", st, device));
+        if (!d_wtot) LP_TRY(dev_alloc(&d_wtot, NUM_BUCKETS * WAVE_MAX, "wave sizes", st, device));
+        int32_t *hist = nullptr;
+        LP_TRY(dev_alloc(&hist, wave_hist_ints(len, waves), "wave histogram", st, device));
+        Launches L;
+        const int nc = NUM_BUCKETS * waves;
+        std::vector<int64_t> tot((size_t)nc);
+        cudaError_t e = cudaSuccess;
+        if (wave_partition(list, len, bb, vgraph, g_vbase, waves, hist, d_wtot, wlist, st, &L.n) != 0)
+            e = cudaGetLastError();
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(tot.data(), d_wtot, (size_t)nc * sizeof(int64_t),
+                                cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        cudaFreeAsync(hist, st);
+        if (e != cudaSuccess) return fail(LP_ECUDA, cuda_msg("wave partition", e));
+        wstart.assign((size_t)nc, 0);
+        wcount = tot;
+        int64_t acc = 0;
+        for (int c = 0; c < nc; ++c) {
+            wstart[(size_t)c] = acc;
+            acc += tot[(size_t)c];
+        }
+        wl_waves = waves;
+        return LP_OK;
+    }
+
+    lp_status ensure_changed(int64_t entries)
+    {
+        if (entries <= changed_cap) return LP_OK;
+        if (changed) cudaFreeAsync(changed, st);
+        if (h_changed) cudaFreeHost(h_changed);
+        changed = nullptr;
+        h_changed = nullptr;
+        changed_cap = 0;
+        LP_TRY(dev_alloc(&changed, entries, "changed counters", st, device));
+        LP_TRY(host_alloc(&h_changed, entries, "changed counters"));
+        changed_cap = entries;
+        return LP_OK;
+    }
+
+    // Sec. 3.2 iteration over every graph of the set
+    lp_status run(const lp_rak_params *p, bool multi)
+    {
+        if (!p) return fail(LP_EINVAL, "params is NULL");
+        if (!(p->tolerance >= 0.0 && p->tolerance <= 1.0))
+            return fail(LP_EINVAL, "tolerance must lie in [0, 1]");
+        if (p->max_iter < 1) return fail(LP_EINVAL, "max_iter must be >= 1");
+        if (p->mode != LP_SYNC && p->mode != LP_ASYNC)
+            return fail(LP_EINVAL, "mode must be LP_SYNC or LP_ASYNC");
+        if (p->mode == LP_ASYNC && p->waves < 1) return fail(LP_EINVAL, "waves must be >= 1");
+        // Sec. 3.3 asynchronous waves; more waves than vertices change nothing
+        int32_t waves = 1;
+        if (p->mode == LP_ASYNC) waves = std::min(p->waves, std::max(max_n, 1));
+        if (waves > WAVE_MAX)
+            return fail(LP_EINVAL, "waves must be <= 4096 unless it is >= the vertex count");
+        if (multi && p->init_labels) return fail(LP_EINVAL, "batches start from unique labels");
+        const bool sync = p->mode == LP_SYNC;
+        LP_TRY(ensure_changed((int64_t)p->max_iter * G));
+        if (waves > 1) LP_TRY(ensure_waves(waves));
+        Launches L;
+
+        // a2: initial labels (Sec. 3.2: unique labels) or a resumed labelling
+        if (p->init_labels) {
+            LP_CU(cudaMemcpyAsync(lab[0], p->init_labels, (size_t)nv * sizeof(int32_t),
+                                  p->init_labels_on_device ? cudaMemcpyDeviceToDevice
+                                                           : cudaMemcpyHostToDevice,
+                                  st));
+            if (check_labels(lab[0], nv, vgraph, g_vbase, g_n, d_ing, st, &L.n) != 0)
+                return fail(LP_ECUDA, cuda_msg("label check", cudaGetLastError()));
+            LP_TRY(read_ingest(-1));
+        } else if (fill_iota(lab[0], nv, vgraph, g_vbase, st, &L.n) != 0) {
+            return fail(LP_ECUDA, cuda_msg("label init", cudaGetLastError()));
+        }
+        if (sync && nv > 0)
+            LP_CU(cudaMemcpyAsync(lab[1], lab[0], (size_t)nv * sizeof(int32_t),
+                                  cudaMemcpyDeviceToDevice, st));
+        LP_CU(cudaMemsetAsync(changed, 0, (size_t)p->max_iter * G * sizeof(int32_t), st));
+        if (multi) {
+            for (int32_t g = 0; g < G; ++g) h_active[g] = 1;
+            LP_CU(cudaMemcpyAsync(g_active, h_active, (size_t)G * sizeof(int32_t),
+                                  cudaMemcpyHostToDevice, st));
+        }
+        std::fill(final_buf.begin(), final_buf.end(), 0);
+        for (auto &r : results) r = lp_rak_result{0, 0, 0, 0.0f};
+        int cur = 0;
+        const bool prof = g_prof_on.load();
+        std::vector<int> prof_launch;  // bucket of each profiled launch
+        std::vector<int64_t> prof_len;  // its vertex count
+        LP_CU(cudaEventRecord(ev0, st));
+
+        SweepArgs a{};
+        a.off = off;
+        a.idx = idx;
+        a.wts = wts;
+        a.vgraph = vgraph;
+        a.g_vbase = g_vbase;
+        a.g_ebase = g_ebase;
+        a.g_active = g_active;
+        a.strict = p->strict ? 1 : 0;
+        a.gtab_key = gt_key;
+        a.gtab_sum = gt_sum;
+        a.gtab_npos = gt_np;
+        a.gtab_slots = gt_slots;
+        a.waves = (uint32_t)waves;
+        a.wave_magic = fastmod_magic((uint32_t)waves);
+
+        int32_t active_left = G;
+        for (int32_t it = 0; it < p->max_iter && active_left > 0; ++it) {
+            const int64_t t = (int64_t)it + p->iter_offset;
+            a.lab_in = lab[cur];
+            a.lab_out = sync ? lab[cur ^ 1] : lab[cur];
+            a.changed = changed + (int64_t)it * G;
+            a.key_t = stream_at(p->seed, (uint64_t)t + 1);
+            for (int launch_i = 0; launch_i < waves * NUM_BUCKETS; ++launch_i) {
+                const int k = launch_i / NUM_BUCKETS, b = launch_i % NUM_BUCKETS;
+                if (waves == 1) {
+                    a.list = list + bb[b];
+                    a.len = bl[b];
+                } else {
+                    a.list = wlist + wstart[(size_t)b * waves + k];
+                    a.len = wcount[(size_t)b * waves + k];
+                }
+                if (a.len == 0) continue;
+                a.wave_k = (uint32_t)k;
+                if (prof) {
+                    while (prof_ev.size() < 2 * (prof_launch.size() + 1)) {
+                        cudaEvent_t e;
+                        LP_CU(cudaEventCreate(&e));
+                        prof_ev.push_back(e);
+                    }
+                    LP_CU(cudaEventRecord(prof_ev[2 * prof_launch.size()], st));
+                }
+                if (sweep_launch(b, a, multi, num_sms, st) != 0)
+                    return fail(LP_ECUDA, cuda_msg("sweep launch", cudaGetLastError()));
+                ++L.n;
+                if (prof) {
+                    LP_CU(cudaEventRecord(prof_ev[2 * prof_launch.size() + 1], st));
+                    prof_launch.push_back(b);
+                    prof_len.push_back(a.len);
+                }
+            }
+            LP_CU(cudaMemcpyAsync(h_changed + (int64_t)it * G, a.changed,
+                                  (size_t)G * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+            LP_CU(cudaStreamSynchronize(st));
+            if (sync) cur ^= 1;
+            bool deactivated = false;
+            for (int32_t g = 0; g < G; ++g) {
+                if (multi && !h_active[g]) continue;
+                const int64_t c = h_changed[(int64_t)it * G + g];
+                lp_rak_result &r = results[(size_t)g];
+                r.iterations = it + 1;
+                r.last_changed = c;
+                final_buf[(size_t)g] = cur;
+                // Sec. 3.2: converged when at most tolerance * n vertices changed
+                if ((double)c <= p->tolerance * (double)h_n[(size_t)g]) {
+                    r.converged = 1;
+                    if (multi) {
+                        h_active[g] = 0;
+                        deactivated = true;
+                    }
+                    --active_left;
+                }
+            }
+            if (multi && deactivated && active_left > 0)
+                LP_CU(cudaMemcpyAsync(g_active, h_active, (size_t)G * sizeof(int32_t),
+                                      cudaMemcpyHostToDevice, st));
+        }
+        LP_CU(cudaEventRecord(ev1, st));
+        LP_CU(cudaEventSynchronize(ev1));
+        float ms = 0.f;
+        LP_CU(cudaEventElapsedTime(&ms, ev0, ev1));
+        for (auto &r : results) r.gpu_ms = ms;
+        if (prof && !prof_launch.empty()) {
+            std::lock_guard<std::mutex> lock(g_prof_mu);
+            for (size_t i = 0; i < prof_launch.size(); ++i) {
+                float kms = 0.f;
+                LP_CU(cudaEventElapsedTime(&kms, prof_ev[2 * i], prof_ev[2 * i + 1]));
+                const int b = prof_launch[i];
+                KernelStat &k = g_prof[b];
+                k.launches += 1;
+                k.ms += kms;
+                const double verts = (double)prof_len[i];
+                // entries of a wave launch: its share of the bucket's entries
+                const double ents = bl[b] ? (double)be[b] * verts / (double)bl[b] : 0.0;
+                k.vertices += verts;
+                k.entries += ents;
+                // algorithmic HBM bytes: row pointer, own label and label write
+                // per vertex; column index (and weight) per entry
+                k.bytes += 12.0 * verts + (wts ? 8.0 : 4.0) * ents;
+            }
+        }
+        history.assign((size_t)results[0].iterations, 0);
+        for (int32_t i = 0; i < results[0].iterations; ++i) history[i] = h_changed[(int64_t)i * G];
+        return LP_OK;
+    }
+
+    // modularity of graph g under labels lab_g (device, n_g entries, validated)
+    lp_status modularity(int32_t g, const int32_t *lab_g, double *q)
+    {
+        const int32_t n = h_n[(size_t)g];
+        const int64_t m = h_m[(size_t)g];
+        if (n > kc_cap) {
+            if (kc) cudaFreeAsync(kc, st);
+            kc = nullptr;
+            kc_cap = 0;
+            LP_TRY(dev_alloc(&kc, n, "community weights", st, device));
+            kc_cap = n;
+        }
+        const int blocks = std::max(1, std::min((int)((n + 255) / 256), num_sms * 4));
+        if (blocks > mpart_blocks) {
+            if (mpart) cudaFreeAsync(mpart, st);
+            mpart = nullptr;
+            mpart_blocks = 0;
+            LP_TRY(dev_alloc(&mpart, 2 * (int64_t)blocks, "modularity partials", st, device));
+            mpart_blocks = blocks;
+        }
+        std::vector<unsigned long long> part(2 * (size_t)blocks);
+        Launches L;
+        if (n > 0) LP_CU(cudaMemsetAsync(kc, 0, (size_t)n * sizeof(unsigned long long), st));
+        LP_CU(cudaMemsetAsync(macc, 0, 2 * sizeof(unsigned long long), st));
+        ModArgs ma{};
+        ma.off = off + h_vbase[(size_t)g] + g;
+        ma.idx = idx + h_ebase[(size_t)g];
+        ma.wts = wts ? wts + h_ebase[(size_t)g] : nullptr;
+        ma.lab = lab_g;
+        ma.n = n;
+        ma.m = m;
+        ma.kc = kc;
+        ma.acc = macc;
+        if (modularity_entries(ma, num_sms, st, &L.n) != 0)
+            return fail(LP_ECUDA, cuda_msg("modularity launch", cudaGetLastError()));
+        if (modularity_sumsq(kc, n, mpart, blocks, st, &L.n) != 0)
+            return fail(LP_ECUDA, cuda_msg("modularity launch", cudaGetLastError()));
+        LP_CU(cudaMemcpyAsync(h_macc, macc, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                              st));
+        LP_CU(cudaMemcpyAsync(part.data(), mpart, part.size() * sizeof(unsigned long long),
+                              cudaMemcpyDeviceToHost, st));
+        LP_CU(cudaStreamSynchronize(st));
+        unsigned __int128 s = 0;
+        for (int b = 0; b < blocks; ++b)
+            s += ((unsigned __int128)part[2 * (size_t)b] << 64) | part[2 * (size_t)b + 1];
+        const unsigned long long l_in = h_macc[0], two_m = h_macc[1];
+        if (two_m == 0) {
+            *q = 0.0;
+            return LP_OK;
+        }
+        const double dm = (double)two_m;
+        *q = (double)l_in / dm - (double)s / (dm * dm);
+        return LP_OK;
+    }
+
+    // copy `n` labels of graph g, starting at vertex base vb, to dst
+    lp_status copy_labels(int32_t g, int32_t *dst, int32_t on_device)
+    {
+        const int32_t n = h_n[(size_t)g];
+        if (n == 0) return LP_OK;
+        LP_CU(cudaMemcpyAsync(dst, lab[final_buf[(size_t)g]] + h_vbase[(size_t)g],
+                              (size_t)n * sizeof(int32_t),
+                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+        LP_CU(cudaStreamSynchronize(st));
+        return LP_OK;
+    }
+};
+
+}  // namespace lp
+
+struct lp_graph {
+    lp::GraphSet s;
+};
+
+struct lp_batch {
+    lp::GraphSet s;
+};
+
+// ----------------------------------------------------------------------------
+// Entry points
+// ----------------------------------------------------------------------------
+extern "C" {
+
+lp_status lp_rak_params_default(lp_rak_params *p)
+{
+    if (!p) return fail(LP_EINVAL, "params is NULL");
+    p->tolerance = 0.05;
+    p->max_iter = 20;
+    p->mode = LP_SYNC;
+    p->strict = 1;
+    p->iter_offset = 0;
+    p->seed = 0;
+    p->init_labels = nullptr;
+    p->init_labels_on_device = 0;
+    p->waves = 31;
+    return LP_OK;
+}
+
+lp_status lp_graph_create(int32_t n, int64_t m, const int32_t *offsets, const int32_t *indices,
+                          const int32_t *weights, uint32_t flags, void *cuda_stream,
+                          lp_graph **out)
+{
+    if (!out) return fail(LP_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n < 0) return fail(LP_EINVAL, "n must be >= 0");
+    if (m < 0 || m > 2147483647LL) return fail(LP_EINVAL, "m must lie in [0, 2^31)");
+    if (!offsets) return fail(LP_EINVAL, "offsets is NULL");
+    if (m > 0 && !indices) return fail(LP_EINVAL, "indices is NULL");
+    if ((flags & LP_FLAG_BORROW) && !(flags & LP_FLAG_DEVICE_PTRS))
+        return fail(LP_EINVAL, "LP_FLAG_BORROW needs LP_FLAG_DEVICE_PTRS");
+    if (flags & ~(uint32_t)(LP_FLAG_DEVICE_PTRS | LP_FLAG_CHECK_SYMMETRIC | LP_FLAG_BORROW))
+        return fail(LP_EINVAL, "unknown flag bits");
+    std::unique_ptr<lp_graph> g(new (std::nothrow) lp_graph);
+    if (!g) return fail(LP_ENOMEM, "host allocation failed");
+    lp::GraphSet &s = g->s;
+    LP_TRY(s.begin(cuda_stream));
+    const bool dev = flags & LP_FLAG_DEVICE_PTRS;
+    const cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    s.G = 1;
+    s.nv = n;
+    s.ne = m;
+    s.h_n = {n};
+    s.h_m = {m};
+    s.h_vbase = {0};
+    s.h_ebase = {0};
+    s.max_n = n;
+    if (flags & LP_FLAG_BORROW) {
+        s.off = const_cast<int32_t *>(offsets);
+        s.idx = const_cast<int32_t *>(indices);
+        s.wts = const_cast<int32_t *>(weights);
+        s.own_off = s.own_idx = s.own_wts = false;
+    } else {
+        LP_TRY(dev_alloc(&s.off, (int64_t)n + 1, "offsets", s.st, s.device));
+        LP_TRY(dev_alloc(&s.idx, m, "indices", s.st, s.device));
+        LP_CU(cudaMemcpyAsync(s.off, offsets, ((size_t)n + 1) * sizeof(int32_t), kind, s.st));
+        if (m > 0) LP_CU(cudaMemcpyAsync(s.idx, indices, (size_t)m * sizeof(int32_t), kind, s.st));
+        if (weights) {
+            LP_TRY(dev_alloc(&s.wts, m, "weights", s.st, s.device));
+            if (m > 0)
+                LP_CU(cudaMemcpyAsync(s.wts, weights, (size_t)m * sizeof(int32_t), kind, s.st));
+        }
+    }
+    LP_TRY(dev_alloc(&s.g_n, 1, "graph sizes", s.st, s.device));
+    LP_CU(cudaMemcpyAsync(s.g_n, &n, sizeof(int32_t), cudaMemcpyHostToDevice, s.st));
+    // a1: validation keeps every later kernel in bounds
+    LP_TRY(s.validate(0, s.off, s.idx, s.wts, n, m, -1));
+    if (flags & LP_FLAG_CHECK_SYMMETRIC) {
+        std::vector<int32_t> ho((size_t)n + 1), hi((size_t)m), hw(weights ? (size_t)m : 0);
+        LP_CU(cudaMemcpy(ho.data(), s.off, ho.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        if (m > 0)
+            LP_CU(cudaMemcpy(hi.data(), s.idx, hi.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        if (weights && m > 0)
+            LP_CU(cudaMemcpy(hw.data(), s.wts, hw.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        if (!host_symmetric(n, ho.data(), hi.data(), weights ? hw.data() : nullptr))
+            return fail(LP_EINVAL, "CSR is not symmetric");
+    }
+    LP_TRY(s.bucket());
+    LP_TRY(s.alloc_labels());
+    LP_CU(cudaStreamSynchronize(s.st));
+    *out = g.release();
+    return LP_OK;
+}
+
+lp_status lp_graph_destroy(lp_graph *g)
+{
+    if (!g) return LP_OK;
+    DeviceGuard dg(g->s.device);
+    delete g;
+    return LP_OK;
+}
+
+lp_status lp_graph_info(const lp_graph *g, int32_t *n, int64_t *m)
+{
+    if (!g) return fail(LP_EINVAL, "graph is NULL");
+    if (n) *n = g->s.nv;
+    if (m) *m = g->s.ne;
+    return LP_OK;
+}
+
+lp_status lp_rak_run(lp_graph *g, const lp_rak_params *p, lp_rak_result *out)
+{
+    if (!g) return fail(LP_EINVAL, "graph is NULL");
+    if (!out) return fail(LP_EINVAL, "result is NULL");
+    DeviceGuard dg(g->s.device);
+    LP_TRY(g->s.run(p, false));
+    *out = g->s.results[0];
+    return LP_OK;
+}
+
+lp_status lp_rak_history(const lp_graph *g, int64_t *changed, int32_t capacity, int32_t *count)
+{
+    if (!g || !count) return fail(LP_EINVAL, "graph or count is NULL");
+    if (capacity > 0 && !changed) return fail(LP_EINVAL, "changed is NULL");
+    const auto &h = g->s.history;
+    *count = (int32_t)h.size();
+    for (int32_t i = 0; i < capacity && i < (int32_t)h.size(); ++i) changed[i] = h[(size_t)i];
+    return LP_OK;
+}
+
+lp_status lp_labels_get(lp_graph *g, int32_t *dst, int32_t dst_on_device)
+{
+    if (!g) return fail(LP_EINVAL, "graph is NULL");
+    if (!dst && g->s.nv > 0) return fail(LP_EINVAL, "dst is NULL");
+    DeviceGuard dg(g->s.device);
+    return g->s.copy_labels(0, dst, dst_on_device);
+}
+
+lp_status lp_modularity(lp_graph *g, const int32_t *labels, int32_t labels_on_device, double *q)
+{
+    if (!g || !q) return fail(LP_EINVAL, "graph or q is NULL");
+    DeviceGuard dg(g->s.device);
+    lp::GraphSet &s = g->s;
+    const int32_t *lab = s.lab[s.final_buf[0]];
+    if (labels) {
+        if (!s.lab_tmp) LP_TRY(dev_alloc(&s.lab_tmp, s.nv, "label staging", s.st, s.device));
+        if (s.nv > 0)
+            LP_CU(cudaMemcpyAsync(s.lab_tmp, labels, (size_t)s.nv * sizeof(int32_t),
+                                  labels_on_device ? cudaMemcpyDeviceToDevice
+                                                   : cudaMemcpyHostToDevice,
+                                  s.st));
+        Launches L;
+        if (lp::check_labels(s.lab_tmp, s.nv, nullptr, nullptr, s.g_n, s.d_ing, s.st, &L.n) != 0)
+            return fail(LP_ECUDA, cuda_msg("label check", cudaGetLastError()));
+        LP_TRY(s.read_ingest(-1));
+        lab = s.lab_tmp;
+    }
+    return s.modularity(0, lab, q);
+}
+
+lp_status lp_batch_create(int32_t count, const lp_graph_desc *graphs, uint32_t flags,
+                          void *cuda_stream, lp_batch **out)
+{
+    if (!out) return fail(LP_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (count < 1 || !graphs) return fail(LP_EINVAL, "need at least one graph");
+    if (flags & ~(uint32_t)LP_FLAG_CHECK_SYMMETRIC)
+        return fail(LP_EINVAL, "batches take host CSR; only LP_FLAG_CHECK_SYMMETRIC is allowed");
+    int64_t nv = 0, ne = 0, noff = 0;
+    bool any_w = false;
+    for (int32_t i = 0; i < count; ++i) {
+        const lp_graph_desc &d = graphs[i];
+        char buf[128];
+        snprintf(buf, sizeof buf, "graph %d: bad n, m or NULL arrays", i);
+        if (d.n < 0 || d.m < 0 || d.m > 2147483647LL || !d.offsets || (d.m > 0 && !d.indices))
+            return fail(LP_EINVAL, buf);
+        nv += d.n;
+        ne += d.m;
+        noff += (int64_t)d.n + 1;
+        any_w = any_w || d.weights;
+    }
+    if (nv + count > 2147483647LL) return fail(LP_EINVAL, "total vertices must stay below 2^31");
+    std::unique_ptr<lp_batch> b(new (std::nothrow) lp_batch);
+    if (!b) return fail(LP_ENOMEM, "host allocation failed");
+    lp::GraphSet &s = b->s;
+    LP_TRY(s.begin(cuda_stream));
+    s.G = count;
+    s.nv = (int32_t)nv;
+    s.ne = ne;
+    s.h_n.resize((size_t)count);
+    s.h_m.resize((size_t)count);
+    s.h_vbase.resize((size_t)count);
+    s.h_ebase.resize((size_t)count);
+    int64_t vb = 0, eb = 0;
+    for (int32_t i = 0; i < count; ++i) {
+        s.h_n[(size_t)i] = graphs[i].n;
+        s.h_m[(size_t)i] = graphs[i].m;
+        s.h_vbase[(size_t)i] = (int32_t)vb;
+        s.h_ebase[(size_t)i] = eb;
+        vb += graphs[i].n;
+        eb += graphs[i].m;
+        s.max_n = std::max(s.max_n, graphs[i].n);
+    }
+    LP_TRY(dev_alloc(&s.off, noff, "offsets", s.st, s.device));
+    LP_TRY(dev_alloc(&s.idx, ne, "indices", s.st, s.device));
+    if (any_w) LP_TRY(dev_alloc(&s.wts, ne, "weights", s.st, s.device));
+    std::vector<int32_t> ones;
+    for (int32_t i = 0; i < count; ++i) {
+        const lp_graph_desc &d = graphs[i];
+        const int64_t ob = (int64_t)s.h_vbase[(size_t)i] + i;
+        const int64_t e0 = s.h_ebase[(size_t)i];
+        LP_CU(cudaMemcpyAsync(s.off + ob, d.offsets, ((size_t)d.n + 1) * sizeof(int32_t),
+                              cudaMemcpyHostToDevice, s.st));
+        if (d.m > 0)
+            LP_CU(cudaMemcpyAsync(s.idx + e0, d.indices, (size_t)d.m * sizeof(int32_t),
+                                  cudaMemcpyHostToDevice, s.st));
+        if (any_w && d.m > 0) {
+            const int32_t *src = d.weights;
+            if (!src) {
+                if ((int64_t)ones.size() < d.m) ones.assign((size_t)d.m, 1);
+                src = ones.data();
+            }
+            LP_CU(cudaMemcpyAsync(s.wts + e0, src, (size_t)d.m * sizeof(int32_t),
+                                  cudaMemcpyHostToDevice, s.st));
+        }
+        if (flags & LP_FLAG_CHECK_SYMMETRIC) {
+            if (!host_symmetric(d.n, d.offsets, d.indices, d.weights)) {
+                char buf[96];
+                snprintf(buf, sizeof buf, "graph %d: CSR is not symmetric", i);
+                return fail(LP_EINVAL, buf);
+            }
+        }
+    }
+    LP_CU(cudaStreamSynchronize(s.st));
+    for (int32_t i = 0; i < count; ++i) {
+        const int64_t ob = (int64_t)s.h_vbase[(size_t)i] + i;
+        const int64_t e0 = s.h_ebase[(size_t)i];
+        LP_TRY(s.validate(i, s.off + ob, s.idx + e0, s.wts ? s.wts + e0 : nullptr, graphs[i].n,
+                          graphs[i].m, i));
+    }
+    // graph of every global vertex, per-graph bases and sizes
+    std::vector<int32_t> vg((size_t)nv);
+    for (int32_t i = 0; i < count; ++i)
+        std::fill(vg.begin() + s.h_vbase[(size_t)i], vg.begin() + s.h_vbase[(size_t)i] + s.h_n[(size_t)i],
+                  i);
+    LP_TRY(dev_alloc(&s.vgraph, nv, "vertex graph ids", s.st, s.device));
+    LP_TRY(dev_alloc(&s.g_vbase, count, "graph bases", s.st, s.device));
+    LP_TRY(dev_alloc(&s.g_ebase, count, "graph bases", s.st, s.device));
+    LP_TRY(dev_alloc(&s.g_n, count, "graph sizes", s.st, s.device));
+    LP_TRY(dev_alloc(&s.g_active, count, "graph states", s.st, s.device));
+    LP_TRY(host_alloc(&s.h_active, count, "graph states"));
+    if (nv > 0)
+        LP_CU(cudaMemcpyAsync(s.vgraph, vg.data(), vg.size() * sizeof(int32_t),
+                              cudaMemcpyHostToDevice, s.st));
+    LP_CU(cudaMemcpyAsync(s.g_vbase, s.h_vbase.data(), (size_t)count * sizeof(int32_t),
+                          cudaMemcpyHostToDevice, s.st));
+    LP_CU(cudaMemcpyAsync(s.g_ebase, s.h_ebase.data(), (size_t)count * sizeof(int64_t),
+                          cudaMemcpyHostToDevice, s.st));
+    LP_CU(cudaMemcpyAsync(s.g_n, s.h_n.data(), (size_t)count * sizeof(int32_t),
+                          cudaMemcpyHostToDevice, s.st));
+    LP_CU(cudaStreamSynchronize(s.st));
+    LP_TRY(s.bucket());
+    LP_TRY(s.alloc_labels());
+    LP_CU(cudaStreamSynchronize(s.st));
+    *out = b.release();
+    return LP_OK;
+}
+
+lp_status lp_batch_destroy(lp_batch *b)
+{
+    if (!b) return LP_OK;
+    DeviceGuard dg(b->s.device);
+    delete b;
+    return LP_OK;
+}
+
+lp_status lp_batch_run(lp_batch *b, const lp_rak_params *p, lp_rak_result *per_graph)
+{
+    if (!b) return fail(LP_EINVAL, "batch is NULL");
+    DeviceGuard dg(b->s.device);
+    LP_TRY(b->s.run(p, true));
+    if (per_graph)
+        for (int32_t i = 0; i < b->s.G; ++i) per_graph[i] = b->s.results[(size_t)i];
+    return LP_OK;
+}
+
+lp_status lp_batch_labels_get(lp_batch *b, int32_t index, int32_t *dst, int32_t dst_on_device)
+{
+    if (!b) return fail(LP_EINVAL, "batch is NULL");
+    if (index < 0 || index >= b->s.G) return fail(LP_EINVAL, "graph index out of range");
+    if (!dst && b->s.h_n[(size_t)index] > 0) return fail(LP_EINVAL, "dst is NULL");
+    DeviceGuard dg(b->s.device);
+    return b->s.copy_labels(index, dst, dst_on_device);
+}
+
+lp_status lp_batch_modularity(lp_batch *b, int32_t index, double *q)
+{
+    if (!b || !q) return fail(LP_EINVAL, "batch or q is NULL");
+    if (index < 0 || index >= b->s.G) return fail(LP_EINVAL, "graph index out of range");
+    DeviceGuard dg(b->s.device);
+    lp::GraphSet &s = b->s;
+    return s.modularity(index, s.lab[s.final_buf[(size_t)index]] + s.h_vbase[(size_t)index], q);
+}
+
+lp_status lp_profile_enable(int32_t on)
+{
+    g_prof_on = on != 0;
+    return LP_OK;
+}
+
+lp_status lp_profile_reset(void)
+{
+    std::lock_guard<std::mutex> lock(g_prof_mu);
+    for (auto &k : g_prof) k = KernelStat{};
+    return LP_OK;
+}
+
+lp_status lp_profile_read(lp_kernel_stat *out, int32_t capacity, int32_t *count)
+{
+    if (!count) return fail(LP_EINVAL, "count is NULL");
+    if (capacity > 0 && !out) return fail(LP_EINVAL, "out is NULL");
+    std::lock_guard<std::mutex> lock(g_prof_mu);
+    *count = 4;
+    for (int i = 0; i < 4 && i < capacity; ++i) {
+        memset(out[i].name, 0, sizeof out[i].name);
+        strncpy(out[i].name, KERNEL_NAMES[i], sizeof out[i].name - 1);
+        out[i].launches = g_prof[i].launches;
+        out[i].total_ms = g_prof[i].ms;
+        out[i].vertices = g_prof[i].vertices;
+        out[i].entries = g_prof[i].entries;
+        out[i].bytes = g_prof[i].bytes;
+    }
+    return LP_OK;
+}
+
+const char *lp_last_error(void) { return g_err.c_str(); }
+
+int64_t lp_launch_count(void) { return g_launches.load(); }
+
+}  // extern "C"

@@ -1,0 +1,425 @@
+// Graph ingest: CSR validation and degree bucketing of the vertices.
+//
+// Validation is what keeps every later kernel in bounds: offsets must be a row
+// pointer (first 0, non-decreasing, last m), indices must lie in [0, n) and
+// weights must be >= 1.  The per-vertex summed weight must stay below 2^31 so
+// that the sweep's int32 sums are exact; it is bounded by max degree x max
+// weight, and only when that bound fails are the rows summed exactly.
+//
+// Bucketing sorts the vertices of a graph set into the four degree buckets
+// (small / warp / cta / hub) with a stable three-pass count-scan-scatter, so
+// the vertices of a bucket stay in ascending id order (coalesced row pointer
+// and label accesses in the sweep).
+#include "lp_internal.cuh"
+
+namespace lp {
+namespace {
+
+constexpr int BK = 1024;  // threads per bucketing block
+
+__device__ __forceinline__ void report(IngestOut *o, int32_t code, int64_t at)
+{
+    if (atomicCAS(&o->err, 0, code) == 0) o->err_at = (int32_t)(at > 2147483647 ? 2147483647 : at);
+}
+
+__global__ void k_val_offsets(const int32_t *off, int32_t n, int64_t m, IngestOut *o)
+{
+    int32_t local_max = 0;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v <= n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t x = off[v];
+        if (v == 0 && x != 0) report(o, ING_OFF_FIRST, 0);
+        if (v == n && (int64_t)x != m) report(o, ING_OFF_LAST, n);
+        if (v < n) {
+            const int32_t y = off[v + 1];
+            if (y < x)
+                report(o, ING_OFF_ORDER, v);
+            else
+                local_max = max(local_max, y - x);
+        }
+    }
+    local_max = (int32_t)__reduce_max_sync(FULL, (uint32_t)local_max);
+    if ((threadIdx.x & 31) == 0 && local_max) atomicMax(&o->max_deg, local_max);
+}
+
+__global__ void k_val_entries(const int32_t *idx, const int32_t *wts, int32_t n, int64_t m,
+                              IngestOut *o)
+{
+    int32_t wmax = 0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t u = __ldg(idx + e);
+        if (u < 0 || u >= n) report(o, ING_INDEX, e);
+        if (wts) {
+            const int32_t w = __ldg(wts + e);
+            if (w < 1)
+                report(o, ING_WEIGHT, e);
+            else
+                wmax = max(wmax, w);
+        }
+    }
+    if (!wts) wmax = m > 0 ? 1 : 0;
+    wmax = (int32_t)__reduce_max_sync(FULL, (uint32_t)wmax);
+    if ((threadIdx.x & 31) == 0 && wmax) atomicMax(&o->max_w, wmax);
+}
+
+__global__ void k_val_wdeg(const int32_t *off, const int32_t *wts, int32_t n, IngestOut *o)
+{
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        int64_t s = 0;
+        for (int32_t e = off[v]; e < off[v + 1]; ++e) s += wts ? wts[e] : 1;
+        if (s >= 2147483648LL) report(o, ING_WDEG, v);
+    }
+}
+
+__device__ __forceinline__ int bucket_of(int32_t d)
+{
+    return d <= 0 ? -1 : d <= SMALL_MAX ? 0 : d <= WARP_MAX ? 1 : d <= CTA_MAX ? 2 : 3;
+}
+
+// graph g's row pointer entries start at off[vbase_g + g], so global vertex v
+// (of graph g) has its row bounds at off[v + g], off[v + g + 1]
+__device__ __forceinline__ int32_t degree_of(const int32_t *off, const int32_t *vgraph, int32_t v)
+{
+    const int32_t g = vgraph ? vgraph[v] : 0;
+    return off[(int64_t)v + g + 1] - off[(int64_t)v + g];
+}
+
+__global__ void __launch_bounds__(BK) k_bucket_count(const int32_t *off, int32_t nv,
+                                                      const int32_t *vgraph, int32_t *blk,
+                                                      unsigned long long *entries)
+{
+    __shared__ int cnt[NUM_BUCKETS];
+    __shared__ unsigned long long ent[NUM_BUCKETS];
+    if (threadIdx.x < NUM_BUCKETS) {
+        cnt[threadIdx.x] = 0;
+        ent[threadIdx.x] = 0;
+    }
+    __syncthreads();
+    const int64_t v = (int64_t)blockIdx.x * BK + threadIdx.x;
+    if (v < nv) {
+        const int32_t d = degree_of(off, vgraph, (int32_t)v);
+        const int b = bucket_of(d);
+        if (b >= 0) {
+            atomicAdd(&cnt[b], 1);
+            atomicAdd(&ent[b], (unsigned long long)d);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < NUM_BUCKETS) {
+        blk[(int64_t)blockIdx.x * NUM_BUCKETS + threadIdx.x] = cnt[threadIdx.x];
+        if (ent[threadIdx.x]) atomicAdd(entries + threadIdx.x, ent[threadIdx.x]);
+    }
+}
+
+// exclusive block scan of one int per thread; returns the prefix, *total the sum
+__device__ int64_t block_exclusive_scan(int64_t x, int64_t *s_warp, int64_t *total)
+{
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    int64_t incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_warp[wib] = incl;
+    __syncthreads();
+    if (wib == 0) {
+        int64_t w = lane < (int)(blockDim.x >> 5) ? s_warp[lane] : 0;
+        int64_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(FULL, wi, o);
+            if (lane >= o) wi += y;
+        }
+        s_warp[lane] = wi - w;
+        if (lane == 31) s_warp[32] = wi;
+    }
+    __syncthreads();
+    const int64_t r = s_warp[wib] + incl - x;
+    *total = s_warp[32];
+    __syncthreads();
+    return r;
+}
+
+// one block: per bucket, exclusive scan of the per-block counts (in place)
+// out[0..4) bucket lengths, out[4..8) bucket starts in the list
+__global__ void __launch_bounds__(BK) k_bucket_scan(int32_t *blk, int64_t nblk, int64_t *out)
+{
+    __shared__ int64_t s_warp[33];
+    int64_t totals[NUM_BUCKETS];
+    for (int c = 0; c < NUM_BUCKETS; ++c) {
+        int64_t running = 0;
+        for (int64_t b0 = 0; b0 < nblk; b0 += BK) {
+            const int64_t b = b0 + threadIdx.x;
+            const int64_t x = b < nblk ? blk[b * NUM_BUCKETS + c] : 0;
+            int64_t tot;
+            const int64_t ex = block_exclusive_scan(x, s_warp, &tot);
+            if (b < nblk) blk[b * NUM_BUCKETS + c] = (int32_t)(running + ex);
+            running += tot;
+        }
+        totals[c] = running;
+    }
+    if (threadIdx.x == 0) {
+        int64_t begin = 0;
+        for (int c = 0; c < NUM_BUCKETS; ++c) {
+            out[c] = totals[c];
+            out[NUM_BUCKETS + c] = begin;
+            begin += totals[c];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(BK) k_bucket_scatter(const int32_t *off, int32_t nv,
+                                                        const int32_t *vgraph, const int32_t *blk,
+                                                        const int64_t *cnt, int32_t *list)
+{
+    __shared__ int s_pre[NUM_BUCKETS][BK / 32];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t v = (int64_t)blockIdx.x * BK + threadIdx.x;
+    const int b = v < nv ? bucket_of(degree_of(off, vgraph, (int32_t)v)) : -1;
+    int rank = 0;
+#pragma unroll
+    for (int c = 0; c < NUM_BUCKETS; ++c) {
+        const unsigned msk = __ballot_sync(FULL, b == c);
+        if (b == c) rank = __popc(msk & ((1u << lane) - 1u));
+        if (lane == 0) s_pre[c][wib] = __popc(msk);
+    }
+    __syncthreads();
+    if (threadIdx.x < NUM_BUCKETS) {
+        int acc = 0;
+        for (int w = 0; w < BK / 32; ++w) {
+            const int t = s_pre[threadIdx.x][w];
+            s_pre[threadIdx.x][w] = acc;
+            acc += t;
+        }
+    }
+    __syncthreads();
+    if (b >= 0)
+        list[cnt[NUM_BUCKETS + b] + blk[(int64_t)blockIdx.x * NUM_BUCKETS + b] + s_pre[b][wib] + rank] =
+            (int32_t)v;
+}
+
+__global__ void k_iota(int32_t *lab, int32_t nv, const int32_t *vgraph, const int32_t *g_vbase)
+{
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nv;
+         v += (int64_t)gridDim.x * blockDim.x)
+        lab[v] = (int32_t)v - (vgraph ? g_vbase[vgraph[v]] : 0);
+}
+
+__global__ void k_check_labels(const int32_t *lab, int32_t nv, const int32_t *vgraph,
+                               const int32_t *g_n, IngestOut *o)
+{
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nv;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t n = g_n[vgraph ? vgraph[v] : 0];
+        const int32_t l = lab[v];
+        if (l < 0 || l >= n) report(o, ING_LABEL, v);
+    }
+}
+
+__global__ void k_degrees_of(const int32_t *off, const int32_t *vgraph, const int32_t *list,
+                             int64_t len, int32_t *deg)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len;
+         i += (int64_t)gridDim.x * blockDim.x)
+        deg[i] = degree_of(off, vgraph, list[i]);
+}
+
+// ---------------------------------------------------------------------------
+// wave partition (asynchronous mode)
+// ---------------------------------------------------------------------------
+constexpr int WV = 1024;  // list entries per block
+
+__device__ __forceinline__ int wave_class(const int32_t *list, int64_t i, const int64_t *bb,
+                                          const int32_t *vgraph, const int32_t *g_vbase,
+                                          uint32_t waves, uint64_t magic)
+{
+    int b = 0;
+#pragma unroll
+    for (int c = 1; c < NUM_BUCKETS; ++c)
+        if (i >= bb[c]) b = c;
+    const int32_t v = list[i];
+    const int32_t lv = v - (vgraph ? g_vbase[vgraph[v]] : 0);
+    return b * (int)waves + (int)fastmod((uint32_t)lv, magic, waves);
+}
+
+struct WaveParams {
+    int64_t bb[NUM_BUCKETS];
+    uint32_t waves;
+    uint64_t magic;
+};
+
+__global__ void __launch_bounds__(WV) k_wave_hist(const int32_t *list, int64_t len, WaveParams p,
+                                                   const int32_t *vgraph, const int32_t *g_vbase,
+                                                   int32_t *hist)
+{
+    extern __shared__ int32_t s_cnt[];  // NUM_BUCKETS * waves
+    const int nc = NUM_BUCKETS * (int)p.waves;
+    for (int c = threadIdx.x; c < nc; c += WV) s_cnt[c] = 0;
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * WV + threadIdx.x;
+    if (i < len) atomicAdd(&s_cnt[wave_class(list, i, p.bb, vgraph, g_vbase, p.waves, p.magic)], 1);
+    __syncthreads();
+    for (int c = threadIdx.x; c < nc; c += WV) hist[(int64_t)c * gridDim.x + blockIdx.x] = s_cnt[c];
+}
+
+// exclusive scan of hist in class-major, block-minor order (one block)
+__global__ void __launch_bounds__(1024) k_wave_scan(int32_t *hist, int64_t total, int64_t nblk,
+                                                     int64_t *class_size)
+{
+    __shared__ int64_t s_warp[33];
+    int64_t running = 0;
+    for (int64_t i0 = 0; i0 < total; i0 += 1024) {
+        const int64_t i = i0 + threadIdx.x;
+        const int64_t x = i < total ? hist[i] : 0;
+        int64_t tot;
+        const int64_t ex = block_exclusive_scan(x, s_warp, &tot);
+        if (i < total) hist[i] = (int32_t)(running + ex);
+        running += tot;
+    }
+    // class sizes from consecutive class starts
+    __syncthreads();
+    const int64_t nc = total / nblk;
+    for (int64_t c = threadIdx.x; c < nc; c += 1024) {
+        const int64_t start = hist[c * nblk];
+        const int64_t next = c + 1 < nc ? (int64_t)hist[(c + 1) * nblk] : running;
+        class_size[c] = next - start;
+    }
+}
+
+__global__ void __launch_bounds__(WV) k_wave_scatter(const int32_t *list, int64_t len,
+                                                      WaveParams p, const int32_t *vgraph,
+                                                      const int32_t *g_vbase, const int32_t *hist,
+                                                      int32_t *out)
+{
+    extern __shared__ int32_t s_cur[];
+    const int nc = NUM_BUCKETS * (int)p.waves;
+    for (int c = threadIdx.x; c < nc; c += WV) s_cur[c] = hist[(int64_t)c * gridDim.x + blockIdx.x];
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * WV + threadIdx.x;
+    if (i < len) {
+        const int c = wave_class(list, i, p.bb, vgraph, g_vbase, p.waves, p.magic);
+        out[atomicAdd(&s_cur[c], 1)] = list[i];
+    }
+}
+
+int grid_for(int64_t items, int threads, int cap)
+{
+    const int64_t b = (items + threads - 1) / threads;
+    return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+}  // namespace
+
+int ingest_validate(const int32_t *off, const int32_t *idx, const int32_t *wts, int32_t n,
+                    int64_t m, IngestOut *d_out, cudaStream_t st, int64_t *launches)
+{
+    if (cudaMemsetAsync(d_out, 0, sizeof(IngestOut), st) != cudaSuccess) return -1;
+    k_val_offsets<<<grid_for((int64_t)n + 1, 256, 4096), 256, 0, st>>>(off, n, m, d_out);
+    ++*launches;
+    if (m > 0) {
+        k_val_entries<<<grid_for(m, 256, 8192), 256, 0, st>>>(idx, wts, n, m, d_out);
+        ++*launches;
+    }
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int ingest_check_wdeg(const int32_t *off, const int32_t *wts, int32_t n, IngestOut *d_out,
+                      cudaStream_t st, int64_t *launches)
+{
+    k_val_wdeg<<<grid_for(n, 256, 4096), 256, 0, st>>>(off, wts, n, d_out);
+    ++*launches;
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+size_t ingest_bucket_scratch_bytes(int32_t nv_total)
+{
+    const int64_t nblk = ((int64_t)nv_total + BK - 1) / BK;
+    return (size_t)(nblk > 0 ? nblk : 1) * NUM_BUCKETS * sizeof(int32_t);
+}
+
+int ingest_bucket(const int32_t *off, int32_t nv, const int32_t *vgraph, const int32_t *,
+                  int32_t *list, int32_t *blk, int64_t *d_counts, cudaStream_t st,
+                  int64_t *launches)
+{
+    const int64_t nblk = ((int64_t)nv + BK - 1) / BK;
+    if (cudaMemsetAsync(d_counts, 0, 3 * NUM_BUCKETS * sizeof(int64_t), st) != cudaSuccess)
+        return -1;
+    if (nblk == 0) return 0;
+    k_bucket_count<<<(int)nblk, BK, 0, st>>>(
+        off, nv, vgraph, blk, reinterpret_cast<unsigned long long *>(d_counts + 2 * NUM_BUCKETS));
+    k_bucket_scan<<<1, BK, 0, st>>>(blk, nblk, d_counts);
+    k_bucket_scatter<<<(int)nblk, BK, 0, st>>>(off, nv, vgraph, blk, d_counts, list);
+    *launches += 3;
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int degrees_of(const int32_t *off, const int32_t *vgraph, const int32_t *list, int64_t len,
+               int32_t *deg, cudaStream_t st, int64_t *launches)
+{
+    if (len == 0) return 0;
+    k_degrees_of<<<grid_for(len, 256, 4096), 256, 0, st>>>(off, vgraph, list, len, deg);
+    ++*launches;
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int64_t wave_hist_ints(int64_t list_len, int waves)
+{
+    const int64_t nblk = (list_len + WV - 1) / WV;
+    return (nblk > 0 ? nblk : 1) * NUM_BUCKETS * (int64_t)waves;
+}
+
+int wave_partition(const int32_t *list, int64_t len, const int64_t *bucket_begin,
+                   const int32_t *vgraph, const int32_t *g_vbase, int waves, int32_t *hist,
+                   int64_t *d_totals, int32_t *out, cudaStream_t st, int64_t *launches)
+{
+    const int nc = NUM_BUCKETS * waves;
+    if (waves < 1 || waves > WAVE_MAX) return -1;
+    if (len == 0) return cudaMemsetAsync(d_totals, 0, (size_t)nc * sizeof(int64_t), st) ==
+                          cudaSuccess ? 0 : -1;
+    WaveParams p;
+    for (int c = 0; c < NUM_BUCKETS; ++c) p.bb[c] = bucket_begin[c];
+    p.waves = (uint32_t)waves;
+    p.magic = fastmod_magic((uint32_t)waves);
+    const int64_t nblk = (len + WV - 1) / WV;
+    const size_t smem = (size_t)nc * sizeof(int32_t);
+    k_wave_hist<<<(int)nblk, WV, smem, st>>>(list, len, p, vgraph, g_vbase, hist);
+    k_wave_scan<<<1, 1024, 0, st>>>(hist, nblk * nc, nblk, d_totals);
+    k_wave_scatter<<<(int)nblk, WV, smem, st>>>(list, len, p, vgraph, g_vbase, hist, out);
+    *launches += 3;
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int wave_prepare()
+{
+    const int bytes = NUM_BUCKETS * WAVE_MAX * (int)sizeof(int32_t);
+    if (cudaFuncSetAttribute(k_wave_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(k_wave_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) !=
+            cudaSuccess)
+        return -1;
+    return 0;
+}
+
+int fill_iota(int32_t *lab, int32_t nv, const int32_t *vgraph, const int32_t *g_vbase,
+              cudaStream_t st, int64_t *launches)
+{
+    if (nv == 0) return 0;
+    k_iota<<<grid_for(nv, 256, 8192), 256, 0, st>>>(lab, nv, vgraph, g_vbase);
+    ++*launches;
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int check_labels(const int32_t *lab, int32_t nv, const int32_t *vgraph, const int32_t *,
+                 const int32_t *g_n, IngestOut *d_out, cudaStream_t st, int64_t *launches)
+{
+    if (cudaMemsetAsync(d_out, 0, sizeof(IngestOut), st) != cudaSuccess) return -1;
+    if (nv == 0) return 0;
+    k_check_labels<<<grid_for(nv, 256, 8192), 256, 0, st>>>(lab, nv, vgraph, g_n, d_out);
+    ++*launches;
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace lp

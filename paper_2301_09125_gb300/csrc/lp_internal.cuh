@@ -1,0 +1,171 @@
+// Internal declarations shared by the library's translation units.
+//
+// Device layout of a graph set (one graph, or a batch of graphs in one arena):
+//   off  int32  per graph n_g + 1 local row offsets, graphs concatenated
+//               (graph g's rows start at off[vbase_g + g])
+//   idx  int32  local neighbour ids, graphs concatenated (graph g's entries
+//               start at ebase_g)
+//   wts  int32  weights aligned with idx, or null for unit weights
+//   lab  int32  two label buffers of NV entries (vertex v of graph g at
+//               vbase_g + v); labels are local vertex ids
+//   list int32  global vertex ids sorted into degree buckets
+//               [small | warp | cta | hub], ascending id inside a bucket
+//               except hub, which is sorted by degree, largest first
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lp {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int32_t EMPTY = -1;
+
+// Degree buckets (Sec. 3.2's per-vertex hashtable, mapped to the GPU's
+// thread / warp / CTA granularity).
+constexpr int SMALL_MAX = 32;   // 1..32: several vertices packed per warp
+constexpr int WARP_MAX = 128;   // 33..128: one warp per vertex
+constexpr int CTA_MAX = 1024;   // 129..1024: one 256-thread CTA per vertex
+                                // > 1024: one 512-thread CTA + overflow table
+constexpr int NUM_BUCKETS = 4;  // small, warp, cta, hub
+
+constexpr int WARP_TABLE = 256;         // slots per warp (>= 2 * WARP_MAX)
+constexpr int CTA_THREADS = 256;
+constexpr int CTA_TABLE = 2048;         // slots (>= 2 * CTA_MAX)
+constexpr int HUB_THREADS = 512;
+constexpr int HUB_TABLE = 8192;         // shared slots; more labels spill to global
+constexpr int HUB_PROBE = 32;           // shared probe window before spilling
+
+// Arguments of one sweep kernel launch (one bucket).
+struct SweepArgs {
+    const int32_t *off;
+    const int32_t *idx;
+    const int32_t *wts;      // null = unit weights
+    const int32_t *lab_in;   // labels read (== lab_out in asynchronous mode)
+    int32_t *lab_out;        // labels written
+    const int32_t *list;     // bucket entries (global vertex ids)
+    int64_t len;             // bucket length
+    // graph set (null for a single graph: every base is 0)
+    const int32_t *vgraph;   // graph of each global vertex
+    const int32_t *g_vbase;  // first global vertex of each graph
+    const int64_t *g_ebase;  // first global entry of each graph
+    const int32_t *g_active; // 1 while the graph is still iterating
+    int32_t *changed;        // changed counter(s) of this iteration (per graph)
+    int strict;              // 1 strict, 0 non-strict
+    uint64_t key_t;          // non-strict stream key of this iteration
+    // asynchronous waves (Sec. 3.3): this launch runs wave `wave_k` of `waves`;
+    // a neighbour u of an earlier wave (u mod waves < wave_k) is read from
+    // lab_out (this iteration), every other one from lab_in.  waves = 1: sync.
+    uint32_t waves;
+    uint32_t wave_k;
+    uint64_t wave_magic;     // fastmod constant of `waves`
+    // hub overflow tables: per CTA, `gtab_slots` slots of key / sum / npos
+    int32_t *gtab_key;
+    int32_t *gtab_sum;
+    uint32_t *gtab_npos;
+    int64_t gtab_slots;
+};
+
+// Modularity arguments (one graph; pointers already offset to that graph).
+struct ModArgs {
+    const int32_t *off;        // n + 1 local row offsets
+    const int32_t *idx;        // m local neighbour ids
+    const int32_t *wts;        // m weights or null
+    const int32_t *lab;        // n labels in [0, n)
+    int32_t n;
+    int64_t m;
+    unsigned long long *kc;    // [n] K_c accumulators (zeroed by the caller)
+    unsigned long long *acc;   // [2] L and 2m accumulators (zeroed by the caller)
+};
+
+// ----------------------------------------------------------------------------
+// SplitMix64 output function (Steele, Lea & Flood 2014), used in counter mode
+// for the non-strict tie key.
+// ----------------------------------------------------------------------------
+constexpr uint64_t GOLDEN = 0x9E3779B97F4A7C15ull;
+
+__host__ __device__ __forceinline__ uint64_t splitmix_out(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Remainder by an invariant divisor d (1 <= d < 2^32) without a divide:
+// M = floor((2^64 - 1) / d) + 1, a mod d = high64((M * a mod 2^64) * d)
+// (Lemire, Kaser & Kurz, "Faster remainder by direct computation", 2019).
+__host__ __device__ __forceinline__ uint64_t fastmod_magic(uint32_t d)
+{
+    return 0xFFFFFFFFFFFFFFFFull / d + 1;
+}
+
+__device__ __forceinline__ uint32_t fastmod(uint32_t a, uint64_t magic, uint32_t d)
+{
+    return (uint32_t)__umul64hi(magic * (uint64_t)a, (uint64_t)d);
+}
+
+// k-th output of the stream whose state starts at `key`
+__host__ __device__ __forceinline__ uint64_t stream_at(uint64_t key, uint64_t k)
+{
+    return splitmix_out(key + k * GOLDEN);
+}
+
+// ----------------------------------------------------------------------------
+// Launchers (lp_sweep.cu, lp_ingest.cu, lp_modularity.cu)
+// ----------------------------------------------------------------------------
+int sweep_prepare();  // per-device kernel attributes; call with the device current
+// launch the sweep kernel of one degree bucket (0 small, 1 warp, 2 cta, 3 hub)
+int sweep_launch(int bucket, const SweepArgs &a, bool multi, int num_sms, cudaStream_t st);
+int hub_grid(int64_t hub_len, int num_sms);  // CTAs of the hub kernel (one overflow table each)
+
+struct IngestOut {
+    int32_t err;          // 0 ok, else an error code below
+    int32_t err_at;       // offending vertex / entry (first seen)
+    int32_t max_w;
+    int32_t max_deg;
+    int32_t wdeg_overflow;
+};
+enum IngestErr : int32_t {
+    ING_OK = 0,
+    ING_OFF_FIRST = 1,
+    ING_OFF_ORDER = 2,
+    ING_OFF_LAST = 3,
+    ING_INDEX = 4,
+    ING_WEIGHT = 5,
+    ING_WDEG = 6,
+    ING_ASYM = 7,
+    ING_LABEL = 8,
+};
+
+int ingest_validate(const int32_t *off, const int32_t *idx, const int32_t *wts, int32_t n,
+                    int64_t m, IngestOut *d_out, cudaStream_t st, int64_t *launches);
+int ingest_check_wdeg(const int32_t *off, const int32_t *wts, int32_t n, IngestOut *d_out,
+                      cudaStream_t st, int64_t *launches);
+int degrees_of(const int32_t *off, const int32_t *vgraph, const int32_t *list, int64_t len,
+               int32_t *deg, cudaStream_t st, int64_t *launches);
+// Bucket every vertex of a graph set.  d_counts[0..4) receives the bucket
+// lengths, [4..8) their starts in `list`, [8..12) their summed degrees.
+int ingest_bucket(const int32_t *off, int32_t nv_total, const int32_t *vgraph,
+                  const int32_t *g_vbase, int32_t *list, int32_t *scratch_blocks,
+                  int64_t *d_counts, cudaStream_t st, int64_t *launches);
+size_t ingest_bucket_scratch_bytes(int32_t nv_total);
+// Wave partition of the bucket lists for asynchronous runs: entries of bucket b
+// and wave k (= local vertex id mod waves) are gathered, class by class
+// (class = b * waves + k), into `out`; d_totals[class] receives the class sizes.
+constexpr int WAVE_MAX = 4096;
+int64_t wave_hist_ints(int64_t list_len, int waves);
+int wave_prepare();  // per-device kernel attributes
+int wave_partition(const int32_t *list, int64_t list_len, const int64_t *bucket_begin,
+                   const int32_t *vgraph, const int32_t *g_vbase, int waves, int32_t *hist,
+                   int64_t *d_totals, int32_t *out, cudaStream_t st, int64_t *launches);
+int fill_iota(int32_t *lab, int32_t nv, const int32_t *vgraph, const int32_t *g_vbase,
+              cudaStream_t st, int64_t *launches);
+int check_labels(const int32_t *lab, int32_t nv, const int32_t *vgraph, const int32_t *g_vbase,
+                 const int32_t *g_n, IngestOut *d_out, cudaStream_t st, int64_t *launches);
+
+int modularity_entries(const ModArgs &a, int num_sms, cudaStream_t st, int64_t *launches);
+// sum of K_c^2 over kc[0..n) into per-block 128-bit partials (hi, lo pairs)
+int modularity_sumsq(const unsigned long long *kc, int64_t n, unsigned long long *partials,
+                     int blocks, cudaStream_t st, int64_t *launches);
+
+}  // namespace lp

@@ -1,0 +1,581 @@
+// One RAK sweep (Sec. 3.2): every vertex of a bucket sums the weights of its
+// neighbours' labels and adopts the heaviest one, with the strict ("first in
+// adjacency order") or non-strict ("random") tie rule.
+//
+// Buckets by degree d:
+//   small  1..32     k_small : a warp packs several whole rows into one 32-lane
+//                              chunk; (owner, label) groups are found with
+//                              __match_any_sync and summed with redux.sync, and
+//                              the per-owner argmax is a segmented redux.sync
+//                              maximum, so no table is needed at all.
+//   warp   33..128   k_warp  : one warp per vertex, a 256-slot open-addressing
+//                              table per warp in shared memory; duplicate labels
+//                              of a 32-entry chunk are merged before insertion.
+//   cta    129..1024 k_cta   : one 256-thread CTA per vertex, 2048-slot table.
+//   hub    > 1024    k_cta   : one 512-thread CTA per vertex, 8192-slot shared
+//                              table; labels whose probe window is full go to a
+//                              per-CTA overflow table in global memory.
+// Every table slot holds (label, summed weight, ~first position); the first
+// position of a label is the smallest row position at which it occurs, so the
+// argmax key (weight desc, [non-strict key asc,] first position asc) is unique
+// and independent of the order in which entries were accumulated.  Weights
+// are summed in int32 (the library rejects graphs whose per-vertex weight sum
+// reaches 2^31), so synchronous results are bit-exact.
+#include "lp_internal.cuh"
+
+namespace lp {
+namespace {
+
+struct Vtx {
+    int32_t v;   // global vertex
+    int32_t g;   // graph
+    int32_t vb;  // first global vertex of the graph
+    int32_t lv;  // local vertex id
+    int32_t d;   // degree
+    int64_t e0;  // global index of the first entry
+};
+
+template <bool MULTI>
+__device__ __forceinline__ bool load_vtx(const SweepArgs &a, int32_t v, Vtx &x)
+{
+    x.v = v;
+    x.g = 0;
+    x.vb = 0;
+    if (MULTI) {
+        x.g = a.vgraph[v];
+        if (!a.g_active[x.g]) return false;
+        x.vb = a.g_vbase[x.g];
+    }
+    x.lv = v - x.vb;
+    const int64_t ob = (int64_t)x.vb + x.g + x.lv;  // graph g's offsets start at vbase_g + g
+    const int32_t rs = __ldg(a.off + ob);
+    const int32_t re = __ldg(a.off + ob + 1);
+    x.d = re - rs;
+    x.e0 = (MULTI ? a.g_ebase[x.g] : 0) + rs;
+    return true;
+}
+
+// Non-strict key of `label` at local vertex lv (see lp.h).
+__device__ __forceinline__ uint64_t tie_key(uint64_t key_t, int32_t lv, int32_t label)
+{
+    return stream_at(stream_at(key_t, (uint64_t)lv + 1), (uint64_t)label + 1);
+}
+
+__device__ __forceinline__ uint32_t slot_hash(int32_t label, int lg)
+{
+    // Fibonacci hashing: the top lg bits of label * 2^32/phi
+    return lg == 0 ? 0u : ((uint32_t)label * 0x9E3779B1u) >> (32 - lg);
+}
+
+struct Cand {
+    uint32_t sum;   // summed weight (0 = no candidate)
+    uint32_t npos;  // 0xFFFFFFFF - first position
+    uint64_t h;     // non-strict key (0 in strict mode)
+    int32_t label;
+};
+
+// strictly better: heavier, then smaller non-strict key, then earlier
+__device__ __forceinline__ bool better(const Cand &x, const Cand &y)
+{
+    if (x.sum != y.sum) return x.sum > y.sum;
+    if (x.h != y.h) return x.h < y.h;
+    return x.npos > y.npos;
+}
+
+__device__ __forceinline__ Cand shfl_cand(const Cand &c, int src)
+{
+    Cand r;
+    r.sum = __shfl_sync(FULL, c.sum, src);
+    r.npos = __shfl_sync(FULL, c.npos, src);
+    r.h = __shfl_sync(FULL, c.h, src);
+    r.label = __shfl_sync(FULL, c.label, src);
+    return r;
+}
+
+__device__ __forceinline__ Cand warp_best(Cand c)
+{
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        Cand x;
+        x.sum = __shfl_xor_sync(FULL, c.sum, o);
+        x.npos = __shfl_xor_sync(FULL, c.npos, o);
+        x.h = __shfl_xor_sync(FULL, c.h, o);
+        x.label = __shfl_xor_sync(FULL, c.label, o);
+        if (better(x, c)) c = x;
+    }
+    return c;
+}
+
+// Label of neighbour u (local id u, global index gi) as seen by this launch.
+// Neither buffer is written at an address this launch reads: lab_in is only
+// written by the next iteration, and lab_out entries of earlier waves were
+// written by earlier launches, so both go through the read-only path.
+__device__ __forceinline__ int32_t neighbour_label(const SweepArgs &a, int64_t gi, int32_t u)
+{
+    if (a.waves > 1 && fastmod((uint32_t)u, a.wave_magic, a.waves) < a.wave_k)
+        return __ldg(a.lab_out + gi);
+    return __ldg(a.lab_in + gi);
+}
+
+__device__ __forceinline__ int32_t own_label(const SweepArgs &a, int64_t v)
+{
+    return __ldg(a.lab_in + v);
+}
+
+// ----------------------------------------------------------------------------
+// small bucket: several rows per warp chunk
+// ----------------------------------------------------------------------------
+template <bool MULTI>
+__global__ void __launch_bounds__(256) k_small(SweepArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    uint32_t my_changed = 0;
+
+    for (int64_t tile = wid; tile * 32 < a.len; tile += nw) {
+        const int64_t i = tile * 32 + lane;
+        Vtx x{0, 0, 0, 0, 0, 0};
+        bool ok = false;
+        if (i < a.len) ok = load_vtx<MULTI>(a, a.list[i], x);
+        const int d = ok ? x.d : 0;
+        const int32_t own = ok ? own_label(a, x.v) : 0;
+
+        int P = d;  // inclusive prefix of degrees over the tile
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, P, o);
+            if (lane >= o) P += y;
+        }
+        const int excl = P - d;
+        const int total_all = __shfl_sync(FULL, P, 31);
+
+        int start = 0, base = 0;
+        while (base < total_all && start < 32) {
+            // greedy packing: rows start.. that end within 32 entries of base
+            // (row `start` always fits: the bucket holds degrees <= 32)
+            const unsigned fits =
+                __ballot_sync(FULL, (lane >= start && P - base <= 32) || lane == start);
+            const int end = 32 - __clz(fits);
+            const int total = __shfl_sync(FULL, P, end - 1) - base;
+
+            // owner of entry `lane`: the last row in [start, end) starting at or before it
+            int o = start;
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1) {
+                const int c = o + step;
+                const int ex = __shfl_sync(FULL, excl, c & 31);
+                if (c < end && ex - base <= lane) o = c;
+            }
+            const bool act = lane < total;
+            const int o_excl = __shfl_sync(FULL, excl, o);
+            const long long o_e0 = __shfl_sync(FULL, (long long)x.e0, o);
+            const int o_vb = MULTI ? __shfl_sync(FULL, x.vb, o) : 0;
+            const int o_lv = __shfl_sync(FULL, x.lv, o);
+            const int o_v = __shfl_sync(FULL, x.v, o);
+            const int32_t o_own = __shfl_sync(FULL, own, o);
+            const int pos = lane - (o_excl - base);
+
+            int w = 0;
+            int32_t l = EMPTY;
+            if (act) {
+                const long long e = o_e0 + pos;
+                const int32_t u = __ldg(a.idx + e);
+                w = a.wts ? __ldg(a.wts + e) : 1;
+                l = neighbour_label(a, (int64_t)o_vb + u, u);
+            }
+            // group equal (owner, label) pairs; the lowest lane holds the first position
+            const unsigned long long key =
+                act ? (((unsigned long long)(unsigned)o << 32) | (unsigned)l) : ~0ull;
+            const unsigned grp = __match_any_sync(FULL, key);
+            const int s = __reduce_add_sync(grp, w);
+            const bool leader = act && lane == __ffs(grp) - 1;
+            // segmented argmax over each owner's lanes
+            const unsigned og = __match_any_sync(FULL, act ? (unsigned)o : 0xFFFFFFFFu);
+            const uint32_t hi = leader ? (uint32_t)s : 0u;
+            const uint32_t npos = leader ? 0xFFFFFFFFu - (uint32_t)pos : 0u;
+            const uint32_t mhi = __reduce_max_sync(og, hi);
+            bool cand = leader && hi == mhi;
+            if (!a.strict) {
+                const uint64_t h = cand ? tie_key(a.key_t, o_lv, l) : ~0ull;
+                const uint32_t hh = __reduce_min_sync(og, cand ? (uint32_t)(h >> 32) : 0xFFFFFFFFu);
+                cand = cand && (uint32_t)(h >> 32) == hh;
+                const uint32_t hl = __reduce_min_sync(og, cand ? (uint32_t)h : 0xFFFFFFFFu);
+                cand = cand && (uint32_t)h == hl;
+            }
+            const uint32_t mlo = __reduce_max_sync(og, cand ? npos : 0u);
+            const bool win = cand && npos == mlo;
+            const bool ch = win && l != o_own;
+            if (win) a.lab_out[o_v] = l;
+            if (MULTI) {
+                const int o_g = __shfl_sync(FULL, x.g, o);
+                const unsigned chm = __ballot_sync(FULL, ch);
+                if (ch) {
+                    const unsigned gg = __match_any_sync(chm, (unsigned)o_g);
+                    if (lane == __ffs(gg) - 1) atomicAdd(a.changed + o_g, __popc(gg));
+                }
+            } else {
+                my_changed += __popc(__ballot_sync(FULL, ch));
+            }
+            base += total;
+            start = end;
+        }
+    }
+    if (!MULTI && lane == 0 && my_changed) atomicAdd(a.changed, (int)my_changed);
+}
+
+// ----------------------------------------------------------------------------
+// warp bucket: one warp per vertex, private shared table
+// ----------------------------------------------------------------------------
+constexpr int WARP_LG = 8;  // log2(WARP_TABLE)
+static_assert((1 << WARP_LG) == WARP_TABLE, "warp table size");
+
+template <bool MULTI>
+__global__ void __launch_bounds__(256) k_warp(SweepArgs a)
+{
+    __shared__ int32_t s_key[8 * WARP_TABLE];
+    __shared__ int32_t s_sum[8 * WARP_TABLE];
+    __shared__ uint32_t s_np[8 * WARP_TABLE];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    volatile int32_t *tk = s_key + wib * WARP_TABLE;
+    int32_t *tk_atomic = s_key + wib * WARP_TABLE;
+    volatile int32_t *ts = s_sum + wib * WARP_TABLE;
+    volatile uint32_t *tp = s_np + wib * WARP_TABLE;
+    for (int j = lane; j < WARP_TABLE; j += 32) {
+        tk[j] = EMPTY;
+        ts[j] = 0;
+        tp[j] = 0;
+    }
+    __syncwarp();
+
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    uint32_t my_changed = 0;
+
+    for (int64_t item = wid; item < a.len; item += nw) {
+        Vtx x;
+        if (!load_vtx<MULTI>(a, a.list[item], x)) continue;  // warp-uniform
+        const int32_t own = own_label(a, x.v);
+        for (int k0 = 0; k0 < x.d; k0 += 32) {
+            const int k = k0 + lane;
+            const bool act = k < x.d;
+            int w = 0;
+            int32_t l = EMPTY;
+            if (act) {
+                const int64_t e = x.e0 + k;
+                const int32_t u = __ldg(a.idx + e);
+                w = a.wts ? __ldg(a.wts + e) : 1;
+                l = neighbour_label(a, (int64_t)x.vb + u, u);
+            }
+            const unsigned grp = __match_any_sync(FULL, (unsigned)l);
+            const int s = __reduce_add_sync(grp, w);
+            if (act && lane == __ffs(grp) - 1) {
+                // one leader per label in this chunk; chunks run in row order, so
+                // the claiming leader holds the label's first position
+                uint32_t h = slot_hash(l, WARP_LG);
+                for (int probe = 0; probe < WARP_TABLE; ++probe) {  // <= 128 labels: always found
+                    int32_t cur = tk[h];
+                    if (cur == EMPTY) {
+                        cur = atomicCAS(tk_atomic + h, EMPTY, l);
+                        if (cur == EMPTY) {
+                            ts[h] = s;
+                            tp[h] = 0xFFFFFFFFu - (uint32_t)k;
+                            break;
+                        }
+                    }
+                    if (cur == l) {
+                        ts[h] = ts[h] + s;
+                        break;
+                    }
+                    h = (h + 1) & (WARP_TABLE - 1);
+                }
+            }
+            __syncwarp();
+        }
+
+        Cand best{0u, 0u, 0ull, EMPTY};
+        if (a.strict) {
+            for (int j = lane; j < WARP_TABLE; j += 32) {
+                const int32_t key = tk[j];
+                if (key != EMPTY) {
+                    const Cand c{(uint32_t)ts[j], tp[j], 0ull, key};
+                    if (better(c, best)) best = c;
+                    tk[j] = EMPTY;
+                    ts[j] = 0;
+                    tp[j] = 0;
+                }
+            }
+        } else {
+            uint32_t mx = 0;
+            for (int j = lane; j < WARP_TABLE; j += 32)
+                if (tk[j] != EMPTY) mx = max(mx, (uint32_t)ts[j]);
+            mx = __reduce_max_sync(FULL, mx);
+            const uint64_t ktv = stream_at(a.key_t, (uint64_t)x.lv + 1);
+            for (int j = lane; j < WARP_TABLE; j += 32) {
+                const int32_t key = tk[j];
+                if (key != EMPTY) {
+                    if ((uint32_t)ts[j] == mx) {
+                        const Cand c{mx, tp[j], stream_at(ktv, (uint64_t)key + 1), key};
+                        if (better(c, best)) best = c;
+                    }
+                    tk[j] = EMPTY;
+                    ts[j] = 0;
+                    tp[j] = 0;
+                }
+            }
+        }
+        best = warp_best(best);
+        if (lane == 0) {
+            a.lab_out[x.v] = best.label;
+            if (best.label != own) {
+                if (MULTI)
+                    atomicAdd(a.changed + x.g, 1);
+                else
+                    ++my_changed;
+            }
+        }
+        __syncwarp();
+    }
+    if (!MULTI && lane == 0 && my_changed) atomicAdd(a.changed, (int)my_changed);
+}
+
+// ----------------------------------------------------------------------------
+// cta / hub buckets: one CTA per vertex, shared table (+ global overflow)
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ int ilog2_ceil(uint32_t x)  // smallest lg with 2^lg >= x
+{
+    return x <= 1 ? 0 : 32 - __clz(x - 1);
+}
+
+template <int NT>
+__device__ __forceinline__ Cand block_best(Cand c, Cand *s_red)
+{
+    c = warp_best(c);
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    if (lane == 0) s_red[wib] = c;
+    __syncthreads();
+    if (wib == 0) {
+        c = lane < NT / 32 ? s_red[lane] : Cand{0u, 0u, 0ull, EMPTY};
+        c = warp_best(c);
+    }
+    return c;  // valid in thread 0
+}
+
+template <int NT>
+__device__ __forceinline__ uint32_t block_max(uint32_t v, uint32_t *s_u)
+{
+    v = __reduce_max_sync(FULL, v);
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    if (lane == 0) s_u[wib] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        v = lane < NT / 32 ? s_u[lane] : 0u;
+        v = __reduce_max_sync(FULL, v);
+        if (lane == 0) s_u[NT / 32] = v;
+    }
+    __syncthreads();
+    return s_u[NT / 32];
+}
+
+// insert (l, s, first position p) into an open-addressing table of 2^lg slots,
+// probing at most `limit` slots; false if the window is full of other labels
+__device__ __forceinline__ bool table_add(int32_t *key, int32_t *sum, uint32_t *npos, int lg,
+                                          int limit, int32_t l, int s, uint32_t p)
+{
+    const uint32_t mask = (1u << lg) - 1u;
+    uint32_t h = slot_hash(l, lg);
+    volatile int32_t *vk = key;
+    for (int i = 0; i < limit; ++i) {
+        int32_t cur = vk[h];
+        if (cur == EMPTY) {
+            cur = atomicCAS(key + h, EMPTY, l);
+            if (cur == EMPTY) cur = l;
+        }
+        if (cur == l) {
+            atomicAdd(sum + h, s);
+            atomicMax(npos + h, 0xFFFFFFFFu - p);
+            return true;
+        }
+        h = (h + 1) & mask;
+    }
+    return false;
+}
+
+template <int NT, int CAP, bool SPILL, bool MULTI>
+__global__ void __launch_bounds__(NT) k_cta(SweepArgs a)
+{
+    extern __shared__ int32_t smem[];
+    int32_t *tk = smem;
+    int32_t *ts = tk + CAP;
+    uint32_t *tp = reinterpret_cast<uint32_t *>(ts + CAP);
+    __shared__ Cand s_red[NT / 32];
+    __shared__ uint32_t s_u[NT / 32 + 1];
+    __shared__ int s_spilled;
+    constexpr int LG = (CAP == 2048) ? 11 : (CAP == 4096) ? 12 : (CAP == 8192) ? 13 : 14;
+    static_assert((1 << LG) == CAP, "table size");
+
+    for (int j = threadIdx.x; j < CAP; j += NT) {
+        tk[j] = EMPTY;
+        ts[j] = 0;
+        tp[j] = 0;
+    }
+    if (threadIdx.x == 0) s_spilled = 0;
+    __syncthreads();
+
+    int32_t *gk = nullptr, *gs = nullptr;
+    uint32_t *gp = nullptr;
+    if (SPILL) {
+        gk = a.gtab_key + (int64_t)blockIdx.x * a.gtab_slots;
+        gs = a.gtab_sum + (int64_t)blockIdx.x * a.gtab_slots;
+        gp = a.gtab_npos + (int64_t)blockIdx.x * a.gtab_slots;
+    }
+    uint32_t my_changed = 0;
+
+    for (int64_t item = blockIdx.x; item < a.len; item += gridDim.x) {
+        Vtx x;
+        if (!load_vtx<MULTI>(a, a.list[item], x)) continue;  // block-uniform
+        const int32_t own = own_label(a, x.v);
+        // overflow table slots for this vertex: 2^glg >= 2d, within the allocation
+        int glg = SPILL ? ilog2_ceil(2u * (uint32_t)x.d) : 0;
+        if (SPILL && ((int64_t)1 << glg) > a.gtab_slots) glg = 63 - __clzll(a.gtab_slots);
+
+        for (int k0 = 0; k0 < x.d; k0 += NT) {
+            const int k = k0 + threadIdx.x;
+            const bool act = k < x.d;
+            int w = 0;
+            int32_t l = EMPTY;
+            if (act) {
+                const int64_t e = x.e0 + k;
+                const int32_t u = __ldg(a.idx + e);
+                w = a.wts ? __ldg(a.wts + e) : 1;
+                l = neighbour_label(a, (int64_t)x.vb + u, u);
+            }
+            const unsigned grp = __match_any_sync(FULL, (unsigned)l);
+            const int s = __reduce_add_sync(grp, w);
+            if (act && (threadIdx.x & 31) == __ffs(grp) - 1) {
+                const bool in_shared = table_add(tk, ts, tp, LG, SPILL ? HUB_PROBE : CAP, l, s, k);
+                if (SPILL && !in_shared) {
+                    s_spilled = 1;
+                    table_add(gk, gs, gp, glg, 1 << glg, l, s, k);
+                }
+            }
+        }
+        __syncthreads();
+        const bool spilled = SPILL && s_spilled;
+
+        Cand best{0u, 0u, 0ull, EMPTY};
+        const int gslots = spilled ? (1 << glg) : 0;
+        if (a.strict) {
+            for (int j = threadIdx.x; j < CAP + gslots; j += NT) {
+                int32_t *K = j < CAP ? tk + j : gk + (j - CAP);
+                int32_t *S = j < CAP ? ts + j : gs + (j - CAP);
+                uint32_t *Q = j < CAP ? tp + j : gp + (j - CAP);
+                const int32_t key = *K;
+                if (key != EMPTY) {
+                    const Cand c{(uint32_t)*S, *Q, 0ull, key};
+                    if (better(c, best)) best = c;
+                    *K = EMPTY;
+                    *S = 0;
+                    *Q = 0;
+                }
+            }
+        } else {
+            uint32_t mx = 0;
+            for (int j = threadIdx.x; j < CAP + gslots; j += NT) {
+                const int32_t key = j < CAP ? tk[j] : gk[j - CAP];
+                if (key != EMPTY) mx = max(mx, (uint32_t)(j < CAP ? ts[j] : gs[j - CAP]));
+            }
+            mx = block_max<NT>(mx, s_u);
+            const uint64_t ktv = stream_at(a.key_t, (uint64_t)x.lv + 1);
+            for (int j = threadIdx.x; j < CAP + gslots; j += NT) {
+                int32_t *K = j < CAP ? tk + j : gk + (j - CAP);
+                int32_t *S = j < CAP ? ts + j : gs + (j - CAP);
+                uint32_t *Q = j < CAP ? tp + j : gp + (j - CAP);
+                const int32_t key = *K;
+                if (key != EMPTY) {
+                    if ((uint32_t)*S == mx) {
+                        const Cand c{mx, *Q, stream_at(ktv, (uint64_t)key + 1), key};
+                        if (better(c, best)) best = c;
+                    }
+                    *K = EMPTY;
+                    *S = 0;
+                    *Q = 0;
+                }
+            }
+        }
+        best = block_best<NT>(best, s_red);
+        if (threadIdx.x == 0) {
+            a.lab_out[x.v] = best.label;
+            if (best.label != own) {
+                if (MULTI)
+                    atomicAdd(a.changed + x.g, 1);
+                else
+                    ++my_changed;
+            }
+            s_spilled = 0;
+        }
+        __syncthreads();
+    }
+    if (!MULTI && threadIdx.x == 0 && my_changed) atomicAdd(a.changed, (int)my_changed);
+}
+
+template <bool MULTI>
+int launch(int bucket, const SweepArgs &a, int num_sms, cudaStream_t st)
+{
+    constexpr size_t cta_smem = (size_t)CTA_TABLE * 12;
+    constexpr size_t hub_smem = (size_t)HUB_TABLE * 12;
+    if (a.len <= 0) return 0;
+    int64_t blocks = 0;
+    switch (bucket) {
+    case 0:
+        blocks = (a.len + 255) / 256;
+        k_small<MULTI><<<(int)(blocks < num_sms * 16 ? blocks : num_sms * 16), 256, 0, st>>>(a);
+        break;
+    case 1:
+        blocks = (a.len + 7) / 8;
+        k_warp<MULTI><<<(int)(blocks < num_sms * 8 ? blocks : num_sms * 8), 256, 0, st>>>(a);
+        break;
+    case 2:
+        blocks = a.len;
+        k_cta<CTA_THREADS, CTA_TABLE, false, MULTI>
+            <<<(int)(blocks < num_sms * 8 ? blocks : num_sms * 8), CTA_THREADS, cta_smem, st>>>(a);
+        break;
+    default:
+        k_cta<HUB_THREADS, HUB_TABLE, true, MULTI>
+            <<<hub_grid(a.len, num_sms), HUB_THREADS, hub_smem, st>>>(a);
+        break;
+    }
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+template <bool MULTI>
+int prepare()
+{
+    if (cudaFuncSetAttribute(k_cta<CTA_THREADS, CTA_TABLE, false, MULTI>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)((size_t)CTA_TABLE * 12)) != cudaSuccess)
+        return -1;
+    if (cudaFuncSetAttribute(k_cta<HUB_THREADS, HUB_TABLE, true, MULTI>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)((size_t)HUB_TABLE * 12)) != cudaSuccess)
+        return -1;
+    return 0;
+}
+
+}  // namespace
+
+int hub_grid(int64_t hub_len, int num_sms)
+{
+    const int64_t cap = (int64_t)num_sms * 2;
+    return (int)(hub_len < cap ? hub_len : cap);
+}
+
+int sweep_prepare() { return prepare<false>() | prepare<true>(); }
+
+int sweep_launch(int bucket, const SweepArgs &a, bool multi, int num_sms, cudaStream_t st)
+{
+    return multi ? launch<true>(bucket, a, num_sms, st) : launch<false>(bucket, a, num_sms, st);
+}
+
+}  // namespace lp

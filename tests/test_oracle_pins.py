@@ -26,7 +26,8 @@ def test_golden_traces(golden_traces):
         off, idx, w = csr_from_adj(case["adj"], case.get("w"))
         labels, iters, conv, hist = oracle.rak(
             off, idx, w, tolerance=case["tolerance"], max_iter=case["max_iter"],
-            mode=case["mode"], strict=True, init_labels=case.get("init"))
+            mode=case["mode"], strict=True, init_labels=case.get("init"),
+            waves=case.get("waves", 0))
         assert labels.tolist() == case["labels"], case["name"]
         assert iters == case["iterations"], case["name"]
         assert conv == case["converged"], case["name"]
@@ -265,6 +266,40 @@ def test_disjoint_cliques_converge_to_one_label_each():
         assert len(np.unique(labels)) == len(sizes)
 
 
+@pytest.mark.parametrize("strict", [True, False])
+def test_async_waves_limits(strict):
+    """One wave is the synchronous rule; n or more waves (or 0) is the plain
+    in-place update in ascending order; waves in between are neither."""
+    for seed in range(6):
+        off, idx, w = random_graph(90, 0.06, 300 + seed, wmax=3)
+        sync = oracle.rak(off, idx, w, tolerance=0.0, max_iter=12, mode="sync", strict=strict,
+                          seed=seed)
+        one = oracle.rak(off, idx, w, tolerance=0.0, max_iter=12, mode="async", strict=strict,
+                         seed=seed, waves=1)
+        assert np.array_equal(sync[0], one[0]) and sync[1] == one[1]
+        assert np.array_equal(sync[3], one[3])
+        seq = oracle.rak(off, idx, w, tolerance=0.0, max_iter=12, mode="async", strict=strict,
+                         seed=seed, waves=0)
+        for big in (90, 91, 1000):
+            b = oracle.rak(off, idx, w, tolerance=0.0, max_iter=12, mode="async", strict=strict,
+                           seed=seed, waves=big)
+            assert np.array_equal(seq[0], b[0]) and np.array_equal(seq[3], b[3])
+
+
+def test_async_wave_visibility():
+    """A vertex of wave k sees new labels exactly for neighbours in waves < k:
+    on a path 0-1-2 with W = 3 the sweep reads left to right like the
+    sequential order, with W = 2 vertex 1 (wave 1) sees vertex 2 (wave 0) new."""
+    off, idx, w = csr_from_adj([[1], [0, 2], [1]], [[1], [1, 5], [5]])
+    # unique labels; v0 -> 1, v2 -> 1 (heavy edge), v1 -> 2 (heavy edge)
+    lab3, _, _, h3 = oracle.rak(off, idx, w, tolerance=0.0, max_iter=1, mode="async", waves=3)
+    # W=3: v0 -> 1; v1 sees new v0 = 1 (w1) and old v2 = 2 (w5) -> 2; v2 sees new v1 = 2 -> 2
+    assert lab3.tolist() == [1, 2, 2] and h3.tolist() == [2]
+    lab2, _, _, h2 = oracle.rak(off, idx, w, tolerance=0.0, max_iter=1, mode="async", waves=2)
+    # W=2: waves {0,2} then {1}: v0 -> 1, v2 sees old v1 = 1 -> 1; v1 sees 1 (w1) and 1 (w5) -> 1
+    assert lab2.tolist() == [1, 1, 1] and h2.tolist() == [2]
+
+
 def test_rejects_bad_arguments():
     off, idx, _ = csr_from_adj([[1], [0]])
     with pytest.raises(ValueError):
@@ -273,3 +308,5 @@ def test_rejects_bad_arguments():
         oracle.rak(off, idx, None, max_iter=0)
     with pytest.raises(ValueError):
         oracle.rak(off, np.array([1, 5], np.int32), None)
+    with pytest.raises(ValueError):
+        oracle.rak(off, idx, None, mode="async", waves=-1)

@@ -1,0 +1,401 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+* synchronous mode and asynchronous mode with W waves (strict and
+  non-strict): labels, iteration count, convergence flag and per-iteration
+  changed counts are bit-exact against the oracle run with the same W;
+* asynchronous mode against the oracle's plain in-place ascending order
+  (every vertex its own wave): on the R-MAT and road configurations the run
+  must converge with modularity within 1e-2 of the oracle's;
+* modularity: within 1e-9 of the oracle for the same labels.
+"""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+from conftest import csr_from_adj, random_graph
+
+pytestmark = pytest.mark.gpu
+
+Q_SYNC_TOL = 1e-9
+Q_ASYNC_TOL = 1e-2
+
+
+@pytest.fixture(scope="module")
+def lp():
+    import torch
+
+    import __graft_entry__
+
+    assert torch.cuda.is_available()
+    __graft_entry__.build()
+    import paper_2301_09125_gb300 as lp
+
+    return lp
+
+
+def gpu_run(lp, off, idx, w, **kw):
+    with lp.Graph(off, idx, w) as G:
+        r = G.rak(**kw)
+        return G.labels(), r, G.history(), G.modularity()
+
+
+def assert_sync_parity(lp, off, idx, w, strict=True, seed=0, tol=0.05, max_iter=20):
+    labels, r, hist, q = gpu_run(lp, off, idx, w, tolerance=tol, max_iter=max_iter,
+                                 mode="sync", strict=strict, seed=seed)
+    ref, iters, conv, ref_hist = oracle.rak(off, idx, w, tol, max_iter, "sync", strict=strict,
+                                            seed=seed)
+    assert r.iterations == iters
+    assert bool(r.converged) == conv
+    assert np.array_equal(hist, ref_hist)
+    mism = np.nonzero(labels != ref)[0]
+    assert mism.size == 0, f"{mism.size} labels differ, first at vertex {mism[:5]}"
+    assert r.last_changed == ref_hist[-1]
+    assert abs(q - oracle.modularity(off, idx, w, ref)) <= Q_SYNC_TOL
+    return r
+
+
+def assert_async_parity(lp, off, idx, w, waves, strict=True, seed=0, tol=0.05, max_iter=20):
+    labels, r, hist, q = gpu_run(lp, off, idx, w, tolerance=tol, max_iter=max_iter,
+                                 mode="async", strict=strict, seed=seed, waves=waves)
+    ref, iters, conv, ref_hist = oracle.rak(off, idx, w, tol, max_iter, "async", strict=strict,
+                                            seed=seed, waves=waves)
+    assert r.iterations == iters and bool(r.converged) == conv
+    assert np.array_equal(hist, ref_hist)
+    mism = np.nonzero(labels != ref)[0]
+    assert mism.size == 0, f"{mism.size} labels differ, first at vertex {mism[:5]}"
+    assert abs(q - oracle.modularity(off, idx, w, ref)) <= Q_SYNC_TOL
+    return labels, r, q
+
+
+def assert_async_quality(lp, off, idx, w, waves=31, tol=0.05, max_iter=20, strict=True, seed=0):
+    """Converged, with modularity within 1e-2 of the oracle's plain in-place
+    ascending-order run (every vertex its own wave)."""
+    labels, r, hist, q = gpu_run(lp, off, idx, w, tolerance=tol, max_iter=max_iter,
+                                 mode="async", strict=strict, seed=seed, waves=waves)
+    n = off.shape[0] - 1
+    assert labels.min() >= 0 and labels.max() < n
+    ref, iters, conv, _ = oracle.rak(off, idx, w, tol, max_iter, "async", strict=strict, seed=seed)
+    q_ref = oracle.modularity(off, idx, w, ref)
+    assert abs(q - oracle.modularity(off, idx, w, labels)) <= Q_SYNC_TOL
+    assert conv and r.converged, (r.as_dict(), iters)
+    assert abs(q - q_ref) <= Q_ASYNC_TOL, (q, q_ref)
+    return q, q_ref
+
+
+# ---------------------------------------------------------------- hand-derived traces
+def test_golden_traces_sync(lp, golden_traces):
+    for case in golden_traces:
+        if case["mode"] != "sync":
+            continue
+        off, idx, w = csr_from_adj(case["adj"], case.get("w"))
+        with lp.Graph(off, idx, w) as G:
+            r = G.rak(tolerance=case["tolerance"], max_iter=case["max_iter"], mode="sync",
+                      init_labels=case.get("init") and np.array(case["init"], np.int32))
+            assert G.labels().tolist() == case["labels"], case["name"]
+            assert r.iterations == case["iterations"], case["name"]
+            assert bool(r.converged) == case["converged"], case["name"]
+            assert G.history().tolist() == case["changed"], case["name"]
+            if "modularity" in case:
+                assert abs(G.modularity() - case["modularity"]) <= 1e-15
+
+
+def test_golden_traces_async(lp, golden_traces):
+    for case in golden_traces:
+        if case["mode"] != "async":
+            continue
+        off, idx, w = csr_from_adj(case["adj"], case.get("w"))
+        # waves 0 in a trace = every vertex its own wave: any W >= n
+        waves = case.get("waves", 0) or 4096
+        with lp.Graph(off, idx, w) as G:
+            r = G.rak(tolerance=case["tolerance"], max_iter=case["max_iter"], mode="async",
+                      waves=waves)
+            assert G.labels().tolist() == case["labels"], case["name"]
+            assert r.iterations == case["iterations"], case["name"]
+            assert bool(r.converged) == case["converged"], case["name"]
+            assert G.history().tolist() == case["changed"], case["name"]
+
+
+# ---------------------------------------------------------------- every degree bucket
+def hub_graph(seed, n=40_000, hubs=3, hub_deg=12_000, p_extra=0.0002):
+    """A sparse random graph plus `hubs` vertices of degree ~hub_deg, so the
+    hub kernel's shared table overflows into the global one in iteration 1."""
+    rng = np.random.default_rng(seed)
+    m_rand = int(p_extra * n * n / 2)
+    u = rng.integers(0, n, m_rand)
+    v = rng.integers(0, n, m_rand)
+    hu = [np.full(hub_deg, h) for h in range(hubs)]
+    hv = [rng.choice(np.arange(hubs, n), hub_deg, replace=False) for _ in range(hubs)]
+    u = np.concatenate([u] + hu)
+    v = np.concatenate([v] + hv)
+    keep = u != v
+    u, v = u[keep], v[keep]
+    a = np.unique(np.stack([np.minimum(u, v), np.maximum(u, v)], 1), axis=0)
+    src = np.concatenate([a[:, 0], a[:, 1]])
+    dst = np.concatenate([a[:, 1], a[:, 0]])
+    perm = rng.permutation(src.size)  # shuffled rows: adjacency order matters
+    src, dst = src[perm], dst[perm]
+    order = np.argsort(src, kind="stable")
+    src, dst = src[order], dst[order]
+    off = np.zeros(n + 1, np.int64)
+    np.add.at(off, src + 1, 1)
+    off = np.cumsum(off).astype(np.int32)
+    pair_w = (a[:, 0] * 7919 + a[:, 1] * 104729) % 5 + 1
+    wmap = dict(zip(map(tuple, a.tolist()), pair_w.tolist()))
+    w = np.array([wmap[(min(x, y), max(x, y))] for x, y in zip(src.tolist(), dst.tolist())],
+                 np.int32)
+    return off, dst.astype(np.int32), w
+
+
+@pytest.mark.parametrize("strict", [True, False])
+@pytest.mark.parametrize("shape", ["small", "warp", "cta", "hub", "mixed"])
+def test_sync_parity_per_bucket(lp, shape, strict):
+    if shape == "small":
+        off, idx, w = random_graph(3000, 6 / 3000, 1, wmax=3)
+    elif shape == "warp":
+        off, idx, w = random_graph(1500, 70 / 1500, 2, wmax=1)
+    elif shape == "cta":
+        off, idx, w = random_graph(2500, 400 / 2500, 3, wmax=4)
+    elif shape == "hub":
+        off, idx, w = hub_graph(4)
+    else:
+        g = gg.rmat(15, seed=5)
+        off, idx, w = g.offsets, g.indices, g.weights
+    deg = np.diff(off)
+    assert deg.max() > {"small": 8, "warp": 33, "cta": 129, "hub": 8192, "mixed": 1024}[shape]
+    assert_sync_parity(lp, off, idx, w, strict=strict, seed=11)
+
+
+@pytest.mark.parametrize("waves", [2, 7, 31, 4096])
+@pytest.mark.parametrize("shape", ["small", "cta", "hub", "mixed"])
+def test_async_parity_per_bucket(lp, shape, waves):
+    if shape == "small":
+        off, idx, w = random_graph(3000, 6 / 3000, 5, wmax=3)
+    elif shape == "cta":
+        off, idx, w = random_graph(2500, 300 / 2500, 6, wmax=4)
+    elif shape == "hub":
+        off, idx, w = hub_graph(7, n=20_000, hub_deg=9_000)
+    else:
+        g = gg.rmat(14, seed=8)
+        off, idx, w = g.offsets, g.indices, g.weights
+    for strict in (True, False):
+        assert_async_parity(lp, off, idx, w, waves, strict=strict, seed=3)
+
+
+def test_async_one_wave_is_sync(lp):
+    g = gg.rmat(13, seed=9)
+    a = gpu_run(lp, g.offsets, g.indices, g.weights, mode="async", waves=1, tolerance=0.0,
+                max_iter=6)
+    b = gpu_run(lp, g.offsets, g.indices, g.weights, mode="sync", tolerance=0.0, max_iter=6)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[2], b[2])
+
+
+def test_sync_parity_unit_weights_and_tolerances(lp):
+    g = gg.sbm_planted(5000, 25, 0.01, 0.001, seed=3)
+    for tol in (0.0, 0.01, 0.05, 0.3, 1.0):
+        assert_sync_parity(lp, g.offsets, g.indices, g.weights, tol=tol, max_iter=30)
+
+
+# ---------------------------------------------------------------- configuration shapes
+def test_sbm10k_config(lp):
+    g = gg.workload("sbm10k")
+    r = assert_sync_parity(lp, g.offsets, g.indices, g.weights, strict=True)
+    assert r.converged
+    assert_sync_parity(lp, g.offsets, g.indices, g.weights, strict=False, seed=1)
+    assert_async_parity(lp, g.offsets, g.indices, g.weights, 31)
+
+
+def test_rmat_and_road_small(lp):
+    g = gg.rmat(16, seed=2)
+    assert_sync_parity(lp, g.offsets, g.indices, g.weights)
+    assert_async_parity(lp, g.offsets, g.indices, g.weights, 31)
+    assert_async_parity(lp, g.offsets, g.indices, g.weights, 2)
+    assert_async_quality(lp, g.offsets, g.indices, g.weights, waves=2)
+    g = gg.grid_road(512, seed=2)
+    assert_sync_parity(lp, g.offsets, g.indices, g.weights)
+    assert_async_parity(lp, g.offsets, g.indices, g.weights, 31)
+    assert_async_quality(lp, g.offsets, g.indices, g.weights, waves=31)
+    g = gg.kmer_like(200_000, seed=2)
+    assert_sync_parity(lp, g.offsets, g.indices, g.weights)
+
+
+# ---------------------------------------------------------------- modularity
+@pytest.mark.parametrize("seed", range(4))
+def test_modularity_parity(lp, seed):
+    rng = np.random.default_rng(seed)
+    off, idx, w = random_graph(int(rng.integers(50, 3000)), 0.02, seed, wmax=7,
+                               self_loops=bool(seed % 2))
+    n = off.shape[0] - 1
+    with lp.Graph(off, idx, w) as G:
+        for k in (1, 3, n // 7 + 1, n):
+            lab = rng.integers(0, k, n).astype(np.int32)
+            q = G.modularity(lab)
+            assert abs(q - oracle.modularity(off, idx, w, lab)) <= Q_SYNC_TOL
+
+
+def test_modularity_large_exact(lp):
+    g = gg.rmat(18, seed=9)
+    rng = np.random.default_rng(1)
+    lab = rng.integers(0, 1000, g.n).astype(np.int32)
+    with lp.Graph(g.offsets, g.indices, g.weights) as G:
+        assert G.modularity(lab) == oracle.modularity(g.offsets, g.indices, g.weights, lab)
+
+
+# ---------------------------------------------------------------- edge cases and resume
+def test_edge_cases(lp):
+    # empty graph
+    off = np.zeros(1, np.int32)
+    labels, r, hist, q = gpu_run(lp, off, np.zeros(0, np.int32), None)
+    assert labels.size == 0 and r.iterations == 1 and r.converged and q == 0.0
+    # vertices without edges
+    off = np.zeros(6, np.int32)
+    labels, r, hist, q = gpu_run(lp, off, np.zeros(0, np.int32), None)
+    assert labels.tolist() == [0, 1, 2, 3, 4] and r.iterations == 1 and hist.tolist() == [0]
+    # a self-loop only
+    off, idx, w = csr_from_adj([[0], []], [[3], []])
+    labels, r, hist, q = gpu_run(lp, off, idx, w)
+    assert labels.tolist() == [0, 1] and q == 0.0
+    # duplicates, self-loops, maximum-degree row of 32 / 33 / 128 / 129 / 1024 / 1025
+    for d in (31, 32, 33, 128, 129, 1024, 1025):
+        rows = [[(v + k) % (d + 1) for k in range(1, d + 1)] for v in range(d + 1)]
+        rows[0] = rows[0] + [0, 1, 1]
+        off, idx, _ = csr_from_adj(rows)
+        assert_sync_parity(lp, off, idx, None, max_iter=5)
+
+
+@pytest.mark.parametrize("mode_strict", [("sync", True), ("sync", False)])
+def test_resume_is_bit_exact(lp, mode_strict):
+    mode, strict = mode_strict
+    g = gg.rmat(14, seed=4)
+    with lp.Graph(g.offsets, g.indices, g.weights) as G:
+        G.rak(tolerance=0.0, max_iter=6, mode=mode, strict=strict, seed=5)
+        full = G.labels().copy()
+        G.rak(tolerance=0.0, max_iter=3, mode=mode, strict=strict, seed=5)
+        mid = G.labels().copy()
+        G.rak(tolerance=0.0, max_iter=3, mode=mode, strict=strict, seed=5, iter_offset=3,
+              init_labels=mid)
+        assert np.array_equal(G.labels(), full)
+
+
+def test_invalid_inputs_are_rejected(lp):
+    off, idx, w = csr_from_adj([[1], [0]])
+    bad = [
+        (np.array([1, 1, 2], np.int32), idx, None, "offsets\\[0\\]"),
+        (np.array([0, 2, 1], np.int32), idx[:1], None, "non-decreasing"),
+        (np.array([0, 1, 3], np.int32), np.array([1, 0, 0], np.int32)[:2], None, "offsets\\[n\\]"),
+        (off, np.array([1, 2], np.int32), None, "column index"),
+        (off, np.array([1, -1], np.int32), None, "column index"),
+        (off, idx, np.array([1, 0], np.int32), "weight"),
+    ]
+    for o, i, ww, msg in bad:
+        with pytest.raises(lp.LPError, match=msg):
+            lp.Graph(o, i, ww)
+    with pytest.raises(lp.LPError, match="symmetric"):
+        lp.Graph(*csr_from_adj([[1], []]), check_symmetric=True)
+    big = np.array([0, 2, 4], np.int32)
+    with pytest.raises(lp.LPError, match="2\\^31"):
+        lp.Graph(big, np.array([1, 1, 0, 0], np.int32),
+                 np.array([2**30, 2**30, 1, 1], np.int32))
+    with lp.Graph(off, idx, None) as G:
+        with pytest.raises(lp.LPError, match="label"):
+            G.modularity(np.array([0, 2], np.int32))
+        with pytest.raises(lp.LPError, match="label"):
+            G.rak(init_labels=np.array([5, 0], np.int32))
+        with pytest.raises(lp.LPError, match="tolerance"):
+            G.rak(tolerance=1.5)
+        with pytest.raises(lp.LPError, match="max_iter"):
+            G.rak(max_iter=0)
+        r = G.rak()  # still usable
+        assert r.iterations >= 1
+
+
+def test_device_pointers_and_borrow(lp):
+    import torch
+
+    g = gg.rmat(14, seed=6)
+    ref, iters, _, _ = oracle.rak(g.offsets, g.indices, g.weights, 0.05, 20, "sync")
+    dev = torch.device("cuda")
+    t = [torch.from_numpy(a).to(dev) for a in (g.offsets, g.indices, g.weights)]
+    for borrow in (False, True):
+        with lp.Graph(*t, borrow=borrow) as G:
+            r = G.rak()
+            out = torch.empty(g.n, dtype=torch.int32, device=dev)
+            G.labels(out)
+            assert np.array_equal(out.cpu().numpy(), ref) and r.iterations == iters
+            q = G.modularity(out)
+            assert abs(q - oracle.modularity(g.offsets, g.indices, g.weights, ref)) <= Q_SYNC_TOL
+
+
+# ---------------------------------------------------------------- batches
+def test_batch_matches_single_graph_runs(lp):
+    params = gg.batch_sbm_params(count=40, seed=77, n_lo=200, n_hi=6000)
+    graphs = gg.batch_sbm(params)
+    graphs[3] = gg.rmat(12, seed=3)          # a weighted graph with hubs in the mix
+    graphs[5] = gg.CSR(np.zeros(1, np.int32), np.zeros(0, np.int32), None)  # empty
+    triples = [(g.offsets, g.indices, g.weights) for g in graphs]
+    h = lp.lp_batch_create(triples)
+    try:
+        for strict in (True, False):
+            res = lp.lp_batch_run(h, len(graphs), tolerance=0.05, max_iter=20, mode="sync",
+                                  strict=strict, seed=2)
+            for i, g in enumerate(graphs):
+                lab = lp.lp_batch_labels_get(h, i, g.n)
+                ref, iters, conv, hist = oracle.rak(g.offsets, g.indices, g.weights, 0.05, 20,
+                                                    "sync", strict=strict, seed=2)
+                assert res[i].iterations == iters and bool(res[i].converged) == conv, i
+                assert res[i].last_changed == hist[-1]
+                assert np.array_equal(lab, ref), i
+                q = lp.lp_batch_modularity(h, i)
+                assert abs(q - oracle.modularity(g.offsets, g.indices, g.weights, ref)) <= Q_SYNC_TOL
+    finally:
+        lp.lp_batch_destroy(h)
+
+
+# ---------------------------------------------------------------- full-size workloads
+def sampled_sync_check(lp, g, strict, seed, samples=20_000):
+    """Two sweeps at full size; each output of the second sweep is checked at
+    sampled vertices (plus every vertex of degree > 1024) against the oracle's
+    single-vertex step; the changed counts must match the label arrays."""
+    rng = np.random.default_rng(seed)
+    deg = np.diff(g.offsets)
+    verts = np.unique(np.concatenate([rng.integers(0, g.n, samples), np.nonzero(deg > 1024)[0]]))
+    verts = verts.astype(np.int32)
+    with lp.Graph(g.offsets, g.indices, g.weights) as G:
+        r1 = G.rak(tolerance=0.0, max_iter=1, mode="sync", strict=strict, seed=seed)
+        lab1 = G.labels().copy()
+        ident = np.arange(g.n, dtype=np.int32)
+        ref1 = oracle.choose_many(g.offsets, g.indices, g.weights, ident, verts, strict=strict,
+                                  seed=seed, t=0)
+        assert np.array_equal(lab1[verts], ref1)
+        assert r1.last_changed == int(np.sum(lab1 != ident))
+        r2 = G.rak(tolerance=0.0, max_iter=1, mode="sync", strict=strict, seed=seed,
+                   iter_offset=1, init_labels=lab1)
+        lab2 = G.labels().copy()
+        ref2 = oracle.choose_many(g.offsets, g.indices, g.weights, lab1, verts, strict=strict,
+                                  seed=seed, t=1)
+        assert np.array_equal(lab2[verts], ref2)
+        assert r2.last_changed == int(np.sum(lab2 != lab1))
+
+
+@pytest.fixture(scope="module")
+def rmat22():
+    return gg.workload("rmat22")
+
+
+@pytest.fixture(scope="module")
+def road4096():
+    return gg.workload("road4096")
+
+
+@pytest.mark.slow
+def test_rmat22_full_size(lp, rmat22):
+    sampled_sync_check(lp, rmat22, strict=True, seed=1)
+    sampled_sync_check(lp, rmat22, strict=False, seed=2)
+    for waves in (2, 31):
+        assert_async_quality(lp, rmat22.offsets, rmat22.indices, rmat22.weights, waves=waves)
+
+
+@pytest.mark.slow
+def test_road4096_full_size(lp, road4096):
+    sampled_sync_check(lp, road4096, strict=True, seed=3)
+    assert_async_quality(lp, road4096.offsets, road4096.indices, road4096.weights, waves=31)
