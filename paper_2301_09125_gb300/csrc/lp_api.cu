@@ -505,7 +505,6 @@ struct GraphSet {
         if (waves > WAVE_MAX)
             return fail(LP_EINVAL, "waves must be <= 4096 unless it is >= the vertex count");
         if (multi && p->init_labels) return fail(LP_EINVAL, "batches start from unique labels");
-        const bool sync = p->mode == LP_SYNC;
         LP_TRY(ensure_changed((int64_t)p->max_iter * G));
         if (waves > 1) LP_TRY(ensure_waves(waves));
         Launches L;
@@ -522,7 +521,9 @@ struct GraphSet {
         } else if (fill_iota(lab[0], nv, vgraph, g_vbase, st, &L.n) != 0) {
             return fail(LP_ECUDA, cuda_msg("label init", cudaGetLastError()));
         }
-        if (sync && nv > 0)
+        // both buffers hold the initial labels: vertices without edges are never
+        // written, and both modes alternate the buffers every iteration
+        if (nv > 0)
             LP_CU(cudaMemcpyAsync(lab[1], lab[0], (size_t)nv * sizeof(int32_t),
                                   cudaMemcpyDeviceToDevice, st));
         LP_CU(cudaMemsetAsync(changed, 0, (size_t)p->max_iter * G * sizeof(int32_t), st));
@@ -558,8 +559,10 @@ struct GraphSet {
         int32_t active_left = G;
         for (int32_t it = 0; it < p->max_iter && active_left > 0; ++it) {
             const int64_t t = (int64_t)it + p->iter_offset;
+            // sync reads lab_in only; async reads lab_out for neighbours of
+            // earlier waves (written by this iteration's earlier launches)
             a.lab_in = lab[cur];
-            a.lab_out = sync ? lab[cur ^ 1] : lab[cur];
+            a.lab_out = lab[cur ^ 1];
             a.changed = changed + (int64_t)it * G;
             a.key_t = stream_at(p->seed, (uint64_t)t + 1);
             for (int launch_i = 0; launch_i < waves * NUM_BUCKETS; ++launch_i) {
@@ -593,7 +596,7 @@ struct GraphSet {
             LP_CU(cudaMemcpyAsync(h_changed + (int64_t)it * G, a.changed,
                                   (size_t)G * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
             LP_CU(cudaStreamSynchronize(st));
-            if (sync) cur ^= 1;
+            cur ^= 1;
             bool deactivated = false;
             for (int32_t g = 0; g < G; ++g) {
                 if (multi && !h_active[g]) continue;
