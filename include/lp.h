@@ -208,6 +208,44 @@ lp_status lp_batch_labels_get(lp_batch *b, int32_t index, int32_t *dst, int32_t 
 lp_status lp_batch_modularity(lp_batch *b, int32_t index, double *q);
 
 /* ---------------------------------------------------------------------------
+ * One sweep without any allocation
+ * ------------------------------------------------------------------------- */
+
+/* One synchronous RAK sweep that allocates no memory.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate device
+ * memory at run time because their GPU memory is already fully reserved by
+ * another allocator (a framework's caching allocator, or a pool sized once
+ * under a fixed budget).  Every other entry point allocates; this one calls no
+ * cudaMalloc, cudaFree or allocating library routine.
+ *   n, m, offsets, indices, weights  a CSR as in lp_graph_create, all DEVICE
+ *             pointers (weights may be NULL); it is validated like there and
+ *             every row may hold at most 4096 entries (else LP_EINVAL).
+ *   labels_in   n device labels in [0, n), read only.
+ *   labels_out  n device labels, written; must differ from labels_in.
+ *   strict, seed, iteration  tie rule, non-strict seed and the iteration
+ *             index t of the non-strict key (see lp_rak_params).
+ *   changed   host pointer, receives the number of vertices whose label changed.
+ *   cuda_stream  stream for the work (NULL = legacy default stream); the call
+ *             returns after the sweep has finished.
+ * labels_out equals the labels after one iteration of lp_rak_run in LP_SYNC
+ * mode started from labels_in with iter_offset = iteration.
+ * Scratch: a file-scope device array of about 12.6 MB, held on every GPU that
+ * loads the library until the process exits (the changed counter, the
+ * validation status and per-CTA overflow tables).  The first call on a device
+ * sets it up (looks up its device address, clears it) and synchronizes the
+ * stream; make that first call before any stream capture.  All calls share the
+ * array, so calls that overlap on the GPU (other threads, other streams) race
+ * and their results are undefined; serialize them.
+ * Errors: LP_EINVAL for NULL pointers, sizes out of range, an invalid CSR, a
+ * row longer than 4096, labels outside [0, n), or labels_in == labels_out;
+ * LP_ECUDA. */
+lp_status lp_rak_sweep_noalloc(int32_t n, int64_t m, const int32_t *offsets,
+                               const int32_t *indices, const int32_t *weights,
+                               const int32_t *labels_in, int32_t *labels_out, int32_t strict,
+                               uint64_t seed, int32_t iteration, int64_t *changed,
+                               void *cuda_stream);
+
+/* ---------------------------------------------------------------------------
  * Diagnostics
  * ------------------------------------------------------------------------- */
 

@@ -89,6 +89,9 @@ SIGNATURES = {
     "lp_profile_reset": (ctypes.c_int, []),
     "lp_profile_read": (ctypes.c_int, [ctypes.POINTER(lp_kernel_stat), ctypes.c_int32,
                                        ctypes.POINTER(ctypes.c_int32)]),
+    "lp_rak_sweep_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, _P, _P, _P, _P, _P,
+                                            ctypes.c_int32, ctypes.c_uint64, ctypes.c_int32,
+                                            ctypes.POINTER(ctypes.c_int64), _P]),
     "lp_last_error": (ctypes.c_char_p, []),
     "lp_launch_count": (ctypes.c_int64, []),
 }
@@ -322,6 +325,28 @@ def lp_profile_read() -> dict:
     return {st.name.decode(): {"launches": st.launches, "total_ms": st.total_ms,
                                "vertices": st.vertices, "entries": st.entries, "bytes": st.bytes}
             for st in stats[:cnt.value]}
+
+
+def lp_rak_sweep_noalloc(offsets, indices, weights, labels_in, labels_out, strict=True, seed=0,
+                         iteration=0, stream=None) -> int:
+    """One synchronous sweep without any device allocation (CUDA tensors
+    only); returns the number of vertices that changed label."""
+    arrays = [_int32_buffer(x, nm) for x, nm in ((offsets, "offsets"), (indices, "indices"),
+                                                 (weights, "weights"), (labels_in, "labels_in"),
+                                                 (labels_out, "labels_out"))]
+    if not all(on_dev for (ptr, on_dev, _), x in zip(arrays, (offsets, indices, weights, labels_in,
+                                                              labels_out)) if x is not None):
+        raise ValueError("lp_rak_sweep_noalloc takes device arrays")
+    n = offsets.shape[0] - 1
+    m = indices.shape[0]
+    if stream is None:
+        stream = _stream_of(offsets)
+    changed = ctypes.c_int64()
+    _check(load().lp_rak_sweep_noalloc(int(n), int(m), arrays[0][0], arrays[1][0], arrays[2][0],
+                                       arrays[3][0], arrays[4][0], 1 if strict else 0,
+                                       int(seed) & (2**64 - 1), int(iteration),
+                                       ctypes.byref(changed), stream))
+    return changed.value
 
 
 def lp_last_error() -> str:

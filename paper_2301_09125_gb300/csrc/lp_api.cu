@@ -716,6 +716,10 @@ struct GraphSet {
     }
 };
 
+lp_status lp_fail(lp_status s, const std::string &msg) { return fail(s, msg); }
+
+void lp_add_launches(int64_t n) { g_launches += n; }
+
 }  // namespace lp
 
 struct lp_graph {

@@ -1,0 +1,124 @@
+// Device helpers shared by the sweep kernels: the non-strict tie key, the
+// table slot hash, argmax candidates with their total order, warp / block
+// reductions of candidates and the open-addressing table insert.
+#pragma once
+
+#include <cstdint>
+
+#include "lp_internal.cuh"
+
+namespace lp {
+namespace {
+
+// Non-strict key of `label` at local vertex lv (see lp.h).
+__device__ __forceinline__ uint64_t tie_key(uint64_t key_t, int32_t lv, int32_t label)
+{
+    return stream_at(stream_at(key_t, (uint64_t)lv + 1), (uint64_t)label + 1);
+}
+
+__device__ __forceinline__ uint32_t slot_hash(int32_t label, int lg)
+{
+    // Fibonacci hashing: the top lg bits of label * 2^32/phi
+    return lg == 0 ? 0u : ((uint32_t)label * 0x9E3779B1u) >> (32 - lg);
+}
+
+struct Cand {
+    uint32_t sum;   // summed weight (0 = no candidate)
+    uint32_t npos;  // 0xFFFFFFFF - first position
+    uint64_t h;     // non-strict key (0 in strict mode)
+    int32_t label;
+};
+
+// strictly better: heavier, then smaller non-strict key, then earlier
+__device__ __forceinline__ bool better(const Cand &x, const Cand &y)
+{
+    if (x.sum != y.sum) return x.sum > y.sum;
+    if (x.h != y.h) return x.h < y.h;
+    return x.npos > y.npos;
+}
+
+__device__ __forceinline__ Cand shfl_cand(const Cand &c, int src)
+{
+    Cand r;
+    r.sum = __shfl_sync(FULL, c.sum, src);
+    r.npos = __shfl_sync(FULL, c.npos, src);
+    r.h = __shfl_sync(FULL, c.h, src);
+    r.label = __shfl_sync(FULL, c.label, src);
+    return r;
+}
+
+__device__ __forceinline__ Cand warp_best(Cand c)
+{
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        Cand x;
+        x.sum = __shfl_xor_sync(FULL, c.sum, o);
+        x.npos = __shfl_xor_sync(FULL, c.npos, o);
+        x.h = __shfl_xor_sync(FULL, c.h, o);
+        x.label = __shfl_xor_sync(FULL, c.label, o);
+        if (better(x, c)) c = x;
+    }
+    return c;
+}
+
+__device__ __forceinline__ int ilog2_ceil(uint32_t x)  // smallest lg with 2^lg >= x
+{
+    return x <= 1 ? 0 : 32 - __clz(x - 1);
+}
+
+template <int NT>
+__device__ __forceinline__ Cand block_best(Cand c, Cand *s_red)
+{
+    c = warp_best(c);
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    if (lane == 0) s_red[wib] = c;
+    __syncthreads();
+    if (wib == 0) {
+        c = lane < NT / 32 ? s_red[lane] : Cand{0u, 0u, 0ull, EMPTY};
+        c = warp_best(c);
+    }
+    return c;  // valid in thread 0
+}
+
+template <int NT>
+__device__ __forceinline__ uint32_t block_max(uint32_t v, uint32_t *s_u)
+{
+    v = __reduce_max_sync(FULL, v);
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    if (lane == 0) s_u[wib] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        v = lane < NT / 32 ? s_u[lane] : 0u;
+        v = __reduce_max_sync(FULL, v);
+        if (lane == 0) s_u[NT / 32] = v;
+    }
+    __syncthreads();
+    return s_u[NT / 32];
+}
+
+// insert (l, s, first position p) into an open-addressing table of 2^lg slots,
+// probing at most `limit` slots; false if the window is full of other labels
+__device__ __forceinline__ bool table_add(int32_t *key, int32_t *sum, uint32_t *npos, int lg,
+                                          int limit, int32_t l, int s, uint32_t p)
+{
+    const uint32_t mask = (1u << lg) - 1u;
+    uint32_t h = slot_hash(l, lg);
+    volatile int32_t *vk = key;
+    for (int i = 0; i < limit; ++i) {
+        int32_t cur = vk[h];
+        if (cur == EMPTY) {
+            cur = atomicCAS(key + h, EMPTY, l);
+            if (cur == EMPTY) cur = l;
+        }
+        if (cur == l) {
+            atomicAdd(sum + h, s);
+            atomicMax(npos + h, 0xFFFFFFFFu - p);
+            return true;
+        }
+        h = (h + 1) & mask;
+    }
+    return false;
+}
+
+}  // namespace
+}  // namespace lp
