@@ -9,6 +9,7 @@ CUDA events on the stream the library launches on.
 
 Workloads (synthetic stand-ins for the paper's SuiteSparse classes):
   rmat22    R-MAT scale 22, edge factor 16, weights 1-4, asynchronous (default)
+  rmat21    the same at scale 21 (profiling size)
   road4096  4096 x 4096 road-like grid, weights 1-16 (sync or async)
   sbm10k    planted partition, 10,000 vertices, synchronous
   kmer8m    k-mer-like chains, 8M vertices
@@ -46,6 +47,7 @@ L2_BYTES = 129 * 2**20
 
 WORKLOADS = {
     "rmat22": dict(mode="async", waves=2, strict=True, tolerance=0.05, max_iter=20),
+    "rmat21": dict(mode="async", waves=2, strict=True, tolerance=0.05, max_iter=20),
     "road4096": dict(mode="async", waves=31, strict=True, tolerance=0.05, max_iter=20),
     "sbm10k": dict(mode="sync", waves=31, strict=True, tolerance=0.05, max_iter=20),
     "kmer8m": dict(mode="async", waves=31, strict=True, tolerance=0.05, max_iter=20),

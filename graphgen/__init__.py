@@ -158,6 +158,7 @@ def num_threads() -> int:
 WORKLOADS = {
     "sbm10k": dict(kind="sbm_planted", n=10_000, k=20, p_in=0.02, p_out=0.0005, seed=1),
     "rmat22": dict(kind="rmat", scale=22, edge_factor=16, seed=1, wmin=1, wmax=4),
+    "rmat21": dict(kind="rmat", scale=21, edge_factor=16, seed=1, wmin=1, wmax=4),
     "road4096": dict(kind="grid_road", side=4096, seed=1, wmin=1, wmax=16),
     "kmer8m": dict(kind="kmer_like", n=8 * 1024 * 1024, seed=1),
 }

@@ -64,9 +64,10 @@ enum { LP_SYNC = 0, LP_ASYNC = 1 };
 enum {
     LP_FLAG_DEVICE_PTRS = 1,     /* offsets/indices/weights are device pointers */
     LP_FLAG_CHECK_SYMMETRIC = 2, /* also reject a CSR whose pattern/weights are not symmetric */
-    LP_FLAG_BORROW = 4           /* with DEVICE_PTRS: keep the caller's indices/weights
-                                    instead of copying them (caller keeps them alive and
-                                    unchanged until lp_graph_destroy) */
+    LP_FLAG_BORROW = 4           /* with DEVICE_PTRS: keep the caller's arrays instead of
+                                    copying them (caller keeps them alive and unchanged
+                                    until lp_graph_destroy); indices and weights that do
+                                    not start on a 16-byte boundary are copied anyway */
 };
 
 /* Parameters of one RAK run (Sec. 3.2). */

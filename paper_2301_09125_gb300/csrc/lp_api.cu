@@ -241,9 +241,11 @@ struct GraphSet {
     uint32_t *gt_np = nullptr;
     int64_t gt_slots = 0;
     // modularity and label staging scratch
-    unsigned long long *kc = nullptr, *macc = nullptr, *mpart = nullptr, *h_macc = nullptr;
+    unsigned long long *kc = nullptr, *macc = nullptr, *h_macc = nullptr;
     int64_t kc_cap = 0;
-    int mpart_blocks = 0;
+    std::vector<double> q_cache;  // per-graph modularity of the current labels
+    bool q_valid = false;
+    int32_t *g_sel = nullptr;     // per graph: buffer holding its final labels
     int32_t *lab_tmp = nullptr;
     IngestOut *d_ing = nullptr, *h_ing = nullptr;
     int64_t *d_counts = nullptr, *h_counts = nullptr;
@@ -284,8 +286,8 @@ struct GraphSet {
         f(gt_np);
         f(kc);
         f(macc);
-        f(mpart);
         fh(h_macc);
+        f(g_sel);
         f(lab_tmp);
         f(d_ing);
         fh(h_ing);
@@ -299,7 +301,8 @@ struct GraphSet {
         changed = h_changed = h_active = nullptr;
         gt_key = gt_sum = nullptr;
         gt_np = nullptr;
-        kc = macc = mpart = h_macc = nullptr;
+        kc = macc = h_macc = nullptr;
+        g_sel = nullptr;
         lab_tmp = nullptr;
         d_ing = h_ing = nullptr;
         d_counts = h_counts = nullptr;
@@ -324,8 +327,6 @@ struct GraphSet {
         LP_TRY(host_alloc(&h_ing, 1, "ingest status"));
         LP_TRY(dev_alloc(&d_counts, 3 * NUM_BUCKETS, "bucket counts", st, device));
         LP_TRY(host_alloc(&h_counts, 3 * NUM_BUCKETS, "bucket counts"));
-        LP_TRY(dev_alloc(&macc, 2, "modularity accumulators", st, device));
-        LP_TRY(host_alloc(&h_macc, 2, "modularity accumulators"));
         LP_CU(cudaEventCreate(&ev0));
         LP_CU(cudaEventCreate(&ev1));
         return LP_OK;
@@ -533,6 +534,7 @@ struct GraphSet {
                                   cudaMemcpyHostToDevice, st));
         }
         std::fill(final_buf.begin(), final_buf.end(), 0);
+        q_valid = false;
         for (auto &r : results) r = lp_rak_result{0, 0, 0, 0.0f};
         int cur = 0;
         const bool prof = g_prof_on.load();
@@ -544,6 +546,7 @@ struct GraphSet {
         a.off = off;
         a.idx = idx;
         a.wts = wts;
+        a.ne = ne;
         a.vgraph = vgraph;
         a.g_vbase = g_vbase;
         a.g_ebase = g_ebase;
@@ -645,61 +648,73 @@ struct GraphSet {
         }
         history.assign((size_t)results[0].iterations, 0);
         for (int32_t i = 0; i < results[0].iterations; ++i) history[i] = h_changed[(int64_t)i * G];
+        if (multi) LP_TRY(gather_final_labels());
         return LP_OK;
     }
 
-    // modularity of graph g under labels lab_g (device, n_g entries, validated)
-    lp_status modularity(int32_t g, const int32_t *lab_g, double *q)
+    // Graphs of a batch stop in different iterations, so their final labels
+    // sit in either buffer; copy them all into buffer 0.
+    lp_status gather_final_labels()
     {
-        const int32_t n = h_n[(size_t)g];
-        const int64_t m = h_m[(size_t)g];
-        if (n > kc_cap) {
+        bool any = false;
+        for (int f : final_buf) any = any || f != 0;
+        if (!any) return LP_OK;
+        if (!g_sel) LP_TRY(dev_alloc(&g_sel, G, "graph buffer selector", st, device));
+        std::vector<int32_t> sel(final_buf.begin(), final_buf.end());
+        LP_CU(cudaMemcpyAsync(g_sel, sel.data(), (size_t)G * sizeof(int32_t),
+                              cudaMemcpyHostToDevice, st));
+        Launches L;
+        if (merge_final_labels(lab[0], lab[1], nv, vgraph, g_sel, st, &L.n) != 0)
+            return fail(LP_ECUDA, cuda_msg("label merge", cudaGetLastError()));
+        LP_CU(cudaStreamSynchronize(st));  // sel lives on the host stack
+        std::fill(final_buf.begin(), final_buf.end(), 0);
+        return LP_OK;
+    }
+
+    // Modularity of every graph under `labels` (nv device labels, valid),
+    // into q_cache.
+    lp_status modularity_all(const int32_t *labels)
+    {
+        if (nv > kc_cap) {
             if (kc) cudaFreeAsync(kc, st);
             kc = nullptr;
             kc_cap = 0;
-            LP_TRY(dev_alloc(&kc, n, "community weights", st, device));
-            kc_cap = n;
+            LP_TRY(dev_alloc(&kc, nv, "community weights", st, device));
+            kc_cap = nv;
         }
-        const int blocks = std::max(1, std::min((int)((n + 255) / 256), num_sms * 4));
-        if (blocks > mpart_blocks) {
-            if (mpart) cudaFreeAsync(mpart, st);
-            mpart = nullptr;
-            mpart_blocks = 0;
-            LP_TRY(dev_alloc(&mpart, 2 * (int64_t)blocks, "modularity partials", st, device));
-            mpart_blocks = blocks;
+        if (!macc) {
+            LP_TRY(dev_alloc(&macc, 4 * (int64_t)G, "modularity accumulators", st, device));
+            LP_TRY(host_alloc(&h_macc, 4 * (int64_t)G, "modularity accumulators"));
         }
-        std::vector<unsigned long long> part(2 * (size_t)blocks);
         Launches L;
-        if (n > 0) LP_CU(cudaMemsetAsync(kc, 0, (size_t)n * sizeof(unsigned long long), st));
-        LP_CU(cudaMemsetAsync(macc, 0, 2 * sizeof(unsigned long long), st));
+        if (nv > 0) LP_CU(cudaMemsetAsync(kc, 0, (size_t)nv * sizeof(unsigned long long), st));
+        LP_CU(cudaMemsetAsync(macc, 0, 4 * (size_t)G * sizeof(unsigned long long), st));
         ModArgs ma{};
-        ma.off = off + h_vbase[(size_t)g] + g;
-        ma.idx = idx + h_ebase[(size_t)g];
-        ma.wts = wts ? wts + h_ebase[(size_t)g] : nullptr;
-        ma.lab = lab_g;
-        ma.n = n;
-        ma.m = m;
+        ma.off = off;
+        ma.idx = idx;
+        ma.wts = wts;
+        ma.lab = labels;
+        ma.list = list;
+        ma.ne = ne;
+        ma.vgraph = vgraph;
+        ma.g_vbase = g_vbase;
+        ma.g_ebase = g_ebase;
         ma.kc = kc;
         ma.acc = macc;
-        if (modularity_entries(ma, num_sms, st, &L.n) != 0)
+        if (modularity_launch(ma, bb, bl, nv, vgraph != nullptr, num_sms, st, &L.n) != 0)
             return fail(LP_ECUDA, cuda_msg("modularity launch", cudaGetLastError()));
-        if (modularity_sumsq(kc, n, mpart, blocks, st, &L.n) != 0)
-            return fail(LP_ECUDA, cuda_msg("modularity launch", cudaGetLastError()));
-        LP_CU(cudaMemcpyAsync(h_macc, macc, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
-                              st));
-        LP_CU(cudaMemcpyAsync(part.data(), mpart, part.size() * sizeof(unsigned long long),
+        LP_CU(cudaMemcpyAsync(h_macc, macc, 4 * (size_t)G * sizeof(unsigned long long),
                               cudaMemcpyDeviceToHost, st));
         LP_CU(cudaStreamSynchronize(st));
-        unsigned __int128 s = 0;
-        for (int b = 0; b < blocks; ++b)
-            s += ((unsigned __int128)part[2 * (size_t)b] << 64) | part[2 * (size_t)b + 1];
-        const unsigned long long l_in = h_macc[0], two_m = h_macc[1];
-        if (two_m == 0) {
-            *q = 0.0;
-            return LP_OK;
+        q_cache.assign((size_t)G, 0.0);
+        for (int32_t g = 0; g < G; ++g) {
+            const unsigned long long *acc = h_macc + 4 * (size_t)g;
+            const unsigned long long l_in = acc[0], two_m = acc[1];
+            const unsigned __int128 s2 = ((unsigned __int128)acc[2] << 64) | acc[3];
+            if (two_m == 0) continue;  // no entries: Q = 0
+            const double dm = (double)two_m;
+            q_cache[(size_t)g] = (double)l_in / dm - (double)s2 / (dm * dm);
         }
-        const double dm = (double)two_m;
-        *q = (double)l_in / dm - (double)s / (dm * dm);
         return LP_OK;
     }
 
@@ -778,7 +793,11 @@ lp_status lp_graph_create(int32_t n, int64_t m, const int32_t *offsets, const in
     s.h_vbase = {0};
     s.h_ebase = {0};
     s.max_n = n;
-    if (flags & LP_FLAG_BORROW) {
+    // the sweep reads indices and weights in aligned 16-byte blocks: borrow
+    // them only when they start on a 16-byte boundary, otherwise copy
+    auto aligned16 = [](const void *p) { return ((uintptr_t)p & 15u) == 0; };
+    const bool borrow = (flags & LP_FLAG_BORROW) && aligned16(indices) && aligned16(weights);
+    if (borrow) {
         s.off = const_cast<int32_t *>(offsets);
         s.idx = const_cast<int32_t *>(indices);
         s.wts = const_cast<int32_t *>(weights);
@@ -794,6 +813,8 @@ lp_status lp_graph_create(int32_t n, int64_t m, const int32_t *offsets, const in
                 LP_CU(cudaMemcpyAsync(s.wts, weights, (size_t)m * sizeof(int32_t), kind, s.st));
         }
     }
+    if (((uintptr_t)s.idx & 15u) || ((uintptr_t)s.wts & 15u))
+        return fail(LP_ECUDA, "device allocation is not 16-byte aligned");
     LP_TRY(dev_alloc(&s.g_n, 1, "graph sizes", s.st, s.device));
     LP_CU(cudaMemcpyAsync(s.g_n, &n, sizeof(int32_t), cudaMemcpyHostToDevice, s.st));
     // a1: validation keeps every later kernel in bounds
@@ -878,7 +899,10 @@ lp_status lp_modularity(lp_graph *g, const int32_t *labels, int32_t labels_on_de
         LP_TRY(s.read_ingest(-1));
         lab = s.lab_tmp;
     }
-    return s.modularity(0, lab, q);
+    LP_TRY(s.modularity_all(lab));
+    s.q_valid = labels == nullptr;
+    *q = s.q_cache[0];
+    return LP_OK;
 }
 
 lp_status lp_batch_create(int32_t count, const lp_graph_desc *graphs, uint32_t flags,
@@ -1022,7 +1046,12 @@ lp_status lp_batch_modularity(lp_batch *b, int32_t index, double *q)
     if (index < 0 || index >= b->s.G) return fail(LP_EINVAL, "graph index out of range");
     DeviceGuard dg(b->s.device);
     lp::GraphSet &s = b->s;
-    return s.modularity(index, s.lab[s.final_buf[(size_t)index]] + s.h_vbase[(size_t)index], q);
+    if (!s.q_valid) {
+        LP_TRY(s.modularity_all(s.lab[0]));  // final labels are gathered in buffer 0
+        s.q_valid = true;
+    }
+    *q = s.q_cache[(size_t)index];
+    return LP_OK;
 }
 
 lp_status lp_profile_enable(int32_t on)

@@ -219,6 +219,14 @@ __global__ void k_check_labels(const int32_t *lab, int32_t nv, const int32_t *vg
     }
 }
 
+__global__ void k_merge_final(int32_t *lab0, const int32_t *lab1, int32_t nv,
+                              const int32_t *vgraph, const int32_t *g_sel)
+{
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nv;
+         v += (int64_t)gridDim.x * blockDim.x)
+        if (g_sel[vgraph[v]]) lab0[v] = lab1[v];
+}
+
 __global__ void k_degrees_of(const int32_t *off, const int32_t *vgraph, const int32_t *list,
                              int64_t len, int32_t *deg)
 {
@@ -401,6 +409,15 @@ int wave_prepare()
             cudaSuccess)
         return -1;
     return 0;
+}
+
+int merge_final_labels(int32_t *lab0, const int32_t *lab1, int32_t nv, const int32_t *vgraph,
+                       const int32_t *g_sel, cudaStream_t st, int64_t *launches)
+{
+    if (nv == 0) return 0;
+    k_merge_final<<<grid_for(nv, 256, 8192), 256, 0, st>>>(lab0, lab1, nv, vgraph, g_sel);
+    ++*launches;
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 int fill_iota(int32_t *lab, int32_t nv, const int32_t *vgraph, const int32_t *g_vbase,

@@ -45,6 +45,7 @@ struct SweepArgs {
     int32_t *lab_out;        // labels written
     const int32_t *list;     // bucket entries (global vertex ids)
     int64_t len;             // bucket length
+    int64_t ne;              // entries in the arena (idx / wts are read in 16-byte blocks)
     // graph set (null for a single graph: every base is 0)
     const int32_t *vgraph;   // graph of each global vertex
     const int32_t *g_vbase;  // first global vertex of each graph
@@ -66,16 +67,20 @@ struct SweepArgs {
     int64_t gtab_slots;
 };
 
-// Modularity arguments (one graph; pointers already offset to that graph).
+// Modularity arguments (a whole graph set; graph layout as for SweepArgs).
 struct ModArgs {
-    const int32_t *off;        // n + 1 local row offsets
-    const int32_t *idx;        // m local neighbour ids
-    const int32_t *wts;        // m weights or null
-    const int32_t *lab;        // n labels in [0, n)
-    int32_t n;
-    int64_t m;
-    unsigned long long *kc;    // [n] K_c accumulators (zeroed by the caller)
-    unsigned long long *acc;   // [2] L and 2m accumulators (zeroed by the caller)
+    const int32_t *off;
+    const int32_t *idx;
+    const int32_t *wts;        // null = unit weights
+    const int32_t *lab;        // labels of every vertex (local ids)
+    const int32_t *list;       // bucket entries
+    int64_t len;
+    int64_t ne;                // entries in the arena
+    const int32_t *vgraph;     // null for a single graph
+    const int32_t *g_vbase;
+    const int64_t *g_ebase;
+    unsigned long long *kc;    // [nv] K_c of community c of graph g at vbase_g + c (zeroed)
+    unsigned long long *acc;   // [4 G]: L, 2m, S high, S low per graph (zeroed)
 };
 
 // ----------------------------------------------------------------------------
@@ -158,14 +163,16 @@ int wave_prepare();  // per-device kernel attributes
 int wave_partition(const int32_t *list, int64_t list_len, const int64_t *bucket_begin,
                    const int32_t *vgraph, const int32_t *g_vbase, int waves, int32_t *hist,
                    int64_t *d_totals, int32_t *out, cudaStream_t st, int64_t *launches);
+// lab0[v] = lab1[v] for the vertices of graphs g with g_sel[g] != 0
+int merge_final_labels(int32_t *lab0, const int32_t *lab1, int32_t nv, const int32_t *vgraph,
+                       const int32_t *g_sel, cudaStream_t st, int64_t *launches);
 int fill_iota(int32_t *lab, int32_t nv, const int32_t *vgraph, const int32_t *g_vbase,
               cudaStream_t st, int64_t *launches);
 int check_labels(const int32_t *lab, int32_t nv, const int32_t *vgraph, const int32_t *g_vbase,
                  const int32_t *g_n, IngestOut *d_out, cudaStream_t st, int64_t *launches);
 
-int modularity_entries(const ModArgs &a, int num_sms, cudaStream_t st, int64_t *launches);
-// sum of K_c^2 over kc[0..n) into per-block 128-bit partials (hi, lo pairs)
-int modularity_sumsq(const unsigned long long *kc, int64_t n, unsigned long long *partials,
-                     int blocks, cudaStream_t st, int64_t *launches);
+// Entry and square passes of the modularity of every graph of a set.
+int modularity_launch(const ModArgs &a, const int64_t *bucket_begin, const int64_t *bucket_len,
+                      int64_t nslots, bool multi, int num_sms, cudaStream_t st, int64_t *launches);
 
 }  // namespace lp

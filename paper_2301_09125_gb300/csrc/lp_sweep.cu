@@ -28,12 +28,13 @@ namespace lp {
 namespace {
 
 struct Vtx {
-    int32_t v;   // global vertex
-    int32_t g;   // graph
-    int32_t vb;  // first global vertex of the graph
-    int32_t lv;  // local vertex id
-    int32_t d;   // degree
-    int64_t e0;  // global index of the first entry
+    int32_t v;    // global vertex
+    int32_t g;    // graph
+    int32_t vb;   // first global vertex of the graph
+    int32_t lv;   // local vertex id
+    int32_t d;    // degree
+    int32_t own;  // label at the start of the iteration
+    int64_t e0;   // global index of the first entry
 };
 
 template <bool MULTI>
@@ -53,8 +54,21 @@ __device__ __forceinline__ bool load_vtx(const SweepArgs &a, int32_t v, Vtx &x)
     const int32_t re = __ldg(a.off + ob + 1);
     x.d = re - rs;
     x.e0 = (MULTI ? a.g_ebase[x.g] : 0) + rs;
+    x.own = __ldg(a.lab_in + v);
     return true;
 }
+
+// Next work item of a grid-stride loop, loaded one step ahead so that its
+// dependent loads (list entry, row bounds, own label) overlap the current one.
+template <bool MULTI>
+struct VtxPipe {
+    Vtx next;
+    bool next_ok = false;
+    __device__ __forceinline__ void fetch(const SweepArgs &a, int64_t item)
+    {
+        next_ok = item < a.len && load_vtx<MULTI>(a, a.list[item], next);
+    }
+};
 
 // Label of neighbour u (local id u, global index gi) as seen by this launch.
 // Neither buffer is written at an address this launch reads: lab_in is only
@@ -62,15 +76,10 @@ __device__ __forceinline__ bool load_vtx(const SweepArgs &a, int32_t v, Vtx &x)
 // written by earlier launches, so both go through the read-only path.
 __device__ __forceinline__ int32_t neighbour_label(const SweepArgs &a, int64_t gi, int32_t u)
 {
-    if (a.waves > 1 && fastmod((uint32_t)u, a.wave_magic, a.waves) < a.wave_k)
-        return __ldg(a.lab_out + gi);
-    return __ldg(a.lab_in + gi);
+    const bool earlier = a.waves > 1 && fastmod((uint32_t)u, a.wave_magic, a.waves) < a.wave_k;
+    return __ldg((earlier ? a.lab_out : a.lab_in) + gi);
 }
 
-__device__ __forceinline__ int32_t own_label(const SweepArgs &a, int64_t v)
-{
-    return __ldg(a.lab_in + v);
-}
 
 // ----------------------------------------------------------------------------
 // small bucket: several rows per warp chunk
@@ -85,11 +94,11 @@ __global__ void __launch_bounds__(256) k_small(SweepArgs a)
 
     for (int64_t tile = wid; tile * 32 < a.len; tile += nw) {
         const int64_t i = tile * 32 + lane;
-        Vtx x{0, 0, 0, 0, 0, 0};
+        Vtx x{0, 0, 0, 0, 0, 0, 0};
         bool ok = false;
         if (i < a.len) ok = load_vtx<MULTI>(a, a.list[i], x);
         const int d = ok ? x.d : 0;
-        const int32_t own = ok ? own_label(a, x.v) : 0;
+        const int32_t own = ok ? x.own : 0;
 
         int P = d;  // inclusive prefix of degrees over the tile
 #pragma unroll
@@ -175,6 +184,103 @@ __global__ void __launch_bounds__(256) k_small(SweepArgs a)
 }
 
 // ----------------------------------------------------------------------------
+// Entry quads: a row is read as aligned 16-byte blocks of 4 entries (column
+// index and weight), so each lane has four label gathers in flight at once.
+// ----------------------------------------------------------------------------
+struct Quad {
+    int32_t l[4];  // label of each entry, EMPTY outside the row
+    int32_t w[4];  // weight, 0 outside the row
+};
+
+__device__ __forceinline__ Quad empty_quad()
+{
+    Quad q;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        q.l[j] = EMPTY;
+        q.w[j] = 0;
+    }
+    return q;
+}
+
+// entries 4*blk .. 4*blk+3 of the arena, kept where they lie in [lo, hi)
+__device__ __forceinline__ Quad load_quad(const SweepArgs &a, int64_t blk, int64_t lo, int64_t hi,
+                                          int32_t vb)
+{
+    const int64_t e0 = blk * 4;
+    int32_t u[4], w[4];
+    if (e0 + 3 < a.ne) {
+        const int4 I = __ldg(reinterpret_cast<const int4 *>(a.idx) + blk);
+        u[0] = I.x;
+        u[1] = I.y;
+        u[2] = I.z;
+        u[3] = I.w;
+        if (a.wts) {
+            const int4 W = __ldg(reinterpret_cast<const int4 *>(a.wts) + blk);
+            w[0] = W.x;
+            w[1] = W.y;
+            w[2] = W.z;
+            w[3] = W.w;
+        } else {
+            w[0] = w[1] = w[2] = w[3] = 1;
+        }
+    } else {  // the arena's last, partial block
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const bool ok = e0 + j < a.ne;
+            u[j] = ok ? __ldg(a.idx + e0 + j) : 0;
+            w[j] = ok ? (a.wts ? __ldg(a.wts + e0 + j) : 1) : 0;
+        }
+    }
+    Quad q;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const bool in = e0 + j >= lo && e0 + j < hi;
+        q.l[j] = in ? neighbour_label(a, (int64_t)vb + u[j], u[j]) : EMPTY;
+        q.w[j] = in ? w[j] : 0;
+    }
+    return q;
+}
+
+// Best candidate of the warp under the total order of `better`, valid in
+// every lane; lanes hold their local best (sum 0 = none).
+__device__ __forceinline__ Cand warp_argmax(const Cand &c, int strict)
+{
+    const uint32_t mx = __reduce_max_sync(FULL, c.sum);
+    bool cand = c.sum == mx;
+    if (!strict) {
+        const uint32_t hh = __reduce_min_sync(FULL, cand ? (uint32_t)(c.h >> 32) : 0xFFFFFFFFu);
+        cand = cand && (uint32_t)(c.h >> 32) == hh;
+        const uint32_t hl = __reduce_min_sync(FULL, cand ? (uint32_t)c.h : 0xFFFFFFFFu);
+        cand = cand && (uint32_t)c.h == hl;
+    }
+    const uint32_t np = __reduce_max_sync(FULL, cand ? c.npos : 0u);
+    cand = cand && c.npos == np;
+    const int src = __ffs(__ballot_sync(FULL, cand)) - 1;
+    Cand r;
+    r.sum = mx;
+    r.npos = np;
+    r.h = __shfl_sync(FULL, c.h, src);
+    r.label = __shfl_sync(FULL, c.label, src);
+    return r;
+}
+
+template <int NT>
+__device__ __forceinline__ Cand block_argmax(const Cand &c, int strict, Cand *s_red)
+{
+    const Cand w = warp_argmax(c, strict);
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    if (lane == 0) s_red[wib] = w;
+    __syncthreads();
+    Cand r{0u, 0u, 0ull, EMPTY};
+    if (wib == 0) {
+        if (lane < NT / 32) r = s_red[lane];
+        r = warp_argmax(r, strict);
+    }
+    return r;  // valid in warp 0
+}
+
+// ----------------------------------------------------------------------------
 // warp bucket: one warp per vertex, private shared table
 // ----------------------------------------------------------------------------
 constexpr int WARP_LG = 8;  // log2(WARP_TABLE)
@@ -203,45 +309,45 @@ __global__ void __launch_bounds__(256) k_warp(SweepArgs a)
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     uint32_t my_changed = 0;
 
+    VtxPipe<MULTI> pipe;
+    pipe.fetch(a, wid);
     for (int64_t item = wid; item < a.len; item += nw) {
-        Vtx x;
-        if (!load_vtx<MULTI>(a, a.list[item], x)) continue;  // warp-uniform
-        const int32_t own = own_label(a, x.v);
-        for (int k0 = 0; k0 < x.d; k0 += 32) {
-            const int k = k0 + lane;
-            const bool act = k < x.d;
-            int w = 0;
-            int32_t l = EMPTY;
-            if (act) {
-                const int64_t e = x.e0 + k;
-                const int32_t u = __ldg(a.idx + e);
-                w = a.wts ? __ldg(a.wts + e) : 1;
-                l = neighbour_label(a, (int64_t)x.vb + u, u);
-            }
-            const unsigned grp = __match_any_sync(FULL, (unsigned)l);
-            const int s = __reduce_add_sync(grp, w);
-            if (act && lane == __ffs(grp) - 1) {
-                // one leader per label in this chunk; chunks run in row order, so
-                // the claiming leader holds the label's first position
-                uint32_t h = slot_hash(l, WARP_LG);
-                for (int probe = 0; probe < WARP_TABLE; ++probe) {  // <= 128 labels: always found
-                    int32_t cur = tk[h];
-                    if (cur == EMPTY) {
-                        cur = atomicCAS(tk_atomic + h, EMPTY, l);
+        const Vtx x = pipe.next;
+        const bool ok = pipe.next_ok;
+        pipe.fetch(a, item + nw);
+        if (!ok) continue;  // warp-uniform
+        const int32_t own = x.own;
+        const int64_t lo = x.e0, hi = x.e0 + x.d;
+        const int64_t b_hi = (hi - 1) >> 2;
+        for (int64_t base = lo >> 2; base <= b_hi; base += 32) {
+            const int64_t blk = base + lane;
+            const Quad q = blk <= b_hi ? load_quad(a, blk, lo, hi, x.vb) : empty_quad();
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int32_t l = q.l[j];
+                const unsigned grp = __match_any_sync(FULL, (unsigned)l);
+                const int s = __reduce_add_sync(grp, q.w[j]);
+                if (l != EMPTY && lane == __ffs(grp) - 1) {
+                    // one leader per label in this round, so plain updates suffice;
+                    // the leader (lowest lane) holds the round's first position
+                    const uint32_t np = 0xFFFFFFFFu - (uint32_t)(blk * 4 + j - lo);
+                    uint32_t h = slot_hash(l, WARP_LG);
+                    for (int probe = 0; probe < WARP_TABLE; ++probe) {  // <= 128 labels: found
+                        int32_t cur = tk[h];
                         if (cur == EMPTY) {
-                            ts[h] = s;
-                            tp[h] = 0xFFFFFFFFu - (uint32_t)k;
+                            cur = atomicCAS(tk_atomic + h, EMPTY, l);
+                            if (cur == EMPTY) cur = l;
+                        }
+                        if (cur == l) {
+                            ts[h] = ts[h] + s;
+                            if (np > tp[h]) tp[h] = np;
                             break;
                         }
+                        h = (h + 1) & (WARP_TABLE - 1);
                     }
-                    if (cur == l) {
-                        ts[h] = ts[h] + s;
-                        break;
-                    }
-                    h = (h + 1) & (WARP_TABLE - 1);
                 }
+                __syncwarp();
             }
-            __syncwarp();
         }
 
         Cand best{0u, 0u, 0ull, EMPTY};
@@ -275,7 +381,7 @@ __global__ void __launch_bounds__(256) k_warp(SweepArgs a)
                 }
             }
         }
-        best = warp_best(best);
+        best = warp_argmax(best, a.strict);
         if (lane == 0) {
             a.lab_out[x.v] = best.label;
             if (best.label != own) {
@@ -323,79 +429,75 @@ __global__ void __launch_bounds__(NT) k_cta(SweepArgs a)
     }
     uint32_t my_changed = 0;
 
+    VtxPipe<MULTI> pipe;
+    pipe.fetch(a, blockIdx.x);
     for (int64_t item = blockIdx.x; item < a.len; item += gridDim.x) {
-        Vtx x;
-        if (!load_vtx<MULTI>(a, a.list[item], x)) continue;  // block-uniform
-        const int32_t own = own_label(a, x.v);
+        const Vtx x = pipe.next;
+        const bool ok = pipe.next_ok;
+        pipe.fetch(a, item + gridDim.x);
+        if (!ok) continue;  // block-uniform
+        const int32_t own = x.own;
+        // shared slots in use for this vertex: 2^lg >= 2d (up to the table size)
+        const int lg = min(ilog2_ceil(2u * (uint32_t)x.d), LG);
+
         // overflow table slots for this vertex: 2^glg >= 2d, within the allocation
         int glg = SPILL ? ilog2_ceil(2u * (uint32_t)x.d) : 0;
         if (SPILL && ((int64_t)1 << glg) > a.gtab_slots) glg = 63 - __clzll(a.gtab_slots);
-
-        for (int k0 = 0; k0 < x.d; k0 += NT) {
-            const int k = k0 + threadIdx.x;
-            const bool act = k < x.d;
-            int w = 0;
-            int32_t l = EMPTY;
-            if (act) {
-                const int64_t e = x.e0 + k;
-                const int32_t u = __ldg(a.idx + e);
-                w = a.wts ? __ldg(a.wts + e) : 1;
-                l = neighbour_label(a, (int64_t)x.vb + u, u);
-            }
-            const unsigned grp = __match_any_sync(FULL, (unsigned)l);
-            const int s = __reduce_add_sync(grp, w);
-            if (act && (threadIdx.x & 31) == __ffs(grp) - 1) {
-                const bool in_shared = table_add(tk, ts, tp, LG, SPILL ? HUB_PROBE : CAP, l, s, k);
-                if (SPILL && !in_shared) {
-                    s_spilled = 1;
-                    table_add(gk, gs, gp, glg, 1 << glg, l, s, k);
+        const int64_t lo = x.e0, hi = x.e0 + x.d;
+        const int64_t b_hi = (hi - 1) >> 2;
+        for (int64_t base = lo >> 2; base <= b_hi; base += NT) {
+            const int64_t blk = base + threadIdx.x;
+            const Quad q = blk <= b_hi ? load_quad(a, blk, lo, hi, x.vb) : empty_quad();
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int32_t l = q.l[j];
+                const unsigned grp = __match_any_sync(FULL, (unsigned)l);
+                const int s = __reduce_add_sync(grp, q.w[j]);
+                if (l != EMPTY && (threadIdx.x & 31) == __ffs(grp) - 1) {
+                    const uint32_t p = (uint32_t)(blk * 4 + j - lo);
+                    const bool in_shared =
+                        table_add(tk, ts, tp, lg, SPILL ? HUB_PROBE : (1 << lg), l, s, p);
+                    if (SPILL && !in_shared) {
+                        s_spilled = 1;
+                        table_add(gk, gs, gp, glg, 1 << glg, l, s, p);
+                    }
                 }
             }
         }
         __syncthreads();
         const bool spilled = SPILL && s_spilled;
+        const int sslots = 1 << lg;
+        const int gslots = spilled ? (1 << glg) : 0;
 
         Cand best{0u, 0u, 0ull, EMPTY};
-        const int gslots = spilled ? (1 << glg) : 0;
-        if (a.strict) {
-            for (int j = threadIdx.x; j < CAP + gslots; j += NT) {
-                int32_t *K = j < CAP ? tk + j : gk + (j - CAP);
-                int32_t *S = j < CAP ? ts + j : gs + (j - CAP);
-                uint32_t *Q = j < CAP ? tp + j : gp + (j - CAP);
-                const int32_t key = *K;
-                if (key != EMPTY) {
-                    const Cand c{(uint32_t)*S, *Q, 0ull, key};
-                    if (better(c, best)) best = c;
-                    *K = EMPTY;
-                    *S = 0;
-                    *Q = 0;
-                }
-            }
-        } else {
-            uint32_t mx = 0;
-            for (int j = threadIdx.x; j < CAP + gslots; j += NT) {
-                const int32_t key = j < CAP ? tk[j] : gk[j - CAP];
-                if (key != EMPTY) mx = max(mx, (uint32_t)(j < CAP ? ts[j] : gs[j - CAP]));
+        uint32_t mx = 0;
+        if (!a.strict) {
+            for (int j = threadIdx.x; j < sslots + gslots; j += NT) {
+                const int32_t key = j < sslots ? tk[j] : gk[j - sslots];
+                if (key != EMPTY) mx = max(mx, (uint32_t)(j < sslots ? ts[j] : gs[j - sslots]));
             }
             mx = block_max<NT>(mx, s_u);
-            const uint64_t ktv = stream_at(a.key_t, (uint64_t)x.lv + 1);
-            for (int j = threadIdx.x; j < CAP + gslots; j += NT) {
-                int32_t *K = j < CAP ? tk + j : gk + (j - CAP);
-                int32_t *S = j < CAP ? ts + j : gs + (j - CAP);
-                uint32_t *Q = j < CAP ? tp + j : gp + (j - CAP);
-                const int32_t key = *K;
-                if (key != EMPTY) {
-                    if ((uint32_t)*S == mx) {
-                        const Cand c{mx, *Q, stream_at(ktv, (uint64_t)key + 1), key};
-                        if (better(c, best)) best = c;
-                    }
-                    *K = EMPTY;
-                    *S = 0;
-                    *Q = 0;
+        }
+        const uint64_t ktv = stream_at(a.key_t, (uint64_t)x.lv + 1);
+        for (int j = threadIdx.x; j < sslots + gslots; j += NT) {
+            int32_t *K = j < sslots ? tk + j : gk + (j - sslots);
+            int32_t *S = j < sslots ? ts + j : gs + (j - sslots);
+            uint32_t *Q = j < sslots ? tp + j : gp + (j - sslots);
+            const int32_t key = *K;
+            if (key != EMPTY) {
+                if (a.strict) {
+                    const Cand c{(uint32_t)*S, *Q, 0ull, key};
+                    if (better(c, best)) best = c;
+                } else if ((uint32_t)*S == mx) {
+                    const Cand c{mx, *Q, stream_at(ktv, (uint64_t)key + 1), key};
+                    if (better(c, best)) best = c;
                 }
+                *K = EMPTY;
+                *S = 0;
+                *Q = 0;
             }
         }
-        best = block_best<NT>(best, s_red);
+        best = block_argmax<NT>(best, a.strict, s_red);
         if (threadIdx.x == 0) {
             a.lab_out[x.v] = best.label;
             if (best.label != own) {
