@@ -237,9 +237,14 @@ struct GraphSet {
     std::vector<lp_rak_result> results;
     std::vector<int64_t> history;  // graph 0
     // hub overflow tables
-    int32_t *gt_key = nullptr, *gt_sum = nullptr;
-    uint32_t *gt_np = nullptr;
-    int64_t gt_slots = 0;
+    // hub segments: tasks of the hub bucket (plain) and of its part in each wave,
+    // global tables (sized for all hubs), used lists and per-task counters
+    HubTask *htask = nullptr, *htask_w = nullptr;
+    int64_t hitems = 0;
+    std::vector<int64_t> hitems_w;
+    unsigned long long *hkey = nullptr;
+    uint32_t *hnpos = nullptr;
+    int32_t *hused = nullptr, *hdone = nullptr, *hnused = nullptr;
     // modularity and label staging scratch
     unsigned long long *kc = nullptr, *macc = nullptr, *h_macc = nullptr;
     int64_t kc_cap = 0;
@@ -281,9 +286,13 @@ struct GraphSet {
         f(changed);
         fh(h_changed);
         fh(h_active);
-        f(gt_key);
-        f(gt_sum);
-        f(gt_np);
+        f(htask);
+        f(htask_w);
+        f(hkey);
+        f(hnpos);
+        f(hused);
+        f(hdone);
+        f(hnused);
         f(kc);
         f(macc);
         fh(h_macc);
@@ -299,8 +308,10 @@ struct GraphSet {
         d_wtot = nullptr;
         g_ebase = nullptr;
         changed = h_changed = h_active = nullptr;
-        gt_key = gt_sum = nullptr;
-        gt_np = nullptr;
+        htask = htask_w = nullptr;
+        hkey = nullptr;
+        hnpos = nullptr;
+        hused = hdone = hnused = nullptr;
         kc = macc = h_macc = nullptr;
         g_sel = nullptr;
         lab_tmp = nullptr;
@@ -418,15 +429,25 @@ struct GraphSet {
             hub_max_deg = hd[order[0]];
             LP_CU(cudaMemcpyAsync(list + bb[3], sorted.data(), bl[3] * sizeof(int32_t),
                                   cudaMemcpyHostToDevice, st));
-            // one overflow table per hub CTA, sized for the largest hub
-            gt_slots = (int64_t)next_pow2(2ull * (uint64_t)hub_max_deg);
-            const int64_t total = gt_slots * hub_grid(bl[3], num_sms);
-            LP_TRY(dev_alloc(&gt_key, total, "hub overflow keys", st, device));
-            LP_TRY(dev_alloc(&gt_sum, total, "hub overflow sums", st, device));
-            LP_TRY(dev_alloc(&gt_np, total, "hub overflow positions", st, device));
-            LP_CU(cudaMemsetAsync(gt_key, 0xFF, total * sizeof(int32_t), st));
-            LP_CU(cudaMemsetAsync(gt_sum, 0, total * sizeof(int32_t), st));
-            LP_CU(cudaMemsetAsync(gt_np, 0, total * sizeof(uint32_t), st));
+            // segment tasks of the hub bucket and one global table per hub of
+            // more than one segment (zeroed; every use leaves it zeroed)
+            LP_TRY(dev_alloc(&htask, bl[3], "hub tasks", st, device));
+            int64_t tot[2] = {0, 0};
+            if (hub_tasks(list + bb[3], bl[3], off, vgraph, htask, d_counts, st, &L.n) != 0)
+                return fail(LP_ECUDA, cuda_msg("hub tasks", cudaGetLastError()));
+            LP_CU(cudaMemcpyAsync(tot, d_counts, sizeof tot, cudaMemcpyDeviceToHost, st));
+            LP_CU(cudaStreamSynchronize(st));
+            hitems = tot[0];
+            const int64_t slots = tot[1] > 0 ? tot[1] : 1;
+            LP_TRY(dev_alloc(&hkey, slots, "hub tables", st, device));
+            LP_TRY(dev_alloc(&hnpos, slots, "hub tables", st, device));
+            LP_TRY(dev_alloc(&hused, slots / 2 + 1, "hub used lists", st, device));
+            LP_TRY(dev_alloc(&hdone, bl[3], "hub counters", st, device));
+            LP_TRY(dev_alloc(&hnused, bl[3], "hub counters", st, device));
+            LP_CU(cudaMemsetAsync(hkey, 0, (size_t)slots * sizeof(unsigned long long), st));
+            LP_CU(cudaMemsetAsync(hnpos, 0, (size_t)slots * sizeof(uint32_t), st));
+            LP_CU(cudaMemsetAsync(hdone, 0, (size_t)bl[3] * sizeof(int32_t), st));
+            LP_CU(cudaMemsetAsync(hnused, 0, (size_t)bl[3] * sizeof(int32_t), st));
             LP_CU(cudaStreamSynchronize(st));
         }
         return LP_OK;
@@ -471,6 +492,33 @@ struct GraphSet {
         for (int c = 0; c < nc; ++c) {
             wstart[(size_t)c] = acc;
             acc += tot[(size_t)c];
+        }
+        // hub tasks of each wave's part of the hub bucket (contiguous classes)
+        hitems_w.assign((size_t)waves, 0);
+        if (bl[3] > 0) {
+            if (!htask_w) LP_TRY(dev_alloc(&htask_w, bl[3], "hub tasks", st, device));
+            const int64_t hub0 = wstart[(size_t)3 * waves];
+            std::vector<int64_t> tots(2 * (size_t)waves, 0);
+            int64_t *d_tot = nullptr;
+            LP_TRY(dev_alloc(&d_tot, 2 * (int64_t)waves, "hub totals", st, device));
+            Launches L2;
+            cudaError_t e2 = cudaSuccess;
+            for (int k = 0; k < waves && e2 == cudaSuccess; ++k) {
+                const int64_t c = wcount[(size_t)3 * waves + k];
+                if (c == 0) continue;
+                const int64_t st0 = wstart[(size_t)3 * waves + k];
+                if (hub_tasks(wlist + st0, c, off, vgraph, htask_w + (st0 - hub0), d_tot + 2 * k,
+                              st, &L2.n) != 0)
+                    e2 = cudaGetLastError();
+            }
+            if (e2 == cudaSuccess)
+                e2 = cudaMemcpyAsync(tots.data(), d_tot, tots.size() * sizeof(int64_t),
+                                     cudaMemcpyDeviceToHost, st);
+            if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(st);
+            cudaFreeAsync(d_tot, st);
+            if (e2 != cudaSuccess) return fail(LP_ECUDA, cuda_msg("wave hub tasks", e2));
+            for (int k = 0; k < waves; ++k)
+                hitems_w[(size_t)k] = wcount[(size_t)3 * waves + k] ? tots[2 * (size_t)k] : 0;
         }
         wl_waves = waves;
         return LP_OK;
@@ -552,10 +600,11 @@ struct GraphSet {
         a.g_ebase = g_ebase;
         a.g_active = g_active;
         a.strict = p->strict ? 1 : 0;
-        a.gtab_key = gt_key;
-        a.gtab_sum = gt_sum;
-        a.gtab_npos = gt_np;
-        a.gtab_slots = gt_slots;
+        a.hkey = hkey;
+        a.hnpos = hnpos;
+        a.hused = hused;
+        a.hdone = hdone;
+        a.hnused = hnused;
         a.waves = (uint32_t)waves;
         a.wave_magic = fastmod_magic((uint32_t)waves);
 
@@ -573,9 +622,15 @@ struct GraphSet {
                 if (waves == 1) {
                     a.list = list + bb[b];
                     a.len = bl[b];
+                    a.htask = htask;
+                    a.hitems = hitems;
                 } else {
                     a.list = wlist + wstart[(size_t)b * waves + k];
                     a.len = wcount[(size_t)b * waves + k];
+                    if (b == 3) {
+                        a.htask = htask_w + (wstart[(size_t)b * waves + k] - wstart[(size_t)b * waves]);
+                        a.hitems = hitems_w[(size_t)k];
+                    }
                 }
                 if (a.len == 0) continue;
                 a.wave_k = (uint32_t)k;

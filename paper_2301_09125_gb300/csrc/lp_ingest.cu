@@ -227,6 +227,47 @@ __global__ void k_merge_final(int32_t *lab0, const int32_t *lab1, int32_t nv,
         if (g_sel[vgraph[v]]) lab0[v] = lab1[v];
 }
 
+// one block: hub tasks with exclusive prefixes of segments and table slots
+__global__ void __launch_bounds__(1024) k_hub_tasks(const int32_t *list, int64_t len,
+                                                     const int32_t *off, const int32_t *vgraph,
+                                                     HubTask *tasks, int64_t *totals)
+{
+    __shared__ int64_t s_warp[33];
+    int64_t seg_run = 0, tab_run = 0;
+    for (int64_t i0 = 0; i0 < len; i0 += 1024) {
+        const int64_t i = i0 + threadIdx.x;
+        int32_t v = 0, d = 0;
+        if (i < len) {
+            v = list[i];
+            d = degree_of(off, vgraph, v);
+        }
+        const int64_t nseg = i < len ? (d + HUB_SEG - 1) / HUB_SEG : 0;
+        int64_t tsz = 0;
+        if (nseg > 1) {
+            tsz = 1;
+            while (tsz < 2 * (int64_t)d) tsz <<= 1;
+        }
+        int64_t tot_seg, tot_tab;
+        const int64_t ex_seg = block_exclusive_scan(nseg, s_warp, &tot_seg);
+        const int64_t ex_tab = block_exclusive_scan(tsz, s_warp, &tot_tab);
+        if (i < len) {
+            HubTask t;
+            t.v = v;
+            t.nseg = (int32_t)nseg;
+            t.first = (int32_t)(seg_run + ex_seg);
+            t.pad = 0;
+            t.tab = tab_run + ex_tab;
+            tasks[i] = t;
+        }
+        seg_run += tot_seg;
+        tab_run += tot_tab;
+    }
+    if (threadIdx.x == 0) {
+        totals[0] = seg_run;
+        totals[1] = tab_run;
+    }
+}
+
 __global__ void k_degrees_of(const int32_t *off, const int32_t *vgraph, const int32_t *list,
                              int64_t len, int32_t *deg)
 {
@@ -409,6 +450,14 @@ int wave_prepare()
             cudaSuccess)
         return -1;
     return 0;
+}
+
+int hub_tasks(const int32_t *list, int64_t len, const int32_t *off, const int32_t *vgraph,
+              HubTask *tasks, int64_t *totals, cudaStream_t st, int64_t *launches)
+{
+    k_hub_tasks<<<1, 1024, 0, st>>>(list, len, off, vgraph, tasks, totals);
+    ++*launches;
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 int merge_final_labels(int32_t *lab0, const int32_t *lab1, int32_t nv, const int32_t *vgraph,

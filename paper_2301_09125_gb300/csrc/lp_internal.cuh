@@ -33,8 +33,21 @@ constexpr int WARP_TABLE = 256;         // slots per warp (>= 2 * WARP_MAX)
 constexpr int CTA_THREADS = 256;
 constexpr int CTA_TABLE = 2048;         // slots (>= 2 * CTA_MAX)
 constexpr int HUB_THREADS = 512;
-constexpr int HUB_TABLE = 8192;         // shared slots; more labels spill to global
-constexpr int HUB_PROBE = 32;           // shared probe window before spilling
+constexpr int HUB_TABLE = 8192;         // shared slots (>= 2 * HUB_SEG)
+constexpr int HUB_SEG = 4096;           // entries of a hub row per work item
+
+// One hub of a list being swept (the hub bucket, or its part in one wave),
+// prepared once per list.  Its row is cut into `nseg` segments of HUB_SEG
+// entries; items first .. first + nseg - 1 of the launch are its segments.
+// A hub of more than one segment owns a global table of 2^ceil(log2(2d))
+// slots starting at slot `tab`, and a used-slot list starting at tab / 2.
+struct HubTask {
+    int32_t v;      // global vertex
+    int32_t nseg;   // segments of its row
+    int32_t first;  // items of the earlier hubs of the list
+    int32_t pad;
+    int64_t tab;    // first slot of its global table
+};
 
 // Arguments of one sweep kernel launch (one bucket).
 struct SweepArgs {
@@ -60,11 +73,17 @@ struct SweepArgs {
     uint32_t waves;
     uint32_t wave_k;
     uint64_t wave_magic;     // fastmod constant of `waves`
-    // hub overflow tables: per CTA, `gtab_slots` slots of key / sum / npos
-    int32_t *gtab_key;
-    int32_t *gtab_sum;
-    uint32_t *gtab_npos;
-    int64_t gtab_slots;
+    // hub launches: the list's tasks, the total of its items (segments), the
+    // global tables (slot = (label + 1) << 32 | summed weight, 0 when free,
+    // plus ~first position), used-slot lists, and per-task counters of
+    // finished segments and used slots (zero between launches)
+    const HubTask *htask;
+    int64_t hitems;
+    unsigned long long *hkey;
+    uint32_t *hnpos;
+    int32_t *hused;
+    int32_t *hdone;
+    int32_t *hnused;
 };
 
 // Modularity arguments (a whole graph set; graph layout as for SweepArgs).
@@ -121,7 +140,10 @@ __host__ __device__ __forceinline__ uint64_t stream_at(uint64_t key, uint64_t k)
 int sweep_prepare();  // per-device kernel attributes; call with the device current
 // launch the sweep kernel of one degree bucket (0 small, 1 warp, 2 cta, 3 hub)
 int sweep_launch(int bucket, const SweepArgs &a, bool multi, int num_sms, cudaStream_t st);
-int hub_grid(int64_t hub_len, int num_sms);  // CTAs of the hub kernel (one overflow table each)
+// Hub tasks of list[0..len): tasks[i] for each entry, totals[0] = items,
+// totals[1] = global table slots.
+int hub_tasks(const int32_t *list, int64_t len, const int32_t *off, const int32_t *vgraph,
+              HubTask *tasks, int64_t *totals, cudaStream_t st, int64_t *launches);
 
 struct IngestOut {
     int32_t err;          // 0 ok, else an error code below

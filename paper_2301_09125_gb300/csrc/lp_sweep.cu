@@ -12,9 +12,12 @@
 //                              table per warp in shared memory; duplicate labels
 //                              of a 32-entry chunk are merged before insertion.
 //   cta    129..1024 k_cta   : one 256-thread CTA per vertex, 2048-slot table.
-//   hub    > 1024    k_cta   : one 512-thread CTA per vertex, 8192-slot shared
-//                              table; labels whose probe window is full go to a
-//                              per-CTA overflow table in global memory.
+//   hub    > 1024    k_hub   : work items are 4096-entry segments of hub rows,
+//                              512 threads each, aggregated in an 8192-slot
+//                              shared table; a row of one segment is finished
+//                              there, longer rows flush each segment into the
+//                              hub's global table and the CTA finishing the
+//                              last segment takes the argmax of the used slots.
 // Every table slot holds (label, summed weight, ~first position); the first
 // position of a label is the smallest row position at which it occurs, so the
 // argmax key (weight desc, [non-strict key asc,] first position asc) is unique
@@ -396,10 +399,64 @@ __global__ void __launch_bounds__(256) k_warp(SweepArgs a)
     if (!MULTI && lane == 0 && my_changed) atomicAdd(a.changed, (int)my_changed);
 }
 
+// Scan the table slots [0, slots): local best candidate (strict or non-strict),
+// resetting every used slot.  Non-strict scans twice: the block maximum first.
+template <int NT>
+__device__ __forceinline__ Cand scan_table(int32_t *tk, int32_t *ts, uint32_t *tp, int slots,
+                                           int strict, uint64_t ktv, uint32_t *s_u)
+{
+    Cand best{0u, 0u, 0ull, EMPTY};
+    uint32_t mx = 0;
+    if (!strict) {
+        for (int j = threadIdx.x; j < slots; j += NT)
+            if (tk[j] != EMPTY) mx = max(mx, (uint32_t)ts[j]);
+        mx = block_max<NT>(mx, s_u);
+    }
+    for (int j = threadIdx.x; j < slots; j += NT) {
+        const int32_t key = tk[j];
+        if (key != EMPTY) {
+            if (strict) {
+                const Cand c{(uint32_t)ts[j], tp[j], 0ull, key};
+                if (better(c, best)) best = c;
+            } else if ((uint32_t)ts[j] == mx) {
+                const Cand c{mx, tp[j], stream_at(ktv, (uint64_t)key + 1), key};
+                if (better(c, best)) best = c;
+            }
+            tk[j] = EMPTY;
+            ts[j] = 0;
+            tp[j] = 0;
+        }
+    }
+    return best;
+}
+
+// Aggregate the entries [lo, hi) of a row starting at global entry `row` into
+// the shared table of 2^lg slots (which must have room for every distinct
+// label of the range), all NT threads cooperating.
+template <int NT>
+__device__ __forceinline__ void accumulate_range(const SweepArgs &a, int64_t row, int64_t lo,
+                                                 int64_t hi, int32_t vb, int32_t *tk, int32_t *ts,
+                                                 uint32_t *tp, int lg)
+{
+    const int64_t b_hi = (hi - 1) >> 2;
+    for (int64_t base = lo >> 2; base <= b_hi; base += NT) {
+        const int64_t blk = base + threadIdx.x;
+        const Quad q = blk <= b_hi ? load_quad(a, blk, lo, hi, vb) : empty_quad();
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int32_t l = q.l[j];
+            const unsigned grp = __match_any_sync(FULL, (unsigned)l);
+            const int s = __reduce_add_sync(grp, q.w[j]);
+            if (l != EMPTY && (threadIdx.x & 31) == __ffs(grp) - 1)
+                table_add(tk, ts, tp, lg, 1 << lg, l, s, (uint32_t)(blk * 4 + j - row));
+        }
+    }
+}
+
 // ----------------------------------------------------------------------------
-// cta / hub buckets: one CTA per vertex, shared table (+ global overflow)
+// cta bucket: one CTA per vertex, shared table
 // ----------------------------------------------------------------------------
-template <int NT, int CAP, bool SPILL, bool MULTI>
+template <int NT, int CAP, bool MULTI>
 __global__ void __launch_bounds__(NT) k_cta(SweepArgs a)
 {
     extern __shared__ int32_t smem[];
@@ -408,7 +465,6 @@ __global__ void __launch_bounds__(NT) k_cta(SweepArgs a)
     uint32_t *tp = reinterpret_cast<uint32_t *>(ts + CAP);
     __shared__ Cand s_red[NT / 32];
     __shared__ uint32_t s_u[NT / 32 + 1];
-    __shared__ int s_spilled;
     constexpr int LG = (CAP == 2048) ? 11 : (CAP == 4096) ? 12 : (CAP == 8192) ? 13 : 14;
     static_assert((1 << LG) == CAP, "table size");
 
@@ -417,16 +473,7 @@ __global__ void __launch_bounds__(NT) k_cta(SweepArgs a)
         ts[j] = 0;
         tp[j] = 0;
     }
-    if (threadIdx.x == 0) s_spilled = 0;
     __syncthreads();
-
-    int32_t *gk = nullptr, *gs = nullptr;
-    uint32_t *gp = nullptr;
-    if (SPILL) {
-        gk = a.gtab_key + (int64_t)blockIdx.x * a.gtab_slots;
-        gs = a.gtab_sum + (int64_t)blockIdx.x * a.gtab_slots;
-        gp = a.gtab_npos + (int64_t)blockIdx.x * a.gtab_slots;
-    }
     uint32_t my_changed = 0;
 
     VtxPipe<MULTI> pipe;
@@ -436,77 +483,186 @@ __global__ void __launch_bounds__(NT) k_cta(SweepArgs a)
         const bool ok = pipe.next_ok;
         pipe.fetch(a, item + gridDim.x);
         if (!ok) continue;  // block-uniform
-        const int32_t own = x.own;
-        // shared slots in use for this vertex: 2^lg >= 2d (up to the table size)
+        // slots in use for this vertex: 2^lg >= 2d (d <= CAP / 2 in this bucket)
         const int lg = min(ilog2_ceil(2u * (uint32_t)x.d), LG);
-
-        // overflow table slots for this vertex: 2^glg >= 2d, within the allocation
-        int glg = SPILL ? ilog2_ceil(2u * (uint32_t)x.d) : 0;
-        if (SPILL && ((int64_t)1 << glg) > a.gtab_slots) glg = 63 - __clzll(a.gtab_slots);
-        const int64_t lo = x.e0, hi = x.e0 + x.d;
-        const int64_t b_hi = (hi - 1) >> 2;
-        for (int64_t base = lo >> 2; base <= b_hi; base += NT) {
-            const int64_t blk = base + threadIdx.x;
-            const Quad q = blk <= b_hi ? load_quad(a, blk, lo, hi, x.vb) : empty_quad();
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int32_t l = q.l[j];
-                const unsigned grp = __match_any_sync(FULL, (unsigned)l);
-                const int s = __reduce_add_sync(grp, q.w[j]);
-                if (l != EMPTY && (threadIdx.x & 31) == __ffs(grp) - 1) {
-                    const uint32_t p = (uint32_t)(blk * 4 + j - lo);
-                    const bool in_shared =
-                        table_add(tk, ts, tp, lg, SPILL ? HUB_PROBE : (1 << lg), l, s, p);
-                    if (SPILL && !in_shared) {
-                        s_spilled = 1;
-                        table_add(gk, gs, gp, glg, 1 << glg, l, s, p);
-                    }
-                }
-            }
-        }
+        accumulate_range<NT>(a, x.e0, x.e0, x.e0 + x.d, x.vb, tk, ts, tp, lg);
         __syncthreads();
-        const bool spilled = SPILL && s_spilled;
-        const int sslots = 1 << lg;
-        const int gslots = spilled ? (1 << glg) : 0;
-
-        Cand best{0u, 0u, 0ull, EMPTY};
-        uint32_t mx = 0;
-        if (!a.strict) {
-            for (int j = threadIdx.x; j < sslots + gslots; j += NT) {
-                const int32_t key = j < sslots ? tk[j] : gk[j - sslots];
-                if (key != EMPTY) mx = max(mx, (uint32_t)(j < sslots ? ts[j] : gs[j - sslots]));
-            }
-            mx = block_max<NT>(mx, s_u);
-        }
-        const uint64_t ktv = stream_at(a.key_t, (uint64_t)x.lv + 1);
-        for (int j = threadIdx.x; j < sslots + gslots; j += NT) {
-            int32_t *K = j < sslots ? tk + j : gk + (j - sslots);
-            int32_t *S = j < sslots ? ts + j : gs + (j - sslots);
-            uint32_t *Q = j < sslots ? tp + j : gp + (j - sslots);
-            const int32_t key = *K;
-            if (key != EMPTY) {
-                if (a.strict) {
-                    const Cand c{(uint32_t)*S, *Q, 0ull, key};
-                    if (better(c, best)) best = c;
-                } else if ((uint32_t)*S == mx) {
-                    const Cand c{mx, *Q, stream_at(ktv, (uint64_t)key + 1), key};
-                    if (better(c, best)) best = c;
-                }
-                *K = EMPTY;
-                *S = 0;
-                *Q = 0;
-            }
-        }
-        best = block_argmax<NT>(best, a.strict, s_red);
+        const Cand best = block_argmax<NT>(
+            scan_table<NT>(tk, ts, tp, 1 << lg, a.strict,
+                           stream_at(a.key_t, (uint64_t)x.lv + 1), s_u),
+            a.strict, s_red);
         if (threadIdx.x == 0) {
             a.lab_out[x.v] = best.label;
-            if (best.label != own) {
+            if (best.label != x.own) {
                 if (MULTI)
                     atomicAdd(a.changed + x.g, 1);
                 else
                     ++my_changed;
             }
-            s_spilled = 0;
+        }
+        __syncthreads();
+    }
+    if (!MULTI && threadIdx.x == 0 && my_changed) atomicAdd(a.changed, (int)my_changed);
+}
+
+// ----------------------------------------------------------------------------
+// hub bucket: work items are 4096-entry segments of hub rows
+// ----------------------------------------------------------------------------
+
+// Add (l, s, ~first position) to a hub's global table of 2^glg slots.
+// Returns the slot when this call claimed it, -1 otherwise.
+__device__ __forceinline__ int64_t global_add(unsigned long long *gk, uint32_t *gp, int glg,
+                                              int32_t l, uint32_t s, uint32_t np)
+{
+    const uint32_t mask = (1u << glg) - 1u;
+    const unsigned long long key = (unsigned long long)((uint32_t)l + 1u) << 32;
+    uint32_t h = slot_hash(l, glg);
+    for (int i = 0; i <= (int)mask; ++i) {
+        const unsigned long long cur = atomicCAS(gk + h, 0ull, key | s);
+        if (cur == 0ull) {
+            atomicMax(gp + h, np);
+            return h;
+        }
+        if ((cur & 0xFFFFFFFF00000000ull) == key) {
+            atomicAdd(gk + h, (unsigned long long)s);  // the sum is the low word
+            atomicMax(gp + h, np);
+            return -1;
+        }
+        h = (h + 1) & mask;
+    }
+    return -1;  // unreachable: the table holds at least 2d slots
+}
+
+template <bool MULTI>
+__global__ void __launch_bounds__(HUB_THREADS, 2) k_hub(SweepArgs a)
+{
+    constexpr int NT = HUB_THREADS;
+    constexpr int LG = 13;
+    static_assert((1 << LG) == HUB_TABLE && HUB_TABLE >= 2 * HUB_SEG, "hub table size");
+    extern __shared__ int32_t smem[];
+    int32_t *tk = smem;
+    int32_t *ts = tk + HUB_TABLE;
+    uint32_t *tp = reinterpret_cast<uint32_t *>(ts + HUB_TABLE);
+    __shared__ Cand s_red[NT / 32];
+    __shared__ uint32_t s_u[NT / 32 + 1];
+    __shared__ int s_last;
+    const int lane = threadIdx.x & 31;
+
+    for (int j = threadIdx.x; j < HUB_TABLE; j += NT) {
+        tk[j] = EMPTY;
+        ts[j] = 0;
+        tp[j] = 0;
+    }
+    __syncthreads();
+    uint32_t my_changed = 0;
+
+    for (int64_t item = blockIdx.x; item < a.hitems; item += gridDim.x) {
+        // the task owning this item: the last one whose first item is <= item
+        int64_t ti = 0, thi = a.len - 1;
+        while (ti < thi) {
+            const int64_t mid = (ti + thi + 1) >> 1;
+            if (__ldg(&a.htask[mid].first) <= item)
+                ti = mid;
+            else
+                thi = mid - 1;
+        }
+        const HubTask t = a.htask[ti];
+        Vtx x;
+        if (!load_vtx<MULTI>(a, t.v, x)) continue;  // block-uniform
+        const int seg = (int)(item - t.first);
+        const int64_t lo = x.e0 + (int64_t)seg * HUB_SEG;
+        const int64_t hi = min(lo + HUB_SEG, x.e0 + x.d);
+        const uint64_t ktv = stream_at(a.key_t, (uint64_t)x.lv + 1);
+
+        if (t.nseg == 1) {  // the whole row fits the shared table
+            const int lg = min(ilog2_ceil(2u * (uint32_t)x.d), LG);
+            accumulate_range<NT>(a, x.e0, lo, hi, x.vb, tk, ts, tp, lg);
+            __syncthreads();
+            const Cand best = block_argmax<NT>(
+                scan_table<NT>(tk, ts, tp, 1 << lg, a.strict, ktv, s_u), a.strict, s_red);
+            if (threadIdx.x == 0) {
+                a.lab_out[x.v] = best.label;
+                if (best.label != x.own) {
+                    if (MULTI)
+                        atomicAdd(a.changed + x.g, 1);
+                    else
+                        ++my_changed;
+                }
+            }
+            __syncthreads();
+            continue;
+        }
+
+        // aggregate the segment, then flush it into the hub's global table
+        accumulate_range<NT>(a, x.e0, lo, hi, x.vb, tk, ts, tp, LG);
+        __syncthreads();
+        const int glg = ilog2_ceil(2u * (uint32_t)x.d);
+        unsigned long long *gk = a.hkey + t.tab;
+        uint32_t *gp = a.hnpos + t.tab;
+        int32_t *gu = a.hused + t.tab / 2;
+        for (int j0 = 0; j0 < HUB_TABLE; j0 += NT) {
+            const int j = j0 + threadIdx.x;
+            const int32_t key = tk[j];
+            int64_t claimed = -1;
+            if (key != EMPTY) {
+                claimed = global_add(gk, gp, glg, key, (uint32_t)ts[j], tp[j]);
+                tk[j] = EMPTY;
+                ts[j] = 0;
+                tp[j] = 0;
+            }
+            // record newly claimed slots in the used list, one atomic per warp
+            const unsigned m = __ballot_sync(FULL, claimed >= 0);
+            if (m) {
+                const int leader = __ffs(m) - 1;
+                int base = 0;
+                if (lane == leader) base = atomicAdd(a.hnused + ti, __popc(m));
+                base = __shfl_sync(FULL, base, leader);
+                if (claimed >= 0) gu[base + __popc(m & ((1u << lane) - 1u))] = (int32_t)claimed;
+            }
+        }
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) s_last = atomicAdd(a.hdone + ti, 1) == t.nseg - 1;
+        __syncthreads();
+        if (!s_last) continue;
+
+        // the last segment of the hub: argmax over its used slots, reset them
+        __threadfence();
+        const int nused = __ldcg(a.hnused + ti);
+        uint32_t mx = 0;
+        if (!a.strict) {
+            for (int u = threadIdx.x; u < nused; u += NT)
+                mx = max(mx, (uint32_t)__ldcg(gk + __ldcg(gu + u)));
+            mx = block_max<NT>(mx, s_u);
+        }
+        Cand best{0u, 0u, 0ull, EMPTY};
+        for (int u = threadIdx.x; u < nused; u += NT) {
+            const int32_t slot = __ldcg(gu + u);
+            const unsigned long long kv = __ldcg(gk + slot);
+            const int32_t label = (int32_t)((uint32_t)(kv >> 32) - 1u);
+            const uint32_t sum = (uint32_t)kv;
+            const uint32_t np = __ldcg(gp + slot);
+            if (a.strict) {
+                const Cand c{sum, np, 0ull, label};
+                if (better(c, best)) best = c;
+            } else if (sum == mx) {
+                const Cand c{sum, np, stream_at(ktv, (uint64_t)label + 1), label};
+                if (better(c, best)) best = c;
+            }
+            gk[slot] = 0ull;
+            gp[slot] = 0u;
+        }
+        best = block_argmax<NT>(best, a.strict, s_red);
+        if (threadIdx.x == 0) {
+            a.lab_out[x.v] = best.label;
+            if (best.label != x.own) {
+                if (MULTI)
+                    atomicAdd(a.changed + x.g, 1);
+                else
+                    ++my_changed;
+            }
+            a.hdone[ti] = 0;
+            a.hnused[ti] = 0;
         }
         __syncthreads();
     }
@@ -531,12 +687,13 @@ int launch(int bucket, const SweepArgs &a, int num_sms, cudaStream_t st)
         break;
     case 2:
         blocks = a.len;
-        k_cta<CTA_THREADS, CTA_TABLE, false, MULTI>
+        k_cta<CTA_THREADS, CTA_TABLE, MULTI>
             <<<(int)(blocks < num_sms * 8 ? blocks : num_sms * 8), CTA_THREADS, cta_smem, st>>>(a);
         break;
     default:
-        k_cta<HUB_THREADS, HUB_TABLE, true, MULTI>
-            <<<hub_grid(a.len, num_sms), HUB_THREADS, hub_smem, st>>>(a);
+        if (a.hitems <= 0) return 0;
+        blocks = a.hitems < (int64_t)num_sms * 2 ? a.hitems : (int64_t)num_sms * 2;
+        k_hub<MULTI><<<(int)blocks, HUB_THREADS, hub_smem, st>>>(a);
         break;
     }
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
@@ -545,12 +702,11 @@ int launch(int bucket, const SweepArgs &a, int num_sms, cudaStream_t st)
 template <bool MULTI>
 int prepare()
 {
-    if (cudaFuncSetAttribute(k_cta<CTA_THREADS, CTA_TABLE, false, MULTI>,
+    if (cudaFuncSetAttribute(k_cta<CTA_THREADS, CTA_TABLE, MULTI>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)((size_t)CTA_TABLE * 12)) != cudaSuccess)
         return -1;
-    if (cudaFuncSetAttribute(k_cta<HUB_THREADS, HUB_TABLE, true, MULTI>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(k_hub<MULTI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)((size_t)HUB_TABLE * 12)) != cudaSuccess)
         return -1;
     return 0;
@@ -558,11 +714,6 @@ int prepare()
 
 }  // namespace
 
-int hub_grid(int64_t hub_len, int num_sms)
-{
-    const int64_t cap = (int64_t)num_sms * 2;
-    return (int)(hub_len < cap ? hub_len : cap);
-}
 
 int sweep_prepare() { return prepare<false>() | prepare<true>(); }
 
