@@ -224,6 +224,7 @@ struct GraphSet {
     int32_t wl_waves = 0;
     std::vector<int64_t> wstart, wcount;  // per class b * waves + k
     int32_t max_n = 0;
+    bool rows_distinct = false;  // no row repeats a neighbour (identity first sweep)
     int32_t hub_max_deg = 0;
     // multi-graph bookkeeping (device copies are null for a single graph)
     int32_t *vgraph = nullptr, *g_vbase = nullptr, *g_active = nullptr, *g_n = nullptr;
@@ -373,6 +374,22 @@ struct GraphSet {
             LP_TRY(read_ingest(graph_index));
         }
         (void)g;
+        return LP_OK;
+    }
+
+    // Every row strictly increasing -> no repeated neighbour: the first sweep
+    // from unique labels can take the identity path.
+    lp_status check_row_order()
+    {
+        rows_distinct = false;
+        uint32_t *bits = nullptr;
+        LP_TRY(dev_alloc(&bits, ne / 32 + 1, "row-start bitmap", st, device));
+        Launches L;
+        const int rc = ingest_row_order(off, idx, nv, ne, vgraph, g_ebase, bits, d_ing, st, &L.n);
+        cudaFreeAsync(bits, st);
+        if (rc != 0) return fail(LP_ECUDA, cuda_msg("row order check", cudaGetLastError()));
+        LP_TRY(read_ingest(-1));
+        rows_distinct = h_ing->repeated == 0;
         return LP_OK;
     }
 
@@ -634,6 +651,9 @@ struct GraphSet {
                 }
                 if (a.len == 0) continue;
                 a.wave_k = (uint32_t)k;
+                // the first sweep from unique labels reads unique labels only
+                // in its first wave (later waves see this sweep's new labels)
+                a.identity = rows_distinct && it == 0 && !p->init_labels && k == 0;
                 if (prof) {
                     while (prof_ev.size() < 2 * (prof_launch.size() + 1)) {
                         cudaEvent_t e;
@@ -884,6 +904,7 @@ lp_status lp_graph_create(int32_t n, int64_t m, const int32_t *offsets, const in
         if (!host_symmetric(n, ho.data(), hi.data(), weights ? hw.data() : nullptr))
             return fail(LP_EINVAL, "CSR is not symmetric");
     }
+    LP_TRY(s.check_row_order());
     LP_TRY(s.bucket());
     LP_TRY(s.alloc_labels());
     LP_CU(cudaStreamSynchronize(s.st));
@@ -1061,6 +1082,7 @@ lp_status lp_batch_create(int32_t count, const lp_graph_desc *graphs, uint32_t f
     LP_CU(cudaMemcpyAsync(s.g_n, s.h_n.data(), (size_t)count * sizeof(int32_t),
                           cudaMemcpyHostToDevice, s.st));
     LP_CU(cudaStreamSynchronize(s.st));
+    LP_TRY(s.check_row_order());
     LP_TRY(s.bucket());
     LP_TRY(s.alloc_labels());
     LP_CU(cudaStreamSynchronize(s.st));

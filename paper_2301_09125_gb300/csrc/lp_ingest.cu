@@ -73,6 +73,35 @@ __global__ void k_val_wdeg(const int32_t *off, const int32_t *wts, int32_t n, In
     }
 }
 
+// row starts of a graph set as a bitmap over global entries
+__global__ void k_mark_row_starts(const int32_t *off, int32_t nv, const int32_t *vgraph,
+                                  const int64_t *g_ebase, uint32_t *bits)
+{
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nv;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t g = vgraph ? vgraph[v] : 0;
+        const int32_t rs = off[v + g], re = off[v + g + 1];
+        if (re > rs) {
+            const int64_t e = (g_ebase ? g_ebase[g] : 0) + rs;
+            atomicOr(bits + (e >> 5), 1u << (e & 31));
+        }
+    }
+}
+
+// entries e, e+1 of one row must satisfy idx[e] < idx[e+1]
+__global__ void k_check_row_order(const int32_t *idx, int64_t ne, const uint32_t *bits,
+                                  IngestOut *o)
+{
+    bool bad = false;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e + 1 < ne;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t f = e + 1;
+        const bool starts = (bits[f >> 5] >> (f & 31)) & 1u;
+        bad = bad || (!starts && __ldg(idx + e) >= __ldg(idx + f));
+    }
+    if (__any_sync(FULL, bad) && (threadIdx.x & 31) == 0) atomicExch(&o->repeated, 1);
+}
+
 __device__ __forceinline__ int bucket_of(int32_t d)
 {
     return d <= 0 ? -1 : d <= SMALL_MAX ? 0 : d <= WARP_MAX ? 1 : d <= CTA_MAX ? 2 : 3;
@@ -372,6 +401,20 @@ int ingest_validate(const int32_t *off, const int32_t *idx, const int32_t *wts, 
         k_val_entries<<<grid_for(m, 256, 8192), 256, 0, st>>>(idx, wts, n, m, d_out);
         ++*launches;
     }
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int ingest_row_order(const int32_t *off, const int32_t *idx, int32_t nv, int64_t ne,
+                     const int32_t *vgraph, const int64_t *g_ebase, uint32_t *bits,
+                     IngestOut *d_out, cudaStream_t st, int64_t *launches)
+{
+    if (cudaMemsetAsync(&d_out->repeated, 0, sizeof(int32_t), st) != cudaSuccess) return -1;
+    if (ne < 2 || nv == 0) return 0;
+    if (cudaMemsetAsync(bits, 0, (size_t)(ne / 32 + 1) * sizeof(uint32_t), st) != cudaSuccess)
+        return -1;
+    k_mark_row_starts<<<grid_for(nv, 256, 8192), 256, 0, st>>>(off, nv, vgraph, g_ebase, bits);
+    k_check_row_order<<<grid_for(ne, 256, 8192), 256, 0, st>>>(idx, ne, bits, d_out);
+    *launches += 2;
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -67,6 +67,9 @@ struct SweepArgs {
     int32_t *changed;        // changed counter(s) of this iteration (per graph)
     int strict;              // 1 strict, 0 non-strict
     uint64_t key_t;          // non-strict stream key of this iteration
+    // 1 when every label this launch reads is the initial unique label and no
+    // row repeats a neighbour: a label's weight is then its one edge weight
+    int identity;
     // asynchronous waves (Sec. 3.3): this launch runs wave `wave_k` of `waves`;
     // a neighbour u of an earlier wave (u mod waves < wave_k) is read from
     // lab_out (this iteration), every other one from lab_in.  waves = 1: sync.
@@ -151,6 +154,7 @@ struct IngestOut {
     int32_t max_w;
     int32_t max_deg;
     int32_t wdeg_overflow;
+    int32_t repeated;     // some row does not list its neighbours in strictly increasing order
 };
 enum IngestErr : int32_t {
     ING_OK = 0,
@@ -166,6 +170,12 @@ enum IngestErr : int32_t {
 
 int ingest_validate(const int32_t *off, const int32_t *idx, const int32_t *wts, int32_t n,
                     int64_t m, IngestOut *d_out, cudaStream_t st, int64_t *launches);
+// Whether every row lists its neighbours in strictly increasing order (then no
+// row repeats a neighbour): d_out->repeated = 0 if so.  Needs a validated CSR
+// set and a scratch bitmap of ne / 32 + 1 words; rows of graph g at ebase_g.
+int ingest_row_order(const int32_t *off, const int32_t *idx, int32_t nv, int64_t ne,
+                     const int32_t *vgraph, const int64_t *g_ebase, uint32_t *bits,
+                     IngestOut *d_out, cudaStream_t st, int64_t *launches);
 int ingest_check_wdeg(const int32_t *off, const int32_t *wts, int32_t n, IngestOut *d_out,
                       cudaStream_t st, int64_t *launches);
 int degrees_of(const int32_t *off, const int32_t *vgraph, const int32_t *list, int64_t len,

@@ -144,13 +144,14 @@ __global__ void __launch_bounds__(256) k_small(SweepArgs a)
                 const long long e = o_e0 + pos;
                 const int32_t u = __ldg(a.idx + e);
                 w = a.wts ? __ldg(a.wts + e) : 1;
-                l = neighbour_label(a, (int64_t)o_vb + u, u);
+                l = a.identity ? u : neighbour_label(a, (int64_t)o_vb + u, u);
             }
-            // group equal (owner, label) pairs; the lowest lane holds the first position
+            // group equal (owner, label) pairs; the lowest lane holds the first
+            // position (in an identity sweep every pair is distinct)
             const unsigned long long key =
                 act ? (((unsigned long long)(unsigned)o << 32) | (unsigned)l) : ~0ull;
-            const unsigned grp = __match_any_sync(FULL, key);
-            const int s = __reduce_add_sync(grp, w);
+            const unsigned grp = a.identity ? (1u << lane) : __match_any_sync(FULL, key);
+            const int s = a.identity ? w : __reduce_add_sync(grp, w);
             const bool leader = act && lane == __ffs(grp) - 1;
             // segmented argmax over each owner's lanes
             const unsigned og = __match_any_sync(FULL, act ? (unsigned)o : 0xFFFFFFFFu);
@@ -206,12 +207,11 @@ __device__ __forceinline__ Quad empty_quad()
     return q;
 }
 
-// entries 4*blk .. 4*blk+3 of the arena, kept where they lie in [lo, hi)
-__device__ __forceinline__ Quad load_quad(const SweepArgs &a, int64_t blk, int64_t lo, int64_t hi,
-                                          int32_t vb)
+// column indices and weights of entries 4*blk .. 4*blk+3 of the arena
+__device__ __forceinline__ void load_block(const SweepArgs &a, int64_t blk, int32_t (&u)[4],
+                                           int32_t (&w)[4])
 {
     const int64_t e0 = blk * 4;
-    int32_t u[4], w[4];
     if (e0 + 3 < a.ne) {
         const int4 I = __ldg(reinterpret_cast<const int4 *>(a.idx) + blk);
         u[0] = I.x;
@@ -235,6 +235,15 @@ __device__ __forceinline__ Quad load_quad(const SweepArgs &a, int64_t blk, int64
             w[j] = ok ? (a.wts ? __ldg(a.wts + e0 + j) : 1) : 0;
         }
     }
+}
+
+// entries 4*blk .. 4*blk+3 of the arena, kept where they lie in [lo, hi)
+__device__ __forceinline__ Quad load_quad(const SweepArgs &a, int64_t blk, int64_t lo, int64_t hi,
+                                          int32_t vb)
+{
+    const int64_t e0 = blk * 4;
+    int32_t u[4], w[4];
+    load_block(a, blk, u, w);
     Quad q;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -243,6 +252,32 @@ __device__ __forceinline__ Quad load_quad(const SweepArgs &a, int64_t blk, int64
         q.w[j] = in ? w[j] : 0;
     }
     return q;
+}
+
+// Identity sweep: the labels read are the initial unique labels (label of u
+// is u) and no row repeats a neighbour, so a label's summed weight is its one
+// edge weight and its first position is that entry's.  The adopted label is
+// the argmax of the entries of [lo, hi) (row starting at entry `row`) under
+// the same order; this folds the thread's blocks into `best`.
+template <int NT>
+__device__ __forceinline__ Cand identity_best(const SweepArgs &a, int64_t row, int64_t lo,
+                                              int64_t hi, uint64_t ktv, int t)
+{
+    Cand best{0u, 0u, 0ull, EMPTY};
+    const int64_t b_hi = (hi - 1) >> 2;
+    for (int64_t blk = (lo >> 2) + t; blk <= b_hi; blk += NT) {
+        int32_t u[4], w[4];
+        load_block(a, blk, u, w);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t e = blk * 4 + j;
+            if (e < lo || e >= hi || (uint32_t)w[j] < best.sum) continue;
+            const Cand c{(uint32_t)w[j], 0xFFFFFFFFu - (uint32_t)(e - row),
+                         a.strict ? 0ull : stream_at(ktv, (uint64_t)u[j] + 1), u[j]};
+            if (better(c, best)) best = c;
+        }
+    }
+    return best;
 }
 
 // Best candidate of the warp under the total order of `better`, valid in
@@ -322,6 +357,21 @@ __global__ void __launch_bounds__(256) k_warp(SweepArgs a)
         const int32_t own = x.own;
         const int64_t lo = x.e0, hi = x.e0 + x.d;
         const int64_t b_hi = (hi - 1) >> 2;
+        if (a.identity) {
+            const Cand best = warp_argmax(
+                identity_best<32>(a, lo, lo, hi, stream_at(a.key_t, (uint64_t)x.lv + 1), lane),
+                a.strict);
+            if (lane == 0) {
+                a.lab_out[x.v] = best.label;
+                if (best.label != own) {
+                    if (MULTI)
+                        atomicAdd(a.changed + x.g, 1);
+                    else
+                        ++my_changed;
+                }
+            }
+            continue;
+        }
         for (int64_t base = lo >> 2; base <= b_hi; base += 32) {
             const int64_t blk = base + lane;
             const Quad q = blk <= b_hi ? load_quad(a, blk, lo, hi, x.vb) : empty_quad();
@@ -485,12 +535,16 @@ __global__ void __launch_bounds__(NT) k_cta(SweepArgs a)
         if (!ok) continue;  // block-uniform
         // slots in use for this vertex: 2^lg >= 2d (d <= CAP / 2 in this bucket)
         const int lg = min(ilog2_ceil(2u * (uint32_t)x.d), LG);
-        accumulate_range<NT>(a, x.e0, x.e0, x.e0 + x.d, x.vb, tk, ts, tp, lg);
-        __syncthreads();
-        const Cand best = block_argmax<NT>(
-            scan_table<NT>(tk, ts, tp, 1 << lg, a.strict,
-                           stream_at(a.key_t, (uint64_t)x.lv + 1), s_u),
-            a.strict, s_red);
+        const uint64_t ktv = stream_at(a.key_t, (uint64_t)x.lv + 1);
+        Cand local;
+        if (a.identity) {
+            local = identity_best<NT>(a, x.e0, x.e0, x.e0 + x.d, ktv, threadIdx.x);
+        } else {
+            accumulate_range<NT>(a, x.e0, x.e0, x.e0 + x.d, x.vb, tk, ts, tp, lg);
+            __syncthreads();
+            local = scan_table<NT>(tk, ts, tp, 1 << lg, a.strict, ktv, s_u);
+        }
+        const Cand best = block_argmax<NT>(local, a.strict, s_red);
         if (threadIdx.x == 0) {
             a.lab_out[x.v] = best.label;
             if (best.label != x.own) {
@@ -576,10 +630,15 @@ __global__ void __launch_bounds__(HUB_THREADS, 2) k_hub(SweepArgs a)
 
         if (t.nseg == 1) {  // the whole row fits the shared table
             const int lg = min(ilog2_ceil(2u * (uint32_t)x.d), LG);
-            accumulate_range<NT>(a, x.e0, lo, hi, x.vb, tk, ts, tp, lg);
-            __syncthreads();
-            const Cand best = block_argmax<NT>(
-                scan_table<NT>(tk, ts, tp, 1 << lg, a.strict, ktv, s_u), a.strict, s_red);
+            Cand local;
+            if (a.identity) {
+                local = identity_best<NT>(a, x.e0, lo, hi, ktv, threadIdx.x);
+            } else {
+                accumulate_range<NT>(a, x.e0, lo, hi, x.vb, tk, ts, tp, lg);
+                __syncthreads();
+                local = scan_table<NT>(tk, ts, tp, 1 << lg, a.strict, ktv, s_u);
+            }
+            const Cand best = block_argmax<NT>(local, a.strict, s_red);
             if (threadIdx.x == 0) {
                 a.lab_out[x.v] = best.label;
                 if (best.label != x.own) {
@@ -593,14 +652,25 @@ __global__ void __launch_bounds__(HUB_THREADS, 2) k_hub(SweepArgs a)
             continue;
         }
 
-        // aggregate the segment, then flush it into the hub's global table
-        accumulate_range<NT>(a, x.e0, lo, hi, x.vb, tk, ts, tp, LG);
-        __syncthreads();
         const int glg = ilog2_ceil(2u * (uint32_t)x.d);
         unsigned long long *gk = a.hkey + t.tab;
         uint32_t *gp = a.hnpos + t.tab;
         int32_t *gu = a.hused + t.tab / 2;
-        for (int j0 = 0; j0 < HUB_TABLE; j0 += NT) {
+        if (a.identity) {
+            // the segment's own winner is the only candidate it contributes
+            const Cand best =
+                block_argmax<NT>(identity_best<NT>(a, x.e0, lo, hi, ktv, threadIdx.x), a.strict,
+                                 s_red);
+            if (threadIdx.x == 0 && best.sum > 0) {
+                const int64_t claimed = global_add(gk, gp, glg, best.label, best.sum, best.npos);
+                if (claimed >= 0) gu[atomicAdd(a.hnused + ti, 1)] = (int32_t)claimed;
+            }
+        } else {
+            // aggregate the segment, then flush it into the hub's global table
+            accumulate_range<NT>(a, x.e0, lo, hi, x.vb, tk, ts, tp, LG);
+            __syncthreads();
+        }
+        for (int j0 = 0; j0 < (a.identity ? 0 : HUB_TABLE); j0 += NT) {
             const int j = j0 + threadIdx.x;
             const int32_t key = tk[j];
             int64_t claimed = -1;

@@ -117,9 +117,10 @@ def test_golden_traces_async(lp, golden_traces):
 
 
 # ---------------------------------------------------------------- every degree bucket
-def hub_graph(seed, n=40_000, hubs=3, hub_deg=12_000, p_extra=0.0002):
-    """A sparse random graph plus `hubs` vertices of degree ~hub_deg, so the
-    hub kernel's shared table overflows into the global one in iteration 1."""
+def hub_graph(seed, n=40_000, hubs=3, hub_deg=12_000, p_extra=0.0002, sorted_rows=False):
+    """A sparse random graph plus `hubs` vertices of degree ~hub_deg, so hub
+    rows span several 4096-entry segments.  Rows are shuffled unless
+    sorted_rows (sorted rows enable the identity first sweep)."""
     rng = np.random.default_rng(seed)
     m_rand = int(p_extra * n * n / 2)
     u = rng.integers(0, n, m_rand)
@@ -135,6 +136,9 @@ def hub_graph(seed, n=40_000, hubs=3, hub_deg=12_000, p_extra=0.0002):
     dst = np.concatenate([a[:, 1], a[:, 0]])
     perm = rng.permutation(src.size)  # shuffled rows: adjacency order matters
     src, dst = src[perm], dst[perm]
+    if sorted_rows:
+        order = np.lexsort((dst, src))
+        src, dst = src[order], dst[order]
     order = np.argsort(src, kind="stable")
     src, dst = src[order], dst[order]
     off = np.zeros(n + 1, np.int64)
@@ -164,6 +168,16 @@ def test_sync_parity_per_bucket(lp, shape, strict):
     deg = np.diff(off)
     assert deg.max() > {"small": 8, "warp": 33, "cta": 129, "hub": 8192, "mixed": 1024}[shape]
     assert_sync_parity(lp, off, idx, w, strict=strict, seed=11)
+
+
+@pytest.mark.parametrize("strict", [True, False])
+def test_identity_first_sweep_multi_segment_hubs(lp, strict):
+    """Sorted rows without repeats: the first sweep takes the identity path,
+    including hubs of several segments; sync and 2-wave async stay exact."""
+    off, idx, w = hub_graph(9, n=30_000, hubs=4, hub_deg=13_000, sorted_rows=True)
+    assert np.all(np.diff(idx)[np.diff(np.repeat(np.arange(off.size - 1), np.diff(off))) == 0] > 0)
+    assert_sync_parity(lp, off, idx, w, strict=strict, seed=4)
+    assert_async_parity(lp, off, idx, w, 2, strict=strict, seed=4)
 
 
 @pytest.mark.parametrize("waves", [2, 7, 31, 4096])
