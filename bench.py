@@ -13,6 +13,13 @@ Workloads (synthetic stand-ins for the paper's SuiteSparse classes):
   road4096  4096 x 4096 road-like grid, weights 1-16 (sync or async)
   sbm10k    planted partition, 10,000 vertices, synchronous
   kmer8m    k-mer-like chains, 8M vertices
+  batch     4096 planted-partition graphs (n log-uniform 1k-200k, 5-500 blocks,
+            mean degree 8-32, mixing 0.3) in one arena, synchronous; metric
+            graphs/s, compared with the same graphs run one at a time
+  serve     Poisson request stream (mean 200 req/s) of SBM / R-MAT / grid
+            graphs (n log-uniform 10k-2M, weights 1-8) drawn from a pool,
+            served with continuous batching; graphs/s and p50/p99 latency,
+            compared with the same arrivals served one graph at a time
 
 Extra keys: ``roofline`` (dominant sweep kernel vs measured HBM bandwidth),
 ``sweep`` (all sweep kernels of one iteration vs the same peak), ``e2e``
@@ -51,6 +58,8 @@ WORKLOADS = {
     "road4096": dict(mode="async", waves=31, strict=True, tolerance=0.05, max_iter=20),
     "sbm10k": dict(mode="sync", waves=31, strict=True, tolerance=0.05, max_iter=20),
     "kmer8m": dict(mode="async", waves=31, strict=True, tolerance=0.05, max_iter=20),
+    "batch": dict(mode="sync", waves=31, strict=True, tolerance=0.05, max_iter=20),
+    "serve": dict(mode="sync", waves=31, strict=True, tolerance=0.05, max_iter=20),
 }
 
 
@@ -69,6 +78,14 @@ def parse():
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--cpu-sweeps", type=int, default=4,
                     help="oracle sweeps in the CPU baseline sample")
+    ap.add_argument("--batch-count", type=int, default=4096, help="graphs of the batch workload")
+    ap.add_argument("--serve-seconds", type=float, default=20.0, help="arrival window (serve)")
+    ap.add_argument("--serve-rate", type=float, default=200.0, help="mean arrivals per second")
+    ap.add_argument("--serve-pool", type=int, default=48, help="distinct graphs in the pool")
+    ap.add_argument("--serve-baseline-seconds", type=float, default=5.0,
+                    help="arrival window replayed one graph at a time")
+    ap.add_argument("--per-graph-sample", type=int, default=256,
+                    help="graphs of the batch timed one at a time")
     return ap.parse_args()
 
 
@@ -229,6 +246,44 @@ def run_reference(args):
                 "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_reference_batch(args):
+    """The CPU oracle on graphs of the batch workload (bounded sample per step)."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import graphgen as gg
+    import oracle
+
+    p = workload_params(args)
+    params = gg.batch_sbm_params(count=args.batch_count, seed=1000)
+    sample = [gg.sbm_mixing(q["n"], q["k"], q["avg_degree"], q["mu"], seed=q["seed"])
+              for q in params[::256][:4]]
+    oracle.build()
+
+    def step():
+        t0 = time.perf_counter()
+        for g in sample:
+            oracle.rak(g.offsets, g.indices, g.weights, p["tolerance"], p["max_iter"], p["mode"],
+                       strict=p["strict"])
+        return time.perf_counter() - t0
+
+    for _ in range(args.warmup):
+        step()
+    tot = sum(step() for _ in range(args.steps))
+    value = len(sample) * args.steps / tot
+    print(json.dumps({
+        "impl": "reference", "metric": f"batched graphs/s ({args.batch_count} SBM graphs)",
+        "value": value, "unit": "graphs/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": "batch", "graphs": args.batch_count, **p},
+        "cpu_baseline": {"value": value, "unit": "graphs/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{len(sample)} graphs of the batch (every 256th) per step"},
+        "e2e": {"value": value, "unit": "graphs/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0}}), flush=True)
     return 0
 
 
@@ -400,8 +455,320 @@ def run_ours(args):
     return 0
 
 
+# --------------------------------------------------------------------------
+# batched graphs (one arena) against one graph at a time
+# --------------------------------------------------------------------------
+def batch_graphs(count):
+    import graphgen as gg
+
+    return gg.batch_sbm(gg.batch_sbm_params(count=count, seed=1000))
+
+
+def run_batch(args):
+    import torch
+
+    import paper_2301_09125_gb300 as lp
+    from paper_2301_09125_gb300 import build
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    build.build()
+    lp.load()
+    p = workload_params(args)
+    count = args.batch_count
+    t0 = time.perf_counter()
+    graphs = batch_graphs(count)
+    gen_s = time.perf_counter() - t0
+    n_tot = sum(g.n for g in graphs)
+    m_tot = sum(g.m for g in graphs)
+    stream = torch.cuda.current_stream(dev)
+    triples = [(g.offsets, g.indices, g.weights) for g in graphs]
+    params, _ = lp.make_params(tolerance=p["tolerance"], max_iter=p["max_iter"], mode=p["mode"],
+                               strict=p["strict"], waves=p["waves"])
+
+    # e2e: ingest from host buffers + run + modularity + labels back
+    t0 = time.perf_counter()
+    h = lp.lp_batch_create(triples, stream=stream.cuda_stream)
+    create_s = time.perf_counter() - t0
+
+    def step():
+        res = lp.lp_batch_run(h, count, params)
+        lp.lp_batch_modularity(h, 0)  # computes every graph's modularity
+        return res
+
+    for _ in range(args.warmup):
+        step()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(nvsmi_id(torch, local), enabled=not args.no_clocks)
+    lp.lp_profile_reset()
+    lp.lp_profile_enable(True)
+    launches0 = lp.lp_launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    iters_entries = 0
+    for _ in range(args.steps):
+        res = step()
+        iters_entries += sum(r.iterations * g.m for r, g in zip(res, graphs))
+    e1.record(stream)
+    barrier()
+    launches = lp.lp_launch_count() - launches0
+    lp.lp_profile_enable(False)
+    prof = lp.lp_profile_read()
+    clock_info = clocks.stop()
+    t_ms = e0.elapsed_time(e1)
+    t_ms, graphs_all = reduce_across_ranks(t_ms, count * args.steps, device=dev)
+    value = graphs_all / (t_ms * 1e-3)
+    gteps = iters_entries * world / (t_ms * 1e-3) / 1e9
+    labels0 = lp.lp_batch_labels_get(h, 0, graphs[0].n)
+    lp.lp_batch_destroy(h)
+    e2e_s = create_s + t_ms * 1e-3 / args.steps
+
+    # the same graphs one at a time: device-resident CSR, create + run + modularity
+    sample = list(range(0, count, max(1, count // args.per_graph_sample)))
+    dev_csr = [tuple(None if a is None else torch.from_numpy(a).to(dev) for a in triples[i])
+               for i in sample]
+    for i in sample[:3]:
+        hh = lp.lp_graph_create(*dev_csr[sample.index(i)], borrow=True, stream=stream.cuda_stream)
+        lp.lp_rak_run(hh, params)
+        lp.lp_graph_destroy(hh)
+    torch.cuda.synchronize()
+    lat = []
+    t0 = time.perf_counter()
+    for j, i in enumerate(sample):
+        s0 = time.perf_counter()
+        hh = lp.lp_graph_create(*dev_csr[j], borrow=True, stream=stream.cuda_stream)
+        lp.lp_rak_run(hh, params)
+        lp.lp_modularity(hh)
+        lp.lp_graph_destroy(hh)
+        lat.append(time.perf_counter() - s0)
+    per_graph_s = time.perf_counter() - t0
+    per_graph_gps = len(sample) / per_graph_s
+
+    peak, peak_kind = measured_peak_gbs()
+    kern = {k: v for k, v in prof.items() if v["launches"] > 0}
+    dom_name = max(kern, key=lambda k: kern[k]["total_ms"])
+    dom = kern[dom_name]
+    achieved = dom["bytes"] / (dom["total_ms"] * 1e-3) / 1e9
+    sweep_ms = sum(v["total_ms"] for v in kern.values())
+    line = {
+        "metric": f"batched graphs/s ({count} SBM graphs)", "value": value, "unit": "graphs/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": "batch", "graphs": count, "n_total": n_tot, "m_total": m_tot, **p,
+                   "step": "lp_batch_run (all graphs, per-graph convergence) + modularity of "
+                           "every graph, arena resident in HBM",
+                   "l2": "inputs larger than L2", "generation_s": round(gen_s, 1),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "gteps": gteps,
+        "per_graph_launch": {"graphs_per_s": per_graph_gps, "sample": len(sample),
+                             "p50_ms": 1e3 * statistics.median(lat),
+                             "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+                             "how": "lp_graph_create (borrowed device CSR) + lp_rak_run + "
+                                    "lp_modularity per graph, sequentially"},
+        "speedup_vs_per_graph": value / per_graph_gps,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": dom_name,
+                     "peak_source": peak_kind},
+        "kernels": {k: {"launches": v["launches"], "ms": v["total_ms"],
+                        "share": v["total_ms"] / sweep_ms} for k, v in kern.items()},
+        "gpu_launches": int(launches),
+        "clocks": clock_info,
+        "e2e": {"value": count * world / e2e_s, "unit": "graphs/s",
+                "h2d_bytes_per_step": int(sum(g.offsets.nbytes + g.indices.nbytes for g in graphs)),
+                "d2h_bytes_per_step": int(labels0.nbytes),
+                "how": "lp_batch_create from host arrays + one run + modularity"},
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+
+        oracle.build()
+        t0 = time.perf_counter()
+        done = 0
+        for g in graphs[::64][:16]:
+            oracle.rak(g.offsets, g.indices, g.weights, p["tolerance"], p["max_iter"], p["mode"],
+                       strict=p["strict"])
+            oracle.modularity(g.offsets, g.indices, g.weights, np.arange(g.n, dtype=np.int32))
+            done += 1
+            if time.perf_counter() - t0 > 25:
+                break
+        t = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": done / t, "unit": "graphs/s", "cores": 1,
+                                "kind": "oracle",
+                                "sample": f"{done} graphs of the batch (every 64th), full runs"}
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------
+# serving with continuous batching against one request at a time
+# --------------------------------------------------------------------------
+def serve_pool(count, seed=7):
+    """Graphs of the serving stream: type uniform over SBM (mean degree 16,
+    mixing 0.3), R-MAT (edge factor 8, 2^round(log2 n) vertices) and grid
+    (side floor(sqrt n)); n log-uniform in [10k, 2M]; weights 1-8."""
+    import math
+
+    import graphgen as gg
+
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(math.exp(rng.uniform(math.log(10_000), math.log(2_000_000))))
+        kind = i % 3
+        if kind == 0:
+            out.append(gg.sbm_mixing(n, max(2, n // 500), 16.0, 0.3, seed=seed + i, wmin=1, wmax=8))
+        elif kind == 1:
+            out.append(gg.rmat(int(round(math.log2(n))), edge_factor=8, seed=seed + i, wmin=1,
+                               wmax=8))
+        else:
+            out.append(gg.grid_road(int(math.isqrt(n)), seed=seed + i, wmin=1, wmax=8))
+    return out
+
+
+def run_serve(args):
+    import torch
+
+    import paper_2301_09125_gb300 as lp
+    from paper_2301_09125_gb300 import build
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local if world > 1 else 0)
+    build.build()
+    lp.load()
+    p = workload_params(args)
+    t0 = time.perf_counter()
+    pool = serve_pool(args.serve_pool)
+    gen_s = time.perf_counter() - t0
+    pinned = [tuple(torch.from_numpy(a).pin_memory() for a in (g.offsets, g.indices, g.weights))
+              for g in pool]
+    rng = np.random.default_rng(11)
+    n_req = int(rng.poisson(args.serve_rate * args.serve_seconds))
+    arrivals = np.sort(rng.uniform(0, args.serve_seconds, n_req))
+    picks = rng.integers(0, len(pool), n_req)
+    params, _ = lp.make_params(tolerance=p["tolerance"], max_iter=p["max_iter"], mode=p["mode"],
+                               strict=p["strict"], waves=p["waves"])
+    cfg = lp.lp_server_config_default()
+    cfg.hbm_budget = 64 << 30
+    cfg.max_active = 64
+    cfg.streams = 8
+
+    # warm-up: every pool graph once through the server
+    srv = lp.lp_server_create(cfg, params)
+    for i, (o, x, w) in enumerate(pinned):
+        lp.lp_server_submit(srv, i, o, x, w)
+    lp.lp_server_drain(srv)
+    lp.lp_server_poll(srv, capacity=len(pool))
+
+    launches0 = lp.lp_launch_count()
+    clocks = ClockSampler(nvsmi_id(torch, local), enabled=not args.no_clocks)
+    outs, done = {}, []
+    start = time.perf_counter()
+    for rid in range(n_req):
+        delay = start + arrivals[rid] - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        o, x, w = pinned[picks[rid]]
+        outs[rid] = np.empty(pool[picks[rid]].n, np.int32)
+        lp.lp_server_submit(srv, rid, o, x, w, outs[rid])
+        for r in lp.lp_server_poll(srv, capacity=256):
+            done.append(r)
+            outs.pop(r.request_id, None)
+    lp.lp_server_drain(srv)
+    done += lp.lp_server_poll(srv, capacity=n_req + 1)
+    makespan = time.perf_counter() - start
+    clock_info = clocks.stop()
+    launches = lp.lp_launch_count() - launches0
+    lp.lp_server_destroy(srv)
+    lat = np.array([r.latency_ms for r in done])
+    queued = np.array([r.queued_ms for r in done])
+    errors = sum(1 for r in done if r.status != 0)
+    entries = sum(r.iterations * pool[picks[r.request_id]].m for r in done)
+
+    # the same arrivals, one graph at a time (no overlap, no batching)
+    nb = int(np.searchsorted(arrivals, args.serve_baseline_seconds))
+    base_lat = []
+    bstart = time.perf_counter()
+    for rid in range(nb):
+        delay = bstart + arrivals[rid] - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        o, x, w = pinned[picks[rid]]
+        h = lp.lp_graph_create(o, x, w)
+        lp.lp_rak_run(h, params)
+        lp.lp_modularity(h)
+        lp.lp_labels_get(h)
+        lp.lp_graph_destroy(h)
+        base_lat.append(1e3 * (time.perf_counter() - bstart - arrivals[rid]))
+    base_span = time.perf_counter() - bstart
+    base_lat = np.array(base_lat) if base_lat else np.zeros(1)
+    line = {
+        "metric": f"served graphs/s (Poisson {args.serve_rate:g} req/s)",
+        "value": len(done) / makespan, "unit": "graphs/s", "n_gpus": 1, "steps": n_req,
+        "warmup": len(pool), "ms_per_step": 1e3 * makespan / max(1, len(done)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": "serve", **p, "requests": n_req, "window_s": args.serve_seconds,
+                   "pool_graphs": len(pool), "pool_generation_s": round(gen_s, 1),
+                   "max_active": cfg.max_active, "streams": cfg.streams,
+                   "hbm_budget_gib": cfg.hbm_budget >> 30,
+                   "l2": "graphs resident per request, no flush",
+                   "parallelism": "single GPU"},
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "mean_queued": float(queued.mean())},
+        "gteps": entries / makespan / 1e9,
+        "errors": errors,
+        "per_graph_launch": {"requests": nb, "graphs_per_s": nb / base_span,
+                             "p50_ms": float(np.percentile(base_lat, 50)),
+                             "p99_ms": float(np.percentile(base_lat, 99)),
+                             "window_s": args.serve_baseline_seconds},
+        "gpu_launches": int(launches),
+        "clocks": clock_info,
+        "e2e": {"value": len(done) / makespan, "unit": "graphs/s",
+                "h2d_bytes_per_step": int(np.mean([pool[i].offsets.nbytes + pool[i].indices.nbytes
+                                                   + pool[i].weights.nbytes for i in picks])),
+                "d2h_bytes_per_step": int(np.mean([pool[i].n * 4 for i in picks])),
+                "how": "submit from pinned host CSR -> labels and modularity back on the host"},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.workload == "serve":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable":
+                              "the serving workload has no CPU reference arm; see the batch and "
+                              "single-graph workloads"}))
+            return 0
+        return run_serve(args)
+    if args.workload == "batch":
+        if args.impl == "reference":
+            return run_reference_batch(args)
+        return run_batch(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -209,6 +209,68 @@ lp_status lp_batch_labels_get(lp_batch *b, int32_t index, int32_t *dst, int32_t 
 lp_status lp_batch_modularity(lp_batch *b, int32_t index, double *q);
 
 /* ---------------------------------------------------------------------------
+ * Serving: a request server with continuous batching.
+ * Each request is one graph run with the server's parameters.  A worker
+ * thread admits a queued request when fewer than max_active requests are on
+ * the device and its estimated footprint (about 16 n + 46 m bytes) fits the
+ * HBM budget still free, ingests it on one of the server's streams, and then
+ * advances it one RAK iteration (Sec. 3.2) at a time, interleaved with the
+ * other admitted requests; a converged request is retired (modularity,
+ * labels) as soon as it finishes, and queued requests take its place.  A
+ * request's result is the same as that of lp_rak_run on its graph alone.
+ * ------------------------------------------------------------------------- */
+typedef struct lp_server lp_server;
+
+typedef struct {
+    int64_t hbm_budget; /* device bytes admitted requests may hold together (default 8 GiB) */
+    int32_t max_active; /* requests on the device at once (default 64) */
+    int32_t streams;    /* CUDA streams the requests are spread over, 1..64 (default 8) */
+} lp_server_config;
+
+typedef struct {
+    int64_t request_id;
+    int32_t status;     /* LP_OK, or the error that ended this request */
+    int32_t iterations;
+    int32_t converged;
+    int32_t pad;
+    double modularity;
+    double queued_ms;   /* submit -> admitted */
+    double latency_ms;  /* submit -> result ready (labels copied) */
+} lp_serve_result;
+
+/* Fill *cfg with the defaults.  Errors: LP_EINVAL on NULL. */
+lp_status lp_server_config_default(lp_server_config *cfg);
+
+/* Start a server on the current device with parameters *p (init_labels must
+ * be NULL).  Errors: LP_EINVAL for bad arguments; LP_ENOMEM; LP_ECUDA. */
+lp_status lp_server_create(const lp_server_config *cfg, const lp_rak_params *p,
+                           lp_server **out);
+
+/* Queue one request.  offsets/indices/weights are a HOST CSR as in
+ * lp_graph_create (weights may be NULL); they are not copied at submit and
+ * must stay valid and unchanged until the request's result has been polled.
+ * labels_out (host, n int32, may be NULL) receives the final labels before the
+ * result is posted.  Thread-safe.
+ * Errors: LP_EINVAL for bad arguments; LP_ENOMEM if the request alone exceeds
+ * the budget.  A CSR that fails validation is reported in its result. */
+lp_status lp_server_submit(lp_server *s, int64_t request_id, int32_t n, int64_t m,
+                           const int32_t *offsets, const int32_t *indices,
+                           const int32_t *weights, int32_t *labels_out);
+
+/* Move up to `capacity` finished results to out (in completion order);
+ * *count receives how many.  Waits up to wait_ms for the first one.
+ * Returns LP_ENOTREADY when none was available.  Thread-safe. */
+lp_status lp_server_poll(lp_server *s, lp_serve_result *out, int32_t capacity, int32_t *count,
+                         int32_t wait_ms);
+
+/* Block until every submitted request has a result.  Errors: LP_EINVAL on NULL. */
+lp_status lp_server_drain(lp_server *s);
+
+/* Finish every submitted request, stop the worker and free the server
+ * (NULL is a no-op).  Unpolled results are discarded. */
+lp_status lp_server_destroy(lp_server *s);
+
+/* ---------------------------------------------------------------------------
  * One sweep without any allocation
  * ------------------------------------------------------------------------- */
 

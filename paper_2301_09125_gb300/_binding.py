@@ -55,6 +55,21 @@ class lp_graph_desc(ctypes.Structure):
                 ("indices", ctypes.c_void_p), ("weights", ctypes.c_void_p)]
 
 
+class lp_server_config(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_int64), ("max_active", ctypes.c_int32),
+                ("streams", ctypes.c_int32)]
+
+
+class lp_serve_result(ctypes.Structure):
+    _fields_ = [("request_id", ctypes.c_int64), ("status", ctypes.c_int32),
+                ("iterations", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("modularity", ctypes.c_double),
+                ("queued_ms", ctypes.c_double), ("latency_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+
+
 class lp_kernel_stat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64),
                 ("total_ms", ctypes.c_double), ("vertices", ctypes.c_double),
@@ -85,6 +100,15 @@ SIGNATURES = {
                                     ctypes.POINTER(lp_rak_result)]),
     "lp_batch_labels_get": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int32]),
     "lp_batch_modularity": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]),
+    "lp_server_config_default": (ctypes.c_int, [ctypes.POINTER(lp_server_config)]),
+    "lp_server_create": (ctypes.c_int, [ctypes.POINTER(lp_server_config),
+                                        ctypes.POINTER(lp_rak_params), ctypes.POINTER(_P)]),
+    "lp_server_submit": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64,
+                                        _P, _P, _P, _P]),
+    "lp_server_poll": (ctypes.c_int, [_P, ctypes.POINTER(lp_serve_result), ctypes.c_int32,
+                                      ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]),
+    "lp_server_drain": (ctypes.c_int, [_P]),
+    "lp_server_destroy": (ctypes.c_int, [_P]),
     "lp_profile_enable": (ctypes.c_int, [ctypes.c_int32]),
     "lp_profile_reset": (ctypes.c_int, []),
     "lp_profile_read": (ctypes.c_int, [ctypes.POINTER(lp_kernel_stat), ctypes.c_int32,
@@ -306,6 +330,56 @@ def lp_batch_modularity(handle: int, index: int) -> float:
     q = ctypes.c_double()
     _check(load().lp_batch_modularity(handle, index, ctypes.byref(q)))
     return q.value
+
+
+# ---------------------------------------------------------------- serving
+def lp_server_config_default() -> lp_server_config:
+    c = lp_server_config()
+    _check(load().lp_server_config_default(ctypes.byref(c)))
+    return c
+
+
+def lp_server_create(config: Optional[lp_server_config] = None,
+                     params: Optional[lp_rak_params] = None, **kw) -> int:
+    """Start a request server; ``kw`` are ``make_params`` arguments."""
+    if config is None:
+        config = lp_server_config_default()
+    if params is None:
+        params, _ = make_params(**kw)
+    h = ctypes.c_void_p()
+    _check(load().lp_server_create(ctypes.byref(config), ctypes.byref(params), ctypes.byref(h)))
+    return h.value
+
+
+def lp_server_submit(handle: int, request_id: int, offsets, indices, weights=None,
+                     labels_out=None) -> None:
+    """Queue a request (host arrays, kept alive by the caller until its
+    result has been polled)."""
+    po, _, ko = _int32_buffer(offsets, "offsets")
+    pi, _, ki = _int32_buffer(indices, "indices")
+    pw, _, _ = _int32_buffer(weights, "weights")
+    pl, _, _ = _int32_buffer(labels_out, "labels_out")
+    n = (ko.shape[0] if hasattr(ko, "shape") else len(ko)) - 1
+    m = ki.shape[0] if hasattr(ki, "shape") else len(ki)
+    _check(load().lp_server_submit(handle, int(request_id), int(n), int(m), po, pi, pw, pl))
+
+
+def lp_server_poll(handle: int, capacity: int = 256, wait_ms: int = 0) -> list:
+    out = (lp_serve_result * capacity)()
+    cnt = ctypes.c_int32()
+    st = load().lp_server_poll(handle, out, capacity, ctypes.byref(cnt), int(wait_ms))
+    if st not in (LP_OK, LP_ENOTREADY):
+        _check(st)
+    return [out[i] for i in range(cnt.value)]
+
+
+def lp_server_drain(handle: int) -> None:
+    _check(load().lp_server_drain(handle))
+
+
+def lp_server_destroy(handle: Optional[int]) -> None:
+    if handle:
+        _check(load().lp_server_destroy(handle))
 
 
 def lp_profile_enable(on: bool = True) -> None:

@@ -321,6 +321,8 @@ struct GraphSet {
         ev0 = ev1 = nullptr;
         for (cudaEvent_t e : prof_ev) cudaEventDestroy(e);
         prof_ev.clear();
+        if (ev_iter) cudaEventDestroy(ev_iter);
+        ev_iter = nullptr;
         cudaStreamSynchronize(st);
     }
 
@@ -555,8 +557,24 @@ struct GraphSet {
         return LP_OK;
     }
 
-    // Sec. 3.2 iteration over every graph of the set
-    lp_status run(const lp_rak_params *p, bool multi)
+    // State of a run in progress (lp_rak_run / lp_batch_run drive it to the
+    // end at once; the serving loop advances it one iteration per tick).
+    struct RunState {
+        lp_rak_params p{};
+        bool multi = false;
+        int32_t waves = 1;
+        int cur = 0;
+        int32_t it = 0;  // iterations launched
+        int32_t active_left = 0;
+        bool prof = false;
+        std::vector<int> prof_launch;   // bucket of each profiled launch
+        std::vector<int64_t> prof_len;  // its vertex count
+        SweepArgs a{};
+    } rs;
+    cudaEvent_t ev_iter = nullptr;  // end of the last launched iteration
+
+    // a2 and the argument checks of Sec. 3.2's iteration over every graph of the set
+    lp_status run_begin(const lp_rak_params *p, bool multi)
     {
         if (!p) return fail(LP_EINVAL, "params is NULL");
         if (!(p->tolerance >= 0.0 && p->tolerance <= 1.0))
@@ -573,6 +591,7 @@ struct GraphSet {
         if (multi && p->init_labels) return fail(LP_EINVAL, "batches start from unique labels");
         LP_TRY(ensure_changed((int64_t)p->max_iter * G));
         if (waves > 1) LP_TRY(ensure_waves(waves));
+        if (!ev_iter) LP_CU(cudaEventCreateWithFlags(&ev_iter, cudaEventDisableTiming));
         Launches L;
 
         // a2: initial labels (Sec. 3.2: unique labels) or a resumed labelling
@@ -601,13 +620,19 @@ struct GraphSet {
         std::fill(final_buf.begin(), final_buf.end(), 0);
         q_valid = false;
         for (auto &r : results) r = lp_rak_result{0, 0, 0, 0.0f};
-        int cur = 0;
-        const bool prof = g_prof_on.load();
-        std::vector<int> prof_launch;  // bucket of each profiled launch
-        std::vector<int64_t> prof_len;  // its vertex count
+        rs.p = *p;
+        rs.multi = multi;
+        rs.waves = waves;
+        rs.cur = 0;
+        rs.it = 0;
+        rs.active_left = G;
+        rs.prof = g_prof_on.load();
+        rs.prof_launch.clear();
+        rs.prof_len.clear();
         LP_CU(cudaEventRecord(ev0, st));
 
-        SweepArgs a{};
+        SweepArgs &a = rs.a;
+        a = SweepArgs{};
         a.off = off;
         a.idx = idx;
         a.wts = wts;
@@ -624,94 +649,116 @@ struct GraphSet {
         a.hnused = hnused;
         a.waves = (uint32_t)waves;
         a.wave_magic = fastmod_magic((uint32_t)waves);
+        return LP_OK;
+    }
 
-        int32_t active_left = G;
-        for (int32_t it = 0; it < p->max_iter && active_left > 0; ++it) {
-            const int64_t t = (int64_t)it + p->iter_offset;
-            // sync reads lab_in only; async reads lab_out for neighbours of
-            // earlier waves (written by this iteration's earlier launches)
-            a.lab_in = lab[cur];
-            a.lab_out = lab[cur ^ 1];
-            a.changed = changed + (int64_t)it * G;
-            a.key_t = stream_at(p->seed, (uint64_t)t + 1);
-            for (int launch_i = 0; launch_i < waves * NUM_BUCKETS; ++launch_i) {
-                const int k = launch_i / NUM_BUCKETS, b = launch_i % NUM_BUCKETS;
-                if (waves == 1) {
-                    a.list = list + bb[b];
-                    a.len = bl[b];
-                    a.htask = htask;
-                    a.hitems = hitems;
-                } else {
-                    a.list = wlist + wstart[(size_t)b * waves + k];
-                    a.len = wcount[(size_t)b * waves + k];
-                    if (b == 3) {
-                        a.htask = htask_w + (wstart[(size_t)b * waves + k] - wstart[(size_t)b * waves]);
-                        a.hitems = hitems_w[(size_t)k];
-                    }
-                }
-                if (a.len == 0) continue;
-                a.wave_k = (uint32_t)k;
-                // the first sweep from unique labels reads unique labels only
-                // in its first wave (later waves see this sweep's new labels)
-                a.identity = rows_distinct && it == 0 && !p->init_labels && k == 0;
-                if (prof) {
-                    while (prof_ev.size() < 2 * (prof_launch.size() + 1)) {
-                        cudaEvent_t e;
-                        LP_CU(cudaEventCreate(&e));
-                        prof_ev.push_back(e);
-                    }
-                    LP_CU(cudaEventRecord(prof_ev[2 * prof_launch.size()], st));
-                }
-                if (sweep_launch(b, a, multi, num_sms, st) != 0)
-                    return fail(LP_ECUDA, cuda_msg("sweep launch", cudaGetLastError()));
-                ++L.n;
-                if (prof) {
-                    LP_CU(cudaEventRecord(prof_ev[2 * prof_launch.size() + 1], st));
-                    prof_launch.push_back(b);
-                    prof_len.push_back(a.len);
+    bool run_done() const { return rs.active_left == 0 || rs.it >= rs.p.max_iter; }
+
+    // launch one iteration (a3-a5 for every bucket and wave) and the read of
+    // its changed counters; ev_iter marks its end
+    lp_status run_launch()
+    {
+        Launches L;
+        const int32_t it = rs.it;
+        const int32_t waves = rs.waves;
+        SweepArgs &a = rs.a;
+        const int64_t t = (int64_t)it + rs.p.iter_offset;
+        // sync reads lab_in only; async reads lab_out for neighbours of
+        // earlier waves (written by this iteration's earlier launches)
+        a.lab_in = lab[rs.cur];
+        a.lab_out = lab[rs.cur ^ 1];
+        a.changed = changed + (int64_t)it * G;
+        a.key_t = stream_at(rs.p.seed, (uint64_t)t + 1);
+        for (int launch_i = 0; launch_i < waves * NUM_BUCKETS; ++launch_i) {
+            const int k = launch_i / NUM_BUCKETS, b = launch_i % NUM_BUCKETS;
+            if (waves == 1) {
+                a.list = list + bb[b];
+                a.len = bl[b];
+                a.htask = htask;
+                a.hitems = hitems;
+            } else {
+                a.list = wlist + wstart[(size_t)b * waves + k];
+                a.len = wcount[(size_t)b * waves + k];
+                if (b == 3) {
+                    a.htask = htask_w + (wstart[(size_t)b * waves + k] - wstart[(size_t)b * waves]);
+                    a.hitems = hitems_w[(size_t)k];
                 }
             }
-            LP_CU(cudaMemcpyAsync(h_changed + (int64_t)it * G, a.changed,
-                                  (size_t)G * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-            LP_CU(cudaStreamSynchronize(st));
-            cur ^= 1;
-            bool deactivated = false;
-            for (int32_t g = 0; g < G; ++g) {
-                if (multi && !h_active[g]) continue;
-                const int64_t c = h_changed[(int64_t)it * G + g];
-                lp_rak_result &r = results[(size_t)g];
-                r.iterations = it + 1;
-                r.last_changed = c;
-                final_buf[(size_t)g] = cur;
-                // Sec. 3.2: converged when at most tolerance * n vertices changed
-                if ((double)c <= p->tolerance * (double)h_n[(size_t)g]) {
-                    r.converged = 1;
-                    if (multi) {
-                        h_active[g] = 0;
-                        deactivated = true;
-                    }
-                    --active_left;
+            if (a.len == 0) continue;
+            a.wave_k = (uint32_t)k;
+            // the first sweep from unique labels reads unique labels only in
+            // its first wave (later waves see this sweep's new labels)
+            a.identity = rows_distinct && it == 0 && !rs.p.init_labels && k == 0;
+            if (rs.prof) {
+                while (prof_ev.size() < 2 * (rs.prof_launch.size() + 1)) {
+                    cudaEvent_t e;
+                    LP_CU(cudaEventCreate(&e));
+                    prof_ev.push_back(e);
                 }
+                LP_CU(cudaEventRecord(prof_ev[2 * rs.prof_launch.size()], st));
             }
-            if (multi && deactivated && active_left > 0)
-                LP_CU(cudaMemcpyAsync(g_active, h_active, (size_t)G * sizeof(int32_t),
-                                      cudaMemcpyHostToDevice, st));
+            if (sweep_launch(b, a, rs.multi, num_sms, st) != 0)
+                return fail(LP_ECUDA, cuda_msg("sweep launch", cudaGetLastError()));
+            ++L.n;
+            if (rs.prof) {
+                LP_CU(cudaEventRecord(prof_ev[2 * rs.prof_launch.size() + 1], st));
+                rs.prof_launch.push_back(b);
+                rs.prof_len.push_back(a.len);
+            }
         }
+        LP_CU(cudaMemcpyAsync(h_changed + (int64_t)it * G, a.changed, (size_t)G * sizeof(int32_t),
+                              cudaMemcpyDeviceToHost, st));
+        LP_CU(cudaEventRecord(ev_iter, st));
+        rs.it = it + 1;
+        return LP_OK;
+    }
+
+    // a6 after the launched iteration has finished on the device
+    lp_status run_finish()
+    {
+        const int32_t it = rs.it - 1;
+        rs.cur ^= 1;
+        bool deactivated = false;
+        for (int32_t g = 0; g < G; ++g) {
+            if (rs.multi && !h_active[g]) continue;
+            const int64_t c = h_changed[(int64_t)it * G + g];
+            lp_rak_result &r = results[(size_t)g];
+            r.iterations = it + 1;
+            r.last_changed = c;
+            final_buf[(size_t)g] = rs.cur;
+            // Sec. 3.2: converged when at most tolerance * n vertices changed
+            if ((double)c <= rs.p.tolerance * (double)h_n[(size_t)g]) {
+                r.converged = 1;
+                if (rs.multi) {
+                    h_active[g] = 0;
+                    deactivated = true;
+                }
+                --rs.active_left;
+            }
+        }
+        if (rs.multi && deactivated && rs.active_left > 0)
+            LP_CU(cudaMemcpyAsync(g_active, h_active, (size_t)G * sizeof(int32_t),
+                                  cudaMemcpyHostToDevice, st));
+        return LP_OK;
+    }
+
+    lp_status run_end()
+    {
         LP_CU(cudaEventRecord(ev1, st));
         LP_CU(cudaEventSynchronize(ev1));
         float ms = 0.f;
         LP_CU(cudaEventElapsedTime(&ms, ev0, ev1));
         for (auto &r : results) r.gpu_ms = ms;
-        if (prof && !prof_launch.empty()) {
+        if (rs.prof && !rs.prof_launch.empty()) {
             std::lock_guard<std::mutex> lock(g_prof_mu);
-            for (size_t i = 0; i < prof_launch.size(); ++i) {
+            for (size_t i = 0; i < rs.prof_launch.size(); ++i) {
                 float kms = 0.f;
                 LP_CU(cudaEventElapsedTime(&kms, prof_ev[2 * i], prof_ev[2 * i + 1]));
-                const int b = prof_launch[i];
+                const int b = rs.prof_launch[i];
                 KernelStat &k = g_prof[b];
                 k.launches += 1;
                 k.ms += kms;
-                const double verts = (double)prof_len[i];
+                const double verts = (double)rs.prof_len[i];
                 // entries of a wave launch: its share of the bucket's entries
                 const double ents = bl[b] ? (double)be[b] * verts / (double)bl[b] : 0.0;
                 k.vertices += verts;
@@ -723,8 +770,20 @@ struct GraphSet {
         }
         history.assign((size_t)results[0].iterations, 0);
         for (int32_t i = 0; i < results[0].iterations; ++i) history[i] = h_changed[(int64_t)i * G];
-        if (multi) LP_TRY(gather_final_labels());
+        if (rs.multi) LP_TRY(gather_final_labels());
         return LP_OK;
+    }
+
+    // Sec. 3.2 iteration over every graph of the set, to the end
+    lp_status run(const lp_rak_params *p, bool multi)
+    {
+        LP_TRY(run_begin(p, multi));
+        while (!run_done()) {
+            LP_TRY(run_launch());
+            LP_CU(cudaEventSynchronize(ev_iter));
+            LP_TRY(run_finish());
+        }
+        return run_end();
     }
 
     // Graphs of a batch stop in different iterations, so their final labels
@@ -808,6 +867,17 @@ struct GraphSet {
 
 lp_status lp_fail(lp_status s, const std::string &msg) { return fail(s, msg); }
 
+}  // namespace lp
+
+struct lp_graph;
+namespace lp {
+// Stepwise iteration of one graph, for the serving loop (lp_serve.cu).
+lp_status graph_run_begin(lp_graph *g, const lp_rak_params *p);
+bool graph_run_done(lp_graph *g);
+lp_status graph_run_launch(lp_graph *g, cudaEvent_t *done_event);
+lp_status graph_run_finish(lp_graph *g);
+lp_status graph_run_end(lp_graph *g, lp_rak_result *r);
+
 void lp_add_launches(int64_t n) { g_launches += n; }
 
 }  // namespace lp
@@ -819,6 +889,30 @@ struct lp_graph {
 struct lp_batch {
     lp::GraphSet s;
 };
+
+namespace lp {
+lp_status graph_run_begin(lp_graph *g, const lp_rak_params *p)
+{
+    DeviceGuard dg(g->s.device);
+    return g->s.run_begin(p, false);
+}
+bool graph_run_done(lp_graph *g) { return g->s.run_done(); }
+lp_status graph_run_launch(lp_graph *g, cudaEvent_t *done_event)
+{
+    DeviceGuard dg(g->s.device);
+    LP_TRY(g->s.run_launch());
+    *done_event = g->s.ev_iter;
+    return LP_OK;
+}
+lp_status graph_run_finish(lp_graph *g) { return g->s.run_finish(); }
+lp_status graph_run_end(lp_graph *g, lp_rak_result *r)
+{
+    DeviceGuard dg(g->s.device);
+    LP_TRY(g->s.run_end());
+    *r = g->s.results[0];
+    return LP_OK;
+}
+}  // namespace lp
 
 // ----------------------------------------------------------------------------
 // Entry points

@@ -33,6 +33,28 @@ __device__ __forceinline__ unsigned long long warp_sum64(unsigned long long v)
     return v;
 }
 
+// Running K_c contribution of one thread: consecutive rows of one community
+// are summed in a register and added with one atomic when the community
+// changes (a converged labelling often has one community for most rows, and
+// atomics on one address serialise).
+struct KcRun {
+    int64_t slot = -1;
+    unsigned long long sum = 0;
+    __device__ __forceinline__ void add(unsigned long long *kc, int64_t s, unsigned long long k)
+    {
+        if (s != slot) {
+            flush(kc);
+            slot = s;
+        }
+        sum += k;
+    }
+    __device__ __forceinline__ void flush(unsigned long long *kc)
+    {
+        if (slot >= 0 && sum) atomicAdd(kc + slot, sum);
+        sum = 0;
+    }
+};
+
 struct MV {  // one vertex as the modularity pass sees it
     int32_t v, g, vb, d;
     int64_t e0;
@@ -60,6 +82,7 @@ __global__ void __launch_bounds__(256) k_mod_small(ModArgs a)
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long l_acc = 0, w_acc = 0;
+    KcRun run;
     for (int64_t tile = wid; tile * 32 < a.len; tile += nw) {
         const int64_t i = tile * 32 + lane;
         MV x{0, 0, 0, 0, 0};
@@ -104,7 +127,7 @@ __global__ void __launch_bounds__(256) k_mod_small(ModArgs a)
             const uint32_t kv = __reduce_add_sync(og, w);
             const uint32_t lv = __reduce_add_sync(og, same);
             if (act && lane == __ffs(og) - 1) {
-                atomicAdd(a.kc + o_vb + o_c, (unsigned long long)kv);
+                run.add(a.kc, (int64_t)o_vb + o_c, kv);
                 if (MULTI) {
                     atomicAdd(a.acc + 4 * (int64_t)o_g, (unsigned long long)lv);
                     atomicAdd(a.acc + 4 * (int64_t)o_g + 1, (unsigned long long)kv);
@@ -117,6 +140,7 @@ __global__ void __launch_bounds__(256) k_mod_small(ModArgs a)
             start = end;
         }
     }
+    run.flush(a.kc);
     if (!MULTI) {
         l_acc = warp_sum64(l_acc);
         w_acc = warp_sum64(w_acc);
@@ -137,6 +161,7 @@ __global__ void __launch_bounds__(256) k_mod_rows(ModArgs a)  // 256 / NT rows p
     const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / NT;
     const int t = threadIdx.x % NT;
     unsigned long long l_tot = 0, w_tot = 0;
+    KcRun run;
     for (int64_t item = grp_id; item < a.len; item += ngrp) {
         const MV x = load_mv<MULTI>(a, a.list[item]);
         const int32_t cv = __ldg(a.lab + x.v);
@@ -186,7 +211,7 @@ __global__ void __launch_bounds__(256) k_mod_rows(ModArgs a)  // 256 / NT rows p
             __syncthreads();
         }
         if (t == 0) {
-            atomicAdd(a.kc + x.vb + cv, kv);
+            run.add(a.kc, (int64_t)x.vb + cv, kv);
             if (MULTI) {
                 atomicAdd(a.acc + 4 * (int64_t)x.g, lv);
                 atomicAdd(a.acc + 4 * (int64_t)x.g + 1, kv);
@@ -196,6 +221,7 @@ __global__ void __launch_bounds__(256) k_mod_rows(ModArgs a)  // 256 / NT rows p
             }
         }
     }
+    run.flush(a.kc);
     if (!MULTI && t == 0 && w_tot) {
         atomicAdd(a.acc, l_tot);
         atomicAdd(a.acc + 1, w_tot);
