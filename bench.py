@@ -81,6 +81,8 @@ def parse():
     ap.add_argument("--batch-count", type=int, default=4096, help="graphs of the batch workload")
     ap.add_argument("--serve-seconds", type=float, default=20.0, help="arrival window (serve)")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="mean arrivals per second")
+    ap.add_argument("--serve-saturation", type=int, default=512,
+                    help="requests of the burst that measures service capacity")
     ap.add_argument("--serve-pool", type=int, default=48, help="distinct graphs in the pool")
     ap.add_argument("--serve-baseline-seconds", type=float, default=5.0,
                     help="arrival window replayed one graph at a time")
@@ -724,6 +726,30 @@ def run_serve(args):
         base_lat.append(1e3 * (time.perf_counter() - bstart - arrivals[rid]))
     base_span = time.perf_counter() - bstart
     base_lat = np.array(base_lat) if base_lat else np.zeros(1)
+
+    # saturation: the same burst of requests submitted at once, served with
+    # continuous batching and one graph at a time (service capacity)
+    sat_picks = np.random.default_rng(13).integers(0, len(pool), args.serve_saturation)
+    srv = lp.lp_server_create(cfg, params)
+    sstart = time.perf_counter()
+    for rid, k in enumerate(sat_picks):
+        o, x, w = pinned[k]
+        outs[("sat", rid)] = np.empty(pool[k].n, np.int32)
+        lp.lp_server_submit(srv, rid, o, x, w, outs[("sat", rid)])
+    lp.lp_server_drain(srv)
+    sat_span = time.perf_counter() - sstart
+    sat_done = lp.lp_server_poll(srv, capacity=len(sat_picks) + 1)
+    lp.lp_server_destroy(srv)
+    sat_err = sum(1 for r in sat_done if r.status != 0)
+    sstart = time.perf_counter()
+    for k in sat_picks:
+        o, x, w = pinned[k]
+        h = lp.lp_graph_create(o, x, w)
+        lp.lp_rak_run(h, params)
+        lp.lp_modularity(h)
+        lp.lp_labels_get(h)
+        lp.lp_graph_destroy(h)
+    seq_span = time.perf_counter() - sstart
     line = {
         "metric": f"served graphs/s (Poisson {args.serve_rate:g} req/s)",
         "value": len(done) / makespan, "unit": "graphs/s", "n_gpus": 1, "steps": n_req,
@@ -744,6 +770,11 @@ def run_serve(args):
                              "p50_ms": float(np.percentile(base_lat, 50)),
                              "p99_ms": float(np.percentile(base_lat, 99)),
                              "window_s": args.serve_baseline_seconds},
+        "saturation": {"requests": len(sat_picks), "errors": sat_err,
+                       "served_graphs_per_s": len(sat_picks) / sat_span,
+                       "per_graph_launch_graphs_per_s": len(sat_picks) / seq_span,
+                       "how": "all requests submitted at t=0; the per-graph arm runs the same "
+                              "requests one after another through lp_graph_create/lp_rak_run"},
         "gpu_launches": int(launches),
         "clocks": clock_info,
         "e2e": {"value": len(done) / makespan, "unit": "graphs/s",

@@ -1,15 +1,16 @@
 // Continuous-batching request server (lp_server_*).
 //
-// Requests (one graph each, host CSR) queue up as they are submitted.  A
-// worker thread admits a queued request as soon as an active slot is free and
-// its estimated device footprint fits the HBM budget, ingests it on one of
-// the server's CUDA streams, and from then on advances it one RAK iteration
-// at a time: whenever a request's in-flight iteration has finished on the
-// device (event query), the worker applies the tolerance test and either
-// launches its next iteration or retires it (modularity, labels copied to the
-// caller's buffer, result queued for lp_server_poll).  Requests therefore join
-// and leave between iterations while the kernels of the others keep running
-// on their streams; each request's result is the same as a lone lp_rak_run.
+// Requests (one graph each, host CSR) queue up as they are submitted.  An
+// admission thread takes a queued request as soon as an active slot is free
+// and its estimated device footprint fits the HBM budget, and ingests it on
+// one of the server's CUDA streams.  A worker thread advances every ingested
+// request one RAK iteration at a time: whenever a request's in-flight
+// iteration has finished on the device (event query), the worker applies the
+// tolerance test and either launches its next iteration or retires it
+// (modularity, labels copied to the caller's buffer, result queued for
+// lp_server_poll).  Requests therefore join and leave between iterations while
+// the kernels of the others keep running on their streams, and ingest never
+// holds up the launches; each result is the same as a lone lp_rak_run.
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -73,15 +74,17 @@ struct lp_server {
     Clock::time_point t0 = Clock::now();
 
     std::mutex mu;
-    std::condition_variable cv_work, cv_done;
-    std::deque<std::unique_ptr<Request>> queue;
+    std::condition_variable cv_work, cv_done, cv_admit;
+    std::deque<std::unique_ptr<Request>> queue;    // submitted, not yet admitted
+    std::deque<std::unique_ptr<Request>> ready;    // ingested, not yet picked up
     std::deque<lp_serve_result> results;
     int64_t outstanding = 0;  // submitted, result not yet queued
+    int64_t slots_used = 0;   // admitted, not yet retired
+    int64_t mem_used = 0;     // footprint of the admitted requests
     bool stop = false;
-    std::thread worker;
+    std::thread worker, admitter;
 
-    std::vector<std::unique_ptr<Request>> active;
-    int64_t mem_used = 0;
+    std::vector<std::unique_ptr<Request>> active;  // worker thread only
 
     void retire(std::unique_ptr<Request> r, lp_status st)
     {
@@ -93,9 +96,11 @@ struct lp_server {
         }
         std::lock_guard<std::mutex> lock(mu);
         mem_used -= r->footprint;
+        --slots_used;
         results.push_back(r->res);
         --outstanding;
         cv_done.notify_all();
+        cv_admit.notify_one();
     }
 
     // ingest and start a request; false if it failed (already retired)
@@ -150,29 +155,48 @@ struct lp_server {
         return false;
     }
 
+    // admission thread: slot and budget check, then ingest on a stream
+    void admit_loop()
+    {
+        cudaSetDevice(device);
+        for (;;) {
+            std::unique_ptr<Request> r;
+            {
+                std::unique_lock<std::mutex> lock(mu);
+                cv_admit.wait(lock, [this] {
+                    return stop || (!queue.empty() && slots_used < cfg.max_active &&
+                                    mem_used + queue.front()->footprint <= cfg.hbm_budget);
+                });
+                if (stop && queue.empty()) return;
+                if (queue.empty()) continue;
+                r = std::move(queue.front());
+                queue.pop_front();
+                mem_used += r->footprint;
+                ++slots_used;
+            }
+            if (admit(r)) {
+                std::lock_guard<std::mutex> lock(mu);
+                ready.push_back(std::move(r));
+                cv_work.notify_one();
+            }
+        }
+    }
+
+    // worker thread: advance every ingested request by iterations
     void run()
     {
         cudaSetDevice(device);
         for (;;) {
-            // admission: free slot and room in the HBM budget
-            std::vector<std::unique_ptr<Request>> admitted;
             {
                 std::unique_lock<std::mutex> lock(mu);
-                for (;;) {
-                    while (!queue.empty() && (int)(active.size() + admitted.size()) < cfg.max_active &&
-                           mem_used + queue.front()->footprint <= cfg.hbm_budget) {
-                        mem_used += queue.front()->footprint;
-                        admitted.push_back(std::move(queue.front()));
-                        queue.pop_front();
-                    }
-                    if (!admitted.empty() || !active.empty()) break;
-                    if (stop) return;
-                    cv_work.wait(lock);
+                if (active.empty())
+                    cv_work.wait(lock, [this] { return !ready.empty() || (stop && outstanding == 0); });
+                if (active.empty() && ready.empty() && stop && outstanding == 0) return;
+                while (!ready.empty()) {
+                    active.push_back(std::move(ready.front()));
+                    ready.pop_front();
                 }
             }
-            for (auto &r : admitted)
-                if (admit(r)) active.push_back(std::move(r));
-
             bool progressed = false;
             for (size_t i = 0; i < active.size();) {
                 if (advance(active[i], &progressed)) {
@@ -183,13 +207,10 @@ struct lp_server {
                 }
             }
             if (!progressed && !active.empty()) {
-                // nothing finished: wait for the oldest in-flight iteration,
-                // unless new requests may be admitted meanwhile
+                // nothing finished: wait briefly for a newly ingested request
                 std::unique_lock<std::mutex> lock(mu);
-                const bool may_admit = !queue.empty() && (int)active.size() < cfg.max_active &&
-                                       mem_used + queue.front()->footprint <= cfg.hbm_budget;
-                lock.unlock();
-                if (!may_admit && active.front()->in_flight) cudaEventSynchronize(active.front()->ev);
+                cv_work.wait_for(lock, std::chrono::microseconds(20),
+                                 [this] { return !ready.empty(); });
             }
         }
     }
@@ -232,6 +253,7 @@ lp_status lp_server_create(const lp_server_config *cfg, const lp_rak_params *p, 
     }
     lp_server *raw = s.get();
     s->worker = std::thread([raw] { raw->run(); });
+    s->admitter = std::thread([raw] { raw->admit_loop(); });
     *out = s.release();
     return LP_OK;
 }
@@ -263,7 +285,7 @@ lp_status lp_server_submit(lp_server *s, int64_t request_id, int32_t n, int64_t 
         s->queue.push_back(std::move(r));
         ++s->outstanding;
     }
-    s->cv_work.notify_one();
+    s->cv_admit.notify_one();
     return LP_OK;
 }
 
@@ -302,6 +324,8 @@ lp_status lp_server_destroy(lp_server *s)
         s->stop = true;
     }
     s->cv_work.notify_all();
+    s->cv_admit.notify_all();
+    if (s->admitter.joinable()) s->admitter.join();
     if (s->worker.joinable()) s->worker.join();
     for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
     delete s;
