@@ -210,14 +210,15 @@ lp_status lp_batch_modularity(lp_batch *b, int32_t index, double *q);
 
 /* ---------------------------------------------------------------------------
  * Serving: a request server with continuous batching.
- * Each request is one graph run with the server's parameters.  A worker
+ * Each request is one graph run with the server's parameters.  An admission
  * thread admits a queued request when fewer than max_active requests are on
- * the device and its estimated footprint (about 16 n + 46 m bytes) fits the
- * HBM budget still free, ingests it on one of the server's streams, and then
- * advances it one RAK iteration (Sec. 3.2) at a time, interleaved with the
- * other admitted requests; a converged request is retired (modularity,
- * labels) as soon as it finishes, and queued requests take its place.  A
- * request's result is the same as that of lp_rak_run on its graph alone.
+ * the device and its estimated footprint (about 40 n + 88 m bytes) fits the
+ * HBM budget still free, and ingests it on one of the server's streams; a
+ * worker thread advances every admitted request one RAK iteration (Sec. 3.2)
+ * at a time, interleaved with the others; a converged request is retired
+ * (modularity, labels) as soon as it finishes, and queued requests take its
+ * place.  A request's result is the same as that of lp_rak_run on its graph
+ * alone.
  * ------------------------------------------------------------------------- */
 typedef struct lp_server lp_server;
 
@@ -317,7 +318,7 @@ lp_status lp_rak_sweep_noalloc(int32_t n, int64_t m, const int32_t *offsets,
  * (a small overhead); the statistics accumulate across runs and graphs until
  * lp_profile_reset. */
 typedef struct {
-    char name[32];    /* "sweep_small", "sweep_warp", "sweep_cta", "sweep_hub" */
+    char name[32];    /* "sweep_small", "sweep_warp", "sweep_cta", "sweep_cta2", "sweep_hub" */
     int64_t launches; /* profiled launches */
     double total_ms;  /* summed event time */
     double vertices;  /* vertices scheduled (summed over launches) */
@@ -334,8 +335,8 @@ lp_status lp_profile_enable(int32_t on);
 lp_status lp_profile_reset(void);
 
 /* Copy up to `capacity` kernel statistics to out; *count receives how many
- * kernels exist (4).  Errors: LP_EINVAL on NULL count, or NULL out with
- * capacity > 0. */
+ * kernels exist (5, one per degree bucket).  Errors: LP_EINVAL on NULL count,
+ * or NULL out with capacity > 0. */
 lp_status lp_profile_read(lp_kernel_stat *out, int32_t capacity, int32_t *count);
 
 /* Message of the last failed call on this thread ("" if none). */

@@ -26,14 +26,15 @@ std::atomic<int64_t> g_launches{0};
 
 // Per-kernel sweep statistics (lp_profile_*): while enabled, every sweep
 // launch is bracketed by CUDA events on the graph's stream.
-const char *const KERNEL_NAMES[4] = {"sweep_small", "sweep_warp", "sweep_cta", "sweep_hub"};
+const char *const KERNEL_NAMES[lp::NUM_BUCKETS] = {"sweep_small", "sweep_warp", "sweep_cta",
+                                                   "sweep_cta2", "sweep_hub"};
 struct KernelStat {
     int64_t launches = 0;
     double ms = 0, vertices = 0, entries = 0, bytes = 0;
 };
 std::mutex g_prof_mu;
 std::atomic<bool> g_prof_on{false};
-KernelStat g_prof[4];
+KernelStat g_prof[lp::NUM_BUCKETS];
 
 lp_status fail(lp_status s, const std::string &msg)
 {
@@ -216,8 +217,8 @@ struct GraphSet {
     bool own_off = true, own_idx = true, own_wts = true;
     int32_t *lab[2] = {nullptr, nullptr};
     int32_t *list = nullptr;
-    int64_t bb[NUM_BUCKETS] = {0, 0, 0, 0}, bl[NUM_BUCKETS] = {0, 0, 0, 0};
-    int64_t be[NUM_BUCKETS] = {0, 0, 0, 0};  // summed degree of each bucket
+    int64_t bb[NUM_BUCKETS] = {}, bl[NUM_BUCKETS] = {};
+    int64_t be[NUM_BUCKETS] = {};  // summed degree of each bucket
     // wave-partitioned bucket lists for asynchronous runs (built per wave count)
     int32_t *wlist = nullptr;
     int64_t *d_wtot = nullptr;
@@ -237,12 +238,16 @@ struct GraphSet {
     std::vector<int> final_buf;
     std::vector<lp_rak_result> results;
     std::vector<int64_t> history;  // graph 0
-    // hub overflow tables
-    // hub segments: tasks of the hub bucket (plain) and of its part in each wave,
-    // global tables (sized for all hubs), used lists and per-task counters
+    // hub tasks of the hub bucket (plain) and of its part in each wave, with
+    // their counts of long rows, segments and partitions; segment records,
+    // partition offsets and bests (sized for the plain list, which every wave
+    // part is a subset of); fallback tables, used lists and per-task counters
     HubTask *htask = nullptr, *htask_w = nullptr;
-    int64_t hitems = 0;
-    std::vector<int64_t> hitems_w;
+    int64_t hmulti = 0, hsegs = 0, hparts = 0;
+    std::vector<int64_t> hmulti_w, hsegs_w, hparts_w;
+    int4 *hrec = nullptr;
+    int32_t *hpoff = nullptr;
+    uint4 *hpbest = nullptr;
     unsigned long long *hkey = nullptr;
     uint32_t *hnpos = nullptr;
     int32_t *hused = nullptr, *hdone = nullptr, *hnused = nullptr;
@@ -292,8 +297,11 @@ struct GraphSet {
         f(hkey);
         f(hnpos);
         f(hused);
-        f(hdone);
         f(hnused);
+        f(hdone);
+        f(hrec);
+        f(hpoff);
+        f(hpbest);
         f(kc);
         f(macc);
         fh(h_macc);
@@ -313,6 +321,9 @@ struct GraphSet {
         hkey = nullptr;
         hnpos = nullptr;
         hused = hdone = hnused = nullptr;
+        hrec = nullptr;
+        hpoff = nullptr;
+        hpbest = nullptr;
         kc = macc = h_macc = nullptr;
         g_sel = nullptr;
         lab_tmp = nullptr;
@@ -423,50 +434,56 @@ struct GraphSet {
         }
         // hub vertices: largest degree first, so the static CTA assignment of
         // the hub kernel balances
-        if (bl[3] > 0) {
+        if (bl[HUB_BUCKET] > 0) {
             int32_t *deg = nullptr;
-            LP_TRY(dev_alloc(&deg, bl[3], "hub degrees", st, device));
-            std::vector<int32_t> hv((size_t)bl[3]), hd((size_t)bl[3]);
+            LP_TRY(dev_alloc(&deg, bl[HUB_BUCKET], "hub degrees", st, device));
+            std::vector<int32_t> hv((size_t)bl[HUB_BUCKET]), hd((size_t)bl[HUB_BUCKET]);
             cudaError_t e = cudaSuccess;
-            if (degrees_of(off, vgraph, list + bb[3], bl[3], deg, st, &L.n) != 0)
+            if (degrees_of(off, vgraph, list + bb[HUB_BUCKET], bl[HUB_BUCKET], deg, st, &L.n) != 0)
                 e = cudaGetLastError();
             if (e == cudaSuccess)
-                e = cudaMemcpyAsync(hv.data(), list + bb[3], bl[3] * sizeof(int32_t),
+                e = cudaMemcpyAsync(hv.data(), list + bb[HUB_BUCKET], bl[HUB_BUCKET] * sizeof(int32_t),
                                     cudaMemcpyDeviceToHost, st);
             if (e == cudaSuccess)
-                e = cudaMemcpyAsync(hd.data(), deg, bl[3] * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                e = cudaMemcpyAsync(hd.data(), deg, bl[HUB_BUCKET] * sizeof(int32_t), cudaMemcpyDeviceToHost,
                                     st);
             if (e == cudaSuccess) e = cudaStreamSynchronize(st);
             cudaFreeAsync(deg, st);
             if (e != cudaSuccess) return fail(LP_ECUDA, cuda_msg("hub degrees", e));
-            std::vector<int64_t> order((size_t)bl[3]);
+            std::vector<int64_t> order((size_t)bl[HUB_BUCKET]);
             for (size_t i = 0; i < order.size(); ++i) order[i] = (int64_t)i;
             std::stable_sort(order.begin(), order.end(),
                              [&](int64_t x, int64_t y) { return hd[x] > hd[y]; });
             std::vector<int32_t> sorted(order.size());
             for (size_t i = 0; i < order.size(); ++i) sorted[i] = hv[order[i]];
             hub_max_deg = hd[order[0]];
-            LP_CU(cudaMemcpyAsync(list + bb[3], sorted.data(), bl[3] * sizeof(int32_t),
+            LP_CU(cudaMemcpyAsync(list + bb[HUB_BUCKET], sorted.data(), bl[HUB_BUCKET] * sizeof(int32_t),
                                   cudaMemcpyHostToDevice, st));
-            // segment tasks of the hub bucket and one global table per hub of
-            // more than one segment (zeroed; every use leaves it zeroed)
-            LP_TRY(dev_alloc(&htask, bl[3], "hub tasks", st, device));
-            int64_t tot[2] = {0, 0};
-            if (hub_tasks(list + bb[3], bl[3], off, vgraph, htask, d_counts, st, &L.n) != 0)
+            // hub tasks, the segment / partition scratch of the long rows and
+            // one fallback table per long row (zeroed; every use leaves it zeroed)
+            LP_TRY(dev_alloc(&htask, bl[HUB_BUCKET], "hub tasks", st, device));
+            int64_t tot[5] = {0, 0, 0, 0, 0};
+            if (hub_tasks(list + bb[HUB_BUCKET], bl[HUB_BUCKET], off, vgraph, htask, d_counts, st, &L.n) != 0)
                 return fail(LP_ECUDA, cuda_msg("hub tasks", cudaGetLastError()));
             LP_CU(cudaMemcpyAsync(tot, d_counts, sizeof tot, cudaMemcpyDeviceToHost, st));
             LP_CU(cudaStreamSynchronize(st));
-            hitems = tot[0];
+            hmulti = tot[0];
+            hsegs = tot[2];
+            hparts = tot[3];
             const int64_t slots = tot[1] > 0 ? tot[1] : 1;
+            LP_TRY(dev_alloc(&hrec, (tot[2] > 0 ? tot[2] : 1) * HUB_SEG, "hub records", st, device));
+            LP_TRY(dev_alloc(&hpoff, tot[4] > 0 ? tot[4] : 1, "hub partition offsets", st, device));
+            LP_TRY(dev_alloc(&hpbest, 2 * (tot[3] > 0 ? tot[3] : 1), "hub partition bests", st,
+                             device));
             LP_TRY(dev_alloc(&hkey, slots, "hub tables", st, device));
             LP_TRY(dev_alloc(&hnpos, slots, "hub tables", st, device));
             LP_TRY(dev_alloc(&hused, slots / 2 + 1, "hub used lists", st, device));
-            LP_TRY(dev_alloc(&hdone, bl[3], "hub counters", st, device));
-            LP_TRY(dev_alloc(&hnused, bl[3], "hub counters", st, device));
+            LP_TRY(dev_alloc(&hdone, bl[HUB_BUCKET], "hub counters", st, device));
+            LP_TRY(dev_alloc(&hnused, bl[HUB_BUCKET], "hub counters", st, device));
             LP_CU(cudaMemsetAsync(hkey, 0, (size_t)slots * sizeof(unsigned long long), st));
             LP_CU(cudaMemsetAsync(hnpos, 0, (size_t)slots * sizeof(uint32_t), st));
-            LP_CU(cudaMemsetAsync(hdone, 0, (size_t)bl[3] * sizeof(int32_t), st));
-            LP_CU(cudaMemsetAsync(hnused, 0, (size_t)bl[3] * sizeof(int32_t), st));
+            LP_CU(cudaMemsetAsync(hdone, 0, (size_t)bl[HUB_BUCKET] * sizeof(int32_t), st));
+            LP_CU(cudaMemsetAsync(hnused, 0, (size_t)bl[HUB_BUCKET] * sizeof(int32_t), st));
             LP_CU(cudaStreamSynchronize(st));
         }
         return LP_OK;
@@ -513,20 +530,22 @@ struct GraphSet {
             acc += tot[(size_t)c];
         }
         // hub tasks of each wave's part of the hub bucket (contiguous classes)
-        hitems_w.assign((size_t)waves, 0);
-        if (bl[3] > 0) {
-            if (!htask_w) LP_TRY(dev_alloc(&htask_w, bl[3], "hub tasks", st, device));
-            const int64_t hub0 = wstart[(size_t)3 * waves];
-            std::vector<int64_t> tots(2 * (size_t)waves, 0);
+        hmulti_w.assign((size_t)waves, 0);
+        hsegs_w.assign((size_t)waves, 0);
+        hparts_w.assign((size_t)waves, 0);
+        if (bl[HUB_BUCKET] > 0) {
+            if (!htask_w) LP_TRY(dev_alloc(&htask_w, bl[HUB_BUCKET], "hub tasks", st, device));
+            const int64_t hub0 = wstart[(size_t)HUB_BUCKET * waves];
+            std::vector<int64_t> tots(5 * (size_t)waves, 0);
             int64_t *d_tot = nullptr;
-            LP_TRY(dev_alloc(&d_tot, 2 * (int64_t)waves, "hub totals", st, device));
+            LP_TRY(dev_alloc(&d_tot, 5 * (int64_t)waves, "hub totals", st, device));
             Launches L2;
-            cudaError_t e2 = cudaSuccess;
+            cudaError_t e2 = cudaMemsetAsync(d_tot, 0, tots.size() * sizeof(int64_t), st);
             for (int k = 0; k < waves && e2 == cudaSuccess; ++k) {
-                const int64_t c = wcount[(size_t)3 * waves + k];
+                const int64_t c = wcount[(size_t)HUB_BUCKET * waves + k];
                 if (c == 0) continue;
-                const int64_t st0 = wstart[(size_t)3 * waves + k];
-                if (hub_tasks(wlist + st0, c, off, vgraph, htask_w + (st0 - hub0), d_tot + 2 * k,
+                const int64_t st0 = wstart[(size_t)HUB_BUCKET * waves + k];
+                if (hub_tasks(wlist + st0, c, off, vgraph, htask_w + (st0 - hub0), d_tot + 5 * k,
                               st, &L2.n) != 0)
                     e2 = cudaGetLastError();
             }
@@ -536,8 +555,11 @@ struct GraphSet {
             if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(st);
             cudaFreeAsync(d_tot, st);
             if (e2 != cudaSuccess) return fail(LP_ECUDA, cuda_msg("wave hub tasks", e2));
-            for (int k = 0; k < waves; ++k)
-                hitems_w[(size_t)k] = wcount[(size_t)3 * waves + k] ? tots[2 * (size_t)k] : 0;
+            for (int k = 0; k < waves; ++k) {
+                hmulti_w[(size_t)k] = tots[5 * (size_t)k];
+                hsegs_w[(size_t)k] = tots[5 * (size_t)k + 2];
+                hparts_w[(size_t)k] = tots[5 * (size_t)k + 3];
+            }
         }
         wl_waves = waves;
         return LP_OK;
@@ -645,8 +667,11 @@ struct GraphSet {
         a.hkey = hkey;
         a.hnpos = hnpos;
         a.hused = hused;
-        a.hdone = hdone;
         a.hnused = hnused;
+        a.hdone = hdone;
+        a.hrec = hrec;
+        a.hpoff = hpoff;
+        a.hpbest = hpbest;
         a.waves = (uint32_t)waves;
         a.wave_magic = fastmod_magic((uint32_t)waves);
         return LP_OK;
@@ -675,13 +700,17 @@ struct GraphSet {
                 a.list = list + bb[b];
                 a.len = bl[b];
                 a.htask = htask;
-                a.hitems = hitems;
+                a.hmulti = hmulti;
+                a.hsegs = hsegs;
+                a.hparts = hparts;
             } else {
                 a.list = wlist + wstart[(size_t)b * waves + k];
                 a.len = wcount[(size_t)b * waves + k];
-                if (b == 3) {
+                if (b == HUB_BUCKET) {
                     a.htask = htask_w + (wstart[(size_t)b * waves + k] - wstart[(size_t)b * waves]);
-                    a.hitems = hitems_w[(size_t)k];
+                    a.hmulti = hmulti_w[(size_t)k];
+                    a.hsegs = hsegs_w[(size_t)k];
+                    a.hparts = hparts_w[(size_t)k];
                 }
             }
             if (a.len == 0) continue;
@@ -689,6 +718,9 @@ struct GraphSet {
             // the first sweep from unique labels reads unique labels only in
             // its first wave (later waves see this sweep's new labels)
             a.identity = rows_distinct && it == 0 && !rs.p.init_labels && k == 0;
+            // labels read in the first sweep from unique labels rarely hold a
+            // majority of a row
+            a.majority = !(it == 0 && !rs.p.init_labels);
             if (rs.prof) {
                 while (prof_ev.size() < 2 * (rs.prof_launch.size() + 1)) {
                     cudaEvent_t e;
@@ -697,9 +729,9 @@ struct GraphSet {
                 }
                 LP_CU(cudaEventRecord(prof_ev[2 * rs.prof_launch.size()], st));
             }
-            if (sweep_launch(b, a, rs.multi, num_sms, st) != 0)
-                return fail(LP_ECUDA, cuda_msg("sweep launch", cudaGetLastError()));
-            ++L.n;
+            const int nk = sweep_launch(b, a, rs.multi, num_sms, st);
+            if (nk < 0) return fail(LP_ECUDA, cuda_msg("sweep launch", cudaGetLastError()));
+            L.n += nk;
             if (rs.prof) {
                 LP_CU(cudaEventRecord(prof_ev[2 * rs.prof_launch.size() + 1], st));
                 rs.prof_launch.push_back(b);
@@ -1243,8 +1275,8 @@ lp_status lp_profile_read(lp_kernel_stat *out, int32_t capacity, int32_t *count)
     if (!count) return fail(LP_EINVAL, "count is NULL");
     if (capacity > 0 && !out) return fail(LP_EINVAL, "out is NULL");
     std::lock_guard<std::mutex> lock(g_prof_mu);
-    *count = 4;
-    for (int i = 0; i < 4 && i < capacity; ++i) {
+    *count = lp::NUM_BUCKETS;
+    for (int i = 0; i < lp::NUM_BUCKETS && i < capacity; ++i) {
         memset(out[i].name, 0, sizeof out[i].name);
         strncpy(out[i].name, KERNEL_NAMES[i], sizeof out[i].name - 1);
         out[i].launches = g_prof[i].launches;

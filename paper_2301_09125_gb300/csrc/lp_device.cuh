@@ -96,13 +96,14 @@ __device__ __forceinline__ uint32_t block_max(uint32_t v, uint32_t *s_u)
     return s_u[NT / 32];
 }
 
-// insert (l, s, first position p) into an open-addressing table of 2^lg slots,
-// probing at most `limit` slots; false if the window is full of other labels
-__device__ __forceinline__ bool table_add(int32_t *key, int32_t *sum, uint32_t *npos, int lg,
-                                          int limit, int32_t l, int s, uint32_t p)
+// insert (l, s, first position p) into an open-addressing table of mask + 1
+// slots, starting at slot h and probing at most `limit` slots; false if that
+// window is full of other labels.  The table may be another CTA's shared
+// memory in the cluster (generic addresses).
+__device__ __forceinline__ bool table_add_at(int32_t *key, int32_t *sum, uint32_t *npos,
+                                             uint32_t mask, uint32_t h, int limit, int32_t l,
+                                             int s, uint32_t p)
 {
-    const uint32_t mask = (1u << lg) - 1u;
-    uint32_t h = slot_hash(l, lg);
     volatile int32_t *vk = key;
     for (int i = 0; i < limit; ++i) {
         int32_t cur = vk[h];
@@ -118,6 +119,13 @@ __device__ __forceinline__ bool table_add(int32_t *key, int32_t *sum, uint32_t *
         h = (h + 1) & mask;
     }
     return false;
+}
+
+// the same for a table of 2^lg slots, starting at the label's hash slot
+__device__ __forceinline__ bool table_add(int32_t *key, int32_t *sum, uint32_t *npos, int lg,
+                                          int limit, int32_t l, int s, uint32_t p)
+{
+    return table_add_at(key, sum, npos, (1u << lg) - 1u, slot_hash(l, lg), limit, l, s, p);
 }
 
 }  // namespace

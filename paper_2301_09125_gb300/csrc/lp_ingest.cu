@@ -104,7 +104,7 @@ __global__ void k_check_row_order(const int32_t *idx, int64_t ne, const uint32_t
 
 __device__ __forceinline__ int bucket_of(int32_t d)
 {
-    return d <= 0 ? -1 : d <= SMALL_MAX ? 0 : d <= WARP_MAX ? 1 : d <= CTA_MAX ? 2 : 3;
+    return d <= 0 ? -1 : d <= SMALL_MAX ? 0 : d <= WARP_MAX ? 1 : d <= CTA_MAX ? 2 : d <= CTA2_MAX ? 3 : 4;
 }
 
 // graph g's row pointer entries start at off[vbase_g + g], so global vertex v
@@ -257,12 +257,22 @@ __global__ void k_merge_final(int32_t *lab0, const int32_t *lab1, int32_t nv,
 }
 
 // one block: hub tasks with exclusive prefixes of segments and table slots
-__global__ void __launch_bounds__(1024) k_hub_tasks(const int32_t *list, int64_t len,
+__global__ void __launch_bounds__(1024) k_hub_tasks(int32_t *list, int64_t len,
                                                      const int32_t *off, const int32_t *vgraph,
                                                      HubTask *tasks, int64_t *totals)
 {
     __shared__ int64_t s_warp[33];
-    int64_t seg_run = 0, tab_run = 0;
+    // rows longer than HUB_ONE_MAX
+    int64_t nbig = 0;
+    for (int64_t i0 = 0; i0 < len; i0 += 1024) {
+        const int64_t i = i0 + threadIdx.x;
+        const int64_t big = i < len && degree_of(off, vgraph, list[i]) > HUB_ONE_MAX;
+        int64_t tot;
+        block_exclusive_scan(big, s_warp, &tot);
+        nbig += tot;
+    }
+    // stable partition into tasks; segments, partitions and tables of long rows
+    int64_t big_run = 0, small_run = nbig, tab_run = 0, seg_run = 0, part_run = 0, poff_run = 0;
     for (int64_t i0 = 0; i0 < len; i0 += 1024) {
         const int64_t i = i0 + threadIdx.x;
         int32_t v = 0, d = 0;
@@ -270,30 +280,49 @@ __global__ void __launch_bounds__(1024) k_hub_tasks(const int32_t *list, int64_t
             v = list[i];
             d = degree_of(off, vgraph, v);
         }
-        const int64_t nseg = i < len ? (d + HUB_SEG - 1) / HUB_SEG : 0;
-        int64_t tsz = 0;
-        if (nseg > 1) {
+        const int64_t big = i < len && d > HUB_ONE_MAX;
+        const int64_t small = i < len && !big;
+        int64_t tsz = 0, nseg = 0, npart = 0;
+        if (big) {
             tsz = 1;
             while (tsz < 2 * (int64_t)d) tsz <<= 1;
+            nseg = ((int64_t)d + HUB_SEG - 1) / HUB_SEG;
+            npart = nseg < HUB_PMAX ? nseg : HUB_PMAX;
         }
-        int64_t tot_seg, tot_tab;
-        const int64_t ex_seg = block_exclusive_scan(nseg, s_warp, &tot_seg);
-        const int64_t ex_tab = block_exclusive_scan(tsz, s_warp, &tot_tab);
+        int64_t t_big, t_small, t_tab, t_seg, t_part, t_poff;
+        const int64_t ex_big = block_exclusive_scan(big, s_warp, &t_big);
+        const int64_t ex_small = block_exclusive_scan(small, s_warp, &t_small);
+        const int64_t ex_tab = block_exclusive_scan(tsz, s_warp, &t_tab);
+        const int64_t ex_seg = block_exclusive_scan(nseg, s_warp, &t_seg);
+        const int64_t ex_part = block_exclusive_scan(npart, s_warp, &t_part);
+        const int64_t ex_poff = block_exclusive_scan(nseg * (npart + 1), s_warp, &t_poff);
         if (i < len) {
             HubTask t;
             t.v = v;
+            t.d = d;
             t.nseg = (int32_t)nseg;
-            t.first = (int32_t)(seg_run + ex_seg);
-            t.pad = 0;
-            t.tab = tab_run + ex_tab;
-            tasks[i] = t;
+            t.npart = (int32_t)npart;
+            t.seg0 = big ? (int32_t)(seg_run + ex_seg) : 0;
+            t.part0 = big ? (int32_t)(part_run + ex_part) : 0;
+            t.poff0 = big ? poff_run + ex_poff : 0;
+            t.tab = big ? tab_run + ex_tab : 0;
+            tasks[big ? big_run + ex_big : small_run + ex_small] = t;
         }
-        seg_run += tot_seg;
-        tab_run += tot_tab;
+        big_run += t_big;
+        small_run += t_small;
+        tab_run += t_tab;
+        seg_run += t_seg;
+        part_run += t_part;
+        poff_run += t_poff;
     }
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < len; i += 1024) list[i] = tasks[i].v;
     if (threadIdx.x == 0) {
-        totals[0] = seg_run;
+        totals[0] = nbig;
         totals[1] = tab_run;
+        totals[2] = seg_run;
+        totals[3] = part_run;
+        totals[4] = poff_run;
     }
 }
 
@@ -495,7 +524,7 @@ int wave_prepare()
     return 0;
 }
 
-int hub_tasks(const int32_t *list, int64_t len, const int32_t *off, const int32_t *vgraph,
+int hub_tasks(int32_t *list, int64_t len, const int32_t *off, const int32_t *vgraph,
               HubTask *tasks, int64_t *totals, cudaStream_t st, int64_t *launches)
 {
     k_hub_tasks<<<1, 1024, 0, st>>>(list, len, off, vgraph, tasks, totals);

@@ -9,7 +9,7 @@
 //   lab  int32  two label buffers of NV entries (vertex v of graph g at
 //               vbase_g + v); labels are local vertex ids
 //   list int32  global vertex ids sorted into degree buckets
-//               [small | warp | cta | hub], ascending id inside a bucket
+//               [small | warp | cta | cta2 | hub], ascending id inside a bucket
 //               except hub, which is sorted by degree, largest first
 #pragma once
 
@@ -25,28 +25,41 @@ constexpr int32_t EMPTY = -1;
 // thread / warp / CTA granularity).
 constexpr int SMALL_MAX = 32;   // 1..32: several vertices packed per warp
 constexpr int WARP_MAX = 128;   // 33..128: one warp per vertex
-constexpr int CTA_MAX = 1024;   // 129..1024: one 256-thread CTA per vertex
-                                // > 1024: one 512-thread CTA + overflow table
-constexpr int NUM_BUCKETS = 4;  // small, warp, cta, hub
+constexpr int CTA_MAX = 512;    // 129..512: one 128-thread CTA per vertex
+constexpr int CTA2_MAX = 1024;  // 513..1024: one 256-thread CTA per vertex
+                                // > 1024: hub
+constexpr int NUM_BUCKETS = 5;  // small, warp, cta, cta2, hub
+constexpr int HUB_BUCKET = NUM_BUCKETS - 1;
 
 constexpr int WARP_TABLE = 256;         // slots per warp (>= 2 * WARP_MAX)
-constexpr int CTA_THREADS = 256;
-constexpr int CTA_TABLE = 2048;         // slots (>= 2 * CTA_MAX)
+constexpr int CTA_THREADS = 128;
+constexpr int CTA_TABLE = 1024;         // slots (>= 2 * CTA_MAX)
+constexpr int CTA2_THREADS = 256;
+constexpr int CTA2_TABLE = 2048;        // slots (>= 2 * CTA2_MAX)
 constexpr int HUB_THREADS = 512;
-constexpr int HUB_TABLE = 8192;         // shared slots (>= 2 * HUB_SEG)
-constexpr int HUB_SEG = 4096;           // entries of a hub row per work item
+constexpr int HUB_TABLE = 8192;         // shared slots per hub CTA (>= 2 * HUB_ONE_MAX)
+constexpr int HUB_ONE_MAX = 4096;       // longest hub row swept by one CTA
+constexpr int HUB_SEG = 4096;           // entries per segment of a longer row
+constexpr int HUB_PMAX = 2048;          // most label partitions of one row
 
 // One hub of a list being swept (the hub bucket, or its part in one wave),
-// prepared once per list.  Its row is cut into `nseg` segments of HUB_SEG
-// entries; items first .. first + nseg - 1 of the launch are its segments.
-// A hub of more than one segment owns a global table of 2^ceil(log2(2d))
-// slots starting at slot `tab`, and a used-slot list starting at tab / 2.
+// prepared once per list.  Rows longer than HUB_ONE_MAX come first.  Such a
+// row is cut into nseg segments of HUB_SEG entries; each segment aggregates
+// its labels in shared memory and writes them out as records grouped into
+// npart partitions by label hash, then one CTA per partition merges the
+// records of all segments, and the last one to finish picks the row's label.
+// A label that finds no room in a partition's shared table goes to the row's
+// global fallback table of 2^ceil(log2(2d)) slots starting at slot `tab`
+// (used-slot list at tab / 2).
 struct HubTask {
-    int32_t v;      // global vertex
-    int32_t nseg;   // segments of its row
-    int32_t first;  // items of the earlier hubs of the list
-    int32_t pad;
-    int64_t tab;    // first slot of its global table
+    int32_t v;       // global vertex
+    int32_t d;       // degree
+    int32_t nseg;    // segments (rows longer than HUB_ONE_MAX)
+    int32_t npart;   // label partitions
+    int32_t seg0;    // first segment item of the row in this list
+    int32_t part0;   // first partition item of the row in this list
+    int64_t poff0;   // first entry of its partition offsets (nseg x (npart + 1))
+    int64_t tab;     // first slot of its fallback table
 };
 
 // Arguments of one sweep kernel launch (one bucket).
@@ -70,18 +83,31 @@ struct SweepArgs {
     // 1 when every label this launch reads is the initial unique label and no
     // row repeats a neighbour: a label's weight is then its one edge weight
     int identity;
+    // 1 when a vertex whose own label holds more than half of its row's weight
+    // may keep it without a table (that label is then the unique maximum);
+    // set where labels have settled enough for the test to pay off
+    int majority;
     // asynchronous waves (Sec. 3.3): this launch runs wave `wave_k` of `waves`;
     // a neighbour u of an earlier wave (u mod waves < wave_k) is read from
     // lab_out (this iteration), every other one from lab_in.  waves = 1: sync.
     uint32_t waves;
     uint32_t wave_k;
     uint64_t wave_magic;     // fastmod constant of `waves`
-    // hub launches: the list's tasks, the total of its items (segments), the
-    // global tables (slot = (label + 1) << 32 | summed weight, 0 when free,
-    // plus ~first position), used-slot lists, and per-task counters of
-    // finished segments and used slots (zero between launches)
+    // hub launches: the list's tasks (aligned with `list`), how many of them
+    // are rows longer than HUB_ONE_MAX, with their segment and partition item
+    // counts; segment records (HUB_SEG int4 per segment item: label, sum,
+    // ~first position), partition offsets, partition bests (32 bytes per
+    // partition item); fallback tables (slot = (label + 1) << 32 | summed
+    // weight, 0 when free, plus ~first position), used-slot lists and
+    // per-task counters of finished partitions and used slots (zero between
+    // launches)
     const HubTask *htask;
-    int64_t hitems;
+    int64_t hmulti;
+    int64_t hsegs;
+    int64_t hparts;
+    int4 *hrec;
+    int32_t *hpoff;
+    void *hpbest;
     unsigned long long *hkey;
     uint32_t *hnpos;
     int32_t *hused;
@@ -141,11 +167,14 @@ __host__ __device__ __forceinline__ uint64_t stream_at(uint64_t key, uint64_t k)
 // Launchers (lp_sweep.cu, lp_ingest.cu, lp_modularity.cu)
 // ----------------------------------------------------------------------------
 int sweep_prepare();  // per-device kernel attributes; call with the device current
-// launch the sweep kernel of one degree bucket (0 small, 1 warp, 2 cta, 3 hub)
+// launch the sweep kernel(s) of one degree bucket (0 small, 1 warp, 2 cta,
+// 3 cta2, 4 hub); returns the number of kernels launched, or -1
 int sweep_launch(int bucket, const SweepArgs &a, bool multi, int num_sms, cudaStream_t st);
-// Hub tasks of list[0..len): tasks[i] for each entry, totals[0] = items,
-// totals[1] = global table slots.
-int hub_tasks(const int32_t *list, int64_t len, const int32_t *off, const int32_t *vgraph,
+// Hub tasks of list[0..len): the rows longer than HUB_ONE_MAX first, then the
+// others, each kind in list order; list is rewritten in the same order so that
+// tasks[i] belongs to list[i].  totals: [0] rows of the first kind, [1] their
+// fallback table slots, [2] segments, [3] partitions, [4] partition offsets.
+int hub_tasks(int32_t *list, int64_t len, const int32_t *off, const int32_t *vgraph,
               HubTask *tasks, int64_t *totals, cudaStream_t st, int64_t *launches);
 
 struct IngestOut {
@@ -180,8 +209,9 @@ int ingest_check_wdeg(const int32_t *off, const int32_t *wts, int32_t n, IngestO
                       cudaStream_t st, int64_t *launches);
 int degrees_of(const int32_t *off, const int32_t *vgraph, const int32_t *list, int64_t len,
                int32_t *deg, cudaStream_t st, int64_t *launches);
-// Bucket every vertex of a graph set.  d_counts[0..4) receives the bucket
-// lengths, [4..8) their starts in `list`, [8..12) their summed degrees.
+// Bucket every vertex of a graph set.  d_counts[0..B) receives the bucket
+// lengths, [B..2B) their starts in `list`, [2B..3B) their summed degrees
+// (B = NUM_BUCKETS).
 int ingest_bucket(const int32_t *off, int32_t nv_total, const int32_t *vgraph,
                   const int32_t *g_vbase, int32_t *list, int32_t *scratch_blocks,
                   int64_t *d_counts, cudaStream_t st, int64_t *launches);

@@ -281,7 +281,8 @@ int modularity_launch(const ModArgs &base, const int64_t *bucket_begin, const in
         else k_mod_rows<32, false><<<g, 256, 0, st>>>(a);
         ++*launches;
     }
-    const int64_t big = bucket_len[2] + bucket_len[3];  // cta and hub buckets are adjacent
+    // the cta, cta2 and hub buckets are adjacent
+    const int64_t big = bucket_len[2] + bucket_len[3] + bucket_len[4];
     if (big > 0) {
         a.list = base.list + bucket_begin[2];
         a.len = big;

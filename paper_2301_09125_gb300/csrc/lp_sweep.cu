@@ -11,13 +11,15 @@
 //   warp   33..128   k_warp  : one warp per vertex, a 256-slot open-addressing
 //                              table per warp in shared memory; duplicate labels
 //                              of a 32-entry chunk are merged before insertion.
-//   cta    129..1024 k_cta   : one 256-thread CTA per vertex, 2048-slot table.
-//   hub    > 1024    k_hub   : work items are 4096-entry segments of hub rows,
-//                              512 threads each, aggregated in an 8192-slot
-//                              shared table; a row of one segment is finished
-//                              there, longer rows flush each segment into the
-//                              hub's global table and the CTA finishing the
-//                              last segment takes the argmax of the used slots.
+//   cta    129..512  k_cta   : one 128-thread CTA per vertex, 1024-slot table.
+//   cta2   513..1024 k_cta   : one 256-thread CTA per vertex, 2048-slot table.
+//   hub    1025..4096 k_cta  : one 512-thread CTA per vertex, 8192-slot table.
+//   hub    > 4096    k_hub_seg + k_hub_merge : the row is cut into 4096-entry
+//                              segments; each segment aggregates its labels in
+//                              a shared table and writes them out as records
+//                              grouped into label partitions, then one CTA per
+//                              partition merges the records of every segment
+//                              and the last one of the row picks its label.
 // Every table slot holds (label, summed weight, ~first position); the first
 // position of a label is the smallest row position at which it occurs, so the
 // argmax key (weight desc, [non-strict key asc,] first position asc) is unique
@@ -254,6 +256,44 @@ __device__ __forceinline__ Quad load_quad(const SweepArgs &a, int64_t blk, int64
     return q;
 }
 
+// Per-warp fast path for a row's dominant label.  Once labels have settled
+// most entries of a row carry the same label, and inserting it once per warp
+// round would serialise many atomics on one table slot.  The warp picks the
+// label of its first entry as its hot label; entries carrying it are summed
+// in registers (with their first position) and inserted once at the end.
+struct HotLabel {
+    int32_t label = EMPTY;       // warp-uniform
+    int sum = 0;                 // lane-local
+    uint32_t pos = 0xFFFFFFFFu;  // lane-local first position
+    __device__ __forceinline__ void pick(const Quad &q)
+    {
+        if (label != EMPTY) return;
+        const unsigned m = __ballot_sync(FULL, q.l[0] != EMPTY);
+        if (m) label = __shfl_sync(FULL, q.l[0], __ffs(m) - 1);
+    }
+    // true if the entry was absorbed
+    __device__ __forceinline__ bool take(int32_t l, int w, uint32_t p)
+    {
+        if (l == EMPTY || l != label) return false;
+        sum += w;
+        pos = min(pos, p);
+        return true;
+    }
+    // warp totals, valid in every lane
+    __device__ __forceinline__ int total() const { return __reduce_add_sync(FULL, sum); }
+    __device__ __forceinline__ uint32_t first() const { return __reduce_min_sync(FULL, pos); }
+};
+
+// Summed weight of the entries of q carrying label `own`, and of all of them.
+__device__ __forceinline__ void own_weight(const Quad &q, int32_t own, uint32_t &ow, uint32_t &tw)
+{
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        tw += (uint32_t)q.w[j];
+        ow += q.l[j] == own ? (uint32_t)q.w[j] : 0u;
+    }
+}
+
 // Identity sweep: the labels read are the initial unique labels (label of u
 // is u) and no row repeats a neighbour, so a label's summed weight is its one
 // edge weight and its first position is that entry's.  The adopted label is
@@ -325,7 +365,7 @@ constexpr int WARP_LG = 8;  // log2(WARP_TABLE)
 static_assert((1 << WARP_LG) == WARP_TABLE, "warp table size");
 
 template <bool MULTI>
-__global__ void __launch_bounds__(256) k_warp(SweepArgs a)
+__global__ void __launch_bounds__(256, MULTI ? 4 : 5) k_warp(SweepArgs a)
 {
     __shared__ int32_t s_key[8 * WARP_TABLE];
     __shared__ int32_t s_sum[8 * WARP_TABLE];
@@ -372,35 +412,64 @@ __global__ void __launch_bounds__(256) k_warp(SweepArgs a)
             }
             continue;
         }
-        for (int64_t base = lo >> 2; base <= b_hi; base += 32) {
+        // a row of at most 32 quads is loaded once, one quad per lane; if the
+        // vertex's own label holds more than half of its weight it stays
+        const int64_t b0 = lo >> 2;
+        const bool one = b_hi - b0 < 32;
+        Quad q1 = empty_quad();
+        if (one) {
+            if (b0 + lane <= b_hi) q1 = load_quad(a, b0 + lane, lo, hi, x.vb);
+            if (a.majority) {
+                uint32_t ow = 0, tw = 0;
+                own_weight(q1, own, ow, tw);
+                ow = __reduce_add_sync(FULL, ow);
+                tw = __reduce_add_sync(FULL, tw);
+                if (2ull * ow > (unsigned long long)tw) {
+                    if (lane == 0) a.lab_out[x.v] = own;
+                    continue;
+                }
+            }
+        }
+        // one writer per label at a time, so plain updates suffice
+        auto insert = [&](int32_t l, int s, uint32_t pos) {
+            const uint32_t np = 0xFFFFFFFFu - pos;
+            uint32_t h = slot_hash(l, WARP_LG);
+            for (int probe = 0; probe < WARP_TABLE; ++probe) {  // <= 128 labels: found
+                int32_t cur = tk[h];
+                if (cur == EMPTY) {
+                    cur = atomicCAS(tk_atomic + h, EMPTY, l);
+                    if (cur == EMPTY) cur = l;
+                }
+                if (cur == l) {
+                    ts[h] = ts[h] + s;
+                    if (np > tp[h]) tp[h] = np;
+                    break;
+                }
+                h = (h + 1) & (WARP_TABLE - 1);
+            }
+        };
+        HotLabel hot;
+        for (int64_t base = b0; base <= b_hi; base += 32) {
             const int64_t blk = base + lane;
-            const Quad q = blk <= b_hi ? load_quad(a, blk, lo, hi, x.vb) : empty_quad();
+            const Quad q = one ? q1 : (blk <= b_hi ? load_quad(a, blk, lo, hi, x.vb) : empty_quad());
+            hot.pick(q);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const int32_t l = q.l[j];
+                const uint32_t pos = (uint32_t)(blk * 4 + j - lo);
+                const int32_t l = hot.take(q.l[j], q.w[j], pos) ? EMPTY : q.l[j];
                 const unsigned grp = __match_any_sync(FULL, (unsigned)l);
                 const int s = __reduce_add_sync(grp, q.w[j]);
-                if (l != EMPTY && lane == __ffs(grp) - 1) {
-                    // one leader per label in this round, so plain updates suffice;
-                    // the leader (lowest lane) holds the round's first position
-                    const uint32_t np = 0xFFFFFFFFu - (uint32_t)(blk * 4 + j - lo);
-                    uint32_t h = slot_hash(l, WARP_LG);
-                    for (int probe = 0; probe < WARP_TABLE; ++probe) {  // <= 128 labels: found
-                        int32_t cur = tk[h];
-                        if (cur == EMPTY) {
-                            cur = atomicCAS(tk_atomic + h, EMPTY, l);
-                            if (cur == EMPTY) cur = l;
-                        }
-                        if (cur == l) {
-                            ts[h] = ts[h] + s;
-                            if (np > tp[h]) tp[h] = np;
-                            break;
-                        }
-                        h = (h + 1) & (WARP_TABLE - 1);
-                    }
-                }
+                // one leader per label in this round; the leader (lowest lane)
+                // holds the round's first position
+                if (l != EMPTY && lane == __ffs(grp) - 1) insert(l, s, pos);
                 __syncwarp();
             }
+        }
+        {
+            const int hs = hot.total();
+            const uint32_t hp = hot.first();
+            if (lane == 0 && hs > 0) insert(hot.label, hs, hp);
+            __syncwarp();
         }
 
         Cand best{0u, 0u, 0ull, EMPTY};
@@ -480,6 +549,35 @@ __device__ __forceinline__ Cand scan_table(int32_t *tk, int32_t *ts, uint32_t *t
     return best;
 }
 
+// Insert one quad (entries 4*blk .. 4*blk+3 of a row starting at global
+// entry `row`) into a shared table of 2^lg slots: the warp's hot label is
+// summed in registers, equal labels of the warp are merged with match / redux
+// before one insert per label.
+__device__ __forceinline__ void insert_quad(const Quad &q, int64_t blk, int64_t row,
+                                            HotLabel &hot, int32_t *tk, int32_t *ts,
+                                            uint32_t *tp, int lg)
+{
+    hot.pick(q);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const uint32_t pos = (uint32_t)(blk * 4 + j - row);
+        const int32_t l = hot.take(q.l[j], q.w[j], pos) ? EMPTY : q.l[j];
+        const unsigned grp = __match_any_sync(FULL, (unsigned)l);
+        const int s = __reduce_add_sync(grp, q.w[j]);
+        if (l != EMPTY && (threadIdx.x & 31) == __ffs(grp) - 1)
+            table_add(tk, ts, tp, lg, 1 << lg, l, s, pos);
+    }
+}
+
+// the warp's hot label total, inserted once
+__device__ __forceinline__ void insert_hot(const HotLabel &hot, int32_t *tk, int32_t *ts,
+                                           uint32_t *tp, int lg)
+{
+    const int hs = hot.total();
+    const uint32_t hp = hot.first();
+    if ((threadIdx.x & 31) == 0 && hs > 0) table_add(tk, ts, tp, lg, 1 << lg, hot.label, hs, hp);
+}
+
 // Aggregate the entries [lo, hi) of a row starting at global entry `row` into
 // the shared table of 2^lg slots (which must have room for every distinct
 // label of the range), all NT threads cooperating.
@@ -489,25 +587,42 @@ __device__ __forceinline__ void accumulate_range(const SweepArgs &a, int64_t row
                                                  uint32_t *tp, int lg)
 {
     const int64_t b_hi = (hi - 1) >> 2;
+    HotLabel hot;
     for (int64_t base = lo >> 2; base <= b_hi; base += NT) {
         const int64_t blk = base + threadIdx.x;
         const Quad q = blk <= b_hi ? load_quad(a, blk, lo, hi, vb) : empty_quad();
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int32_t l = q.l[j];
-            const unsigned grp = __match_any_sync(FULL, (unsigned)l);
-            const int s = __reduce_add_sync(grp, q.w[j]);
-            if (l != EMPTY && (threadIdx.x & 31) == __ffs(grp) - 1)
-                table_add(tk, ts, tp, lg, 1 << lg, l, s, (uint32_t)(blk * 4 + j - row));
-        }
+        insert_quad(q, blk, row, hot, tk, ts, tp, lg);
     }
+    insert_hot(hot, tk, ts, tp, lg);
+}
+
+// Block sums of x and y, valid in every thread (s: 2 * NT / 32 words).
+template <int NT>
+__device__ __forceinline__ uint2 block_sum2(uint32_t x, uint32_t y, uint32_t *s)
+{
+    x = __reduce_add_sync(FULL, x);
+    y = __reduce_add_sync(FULL, y);
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    if (lane == 0) {
+        s[wib] = x;
+        s[NT / 32 + wib] = y;
+    }
+    __syncthreads();
+    uint2 r{0u, 0u};
+#pragma unroll
+    for (int k = 0; k < NT / 32; ++k) {
+        r.x += s[k];
+        r.y += s[NT / 32 + k];
+    }
+    __syncthreads();
+    return r;
 }
 
 // ----------------------------------------------------------------------------
 // cta bucket: one CTA per vertex, shared table
 // ----------------------------------------------------------------------------
 template <int NT, int CAP, bool MULTI>
-__global__ void __launch_bounds__(NT) k_cta(SweepArgs a)
+__global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 2048 / NT) k_cta(SweepArgs a)
 {
     extern __shared__ int32_t smem[];
     int32_t *tk = smem;
@@ -515,8 +630,11 @@ __global__ void __launch_bounds__(NT) k_cta(SweepArgs a)
     uint32_t *tp = reinterpret_cast<uint32_t *>(ts + CAP);
     __shared__ Cand s_red[NT / 32];
     __shared__ uint32_t s_u[NT / 32 + 1];
-    constexpr int LG = (CAP == 2048) ? 11 : (CAP == 4096) ? 12 : (CAP == 8192) ? 13 : 14;
+    __shared__ uint32_t s_u2[2 * (NT / 32)];
+    constexpr int LG = (CAP == 1024) ? 10 : (CAP == 2048) ? 11 : (CAP == 4096) ? 12 : (CAP == 8192) ? 13 : 14;
     static_assert((1 << LG) == CAP, "table size");
+    // quads per thread that hold a row of CAP / 2 entries starting 16-byte aligned
+    constexpr int R = CAP / 2 / (4 * NT) > 0 ? CAP / 2 / (4 * NT) : 1;
 
     for (int j = threadIdx.x; j < CAP; j += NT) {
         tk[j] = EMPTY;
@@ -536,15 +654,46 @@ __global__ void __launch_bounds__(NT) k_cta(SweepArgs a)
         // slots in use for this vertex: 2^lg >= 2d (d <= CAP / 2 in this bucket)
         const int lg = min(ilog2_ceil(2u * (uint32_t)x.d), LG);
         const uint64_t ktv = stream_at(a.key_t, (uint64_t)x.lv + 1);
-        Cand local;
+        const int64_t end = x.e0 + x.d;
+        const int64_t b0 = x.e0 >> 2, b_hi = (end - 1) >> 2;
+        Cand best{0u, 0u, 0ull, x.own};
         if (a.identity) {
-            local = identity_best<NT>(a, x.e0, x.e0, x.e0 + x.d, ktv, threadIdx.x);
+            best = block_argmax<NT>(identity_best<NT>(a, x.e0, x.e0, end, ktv, threadIdx.x),
+                                    a.strict, s_red);
+        } else if (b_hi - b0 < (int64_t)R * NT) {
+            // the row in registers, R quads per thread
+            Quad q[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int64_t blk = b0 + r * NT + threadIdx.x;
+                q[r] = blk <= b_hi ? load_quad(a, blk, x.e0, end, x.vb) : empty_quad();
+            }
+            // a label holding more than half of the row's weight is the
+            // unique maximum: the vertex keeps its own label if it does
+            bool settled = false;
+            if (a.majority) {
+                uint32_t ow = 0, tw = 0;
+#pragma unroll
+                for (int r = 0; r < R; ++r) own_weight(q[r], x.own, ow, tw);
+                const uint2 s2 = block_sum2<NT>(ow, tw, s_u2);
+                settled = 2ull * s2.x > (unsigned long long)s2.y;
+            }
+            if (!settled) {
+                HotLabel hot;
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    insert_quad(q[r], b0 + r * NT + threadIdx.x, x.e0, hot, tk, ts, tp, lg);
+                insert_hot(hot, tk, ts, tp, lg);
+                __syncthreads();
+                best = block_argmax<NT>(scan_table<NT>(tk, ts, tp, 1 << lg, a.strict, ktv, s_u),
+                                        a.strict, s_red);
+            }
         } else {
-            accumulate_range<NT>(a, x.e0, x.e0, x.e0 + x.d, x.vb, tk, ts, tp, lg);
+            accumulate_range<NT>(a, x.e0, x.e0, end, x.vb, tk, ts, tp, lg);
             __syncthreads();
-            local = scan_table<NT>(tk, ts, tp, 1 << lg, a.strict, ktv, s_u);
+            best = block_argmax<NT>(scan_table<NT>(tk, ts, tp, 1 << lg, a.strict, ktv, s_u),
+                                    a.strict, s_red);
         }
-        const Cand best = block_argmax<NT>(local, a.strict, s_red);
         if (threadIdx.x == 0) {
             a.lab_out[x.v] = best.label;
             if (best.label != x.own) {
@@ -560,10 +709,10 @@ __global__ void __launch_bounds__(NT) k_cta(SweepArgs a)
 }
 
 // ----------------------------------------------------------------------------
-// hub bucket: work items are 4096-entry segments of hub rows
+// hub bucket, rows longer than HUB_ONE_MAX: segments, then label partitions
 // ----------------------------------------------------------------------------
 
-// Add (l, s, ~first position) to a hub's global table of 2^glg slots.
+// Add (l, s, ~first position) to a row's fallback table of 2^glg global slots.
 // Returns the slot when this call claimed it, -1 otherwise.
 __device__ __forceinline__ int64_t global_add(unsigned long long *gk, uint32_t *gp, int glg,
                                               int32_t l, uint32_t s, uint32_t np)
@@ -587,8 +736,87 @@ __device__ __forceinline__ int64_t global_add(unsigned long long *gk, uint32_t *
     return -1;  // unreachable: the table holds at least 2d slots
 }
 
+// Partition of label l among np: the 32-bit finaliser of MurmurHash3
+// (Appleby) and a multiply-shift range reduction, independent of slot_hash.
+__device__ __forceinline__ uint32_t part_of(int32_t l, uint32_t np)
+{
+    uint32_t h = (uint32_t)l;
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    h *= 0xC2B2AE35u;
+    h ^= h >> 16;
+    return (uint32_t)(((uint64_t)h * np) >> 32);
+}
+
+// Index of the task owning work item `item`: the last task i in [0, n) whose
+// first item first(i) is <= item.
+template <typename F>
+__device__ __forceinline__ int64_t find_task(int64_t n, int64_t item, F first)
+{
+    int64_t lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (first(mid) <= item)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// In-place exclusive scan of c[0..n) (n <= HUB_PMAX) by NT threads; c[n]
+// receives the total.
+template <int NT>
+__device__ __forceinline__ void block_scan_counts(int32_t *c, int n, int32_t *s_w)
+{
+    constexpr int PER = (HUB_PMAX + NT - 1) / NT;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    int v[PER];
+    int sum = 0;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int q = t * PER + k;
+        v[k] = q < n ? c[q] : 0;
+        sum += v[k];
+    }
+    int inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) s_w[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        const int x = lane < NT / 32 ? s_w[lane] : 0;
+        int xi = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, xi, o);
+            if (lane >= o) xi += y;
+        }
+        if (lane < NT / 32) s_w[lane] = xi - x;
+        if (lane == 31) s_w[NT / 32] = xi;
+    }
+    __syncthreads();
+    int run = s_w[w] + inc - sum;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int q = t * PER + k;
+        if (q < n) c[q] = run;
+        run += v[k];
+    }
+    if (t == 0) c[n] = s_w[NT / 32];
+    __syncthreads();
+}
+
+// Segment pass: a segment's entries are aggregated in the shared table and
+// written out as (label, sum, ~first position) records grouped by partition,
+// with the partition offsets.  In an identity sweep the segment's own winner
+// is its only record.
 template <bool MULTI>
-__global__ void __launch_bounds__(HUB_THREADS, 2) k_hub(SweepArgs a)
+__global__ void __launch_bounds__(HUB_THREADS, 2) k_hub_seg(SweepArgs a)
 {
     constexpr int NT = HUB_THREADS;
     constexpr int LG = 13;
@@ -598,9 +826,86 @@ __global__ void __launch_bounds__(HUB_THREADS, 2) k_hub(SweepArgs a)
     int32_t *ts = tk + HUB_TABLE;
     uint32_t *tp = reinterpret_cast<uint32_t *>(ts + HUB_TABLE);
     __shared__ Cand s_red[NT / 32];
+    __shared__ int32_t s_cnt[HUB_PMAX + 1];
+    __shared__ int32_t s_w[NT / 32 + 1];
+
+    for (int j = threadIdx.x; j < HUB_TABLE; j += NT) {
+        tk[j] = EMPTY;
+        ts[j] = 0;
+        tp[j] = 0;
+    }
+    __syncthreads();
+    for (int64_t item = blockIdx.x; item < a.hsegs; item += gridDim.x) {
+        const int64_t ti = find_task(a.hmulti, item, [&](int64_t i) {
+            return (int64_t)__ldg(&a.htask[i].seg0);
+        });
+        const HubTask t = a.htask[ti];
+        Vtx x;
+        if (!load_vtx<MULTI>(a, t.v, x)) continue;  // block-uniform
+        const int seg = (int)(item - t.seg0);
+        const int64_t lo = x.e0 + (int64_t)seg * HUB_SEG;
+        const int64_t hi = min(lo + HUB_SEG, x.e0 + x.d);
+        const int np = t.npart;
+        int4 *out = a.hrec + item * HUB_SEG;
+        int32_t *poff = a.hpoff + t.poff0 + (int64_t)seg * (np + 1);
+        if (a.identity) {
+            const uint64_t ktv = stream_at(a.key_t, (uint64_t)x.lv + 1);
+            const Cand best = block_argmax<NT>(identity_best<NT>(a, x.e0, lo, hi, ktv, threadIdx.x),
+                                               a.strict, s_red);
+            if (threadIdx.x == 0) {
+                s_cnt[0] = best.sum > 0 ? (int)part_of(best.label, (uint32_t)np) : -1;
+                out[0] = make_int4(best.label, (int)best.sum, (int)best.npos, 0);
+            }
+            __syncthreads();
+            const int bp = s_cnt[0];
+            for (int q = threadIdx.x; q <= np; q += NT) poff[q] = (bp >= 0 && q > bp) ? 1 : 0;
+            __syncthreads();
+            continue;
+        }
+        accumulate_range<NT>(a, x.e0, lo, hi, x.vb, tk, ts, tp, LG);
+        for (int q = threadIdx.x; q < np; q += NT) s_cnt[q] = 0;
+        __syncthreads();
+        for (int j = threadIdx.x; j < HUB_TABLE; j += NT)
+            if (tk[j] != EMPTY) atomicAdd(&s_cnt[part_of(tk[j], (uint32_t)np)], 1);
+        __syncthreads();
+        block_scan_counts<NT>(s_cnt, np, s_w);
+        for (int q = threadIdx.x; q <= np; q += NT) poff[q] = s_cnt[q];
+        __syncthreads();
+        for (int j = threadIdx.x; j < HUB_TABLE; j += NT) {
+            const int32_t key = tk[j];
+            if (key != EMPTY) {
+                const int at = atomicAdd(&s_cnt[part_of(key, (uint32_t)np)], 1);
+                out[at] = make_int4(key, ts[j], (int)tp[j], 0);
+                tk[j] = EMPTY;
+                ts[j] = 0;
+                tp[j] = 0;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Partition pass: the records of one partition of a row, from every segment,
+// are merged in the shared table (a label without room goes to the row's
+// fallback table); its best candidate is stored, and the CTA finishing the
+// row's last partition picks the best of the partition bests and of the
+// fallback slots.
+template <bool MULTI>
+__global__ void __launch_bounds__(HUB_THREADS, 2) k_hub_merge(SweepArgs a)
+{
+    constexpr int NT = HUB_THREADS;
+    constexpr int LG = 13;
+    constexpr int PROBE = 256;
+    extern __shared__ int32_t smem[];
+    int32_t *tk = smem;
+    int32_t *ts = tk + HUB_TABLE;
+    uint32_t *tp = reinterpret_cast<uint32_t *>(ts + HUB_TABLE);
+    __shared__ Cand s_red[NT / 32];
     __shared__ uint32_t s_u[NT / 32 + 1];
     __shared__ int s_last;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    // partition best of item i: sum, ~first position, label | non-strict key
+    uint4 *pbest = reinterpret_cast<uint4 *>(a.hpbest);
 
     for (int j = threadIdx.x; j < HUB_TABLE; j += NT) {
         tk[j] = EMPTY;
@@ -609,120 +914,66 @@ __global__ void __launch_bounds__(HUB_THREADS, 2) k_hub(SweepArgs a)
     }
     __syncthreads();
     uint32_t my_changed = 0;
-
-    for (int64_t item = blockIdx.x; item < a.hitems; item += gridDim.x) {
-        // the task owning this item: the last one whose first item is <= item
-        int64_t ti = 0, thi = a.len - 1;
-        while (ti < thi) {
-            const int64_t mid = (ti + thi + 1) >> 1;
-            if (__ldg(&a.htask[mid].first) <= item)
-                ti = mid;
-            else
-                thi = mid - 1;
-        }
+    for (int64_t item = blockIdx.x; item < a.hparts; item += gridDim.x) {
+        const int64_t ti = find_task(a.hmulti, item, [&](int64_t i) {
+            return (int64_t)__ldg(&a.htask[i].part0);
+        });
         const HubTask t = a.htask[ti];
         Vtx x;
         if (!load_vtx<MULTI>(a, t.v, x)) continue;  // block-uniform
-        const int seg = (int)(item - t.first);
-        const int64_t lo = x.e0 + (int64_t)seg * HUB_SEG;
-        const int64_t hi = min(lo + HUB_SEG, x.e0 + x.d);
+        const int p = (int)(item - t.part0);
+        const int np = t.npart;
         const uint64_t ktv = stream_at(a.key_t, (uint64_t)x.lv + 1);
-
-        if (t.nseg == 1) {  // the whole row fits the shared table
-            const int lg = min(ilog2_ceil(2u * (uint32_t)x.d), LG);
-            Cand local;
-            if (a.identity) {
-                local = identity_best<NT>(a, x.e0, lo, hi, ktv, threadIdx.x);
-            } else {
-                accumulate_range<NT>(a, x.e0, lo, hi, x.vb, tk, ts, tp, lg);
-                __syncthreads();
-                local = scan_table<NT>(tk, ts, tp, 1 << lg, a.strict, ktv, s_u);
-            }
-            const Cand best = block_argmax<NT>(local, a.strict, s_red);
-            if (threadIdx.x == 0) {
-                a.lab_out[x.v] = best.label;
-                if (best.label != x.own) {
-                    if (MULTI)
-                        atomicAdd(a.changed + x.g, 1);
-                    else
-                        ++my_changed;
-                }
-            }
-            __syncthreads();
-            continue;
-        }
-
         const int glg = ilog2_ceil(2u * (uint32_t)x.d);
         unsigned long long *gk = a.hkey + t.tab;
         uint32_t *gp = a.hnpos + t.tab;
         int32_t *gu = a.hused + t.tab / 2;
-        if (a.identity) {
-            // the segment's own winner is the only candidate it contributes
-            const Cand best =
-                block_argmax<NT>(identity_best<NT>(a, x.e0, lo, hi, ktv, threadIdx.x), a.strict,
-                                 s_red);
-            if (threadIdx.x == 0 && best.sum > 0) {
-                const int64_t claimed = global_add(gk, gp, glg, best.label, best.sum, best.npos);
-                if (claimed >= 0) gu[atomicAdd(a.hnused + ti, 1)] = (int32_t)claimed;
-            }
-        } else {
-            // aggregate the segment, then flush it into the hub's global table
-            accumulate_range<NT>(a, x.e0, lo, hi, x.vb, tk, ts, tp, LG);
-            __syncthreads();
-        }
-        for (int j0 = 0; j0 < (a.identity ? 0 : HUB_TABLE); j0 += NT) {
-            const int j = j0 + threadIdx.x;
-            const int32_t key = tk[j];
-            int64_t claimed = -1;
-            if (key != EMPTY) {
-                claimed = global_add(gk, gp, glg, key, (uint32_t)ts[j], tp[j]);
-                tk[j] = EMPTY;
-                ts[j] = 0;
-                tp[j] = 0;
-            }
-            // record newly claimed slots in the used list, one atomic per warp
-            const unsigned m = __ballot_sync(FULL, claimed >= 0);
-            if (m) {
-                const int leader = __ffs(m) - 1;
-                int base = 0;
-                if (lane == leader) base = atomicAdd(a.hnused + ti, __popc(m));
-                base = __shfl_sync(FULL, base, leader);
-                if (claimed >= 0) gu[base + __popc(m & ((1u << lane) - 1u))] = (int32_t)claimed;
+        // a warp per segment's run of this partition
+        for (int s = wib; s < t.nseg; s += NT / 32) {
+            const int32_t *po = a.hpoff + t.poff0 + (int64_t)s * (np + 1);
+            const int b = __ldg(po + p), e = __ldg(po + p + 1);
+            const int4 *rec = a.hrec + (int64_t)(t.seg0 + s) * HUB_SEG;
+            for (int r = b + lane; r < e; r += 32) {
+                const int4 R = __ldg(rec + r);
+                if (!table_add(tk, ts, tp, LG, PROBE, R.x, R.y, 0xFFFFFFFFu - (uint32_t)R.z)) {
+                    const int64_t c = global_add(gk, gp, glg, R.x, (uint32_t)R.y, (uint32_t)R.z);
+                    if (c >= 0) gu[atomicAdd(a.hnused + ti, 1)] = (int32_t)c;
+                }
             }
         }
-        __threadfence();
         __syncthreads();
-        if (threadIdx.x == 0) s_last = atomicAdd(a.hdone + ti, 1) == t.nseg - 1;
+        Cand best = block_argmax<NT>(scan_table<NT>(tk, ts, tp, HUB_TABLE, a.strict, ktv, s_u),
+                                     a.strict, s_red);
+        if (threadIdx.x == 0) {
+            pbest[2 * item] = make_uint4(best.sum, best.npos, (uint32_t)best.label, 0u);
+            pbest[2 * item + 1] = make_uint4((uint32_t)best.h, (uint32_t)(best.h >> 32), 0u, 0u);
+            __threadfence();
+            s_last = atomicAdd(a.hdone + ti, 1) == np - 1;
+        }
         __syncthreads();
         if (!s_last) continue;
 
-        // the last segment of the hub: argmax over its used slots, reset them
+        // the row's last partition: best of the partition bests and fallback slots
         __threadfence();
         const int nused = __ldcg(a.hnused + ti);
-        uint32_t mx = 0;
-        if (!a.strict) {
-            for (int u = threadIdx.x; u < nused; u += NT)
-                mx = max(mx, (uint32_t)__ldcg(gk + __ldcg(gu + u)));
-            mx = block_max<NT>(mx, s_u);
+        Cand c{0u, 0u, 0ull, EMPTY};
+        for (int q = threadIdx.x; q < np; q += NT) {
+            const uint4 A = __ldcg(pbest + 2 * (t.part0 + q));
+            const uint4 B = __ldcg(pbest + 2 * (t.part0 + q) + 1);
+            const Cand y{A.x, A.y, (uint64_t)B.x | ((uint64_t)B.y << 32), (int32_t)A.z};
+            if (better(y, c)) c = y;
         }
-        Cand best{0u, 0u, 0ull, EMPTY};
         for (int u = threadIdx.x; u < nused; u += NT) {
             const int32_t slot = __ldcg(gu + u);
             const unsigned long long kv = __ldcg(gk + slot);
             const int32_t label = (int32_t)((uint32_t)(kv >> 32) - 1u);
-            const uint32_t sum = (uint32_t)kv;
-            const uint32_t np = __ldcg(gp + slot);
-            if (a.strict) {
-                const Cand c{sum, np, 0ull, label};
-                if (better(c, best)) best = c;
-            } else if (sum == mx) {
-                const Cand c{sum, np, stream_at(ktv, (uint64_t)label + 1), label};
-                if (better(c, best)) best = c;
-            }
+            const Cand y{(uint32_t)kv, __ldcg(gp + slot),
+                         a.strict ? 0ull : stream_at(ktv, (uint64_t)label + 1), label};
+            if (better(y, c)) c = y;
             gk[slot] = 0ull;
             gp[slot] = 0u;
         }
-        best = block_argmax<NT>(best, a.strict, s_red);
+        best = block_argmax<NT>(c, a.strict, s_red);
         if (threadIdx.x == 0) {
             a.lab_out[x.v] = best.label;
             if (best.label != x.own) {
@@ -743,9 +994,11 @@ template <bool MULTI>
 int launch(int bucket, const SweepArgs &a, int num_sms, cudaStream_t st)
 {
     constexpr size_t cta_smem = (size_t)CTA_TABLE * 12;
+    constexpr size_t cta2_smem = (size_t)CTA2_TABLE * 12;
     constexpr size_t hub_smem = (size_t)HUB_TABLE * 12;
     if (a.len <= 0) return 0;
     int64_t blocks = 0;
+    int n = 1;
     switch (bucket) {
     case 0:
         blocks = (a.len + 255) / 256;
@@ -758,15 +1011,34 @@ int launch(int bucket, const SweepArgs &a, int num_sms, cudaStream_t st)
     case 2:
         blocks = a.len;
         k_cta<CTA_THREADS, CTA_TABLE, MULTI>
-            <<<(int)(blocks < num_sms * 8 ? blocks : num_sms * 8), CTA_THREADS, cta_smem, st>>>(a);
+            <<<(int)(blocks < num_sms * 16 ? blocks : num_sms * 16), CTA_THREADS, cta_smem, st>>>(a);
         break;
-    default:
-        if (a.hitems <= 0) return 0;
-        blocks = a.hitems < (int64_t)num_sms * 2 ? a.hitems : (int64_t)num_sms * 2;
-        k_hub<MULTI><<<(int)blocks, HUB_THREADS, hub_smem, st>>>(a);
+    case 3:
+        blocks = a.len;
+        k_cta<CTA2_THREADS, CTA2_TABLE, MULTI>
+            <<<(int)(blocks < num_sms * 8 ? blocks : num_sms * 8), CTA2_THREADS, cta2_smem, st>>>(a);
+        break;
+    default: {
+        n = 0;
+        if (a.hmulti > 0) {  // long rows: segments, then label partitions
+            const int64_t cap = (int64_t)num_sms * 2;
+            k_hub_seg<MULTI><<<(int)(a.hsegs < cap ? a.hsegs : cap), HUB_THREADS, hub_smem, st>>>(a);
+            k_hub_merge<MULTI>
+                <<<(int)(a.hparts < cap ? a.hparts : cap), HUB_THREADS, hub_smem, st>>>(a);
+            n += 2;
+        }
+        if (a.len > a.hmulti) {  // the other hub rows: one CTA each
+            SweepArgs b = a;
+            b.list = a.list + a.hmulti;
+            b.len = a.len - a.hmulti;
+            blocks = b.len < (int64_t)num_sms * 2 ? b.len : (int64_t)num_sms * 2;
+            k_cta<HUB_THREADS, HUB_TABLE, MULTI><<<(int)blocks, HUB_THREADS, hub_smem, st>>>(b);
+            ++n;
+        }
         break;
     }
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    }
+    return cudaGetLastError() == cudaSuccess ? n : -1;
 }
 
 template <bool MULTI>
@@ -776,7 +1048,18 @@ int prepare()
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)((size_t)CTA_TABLE * 12)) != cudaSuccess)
         return -1;
-    if (cudaFuncSetAttribute(k_hub<MULTI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(k_cta<CTA2_THREADS, CTA2_TABLE, MULTI>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)((size_t)CTA2_TABLE * 12)) != cudaSuccess)
+        return -1;
+    if (cudaFuncSetAttribute(k_cta<HUB_THREADS, HUB_TABLE, MULTI>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)((size_t)HUB_TABLE * 12)) != cudaSuccess)
+        return -1;
+    if (cudaFuncSetAttribute(k_hub_seg<MULTI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)((size_t)HUB_TABLE * 12)) != cudaSuccess)
+        return -1;
+    if (cudaFuncSetAttribute(k_hub_merge<MULTI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)((size_t)HUB_TABLE * 12)) != cudaSuccess)
         return -1;
     return 0;

@@ -119,8 +119,9 @@ def test_golden_traces_async(lp, golden_traces):
 # ---------------------------------------------------------------- every degree bucket
 def hub_graph(seed, n=40_000, hubs=3, hub_deg=12_000, p_extra=0.0002, sorted_rows=False):
     """A sparse random graph plus `hubs` vertices of degree ~hub_deg, so hub
-    rows span several 4096-entry segments.  Rows are shuffled unless
-    sorted_rows (sorted rows enable the identity first sweep)."""
+    rows are longer than 4096 entries (swept by CTA clusters).  Rows are
+    shuffled unless sorted_rows (sorted rows enable the identity first
+    sweep)."""
     rng = np.random.default_rng(seed)
     m_rand = int(p_extra * n * n / 2)
     u = rng.integers(0, n, m_rand)
@@ -152,7 +153,7 @@ def hub_graph(seed, n=40_000, hubs=3, hub_deg=12_000, p_extra=0.0002, sorted_row
 
 
 @pytest.mark.parametrize("strict", [True, False])
-@pytest.mark.parametrize("shape", ["small", "warp", "cta", "hub", "mixed"])
+@pytest.mark.parametrize("shape", ["small", "warp", "cta", "cta2", "hub", "mixed"])
 def test_sync_parity_per_bucket(lp, shape, strict):
     if shape == "small":
         off, idx, w = random_graph(3000, 6 / 3000, 1, wmax=3)
@@ -160,33 +161,63 @@ def test_sync_parity_per_bucket(lp, shape, strict):
         off, idx, w = random_graph(1500, 70 / 1500, 2, wmax=1)
     elif shape == "cta":
         off, idx, w = random_graph(2500, 400 / 2500, 3, wmax=4)
+    elif shape == "cta2":
+        off, idx, w = random_graph(2000, 800 / 2000, 13, wmax=4)
     elif shape == "hub":
         off, idx, w = hub_graph(4)
     else:
         g = gg.rmat(15, seed=5)
         off, idx, w = g.offsets, g.indices, g.weights
     deg = np.diff(off)
-    assert deg.max() > {"small": 8, "warp": 33, "cta": 129, "hub": 8192, "mixed": 1024}[shape]
+    assert deg.max() > {"small": 8, "warp": 33, "cta": 129, "cta2": 513, "hub": 8192,
+                        "mixed": 1024}[shape]
     assert_sync_parity(lp, off, idx, w, strict=strict, seed=11)
 
 
 @pytest.mark.parametrize("strict", [True, False])
-def test_identity_first_sweep_multi_segment_hubs(lp, strict):
+def test_identity_first_sweep_cluster_rows(lp, strict):
     """Sorted rows without repeats: the first sweep takes the identity path,
-    including hubs of several segments; sync and 2-wave async stay exact."""
+    including rows swept by CTA clusters; sync and 2-wave async stay exact."""
     off, idx, w = hub_graph(9, n=30_000, hubs=4, hub_deg=13_000, sorted_rows=True)
     assert np.all(np.diff(idx)[np.diff(np.repeat(np.arange(off.size - 1), np.diff(off))) == 0] > 0)
     assert_sync_parity(lp, off, idx, w, strict=strict, seed=4)
     assert_async_parity(lp, off, idx, w, 2, strict=strict, seed=4)
 
 
+@pytest.mark.parametrize("strict", [True, False])
+@pytest.mark.parametrize("mode", ["sync", "async"])
+def test_cluster_rows_overflow_tables(lp, strict, mode):
+    """Rows longer than 4096 entries are swept by CTA clusters.  From distinct
+    shuffled labels, two rows of 150k entries hold more distinct labels than
+    the cluster's shared tables keep within their probe windows, so part of
+    them go through the rows' global overflow tables.  Labels and changed
+    counts match the oracle for three sweeps (2-wave async in async mode)."""
+    off, idx, w = hub_graph(21, n=200_000, hubs=2, hub_deg=150_000, p_extra=2e-5)
+    n = off.shape[0] - 1
+    init = np.random.default_rng(5).permutation(n).astype(np.int32)
+    waves = 2 if mode == "async" else 0
+    kw = dict(waves=waves) if waves else {}
+    with lp.Graph(off, idx, w) as G:
+        r = G.rak(tolerance=0.0, max_iter=3, mode=mode, strict=strict, seed=5, init_labels=init,
+                  **kw)
+        labels, hist = G.labels(), G.history()
+    ref, iters, conv, ref_hist = oracle.rak(off, idx, w, 0.0, 3, mode, strict=strict, seed=5,
+                                            init_labels=init, waves=waves)
+    assert r.iterations == iters == 3
+    assert np.array_equal(hist, ref_hist)
+    mism = np.nonzero(labels != ref)[0]
+    assert mism.size == 0, f"{mism.size} labels differ, first at vertex {mism[:5]}"
+
+
 @pytest.mark.parametrize("waves", [2, 7, 31, 4096])
-@pytest.mark.parametrize("shape", ["small", "cta", "hub", "mixed"])
+@pytest.mark.parametrize("shape", ["small", "cta", "cta2", "hub", "mixed"])
 def test_async_parity_per_bucket(lp, shape, waves):
     if shape == "small":
         off, idx, w = random_graph(3000, 6 / 3000, 5, wmax=3)
     elif shape == "cta":
         off, idx, w = random_graph(2500, 300 / 2500, 6, wmax=4)
+    elif shape == "cta2":
+        off, idx, w = random_graph(2000, 700 / 2000, 14, wmax=4)
     elif shape == "hub":
         off, idx, w = hub_graph(7, n=20_000, hub_deg=9_000)
     else:
