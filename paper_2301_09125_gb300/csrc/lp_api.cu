@@ -244,7 +244,9 @@ struct GraphSet {
     // part is a subset of); fallback tables, used lists and per-task counters
     HubTask *htask = nullptr, *htask_w = nullptr;
     int64_t hmulti = 0, hsegs = 0, hparts = 0;
-    std::vector<int64_t> hmulti_w, hsegs_w, hparts_w;
+    std::vector<int64_t> hmulti_w, hsegs_w, hparts_w, hsegs_at_w, hparts_at_w;
+    int32_t *hseg_task = nullptr, *hpart_task = nullptr;      // plain list
+    int32_t *hseg_task_w = nullptr, *hpart_task_w = nullptr;  // wave lists, wave after wave
     int4 *hrec = nullptr;
     int32_t *hpoff = nullptr;
     uint4 *hpbest = nullptr;
@@ -302,6 +304,10 @@ struct GraphSet {
         f(hrec);
         f(hpoff);
         f(hpbest);
+        f(hseg_task);
+        f(hpart_task);
+        f(hseg_task_w);
+        f(hpart_task_w);
         f(kc);
         f(macc);
         fh(h_macc);
@@ -324,6 +330,7 @@ struct GraphSet {
         hrec = nullptr;
         hpoff = nullptr;
         hpbest = nullptr;
+        hseg_task = hpart_task = hseg_task_w = hpart_task_w = nullptr;
         kc = macc = h_macc = nullptr;
         g_sel = nullptr;
         lab_tmp = nullptr;
@@ -387,6 +394,25 @@ struct GraphSet {
             LP_TRY(read_ingest(graph_index));
         }
         (void)g;
+        return LP_OK;
+    }
+
+    // validate a single graph's device CSR and check its row order in one pass
+    lp_status validate_single(int32_t n, int64_t m)
+    {
+        uint32_t *bits = nullptr;
+        LP_TRY(dev_alloc(&bits, m / 32 + 1, "row-start bitmap", st, device));
+        Launches L;
+        const int rc = ingest_validate_ordered(off, idx, wts, n, m, bits, d_ing, st, &L.n);
+        cudaFreeAsync(bits, st);
+        if (rc != 0) return fail(LP_ECUDA, cuda_msg("validation launch", cudaGetLastError()));
+        LP_TRY(read_ingest(-1));
+        if ((int64_t)h_ing->max_deg * (int64_t)h_ing->max_w >= 2147483648LL) {
+            if (ingest_check_wdeg(off, wts, n, d_ing, st, &L.n) != 0)
+                return fail(LP_ECUDA, cuda_msg("weight-sum launch", cudaGetLastError()));
+            LP_TRY(read_ingest(-1));
+        }
+        rows_distinct = h_ing->repeated == 0;
         return LP_OK;
     }
 
@@ -475,6 +501,10 @@ struct GraphSet {
             LP_TRY(dev_alloc(&hpoff, tot[4] > 0 ? tot[4] : 1, "hub partition offsets", st, device));
             LP_TRY(dev_alloc(&hpbest, 2 * (tot[3] > 0 ? tot[3] : 1), "hub partition bests", st,
                              device));
+            LP_TRY(dev_alloc(&hseg_task, tot[2], "hub item maps", st, device));
+            LP_TRY(dev_alloc(&hpart_task, tot[3], "hub item maps", st, device));
+            if (hub_item_maps(htask, hmulti, hseg_task, hpart_task, st, &L.n) != 0)
+                return fail(LP_ECUDA, cuda_msg("hub item maps", cudaGetLastError()));
             LP_TRY(dev_alloc(&hkey, slots, "hub tables", st, device));
             LP_TRY(dev_alloc(&hnpos, slots, "hub tables", st, device));
             LP_TRY(dev_alloc(&hused, slots / 2 + 1, "hub used lists", st, device));
@@ -555,10 +585,29 @@ struct GraphSet {
             if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(st);
             cudaFreeAsync(d_tot, st);
             if (e2 != cudaSuccess) return fail(LP_ECUDA, cuda_msg("wave hub tasks", e2));
+            hsegs_at_w.assign((size_t)waves, 0);
+            hparts_at_w.assign((size_t)waves, 0);
+            int64_t seg_at = 0, part_at = 0;
             for (int k = 0; k < waves; ++k) {
                 hmulti_w[(size_t)k] = tots[5 * (size_t)k];
                 hsegs_w[(size_t)k] = tots[5 * (size_t)k + 2];
                 hparts_w[(size_t)k] = tots[5 * (size_t)k + 3];
+                hsegs_at_w[(size_t)k] = seg_at;
+                hparts_at_w[(size_t)k] = part_at;
+                seg_at += hsegs_w[(size_t)k];
+                part_at += hparts_w[(size_t)k];
+            }
+            // the waves' item maps, wave after wave (together the plain list's size)
+            if (!hseg_task_w) LP_TRY(dev_alloc(&hseg_task_w, hsegs, "hub item maps", st, device));
+            if (!hpart_task_w)
+                LP_TRY(dev_alloc(&hpart_task_w, hparts, "hub item maps", st, device));
+            for (int k = 0; k < waves; ++k) {
+                if (hmulti_w[(size_t)k] == 0) continue;
+                const int64_t st0 = wstart[(size_t)HUB_BUCKET * waves + k];
+                if (hub_item_maps(htask_w + (st0 - hub0), hmulti_w[(size_t)k],
+                                  hseg_task_w + hsegs_at_w[(size_t)k],
+                                  hpart_task_w + hparts_at_w[(size_t)k], st, &L2.n) != 0)
+                    return fail(LP_ECUDA, cuda_msg("wave hub item maps", cudaGetLastError()));
             }
         }
         wl_waves = waves;
@@ -703,6 +752,8 @@ struct GraphSet {
                 a.hmulti = hmulti;
                 a.hsegs = hsegs;
                 a.hparts = hparts;
+                a.hseg_task = hseg_task;
+                a.hpart_task = hpart_task;
             } else {
                 a.list = wlist + wstart[(size_t)b * waves + k];
                 a.len = wcount[(size_t)b * waves + k];
@@ -711,6 +762,10 @@ struct GraphSet {
                     a.hmulti = hmulti_w[(size_t)k];
                     a.hsegs = hsegs_w[(size_t)k];
                     a.hparts = hparts_w[(size_t)k];
+                    if (hmulti_w[(size_t)k] > 0) {
+                        a.hseg_task = hseg_task_w + hsegs_at_w[(size_t)k];
+                        a.hpart_task = hpart_task_w + hparts_at_w[(size_t)k];
+                    }
                 }
             }
             if (a.len == 0) continue;
@@ -1019,7 +1074,7 @@ lp_status lp_graph_create(int32_t n, int64_t m, const int32_t *offsets, const in
     LP_TRY(dev_alloc(&s.g_n, 1, "graph sizes", s.st, s.device));
     LP_CU(cudaMemcpyAsync(s.g_n, &n, sizeof(int32_t), cudaMemcpyHostToDevice, s.st));
     // a1: validation keeps every later kernel in bounds
-    LP_TRY(s.validate(0, s.off, s.idx, s.wts, n, m, -1));
+    LP_TRY(s.validate_single(n, m));
     if (flags & LP_FLAG_CHECK_SYMMETRIC) {
         std::vector<int32_t> ho((size_t)n + 1), hi((size_t)m), hw(weights ? (size_t)m : 0);
         LP_CU(cudaMemcpy(ho.data(), s.off, ho.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
@@ -1030,7 +1085,6 @@ lp_status lp_graph_create(int32_t n, int64_t m, const int32_t *offsets, const in
         if (!host_symmetric(n, ho.data(), hi.data(), weights ? hw.data() : nullptr))
             return fail(LP_EINVAL, "CSR is not symmetric");
     }
-    LP_TRY(s.check_row_order());
     LP_TRY(s.bucket());
     LP_TRY(s.alloc_labels());
     LP_CU(cudaStreamSynchronize(s.st));

@@ -73,19 +73,79 @@ __global__ void k_val_wdeg(const int32_t *off, const int32_t *wts, int32_t n, In
     }
 }
 
-// row starts of a graph set as a bitmap over global entries
+// row starts of a graph set as a bitmap over global entries (rows outside
+// [0, ne) are skipped: this may run before the offsets are known valid)
 __global__ void k_mark_row_starts(const int32_t *off, int32_t nv, const int32_t *vgraph,
-                                  const int64_t *g_ebase, uint32_t *bits)
+                                  const int64_t *g_ebase, int64_t ne, uint32_t *bits)
 {
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nv;
          v += (int64_t)gridDim.x * blockDim.x) {
         const int32_t g = vgraph ? vgraph[v] : 0;
         const int32_t rs = off[v + g], re = off[v + g + 1];
-        if (re > rs) {
+        if (re > rs && rs >= 0) {
             const int64_t e = (g_ebase ? g_ebase[g] : 0) + rs;
-            atomicOr(bits + (e >> 5), 1u << (e & 31));
+            if (e < ne) atomicOr(bits + (e >> 5), 1u << (e & 31));
         }
     }
+}
+
+// One graph's entries in 16-byte blocks: index in [0, n), weight >= 1, and
+// (rows marked in bits) strictly increasing indices within each row.
+__global__ void k_val_entries4(const int32_t *idx, const int32_t *wts, int32_t n, int64_t m,
+                               const uint32_t *bits, IngestOut *o)
+{
+    int32_t wmax = 0;
+    bool unordered = false;
+    const int64_t nb = (m + 3) / 4;
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nb;
+         b += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e0 = 4 * b;
+        int32_t u[5], w[4];
+        if (e0 + 3 < m) {
+            const int4 I = __ldcs(reinterpret_cast<const int4 *>(idx) + b);
+            u[0] = I.x;
+            u[1] = I.y;
+            u[2] = I.z;
+            u[3] = I.w;
+            if (wts) {
+                const int4 W = __ldcs(reinterpret_cast<const int4 *>(wts) + b);
+                w[0] = W.x;
+                w[1] = W.y;
+                w[2] = W.z;
+                w[3] = W.w;
+            } else {
+                w[0] = w[1] = w[2] = w[3] = 1;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                u[j] = e0 + j < m ? idx[e0 + j] : 0;
+                w[j] = e0 + j < m ? (wts ? wts[e0 + j] : 1) : 1;
+            }
+        }
+        u[4] = e0 + 4 < m ? __ldg(idx + e0 + 4) : 0;
+        // positions e0 .. e0 + 3 share one bitmap word; e0 + 4 may start the next
+        const uint32_t word = bits[e0 >> 5];
+        const uint32_t next = e0 + 4 < m ? bits[(e0 + 4) >> 5] : 0u;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t e = e0 + j;
+            if (e >= m) break;
+            if (u[j] < 0 || u[j] >= n) report(o, ING_INDEX, e);
+            if (w[j] < 1)
+                report(o, ING_WEIGHT, e);
+            else
+                wmax = max(wmax, w[j]);
+            const int64_t f = e + 1;
+            if (f < m) {
+                const bool starts = ((j < 3 ? word : next) >> (f & 31)) & 1u;
+                unordered = unordered || (!starts && u[j] >= u[j + 1]);
+            }
+        }
+    }
+    wmax = (int32_t)__reduce_max_sync(FULL, (uint32_t)wmax);
+    if ((threadIdx.x & 31) == 0 && wmax) atomicMax(&o->max_w, wmax);
+    if (__any_sync(FULL, unordered) && (threadIdx.x & 31) == 0) atomicExch(&o->repeated, 1);
 }
 
 // entries e, e+1 of one row must satisfy idx[e] < idx[e+1]
@@ -127,13 +187,22 @@ __global__ void __launch_bounds__(BK) k_bucket_count(const int32_t *off, int32_t
     }
     __syncthreads();
     const int64_t v = (int64_t)blockIdx.x * BK + threadIdx.x;
-    if (v < nv) {
-        const int32_t d = degree_of(off, vgraph, (int32_t)v);
-        const int b = bucket_of(d);
-        if (b >= 0) {
-            atomicAdd(&cnt[b], 1);
-            atomicAdd(&ent[b], (unsigned long long)d);
+    const int32_t d = v < nv ? degree_of(off, vgraph, (int32_t)v) : 0;
+    const int b = bucket_of(d);
+    // one shared atomic per warp and bucket (rows of every bucket but the last
+    // are short enough for a 32-bit warp sum)
+#pragma unroll
+    for (int c = 0; c < NUM_BUCKETS - 1; ++c) {
+        const unsigned mask = __ballot_sync(FULL, b == c);
+        const uint32_t sum = __reduce_add_sync(FULL, b == c ? (uint32_t)d : 0u);
+        if ((threadIdx.x & 31) == 0 && mask) {
+            atomicAdd(&cnt[c], __popc(mask));
+            atomicAdd(&ent[c], (unsigned long long)sum);
         }
+    }
+    if (b == NUM_BUCKETS - 1) {
+        atomicAdd(&cnt[b], 1);
+        atomicAdd(&ent[b], (unsigned long long)d);
     }
     __syncthreads();
     if (threadIdx.x < NUM_BUCKETS) {
@@ -326,6 +395,17 @@ __global__ void __launch_bounds__(1024) k_hub_tasks(int32_t *list, int64_t len,
     }
 }
 
+__global__ void k_hub_item_maps(const HubTask *tasks, int64_t nbig, int32_t *seg_task,
+                                int32_t *part_task)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nbig;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const HubTask t = tasks[i];
+        for (int s = 0; s < t.nseg; ++s) seg_task[t.seg0 + s] = (int32_t)i;
+        for (int p = 0; p < t.npart; ++p) part_task[t.part0 + p] = (int32_t)i;
+    }
+}
+
 __global__ void k_degrees_of(const int32_t *off, const int32_t *vgraph, const int32_t *list,
                              int64_t len, int32_t *deg)
 {
@@ -433,6 +513,25 @@ int ingest_validate(const int32_t *off, const int32_t *idx, const int32_t *wts, 
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
+int ingest_validate_ordered(const int32_t *off, const int32_t *idx, const int32_t *wts, int32_t n,
+                            int64_t m, uint32_t *bits, IngestOut *d_out, cudaStream_t st,
+                            int64_t *launches)
+{
+    if (cudaMemsetAsync(d_out, 0, sizeof(IngestOut), st) != cudaSuccess) return -1;
+    k_val_offsets<<<grid_for((int64_t)n + 1, 256, 4096), 256, 0, st>>>(off, n, m, d_out);
+    ++*launches;
+    if (m > 0) {
+        if (cudaMemsetAsync(bits, 0, (size_t)(m / 32 + 1) * sizeof(uint32_t), st) != cudaSuccess)
+            return -1;
+        k_mark_row_starts<<<grid_for(n, 256, 8192), 256, 0, st>>>(off, n, nullptr, nullptr, m,
+                                                                   bits);
+        k_val_entries4<<<grid_for((m + 3) / 4, 256, 8192), 256, 0, st>>>(idx, wts, n, m, bits,
+                                                                          d_out);
+        *launches += 2;
+    }
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 int ingest_row_order(const int32_t *off, const int32_t *idx, int32_t nv, int64_t ne,
                      const int32_t *vgraph, const int64_t *g_ebase, uint32_t *bits,
                      IngestOut *d_out, cudaStream_t st, int64_t *launches)
@@ -441,7 +540,8 @@ int ingest_row_order(const int32_t *off, const int32_t *idx, int32_t nv, int64_t
     if (ne < 2 || nv == 0) return 0;
     if (cudaMemsetAsync(bits, 0, (size_t)(ne / 32 + 1) * sizeof(uint32_t), st) != cudaSuccess)
         return -1;
-    k_mark_row_starts<<<grid_for(nv, 256, 8192), 256, 0, st>>>(off, nv, vgraph, g_ebase, bits);
+    k_mark_row_starts<<<grid_for(nv, 256, 8192), 256, 0, st>>>(off, nv, vgraph, g_ebase, ne,
+                                                                bits);
     k_check_row_order<<<grid_for(ne, 256, 8192), 256, 0, st>>>(idx, ne, bits, d_out);
     *launches += 2;
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
@@ -528,6 +628,15 @@ int hub_tasks(int32_t *list, int64_t len, const int32_t *off, const int32_t *vgr
               HubTask *tasks, int64_t *totals, cudaStream_t st, int64_t *launches)
 {
     k_hub_tasks<<<1, 1024, 0, st>>>(list, len, off, vgraph, tasks, totals);
+    ++*launches;
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int hub_item_maps(const HubTask *tasks, int64_t nbig, int32_t *seg_task, int32_t *part_task,
+                  cudaStream_t st, int64_t *launches)
+{
+    if (nbig <= 0) return 0;
+    k_hub_item_maps<<<grid_for(nbig, 128, 1024), 128, 0, st>>>(tasks, nbig, seg_task, part_task);
     ++*launches;
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

@@ -105,6 +105,8 @@ struct SweepArgs {
     int64_t hmulti;
     int64_t hsegs;
     int64_t hparts;
+    const int32_t *hseg_task;   // task of each segment item
+    const int32_t *hpart_task;  // task of each partition item
     int4 *hrec;
     int32_t *hpoff;
     void *hpbest;
@@ -176,6 +178,9 @@ int sweep_launch(int bucket, const SweepArgs &a, bool multi, int num_sms, cudaSt
 // fallback table slots, [2] segments, [3] partitions, [4] partition offsets.
 int hub_tasks(int32_t *list, int64_t len, const int32_t *off, const int32_t *vgraph,
               HubTask *tasks, int64_t *totals, cudaStream_t st, int64_t *launches);
+// Task index of every segment item and partition item of the first nbig tasks.
+int hub_item_maps(const HubTask *tasks, int64_t nbig, int32_t *seg_task, int32_t *part_task,
+                  cudaStream_t st, int64_t *launches);
 
 struct IngestOut {
     int32_t err;          // 0 ok, else an error code below
@@ -199,6 +204,11 @@ enum IngestErr : int32_t {
 
 int ingest_validate(const int32_t *off, const int32_t *idx, const int32_t *wts, int32_t n,
                     int64_t m, IngestOut *d_out, cudaStream_t st, int64_t *launches);
+// ingest_validate and the row-order check of ingest_row_order in one pass over
+// one graph's entries (bits: scratch of m / 32 + 1 words).
+int ingest_validate_ordered(const int32_t *off, const int32_t *idx, const int32_t *wts, int32_t n,
+                            int64_t m, uint32_t *bits, IngestOut *d_out, cudaStream_t st,
+                            int64_t *launches);
 // Whether every row lists its neighbours in strictly increasing order (then no
 // row repeats a neighbour): d_out->repeated = 0 if so.  Needs a validated CSR
 // set and a scratch bitmap of ne / 32 + 1 words; rows of graph g at ebase_g.

@@ -75,6 +75,50 @@ struct VtxPipe {
     }
 };
 
+// L2 eviction policies (PTX createpolicy): the CSR entries are read once per
+// sweep and should not push the label arrays, which every sweep gathers from
+// at random, out of L2.
+__device__ __forceinline__ uint64_t policy_evict_first()
+{
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ uint64_t policy_evict_last()
+{
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+// read-only loads with an L2 policy: a 16-byte block of entries, one entry,
+// one label
+__device__ __forceinline__ int4 ld_entries4(const int32_t *base, int64_t blk)
+{
+    int4 r;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.s32 {%0, %1, %2, %3}, [%4], %5;"
+        : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+        : "l"(reinterpret_cast<const int4 *>(base) + blk), "l"(policy_evict_first()));
+    return r;
+}
+
+__device__ __forceinline__ int32_t ld_entry(const int32_t *p)
+{
+    int32_t r;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.s32 %0, [%1], %2;"
+        : "=r"(r)
+        : "l"(p), "l"(policy_evict_first()));
+    return r;
+}
+
+__device__ __forceinline__ int32_t ld_label(const int32_t *p)
+{
+    int32_t r;
+    asm("ld.global.nc.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(r) : "l"(p), "l"(policy_evict_last()));
+    return r;
+}
+
 // Label of neighbour u (local id u, global index gi) as seen by this launch.
 // Neither buffer is written at an address this launch reads: lab_in is only
 // written by the next iteration, and lab_out entries of earlier waves were
@@ -82,7 +126,7 @@ struct VtxPipe {
 __device__ __forceinline__ int32_t neighbour_label(const SweepArgs &a, int64_t gi, int32_t u)
 {
     const bool earlier = a.waves > 1 && fastmod((uint32_t)u, a.wave_magic, a.waves) < a.wave_k;
-    return __ldg((earlier ? a.lab_out : a.lab_in) + gi);
+    return ld_label((earlier ? a.lab_out : a.lab_in) + gi);
 }
 
 
@@ -144,8 +188,8 @@ __global__ void __launch_bounds__(256) k_small(SweepArgs a)
             int32_t l = EMPTY;
             if (act) {
                 const long long e = o_e0 + pos;
-                const int32_t u = __ldg(a.idx + e);
-                w = a.wts ? __ldg(a.wts + e) : 1;
+                const int32_t u = ld_entry(a.idx + e);
+                w = a.wts ? ld_entry(a.wts + e) : 1;
                 l = a.identity ? u : neighbour_label(a, (int64_t)o_vb + u, u);
             }
             // group equal (owner, label) pairs; the lowest lane holds the first
@@ -215,13 +259,13 @@ __device__ __forceinline__ void load_block(const SweepArgs &a, int64_t blk, int3
 {
     const int64_t e0 = blk * 4;
     if (e0 + 3 < a.ne) {
-        const int4 I = __ldg(reinterpret_cast<const int4 *>(a.idx) + blk);
+        const int4 I = ld_entries4(a.idx, blk);
         u[0] = I.x;
         u[1] = I.y;
         u[2] = I.z;
         u[3] = I.w;
         if (a.wts) {
-            const int4 W = __ldg(reinterpret_cast<const int4 *>(a.wts) + blk);
+            const int4 W = ld_entries4(a.wts, blk);
             w[0] = W.x;
             w[1] = W.y;
             w[2] = W.z;
@@ -749,22 +793,6 @@ __device__ __forceinline__ uint32_t part_of(int32_t l, uint32_t np)
     return (uint32_t)(((uint64_t)h * np) >> 32);
 }
 
-// Index of the task owning work item `item`: the last task i in [0, n) whose
-// first item first(i) is <= item.
-template <typename F>
-__device__ __forceinline__ int64_t find_task(int64_t n, int64_t item, F first)
-{
-    int64_t lo = 0, hi = n - 1;
-    while (lo < hi) {
-        const int64_t mid = (lo + hi + 1) >> 1;
-        if (first(mid) <= item)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    return lo;
-}
-
 // In-place exclusive scan of c[0..n) (n <= HUB_PMAX) by NT threads; c[n]
 // receives the total.
 template <int NT>
@@ -836,9 +864,7 @@ __global__ void __launch_bounds__(HUB_THREADS, 2) k_hub_seg(SweepArgs a)
     }
     __syncthreads();
     for (int64_t item = blockIdx.x; item < a.hsegs; item += gridDim.x) {
-        const int64_t ti = find_task(a.hmulti, item, [&](int64_t i) {
-            return (int64_t)__ldg(&a.htask[i].seg0);
-        });
+        const int64_t ti = __ldg(a.hseg_task + item);
         const HubTask t = a.htask[ti];
         Vtx x;
         if (!load_vtx<MULTI>(a, t.v, x)) continue;  // block-uniform
@@ -903,7 +929,7 @@ __global__ void __launch_bounds__(HUB_THREADS, 2) k_hub_merge(SweepArgs a)
     __shared__ Cand s_red[NT / 32];
     __shared__ uint32_t s_u[NT / 32 + 1];
     __shared__ int s_last;
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    __shared__ int32_t s_rb[NT], s_re[NT];
     // partition best of item i: sum, ~first position, label | non-strict key
     uint4 *pbest = reinterpret_cast<uint4 *>(a.hpbest);
 
@@ -915,9 +941,7 @@ __global__ void __launch_bounds__(HUB_THREADS, 2) k_hub_merge(SweepArgs a)
     __syncthreads();
     uint32_t my_changed = 0;
     for (int64_t item = blockIdx.x; item < a.hparts; item += gridDim.x) {
-        const int64_t ti = find_task(a.hmulti, item, [&](int64_t i) {
-            return (int64_t)__ldg(&a.htask[i].part0);
-        });
+        const int64_t ti = __ldg(a.hpart_task + item);
         const HubTask t = a.htask[ti];
         Vtx x;
         if (!load_vtx<MULTI>(a, t.v, x)) continue;  // block-uniform
@@ -928,20 +952,29 @@ __global__ void __launch_bounds__(HUB_THREADS, 2) k_hub_merge(SweepArgs a)
         unsigned long long *gk = a.hkey + t.tab;
         uint32_t *gp = a.hnpos + t.tab;
         int32_t *gu = a.hused + t.tab / 2;
-        // a warp per segment's run of this partition
-        for (int s = wib; s < t.nseg; s += NT / 32) {
-            const int32_t *po = a.hpoff + t.poff0 + (int64_t)s * (np + 1);
-            const int b = __ldg(po + p), e = __ldg(po + p + 1);
-            const int4 *rec = a.hrec + (int64_t)(t.seg0 + s) * HUB_SEG;
-            for (int r = b + lane; r < e; r += 32) {
-                const int4 R = __ldg(rec + r);
-                if (!table_add(tk, ts, tp, LG, PROBE, R.x, R.y, 0xFFFFFFFFu - (uint32_t)R.z)) {
-                    const int64_t c = global_add(gk, gp, glg, R.x, (uint32_t)R.y, (uint32_t)R.z);
-                    if (c >= 0) gu[atomicAdd(a.hnused + ti, 1)] = (int32_t)c;
+        // this partition's run in every segment: run bounds are staged for up
+        // to NT segments at a time, then all threads share each run
+        for (int s0 = 0; s0 < t.nseg; s0 += NT) {
+            const int ns = min(NT, t.nseg - s0);
+            if ((int)threadIdx.x < ns) {
+                const int32_t *po = a.hpoff + t.poff0 + (int64_t)(s0 + threadIdx.x) * (np + 1);
+                s_rb[threadIdx.x] = __ldg(po + p);
+                s_re[threadIdx.x] = __ldg(po + p + 1);
+            }
+            __syncthreads();
+            for (int s = 0; s < ns; ++s) {
+                const int4 *rec = a.hrec + (int64_t)(t.seg0 + s0 + s) * HUB_SEG;
+                for (int r = s_rb[s] + threadIdx.x; r < s_re[s]; r += NT) {
+                    const int4 R = __ldcs(rec + r);
+                    if (!table_add(tk, ts, tp, LG, PROBE, R.x, R.y, 0xFFFFFFFFu - (uint32_t)R.z)) {
+                        const int64_t c =
+                            global_add(gk, gp, glg, R.x, (uint32_t)R.y, (uint32_t)R.z);
+                        if (c >= 0) gu[atomicAdd(a.hnused + ti, 1)] = (int32_t)c;
+                    }
                 }
             }
+            __syncthreads();
         }
-        __syncthreads();
         Cand best = block_argmax<NT>(scan_table<NT>(tk, ts, tp, HUB_TABLE, a.strict, ktv, s_u),
                                      a.strict, s_red);
         if (threadIdx.x == 0) {
