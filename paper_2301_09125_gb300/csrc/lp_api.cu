@@ -308,6 +308,7 @@ struct GraphSet {
         f(hpart_task);
         f(hseg_task_w);
         f(hpart_task_w);
+        f(d_res);
         f(kc);
         f(macc);
         fh(h_macc);
@@ -331,6 +332,7 @@ struct GraphSet {
         hpoff = nullptr;
         hpbest = nullptr;
         hseg_task = hpart_task = hseg_task_w = hpart_task_w = nullptr;
+        d_res = nullptr;
         kc = macc = h_macc = nullptr;
         g_sel = nullptr;
         lab_tmp = nullptr;
@@ -341,6 +343,11 @@ struct GraphSet {
         prof_ev.clear();
         if (ev_iter) cudaEventDestroy(ev_iter);
         ev_iter = nullptr;
+        drop_graph();
+        if (gr_stream) cudaStreamDestroy(gr_stream);
+        gr_stream = nullptr;
+        if (h_res) cudaFreeHost(h_res);
+        h_res = nullptr;
         cudaStreamSynchronize(st);
     }
 
@@ -728,19 +735,18 @@ struct GraphSet {
 
     bool run_done() const { return rs.active_left == 0 || rs.it >= rs.p.max_iter; }
 
-    // launch one iteration (a3-a5 for every bucket and wave) and the read of
-    // its changed counters; ev_iter marks its end
-    lp_status run_launch()
+    // Launch iteration `it`'s sweeps (a3-a5 for every bucket and wave) on
+    // stream s, reading label buffer `cur` and writing cur ^ 1; profiled
+    // launches are bracketed by events and listed in rs.prof_launch.
+    lp_status launch_sweeps(cudaStream_t s, int32_t it, int cur, bool prof, int64_t *kernels)
     {
-        Launches L;
-        const int32_t it = rs.it;
         const int32_t waves = rs.waves;
         SweepArgs &a = rs.a;
         const int64_t t = (int64_t)it + rs.p.iter_offset;
         // sync reads lab_in only; async reads lab_out for neighbours of
         // earlier waves (written by this iteration's earlier launches)
-        a.lab_in = lab[rs.cur];
-        a.lab_out = lab[rs.cur ^ 1];
+        a.lab_in = lab[cur];
+        a.lab_out = lab[cur ^ 1];
         a.changed = changed + (int64_t)it * G;
         a.key_t = stream_at(rs.p.seed, (uint64_t)t + 1);
         for (int launch_i = 0; launch_i < waves * NUM_BUCKETS; ++launch_i) {
@@ -776,28 +782,200 @@ struct GraphSet {
             // labels read in the first sweep from unique labels rarely hold a
             // majority of a row
             a.majority = !(it == 0 && !rs.p.init_labels);
-            if (rs.prof) {
+            if (prof) {
                 while (prof_ev.size() < 2 * (rs.prof_launch.size() + 1)) {
                     cudaEvent_t e;
                     LP_CU(cudaEventCreate(&e));
                     prof_ev.push_back(e);
                 }
-                LP_CU(cudaEventRecord(prof_ev[2 * rs.prof_launch.size()], st));
+                LP_CU(cudaEventRecord(prof_ev[2 * rs.prof_launch.size()], s));
             }
-            const int nk = sweep_launch(b, a, rs.multi, num_sms, st);
+            const int nk = sweep_launch(b, a, rs.multi, num_sms, s);
             if (nk < 0) return fail(LP_ECUDA, cuda_msg("sweep launch", cudaGetLastError()));
-            L.n += nk;
-            if (rs.prof) {
-                LP_CU(cudaEventRecord(prof_ev[2 * rs.prof_launch.size() + 1], st));
+            *kernels += nk;
+            if (prof) {
+                LP_CU(cudaEventRecord(prof_ev[2 * rs.prof_launch.size() + 1], s));
                 rs.prof_launch.push_back(b);
                 rs.prof_len.push_back(a.len);
             }
         }
-        LP_CU(cudaMemcpyAsync(h_changed + (int64_t)it * G, a.changed, (size_t)G * sizeof(int32_t),
-                              cudaMemcpyDeviceToHost, st));
+        return LP_OK;
+    }
+
+    // launch one iteration and the read of its changed counters; ev_iter
+    // marks its end
+    lp_status run_launch()
+    {
+        Launches L;
+        const int32_t it = rs.it;
+        LP_TRY(launch_sweeps(st, it, rs.cur, rs.prof, &L.n));
+        LP_CU(cudaMemcpyAsync(h_changed + (int64_t)it * G, changed + (int64_t)it * G,
+                              (size_t)G * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         LP_CU(cudaEventRecord(ev_iter, st));
         rs.it = it + 1;
         return LP_OK;
+    }
+
+    // ------------------------------------------------------------------
+    // A whole run as one CUDA graph: iteration i is a conditional (if) node
+    // holding its sweeps and the device-side tolerance test, which arms
+    // node i + 1 only while some graph goes on.  Built once per parameter
+    // set and replayed; used whenever per-launch profiling is off.
+    // ------------------------------------------------------------------
+    struct GraphKey {
+        double tolerance = -1.0;
+        int32_t max_iter = 0, mode = -1, strict = -1, iter_offset = 0, waves = 0;
+        uint64_t seed = 0;
+        bool init = false, multi = false;
+        bool operator==(const GraphKey &o) const
+        {
+            return tolerance == o.tolerance && max_iter == o.max_iter && mode == o.mode &&
+                   strict == o.strict && iter_offset == o.iter_offset && waves == o.waves &&
+                   seed == o.seed && init == o.init && multi == o.multi;
+        }
+    };
+    GraphKey gr_key{};
+    GraphKey gr_last{};  // parameters of the previous run
+
+    GraphKey key_of(const lp_rak_params *p, bool multi) const
+    {
+        GraphKey k;
+        k.tolerance = p->tolerance;
+        k.max_iter = p->max_iter;
+        k.mode = p->mode;
+        k.strict = p->strict ? 1 : 0;
+        k.iter_offset = p->iter_offset;
+        k.waves = p->mode == LP_ASYNC ? std::min(p->waves, std::max(max_n, 1)) : 1;
+        k.seed = p->seed;
+        k.init = p->init_labels != nullptr;
+        k.multi = multi;
+        return k;
+    }
+
+    // true when this run repeats the previous run's parameters (or a run
+    // graph for them exists)
+    bool repeat_key(const lp_rak_params *p, bool multi)
+    {
+        if (!p) return false;
+        const GraphKey k = key_of(p, multi);
+        const bool rep = (gr_exec && k == gr_key) || k == gr_last;
+        gr_last = k;
+        return rep;
+    }
+    cudaGraph_t gr_graph = nullptr;
+    cudaGraphExec_t gr_exec = nullptr;
+    cudaStream_t gr_stream = nullptr;  // capture stream
+    int64_t gr_kernels_per_iter = 0;
+    int32_t *d_res = nullptr, *h_res = nullptr;  // iterations | converged | final | last (x2)
+
+    RunResults run_results() const
+    {
+        RunResults r;
+        r.iterations = d_res;
+        r.converged = d_res + G;
+        r.final_buf = d_res + 2 * (int64_t)G;
+        r.last_changed = reinterpret_cast<long long *>(d_res + 4 * (int64_t)G);
+        return r;
+    }
+
+    void drop_graph()
+    {
+        if (gr_exec) cudaGraphExecDestroy(gr_exec);
+        if (gr_graph) cudaGraphDestroy(gr_graph);
+        gr_exec = nullptr;
+        gr_graph = nullptr;
+        gr_key = GraphKey{};
+    }
+
+    lp_status ensure_graph()
+    {
+        const GraphKey k = key_of(&rs.p, rs.multi);
+        if (gr_exec && k == gr_key) return LP_OK;
+        drop_graph();
+        if (!gr_stream) LP_CU(cudaStreamCreateWithFlags(&gr_stream, cudaStreamNonBlocking));
+        if (!d_res) {
+            LP_TRY(dev_alloc(&d_res, 6 * (int64_t)G, "run results", st, device));
+            LP_TRY(host_alloc(&h_res, 6 * (int64_t)G, "run results"));
+        }
+        LP_CU(cudaGraphCreate(&gr_graph, 0));
+        const int32_t n_it = rs.p.max_iter;
+        std::vector<cudaGraphConditionalHandle> h((size_t)n_it);
+        for (int32_t it = 0; it < n_it; ++it)
+            LP_CU(cudaGraphConditionalHandleCreate(&h[(size_t)it], gr_graph, it == 0 ? 1u : 0u,
+                                                   cudaGraphCondAssignDefault));
+        const RunResults res = run_results();
+        cudaGraphNode_t prev = nullptr;
+        for (int32_t it = 0; it < n_it; ++it) {
+            cudaGraphNodeParams cp{};
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = h[(size_t)it];
+            cp.conditional.type = cudaGraphCondTypeIf;
+            cp.conditional.size = 1;
+            cudaGraphNode_t node;
+            LP_CU(cudaGraphAddNode(&node, gr_graph, prev ? &prev : nullptr, nullptr, prev ? 1 : 0,
+                                   &cp));
+            cudaGraph_t body = cp.conditional.phGraph_out[0];
+            LP_CU(cudaStreamBeginCaptureToGraph(gr_stream, body, nullptr, nullptr, 0,
+                                                cudaStreamCaptureModeThreadLocal));
+            int64_t nk = 0;
+            lp_status ls = launch_sweeps(gr_stream, it, it & 1, false, &nk);
+            if (ls == LP_OK &&
+                converge_launch(changed + (int64_t)it * G, g_n, g_active, G, rs.p.tolerance, it,
+                                rs.multi, res, it + 1 < n_it ? h[(size_t)it + 1] : h[0],
+                                it + 1 < n_it, gr_stream) != 0)
+                ls = fail(LP_ECUDA, cuda_msg("convergence launch", cudaGetLastError()));
+            cudaGraph_t captured = nullptr;
+            const cudaError_t ce = cudaStreamEndCapture(gr_stream, &captured);
+            if (ls != LP_OK) {
+                drop_graph();
+                return ls;
+            }
+            if (ce != cudaSuccess) {
+                drop_graph();
+                return fail(LP_ECUDA, cuda_msg("run capture", ce));
+            }
+            gr_kernels_per_iter = nk + 1;
+            prev = node;
+        }
+        const cudaError_t ie = cudaGraphInstantiate(&gr_exec, gr_graph, 0);
+        if (ie != cudaSuccess) {
+            gr_exec = nullptr;
+            drop_graph();
+            return fail(LP_ECUDA, cuda_msg("run graph instantiation", ie));
+        }
+        gr_key = k;
+        return LP_OK;
+    }
+
+    // Sec. 3.2's iteration over every graph of the set, launched as one graph
+    lp_status run_graph(const lp_rak_params *p, bool multi)
+    {
+        LP_TRY(run_begin(p, multi));
+        LP_TRY(ensure_graph());
+        const size_t res_bytes = 6 * (size_t)G * sizeof(int32_t);
+        LP_CU(cudaMemsetAsync(d_res, 0, res_bytes, st));
+        LP_CU(cudaGraphLaunch(gr_exec, st));
+        LP_CU(cudaMemcpyAsync(h_res, d_res, res_bytes, cudaMemcpyDeviceToHost, st));
+        LP_CU(cudaMemcpyAsync(h_changed, changed, (size_t)rs.p.max_iter * G * sizeof(int32_t),
+                              cudaMemcpyDeviceToHost, st));
+        LP_CU(cudaEventRecord(ev_iter, st));
+        LP_CU(cudaEventSynchronize(ev_iter));
+        const long long *last = reinterpret_cast<const long long *>(h_res + 4 * (int64_t)G);
+        int32_t ran = 0;
+        rs.active_left = 0;
+        for (int32_t g = 0; g < G; ++g) {
+            lp_rak_result &r = results[(size_t)g];
+            r.iterations = h_res[g];
+            r.converged = h_res[G + g];
+            r.last_changed = last[g];
+            final_buf[(size_t)g] = h_res[2 * (int64_t)G + g];
+            ran = std::max(ran, r.iterations);
+            if (!r.converged) ++rs.active_left;
+        }
+        rs.it = ran;
+        rs.cur = ran & 1;
+        g_launches += (int64_t)ran * gr_kernels_per_iter;
+        return run_end();
     }
 
     // a6 after the launched iteration has finished on the device
@@ -861,9 +1039,14 @@ struct GraphSet {
         return LP_OK;
     }
 
-    // Sec. 3.2 iteration over every graph of the set, to the end
+    // Sec. 3.2 iteration over every graph of the set, to the end: one graph
+    // launch, or (while per-launch profiling is on) one host round trip per
+    // iteration with events around every sweep launch
     lp_status run(const lp_rak_params *p, bool multi)
     {
+        // capturing a run costs about as much as a run of a mid-size graph, so
+        // a graph is captured once the same parameters come back
+        if (!g_prof_on.load() && repeat_key(p, multi)) return run_graph(p, multi);
         LP_TRY(run_begin(p, multi));
         while (!run_done()) {
             LP_TRY(run_launch());

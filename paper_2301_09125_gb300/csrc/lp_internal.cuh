@@ -243,6 +243,19 @@ int fill_iota(int32_t *lab, int32_t nv, const int32_t *vgraph, const int32_t *g_
 int check_labels(const int32_t *lab, int32_t nv, const int32_t *vgraph, const int32_t *g_vbase,
                  const int32_t *g_n, IngestOut *d_out, cudaStream_t st, int64_t *launches);
 
+// Per-graph results of a run captured as a CUDA graph (device arrays of G).
+struct RunResults {
+    int32_t *iterations;
+    int32_t *converged;
+    int32_t *final_buf;      // label buffer holding the final labels
+    long long *last_changed;
+};
+// The tolerance test of iteration `it` on the device (Sec. 3.2); arms `next`
+// (the following iteration's conditional node) if some graph goes on.
+int converge_launch(const int32_t *changed_it, const int32_t *g_n, int32_t *g_active, int32_t G,
+                    double tolerance, int32_t it, bool multi, const RunResults &res,
+                    cudaGraphConditionalHandle next, bool has_next, cudaStream_t st);
+
 // Entry and square passes of the modularity of every graph of a set.
 int modularity_launch(const ModArgs &a, const int64_t *bucket_begin, const int64_t *bucket_len,
                       int64_t nslots, bool multi, int num_sms, cudaStream_t st, int64_t *launches);

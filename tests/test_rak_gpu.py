@@ -396,6 +396,60 @@ def test_batch_matches_single_graph_runs(lp):
         lp.lp_batch_destroy(h)
 
 
+def test_graph_launch_and_host_loop_agree(lp):
+    """A run that repeats the previous run's parameters is one CUDA graph
+    launch (a conditional node per iteration, the tolerance test on the
+    device); other runs, and every run while per-launch profiling is on, are
+    driven by the host iteration by iteration.  Both give identical results,
+    for a batch and for single graphs, also when a captured graph is replayed
+    and when it is rebuilt for other parameters."""
+    params = gg.batch_sbm_params(count=12, seed=91, n_lo=300, n_hi=4000)
+    graphs = gg.batch_sbm(params)
+    graphs[2] = gg.rmat(11, seed=4)
+    triples = [(g.offsets, g.indices, g.weights) for g in graphs]
+
+    def batch_run(mode, waves):
+        h = lp.lp_batch_create(triples)
+        try:
+            out = []
+            for rep in range(2):  # the second call reuses the captured graph
+                res = lp.lp_batch_run(h, len(graphs), tolerance=0.02, max_iter=15, mode=mode,
+                                      waves=waves, strict=False, seed=5)
+                out.append([(r.iterations, r.converged, r.last_changed) for r in res] +
+                           [lp.lp_batch_labels_get(h, i, g.n).tolist()
+                            for i, g in enumerate(graphs)])
+            assert out[0] == out[1]
+            return out[0]
+        finally:
+            lp.lp_batch_destroy(h)
+
+    for mode, waves in (("sync", 31), ("async", 3)):
+        graph_mode = batch_run(mode, waves)
+        lp.lp_profile_enable(True)
+        try:
+            host_loop = batch_run(mode, waves)
+        finally:
+            lp.lp_profile_enable(False)
+        assert graph_mode == host_loop
+
+    # single graph: a run repeating the previous run's parameters is captured
+    # (first repeat) and replayed (later repeats); profiled runs are host-driven
+    g = gg.rmat(13, seed=6)
+    with lp.Graph(g.offsets, g.indices, g.weights) as G:
+        for kw in (dict(mode="sync"), dict(mode="async", waves=2),
+                   dict(mode="sync", tolerance=0.0, max_iter=4), dict(mode="sync")):
+            runs = []
+            for prof in (False, False, False, True):
+                lp.lp_profile_enable(prof)
+                try:
+                    r = G.rak(**kw)
+                finally:
+                    lp.lp_profile_enable(False)
+                runs.append((r.iterations, r.converged, r.last_changed, G.history().tolist(),
+                             G.labels().tolist()))
+            assert all(x == runs[0] for x in runs), kw
+
+
 # ---------------------------------------------------------------- full-size workloads
 def sampled_sync_check(lp, g, strict, seed, samples=20_000):
     """Two sweeps at full size; each output of the second sweep is checked at
