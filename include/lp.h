@@ -200,6 +200,44 @@ lp_status lp_batch_destroy(lp_batch *b);
  * Errors: as lp_rak_run. */
 lp_status lp_batch_run(lp_batch *b, const lp_rak_params *p, lp_rak_result *per_graph);
 
+/* ---------------------------------------------------------------------------
+ * Bucket autotuning (no counterpart in the paper, which runs on a CPU).
+ * Vertices are sorted into degree buckets, each swept by its own kernel
+ * (several short rows per warp; one warp per row; one 128-, 256- or 512-thread
+ * CTA per row; segments for the longest rows).  The autotuner times `sweeps`
+ * iterations (tolerance 0, from unique labels, with p's mode / waves / tie
+ * rule / seed) for each of 16 choices of the buckets' largest degrees within
+ * the kernels' capacities (small <= 32, warp <= 128, cta <= 512, cta2 <= 1024)
+ * and keeps the fastest.  Results of later runs do not depend on the choice.
+ * Labels are left in an unspecified state; the next run starts afresh.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int32_t small_max;   /* chosen largest degree of the small bucket */
+    int32_t warp_max;    /* ... of the warp bucket */
+    int32_t cta_max;     /* ... of the 128-thread CTA bucket */
+    int32_t cta2_max;    /* ... of the 256-thread CTA bucket */
+    int32_t candidates;  /* choices timed */
+    float default_ms;    /* timed iterations with the default bounds (32/128/512/1024) */
+    float best_ms;       /* timed iterations with the chosen bounds */
+} lp_tune_result;
+
+/* Autotune a batch's buckets (p->init_labels must be NULL; 1 <= sweeps <= 100).
+ * Errors: LP_EINVAL on NULL arguments or a bad parameter; LP_ENOMEM; LP_ECUDA. */
+lp_status lp_batch_autotune(lp_batch *b, const lp_rak_params *p, int32_t sweeps,
+                            lp_tune_result *out);
+
+/* Autotune a single graph's buckets (p->init_labels is ignored).
+ * Errors: as lp_batch_autotune. */
+lp_status lp_graph_autotune(lp_graph *g, const lp_rak_params *p, int32_t sweeps,
+                            lp_tune_result *out);
+
+/* Set the buckets' largest degrees directly (max_degree[4]: small, warp,
+ * cta, cta2; non-decreasing, >= 1, at most 32 / 128 / 512 / 1024), e.g. an
+ * autotuning result from a similar graph.
+ * Errors: LP_EINVAL on NULL or out-of-range bounds; LP_ENOMEM; LP_ECUDA. */
+lp_status lp_graph_set_buckets(lp_graph *g, const int32_t *max_degree);
+lp_status lp_batch_set_buckets(lp_batch *b, const int32_t *max_degree);
+
 /* Labels of graph `index` after the last lp_batch_run (n_index int32).
  * Errors: LP_EINVAL on NULL or index out of range; LP_ECUDA. */
 lp_status lp_batch_labels_get(lp_batch *b, int32_t index, int32_t *dst, int32_t dst_on_device);

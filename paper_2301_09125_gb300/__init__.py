@@ -10,10 +10,11 @@ the thin Python binding of that ABI; build the library with
 from ._binding import (  # noqa: F401
     LP_ASYNC, LP_EINVAL, LP_ECUDA, LP_ENOMEM, LP_ENOTREADY, LP_ETIMEOUT, LP_FLAG_BORROW,
     LP_FLAG_CHECK_SYMMETRIC, LP_FLAG_DEVICE_PTRS, LP_OK, LP_SYNC, SIGNATURES, Graph, LPError,
-    load, lp_batch_create, lp_batch_destroy, lp_batch_labels_get, lp_batch_modularity,
-    lp_batch_run, lp_graph_create, lp_graph_destroy, lp_graph_info, lp_labels_get,
+    load, lp_batch_autotune, lp_batch_create, lp_batch_destroy, lp_batch_labels_get,
+    lp_batch_modularity, lp_batch_run, lp_batch_set_buckets, lp_graph_autotune,
+    lp_graph_create, lp_graph_set_buckets, lp_graph_destroy, lp_graph_info, lp_labels_get,
     lp_last_error, lp_launch_count, lp_modularity, lp_profile_enable, lp_profile_read,
     lp_profile_reset, lp_rak_history, lp_rak_params,
     lp_rak_params_default, lp_rak_result, lp_rak_run, lp_rak_sweep_noalloc, lp_serve_result,
     lp_server_config, lp_server_config_default, lp_server_create, lp_server_destroy,
-    lp_server_drain, lp_server_poll, lp_server_submit, make_params)
+    lp_server_drain, lp_server_poll, lp_server_submit, lp_tune_result, make_params)

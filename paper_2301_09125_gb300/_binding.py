@@ -76,6 +76,16 @@ class lp_kernel_stat(ctypes.Structure):
                 ("entries", ctypes.c_double), ("bytes", ctypes.c_double)]
 
 
+class lp_tune_result(ctypes.Structure):
+    _fields_ = [("small_max", ctypes.c_int32), ("warp_max", ctypes.c_int32),
+                ("cta_max", ctypes.c_int32), ("cta2_max", ctypes.c_int32),
+                ("candidates", ctypes.c_int32), ("default_ms", ctypes.c_float),
+                ("best_ms", ctypes.c_float)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _lib = None
 
 # Every symbol include/lp.h declares, with its ctypes signature.
@@ -98,6 +108,12 @@ SIGNATURES = {
     "lp_batch_destroy": (ctypes.c_int, [_P]),
     "lp_batch_run": (ctypes.c_int, [_P, ctypes.POINTER(lp_rak_params),
                                     ctypes.POINTER(lp_rak_result)]),
+    "lp_batch_autotune": (ctypes.c_int, [_P, ctypes.POINTER(lp_rak_params), ctypes.c_int32,
+                                         ctypes.POINTER(lp_tune_result)]),
+    "lp_graph_autotune": (ctypes.c_int, [_P, ctypes.POINTER(lp_rak_params), ctypes.c_int32,
+                                         ctypes.POINTER(lp_tune_result)]),
+    "lp_graph_set_buckets": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32)]),
+    "lp_batch_set_buckets": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32)]),
     "lp_batch_labels_get": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int32]),
     "lp_batch_modularity": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]),
     "lp_server_config_default": (ctypes.c_int, [ctypes.POINTER(lp_server_config)]),
@@ -309,6 +325,40 @@ def lp_batch_destroy(handle: Optional[int]) -> None:
         _check(load().lp_batch_destroy(handle))
 
 
+def lp_batch_autotune(handle: int, params: Optional[lp_rak_params] = None, sweeps: int = 5,
+                      **kw) -> lp_tune_result:
+    """Pick the batch's bucket bounds by timing `sweeps` iterations of each
+    candidate (keyword arguments as for make_params)."""
+    if params is None:
+        params, _ = make_params(**kw)
+    out = lp_tune_result()
+    _check(load().lp_batch_autotune(handle, ctypes.byref(params), int(sweeps), ctypes.byref(out)))
+    return out
+
+
+def lp_graph_autotune(handle: int, params: Optional[lp_rak_params] = None, sweeps: int = 5,
+                      **kw) -> lp_tune_result:
+    """Pick a graph's bucket bounds by timing `sweeps` iterations of each
+    candidate (keyword arguments as for make_params)."""
+    if params is None:
+        params, _ = make_params(**kw)
+    out = lp_tune_result()
+    _check(load().lp_graph_autotune(handle, ctypes.byref(params), int(sweeps), ctypes.byref(out)))
+    return out
+
+
+def lp_graph_set_buckets(handle: int, max_degree) -> None:
+    """Set the largest degree of the small / warp / cta / cta2 buckets."""
+    arr = (ctypes.c_int32 * 4)(*[int(x) for x in max_degree])
+    _check(load().lp_graph_set_buckets(handle, arr))
+
+
+def lp_batch_set_buckets(handle: int, max_degree) -> None:
+    """Set the largest degree of the small / warp / cta / cta2 buckets."""
+    arr = (ctypes.c_int32 * 4)(*[int(x) for x in max_degree])
+    _check(load().lp_batch_set_buckets(handle, arr))
+
+
 def lp_batch_run(handle: int, count: int, params: Optional[lp_rak_params] = None, **kw):
     """Run every graph of a batch; returns the per-graph results."""
     if params is None:
@@ -442,6 +492,12 @@ class Graph:
 
     def rak(self, **kw) -> lp_rak_result:
         return lp_rak_run(self.handle, **kw)
+
+    def autotune(self, sweeps: int = 5, **kw) -> lp_tune_result:
+        return lp_graph_autotune(self.handle, sweeps=sweeps, **kw)
+
+    def set_buckets(self, max_degree) -> None:
+        lp_graph_set_buckets(self.handle, max_degree)
 
     def labels(self, out=None):
         return lp_labels_get(self.handle, out)

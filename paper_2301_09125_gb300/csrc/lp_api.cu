@@ -217,6 +217,7 @@ struct GraphSet {
     bool own_off = true, own_idx = true, own_wts = true;
     int32_t *lab[2] = {nullptr, nullptr};
     int32_t *list = nullptr;
+    Thresholds th{};  // bucket bounds (defaults, or the autotuner's choice)
     int64_t bb[NUM_BUCKETS] = {}, bl[NUM_BUCKETS] = {};
     int64_t be[NUM_BUCKETS] = {};  // summed degree of each bucket
     // wave-partitioned bucket lists for asynchronous runs (built per wave count)
@@ -450,7 +451,7 @@ struct GraphSet {
             cudaFreeAsync(blk, st);
             return LP_ENOMEM;
         }
-        if (ingest_bucket(off, nv, vgraph, g_vbase, list, blk, d_counts, st, &L.n) != 0)
+        if (ingest_bucket(off, nv, vgraph, g_vbase, th, list, blk, d_counts, st, &L.n) != 0)
             s = fail(LP_ECUDA, cuda_msg("bucketing launch", cudaGetLastError()));
         if (s == LP_OK) {
             cudaError_t e = cudaMemcpyAsync(h_counts, d_counts, 3 * NUM_BUCKETS * sizeof(int64_t),
@@ -523,6 +524,104 @@ struct GraphSet {
             LP_CU(cudaMemsetAsync(hnused, 0, (size_t)bl[HUB_BUCKET] * sizeof(int32_t), st));
             LP_CU(cudaStreamSynchronize(st));
         }
+        return LP_OK;
+    }
+
+    // Sort the vertices into buckets again with other bounds: every list
+    // derived from the buckets (hub tasks and scratch, wave lists, captured
+    // run graphs) is dropped and rebuilt on demand.
+    lp_status rebucket(const Thresholds &t)
+    {
+        LP_CU(cudaStreamSynchronize(st));
+        auto f = [this](void *p) {
+            if (p) cudaFreeAsync(p, st);
+        };
+        f(list);
+        f(htask);
+        f(htask_w);
+        f(hrec);
+        f(hpoff);
+        f(hpbest);
+        f(hkey);
+        f(hnpos);
+        f(hused);
+        f(hdone);
+        f(hnused);
+        f(hseg_task);
+        f(hpart_task);
+        f(hseg_task_w);
+        f(hpart_task_w);
+        f(wlist);
+        list = wlist = nullptr;
+        htask = htask_w = nullptr;
+        hrec = nullptr;
+        hpoff = nullptr;
+        hpbest = nullptr;
+        hkey = nullptr;
+        hnpos = nullptr;
+        hused = hdone = hnused = nullptr;
+        hseg_task = hpart_task = hseg_task_w = hpart_task_w = nullptr;
+        hmulti = hsegs = hparts = 0;
+        wl_waves = 0;
+        drop_graph();
+        gr_last = GraphKey{};
+        th = t;
+        return bucket();
+    }
+
+    // Time `sweeps` iterations (tolerance 0, from unique labels) for a grid
+    // of bucket bounds within the kernels' capacities and keep the fastest.
+    // Labels, iteration counts and modularity do not depend on the bounds.
+    lp_status autotune(const lp_rak_params *p, bool multi, int32_t sweeps, lp_tune_result *out)
+    {
+        if (!p || !out) return fail(LP_EINVAL, "params or out is NULL");
+        if (sweeps < 1 || sweeps > 100) return fail(LP_EINVAL, "sweeps must lie in [1, 100]");
+        lp_rak_params q = *p;
+        q.tolerance = 0.0;
+        q.max_iter = sweeps;
+        q.iter_offset = 0;
+        q.init_labels = nullptr;
+        const Thresholds def{};
+        auto timed = [&](const Thresholds &t, float *ms) -> lp_status {
+            LP_TRY(rebucket(t));
+            LP_TRY(run_host(&q, multi));
+            *ms = results[0].gpu_ms;
+            return LP_OK;
+        };
+        const int32_t small_c[] = {8, 16, 24, SMALL_MAX};
+        const int32_t warp_c[] = {64, WARP_MAX};
+        const int32_t cta_c[] = {256, CTA_MAX};
+        Thresholds best = def;
+        float best_ms = 0.f;
+        LP_TRY(timed(def, &best_ms));
+        out->default_ms = best_ms;
+        int32_t n = 1;
+        for (int32_t a : small_c)
+            for (int32_t b : warp_c)
+                for (int32_t c : cta_c) {
+                    Thresholds t;
+                    t.max[0] = a;
+                    t.max[1] = b;
+                    t.max[2] = c;
+                    t.max[3] = CTA2_MAX;
+                    bool same = true;
+                    for (int k = 0; k < NUM_BUCKETS - 1; ++k) same = same && t.max[k] == def.max[k];
+                    if (same) continue;
+                    float ms = 0.f;
+                    LP_TRY(timed(t, &ms));
+                    ++n;
+                    if (ms < best_ms) {
+                        best_ms = ms;
+                        best = t;
+                    }
+                }
+        LP_TRY(rebucket(best));
+        out->small_max = best.max[0];
+        out->warp_max = best.max[1];
+        out->cta_max = best.max[2];
+        out->cta2_max = best.max[3];
+        out->candidates = n;
+        out->best_ms = best_ms;
         return LP_OK;
     }
 
@@ -1047,6 +1146,11 @@ struct GraphSet {
         // capturing a run costs about as much as a run of a mid-size graph, so
         // a graph is captured once the same parameters come back
         if (!g_prof_on.load() && repeat_key(p, multi)) return run_graph(p, multi);
+        return run_host(p, multi);
+    }
+
+    lp_status run_host(const lp_rak_params *p, bool multi)
+    {
         LP_TRY(run_begin(p, multi));
         while (!run_done()) {
             LP_TRY(run_launch());
@@ -1275,6 +1379,14 @@ lp_status lp_graph_create(int32_t n, int64_t m, const int32_t *offsets, const in
     return LP_OK;
 }
 
+lp_status lp_graph_autotune(lp_graph *g, const lp_rak_params *p, int32_t sweeps,
+                            lp_tune_result *out)
+{
+    if (!g) return fail(LP_EINVAL, "graph is NULL");
+    DeviceGuard dg(g->s.device);
+    return g->s.autotune(p, false, sweeps, out);
+}
+
 lp_status lp_graph_destroy(lp_graph *g)
 {
     if (!g) return LP_OK;
@@ -1469,6 +1581,47 @@ lp_status lp_batch_run(lp_batch *b, const lp_rak_params *p, lp_rak_result *per_g
     if (per_graph)
         for (int32_t i = 0; i < b->s.G; ++i) per_graph[i] = b->s.results[(size_t)i];
     return LP_OK;
+}
+
+namespace {
+lp_status set_buckets(lp::GraphSet &s, const int32_t *max_degree)
+{
+    if (!max_degree) return fail(LP_EINVAL, "max_degree is NULL");
+    const int32_t cap[lp::NUM_BUCKETS - 1] = {lp::SMALL_MAX, lp::WARP_MAX, lp::CTA_MAX,
+                                               lp::CTA2_MAX};
+    lp::Thresholds t;
+    int32_t prev = 1;
+    for (int k = 0; k < lp::NUM_BUCKETS - 1; ++k) {
+        if (max_degree[k] < prev || max_degree[k] > cap[k])
+            return fail(LP_EINVAL, "bucket bounds must be non-decreasing, >= 1 and within "
+                                   "32 / 128 / 512 / 1024");
+        t.max[k] = prev = max_degree[k];
+    }
+    return s.rebucket(t);
+}
+}  // namespace
+
+lp_status lp_graph_set_buckets(lp_graph *g, const int32_t *max_degree)
+{
+    if (!g) return fail(LP_EINVAL, "graph is NULL");
+    DeviceGuard dg(g->s.device);
+    return set_buckets(g->s, max_degree);
+}
+
+lp_status lp_batch_set_buckets(lp_batch *b, const int32_t *max_degree)
+{
+    if (!b) return fail(LP_EINVAL, "batch is NULL");
+    DeviceGuard dg(b->s.device);
+    return set_buckets(b->s, max_degree);
+}
+
+lp_status lp_batch_autotune(lp_batch *b, const lp_rak_params *p, int32_t sweeps,
+                            lp_tune_result *out)
+{
+    if (!b) return fail(LP_EINVAL, "batch is NULL");
+    DeviceGuard dg(b->s.device);
+    if (p && p->init_labels) return fail(LP_EINVAL, "batches start from unique labels");
+    return b->s.autotune(p, true, sweeps, out);
 }
 
 lp_status lp_batch_labels_get(lp_batch *b, int32_t index, int32_t *dst, int32_t dst_on_device)

@@ -162,9 +162,13 @@ __global__ void k_check_row_order(const int32_t *idx, int64_t ne, const uint32_t
     if (__any_sync(FULL, bad) && (threadIdx.x & 31) == 0) atomicExch(&o->repeated, 1);
 }
 
-__device__ __forceinline__ int bucket_of(int32_t d)
+__device__ __forceinline__ int bucket_of(int32_t d, const Thresholds &th)
 {
-    return d <= 0 ? -1 : d <= SMALL_MAX ? 0 : d <= WARP_MAX ? 1 : d <= CTA_MAX ? 2 : d <= CTA2_MAX ? 3 : 4;
+    if (d <= 0) return -1;
+#pragma unroll
+    for (int b = 0; b < NUM_BUCKETS - 1; ++b)
+        if (d <= th.max[b]) return b;
+    return NUM_BUCKETS - 1;
 }
 
 // graph g's row pointer entries start at off[vbase_g + g], so global vertex v
@@ -176,8 +180,8 @@ __device__ __forceinline__ int32_t degree_of(const int32_t *off, const int32_t *
 }
 
 __global__ void __launch_bounds__(BK) k_bucket_count(const int32_t *off, int32_t nv,
-                                                      const int32_t *vgraph, int32_t *blk,
-                                                      unsigned long long *entries)
+                                                      const int32_t *vgraph, Thresholds th,
+                                                      int32_t *blk, unsigned long long *entries)
 {
     __shared__ int cnt[NUM_BUCKETS];
     __shared__ unsigned long long ent[NUM_BUCKETS];
@@ -188,7 +192,7 @@ __global__ void __launch_bounds__(BK) k_bucket_count(const int32_t *off, int32_t
     __syncthreads();
     const int64_t v = (int64_t)blockIdx.x * BK + threadIdx.x;
     const int32_t d = v < nv ? degree_of(off, vgraph, (int32_t)v) : 0;
-    const int b = bucket_of(d);
+    const int b = bucket_of(d, th);
     // one shared atomic per warp and bucket (rows of every bucket but the last
     // are short enough for a 32-bit warp sum)
 #pragma unroll
@@ -270,13 +274,14 @@ __global__ void __launch_bounds__(BK) k_bucket_scan(int32_t *blk, int64_t nblk, 
 }
 
 __global__ void __launch_bounds__(BK) k_bucket_scatter(const int32_t *off, int32_t nv,
-                                                        const int32_t *vgraph, const int32_t *blk,
-                                                        const int64_t *cnt, int32_t *list)
+                                                        const int32_t *vgraph, Thresholds th,
+                                                        const int32_t *blk, const int64_t *cnt,
+                                                        int32_t *list)
 {
     __shared__ int s_pre[NUM_BUCKETS][BK / 32];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int64_t v = (int64_t)blockIdx.x * BK + threadIdx.x;
-    const int b = v < nv ? bucket_of(degree_of(off, vgraph, (int32_t)v)) : -1;
+    const int b = v < nv ? bucket_of(degree_of(off, vgraph, (int32_t)v), th) : -1;
     int rank = 0;
 #pragma unroll
     for (int c = 0; c < NUM_BUCKETS; ++c) {
@@ -562,17 +567,18 @@ size_t ingest_bucket_scratch_bytes(int32_t nv_total)
 }
 
 int ingest_bucket(const int32_t *off, int32_t nv, const int32_t *vgraph, const int32_t *,
-                  int32_t *list, int32_t *blk, int64_t *d_counts, cudaStream_t st,
-                  int64_t *launches)
+                  const Thresholds &th, int32_t *list, int32_t *blk, int64_t *d_counts,
+                  cudaStream_t st, int64_t *launches)
 {
     const int64_t nblk = ((int64_t)nv + BK - 1) / BK;
     if (cudaMemsetAsync(d_counts, 0, 3 * NUM_BUCKETS * sizeof(int64_t), st) != cudaSuccess)
         return -1;
     if (nblk == 0) return 0;
     k_bucket_count<<<(int)nblk, BK, 0, st>>>(
-        off, nv, vgraph, blk, reinterpret_cast<unsigned long long *>(d_counts + 2 * NUM_BUCKETS));
+        off, nv, vgraph, th, blk,
+        reinterpret_cast<unsigned long long *>(d_counts + 2 * NUM_BUCKETS));
     k_bucket_scan<<<1, BK, 0, st>>>(blk, nblk, d_counts);
-    k_bucket_scatter<<<(int)nblk, BK, 0, st>>>(off, nv, vgraph, blk, d_counts, list);
+    k_bucket_scatter<<<(int)nblk, BK, 0, st>>>(off, nv, vgraph, th, blk, d_counts, list);
     *launches += 3;
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

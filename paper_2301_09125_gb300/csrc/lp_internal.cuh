@@ -31,6 +31,14 @@ constexpr int CTA2_MAX = 1024;  // 513..1024: one 256-thread CTA per vertex
 constexpr int NUM_BUCKETS = 5;  // small, warp, cta, cta2, hub
 constexpr int HUB_BUCKET = NUM_BUCKETS - 1;
 
+// Largest degree of each bucket but the hub bucket.  The defaults are the
+// constants above; a graph set may be re-bucketed with other values (the
+// autotuner), each at most its bucket kernel's capacity above and
+// non-decreasing.
+struct Thresholds {
+    int32_t max[NUM_BUCKETS - 1] = {SMALL_MAX, WARP_MAX, CTA_MAX, CTA2_MAX};
+};
+
 constexpr int WARP_TABLE = 256;         // slots per warp (>= 2 * WARP_MAX)
 constexpr int CTA_THREADS = 128;
 constexpr int CTA_TABLE = 1024;         // slots (>= 2 * CTA_MAX)
@@ -223,8 +231,9 @@ int degrees_of(const int32_t *off, const int32_t *vgraph, const int32_t *list, i
 // lengths, [B..2B) their starts in `list`, [2B..3B) their summed degrees
 // (B = NUM_BUCKETS).
 int ingest_bucket(const int32_t *off, int32_t nv_total, const int32_t *vgraph,
-                  const int32_t *g_vbase, int32_t *list, int32_t *scratch_blocks,
-                  int64_t *d_counts, cudaStream_t st, int64_t *launches);
+                  const int32_t *g_vbase, const Thresholds &th, int32_t *list,
+                  int32_t *scratch_blocks, int64_t *d_counts, cudaStream_t st,
+                  int64_t *launches);
 size_t ingest_bucket_scratch_bytes(int32_t nv_total);
 // Wave partition of the bucket lists for asynchronous runs: entries of bucket b
 // and wave k (= local vertex id mod waves) are gathered, class by class

@@ -450,6 +450,70 @@ def test_graph_launch_and_host_loop_agree(lp):
             assert all(x == runs[0] for x in runs), kw
 
 
+@pytest.mark.parametrize("bounds", [(8, 64, 256, 1024), (16, 128, 512, 1024), (1, 1, 1, 1),
+                                    (32, 32, 129, 513)])
+def test_bucket_bounds_keep_parity(lp, bounds):
+    """Any bucket bounds within the kernels' capacities give the oracle's
+    labels (sync and 2-wave async), for a single graph and a batch."""
+    g = gg.rmat(14, seed=17)
+    with lp.Graph(g.offsets, g.indices, g.weights) as G:
+        G.set_buckets(bounds)
+        for mode, waves in (("sync", 0), ("async", 2)):
+            kw = dict(waves=waves) if waves else {}
+            r = G.rak(tolerance=0.05, max_iter=20, mode=mode, strict=False, seed=3, **kw)
+            ref, iters, conv, hist = oracle.rak(g.offsets, g.indices, g.weights, 0.05, 20, mode,
+                                                strict=False, seed=3, waves=waves)
+            assert r.iterations == iters and np.array_equal(G.history(), hist)
+            assert np.array_equal(G.labels(), ref)
+    graphs = gg.batch_sbm(gg.batch_sbm_params(count=10, seed=55, n_lo=300, n_hi=3000))
+    graphs[1] = gg.rmat(10, seed=8)
+    h = lp.lp_batch_create([(x.offsets, x.indices, x.weights) for x in graphs])
+    try:
+        lp.lp_batch_set_buckets(h, bounds)
+        res = lp.lp_batch_run(h, len(graphs), tolerance=0.05, max_iter=20, mode="sync")
+        for i, x in enumerate(graphs):
+            ref, iters, conv, _ = oracle.rak(x.offsets, x.indices, x.weights, 0.05, 20, "sync")
+            assert res[i].iterations == iters
+            assert np.array_equal(lp.lp_batch_labels_get(h, i, x.n), ref), i
+    finally:
+        lp.lp_batch_destroy(h)
+
+
+def test_bucket_bounds_are_checked(lp):
+    g = gg.rmat(8, seed=1)
+    with lp.Graph(g.offsets, g.indices, g.weights) as G:
+        for bad in ((0, 64, 256, 1024), (33, 64, 256, 1024), (16, 8, 256, 1024),
+                    (16, 129, 256, 1024), (16, 64, 513, 1024), (16, 64, 256, 1025)):
+            with pytest.raises(lp.LPError):
+                G.set_buckets(bad)
+
+
+def test_autotune_then_run_matches_oracle(lp):
+    """The autotuner times 16 bucket choices and keeps the fastest; runs
+    after it still give the oracle's results."""
+    graphs = gg.batch_sbm(gg.batch_sbm_params(count=16, seed=66, n_lo=500, n_hi=5000))
+    h = lp.lp_batch_create([(x.offsets, x.indices, x.weights) for x in graphs])
+    try:
+        t = lp.lp_batch_autotune(h, sweeps=3, mode="sync")
+        assert t.candidates == 16 and t.best_ms <= t.default_ms
+        assert 1 <= t.small_max <= 32 and t.small_max <= t.warp_max <= 128
+        assert t.warp_max <= t.cta_max <= 512 and t.cta_max <= t.cta2_max <= 1024
+        res = lp.lp_batch_run(h, len(graphs), tolerance=0.05, max_iter=20, mode="sync")
+        for i, x in enumerate(graphs):
+            ref, iters, conv, _ = oracle.rak(x.offsets, x.indices, x.weights, 0.05, 20, "sync")
+            assert res[i].iterations == iters
+            assert np.array_equal(lp.lp_batch_labels_get(h, i, x.n), ref), i
+    finally:
+        lp.lp_batch_destroy(h)
+    g = gg.rmat(13, seed=23)
+    with lp.Graph(g.offsets, g.indices, g.weights) as G:
+        t = G.autotune(sweeps=3, mode="async", waves=2)
+        assert t.candidates == 16
+        G.rak(tolerance=0.05, max_iter=20, mode="async", waves=2)
+        ref, _, _, _ = oracle.rak(g.offsets, g.indices, g.weights, 0.05, 20, "async", waves=2)
+        assert np.array_equal(G.labels(), ref)
+
+
 # ---------------------------------------------------------------- full-size workloads
 def sampled_sync_check(lp, g, strict, seed, samples=20_000):
     """Two sweeps at full size; each output of the second sweep is checked at
