@@ -881,6 +881,8 @@ struct GraphSet {
             // labels read in the first sweep from unique labels rarely hold a
             // majority of a row
             a.majority = !(it == 0 && !rs.p.init_labels);
+            a.changed_prev = it > 0 ? changed + (int64_t)(it - 1) * G : nullptr;
+            a.g_n = g_n;
             if (prof) {
                 while (prof_ev.size() < 2 * (rs.prof_launch.size() + 1)) {
                     cudaEvent_t e;

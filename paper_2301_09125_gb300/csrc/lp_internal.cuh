@@ -92,9 +92,13 @@ struct SweepArgs {
     // row repeats a neighbour: a label's weight is then its one edge weight
     int identity;
     // 1 when a vertex whose own label holds more than half of its row's weight
-    // may keep it without a table (that label is then the unique maximum);
-    // set where labels have settled enough for the test to pay off
+    // may keep it without a table (that label is then the unique maximum).
+    // changed_prev (the previous iteration's changed count per graph, or
+    // null) and g_n (vertices per graph) let a kernel try the test only once
+    // labels have settled.
     int majority;
+    const int32_t *changed_prev;
+    const int32_t *g_n;
     // asynchronous waves (Sec. 3.3): this launch runs wave `wave_k` of `waves`;
     // a neighbour u of an earlier wave (u mod waves < wave_k) is read from
     // lab_out (this iteration), every other one from lab_in.  waves = 1: sync.

@@ -119,6 +119,19 @@ __device__ __forceinline__ int32_t ld_label(const int32_t *p)
     return r;
 }
 
+// Whether graph g's vertices try the majority test in this launch.  Kernels
+// that reuse the loaded row for their table path lose little when the test
+// fails and always try it; the small-row kernel reads its rows a second time
+// then, and tries it only after an iteration that changed fewer than a
+// quarter of the graph's labels (measured on R-MAT and SBM: by then most rows
+// hold an own-label majority).
+__device__ __forceinline__ bool try_majority(const SweepArgs &a, int32_t g, bool costly)
+{
+    if (!a.majority || a.identity) return false;
+    if (!costly || !a.changed_prev) return true;
+    return 4ll * __ldg(a.changed_prev + g) < (long long)__ldg(a.g_n + g);
+}
+
 // Label of neighbour u (local id u, global index gi) as seen by this launch.
 // Neither buffer is written at an address this launch reads: lab_in is only
 // written by the next iteration, and lab_out entries of earlier waves were
@@ -129,109 +142,6 @@ __device__ __forceinline__ int32_t neighbour_label(const SweepArgs &a, int64_t g
     return ld_label((earlier ? a.lab_out : a.lab_in) + gi);
 }
 
-
-// ----------------------------------------------------------------------------
-// small bucket: several rows per warp chunk
-// ----------------------------------------------------------------------------
-template <bool MULTI>
-__global__ void __launch_bounds__(256) k_small(SweepArgs a)
-{
-    const int lane = threadIdx.x & 31;
-    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    uint32_t my_changed = 0;
-
-    for (int64_t tile = wid; tile * 32 < a.len; tile += nw) {
-        const int64_t i = tile * 32 + lane;
-        Vtx x{0, 0, 0, 0, 0, 0, 0};
-        bool ok = false;
-        if (i < a.len) ok = load_vtx<MULTI>(a, a.list[i], x);
-        const int d = ok ? x.d : 0;
-        const int32_t own = ok ? x.own : 0;
-
-        int P = d;  // inclusive prefix of degrees over the tile
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(FULL, P, o);
-            if (lane >= o) P += y;
-        }
-        const int excl = P - d;
-        const int total_all = __shfl_sync(FULL, P, 31);
-
-        int start = 0, base = 0;
-        while (base < total_all && start < 32) {
-            // greedy packing: rows start.. that end within 32 entries of base
-            // (row `start` always fits: the bucket holds degrees <= 32)
-            const unsigned fits =
-                __ballot_sync(FULL, (lane >= start && P - base <= 32) || lane == start);
-            const int end = 32 - __clz(fits);
-            const int total = __shfl_sync(FULL, P, end - 1) - base;
-
-            // owner of entry `lane`: the last row in [start, end) starting at or before it
-            int o = start;
-#pragma unroll
-            for (int step = 16; step >= 1; step >>= 1) {
-                const int c = o + step;
-                const int ex = __shfl_sync(FULL, excl, c & 31);
-                if (c < end && ex - base <= lane) o = c;
-            }
-            const bool act = lane < total;
-            const int o_excl = __shfl_sync(FULL, excl, o);
-            const long long o_e0 = __shfl_sync(FULL, (long long)x.e0, o);
-            const int o_vb = MULTI ? __shfl_sync(FULL, x.vb, o) : 0;
-            const int o_lv = __shfl_sync(FULL, x.lv, o);
-            const int o_v = __shfl_sync(FULL, x.v, o);
-            const int32_t o_own = __shfl_sync(FULL, own, o);
-            const int pos = lane - (o_excl - base);
-
-            int w = 0;
-            int32_t l = EMPTY;
-            if (act) {
-                const long long e = o_e0 + pos;
-                const int32_t u = ld_entry(a.idx + e);
-                w = a.wts ? ld_entry(a.wts + e) : 1;
-                l = a.identity ? u : neighbour_label(a, (int64_t)o_vb + u, u);
-            }
-            // group equal (owner, label) pairs; the lowest lane holds the first
-            // position (in an identity sweep every pair is distinct)
-            const unsigned long long key =
-                act ? (((unsigned long long)(unsigned)o << 32) | (unsigned)l) : ~0ull;
-            const unsigned grp = a.identity ? (1u << lane) : __match_any_sync(FULL, key);
-            const int s = a.identity ? w : __reduce_add_sync(grp, w);
-            const bool leader = act && lane == __ffs(grp) - 1;
-            // segmented argmax over each owner's lanes
-            const unsigned og = __match_any_sync(FULL, act ? (unsigned)o : 0xFFFFFFFFu);
-            const uint32_t hi = leader ? (uint32_t)s : 0u;
-            const uint32_t npos = leader ? 0xFFFFFFFFu - (uint32_t)pos : 0u;
-            const uint32_t mhi = __reduce_max_sync(og, hi);
-            bool cand = leader && hi == mhi;
-            if (!a.strict) {
-                const uint64_t h = cand ? tie_key(a.key_t, o_lv, l) : ~0ull;
-                const uint32_t hh = __reduce_min_sync(og, cand ? (uint32_t)(h >> 32) : 0xFFFFFFFFu);
-                cand = cand && (uint32_t)(h >> 32) == hh;
-                const uint32_t hl = __reduce_min_sync(og, cand ? (uint32_t)h : 0xFFFFFFFFu);
-                cand = cand && (uint32_t)h == hl;
-            }
-            const uint32_t mlo = __reduce_max_sync(og, cand ? npos : 0u);
-            const bool win = cand && npos == mlo;
-            const bool ch = win && l != o_own;
-            if (win) a.lab_out[o_v] = l;
-            if (MULTI) {
-                const int o_g = __shfl_sync(FULL, x.g, o);
-                const unsigned chm = __ballot_sync(FULL, ch);
-                if (ch) {
-                    const unsigned gg = __match_any_sync(chm, (unsigned)o_g);
-                    if (lane == __ffs(gg) - 1) atomicAdd(a.changed + o_g, __popc(gg));
-                }
-            } else {
-                my_changed += __popc(__ballot_sync(FULL, ch));
-            }
-            base += total;
-            start = end;
-        }
-    }
-    if (!MULTI && lane == 0 && my_changed) atomicAdd(a.changed, (int)my_changed);
-}
 
 // ----------------------------------------------------------------------------
 // Entry quads: a row is read as aligned 16-byte blocks of 4 entries (column
@@ -403,6 +313,162 @@ __device__ __forceinline__ Cand block_argmax(const Cand &c, int strict, Cand *s_
 }
 
 // ----------------------------------------------------------------------------
+// small bucket: several rows per warp chunk
+// ----------------------------------------------------------------------------
+template <bool MULTI>
+__global__ void __launch_bounds__(256, 6) k_small(SweepArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    uint32_t my_changed = 0;
+
+    for (int64_t tile = wid; tile * 32 < a.len; tile += nw) {
+        const int64_t i = tile * 32 + lane;
+        Vtx x{0, 0, 0, 0, 0, 0, 0};
+        bool ok = false;
+        if (i < a.len) ok = load_vtx<MULTI>(a, a.list[i], x);
+        int d = ok ? x.d : 0;
+        const int32_t own = ok ? x.own : 0;
+
+        if (__any_sync(FULL, ok && try_majority(a, x.g, true))) {
+            // Majority pass: rows are read as aligned 16-byte blocks, several
+            // rows per 32-block chunk; a row whose own label holds more than
+            // half of its weight keeps it (the unique maximum) and drops out.
+            const int64_t q0 = x.e0 >> 2;
+            const int nq = d > 0 ? (int)(((x.e0 + d - 1) >> 2) - q0 + 1) : 0;  // <= 9
+            int Q = nq;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(FULL, Q, o);
+                if (lane >= o) Q += y;
+            }
+            const int qexcl = Q - nq;
+            const int qtotal = __shfl_sync(FULL, Q, 31);
+            unsigned settled = 0u;
+            int start = 0, base = 0;
+            while (base < qtotal && start < 32) {
+                const unsigned fits =
+                    __ballot_sync(FULL, (lane >= start && Q - base <= 32) || lane == start);
+                const int end = 32 - __clz(fits);
+                const int total = __shfl_sync(FULL, Q, end - 1) - base;
+                int o = start;
+#pragma unroll
+                for (int step = 16; step >= 1; step >>= 1) {
+                    const int c = o + step;
+                    const int ex = __shfl_sync(FULL, qexcl, c & 31);
+                    if (c < end && ex - base <= lane) o = c;
+                }
+                const bool act = lane < total;
+                const long long o_e0 = __shfl_sync(FULL, (long long)x.e0, o);
+                const int o_d = __shfl_sync(FULL, d, o);
+                const int o_vb = MULTI ? __shfl_sync(FULL, x.vb, o) : 0;
+                const int32_t o_own = __shfl_sync(FULL, own, o);
+                const int o_qex = __shfl_sync(FULL, qexcl, o);
+                uint32_t ow = 0, tw = 0;
+                if (act) {
+                    const int64_t blk = (o_e0 >> 2) + (lane - (o_qex - base));
+                    own_weight(load_quad(a, blk, o_e0, o_e0 + o_d, o_vb), o_own, ow, tw);
+                }
+                const unsigned og = __match_any_sync(FULL, act ? (unsigned)o : 0xFFFFFFFFu);
+                const uint32_t OW = __reduce_add_sync(og, ow);
+                const uint32_t TW = __reduce_add_sync(og, tw);
+                const bool keep = act && lane == __ffs(og) - 1 && 2ull * OW > (unsigned long long)TW;
+                settled |= __reduce_or_sync(FULL, keep ? (1u << o) : 0u);
+                base += total;
+                start = end;
+            }
+            if ((settled >> lane) & 1u) {
+                a.lab_out[x.v] = own;
+                d = 0;  // settled: left out of the table-free pass below
+            }
+        }
+
+        int P = d;  // inclusive prefix of degrees over the tile
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, P, o);
+            if (lane >= o) P += y;
+        }
+        const int excl = P - d;
+        const int total_all = __shfl_sync(FULL, P, 31);
+
+        int start = 0, base = 0;
+        while (base < total_all && start < 32) {
+            // greedy packing: rows start.. that end within 32 entries of base
+            // (row `start` always fits: the bucket holds degrees <= 32)
+            const unsigned fits =
+                __ballot_sync(FULL, (lane >= start && P - base <= 32) || lane == start);
+            const int end = 32 - __clz(fits);
+            const int total = __shfl_sync(FULL, P, end - 1) - base;
+
+            // owner of entry `lane`: the last row in [start, end) starting at or before it
+            int o = start;
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1) {
+                const int c = o + step;
+                const int ex = __shfl_sync(FULL, excl, c & 31);
+                if (c < end && ex - base <= lane) o = c;
+            }
+            const bool act = lane < total;
+            const int o_excl = __shfl_sync(FULL, excl, o);
+            const long long o_e0 = __shfl_sync(FULL, (long long)x.e0, o);
+            const int o_vb = MULTI ? __shfl_sync(FULL, x.vb, o) : 0;
+            const int o_lv = __shfl_sync(FULL, x.lv, o);
+            const int o_v = __shfl_sync(FULL, x.v, o);
+            const int32_t o_own = __shfl_sync(FULL, own, o);
+            const int pos = lane - (o_excl - base);
+
+            int w = 0;
+            int32_t l = EMPTY;
+            if (act) {
+                const long long e = o_e0 + pos;
+                const int32_t u = ld_entry(a.idx + e);
+                w = a.wts ? ld_entry(a.wts + e) : 1;
+                l = a.identity ? u : neighbour_label(a, (int64_t)o_vb + u, u);
+            }
+            // group equal (owner, label) pairs; the lowest lane holds the first
+            // position (in an identity sweep every pair is distinct)
+            const unsigned long long key =
+                act ? (((unsigned long long)(unsigned)o << 32) | (unsigned)l) : ~0ull;
+            const unsigned grp = a.identity ? (1u << lane) : __match_any_sync(FULL, key);
+            const int s = a.identity ? w : __reduce_add_sync(grp, w);
+            const bool leader = act && lane == __ffs(grp) - 1;
+            // segmented argmax over each owner's lanes
+            const unsigned og = __match_any_sync(FULL, act ? (unsigned)o : 0xFFFFFFFFu);
+            const uint32_t hi = leader ? (uint32_t)s : 0u;
+            const uint32_t npos = leader ? 0xFFFFFFFFu - (uint32_t)pos : 0u;
+            const uint32_t mhi = __reduce_max_sync(og, hi);
+            bool cand = leader && hi == mhi;
+            if (!a.strict) {
+                const uint64_t h = cand ? tie_key(a.key_t, o_lv, l) : ~0ull;
+                const uint32_t hh = __reduce_min_sync(og, cand ? (uint32_t)(h >> 32) : 0xFFFFFFFFu);
+                cand = cand && (uint32_t)(h >> 32) == hh;
+                const uint32_t hl = __reduce_min_sync(og, cand ? (uint32_t)h : 0xFFFFFFFFu);
+                cand = cand && (uint32_t)h == hl;
+            }
+            const uint32_t mlo = __reduce_max_sync(og, cand ? npos : 0u);
+            const bool win = cand && npos == mlo;
+            const bool ch = win && l != o_own;
+            if (win) a.lab_out[o_v] = l;
+            if (MULTI) {
+                const int o_g = __shfl_sync(FULL, x.g, o);
+                const unsigned chm = __ballot_sync(FULL, ch);
+                if (ch) {
+                    const unsigned gg = __match_any_sync(chm, (unsigned)o_g);
+                    if (lane == __ffs(gg) - 1) atomicAdd(a.changed + o_g, __popc(gg));
+                }
+            } else {
+                my_changed += __popc(__ballot_sync(FULL, ch));
+            }
+            base += total;
+            start = end;
+        }
+    }
+    if (!MULTI && lane == 0 && my_changed) atomicAdd(a.changed, (int)my_changed);
+}
+
+// ----------------------------------------------------------------------------
 // warp bucket: one warp per vertex, private shared table
 // ----------------------------------------------------------------------------
 constexpr int WARP_LG = 8;  // log2(WARP_TABLE)
@@ -463,7 +529,7 @@ __global__ void __launch_bounds__(256, MULTI ? 4 : 5) k_warp(SweepArgs a)
         Quad q1 = empty_quad();
         if (one) {
             if (b0 + lane <= b_hi) q1 = load_quad(a, b0 + lane, lo, hi, x.vb);
-            if (a.majority) {
+            if (try_majority(a, x.g, false)) {
                 uint32_t ow = 0, tw = 0;
                 own_weight(q1, own, ow, tw);
                 ow = __reduce_add_sync(FULL, ow);
@@ -715,7 +781,7 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 2048 / NT) k_cta(SweepArgs
             // a label holding more than half of the row's weight is the
             // unique maximum: the vertex keeps its own label if it does
             bool settled = false;
-            if (a.majority) {
+            if (try_majority(a, x.g, false)) {
                 uint32_t ow = 0, tw = 0;
 #pragma unroll
                 for (int r = 0; r < R; ++r) own_weight(q[r], x.own, ow, tw);
