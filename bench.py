@@ -190,6 +190,36 @@ def reduce_across_ranks(t_ms, entries, device=None):
     return float(t.item()), float(e.item())
 
 
+def sweep_sources_hash():
+    """First 16 hex digits of the SHA-256 of the sweep kernel sources."""
+    import hashlib
+
+    h = hashlib.sha256()
+    csrc = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2301_09125_gb300",
+                        "csrc")
+    for f in ("lp_sweep.cu", "lp_device.cuh", "lp_internal.cuh"):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_ratio(kernel):
+    """DRAM traffic / algorithmic bytes of a bucket launch from the committed
+    ncu summary, or None when the sweep sources changed since it was taken."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles",
+                        "dram_traffic_rmat21_async_w2.md")
+    try:
+        lines = [ln.split() for ln in open(path) if ln.strip().startswith(("traffic_ratio",
+                                                                           "sweep_sources"))]
+    except OSError:
+        return None
+    src = [x[1] for x in lines if x[0] == "sweep_sources_sha256_16"]
+    if not src or src[0] != sweep_sources_hash():
+        return None
+    r = [float(x[2]) for x in lines if x[0] == "traffic_ratio" and x[1] == kernel]
+    return r[0] if r else None
+
+
 def gen_graph(name):
     import graphgen as gg
 
@@ -400,9 +430,13 @@ def run_ours(args):
     total_sweeps = sum(iters)
     sweep_bytes = alg_bytes_per_sweep(g)
     per_sweep_ms = sweep_ms / total_sweeps
+    ratio = traffic_ratio(dom_name)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "kernel": dom_name,
-                "peak_source": peak_kind}
+                "frac": achieved / peak,
+                "traffic": None if ratio is None else ratio * dom["bytes"] / dom["launches"],
+                "kernel": dom_name, "peak_source": peak_kind,
+                "traffic_source": "profiles/dram_traffic_rmat21_async_w2.md (ratio to "
+                                  "algorithmic bytes, scaled to this launch)"}
     line = {
         "metric": f"RAK GTEPS ({args.workload})", "value": value, "unit": "GTEPS",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
