@@ -10,6 +10,50 @@
 namespace lp {
 namespace {
 
+// L2 eviction policies (PTX createpolicy): the CSR entries are read once per
+// sweep and should not push the label arrays, which every sweep gathers from
+// at random, out of L2.
+__device__ __forceinline__ uint64_t policy_evict_first()
+{
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ uint64_t policy_evict_last()
+{
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+// read-only loads with an L2 policy: a 16-byte block of entries, one entry,
+// one label
+__device__ __forceinline__ int4 ld_entries4(const int32_t *base, int64_t blk)
+{
+    int4 r;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.s32 {%0, %1, %2, %3}, [%4], %5;"
+        : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+        : "l"(reinterpret_cast<const int4 *>(base) + blk), "l"(policy_evict_first()));
+    return r;
+}
+
+__device__ __forceinline__ int32_t ld_entry(const int32_t *p)
+{
+    int32_t r;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.s32 %0, [%1], %2;"
+        : "=r"(r)
+        : "l"(p), "l"(policy_evict_first()));
+    return r;
+}
+
+__device__ __forceinline__ int32_t ld_label(const int32_t *p)
+{
+    int32_t r;
+    asm("ld.global.nc.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(r) : "l"(p), "l"(policy_evict_last()));
+    return r;
+}
+
 // Non-strict key of `label` at local vertex lv (see lp.h).
 __device__ __forceinline__ uint64_t tie_key(uint64_t key_t, int32_t lv, int32_t label)
 {

@@ -6,12 +6,15 @@
 //   S   = sum_c K_c^2  (128-bit)
 //   Q   = L / 2m - S / (2m)^2   (formed in double on the host)
 //
-// The entry pass reuses the sweep's degree buckets: rows of degree <= 32 are
-// packed several to a warp chunk, longer rows get a warp or a CTA reading
-// aligned 16-byte blocks.  Each row adds k_v to K_{c_v} with one 64-bit
-// atomic; L and 2m are summed in registers and flushed once per warp (one
-// graph) or per row (graph sets).  The square pass adds K_c^2 into per-graph
-// 128-bit accumulators (carry-propagating 64-bit atomics).
+// The entry pass reuses the sweep's degree buckets: rows of the small bucket
+// (<= 32 entries) are read as aligned 16-byte blocks packed several rows to a
+// 32-block warp chunk, longer rows get a warp or a CTA of 128, 256 or 512
+// threads reading aligned blocks.  Each row adds k_v to K_{c_v} (per-thread
+// run aggregation, one 64-bit atomic per run); L and 2m are summed in
+// registers and flushed once per warp (one graph) or per row (graph sets).
+// The square pass adds K_c^2 into per-graph 128-bit accumulators
+// (carry-propagating 64-bit atomics).
+#include "lp_device.cuh"
 #include "lp_internal.cuh"
 
 namespace lp {
@@ -74,7 +77,46 @@ __device__ __forceinline__ MV load_mv(const ModArgs &a, int32_t v)
     return x;
 }
 
-// rows of degree 1..32, packed into 32-entry chunks (as in the small sweep)
+// One 16-byte block of a row's entries: summed weight (k part) and summed
+// weight of the entries whose neighbour carries label c (L part).
+__device__ __forceinline__ void mod_block(const ModArgs &a, int64_t blk, int64_t lo, int64_t hi,
+                                          int32_t vb, int32_t c, uint32_t &kw, uint32_t &lw)
+{
+    const int64_t e0 = blk * 4;
+    int32_t u[4], w[4];
+    if (e0 + 3 < a.ne) {
+        const int4 I = ld_entries4(a.idx, blk);
+        u[0] = I.x;
+        u[1] = I.y;
+        u[2] = I.z;
+        u[3] = I.w;
+        if (a.wts) {
+            const int4 W = ld_entries4(a.wts, blk);
+            w[0] = W.x;
+            w[1] = W.y;
+            w[2] = W.z;
+            w[3] = W.w;
+        } else {
+            w[0] = w[1] = w[2] = w[3] = 1;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            u[j] = e0 + j < a.ne ? __ldg(a.idx + e0 + j) : 0;
+            w[j] = e0 + j < a.ne ? (a.wts ? __ldg(a.wts + e0 + j) : 1) : 0;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        if (e0 + j >= lo && e0 + j < hi) {
+            kw += (uint32_t)w[j];
+            if (ld_label(a.lab + vb + u[j]) == c) lw += (uint32_t)w[j];
+        }
+    }
+}
+
+// rows of degree 1..32 as aligned blocks (<= 9 per row), whole rows packed
+// into 32-block chunks
 template <bool MULTI>
 __global__ void __launch_bounds__(256) k_mod_small(ModArgs a)
 {
@@ -88,44 +130,44 @@ __global__ void __launch_bounds__(256) k_mod_small(ModArgs a)
         MV x{0, 0, 0, 0, 0};
         if (i < a.len) x = load_mv<MULTI>(a, a.list[i]);
         const int32_t cv = i < a.len ? __ldg(a.lab + x.v) : 0;
-        int P = x.d;
+        const int64_t q0 = x.e0 >> 2;
+        const int nq = x.d > 0 ? (int)(((x.e0 + x.d - 1) >> 2) - q0 + 1) : 0;
+        int Q = nq;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(FULL, P, o);
-            if (lane >= o) P += y;
+            const int y = __shfl_up_sync(FULL, Q, o);
+            if (lane >= o) Q += y;
         }
-        const int excl = P - x.d;
-        const int total_all = __shfl_sync(FULL, P, 31);
+        const int qexcl = Q - nq;
+        const int qtotal = __shfl_sync(FULL, Q, 31);
         int start = 0, base = 0;
-        while (base < total_all && start < 32) {
+        while (base < qtotal && start < 32) {
             const unsigned fits =
-                __ballot_sync(FULL, (lane >= start && P - base <= 32) || lane == start);
+                __ballot_sync(FULL, (lane >= start && Q - base <= 32) || lane == start);
             const int end = 32 - __clz(fits);
-            const int total = __shfl_sync(FULL, P, end - 1) - base;
+            const int total = __shfl_sync(FULL, Q, end - 1) - base;
             int o = start;
 #pragma unroll
             for (int step = 16; step >= 1; step >>= 1) {
                 const int c = o + step;
-                const int ex = __shfl_sync(FULL, excl, c & 31);
+                const int ex = __shfl_sync(FULL, qexcl, c & 31);
                 if (c < end && ex - base <= lane) o = c;
             }
             const bool act = lane < total;
-            const int o_excl = __shfl_sync(FULL, excl, o);
             const long long o_e0 = __shfl_sync(FULL, (long long)x.e0, o);
+            const int o_d = __shfl_sync(FULL, x.d, o);
             const int o_vb = MULTI ? __shfl_sync(FULL, x.vb, o) : 0;
             const int o_c = __shfl_sync(FULL, cv, o);
             const int o_g = MULTI ? __shfl_sync(FULL, x.g, o) : 0;
-            uint32_t w = 0, same = 0;
-            if (act) {
-                const long long e = o_e0 + lane - (o_excl - base);
-                const int32_t u = __ldg(a.idx + e);
-                w = a.wts ? (uint32_t)__ldg(a.wts + e) : 1u;
-                same = __ldg(a.lab + o_vb + u) == o_c ? w : 0u;
-            }
+            const int o_qex = __shfl_sync(FULL, qexcl, o);
+            uint32_t kw = 0, lw = 0;
+            if (act)
+                mod_block(a, (o_e0 >> 2) + (lane - (o_qex - base)), o_e0, o_e0 + o_d, o_vb, o_c,
+                          kw, lw);
             // one row lies wholly in the chunk: its sums are k_v and L_v (< 2^31)
             const unsigned og = __match_any_sync(FULL, act ? (unsigned)o : 0xFFFFFFFFu);
-            const uint32_t kv = __reduce_add_sync(og, w);
-            const uint32_t lv = __reduce_add_sync(og, same);
+            const uint32_t kv = __reduce_add_sync(og, kw);
+            const uint32_t lv = __reduce_add_sync(og, lw);
             if (act && lane == __ffs(og) - 1) {
                 run.add(a.kc, (int64_t)o_vb + o_c, kv);
                 if (MULTI) {
@@ -153,64 +195,49 @@ __global__ void __launch_bounds__(256) k_mod_small(ModArgs a)
 
 // rows of degree > 32: NT threads per row, aligned 16-byte blocks
 template <int NT, bool MULTI>
-__global__ void __launch_bounds__(256) k_mod_rows(ModArgs a)  // 256 / NT rows per CTA
+__global__ void __launch_bounds__(NT > 256 ? NT : 256) k_mod_rows(ModArgs a)
 {
-    __shared__ unsigned long long s_l[NT / 32], s_w[NT / 32];
+    constexpr int BT = NT > 256 ? NT : 256;  // threads per CTA: BT / NT rows at a time
+    __shared__ unsigned long long s_l[BT / 32], s_w[BT / 32];
+    constexpr int G = BT / NT;  // rows per CTA at a time
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int64_t grp_id = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / NT;
-    const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / NT;
+    const int grp = threadIdx.x / NT;
     const int t = threadIdx.x % NT;
     unsigned long long l_tot = 0, w_tot = 0;
     KcRun run;
-    for (int64_t item = grp_id; item < a.len; item += ngrp) {
-        const MV x = load_mv<MULTI>(a, a.list[item]);
-        const int32_t cv = __ldg(a.lab + x.v);
-        const int64_t lo = x.e0, hi = x.e0 + x.d, b_hi = (hi - 1) >> 2;
-        unsigned long long kv = 0, lv = 0;
-        for (int64_t blk = (lo >> 2) + t; blk <= b_hi; blk += NT) {
-            const int64_t e0 = blk * 4;
-            int32_t u[4], w[4];
-            if (e0 + 3 < a.ne) {
-                const int4 I = __ldg(reinterpret_cast<const int4 *>(a.idx) + blk);
-                u[0] = I.x; u[1] = I.y; u[2] = I.z; u[3] = I.w;
-                if (a.wts) {
-                    const int4 W = __ldg(reinterpret_cast<const int4 *>(a.wts) + blk);
-                    w[0] = W.x; w[1] = W.y; w[2] = W.z; w[3] = W.w;
-                } else {
-                    w[0] = w[1] = w[2] = w[3] = 1;
-                }
-            } else {
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    u[j] = e0 + j < a.ne ? __ldg(a.idx + e0 + j) : 0;
-                    w[j] = e0 + j < a.ne ? (a.wts ? __ldg(a.wts + e0 + j) : 1) : 0;
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                if (e0 + j >= lo && e0 + j < hi) {
-                    kv += (unsigned)w[j];
-                    if (__ldg(a.lab + x.vb + u[j]) == cv) lv += (unsigned)w[j];
-                }
-            }
+    // every group of the CTA makes the same number of trips (barriers below)
+    for (int64_t base = (int64_t)blockIdx.x * G; base < a.len; base += (int64_t)gridDim.x * G) {
+        const int64_t item = base + grp;
+        const bool have = item < a.len;
+        MV x{0, 0, 0, 0, 0};
+        int32_t cv = 0;
+        if (have) {
+            x = load_mv<MULTI>(a, a.list[item]);
+            cv = __ldg(a.lab + x.v);
         }
-        kv = warp_sum64(kv);
-        lv = warp_sum64(lv);
+        const int64_t lo = x.e0, hi = x.e0 + x.d, b_hi = (hi - 1) >> 2;
+        uint32_t kw = 0, lw = 0;  // row sums < 2^31 (ingest bound)
+        if (have)
+            for (int64_t blk = (lo >> 2) + t; blk <= b_hi; blk += NT)
+                mod_block(a, blk, lo, hi, x.vb, cv, kw, lw);
+        unsigned long long kv = __reduce_add_sync(FULL, kw);
+        unsigned long long lv = __reduce_add_sync(FULL, lw);
         if (NT > 32) {
             if (lane == 0) {
                 s_l[wib] = lv;
                 s_w[wib] = kv;
             }
             __syncthreads();
-            if (threadIdx.x == 0) {
+            if (t == 0) {
+                const int w0 = wib;  // first warp of this row's group
                 for (int k = 1; k < NT / 32; ++k) {
-                    lv += s_l[k];
-                    kv += s_w[k];
+                    lv += s_l[w0 + k];
+                    kv += s_w[w0 + k];
                 }
             }
             __syncthreads();
         }
-        if (t == 0) {
+        if (t == 0 && have) {
             run.add(a.kc, (int64_t)x.vb + cv, kv);
             if (MULTI) {
                 atomicAdd(a.acc + 4 * (int64_t)x.g, lv);
@@ -273,23 +300,27 @@ int modularity_launch(const ModArgs &base, const int64_t *bucket_begin, const in
         else k_mod_small<false><<<g, 256, 0, st>>>(a);
         ++*launches;
     }
-    if (bucket_len[1] > 0) {
-        a.list = base.list + bucket_begin[1];
-        a.len = bucket_len[1];
-        const int g = grid_cap((a.len + 7) / 8, num_sms * 8);
-        if (multi) k_mod_rows<32, true><<<g, 256, 0, st>>>(a);
-        else k_mod_rows<32, false><<<g, 256, 0, st>>>(a);
+    // one warp per row (warp bucket), 128 / 256 / 512 threads per row (cta,
+    // cta2 and hub buckets)
+    auto rows = [&](int b, auto kernel, int nt, int bt) {
+        if (bucket_len[b] <= 0) return;
+        a.list = base.list + bucket_begin[b];
+        a.len = bucket_len[b];
+        const int64_t per_cta = bt / nt;
+        const int g = grid_cap((a.len + per_cta - 1) / per_cta, num_sms * (2048 / bt));
+        kernel<<<g, bt, 0, st>>>(a);
         ++*launches;
-    }
-    // the cta, cta2 and hub buckets are adjacent
-    const int64_t big = bucket_len[2] + bucket_len[3] + bucket_len[4];
-    if (big > 0) {
-        a.list = base.list + bucket_begin[2];
-        a.len = big;
-        const int g = grid_cap(big, num_sms * 8);
-        if (multi) k_mod_rows<256, true><<<g, 256, 0, st>>>(a);
-        else k_mod_rows<256, false><<<g, 256, 0, st>>>(a);
-        ++*launches;
+    };
+    if (multi) {
+        rows(1, k_mod_rows<32, true>, 32, 256);
+        rows(2, k_mod_rows<128, true>, 128, 256);
+        rows(3, k_mod_rows<256, true>, 256, 256);
+        rows(4, k_mod_rows<512, true>, 512, 512);
+    } else {
+        rows(1, k_mod_rows<32, false>, 32, 256);
+        rows(2, k_mod_rows<128, false>, 128, 256);
+        rows(3, k_mod_rows<256, false>, 256, 256);
+        rows(4, k_mod_rows<512, false>, 512, 512);
     }
     if (nslots > 0) {
         const int64_t threads = (nslots + SQ_RUN - 1) / SQ_RUN;
