@@ -264,6 +264,17 @@ def test_rmat_and_road_small(lp):
     assert_sync_parity(lp, g.offsets, g.indices, g.weights)
 
 
+def test_async_wave_counts_of_the_benchmarks(lp):
+    """The wave counts the benchmarks use keep modularity within 1e-2 of the
+    sequential in-place order: 3 waves on the road grid (coprime with its
+    power-of-two width, so vertical neighbours update in different waves) and
+    127 waves on the k-mer paths (random neighbour ids)."""
+    g = gg.grid_road(1024, seed=2)
+    assert_async_quality(lp, g.offsets, g.indices, g.weights, waves=3)
+    g = gg.kmer_like(1 << 20, seed=2)
+    assert_async_quality(lp, g.offsets, g.indices, g.weights, waves=127)
+
+
 # ---------------------------------------------------------------- modularity
 @pytest.mark.parametrize("seed", range(4))
 def test_modularity_parity(lp, seed):
