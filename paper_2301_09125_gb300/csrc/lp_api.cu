@@ -310,6 +310,7 @@ struct GraphSet {
         f(hseg_task_w);
         f(hpart_task_w);
         f(d_res);
+        f(d_stop);
         f(kc);
         f(macc);
         fh(h_macc);
@@ -334,6 +335,7 @@ struct GraphSet {
         hpbest = nullptr;
         hseg_task = hpart_task = hseg_task_w = hpart_task_w = nullptr;
         d_res = nullptr;
+        d_stop = nullptr;
         kc = macc = h_macc = nullptr;
         g_sel = nullptr;
         lab_tmp = nullptr;
@@ -349,6 +351,13 @@ struct GraphSet {
         gr_stream = nullptr;
         if (h_res) cudaFreeHost(h_res);
         h_res = nullptr;
+        if (h_stop) cudaFreeHost(h_stop);
+        h_stop = nullptr;
+        h_stop_cap = 0;
+        for (cudaEvent_t &e : run_ev) {
+            if (e) cudaEventDestroy(e);
+            e = nullptr;
+        }
         cudaStreamSynchronize(st);
     }
 
@@ -746,6 +755,7 @@ struct GraphSet {
         bool prof = false;
         std::vector<int> prof_launch;   // bucket of each profiled launch
         std::vector<int64_t> prof_len;  // its vertex count
+        std::vector<int32_t> prof_iter; // its iteration (launches past the end are not counted)
         SweepArgs a{};
     } rs;
     cudaEvent_t ev_iter = nullptr;  // end of the last launched iteration
@@ -806,6 +816,7 @@ struct GraphSet {
         rs.prof = g_prof_on.load();
         rs.prof_launch.clear();
         rs.prof_len.clear();
+        rs.prof_iter.clear();
         LP_CU(cudaEventRecord(ev0, st));
 
         SweepArgs &a = rs.a;
@@ -1023,7 +1034,7 @@ struct GraphSet {
             if (ls == LP_OK &&
                 converge_launch(changed + (int64_t)it * G, g_n, g_active, G, rs.p.tolerance, it,
                                 rs.multi, res, it + 1 < n_it ? h[(size_t)it + 1] : h[0],
-                                it + 1 < n_it, gr_stream) != 0)
+                                it + 1 < n_it, nullptr, false, gr_stream) != 0)
                 ls = fail(LP_ECUDA, cuda_msg("convergence launch", cudaGetLastError()));
             cudaGraph_t captured = nullptr;
             const cudaError_t ce = cudaStreamEndCapture(gr_stream, &captured);
@@ -1118,6 +1129,7 @@ struct GraphSet {
         if (rs.prof && !rs.prof_launch.empty()) {
             std::lock_guard<std::mutex> lock(g_prof_mu);
             for (size_t i = 0; i < rs.prof_launch.size(); ++i) {
+                if (i < rs.prof_iter.size() && rs.prof_iter[i] >= rs.it) continue;
                 float kms = 0.f;
                 LP_CU(cudaEventElapsedTime(&kms, prof_ev[2 * i], prof_ev[2 * i + 1]));
                 const int b = rs.prof_launch[i];
@@ -1151,14 +1163,74 @@ struct GraphSet {
         return run_host(p, multi);
     }
 
+    // Sec. 3.2's iteration launched from the host without waiting for each
+    // iteration: the tolerance test runs on the device after every iteration
+    // and raises a stop flag once the run is over; the host checks the flag
+    // of the iteration RUN_LAG before the one it has just launched, so that
+    // iterations launched past the end (at most RUN_LAG) return at once.
+    static constexpr int RUN_LAG = 2;
+    int32_t *d_stop = nullptr, *h_stop = nullptr;
+    int32_t h_stop_cap = 0;
+    cudaEvent_t run_ev[RUN_LAG + 1] = {};
+
     lp_status run_host(const lp_rak_params *p, bool multi)
     {
         LP_TRY(run_begin(p, multi));
-        while (!run_done()) {
-            LP_TRY(run_launch());
-            LP_CU(cudaEventSynchronize(ev_iter));
-            LP_TRY(run_finish());
+        if (!d_stop) LP_TRY(dev_alloc(&d_stop, 1, "stop flag", st, device));
+        if (h_stop_cap < rs.p.max_iter) {
+            if (h_stop) cudaFreeHost(h_stop);
+            h_stop = nullptr;
+            h_stop_cap = 0;
+            LP_TRY(host_alloc(&h_stop, rs.p.max_iter, "stop flags"));
+            h_stop_cap = rs.p.max_iter;
         }
+        if (!d_res) {
+            LP_TRY(dev_alloc(&d_res, 6 * (int64_t)G, "run results", st, device));
+            LP_TRY(host_alloc(&h_res, 6 * (int64_t)G, "run results"));
+        }
+        for (cudaEvent_t &e : run_ev)
+            if (!e) LP_CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        const size_t res_bytes = 6 * (size_t)G * sizeof(int32_t);
+        LP_CU(cudaMemsetAsync(d_stop, 0, sizeof(int32_t), st));
+        LP_CU(cudaMemsetAsync(d_res, 0, res_bytes, st));
+        rs.a.stop = d_stop;
+        const RunResults res = run_results();
+        for (int32_t it = 0; it < rs.p.max_iter; ++it) {
+            Launches L;
+            LP_TRY(launch_sweeps(st, it, it & 1, rs.prof, &L.n));
+            while (rs.prof_iter.size() < rs.prof_launch.size()) rs.prof_iter.push_back(it);
+            if (converge_launch(changed + (int64_t)it * G, g_n, g_active, G, rs.p.tolerance, it,
+                                rs.multi, res, 0, false, d_stop, it + 1 == rs.p.max_iter,
+                                st) != 0)
+                return fail(LP_ECUDA, cuda_msg("convergence launch", cudaGetLastError()));
+            ++L.n;
+            LP_CU(cudaMemcpyAsync(h_stop + it, d_stop, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                  st));
+            LP_CU(cudaEventRecord(run_ev[it % (RUN_LAG + 1)], st));
+            if (it >= RUN_LAG) {
+                LP_CU(cudaEventSynchronize(run_ev[(it - RUN_LAG) % (RUN_LAG + 1)]));
+                if (h_stop[it - RUN_LAG]) break;
+            }
+        }
+        LP_CU(cudaMemcpyAsync(h_res, d_res, res_bytes, cudaMemcpyDeviceToHost, st));
+        LP_CU(cudaMemcpyAsync(h_changed, changed, (size_t)rs.p.max_iter * G * sizeof(int32_t),
+                              cudaMemcpyDeviceToHost, st));
+        LP_CU(cudaEventRecord(ev_iter, st));
+        LP_CU(cudaEventSynchronize(ev_iter));
+        const long long *last = reinterpret_cast<const long long *>(h_res + 4 * (int64_t)G);
+        int32_t ran = 0;
+        rs.active_left = 0;
+        for (int32_t g = 0; g < G; ++g) {
+            lp_rak_result &r = results[(size_t)g];
+            r.iterations = h_res[g];
+            r.converged = h_res[G + g];
+            r.last_changed = last[g];
+            final_buf[(size_t)g] = h_res[2 * (int64_t)G + g];
+            ran = std::max(ran, r.iterations);
+            if (!r.converged) ++rs.active_left;
+        }
+        rs.it = ran;
+        rs.cur = ran & 1;
         return run_end();
     }
 

@@ -99,6 +99,9 @@ struct SweepArgs {
     int majority;
     const int32_t *changed_prev;
     const int32_t *g_n;
+    // raised by the device-side tolerance test once the run is over: kernels
+    // of iterations launched ahead of it return at once (null: not used)
+    const int32_t *stop;
     // asynchronous waves (Sec. 3.3): this launch runs wave `wave_k` of `waves`;
     // a neighbour u of an earlier wave (u mod waves < wave_k) is read from
     // lab_out (this iteration), every other one from lab_in.  waves = 1: sync.
@@ -264,10 +267,13 @@ struct RunResults {
     long long *last_changed;
 };
 // The tolerance test of iteration `it` on the device (Sec. 3.2); arms `next`
-// (the following iteration's conditional node) if some graph goes on.
+// (the following iteration's conditional node) if some graph goes on and
+// has_next; with `stop`, raises *stop when no graph goes on or `it` is the
+// last iteration, and does nothing once *stop is raised.
 int converge_launch(const int32_t *changed_it, const int32_t *g_n, int32_t *g_active, int32_t G,
                     double tolerance, int32_t it, bool multi, const RunResults &res,
-                    cudaGraphConditionalHandle next, bool has_next, cudaStream_t st);
+                    cudaGraphConditionalHandle next, bool has_next, int32_t *stop, bool last,
+                    cudaStream_t st);
 
 // Entry and square passes of the modularity of every graph of a set.
 int modularity_launch(const ModArgs &a, const int64_t *bucket_begin, const int64_t *bucket_len,

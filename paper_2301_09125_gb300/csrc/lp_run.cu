@@ -1,11 +1,13 @@
-// Device-side convergence test (Sec. 3.2) for runs captured as one CUDA graph.
+// Device-side convergence test (Sec. 3.2).
 //
-// A run of at most max_iter iterations is captured once as a chain of
-// conditional (if) graph nodes, one per iteration: node i holds iteration i's
-// sweep launches followed by k_converge, which applies the tolerance test to
-// every graph still iterating and arms node i + 1 only if some graph goes
-// on.  The host launches the whole run with one cudaGraphLaunch and reads the
-// per-graph results once at the end.
+// Runs keep the tolerance test on the device: after each iteration's sweeps,
+// k_converge applies it to every graph still iterating and records the
+// results.  A run captured as one CUDA graph is a chain of conditional (if)
+// nodes, one per iteration, and k_converge arms the next node only if some
+// graph goes on; a run driven from the host launches iterations ahead
+// without waiting, and k_converge raises a stop flag that makes the kernels
+// of iterations launched past the end return at once.  Either way the host
+// reads the per-graph results once at the end.
 #include "lp_internal.cuh"
 
 namespace lp {
@@ -17,8 +19,9 @@ namespace {
 __global__ void __launch_bounds__(1024)
     k_converge(const int32_t *changed_it, const int32_t *g_n, int32_t *g_active, int32_t G,
                double tolerance, int32_t it, int32_t multi, RunResults res,
-               cudaGraphConditionalHandle next, int32_t has_next)
+               cudaGraphConditionalHandle next, int32_t has_next, int32_t *stop, int32_t last)
 {
+    if (stop && *stop) return;  // launched ahead of a run that has ended
     int going = 0;
     for (int32_t g = threadIdx.x; g < G; g += blockDim.x) {
         if (multi && !g_active[g]) continue;
@@ -34,17 +37,21 @@ __global__ void __launch_bounds__(1024)
         }
     }
     going = __syncthreads_or(going);
-    if (threadIdx.x == 0 && going && has_next) cudaGraphSetConditional(next, 1u);
+    if (threadIdx.x == 0) {
+        if (going && has_next) cudaGraphSetConditional(next, 1u);
+        if (stop && (!going || last)) *stop = 1;
+    }
 }
 
 }  // namespace
 
 int converge_launch(const int32_t *changed_it, const int32_t *g_n, int32_t *g_active, int32_t G,
                     double tolerance, int32_t it, bool multi, const RunResults &res,
-                    cudaGraphConditionalHandle next, bool has_next, cudaStream_t st)
+                    cudaGraphConditionalHandle next, bool has_next, int32_t *stop, bool last,
+                    cudaStream_t st)
 {
     k_converge<<<1, 1024, 0, st>>>(changed_it, g_n, g_active, G, tolerance, it, multi ? 1 : 0,
-                                   res, next, has_next ? 1 : 0);
+                                   res, next, has_next ? 1 : 0, stop, last ? 1 : 0);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

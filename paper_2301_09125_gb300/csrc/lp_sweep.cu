@@ -274,6 +274,7 @@ __device__ __forceinline__ Cand block_argmax(const Cand &c, int strict, Cand *s_
 template <bool MULTI>
 __global__ void __launch_bounds__(256, 6) k_small(SweepArgs a)
 {
+    if (a.stop && *a.stop) return;  // launched past the end of the run
     const int lane = threadIdx.x & 31;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -433,6 +434,7 @@ static_assert((1 << WARP_LG) == WARP_TABLE, "warp table size");
 template <bool MULTI>
 __global__ void __launch_bounds__(256, MULTI ? 4 : 5) k_warp(SweepArgs a)
 {
+    if (a.stop && *a.stop) return;  // launched past the end of the run
     __shared__ int32_t s_key[8 * WARP_TABLE];
     __shared__ int32_t s_sum[8 * WARP_TABLE];
     __shared__ uint32_t s_np[8 * WARP_TABLE];
@@ -690,6 +692,7 @@ __device__ __forceinline__ uint2 block_sum2(uint32_t x, uint32_t y, uint32_t *s)
 template <int NT, int CAP, bool MULTI>
 __global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 2048 / NT) k_cta(SweepArgs a)
 {
+    if (a.stop && *a.stop) return;  // launched past the end of the run
     extern __shared__ int32_t smem[];
     int32_t *tk = smem;
     int32_t *ts = tk + CAP;
@@ -868,6 +871,7 @@ __device__ __forceinline__ void block_scan_counts(int32_t *c, int n, int32_t *s_
 template <bool MULTI>
 __global__ void __launch_bounds__(HUB_THREADS, 2) k_hub_seg(SweepArgs a)
 {
+    if (a.stop && *a.stop) return;  // launched past the end of the run
     constexpr int NT = HUB_THREADS;
     constexpr int LG = 13;
     static_assert((1 << LG) == HUB_TABLE && HUB_TABLE >= 2 * HUB_SEG, "hub table size");
@@ -941,6 +945,7 @@ __global__ void __launch_bounds__(HUB_THREADS, 2) k_hub_seg(SweepArgs a)
 template <bool MULTI>
 __global__ void __launch_bounds__(HUB_THREADS, 2) k_hub_merge(SweepArgs a)
 {
+    if (a.stop && *a.stop) return;  // launched past the end of the run
     constexpr int NT = HUB_THREADS;
     constexpr int LG = 13;
     constexpr int PROBE = 256;
