@@ -254,6 +254,7 @@ struct GraphSet {
     unsigned long long *hkey = nullptr;
     uint32_t *hnpos = nullptr;
     int32_t *hused = nullptr, *hdone = nullptr, *hnused = nullptr;
+    uint32_t *hmaj = nullptr;  // long rows' majority counters (2 per hub task)
     // modularity and label staging scratch
     unsigned long long *kc = nullptr, *macc = nullptr, *h_macc = nullptr;
     int64_t kc_cap = 0;
@@ -305,6 +306,7 @@ struct GraphSet {
         f(hrec);
         f(hpoff);
         f(hpbest);
+        f(hmaj);
         f(hseg_task);
         f(hpart_task);
         f(hseg_task_w);
@@ -333,6 +335,7 @@ struct GraphSet {
         hrec = nullptr;
         hpoff = nullptr;
         hpbest = nullptr;
+        hmaj = nullptr;
         hseg_task = hpart_task = hseg_task_w = hpart_task_w = nullptr;
         d_res = nullptr;
         d_stop = nullptr;
@@ -527,6 +530,7 @@ struct GraphSet {
             LP_TRY(dev_alloc(&hused, slots / 2 + 1, "hub used lists", st, device));
             LP_TRY(dev_alloc(&hdone, bl[HUB_BUCKET], "hub counters", st, device));
             LP_TRY(dev_alloc(&hnused, bl[HUB_BUCKET], "hub counters", st, device));
+            LP_TRY(dev_alloc(&hmaj, 2 * bl[HUB_BUCKET], "hub majority counters", st, device));
             LP_CU(cudaMemsetAsync(hkey, 0, (size_t)slots * sizeof(unsigned long long), st));
             LP_CU(cudaMemsetAsync(hnpos, 0, (size_t)slots * sizeof(uint32_t), st));
             LP_CU(cudaMemsetAsync(hdone, 0, (size_t)bl[HUB_BUCKET] * sizeof(int32_t), st));
@@ -551,6 +555,7 @@ struct GraphSet {
         f(hrec);
         f(hpoff);
         f(hpbest);
+        f(hmaj);
         f(hkey);
         f(hnpos);
         f(hused);
@@ -566,6 +571,7 @@ struct GraphSet {
         hrec = nullptr;
         hpoff = nullptr;
         hpbest = nullptr;
+        hmaj = nullptr;
         hkey = nullptr;
         hnpos = nullptr;
         hused = hdone = hnused = nullptr;
@@ -838,6 +844,7 @@ struct GraphSet {
         a.hrec = hrec;
         a.hpoff = hpoff;
         a.hpbest = hpbest;
+        a.hmaj = hmaj;
         a.waves = (uint32_t)waves;
         a.wave_magic = fastmod_magic((uint32_t)waves);
         return LP_OK;

@@ -130,6 +130,9 @@ struct SweepArgs {
     int32_t *hused;
     int32_t *hdone;
     int32_t *hnused;
+    // per long-row task: own-label weight and total weight of the row (the
+    // majority test of rows longer than HUB_ONE_MAX, summed over segments)
+    uint32_t *hmaj;
 };
 
 // Modularity arguments (a whole graph set; graph layout as for SweepArgs).

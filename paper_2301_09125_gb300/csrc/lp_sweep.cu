@@ -864,6 +864,44 @@ __device__ __forceinline__ void block_scan_counts(int32_t *c, int n, int32_t *s_
     __syncthreads();
 }
 
+// Majority pre-pass over the segments of the long rows: each segment adds its
+// row's own-label weight and total weight into the row's two counters, so the
+// segment and partition passes can skip rows whose own label holds more than
+// half of the weight (that label is then the row's unique maximum).
+template <bool MULTI>
+__global__ void __launch_bounds__(HUB_THREADS) k_hub_major(SweepArgs a)
+{
+    constexpr int NT = HUB_THREADS;
+    if (a.stop && *a.stop) return;  // launched past the end of the run
+    __shared__ uint32_t s_sum[2 * (NT / 32)];
+    for (int64_t item = blockIdx.x; item < a.hsegs; item += gridDim.x) {
+        const int64_t ti = __ldg(a.hseg_task + item);
+        const HubTask t = a.htask[ti];
+        Vtx x;
+        // a pre-pass costs under a tenth of a high-cardinality segment pass
+        if (!load_vtx<MULTI>(a, t.v, x) || !try_majority(a, x.g, false)) continue;  // uniform
+        const int64_t lo = x.e0 + (int64_t)(item - t.seg0) * HUB_SEG;
+        const int64_t hi = min(lo + HUB_SEG, x.e0 + x.d);
+        uint32_t ow = 0u, tw = 0u;
+        for (int64_t blk = (lo >> 2) + threadIdx.x; blk <= (hi - 1) >> 2; blk += NT)
+            own_weight(load_quad(a, blk, lo, hi, x.vb), x.own, ow, tw);
+        const uint2 s2 = block_sum2<NT>(ow, tw, s_sum);
+        if (threadIdx.x == 0) {
+            atomicAdd(a.hmaj + 2 * ti, s2.x);
+            atomicAdd(a.hmaj + 2 * ti + 1, s2.y);
+        }
+    }
+}
+
+// whether the long row of task ti keeps its own label (pre-pass counters)
+template <bool MULTI>
+__device__ __forceinline__ bool hub_settled(const SweepArgs &a, int64_t ti, int32_t g)
+{
+    if (!a.hmaj || !try_majority(a, g, false)) return false;
+    const uint32_t own = __ldcg(a.hmaj + 2 * ti), tot = __ldcg(a.hmaj + 2 * ti + 1);
+    return 2ull * own > (unsigned long long)tot;
+}
+
 // Segment pass: a segment's entries are aggregated in the shared table and
 // written out as (label, sum, ~first position) records grouped by partition,
 // with the partition offsets.  In an identity sweep the segment's own winner
@@ -900,6 +938,10 @@ __global__ void __launch_bounds__(HUB_THREADS, 2) k_hub_seg(SweepArgs a)
         const int np = t.npart;
         int4 *out = a.hrec + item * HUB_SEG;
         int32_t *poff = a.hpoff + t.poff0 + (int64_t)seg * (np + 1);
+        if (hub_settled<MULTI>(a, ti, x.g)) {  // no records
+            for (int q = threadIdx.x; q <= np; q += NT) poff[q] = 0;
+            continue;
+        }
         if (a.identity) {
             const uint64_t ktv = stream_at(a.key_t, (uint64_t)x.lv + 1);
             const Cand best = block_argmax<NT>(identity_best<NT>(a, x.e0, lo, hi, ktv, threadIdx.x),
@@ -974,6 +1016,10 @@ __global__ void __launch_bounds__(HUB_THREADS, 2) k_hub_merge(SweepArgs a)
         if (!load_vtx<MULTI>(a, t.v, x)) continue;  // block-uniform
         const int p = (int)(item - t.part0);
         const int np = t.npart;
+        if (hub_settled<MULTI>(a, ti, x.g)) {  // the row keeps its own label
+            if (p == 0 && threadIdx.x == 0) a.lab_out[x.v] = x.own;
+            continue;
+        }
         const uint64_t ktv = stream_at(a.key_t, (uint64_t)x.lv + 1);
         const int glg = ilog2_ceil(2u * (uint32_t)x.d);
         unsigned long long *gk = a.hkey + t.tab;
@@ -1082,9 +1128,20 @@ int launch(int bucket, const SweepArgs &a, int num_sms, cudaStream_t st)
         n = 0;
         if (a.hmulti > 0) {  // long rows: segments, then label partitions
             const int64_t cap = (int64_t)num_sms * 2;
-            k_hub_seg<MULTI><<<(int)(a.hsegs < cap ? a.hsegs : cap), HUB_THREADS, hub_smem, st>>>(a);
+            SweepArgs h = a;
+            if (a.majority && !a.identity && a.hmaj) {
+                if (cudaMemsetAsync(a.hmaj, 0, (size_t)a.hmulti * 2 * sizeof(uint32_t), st) !=
+                    cudaSuccess)
+                    return -1;
+                k_hub_major<MULTI>
+                    <<<(int)(a.hsegs < cap * 2 ? a.hsegs : cap * 2), HUB_THREADS, 0, st>>>(a);
+                ++n;
+            } else {
+                h.hmaj = nullptr;
+            }
+            k_hub_seg<MULTI><<<(int)(a.hsegs < cap ? a.hsegs : cap), HUB_THREADS, hub_smem, st>>>(h);
             k_hub_merge<MULTI>
-                <<<(int)(a.hparts < cap ? a.hparts : cap), HUB_THREADS, hub_smem, st>>>(a);
+                <<<(int)(a.hparts < cap ? a.hparts : cap), HUB_THREADS, hub_smem, st>>>(h);
             n += 2;
         }
         if (a.len > a.hmulti) {  // the other hub rows: one CTA each
