@@ -36,27 +36,86 @@ __device__ __forceinline__ unsigned long long warp_sum64(unsigned long long v)
     return v;
 }
 
-// Running K_c contribution of one thread: consecutive rows of one community
-// are summed in a register and added with one atomic when the community
-// changes (a converged labelling often has one community for most rows, and
-// atomics on one address serialise).
+// Running K_c contributions of one thread, cached for two communities:
+// consecutive rows of a cached community are summed in a register and added
+// with one atomic when the entry is evicted (least recently used).  A
+// converged labelling often has one giant community, and atomics on one
+// address serialise, so the giant community's slot should stay cached.
 struct KcRun {
-    int64_t slot = -1;
-    unsigned long long sum = 0;
+    int64_t s0 = -1, s1 = -1;
+    unsigned long long k0 = 0, k1 = 0;
     __device__ __forceinline__ void add(unsigned long long *kc, int64_t s, unsigned long long k)
     {
-        if (s != slot) {
-            flush(kc);
-            slot = s;
+        if (s == s0) {
+            k0 += k;
+            return;
         }
-        sum += k;
+        if (s == s1) {  // becomes the most recent entry
+            s1 = s0;
+            s0 = s;
+            const unsigned long long t = k1;
+            k1 = k0;
+            k0 = t + k;
+            return;
+        }
+        if (s1 >= 0 && k1) atomicAdd(kc + s1, k1);
+        s1 = s0;
+        k1 = k0;
+        s0 = s;
+        k0 = k;
     }
     __device__ __forceinline__ void flush(unsigned long long *kc)
     {
-        if (slot >= 0 && sum) atomicAdd(kc + slot, sum);
-        sum = 0;
+        if (s0 >= 0 && k0) atomicAdd(kc + s0, k0);
+        if (s1 >= 0 && k1) atomicAdd(kc + s1, k1);
+        k0 = k1 = 0;
     }
 };
+
+// Running L and 2m contributions of one thread to one graph of a graph set.
+struct AccRun {
+    int32_t g = -1;
+    unsigned long long l = 0, w = 0;
+    __device__ __forceinline__ void add(unsigned long long *acc, int32_t gg, unsigned long long lv,
+                                        unsigned long long kv)
+    {
+        if (gg != g) {
+            flush(acc);
+            g = gg;
+        }
+        l += lv;
+        w += kv;
+    }
+    __device__ __forceinline__ void flush(unsigned long long *acc)
+    {
+        if (g >= 0 && w) {
+            atomicAdd(acc + 4 * (int64_t)g, l);
+            atomicAdd(acc + 4 * (int64_t)g + 1, w);
+        }
+        l = w = 0;
+    }
+};
+
+// Sum every thread's (l, w) of a single graph into acc[0..1], one pair of
+// global atomics per block (every thread of the block calls this).
+__device__ __forceinline__ void block_flush_lw(unsigned long long *acc, unsigned long long l,
+                                               unsigned long long w)
+{
+    __shared__ unsigned long long s_lw[2];
+    if (threadIdx.x == 0) s_lw[0] = s_lw[1] = 0;
+    __syncthreads();
+    l = warp_sum64(l);
+    w = warp_sum64(w);
+    if ((threadIdx.x & 31) == 0 && w) {
+        atomicAdd(s_lw, l);
+        atomicAdd(s_lw + 1, w);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && s_lw[1]) {
+        atomicAdd(acc, s_lw[0]);
+        atomicAdd(acc + 1, s_lw[1]);
+    }
+}
 
 struct MV {  // one vertex as the modularity pass sees it
     int32_t v, g, vb, d;
@@ -125,6 +184,7 @@ __global__ void __launch_bounds__(256) k_mod_small(ModArgs a)
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long l_acc = 0, w_acc = 0;
     KcRun run;
+    AccRun graph_run;
     for (int64_t tile = wid; tile * 32 < a.len; tile += nw) {
         const int64_t i = tile * 32 + lane;
         MV x{0, 0, 0, 0, 0};
@@ -168,11 +228,18 @@ __global__ void __launch_bounds__(256) k_mod_small(ModArgs a)
             const unsigned og = __match_any_sync(FULL, act ? (unsigned)o : 0xFFFFFFFFu);
             const uint32_t kv = __reduce_add_sync(og, kw);
             const uint32_t lv = __reduce_add_sync(og, lw);
-            if (act && lane == __ffs(og) - 1) {
-                run.add(a.kc, (int64_t)o_vb + o_c, kv);
+            const bool row_lead = act && lane == __ffs(og) - 1;
+            // rows of one community in the chunk add to K_c together: k_v < 2^31,
+            // so the sum is formed from 16-bit halves (each sum < 2^21)
+            const int32_t slot = o_vb + o_c;  // < 2^31 (vertex count bound)
+            const unsigned sg = __match_any_sync(FULL, row_lead ? (unsigned)slot : 0xFFFFFFFFu);
+            const uint32_t k_lo = __reduce_add_sync(sg, row_lead ? kv & 0xFFFFu : 0u);
+            const uint32_t k_hi = __reduce_add_sync(sg, row_lead ? kv >> 16 : 0u);
+            if (row_lead) {
+                if (lane == __ffs(sg) - 1)
+                    run.add(a.kc, slot, (unsigned long long)k_lo + ((unsigned long long)k_hi << 16));
                 if (MULTI) {
-                    atomicAdd(a.acc + 4 * (int64_t)o_g, (unsigned long long)lv);
-                    atomicAdd(a.acc + 4 * (int64_t)o_g + 1, (unsigned long long)kv);
+                    graph_run.add(a.acc, o_g, lv, kv);
                 } else {
                     l_acc += lv;
                     w_acc += kv;
@@ -183,14 +250,10 @@ __global__ void __launch_bounds__(256) k_mod_small(ModArgs a)
         }
     }
     run.flush(a.kc);
-    if (!MULTI) {
-        l_acc = warp_sum64(l_acc);
-        w_acc = warp_sum64(w_acc);
-        if (lane == 0 && w_acc) {
-            atomicAdd(a.acc, l_acc);
-            atomicAdd(a.acc + 1, w_acc);
-        }
-    }
+    if (MULTI)
+        graph_run.flush(a.acc);
+    else
+        block_flush_lw(a.acc, l_acc, w_acc);
 }
 
 // rows of degree > 32: NT threads per row, aligned 16-byte blocks
@@ -205,6 +268,7 @@ __global__ void __launch_bounds__(NT > 256 ? NT : 256) k_mod_rows(ModArgs a)
     const int t = threadIdx.x % NT;
     unsigned long long l_tot = 0, w_tot = 0;
     KcRun run;
+    AccRun graph_run;
     // every group of the CTA makes the same number of trips (barriers below)
     for (int64_t base = (int64_t)blockIdx.x * G; base < a.len; base += (int64_t)gridDim.x * G) {
         const int64_t item = base + grp;
@@ -240,8 +304,7 @@ __global__ void __launch_bounds__(NT > 256 ? NT : 256) k_mod_rows(ModArgs a)
         if (t == 0 && have) {
             run.add(a.kc, (int64_t)x.vb + cv, kv);
             if (MULTI) {
-                atomicAdd(a.acc + 4 * (int64_t)x.g, lv);
-                atomicAdd(a.acc + 4 * (int64_t)x.g + 1, kv);
+                graph_run.add(a.acc, x.g, lv, kv);
             } else {
                 l_tot += lv;
                 w_tot += kv;
@@ -249,21 +312,24 @@ __global__ void __launch_bounds__(NT > 256 ? NT : 256) k_mod_rows(ModArgs a)
         }
     }
     run.flush(a.kc);
-    if (!MULTI && t == 0 && w_tot) {
-        atomicAdd(a.acc, l_tot);
-        atomicAdd(a.acc + 1, w_tot);
-    }
+    if (MULTI)
+        graph_run.flush(a.acc);
+    else
+        block_flush_lw(a.acc, l_tot, w_tot);
 }
 
 // sum of K_c^2 per graph: each thread squares a run of consecutive slots and
 // flushes its 128-bit sum whenever the run crosses into another graph
 constexpr int SQ_RUN = 64;
 
+__device__ __forceinline__ void sumsq_block_add(unsigned long long *s_acc, unsigned long long hi,
+                                                unsigned long long lo);
+
 template <bool MULTI>
 __global__ void __launch_bounds__(256) k_mod_sumsq(ModArgs a, int64_t nslots)
 {
     const int64_t first = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * SQ_RUN;
-    if (first >= nslots) return;
+    if (MULTI && first >= nslots) return;
     const int64_t last = first + SQ_RUN < nslots ? first + SQ_RUN : nslots;
     int32_t g = MULTI ? a.vgraph[first] : 0;
     unsigned long long hi = 0, lo = 0;
@@ -281,7 +347,38 @@ __global__ void __launch_bounds__(256) k_mod_sumsq(ModArgs a, int64_t nslots)
         lo += sq_lo;
         hi += sq_hi + (lo < sq_lo ? 1ull : 0ull);
     }
-    if (hi | lo) add_u128(a.acc + 4 * (int64_t)g + 2, hi, lo);
+    if constexpr (MULTI) {
+        if (hi | lo) add_u128(a.acc + 4 * (int64_t)g + 2, hi, lo);
+    } else {
+        sumsq_block_add(a.acc + 2, hi, lo);
+    }
+}
+
+// one graph: 128-bit sums over the warp, then the block, then one add
+__device__ __forceinline__ void sumsq_block_add(unsigned long long *s_acc, unsigned long long hi,
+                                                unsigned long long lo)
+{
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        const unsigned long long olo = __shfl_xor_sync(FULL, lo, o);
+        const unsigned long long ohi = __shfl_xor_sync(FULL, hi, o);
+        lo += olo;
+        hi += ohi + (lo < olo ? 1ull : 0ull);
+    }
+    __shared__ unsigned long long s_hl[2 * 8];
+    const int wib = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        s_hl[2 * wib] = hi;
+        s_hl[2 * wib + 1] = lo;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
+            lo += s_hl[2 * k + 1];
+            hi += s_hl[2 * k] + (lo < s_hl[2 * k + 1] ? 1ull : 0ull);
+        }
+        if (hi | lo) add_u128(s_acc, hi, lo);
+    }
 }
 
 int grid_cap(int64_t blocks, int cap) { return (int)(blocks < 1 ? 1 : (blocks > cap ? cap : blocks)); }
