@@ -271,6 +271,8 @@ __device__ __forceinline__ Cand block_argmax(const Cand &c, int strict, Cand *s_
 // ----------------------------------------------------------------------------
 // small bucket: several rows per warp chunk
 // ----------------------------------------------------------------------------
+constexpr int TINY = 8;  // rows of up to TINY entries get one lane each
+
 template <bool MULTI>
 __global__ void __launch_bounds__(256, 6) k_small(SweepArgs a)
 {
@@ -288,7 +290,73 @@ __global__ void __launch_bounds__(256, 6) k_small(SweepArgs a)
         int d = ok ? x.d : 0;
         const int32_t own = ok ? x.own : 0;
 
-        if (__any_sync(FULL, ok && try_majority(a, x.g, true))) {
+        // Rows of at most TINY entries: one lane per row.  The lane loads the
+        // row and forms every entry's label total over the row in registers
+        // (O(d^2) compares); the first entry reaching the maximum holds the
+        // label with the earliest first position (strict ties).
+        const bool tiny = d >= 1 && d <= TINY;
+        if (__any_sync(FULL, tiny)) {
+            int32_t lab[TINY];
+            uint32_t wt[TINY];
+#pragma unroll
+            for (int j = 0; j < TINY; ++j) {
+                lab[j] = EMPTY;
+                wt[j] = 0u;
+                if (tiny && j < d) {
+                    const int64_t e = x.e0 + j;
+                    const int32_t u = ld_entry(a.idx + e);
+                    wt[j] = a.wts ? (uint32_t)ld_entry(a.wts + e) : 1u;
+                    lab[j] = a.identity ? u : neighbour_label(a, (int64_t)x.vb + u, u);
+                }
+            }
+            // entries past the row are EMPTY with weight 0: their totals are 0
+            uint32_t bs = 0u;
+            int32_t bl = own;
+#pragma unroll
+            for (int j = 0; j < TINY; ++j) {
+                uint32_t t = 0u;
+#pragma unroll
+                for (int k = 0; k < TINY; ++k) t += lab[k] == lab[j] ? wt[k] : 0u;
+                if (t > bs) {
+                    bs = t;
+                    bl = lab[j];
+                }
+            }
+            if (!a.strict && tiny) {
+                // among the labels of maximum total, the least tie key (then
+                // the earliest first position)
+                uint64_t bh = ~0ull;
+#pragma unroll
+                for (int j = 0; j < TINY; ++j) {
+                    uint32_t t = 0u;
+#pragma unroll
+                    for (int k = 0; k < TINY; ++k) t += lab[k] == lab[j] ? wt[k] : 0u;
+                    if (t == bs) {
+                        const uint64_t h = tie_key(a.key_t, x.lv, lab[j]);
+                        if (h < bh) {
+                            bh = h;
+                            bl = lab[j];
+                        }
+                    }
+                }
+            }
+            const bool ch = tiny && bl != own;
+            if (tiny) {
+                a.lab_out[x.v] = bl;
+                d = 0;  // done: left out of the passes below
+            }
+            if (MULTI) {
+                const unsigned chm = __ballot_sync(FULL, ch);
+                if (ch) {
+                    const unsigned gg = __match_any_sync(chm, (unsigned)x.g);
+                    if (lane == __ffs(gg) - 1) atomicAdd(a.changed + x.g, __popc(gg));
+                }
+            } else {
+                my_changed += __popc(__ballot_sync(FULL, ch));
+            }
+        }
+
+        if (__any_sync(FULL, d > 0 && try_majority(a, x.g, true))) {
             // Majority pass: rows are read as aligned 16-byte blocks, several
             // rows per 32-block chunk; a row whose own label holds more than
             // half of its weight keeps it (the unique maximum) and drops out.
