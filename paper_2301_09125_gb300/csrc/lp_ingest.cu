@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(BK) k_bucket_count(const int32_t *off, int32_t
     }
     __syncthreads();
     if (threadIdx.x < NUM_BUCKETS) {
-        blk[(int64_t)blockIdx.x * NUM_BUCKETS + threadIdx.x] = cnt[threadIdx.x];
+        blk[(int64_t)threadIdx.x * gridDim.x + blockIdx.x] = cnt[threadIdx.x];
         if (ent[threadIdx.x]) atomicAdd(entries + threadIdx.x, ent[threadIdx.x]);
     }
 }
@@ -245,31 +245,39 @@ __device__ int64_t block_exclusive_scan(int64_t x, int64_t *s_warp, int64_t *tot
     return r;
 }
 
-// one block: per bucket, exclusive scan of the per-block counts (in place)
-// out[0..4) bucket lengths, out[4..8) bucket starts in the list
-__global__ void __launch_bounds__(BK) k_bucket_scan(int32_t *blk, int64_t nblk, int64_t *out)
+// Counting-sort scans.  Per-block counts are stored class-major: the count
+// of class c in block b at hist[c * nblk + b].  One block per class turns its
+// counts into exclusive offsets within the class (in place) and records the
+// class size; one block then turns the sizes into class starts.
+__global__ void __launch_bounds__(1024) k_class_scan(int32_t *hist, int64_t nblk,
+                                                      int64_t *class_size)
 {
     __shared__ int64_t s_warp[33];
-    int64_t totals[NUM_BUCKETS];
-    for (int c = 0; c < NUM_BUCKETS; ++c) {
-        int64_t running = 0;
-        for (int64_t b0 = 0; b0 < nblk; b0 += BK) {
-            const int64_t b = b0 + threadIdx.x;
-            const int64_t x = b < nblk ? blk[b * NUM_BUCKETS + c] : 0;
-            int64_t tot;
-            const int64_t ex = block_exclusive_scan(x, s_warp, &tot);
-            if (b < nblk) blk[b * NUM_BUCKETS + c] = (int32_t)(running + ex);
-            running += tot;
-        }
-        totals[c] = running;
+    int32_t *h = hist + (int64_t)blockIdx.x * nblk;
+    int64_t running = 0;
+    for (int64_t i0 = 0; i0 < nblk; i0 += 1024) {
+        const int64_t i = i0 + threadIdx.x;
+        const int64_t x = i < nblk ? h[i] : 0;
+        int64_t tot;
+        const int64_t ex = block_exclusive_scan(x, s_warp, &tot);
+        if (i < nblk) h[i] = (int32_t)(running + ex);
+        running += tot;
     }
-    if (threadIdx.x == 0) {
-        int64_t begin = 0;
-        for (int c = 0; c < NUM_BUCKETS; ++c) {
-            out[c] = totals[c];
-            out[NUM_BUCKETS + c] = begin;
-            begin += totals[c];
-        }
+    if (threadIdx.x == 0) class_size[blockIdx.x] = running;
+}
+
+__global__ void __launch_bounds__(1024) k_class_begin(const int64_t *class_size, int64_t nc,
+                                                       int64_t *class_begin)
+{
+    __shared__ int64_t s_warp[33];
+    int64_t running = 0;
+    for (int64_t i0 = 0; i0 < nc; i0 += 1024) {
+        const int64_t i = i0 + threadIdx.x;
+        const int64_t x = i < nc ? class_size[i] : 0;
+        int64_t tot;
+        const int64_t ex = block_exclusive_scan(x, s_warp, &tot);
+        if (i < nc) class_begin[i] = running + ex;
+        running += tot;
     }
 }
 
@@ -300,7 +308,7 @@ __global__ void __launch_bounds__(BK) k_bucket_scatter(const int32_t *off, int32
     }
     __syncthreads();
     if (b >= 0)
-        list[cnt[NUM_BUCKETS + b] + blk[(int64_t)blockIdx.x * NUM_BUCKETS + b] + s_pre[b][wib] + rank] =
+        list[cnt[NUM_BUCKETS + b] + blk[(int64_t)b * gridDim.x + blockIdx.x] + s_pre[b][wib] + rank] =
             (int32_t)v;
 }
 
@@ -457,38 +465,15 @@ __global__ void __launch_bounds__(WV) k_wave_hist(const int32_t *list, int64_t l
     for (int c = threadIdx.x; c < nc; c += WV) hist[(int64_t)c * gridDim.x + blockIdx.x] = s_cnt[c];
 }
 
-// exclusive scan of hist in class-major, block-minor order (one block)
-__global__ void __launch_bounds__(1024) k_wave_scan(int32_t *hist, int64_t total, int64_t nblk,
-                                                     int64_t *class_size)
-{
-    __shared__ int64_t s_warp[33];
-    int64_t running = 0;
-    for (int64_t i0 = 0; i0 < total; i0 += 1024) {
-        const int64_t i = i0 + threadIdx.x;
-        const int64_t x = i < total ? hist[i] : 0;
-        int64_t tot;
-        const int64_t ex = block_exclusive_scan(x, s_warp, &tot);
-        if (i < total) hist[i] = (int32_t)(running + ex);
-        running += tot;
-    }
-    // class sizes from consecutive class starts
-    __syncthreads();
-    const int64_t nc = total / nblk;
-    for (int64_t c = threadIdx.x; c < nc; c += 1024) {
-        const int64_t start = hist[c * nblk];
-        const int64_t next = c + 1 < nc ? (int64_t)hist[(c + 1) * nblk] : running;
-        class_size[c] = next - start;
-    }
-}
-
 __global__ void __launch_bounds__(WV) k_wave_scatter(const int32_t *list, int64_t len,
                                                       WaveParams p, const int32_t *vgraph,
                                                       const int32_t *g_vbase, const int32_t *hist,
-                                                      int32_t *out)
+                                                      const int64_t *class_begin, int32_t *out)
 {
     extern __shared__ int32_t s_cur[];
     const int nc = NUM_BUCKETS * (int)p.waves;
-    for (int c = threadIdx.x; c < nc; c += WV) s_cur[c] = hist[(int64_t)c * gridDim.x + blockIdx.x];
+    for (int c = threadIdx.x; c < nc; c += WV)
+        s_cur[c] = (int32_t)class_begin[c] + hist[(int64_t)c * gridDim.x + blockIdx.x];
     __syncthreads();
     const int64_t i = (int64_t)blockIdx.x * WV + threadIdx.x;
     if (i < len) {
@@ -577,9 +562,10 @@ int ingest_bucket(const int32_t *off, int32_t nv, const int32_t *vgraph, const i
     k_bucket_count<<<(int)nblk, BK, 0, st>>>(
         off, nv, vgraph, th, blk,
         reinterpret_cast<unsigned long long *>(d_counts + 2 * NUM_BUCKETS));
-    k_bucket_scan<<<1, BK, 0, st>>>(blk, nblk, d_counts);
+    k_class_scan<<<NUM_BUCKETS, 1024, 0, st>>>(blk, nblk, d_counts);
+    k_class_begin<<<1, 1024, 0, st>>>(d_counts, NUM_BUCKETS, d_counts + NUM_BUCKETS);
     k_bucket_scatter<<<(int)nblk, BK, 0, st>>>(off, nv, vgraph, th, blk, d_counts, list);
-    *launches += 3;
+    *launches += 4;
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -592,10 +578,11 @@ int degrees_of(const int32_t *off, const int32_t *vgraph, const int32_t *list, i
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
+// class starts (int64, first) and per-block class counts
 int64_t wave_hist_ints(int64_t list_len, int waves)
 {
     const int64_t nblk = (list_len + WV - 1) / WV;
-    return (nblk > 0 ? nblk : 1) * NUM_BUCKETS * (int64_t)waves;
+    return ((nblk > 0 ? nblk : 1) + 2) * NUM_BUCKETS * (int64_t)waves;
 }
 
 int wave_partition(const int32_t *list, int64_t len, const int64_t *bucket_begin,
@@ -612,10 +599,14 @@ int wave_partition(const int32_t *list, int64_t len, const int64_t *bucket_begin
     p.magic = fastmod_magic((uint32_t)waves);
     const int64_t nblk = (len + WV - 1) / WV;
     const size_t smem = (size_t)nc * sizeof(int32_t);
-    k_wave_hist<<<(int)nblk, WV, smem, st>>>(list, len, p, vgraph, g_vbase, hist);
-    k_wave_scan<<<1, 1024, 0, st>>>(hist, nblk * nc, nblk, d_totals);
-    k_wave_scatter<<<(int)nblk, WV, smem, st>>>(list, len, p, vgraph, g_vbase, hist, out);
-    *launches += 3;
+    int64_t *class_begin = reinterpret_cast<int64_t *>(hist);
+    int32_t *counts = hist + 2 * (int64_t)nc;
+    k_wave_hist<<<(int)nblk, WV, smem, st>>>(list, len, p, vgraph, g_vbase, counts);
+    k_class_scan<<<nc, 1024, 0, st>>>(counts, nblk, d_totals);
+    k_class_begin<<<1, 1024, 0, st>>>(d_totals, nc, class_begin);
+    k_wave_scatter<<<(int)nblk, WV, smem, st>>>(list, len, p, vgraph, g_vbase, counts,
+                                                class_begin, out);
+    *launches += 4;
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -175,6 +175,42 @@ def test_sync_parity_per_bucket(lp, shape, strict):
 
 
 @pytest.mark.parametrize("strict", [True, False])
+def test_tiny_rows_with_ties(lp, strict):
+    """Rows of at most 8 entries take one lane each: unit weights make most
+    label totals tie, and the degrees straddle the 8-entry boundary."""
+    off, idx, w = random_graph(4000, 4 / 4000, 21)
+    deg = np.diff(off)
+    assert (deg == 1).any() and (deg == 8).any() and (deg > 8).any()
+    assert_sync_parity(lp, off, idx, w, strict=strict, seed=4)
+    assert_async_parity(lp, off, idx, w, 3, strict=strict, seed=4)
+
+
+def test_batch_of_tiny_row_graphs(lp):
+    """Graph sets of road grids and k-mer paths (every row has at most 8
+    entries): per-graph change counts and labels as run one by one."""
+    graphs = [gg.grid_road(48 + 16 * i, seed=i) for i in range(5)]
+    graphs += [gg.kmer_like(3000 + 1000 * i, seed=i) for i in range(5)]
+    assert all(np.diff(g.offsets).max() <= 8 for g in graphs)
+    triples = [(g.offsets, g.indices, g.weights) for g in graphs]
+    h = lp.lp_batch_create(triples)
+    try:
+        for mode, waves, strict in (("sync", None, True), ("sync", None, False),
+                                    ("async", 3, True), ("async", 3, False)):
+            kw = {} if waves is None else {"waves": waves}
+            res = lp.lp_batch_run(h, len(graphs), tolerance=0.05, max_iter=20, mode=mode,
+                                  strict=strict, seed=6, **kw)
+            for i, g in enumerate(graphs):
+                lab = lp.lp_batch_labels_get(h, i, g.n)
+                ref, iters, conv, hist = oracle.rak(g.offsets, g.indices, g.weights, 0.05, 20,
+                                                    mode, strict=strict, seed=6, **kw)
+                assert res[i].iterations == iters and bool(res[i].converged) == conv, i
+                assert res[i].last_changed == hist[-1], i
+                assert np.array_equal(lab, ref), (mode, strict, i)
+    finally:
+        lp.lp_batch_destroy(h)
+
+
+@pytest.mark.parametrize("strict", [True, False])
 def test_identity_first_sweep_cluster_rows(lp, strict):
     """Sorted rows without repeats: the first sweep takes the identity path,
     including rows swept by CTA clusters; sync and 2-wave async stay exact."""
