@@ -98,13 +98,9 @@ __global__ void __launch_bounds__(NA_THREADS) k_sweep_noalloc(NoAllocArgs a)
                 w = a.wts ? __ldg(a.wts + rs + k) : 1;
                 l = __ldg(a.lab_in + u);
             }
-            const unsigned grp = __match_any_sync(FULL, (unsigned)l);
-            const int s = __reduce_add_sync(grp, w);
-            if (act && (threadIdx.x & 31) == __ffs(grp) - 1) {
-                if (!table_add(tk, ts, tp, NA_TABLE_LG, NA_PROBE, l, s, k)) {
-                    s_spilled = 1;
-                    table_add(gk, gs, gp, glg, 1 << glg, l, s, k);
-                }
+            if (act && !table_add(tk, ts, tp, NA_TABLE_LG, NA_PROBE, l, w, k)) {
+                s_spilled = 1;
+                table_add(gk, gs, gp, glg, 1 << glg, l, w, k);
             }
         }
         __syncthreads();

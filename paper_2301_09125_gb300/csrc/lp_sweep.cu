@@ -9,8 +9,7 @@
 //                              the per-owner argmax is a segmented redux.sync
 //                              maximum, so no table is needed at all.
 //   warp   33..128   k_warp  : one warp per vertex, a 256-slot open-addressing
-//                              table per warp in shared memory; duplicate labels
-//                              of a 32-entry chunk are merged before insertion.
+//                              table per warp in shared memory.
 //   cta    129..512  k_cta   : one 128-thread CTA per vertex, 1024-slot table.
 //   cta2   513..1024 k_cta   : one 256-thread CTA per vertex, 2048-slot table.
 //   hub    1025..4096 k_cta  : one 512-thread CTA per vertex, 8192-slot table.
@@ -20,6 +19,10 @@
 //                              grouped into label partitions, then one CTA per
 //                              partition merges the records of every segment
 //                              and the last one of the row picks its label.
+// Table rows insert their entries lane by lane with shared-memory atomics (a
+// warp-wide __match_any_sync merge of equal labels before insertion cost more
+// than the atomics it saved); the one label a warp sees most once labels have
+// settled is summed in registers instead (HotLabel).
 // Every table slot holds (label, summed weight, ~first position); the first
 // position of a label is the smallest row position at which it occurs, so the
 // argmax key (weight desc, [non-strict key asc,] first position asc) is unique
@@ -493,6 +496,31 @@ __global__ void __launch_bounds__(256, 6) k_small(SweepArgs a)
     if (!MULTI && lane == 0 && my_changed) atomicAdd(a.changed, (int)my_changed);
 }
 
+// Insert one quad (entries 4*blk .. 4*blk+3 of a row starting at global
+// entry `row`) into a shared table of 2^lg slots: entries of the warp's hot
+// label are summed in registers, every other entry is added by its lane.
+__device__ __forceinline__ void insert_quad(const Quad &q, int64_t blk, int64_t row,
+                                            HotLabel &hot, int32_t *tk, int32_t *ts,
+                                            uint32_t *tp, int lg)
+{
+    hot.pick(q);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const uint32_t pos = (uint32_t)(blk * 4 + j - row);
+        if (!hot.take(q.l[j], q.w[j], pos) && q.l[j] != EMPTY)
+            table_add(tk, ts, tp, lg, 1 << lg, q.l[j], q.w[j], pos);
+    }
+}
+
+// the warp's hot label total, inserted once
+__device__ __forceinline__ void insert_hot(const HotLabel &hot, int32_t *tk, int32_t *ts,
+                                           uint32_t *tp, int lg)
+{
+    const int hs = hot.total();
+    const uint32_t hp = hot.first();
+    if ((threadIdx.x & 31) == 0 && hs > 0) table_add(tk, ts, tp, lg, 1 << lg, hot.label, hs, hp);
+}
+
 // ----------------------------------------------------------------------------
 // warp bucket: one warp per vertex, private shared table
 // ----------------------------------------------------------------------------
@@ -512,6 +540,8 @@ __global__ void __launch_bounds__(256, MULTI ? 4 : 5) k_warp(SweepArgs a)
     int32_t *tk_atomic = s_key + wib * WARP_TABLE;
     volatile int32_t *ts = s_sum + wib * WARP_TABLE;
     volatile uint32_t *tp = s_np + wib * WARP_TABLE;
+    int32_t *ts_atomic = s_sum + wib * WARP_TABLE;
+    uint32_t *tp_atomic = s_np + wib * WARP_TABLE;
     for (int j = lane; j < WARP_TABLE; j += 32) {
         tk[j] = EMPTY;
         ts[j] = 0;
@@ -566,47 +596,15 @@ __global__ void __launch_bounds__(256, MULTI ? 4 : 5) k_warp(SweepArgs a)
                 }
             }
         }
-        // one writer per label at a time, so plain updates suffice
-        auto insert = [&](int32_t l, int s, uint32_t pos) {
-            const uint32_t np = 0xFFFFFFFFu - pos;
-            uint32_t h = slot_hash(l, WARP_LG);
-            for (int probe = 0; probe < WARP_TABLE; ++probe) {  // <= 128 labels: found
-                int32_t cur = tk[h];
-                if (cur == EMPTY) {
-                    cur = atomicCAS(tk_atomic + h, EMPTY, l);
-                    if (cur == EMPTY) cur = l;
-                }
-                if (cur == l) {
-                    ts[h] = ts[h] + s;
-                    if (np > tp[h]) tp[h] = np;
-                    break;
-                }
-                h = (h + 1) & (WARP_TABLE - 1);
-            }
-        };
+        // <= 128 labels in 256 slots: every insert finds its slot
         HotLabel hot;
         for (int64_t base = b0; base <= b_hi; base += 32) {
             const int64_t blk = base + lane;
             const Quad q = one ? q1 : (blk <= b_hi ? load_quad(a, blk, lo, hi, x.vb) : empty_quad());
-            hot.pick(q);
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const uint32_t pos = (uint32_t)(blk * 4 + j - lo);
-                const int32_t l = hot.take(q.l[j], q.w[j], pos) ? EMPTY : q.l[j];
-                const unsigned grp = __match_any_sync(FULL, (unsigned)l);
-                const int s = __reduce_add_sync(grp, q.w[j]);
-                // one leader per label in this round; the leader (lowest lane)
-                // holds the round's first position
-                if (l != EMPTY && lane == __ffs(grp) - 1) insert(l, s, pos);
-                __syncwarp();
-            }
+            insert_quad(q, blk, lo, hot, tk_atomic, ts_atomic, tp_atomic, WARP_LG);
         }
-        {
-            const int hs = hot.total();
-            const uint32_t hp = hot.first();
-            if (lane == 0 && hs > 0) insert(hot.label, hs, hp);
-            __syncwarp();
-        }
+        insert_hot(hot, tk_atomic, ts_atomic, tp_atomic, WARP_LG);
+        __syncwarp();
 
         Cand best{0u, 0u, 0ull, EMPTY};
         if (a.strict) {
@@ -683,35 +681,6 @@ __device__ __forceinline__ Cand scan_table(int32_t *tk, int32_t *ts, uint32_t *t
         }
     }
     return best;
-}
-
-// Insert one quad (entries 4*blk .. 4*blk+3 of a row starting at global
-// entry `row`) into a shared table of 2^lg slots: the warp's hot label is
-// summed in registers, equal labels of the warp are merged with match / redux
-// before one insert per label.
-__device__ __forceinline__ void insert_quad(const Quad &q, int64_t blk, int64_t row,
-                                            HotLabel &hot, int32_t *tk, int32_t *ts,
-                                            uint32_t *tp, int lg)
-{
-    hot.pick(q);
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const uint32_t pos = (uint32_t)(blk * 4 + j - row);
-        const int32_t l = hot.take(q.l[j], q.w[j], pos) ? EMPTY : q.l[j];
-        const unsigned grp = __match_any_sync(FULL, (unsigned)l);
-        const int s = __reduce_add_sync(grp, q.w[j]);
-        if (l != EMPTY && (threadIdx.x & 31) == __ffs(grp) - 1)
-            table_add(tk, ts, tp, lg, 1 << lg, l, s, pos);
-    }
-}
-
-// the warp's hot label total, inserted once
-__device__ __forceinline__ void insert_hot(const HotLabel &hot, int32_t *tk, int32_t *ts,
-                                           uint32_t *tp, int lg)
-{
-    const int hs = hot.total();
-    const uint32_t hp = hot.first();
-    if ((threadIdx.x & 31) == 0 && hs > 0) table_add(tk, ts, tp, lg, 1 << lg, hot.label, hs, hp);
 }
 
 // Aggregate the entries [lo, hi) of a row starting at global entry `row` into
