@@ -105,6 +105,12 @@ __device__ __forceinline__ Cand warp_best(Cand c)
     return c;
 }
 
+// Lanes [lo, lo + len) of a warp as a mask (0 <= lo, lo + len <= 32).
+__device__ __forceinline__ unsigned lane_range(int lo, int len)
+{
+    return (len >= 32 ? 0xFFFFFFFFu : ((1u << len) - 1u)) << lo;
+}
+
 __device__ __forceinline__ int ilog2_ceil(uint32_t x)  // smallest lg with 2^lg >= x
 {
     return x <= 1 ? 0 : 32 - __clz(x - 1);

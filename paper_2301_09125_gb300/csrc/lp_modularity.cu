@@ -224,8 +224,10 @@ __global__ void __launch_bounds__(256) k_mod_small(ModArgs a)
             if (act)
                 mod_block(a, (o_e0 >> 2) + (lane - (o_qex - base)), o_e0, o_e0 + o_d, o_vb, o_c,
                           kw, lw);
-            // one row lies wholly in the chunk: its sums are k_v and L_v (< 2^31)
-            const unsigned og = __match_any_sync(FULL, act ? (unsigned)o : 0xFFFFFFFFu);
+            // the row's blocks fill lanes [o_qex - base, + its block count); one
+            // row lies wholly in the chunk, so its sums are k_v and L_v (< 2^31)
+            const int o_nq = (int)(((o_e0 + o_d - 1) >> 2) - (o_e0 >> 2) + 1);
+            const unsigned og = act ? lane_range(o_qex - base, o_nq) : ~lane_range(0, total);
             const uint32_t kv = __reduce_add_sync(og, kw);
             const uint32_t lv = __reduce_add_sync(og, lw);
             const bool row_lead = act && lane == __ffs(og) - 1;

@@ -3,11 +3,13 @@
 // adjacency order") or non-strict ("random") tie rule.
 //
 // Buckets by degree d:
-//   small  1..32     k_small : a warp packs several whole rows into one 32-lane
-//                              chunk; (owner, label) groups are found with
-//                              __match_any_sync and summed with redux.sync, and
-//                              the per-owner argmax is a segmented redux.sync
-//                              maximum, so no table is needed at all.
+//   small  1..32     k_small : rows of up to 8 entries take one lane each and
+//                              count their labels in registers; longer rows are
+//                              packed whole into 32-lane chunks, where equal
+//                              labels of a row are found with __match_any_sync
+//                              and summed with redux.sync and the per-row
+//                              argmax is a segmented redux.sync maximum, so no
+//                              table is needed at all.
 //   warp   33..128   k_warp  : one warp per vertex, a 256-slot open-addressing
 //                              table per warp in shared memory.
 //   cta    129..512  k_cta   : one 128-thread CTA per vertex, 1024-slot table.
@@ -398,7 +400,10 @@ __global__ void __launch_bounds__(256, 6) k_small(SweepArgs a)
                     const int64_t blk = (o_e0 >> 2) + (lane - (o_qex - base));
                     own_weight(load_quad(a, blk, o_e0, o_e0 + o_d, o_vb), o_own, ow, tw);
                 }
-                const unsigned og = __match_any_sync(FULL, act ? (unsigned)o : 0xFFFFFFFFu);
+                // the row's quads fill lanes [o_qex - base, + its quad count)
+                const int o_nq = (int)(((o_e0 + o_d - 1) >> 2) - (o_e0 >> 2) + 1);
+                const unsigned og =
+                    act ? lane_range(o_qex - base, o_nq) : ~lane_range(0, total);
                 const uint32_t OW = __reduce_add_sync(og, ow);
                 const uint32_t TW = __reduce_add_sync(og, tw);
                 const bool keep = act && lane == __ffs(og) - 1 && 2ull * OW > (unsigned long long)TW;
@@ -440,6 +445,7 @@ __global__ void __launch_bounds__(256, 6) k_small(SweepArgs a)
             }
             const bool act = lane < total;
             const int o_excl = __shfl_sync(FULL, excl, o);
+            const int o_d = __shfl_sync(FULL, d, o);
             const long long o_e0 = __shfl_sync(FULL, (long long)x.e0, o);
             const int o_vb = MULTI ? __shfl_sync(FULL, x.vb, o) : 0;
             const int o_lv = __shfl_sync(FULL, x.lv, o);
@@ -455,15 +461,16 @@ __global__ void __launch_bounds__(256, 6) k_small(SweepArgs a)
                 w = a.wts ? ld_entry(a.wts + e) : 1;
                 l = a.identity ? u : neighbour_label(a, (int64_t)o_vb + u, u);
             }
-            // group equal (owner, label) pairs; the lowest lane holds the first
-            // position (in an identity sweep every pair is distinct)
-            const unsigned long long key =
-                act ? (((unsigned long long)(unsigned)o << 32) | (unsigned)l) : ~0ull;
-            const unsigned grp = a.identity ? (1u << lane) : __match_any_sync(FULL, key);
+            // the owner's lanes (its whole row: rows fit in the chunk), then the
+            // lanes of the owner with an equal label; the lowest lane of a
+            // group holds its first position (in an identity sweep every
+            // label of a row is distinct)
+            const unsigned og = act ? lane_range(o_excl - base, o_d) : ~lane_range(0, total);
+            const unsigned grp =
+                a.identity ? (1u << lane) : __match_any_sync(FULL, (unsigned)l) & og;
             const int s = a.identity ? w : __reduce_add_sync(grp, w);
             const bool leader = act && lane == __ffs(grp) - 1;
             // segmented argmax over each owner's lanes
-            const unsigned og = __match_any_sync(FULL, act ? (unsigned)o : 0xFFFFFFFFu);
             const uint32_t hi = leader ? (uint32_t)s : 0u;
             const uint32_t npos = leader ? 0xFFFFFFFFu - (uint32_t)pos : 0u;
             const uint32_t mhi = __reduce_max_sync(og, hi);
