@@ -466,10 +466,27 @@ __global__ void __launch_bounds__(256, 6) k_small(SweepArgs a)
             // group holds its first position (in an identity sweep every
             // label of a row is distinct)
             const unsigned og = act ? lane_range(o_excl - base, o_d) : ~lane_range(0, total);
-            const unsigned grp =
-                a.identity ? (1u << lane) : __match_any_sync(FULL, (unsigned)l) & og;
-            const int s = a.identity ? w : __reduce_add_sync(grp, w);
-            const bool leader = act && lane == __ffs(grp) - 1;
+            int s = w;
+            bool leader = act;
+            if (!a.identity) {
+                // every lane sums the weights of its row's entries holding its
+                // label, reading the k-th entry of its own row from the lane
+                // holding it (rows of the chunk in step); the entry at the
+                // label's first position leads
+                s = 0;
+                int first = 32;
+                const int seg = o_excl - base;
+                const int dmax = __reduce_max_sync(FULL, act ? (unsigned)o_d : 0u);
+                for (int k = 0; k < dmax; ++k) {
+                    const int src = (seg + k) & 31;
+                    const int32_t lk = __shfl_sync(FULL, l, src);
+                    const int wk = __shfl_sync(FULL, w, src);
+                    const bool same = act && k < o_d && lk == l;
+                    s += same ? wk : 0;
+                    first = same && k < first ? k : first;
+                }
+                leader = act && pos == first;
+            }
             // segmented argmax over each owner's lanes
             const uint32_t hi = leader ? (uint32_t)s : 0u;
             const uint32_t npos = leader ? 0xFFFFFFFFu - (uint32_t)pos : 0u;
