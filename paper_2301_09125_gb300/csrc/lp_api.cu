@@ -896,9 +896,9 @@ struct GraphSet {
             // the first sweep from unique labels reads unique labels only in
             // its first wave (later waves see this sweep's new labels)
             a.identity = rows_distinct && it == 0 && !rs.p.init_labels && k == 0;
-            // labels read in the first sweep from unique labels rarely hold a
-            // majority of a row
-            a.majority = !(it == 0 && !rs.p.init_labels);
+            // labels read in the first two sweeps from unique labels rarely
+            // hold a majority of a row
+            a.majority = rs.p.init_labels || it >= 2;
             a.changed_prev = it > 0 ? changed + (int64_t)(it - 1) * G : nullptr;
             a.g_n = g_n;
             if (prof) {

@@ -80,17 +80,18 @@ struct VtxPipe {
     }
 };
 
-// Whether graph g's vertices try the majority test in this launch.  Kernels
-// that reuse the loaded row for their table path lose little when the test
-// fails and always try it; the small-row kernel reads its rows a second time
-// then, and tries it only after an iteration that changed fewer than a
-// quarter of the graph's labels (measured on R-MAT and SBM: by then most rows
-// hold an own-label majority).
-__device__ __forceinline__ bool try_majority(const SweepArgs &a, int32_t g, bool costly)
+// Whether graph g's vertices try the majority test in this launch: not in
+// the first two sweeps from unique labels (the host clears a.majority; the
+// labels are still too fragmented: on R-MAT no row longer than 32 entries
+// passed the test in the second sweep and all of them in the third), and only
+// after an iteration that changed fewer than 60% of the graph's labels (a
+// synchronous run that oscillates changes nearly all of them and no row
+// passes).
+__device__ __forceinline__ bool try_majority(const SweepArgs &a, int32_t g)
 {
     if (!a.majority || a.identity) return false;
-    if (!costly || !a.changed_prev) return true;
-    return 4ll * __ldg(a.changed_prev + g) < (long long)__ldg(a.g_n + g);
+    if (!a.changed_prev) return true;
+    return 5ll * __ldg(a.changed_prev + g) < 3ll * __ldg(a.g_n + g);
 }
 
 // Label of neighbour u (local id u, global index gi) as seen by this launch.
@@ -361,7 +362,7 @@ __global__ void __launch_bounds__(256, 6) k_small(SweepArgs a)
             }
         }
 
-        if (__any_sync(FULL, d > 0 && try_majority(a, x.g, true))) {
+        if (__any_sync(FULL, d > 0 && try_majority(a, x.g))) {
             // Majority pass: rows are read as aligned 16-byte blocks, several
             // rows per 32-block chunk; a row whose own label holds more than
             // half of its weight keeps it (the unique maximum) and drops out.
@@ -609,7 +610,7 @@ __global__ void __launch_bounds__(256, MULTI ? 4 : 5) k_warp(SweepArgs a)
         Quad q1 = empty_quad();
         if (one) {
             if (b0 + lane <= b_hi) q1 = load_quad(a, b0 + lane, lo, hi, x.vb);
-            if (try_majority(a, x.g, false)) {
+            if (try_majority(a, x.g)) {
                 uint32_t ow = 0, tw = 0;
                 own_weight(q1, own, ow, tw);
                 ow = __reduce_add_sync(FULL, ow);
@@ -801,7 +802,7 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 2048 / NT) k_cta(SweepArgs
             // a label holding more than half of the row's weight is the
             // unique maximum: the vertex keeps its own label if it does
             bool settled = false;
-            if (try_majority(a, x.g, false)) {
+            if (try_majority(a, x.g)) {
                 uint32_t ow = 0, tw = 0;
 #pragma unroll
                 for (int r = 0; r < R; ++r) own_weight(q[r], x.own, ow, tw);
@@ -940,7 +941,7 @@ __global__ void __launch_bounds__(HUB_THREADS) k_hub_major(SweepArgs a)
         const HubTask t = a.htask[ti];
         Vtx x;
         // a pre-pass costs under a tenth of a high-cardinality segment pass
-        if (!load_vtx<MULTI>(a, t.v, x) || !try_majority(a, x.g, false)) continue;  // uniform
+        if (!load_vtx<MULTI>(a, t.v, x) || !try_majority(a, x.g)) continue;  // uniform
         const int64_t lo = x.e0 + (int64_t)(item - t.seg0) * HUB_SEG;
         const int64_t hi = min(lo + HUB_SEG, x.e0 + x.d);
         uint32_t ow = 0u, tw = 0u;
@@ -958,7 +959,7 @@ __global__ void __launch_bounds__(HUB_THREADS) k_hub_major(SweepArgs a)
 template <bool MULTI>
 __device__ __forceinline__ bool hub_settled(const SweepArgs &a, int64_t ti, int32_t g)
 {
-    if (!a.hmaj || !try_majority(a, g, false)) return false;
+    if (!a.hmaj || !try_majority(a, g)) return false;
     const uint32_t own = __ldcg(a.hmaj + 2 * ti), tot = __ldcg(a.hmaj + 2 * ti + 1);
     return 2ull * own > (unsigned long long)tot;
 }
