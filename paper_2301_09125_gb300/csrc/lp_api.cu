@@ -255,6 +255,7 @@ struct GraphSet {
     uint32_t *hnpos = nullptr;
     int32_t *hused = nullptr, *hdone = nullptr, *hnused = nullptr;
     uint32_t *hmaj = nullptr;  // long rows' majority counters (2 per hub task)
+    uint8_t *vmaj = nullptr;   // per vertex: settled by the majority pre-pass
     // modularity and label staging scratch
     unsigned long long *kc = nullptr, *macc = nullptr, *h_macc = nullptr;
     int64_t kc_cap = 0;
@@ -322,6 +323,7 @@ struct GraphSet {
         fh(h_ing);
         f(d_counts);
         fh(h_counts);
+        f(vmaj);
         if (ev0) cudaEventDestroy(ev0);
         if (ev1) cudaEventDestroy(ev1);
         lab[0] = lab[1] = list = wlist = vgraph = g_vbase = g_active = g_n = nullptr;
@@ -336,6 +338,7 @@ struct GraphSet {
         hpoff = nullptr;
         hpbest = nullptr;
         hmaj = nullptr;
+        vmaj = nullptr;
         hseg_task = hpart_task = hseg_task_w = hpart_task_w = nullptr;
         d_res = nullptr;
         d_stop = nullptr;
@@ -478,6 +481,8 @@ struct GraphSet {
             bb[c] = h_counts[NUM_BUCKETS + c];
             be[c] = h_counts[2 * NUM_BUCKETS + c];
         }
+        if (!vmaj && bl[2] + bl[3] + bl[HUB_BUCKET] > 0)
+            LP_TRY(dev_alloc(&vmaj, nv, "majority flags", st, device));
         // hub vertices: largest degree first, so the static CTA assignment of
         // the hub kernel balances
         if (bl[HUB_BUCKET] > 0) {
@@ -845,6 +850,7 @@ struct GraphSet {
         a.hpoff = hpoff;
         a.hpbest = hpbest;
         a.hmaj = hmaj;
+        a.vmaj = vmaj;
         a.waves = (uint32_t)waves;
         a.wave_magic = fastmod_magic((uint32_t)waves);
         return LP_OK;

@@ -133,6 +133,9 @@ struct SweepArgs {
     // per long-row task: own-label weight and total weight of the row (the
     // majority test of rows longer than HUB_ONE_MAX, summed over segments)
     uint32_t *hmaj;
+    // per vertex: 1 if the majority pre-pass of this launch settled its row
+    // (rows of the cta, cta2 and hub buckets; null = no pre-pass)
+    uint8_t *vmaj;
 };
 
 // Modularity arguments (a whole graph set; graph layout as for SweepArgs).

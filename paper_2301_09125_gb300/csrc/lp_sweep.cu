@@ -74,9 +74,11 @@ template <bool MULTI>
 struct VtxPipe {
     Vtx next;
     bool next_ok = false;
+    uint8_t next_maj = 0;  // the majority pre-pass flag (when there is one)
     __device__ __forceinline__ void fetch(const SweepArgs &a, int64_t item)
     {
         next_ok = item < a.len && load_vtx<MULTI>(a, a.list[item], next);
+        next_maj = next_ok && a.vmaj ? a.vmaj[next.v] : 0;
     }
 };
 
@@ -780,8 +782,13 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 2048 / NT) k_cta(SweepArgs
     for (int64_t item = blockIdx.x; item < a.len; item += gridDim.x) {
         const Vtx x = pipe.next;
         const bool ok = pipe.next_ok;
+        const uint8_t maj = pipe.next_maj;
         pipe.fetch(a, item + gridDim.x);
         if (!ok) continue;  // block-uniform
+        // the pre-pass of this launch tested the row (and wrote its label if
+        // it settled)
+        const bool pre = a.vmaj && try_majority(a, x.g);
+        if (pre && maj) continue;
         // slots in use for this vertex: 2^lg >= 2d (d <= CAP / 2 in this bucket)
         const int lg = min(ilog2_ceil(2u * (uint32_t)x.d), LG);
         const uint64_t ktv = stream_at(a.key_t, (uint64_t)x.lv + 1);
@@ -802,7 +809,7 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 2048 / NT) k_cta(SweepArgs
             // a label holding more than half of the row's weight is the
             // unique maximum: the vertex keeps its own label if it does
             bool settled = false;
-            if (try_majority(a, x.g)) {
+            if (!pre && try_majority(a, x.g)) {
                 uint32_t ow = 0, tw = 0;
 #pragma unroll
                 for (int r = 0; r < R; ++r) own_weight(q[r], x.own, ow, tw);
@@ -837,6 +844,55 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 2048 / NT) k_cta(SweepArgs
         __syncthreads();
     }
     if (!MULTI && threadIdx.x == 0 && my_changed) atomicAdd(a.changed, (int)my_changed);
+}
+
+// ----------------------------------------------------------------------------
+// Majority pre-pass for the rows of the CTA kernels (cta, cta2 and hub rows up
+// to HUB_ONE_MAX entries): one warp per row counts the weight of the entries
+// carrying the row's own label.  A row where that label holds more than half
+// of the weight keeps it (the unique maximum): the label is written here and
+// the row's flag tells the CTA kernel to skip it.  Once labels have settled
+// nearly every such row passes, and a warp reads a row with a fraction of
+// the instructions a CTA spends on it.
+// ----------------------------------------------------------------------------
+template <bool MULTI>
+__global__ void __launch_bounds__(256) k_major_rows(SweepArgs a)
+{
+    if (a.stop && *a.stop) return;  // launched past the end of the run
+    if (!MULTI && !try_majority(a, 0)) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    VtxPipe<MULTI> pipe;
+    pipe.fetch(a, wid);
+    for (int64_t item = wid; item < a.len; item += nw) {
+        const Vtx x = pipe.next;
+        const bool ok = pipe.next_ok;
+        pipe.fetch(a, item + nw);
+        if (!ok || (MULTI && !try_majority(a, x.g))) continue;  // warp-uniform
+        const int64_t lo = x.e0, hi = x.e0 + x.d;
+        uint32_t ow = 0u, tw = 0u;
+#pragma unroll 4
+        for (int64_t blk = (lo >> 2) + lane; blk <= (hi - 1) >> 2; blk += 32)
+            own_weight(load_quad(a, blk, lo, hi, x.vb), x.own, ow, tw);
+        ow = __reduce_add_sync(FULL, ow);  // row sums < 2^31
+        tw = __reduce_add_sync(FULL, tw);
+        if (lane == 0) {
+            const bool settled = 2ull * ow > (unsigned long long)tw;
+            a.vmaj[x.v] = settled ? 1 : 0;
+            if (settled) a.lab_out[x.v] = x.own;
+        }
+    }
+}
+
+// the pre-pass over a bucket's list, when the sweep tries the majority test
+template <bool MULTI>
+int launch_major(const SweepArgs &a, int num_sms, cudaStream_t st)
+{
+    if (!a.vmaj || !a.majority || a.identity || a.len <= 0) return 0;
+    const int64_t blocks = (a.len + 7) / 8;
+    k_major_rows<MULTI><<<(int)(blocks < num_sms * 8 ? blocks : num_sms * 8), 256, 0, st>>>(a);
+    return 1;
 }
 
 // ----------------------------------------------------------------------------
@@ -1178,11 +1234,13 @@ int launch(int bucket, const SweepArgs &a, int num_sms, cudaStream_t st)
         break;
     case 2:
         blocks = a.len;
+        n += launch_major<MULTI>(a, num_sms, st);
         k_cta<CTA_THREADS, CTA_TABLE, MULTI>
             <<<(int)(blocks < num_sms * 16 ? blocks : num_sms * 16), CTA_THREADS, cta_smem, st>>>(a);
         break;
     case 3:
         blocks = a.len;
+        n += launch_major<MULTI>(a, num_sms, st);
         k_cta<CTA2_THREADS, CTA2_TABLE, MULTI>
             <<<(int)(blocks < num_sms * 8 ? blocks : num_sms * 8), CTA2_THREADS, cta2_smem, st>>>(a);
         break;
@@ -1211,6 +1269,7 @@ int launch(int bucket, const SweepArgs &a, int num_sms, cudaStream_t st)
             b.list = a.list + a.hmulti;
             b.len = a.len - a.hmulti;
             blocks = b.len < (int64_t)num_sms * 2 ? b.len : (int64_t)num_sms * 2;
+            n += launch_major<MULTI>(b, num_sms, st);
             k_cta<HUB_THREADS, HUB_TABLE, MULTI><<<(int)blocks, HUB_THREADS, hub_smem, st>>>(b);
             ++n;
         }
