@@ -5,13 +5,15 @@
 // Buckets by degree d:
 //   small  1..32     k_small : rows of up to 8 entries take one lane each and
 //                              count their labels in registers; longer rows are
-//                              packed whole into 32-lane chunks, where equal
-//                              labels of a row are found with __match_any_sync
-//                              and summed with redux.sync and the per-row
-//                              argmax is a segmented redux.sync maximum, so no
-//                              table is needed at all.
+//                              packed whole into 32-lane chunks, where each
+//                              lane sums its label's weight over its row with
+//                              shuffles and the per-row argmax is a segmented
+//                              redux.sync maximum, so no table is needed.
 //   warp   33..128   k_warp  : one warp per vertex, a 256-slot open-addressing
 //                              table per warp in shared memory.
+//   (cta, cta2 and hub rows up to 4096 entries: once labels settle, a warp per
+//    row first tests the majority rule, k_major_rows, and the CTA kernel skips
+//    the rows it settled.)
 //   cta    129..512  k_cta   : one 128-thread CTA per vertex, 1024-slot table.
 //   cta2   513..1024 k_cta   : one 256-thread CTA per vertex, 2048-slot table.
 //   hub    1025..4096 k_cta  : one 512-thread CTA per vertex, 8192-slot table.
