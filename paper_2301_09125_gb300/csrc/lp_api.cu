@@ -227,7 +227,6 @@ struct GraphSet {
     std::vector<int64_t> wstart, wcount;  // per class b * waves + k
     int32_t max_n = 0;
     bool rows_distinct = false;  // no row repeats a neighbour (identity first sweep)
-    int32_t hub_max_deg = 0;
     // multi-graph bookkeeping (device copies are null for a single graph)
     int32_t *vgraph = nullptr, *g_vbase = nullptr, *g_active = nullptr, *g_n = nullptr;
     int64_t *g_ebase = nullptr;
@@ -483,33 +482,19 @@ struct GraphSet {
         }
         if (!vmaj && bl[2] + bl[3] + bl[HUB_BUCKET] > 0)
             LP_TRY(dev_alloc(&vmaj, nv, "majority flags", st, device));
-        // hub vertices: largest degree first, so the static CTA assignment of
-        // the hub kernel balances
+        // hub vertices: longest rows first, so the static CTA assignment of
+        // the hub kernels balances
         if (bl[HUB_BUCKET] > 0) {
-            int32_t *deg = nullptr;
-            LP_TRY(dev_alloc(&deg, bl[HUB_BUCKET], "hub degrees", st, device));
-            std::vector<int32_t> hv((size_t)bl[HUB_BUCKET]), hd((size_t)bl[HUB_BUCKET]);
+            int32_t *ordered = nullptr;
+            LP_TRY(dev_alloc(&ordered, bl[HUB_BUCKET], "hub order", st, device));
             cudaError_t e = cudaSuccess;
-            if (degrees_of(off, vgraph, list + bb[HUB_BUCKET], bl[HUB_BUCKET], deg, st, &L.n) != 0)
+            if (hub_order(list + bb[HUB_BUCKET], bl[HUB_BUCKET], off, vgraph, ordered, st, &L.n) != 0)
                 e = cudaGetLastError();
             if (e == cudaSuccess)
-                e = cudaMemcpyAsync(hv.data(), list + bb[HUB_BUCKET], bl[HUB_BUCKET] * sizeof(int32_t),
-                                    cudaMemcpyDeviceToHost, st);
-            if (e == cudaSuccess)
-                e = cudaMemcpyAsync(hd.data(), deg, bl[HUB_BUCKET] * sizeof(int32_t), cudaMemcpyDeviceToHost,
-                                    st);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-            cudaFreeAsync(deg, st);
-            if (e != cudaSuccess) return fail(LP_ECUDA, cuda_msg("hub degrees", e));
-            std::vector<int64_t> order((size_t)bl[HUB_BUCKET]);
-            for (size_t i = 0; i < order.size(); ++i) order[i] = (int64_t)i;
-            std::stable_sort(order.begin(), order.end(),
-                             [&](int64_t x, int64_t y) { return hd[x] > hd[y]; });
-            std::vector<int32_t> sorted(order.size());
-            for (size_t i = 0; i < order.size(); ++i) sorted[i] = hv[order[i]];
-            hub_max_deg = hd[order[0]];
-            LP_CU(cudaMemcpyAsync(list + bb[HUB_BUCKET], sorted.data(), bl[HUB_BUCKET] * sizeof(int32_t),
-                                  cudaMemcpyHostToDevice, st));
+                e = cudaMemcpyAsync(list + bb[HUB_BUCKET], ordered, bl[HUB_BUCKET] * sizeof(int32_t),
+                                    cudaMemcpyDeviceToDevice, st);
+            cudaFreeAsync(ordered, st);
+            if (e != cudaSuccess) return fail(LP_ECUDA, cuda_msg("hub order", e));
             // hub tasks, the segment / partition scratch of the long rows and
             // one fallback table per long row (zeroed; every use leaves it zeroed)
             LP_TRY(dev_alloc(&htask, bl[HUB_BUCKET], "hub tasks", st, device));

@@ -245,6 +245,49 @@ __device__ int64_t block_exclusive_scan(int64_t x, int64_t *s_warp, int64_t *tot
     return r;
 }
 
+// Exclusive block scans of K values per thread in one pass: ex[k] the prefix,
+// tot[k] the block total of value k (s: shared scratch of 33 rows).
+template <int K>
+__device__ void block_exclusive_scan_k(const int64_t (&x)[K], int64_t (&ex)[K], int64_t (&tot)[K],
+                                       int64_t (*s)[K])
+{
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int nw = (int)(blockDim.x >> 5);
+    int64_t inc[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        inc[k] = x[k];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(FULL, inc[k], o);
+            if (lane >= o) inc[k] += y;
+        }
+        if (lane == 31) s[wib][k] = inc[k];
+    }
+    __syncthreads();
+    if (wib == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int64_t w = lane < nw ? s[lane][k] : 0;
+            int64_t wi = w;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int64_t y = __shfl_up_sync(FULL, wi, o);
+                if (lane >= o) wi += y;
+            }
+            s[lane][k] = wi - w;
+            if (lane == 31) s[32][k] = wi;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        ex[k] = s[wib][k] + inc[k] - x[k];
+        tot[k] = s[32][k];
+    }
+    __syncthreads();
+}
+
 // Counting-sort scans.  Per-block counts are stored class-major: the count
 // of class c in block b at hist[c * nblk + b].  One block per class turns its
 // counts into exclusive offsets within the class (in place) and records the
@@ -344,6 +387,7 @@ __global__ void __launch_bounds__(1024) k_hub_tasks(int32_t *list, int64_t len,
                                                      HubTask *tasks, int64_t *totals)
 {
     __shared__ int64_t s_warp[33];
+    __shared__ int64_t s_scan6[33][6];
     // rows longer than HUB_ONE_MAX
     int64_t nbig = 0;
     for (int64_t i0 = 0; i0 < len; i0 += 1024) {
@@ -371,13 +415,13 @@ __global__ void __launch_bounds__(1024) k_hub_tasks(int32_t *list, int64_t len,
             nseg = ((int64_t)d + HUB_SEG - 1) / HUB_SEG;
             npart = nseg < HUB_PMAX ? nseg : HUB_PMAX;
         }
-        int64_t t_big, t_small, t_tab, t_seg, t_part, t_poff;
-        const int64_t ex_big = block_exclusive_scan(big, s_warp, &t_big);
-        const int64_t ex_small = block_exclusive_scan(small, s_warp, &t_small);
-        const int64_t ex_tab = block_exclusive_scan(tsz, s_warp, &t_tab);
-        const int64_t ex_seg = block_exclusive_scan(nseg, s_warp, &t_seg);
-        const int64_t ex_part = block_exclusive_scan(npart, s_warp, &t_part);
-        const int64_t ex_poff = block_exclusive_scan(nseg * (npart + 1), s_warp, &t_poff);
+        const int64_t xs[6] = {big, small, tsz, nseg, npart, nseg * (npart + 1)};
+        int64_t exs[6], ts[6];
+        block_exclusive_scan_k<6>(xs, exs, ts, s_scan6);
+        const int64_t ex_big = exs[0], ex_small = exs[1], ex_tab = exs[2], ex_seg = exs[3],
+                      ex_part = exs[4], ex_poff = exs[5];
+        const int64_t t_big = ts[0], t_small = ts[1], t_tab = ts[2], t_seg = ts[3],
+                      t_part = ts[4], t_poff = ts[5];
         if (i < len) {
             HubTask t;
             t.v = v;
@@ -408,6 +452,57 @@ __global__ void __launch_bounds__(1024) k_hub_tasks(int32_t *list, int64_t len,
     }
 }
 
+// Hub rows in decreasing order of floor(log2(degree)), stable within a class:
+// the longest rows come first, so the hub kernels' static CTA assignment
+// starts them first and the grid stays balanced.  One block.
+__global__ void __launch_bounds__(1024) k_hub_order(const int32_t *list, int64_t len,
+                                                     const int32_t *off, const int32_t *vgraph,
+                                                     int32_t *out)
+{
+    __shared__ int32_t s_start[32];      // next position of each class
+    __shared__ int32_t s_wc[32][33];     // per warp and class: count, then position
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    if (threadIdx.x < 32) s_start[threadIdx.x] = 0;
+    __syncthreads();
+    // class = count of leading zero bits of the degree (degrees >= 1)
+    for (int64_t i = threadIdx.x; i < len; i += 1024)
+        atomicAdd(&s_start[__clz(degree_of(off, vgraph, list[i]))], 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int32_t run = 0;
+        for (int c = 0; c < 32; ++c) {
+            const int32_t t = s_start[c];
+            s_start[c] = run;
+            run += t;
+        }
+    }
+    __syncthreads();
+    for (int64_t i0 = 0; i0 < len; i0 += 1024) {
+        const int64_t i = i0 + threadIdx.x;
+        const bool have = i < len;
+        const int32_t v = have ? list[i] : 0;
+        const int c = have ? __clz(degree_of(off, vgraph, v)) : 32;
+        const unsigned peers = __match_any_sync(FULL, (unsigned)c);
+        const int rank = __popc(peers & ((1u << lane) - 1u));
+        s_wc[wib][lane] = 0;
+        __syncwarp();
+        if (have && rank == 0) s_wc[wib][c] = __popc(peers);
+        __syncthreads();
+        if (threadIdx.x < 32) {  // positions per class, warp after warp
+            int32_t run = s_start[threadIdx.x];
+            for (int w = 0; w < 32; ++w) {
+                const int32_t t = s_wc[w][threadIdx.x];
+                s_wc[w][threadIdx.x] = run;
+                run += t;
+            }
+            s_start[threadIdx.x] = run;
+        }
+        __syncthreads();
+        if (have) out[s_wc[wib][c] + rank] = v;
+        __syncthreads();
+    }
+}
+
 __global__ void k_hub_item_maps(const HubTask *tasks, int64_t nbig, int32_t *seg_task,
                                 int32_t *part_task)
 {
@@ -419,13 +514,6 @@ __global__ void k_hub_item_maps(const HubTask *tasks, int64_t nbig, int32_t *seg
     }
 }
 
-__global__ void k_degrees_of(const int32_t *off, const int32_t *vgraph, const int32_t *list,
-                             int64_t len, int32_t *deg)
-{
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len;
-         i += (int64_t)gridDim.x * blockDim.x)
-        deg[i] = degree_of(off, vgraph, list[i]);
-}
 
 // ---------------------------------------------------------------------------
 // wave partition (asynchronous mode)
@@ -569,15 +657,6 @@ int ingest_bucket(const int32_t *off, int32_t nv, const int32_t *vgraph, const i
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-int degrees_of(const int32_t *off, const int32_t *vgraph, const int32_t *list, int64_t len,
-               int32_t *deg, cudaStream_t st, int64_t *launches)
-{
-    if (len == 0) return 0;
-    k_degrees_of<<<grid_for(len, 256, 4096), 256, 0, st>>>(off, vgraph, list, len, deg);
-    ++*launches;
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
-}
-
 // class starts (int64, first) and per-block class counts
 int64_t wave_hist_ints(int64_t list_len, int waves)
 {
@@ -625,6 +704,15 @@ int hub_tasks(int32_t *list, int64_t len, const int32_t *off, const int32_t *vgr
               HubTask *tasks, int64_t *totals, cudaStream_t st, int64_t *launches)
 {
     k_hub_tasks<<<1, 1024, 0, st>>>(list, len, off, vgraph, tasks, totals);
+    ++*launches;
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int hub_order(const int32_t *list, int64_t len, const int32_t *off, const int32_t *vgraph,
+              int32_t *out, cudaStream_t st, int64_t *launches)
+{
+    if (len <= 0) return 0;
+    k_hub_order<<<1, 1024, 0, st>>>(list, len, off, vgraph, out);
     ++*launches;
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

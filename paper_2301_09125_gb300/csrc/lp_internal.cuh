@@ -197,6 +197,10 @@ int sweep_launch(int bucket, const SweepArgs &a, bool multi, int num_sms, cudaSt
 // others, each kind in list order; list is rewritten in the same order so that
 // tasks[i] belongs to list[i].  totals: [0] rows of the first kind, [1] their
 // fallback table slots, [2] segments, [3] partitions, [4] partition offsets.
+// out = the hub rows of list in decreasing order of floor(log2(degree)),
+// stable within a class
+int hub_order(const int32_t *list, int64_t len, const int32_t *off, const int32_t *vgraph,
+              int32_t *out, cudaStream_t st, int64_t *launches);
 int hub_tasks(int32_t *list, int64_t len, const int32_t *off, const int32_t *vgraph,
               HubTask *tasks, int64_t *totals, cudaStream_t st, int64_t *launches);
 // Task index of every segment item and partition item of the first nbig tasks.
@@ -238,8 +242,6 @@ int ingest_row_order(const int32_t *off, const int32_t *idx, int32_t nv, int64_t
                      IngestOut *d_out, cudaStream_t st, int64_t *launches);
 int ingest_check_wdeg(const int32_t *off, const int32_t *wts, int32_t n, IngestOut *d_out,
                       cudaStream_t st, int64_t *launches);
-int degrees_of(const int32_t *off, const int32_t *vgraph, const int32_t *list, int64_t len,
-               int32_t *deg, cudaStream_t st, int64_t *launches);
 // Bucket every vertex of a graph set.  d_counts[0..B) receives the bucket
 // lengths, [B..2B) their starts in `list`, [2B..3B) their summed degrees
 // (B = NUM_BUCKETS).
