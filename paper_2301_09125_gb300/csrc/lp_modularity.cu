@@ -174,8 +174,11 @@ __device__ __forceinline__ void mod_block(const ModArgs &a, int64_t blk, int64_t
     }
 }
 
-// rows of degree 1..32 as aligned blocks (<= 9 per row), whole rows packed
-// into 32-block chunks
+constexpr int MOD_TINY = 8;
+
+// tiles whose rows all have degree <= MOD_TINY: one lane per row; other
+// tiles: rows as aligned blocks (<= 9 per row), whole rows packed into
+// 32-block chunks
 template <bool MULTI>
 __global__ void __launch_bounds__(256) k_mod_small(ModArgs a)
 {
@@ -190,6 +193,30 @@ __global__ void __launch_bounds__(256) k_mod_small(ModArgs a)
         MV x{0, 0, 0, 0, 0};
         if (i < a.len) x = load_mv<MULTI>(a, a.list[i]);
         const int32_t cv = i < a.len ? __ldg(a.lab + x.v) : 0;
+        // a tile of rows of up to MOD_TINY entries: each lane sums its own row
+        // (a tile that mixes in longer rows takes the packed pass: a second
+        // chain of dependent loads in the same tile costs more than it saves)
+        if (__all_sync(FULL, x.d <= MOD_TINY) && x.d >= 1) {
+            uint32_t kw = 0, lw = 0;
+#pragma unroll
+            for (int j = 0; j < MOD_TINY; ++j) {
+                if (j < x.d) {
+                    const int64_t e = x.e0 + j;
+                    const int32_t u = ld_entry(a.idx + e);
+                    const uint32_t w = a.wts ? (uint32_t)ld_entry(a.wts + e) : 1u;
+                    kw += w;
+                    if (ld_label(a.lab + x.vb + u) == cv) lw += w;
+                }
+            }
+            run.add(a.kc, (int64_t)x.vb + cv, kw);
+            if (MULTI) {
+                graph_run.add(a.acc, x.g, lw, kw);
+            } else {
+                l_acc += lw;
+                w_acc += kw;
+            }
+            x.d = 0;  // done: left out of the packed pass
+        }
         const int64_t q0 = x.e0 >> 2;
         const int nq = x.d > 0 ? (int)(((x.e0 + x.d - 1) >> 2) - q0 + 1) : 0;
         int Q = nq;

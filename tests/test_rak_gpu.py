@@ -443,6 +443,36 @@ def test_batch_matches_single_graph_runs(lp):
         lp.lp_batch_destroy(h)
 
 
+def test_batch_majority_policy_per_graph(lp):
+    """Graph sets where the majority pre-pass runs for some graphs and not for
+    others in the same launch: the pre-pass and the CTA kernels must agree on
+    each graph's policy (a synchronous SBM oscillates, changing nearly every
+    label, while the graphs with long rows settle)."""
+    off, idx, w = hub_graph(9, n=20_000, hubs=2, hub_deg=6_000)
+    graphs = [gg.CSR(off, idx, w)]
+    off, idx, w = random_graph(2000, 800 / 2000, 14, wmax=4)       # cta2 rows
+    graphs.append(gg.CSR(off, idx, w))
+    off, idx, w = random_graph(2500, 300 / 2500, 15, wmax=3)       # cta rows
+    graphs.append(gg.CSR(off, idx, w))
+    graphs.append(gg.sbm_planted(3000, 6, 0.02, 0.0005, seed=3))     # oscillates in sync
+    graphs.append(gg.rmat(13, seed=8))
+    triples = [(g.offsets, g.indices, g.weights) for g in graphs]
+    h = lp.lp_batch_create(triples)
+    try:
+        for mode, waves in (("sync", None), ("async", 2)):
+            kw = {} if waves is None else {"waves": waves}
+            res = lp.lp_batch_run(h, len(graphs), tolerance=0.0, max_iter=6, mode=mode,
+                                  strict=True, seed=1, **kw)
+            for i, g in enumerate(graphs):
+                lab = lp.lp_batch_labels_get(h, i, g.n)
+                ref, iters, conv, hist = oracle.rak(g.offsets, g.indices, g.weights, 0.0, 6,
+                                                    mode, strict=True, seed=1, **kw)
+                assert res[i].iterations == iters and res[i].last_changed == hist[-1], (mode, i)
+                assert np.array_equal(lab, ref), (mode, i)
+    finally:
+        lp.lp_batch_destroy(h)
+
+
 def test_graph_launch_and_host_loop_agree(lp):
     """A run that repeats the previous run's parameters is one CUDA graph
     launch (a conditional node per iteration, the tolerance test on the
