@@ -630,6 +630,12 @@ struct GraphSet {
         return LP_OK;
     }
 
+    // mean degree of the small bucket, rounded up (sizes its kernels' tiles)
+    int32_t small_mean_deg() const
+    {
+        return bl[0] > 0 ? (int32_t)((be[0] + bl[0] - 1) / bl[0]) : 0;
+    }
+
     lp_status alloc_labels()
     {
         LP_TRY(dev_alloc(&lab[0], nv, "labels", st, device));
@@ -836,6 +842,7 @@ struct GraphSet {
         a.hpbest = hpbest;
         a.hmaj = hmaj;
         a.vmaj = vmaj;
+        a.small_mean_deg = small_mean_deg();
         a.waves = (uint32_t)waves;
         a.wave_magic = fastmod_magic((uint32_t)waves);
         return LP_OK;
@@ -1281,6 +1288,7 @@ struct GraphSet {
         ma.g_ebase = g_ebase;
         ma.kc = kc;
         ma.acc = macc;
+        ma.small_mean_deg = small_mean_deg();
         if (modularity_launch(ma, bb, bl, nv, vgraph != nullptr, num_sms, st, &L.n) != 0)
             return fail(LP_ECUDA, cuda_msg("modularity launch", cudaGetLastError()));
         LP_CU(cudaMemcpyAsync(h_macc, macc, 4 * (size_t)G * sizeof(unsigned long long),

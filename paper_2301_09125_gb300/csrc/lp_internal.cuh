@@ -108,6 +108,11 @@ struct SweepArgs {
     uint32_t waves;
     uint32_t wave_k;
     uint64_t wave_magic;     // fastmod constant of `waves`
+    // small-row kernel: list entries per warp tile (32, or fewer for short
+    // lists of rows long enough to need several chunks; set by the launch
+    // from the bucket's mean degree)
+    int32_t tile_rows;
+    int32_t small_mean_deg;
     // hub launches: the list's tasks (aligned with `list`), how many of them
     // are rows longer than HUB_ONE_MAX, with their segment and partition item
     // counts; segment records (HUB_SEG int4 per segment item: label, sum,
@@ -152,7 +157,21 @@ struct ModArgs {
     const int64_t *g_ebase;
     unsigned long long *kc;    // [nv] K_c of community c of graph g at vbase_g + c (zeroed)
     unsigned long long *acc;   // [4 G]: L, 2m, S high, S low per graph (zeroed)
+    int32_t tile_rows;         // small-row kernel: list entries per warp tile
+    int32_t small_mean_deg;    // mean degree of the small bucket (rounded up)
 };
+
+// Rows per warp tile of the small-row kernels: fewer than 32 while a list
+// would fill under 32 warps per SM and its rows are long enough that a tile
+// takes several packed chunks one after another (rows of a few entries are
+// summed one per lane, where a partly used warp only adds overhead).
+inline int32_t small_tile_rows(int64_t len, int32_t mean_deg, int num_sms)
+{
+    int32_t rt = 32;
+    while (rt > 4 && (len + rt - 1) / rt < (int64_t)num_sms * 32 && (int64_t)mean_deg * rt > 64)
+        rt >>= 1;
+    return rt;
+}
 
 // ----------------------------------------------------------------------------
 // SplitMix64 output function (Steele, Lea & Flood 2014), used in counter mode

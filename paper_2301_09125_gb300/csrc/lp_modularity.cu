@@ -188,11 +188,13 @@ __global__ void __launch_bounds__(256) k_mod_small(ModArgs a)
     unsigned long long l_acc = 0, w_acc = 0;
     KcRun run;
     AccRun graph_run;
-    for (int64_t tile = wid; tile * 32 < a.len; tile += nw) {
-        const int64_t i = tile * 32 + lane;
+    const int rt = a.tile_rows;  // rows per tile: lanes rt..31 hold none
+    for (int64_t tile = wid; tile * rt < a.len; tile += nw) {
+        const int64_t i = tile * rt + lane;
+        const bool have = lane < rt && i < a.len;
         MV x{0, 0, 0, 0, 0};
-        if (i < a.len) x = load_mv<MULTI>(a, a.list[i]);
-        const int32_t cv = i < a.len ? __ldg(a.lab + x.v) : 0;
+        if (have) x = load_mv<MULTI>(a, a.list[i]);
+        const int32_t cv = have ? __ldg(a.lab + x.v) : 0;
         // a tile of rows of up to MOD_TINY entries: each lane sums its own row
         // (a tile that mixes in longer rows takes the packed pass: a second
         // chain of dependent loads in the same tile costs more than it saves)
@@ -421,7 +423,8 @@ int modularity_launch(const ModArgs &base, const int64_t *bucket_begin, const in
     if (bucket_len[0] > 0) {
         a.list = base.list + bucket_begin[0];
         a.len = bucket_len[0];
-        const int g = grid_cap((a.len + 255) / 256, num_sms * 16);
+        a.tile_rows = small_tile_rows(a.len, a.small_mean_deg, num_sms);
+        const int g = grid_cap(((a.len + a.tile_rows - 1) / a.tile_rows + 7) / 8, num_sms * 16);
         if (multi) k_mod_small<true><<<g, 256, 0, st>>>(a);
         else k_mod_small<false><<<g, 256, 0, st>>>(a);
         ++*launches;

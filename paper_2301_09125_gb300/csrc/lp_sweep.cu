@@ -292,11 +292,12 @@ __global__ void __launch_bounds__(256, 6) k_small(SweepArgs a)
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     uint32_t my_changed = 0;
 
-    for (int64_t tile = wid; tile * 32 < a.len; tile += nw) {
-        const int64_t i = tile * 32 + lane;
+    const int rt = a.tile_rows;  // rows per tile: lanes rt..31 hold none
+    for (int64_t tile = wid; tile * rt < a.len; tile += nw) {
+        const int64_t i = tile * rt + lane;
         Vtx x{0, 0, 0, 0, 0, 0, 0};
         bool ok = false;
-        if (i < a.len) ok = load_vtx<MULTI>(a, a.list[i], x);
+        if (lane < rt && i < a.len) ok = load_vtx<MULTI>(a, a.list[i], x);
         int d = ok ? x.d : 0;
         const int32_t own = ok ? x.own : 0;
 
@@ -1226,10 +1227,13 @@ int launch(int bucket, const SweepArgs &a, int num_sms, cudaStream_t st)
     int64_t blocks = 0;
     int n = 1;
     switch (bucket) {
-    case 0:
-        blocks = (a.len + 255) / 256;
-        k_small<MULTI><<<(int)(blocks < num_sms * 16 ? blocks : num_sms * 16), 256, 0, st>>>(a);
+    case 0: {
+        SweepArgs b = a;
+        b.tile_rows = small_tile_rows(a.len, a.small_mean_deg, num_sms);
+        blocks = ((a.len + b.tile_rows - 1) / b.tile_rows + 7) / 8;
+        k_small<MULTI><<<(int)(blocks < num_sms * 16 ? blocks : num_sms * 16), 256, 0, st>>>(b);
         break;
+    }
     case 1:
         blocks = (a.len + 7) / 8;
         k_warp<MULTI><<<(int)(blocks < num_sms * 8 ? blocks : num_sms * 8), 256, 0, st>>>(a);
