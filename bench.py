@@ -395,7 +395,7 @@ def run_ours(args):
     barrier()
     e0.record(stream)
     for _ in range(args.steps):
-        r, q = step()  # each run is one CUDA graph launch
+        r, q = step()  # a fresh handle per step: the run is launched from the host
         iters.append(r.iterations)
         qs.append(q)
         run_ms.append(r.gpu_ms)
@@ -461,7 +461,8 @@ def run_ours(args):
                   "hbm_frac": sweep_bytes / (per_sweep_ms * 1e-3) / 1e9 / peak,
                   "run_ms_per_step": statistics.mean(run_ms),
                   "profiled_ms_per_step": prof_ms / args.steps,
-                  "how": "steps timed with each RAK run as one CUDA graph launch; kernel "
+                  "how": "steps timed with each RAK run launched from the host ahead of "
+                         "its device-side tolerance test; kernel "
                          "times from a second pass of the same steps with CUDA events "
                          "around every sweep launch"},
         "kernels": {k: {"launches": v["launches"], "ms": v["total_ms"],
