@@ -255,6 +255,11 @@ struct GraphSet {
     int32_t *hused = nullptr, *hdone = nullptr, *hnused = nullptr;
     uint32_t *hmaj = nullptr;  // long rows' majority counters (2 per hub task)
     uint8_t *vmaj = nullptr;   // per vertex: settled by the majority pre-pass
+    // all-waves launches of many-wave runs over small rows only: wave starts
+    // of the small bucket (device) and the grid barrier's words (count,
+    // generation, error flag)
+    int64_t *d_wstart0 = nullptr;
+    int32_t *d_coop = nullptr;
     // modularity and label staging scratch
     unsigned long long *kc = nullptr, *macc = nullptr, *h_macc = nullptr;
     int64_t kc_cap = 0;
@@ -323,6 +328,8 @@ struct GraphSet {
         f(d_counts);
         fh(h_counts);
         f(vmaj);
+        f(d_wstart0);
+        f(d_coop);
         if (ev0) cudaEventDestroy(ev0);
         if (ev1) cudaEventDestroy(ev1);
         lab[0] = lab[1] = list = wlist = vgraph = g_vbase = g_active = g_n = nullptr;
@@ -338,6 +345,8 @@ struct GraphSet {
         hpbest = nullptr;
         hmaj = nullptr;
         vmaj = nullptr;
+        d_wstart0 = nullptr;
+        d_coop = nullptr;
         hseg_task = hpart_task = hseg_task_w = hpart_task_w = nullptr;
         d_res = nullptr;
         d_stop = nullptr;
@@ -676,6 +685,10 @@ struct GraphSet {
             wstart[(size_t)c] = acc;
             acc += tot[(size_t)c];
         }
+        if (!d_wstart0) LP_TRY(dev_alloc(&d_wstart0, WAVE_MAX, "wave starts", st, device));
+        LP_CU(cudaMemcpyAsync(d_wstart0, wstart.data(), (size_t)waves * sizeof(int64_t),
+                              cudaMemcpyHostToDevice, st));
+        LP_CU(cudaStreamSynchronize(st));  // wstart is host memory that may change
         // hub tasks of each wave's part of the hub bucket (contiguous classes)
         hmulti_w.assign((size_t)waves, 0);
         hsegs_w.assign((size_t)waves, 0);
@@ -755,6 +768,7 @@ struct GraphSet {
         int32_t it = 0;  // iterations launched
         int32_t active_left = 0;
         bool prof = false;
+        bool coop = false;              // an all-waves launch ran in this run
         std::vector<int> prof_launch;   // bucket of each profiled launch
         std::vector<int64_t> prof_len;  // its vertex count
         std::vector<int32_t> prof_iter; // its iteration (launches past the end are not counted)
@@ -816,6 +830,7 @@ struct GraphSet {
         rs.it = 0;
         rs.active_left = G;
         rs.prof = g_prof_on.load();
+        rs.coop = false;
         rs.prof_launch.clear();
         rs.prof_len.clear();
         rs.prof_iter.clear();
@@ -853,7 +868,8 @@ struct GraphSet {
     // Launch iteration `it`'s sweeps (a3-a5 for every bucket and wave) on
     // stream s, reading label buffer `cur` and writing cur ^ 1; profiled
     // launches are bracketed by events and listed in rs.prof_launch.
-    lp_status launch_sweeps(cudaStream_t s, int32_t it, int cur, bool prof, int64_t *kernels)
+    lp_status launch_sweeps(cudaStream_t s, int32_t it, int cur, bool prof, int64_t *kernels,
+                            bool capturing = false)
     {
         const int32_t waves = rs.waves;
         SweepArgs &a = rs.a;
@@ -864,6 +880,44 @@ struct GraphSet {
         a.lab_out = lab[cur ^ 1];
         a.changed = changed + (int64_t)it * G;
         a.key_t = stream_at(rs.p.seed, (uint64_t)t + 1);
+        // labels read in the first two sweeps from unique labels rarely hold a
+        // majority of a row
+        a.majority = rs.p.init_labels || it >= 2;
+        a.changed_prev = it > 0 ? changed + (int64_t)(it - 1) * G : nullptr;
+        a.g_n = g_n;
+        // many waves over small rows only (one graph, not captured): one
+        // cooperative launch sweeps every wave with grid barriers between them
+        if (!capturing && !rs.multi && waves >= COOP_MIN_WAVES && bl[0] > 0 &&
+            bl[1] + bl[2] + bl[3] + bl[HUB_BUCKET] == 0) {
+            if (!d_coop) {
+                LP_TRY(dev_alloc(&d_coop, 4, "grid barrier", st, device));
+                LP_CU(cudaMemsetAsync(d_coop, 0, 4 * sizeof(int32_t), s));
+            }
+            int64_t max_len = 0;
+            for (int k = 0; k < waves; ++k) max_len = std::max(max_len, wcount[(size_t)k]);
+            a.identity = rows_distinct && it == 0 && !rs.p.init_labels;  // wave 0 only
+            if (prof) {
+                while (prof_ev.size() < 2 * (rs.prof_launch.size() + 1)) {
+                    cudaEvent_t e;
+                    LP_CU(cudaEventCreate(&e));
+                    prof_ev.push_back(e);
+                }
+                LP_CU(cudaEventRecord(prof_ev[2 * rs.prof_launch.size()], s));
+            }
+            LP_CU(cudaMemsetAsync(d_coop, 0, 2 * sizeof(int32_t), s));
+            const int nk = small_waves_launch(a, wlist, d_wstart0, d_wtot, max_len,
+                                              reinterpret_cast<unsigned *>(d_coop), d_coop + 2,
+                                              num_sms, s);
+            if (nk < 0) return fail(LP_ECUDA, cuda_msg("all-waves launch", cudaGetLastError()));
+            *kernels += nk;
+            rs.coop = true;
+            if (prof) {
+                LP_CU(cudaEventRecord(prof_ev[2 * rs.prof_launch.size() + 1], s));
+                rs.prof_launch.push_back(0);
+                rs.prof_len.push_back(bl[0]);
+            }
+            return LP_OK;
+        }
         for (int launch_i = 0; launch_i < waves * NUM_BUCKETS; ++launch_i) {
             const int k = launch_i / NUM_BUCKETS, b = launch_i % NUM_BUCKETS;
             if (waves == 1) {
@@ -894,11 +948,6 @@ struct GraphSet {
             // the first sweep from unique labels reads unique labels only in
             // its first wave (later waves see this sweep's new labels)
             a.identity = rows_distinct && it == 0 && !rs.p.init_labels && k == 0;
-            // labels read in the first two sweeps from unique labels rarely
-            // hold a majority of a row
-            a.majority = rs.p.init_labels || it >= 2;
-            a.changed_prev = it > 0 ? changed + (int64_t)(it - 1) * G : nullptr;
-            a.g_n = g_n;
             if (prof) {
                 while (prof_ev.size() < 2 * (rs.prof_launch.size() + 1)) {
                     cudaEvent_t e;
@@ -1035,7 +1084,7 @@ struct GraphSet {
             LP_CU(cudaStreamBeginCaptureToGraph(gr_stream, body, nullptr, nullptr, 0,
                                                 cudaStreamCaptureModeThreadLocal));
             int64_t nk = 0;
-            lp_status ls = launch_sweeps(gr_stream, it, it & 1, false, &nk);
+            lp_status ls = launch_sweeps(gr_stream, it, it & 1, false, &nk, true);
             if (ls == LP_OK &&
                 converge_launch(changed + (int64_t)it * G, g_n, g_active, G, rs.p.tolerance, it,
                                 rs.multi, res, it + 1 < n_it ? h[(size_t)it + 1] : h[0],
@@ -1128,6 +1177,14 @@ struct GraphSet {
     {
         LP_CU(cudaEventRecord(ev1, st));
         LP_CU(cudaEventSynchronize(ev1));
+        if (rs.coop) {
+            int32_t err = 0;
+            LP_CU(cudaMemcpy(&err, d_coop + 2, sizeof(int32_t), cudaMemcpyDeviceToHost));
+            if (err) {
+                LP_CU(cudaMemset(d_coop, 0, 4 * sizeof(int32_t)));
+                return fail(LP_ECUDA, "a grid barrier of the all-waves sweep timed out");
+            }
+        }
         float ms = 0.f;
         LP_CU(cudaEventElapsedTime(&ms, ev0, ev1));
         for (auto &r : results) r.gpu_ms = ms;

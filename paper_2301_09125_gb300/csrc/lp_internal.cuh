@@ -212,6 +212,14 @@ int sweep_prepare();  // per-device kernel attributes; call with the device curr
 // launch the sweep kernel(s) of one degree bucket (0 small, 1 warp, 2 cta,
 // 3 cta2, 4 hub); returns the number of kernels launched, or -1
 int sweep_launch(int bucket, const SweepArgs &a, bool multi, int num_sms, cudaStream_t st);
+// Every wave of an asynchronous single-graph sweep whose rows all lie in the
+// small bucket, as one cooperative launch (wave k's list: wlist + wstart[k],
+// wcount[k] entries, both device arrays; max_len the longest).  bar: two
+// zeroed device words (left zeroed); *err set to 1 if a grid barrier timed
+// out.  Returns the kernel count (1) or -1.
+int small_waves_launch(const SweepArgs &a, const int32_t *wlist, const int64_t *wstart,
+                       const int64_t *wcount, int64_t max_len, unsigned *bar, int32_t *err,
+                       int num_sms, cudaStream_t st);
 // Hub tasks of list[0..len): the rows longer than HUB_ONE_MAX first, then the
 // others, each kind in list order; list is rewritten in the same order so that
 // tasks[i] belongs to list[i].  totals: [0] rows of the first kind, [1] their
@@ -273,6 +281,9 @@ size_t ingest_bucket_scratch_bytes(int32_t nv_total);
 // and wave k (= local vertex id mod waves) are gathered, class by class
 // (class = b * waves + k), into `out`; d_totals[class] receives the class sizes.
 constexpr int WAVE_MAX = 4096;
+// asynchronous runs of at least this many waves over small rows only sweep
+// all waves of an iteration in one cooperative launch
+constexpr int COOP_MIN_WAVES = 8;
 int64_t wave_hist_ints(int64_t list_len, int waves);
 int wave_prepare();  // per-device kernel attributes
 int wave_partition(const int32_t *list, int64_t list_len, const int64_t *bucket_begin,

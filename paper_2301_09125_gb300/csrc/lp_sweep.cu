@@ -101,10 +101,16 @@ __device__ __forceinline__ bool try_majority(const SweepArgs &a, int32_t g)
 // Label of neighbour u (local id u, global index gi) as seen by this launch.
 // Neither buffer is written at an address this launch reads: lab_in is only
 // written by the next iteration, and lab_out entries of earlier waves were
-// written by earlier launches, so both go through the read-only path.
+// written by earlier launches, so both go through the read-only path.  When
+// one launch sweeps every wave (COH), earlier waves' labels were written by
+// other CTAs of the same launch before a grid barrier: they are read from L2
+// (ld.global.cg), which the barrier's fences make coherent, never through a
+// possibly stale L1 line.
+template <bool COH = false>
 __device__ __forceinline__ int32_t neighbour_label(const SweepArgs &a, int64_t gi, int32_t u)
 {
     const bool earlier = a.waves > 1 && fastmod((uint32_t)u, a.wave_magic, a.waves) < a.wave_k;
+    if (COH && earlier) return __ldcg(a.lab_out + gi);
     return ld_label((earlier ? a.lab_out : a.lab_in) + gi);
 }
 
@@ -160,6 +166,7 @@ __device__ __forceinline__ void load_block(const SweepArgs &a, int64_t blk, int3
 }
 
 // entries 4*blk .. 4*blk+3 of the arena, kept where they lie in [lo, hi)
+template <bool COH = false>
 __device__ __forceinline__ Quad load_quad(const SweepArgs &a, int64_t blk, int64_t lo, int64_t hi,
                                           int32_t vb)
 {
@@ -170,7 +177,7 @@ __device__ __forceinline__ Quad load_quad(const SweepArgs &a, int64_t blk, int64
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const bool in = e0 + j >= lo && e0 + j < hi;
-        q.l[j] = in ? neighbour_label(a, (int64_t)vb + u[j], u[j]) : EMPTY;
+        q.l[j] = in ? neighbour_label<COH>(a, (int64_t)vb + u[j], u[j]) : EMPTY;
         q.w[j] = in ? w[j] : 0;
     }
     return q;
@@ -283,10 +290,9 @@ __device__ __forceinline__ Cand block_argmax(const Cand &c, int strict, Cand *s_
 // ----------------------------------------------------------------------------
 constexpr int TINY = 8;  // rows of up to TINY entries get one lane each
 
-template <bool MULTI>
-__global__ void __launch_bounds__(256, 6) k_small(SweepArgs a)
+template <bool MULTI, bool COH = false>
+__device__ __forceinline__ void small_sweep(const SweepArgs &a)
 {
-    if (a.stop && *a.stop) return;  // launched past the end of the run
     const int lane = threadIdx.x & 31;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -317,7 +323,7 @@ __global__ void __launch_bounds__(256, 6) k_small(SweepArgs a)
                     const int64_t e = x.e0 + j;
                     const int32_t u = ld_entry(a.idx + e);
                     wt[j] = a.wts ? (uint32_t)ld_entry(a.wts + e) : 1u;
-                    lab[j] = a.identity ? u : neighbour_label(a, (int64_t)x.vb + u, u);
+                    lab[j] = a.identity ? u : neighbour_label<COH>(a, (int64_t)x.vb + u, u);
                 }
             }
             // entries past the row are EMPTY with weight 0: their totals are 0
@@ -404,7 +410,7 @@ __global__ void __launch_bounds__(256, 6) k_small(SweepArgs a)
                 uint32_t ow = 0, tw = 0;
                 if (act) {
                     const int64_t blk = (o_e0 >> 2) + (lane - (o_qex - base));
-                    own_weight(load_quad(a, blk, o_e0, o_e0 + o_d, o_vb), o_own, ow, tw);
+                    own_weight(load_quad<COH>(a, blk, o_e0, o_e0 + o_d, o_vb), o_own, ow, tw);
                 }
                 // the row's quads fill lanes [o_qex - base, + its quad count)
                 const int o_nq = (int)(((o_e0 + o_d - 1) >> 2) - (o_e0 >> 2) + 1);
@@ -465,7 +471,7 @@ __global__ void __launch_bounds__(256, 6) k_small(SweepArgs a)
                 const long long e = o_e0 + pos;
                 const int32_t u = ld_entry(a.idx + e);
                 w = a.wts ? ld_entry(a.wts + e) : 1;
-                l = a.identity ? u : neighbour_label(a, (int64_t)o_vb + u, u);
+                l = a.identity ? u : neighbour_label<COH>(a, (int64_t)o_vb + u, u);
             }
             // the owner's lanes (its whole row: rows fit in the chunk), then the
             // lanes of the owner with an equal label; the lowest lane of a
@@ -524,6 +530,70 @@ __global__ void __launch_bounds__(256, 6) k_small(SweepArgs a)
         }
     }
     if (!MULTI && lane == 0 && my_changed) atomicAdd(a.changed, (int)my_changed);
+}
+
+template <bool MULTI>
+__global__ void __launch_bounds__(256, 6) k_small(SweepArgs a)
+{
+    if (a.stop && *a.stop) return;  // launched past the end of the run
+    small_sweep<MULTI>(a);
+}
+
+// Grid-wide barrier of a cooperative launch (every CTA resident).  bar[0]
+// counts arrivals, bar[1] is the generation: the last CTA to arrive resets
+// the count and advances the generation.  A CTA that polls more than
+// BARRIER_SPIN times records *err = 1; every CTA returns false once *err is
+// set, so the kernel ends instead of waiting.
+constexpr uint32_t BARRIER_SPIN = 1u << 22;
+
+__device__ bool grid_barrier(unsigned *bar, int32_t *err)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *vgen = bar + 1;
+        const unsigned gen = *vgen;
+        __threadfence();
+        int ok = 1;
+        if (atomicAdd(bar, 1u) + 1u == gridDim.x) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            for (uint32_t spins = 0; *vgen == gen; ++spins) {
+                if (spins >= BARRIER_SPIN) {
+                    atomicExch(err, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        s_ok = ok && *(volatile int32_t *)err == 0;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Every wave of an asynchronous sweep of a single graph whose rows are all in
+// the small bucket, in one cooperative launch: the grid sweeps wave k's list,
+// then meets at a grid barrier before wave k + 1 (whose rows read wave k's
+// labels).  With many short waves this replaces a launch per wave.
+__global__ void __launch_bounds__(256, 6) k_small_waves(SweepArgs a, const int32_t *wlist,
+                                                        const int64_t *wstart, const int64_t *wcount,
+                                                        unsigned *bar, int32_t *err)
+{
+    if (a.stop && *a.stop) return;  // launched past the end of the run
+    for (uint32_t k = 0; k < a.waves; ++k) {
+        SweepArgs b = a;
+        b.list = wlist + wstart[k];
+        b.len = wcount[k];
+        b.wave_k = k;
+        b.identity = a.identity && k == 0;  // later waves read this sweep's labels
+        small_sweep<false, true>(b);
+        if (k + 1 < a.waves && !grid_barrier(bar, err)) return;
+    }
 }
 
 // Insert one quad (entries 4*blk .. 4*blk+3 of a row starting at global
@@ -1317,6 +1387,27 @@ int sweep_prepare() { return prepare<false>() | prepare<true>(); }
 int sweep_launch(int bucket, const SweepArgs &a, bool multi, int num_sms, cudaStream_t st)
 {
     return multi ? launch<true>(bucket, a, num_sms, st) : launch<false>(bucket, a, num_sms, st);
+}
+
+int small_waves_launch(const SweepArgs &a, const int32_t *wlist, const int64_t *wstart,
+                       const int64_t *wcount, int64_t max_len, unsigned *bar, int32_t *err,
+                       int num_sms, cudaStream_t st)
+{
+    static int per_sm = -1;  // resident CTAs per SM (same kernel on every device here)
+    if (per_sm < 0 &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_small_waves, 256, 0) != cudaSuccess)
+        return -1;
+    if (per_sm <= 0) return -1;
+    SweepArgs b = a;
+    b.tile_rows = small_tile_rows(max_len, a.small_mean_deg, num_sms);
+    const int64_t want = ((max_len + b.tile_rows - 1) / b.tile_rows + 7) / 8;
+    const int64_t cap = (int64_t)per_sm * num_sms;
+    const int grid = (int)(want < 1 ? 1 : (want < cap ? want : cap));
+    void *args[] = {&b, &wlist, &wstart, &wcount, &bar, &err};
+    if (cudaLaunchCooperativeKernel((const void *)k_small_waves, dim3(grid), dim3(256), args, 0, st) !=
+        cudaSuccess)
+        return -1;
+    return 1;
 }
 
 }  // namespace lp

@@ -300,6 +300,27 @@ def test_rmat_and_road_small(lp):
     assert_sync_parity(lp, g.offsets, g.indices, g.weights)
 
 
+@pytest.mark.parametrize("waves", [8, 127])
+def test_all_waves_launch_parity(lp, waves):
+    """Asynchronous runs of 8 or more waves over rows of at most 32 entries
+    sweep every wave of an iteration in one cooperative launch with grid
+    barriers: labels bit-exact with the oracle, also when resumed."""
+    g = gg.kmer_like(120_000, seed=4)
+    for strict in (True, False):
+        labels, r, q = assert_async_parity(lp, g.offsets, g.indices, g.weights, waves,
+                                           strict=strict, seed=3)
+    g = gg.grid_road(256, seed=5)
+    assert_async_parity(lp, g.offsets, g.indices, g.weights, waves, strict=False, seed=2)
+    # two iterations, then a resumed run from those labels
+    ref1, _, _, _ = oracle.rak(g.offsets, g.indices, g.weights, 0.0, 2, "async", seed=2,
+                               waves=waves)
+    ref2, _, _, _ = oracle.rak(g.offsets, g.indices, g.weights, 0.0, 2, "async", seed=2,
+                               waves=waves, iter_offset=2, init_labels=ref1)
+    lab, r, _, _ = gpu_run(lp, g.offsets, g.indices, g.weights, tolerance=0.0, max_iter=2,
+                           mode="async", seed=2, waves=waves, iter_offset=2, init_labels=ref1)
+    assert np.array_equal(lab, ref2)
+
+
 def test_async_wave_counts_of_the_benchmarks(lp):
     """The wave counts the benchmarks use keep modularity within 1e-2 of the
     sequential in-place order: 3 waves on the road grid (coprime with its
