@@ -377,6 +377,14 @@ lp_status lp_profile_reset(void);
  * or NULL out with capacity > 0. */
 lp_status lp_profile_read(lp_kernel_stat *out, int32_t capacity, int32_t *count);
 
+/* Self-test of the time limit on the grid barrier that the all-waves sweep
+ * (asynchronous runs of 8 or more waves over rows of at most 32 entries)
+ * waits at: four CTAs of one cooperative launch wait for a fifth that never
+ * arrives, give up after 4096 polls and record the timeout.  *timed_out = 1
+ * when they did; the CUDA context stays usable.  Synchronises the device.
+ * Errors: LP_EINVAL on NULL, LP_ENOMEM, LP_ECUDA. */
+lp_status lp_selftest_barrier_timeout(int32_t *timed_out);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char *lp_last_error(void);
 

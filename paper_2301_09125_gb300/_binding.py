@@ -132,6 +132,7 @@ SIGNATURES = {
     "lp_rak_sweep_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, _P, _P, _P, _P, _P,
                                             ctypes.c_int32, ctypes.c_uint64, ctypes.c_int32,
                                             ctypes.POINTER(ctypes.c_int64), _P]),
+    "lp_selftest_barrier_timeout": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int32)]),
     "lp_last_error": (ctypes.c_char_p, []),
     "lp_launch_count": (ctypes.c_int64, []),
 }
@@ -475,6 +476,14 @@ def lp_rak_sweep_noalloc(offsets, indices, weights, labels_in, labels_out, stric
 
 def lp_last_error() -> str:
     return load().lp_last_error().decode(errors="replace")
+
+
+def lp_selftest_barrier_timeout() -> bool:
+    """True when a grid barrier that can never complete gave up after its
+    poll limit and reported the timeout (the context stays usable)."""
+    out = ctypes.c_int32()
+    _check(load().lp_selftest_barrier_timeout(ctypes.byref(out)))
+    return out.value == 1
 
 
 def lp_launch_count() -> int:

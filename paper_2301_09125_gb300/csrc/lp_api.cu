@@ -1815,6 +1815,27 @@ lp_status lp_profile_read(lp_kernel_stat *out, int32_t capacity, int32_t *count)
     return LP_OK;
 }
 
+lp_status lp_selftest_barrier_timeout(int32_t *timed_out)
+{
+    if (!timed_out) return fail(LP_EINVAL, "timed_out is NULL");
+    *timed_out = 0;
+    int32_t *d = nullptr;  // bar[0], bar[1], err
+    if (cudaMalloc(&d, 4 * sizeof(int32_t)) != cudaSuccess)
+        return fail(LP_ENOMEM, "barrier self-test: cudaMalloc failed");
+    cudaError_t e = cudaMemset(d, 0, 4 * sizeof(int32_t));
+    if (e == cudaSuccess &&
+        lp::barrier_probe_launch(reinterpret_cast<unsigned *>(d), d + 2, 4096, nullptr) != 1)
+        e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    int32_t err = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&err, d + 2, sizeof(int32_t), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(LP_ECUDA, cuda_msg("barrier self-test", e));
+    ++g_launches;
+    *timed_out = err;
+    return LP_OK;
+}
+
 const char *lp_last_error(void) { return g_err.c_str(); }
 
 int64_t lp_launch_count(void) { return g_launches.load(); }

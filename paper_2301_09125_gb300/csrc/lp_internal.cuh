@@ -217,6 +217,9 @@ int sweep_launch(int bucket, const SweepArgs &a, bool multi, int num_sms, cudaSt
 // wcount[k] entries, both device arrays; max_len the longest).  bar: two
 // zeroed device words (left zeroed); *err set to 1 if a grid barrier timed
 // out.  Returns the kernel count (1) or -1.
+// Four CTAs wait at a grid barrier for a fifth that never comes: the wait
+// gives up after spin_limit polls and sets *err (bar: two zeroed words).
+int barrier_probe_launch(unsigned *bar, int32_t *err, uint32_t spin_limit, cudaStream_t st);
 int small_waves_launch(const SweepArgs &a, const int32_t *wlist, const int64_t *wstart,
                        const int64_t *wcount, int64_t max_len, unsigned *bar, int32_t *err,
                        int num_sms, cudaStream_t st);

@@ -546,8 +546,10 @@ __global__ void __launch_bounds__(256, 6) k_small(SweepArgs a)
 // set, so the kernel ends instead of waiting.
 constexpr uint32_t BARRIER_SPIN = 1u << 22;
 
-__device__ bool grid_barrier(unsigned *bar, int32_t *err)
+__device__ bool grid_barrier(unsigned *bar, int32_t *err, unsigned expected = 0,
+                             uint32_t spin_limit = BARRIER_SPIN)
 {
+    if (expected == 0) expected = gridDim.x;
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -555,13 +557,13 @@ __device__ bool grid_barrier(unsigned *bar, int32_t *err)
         const unsigned gen = *vgen;
         __threadfence();
         int ok = 1;
-        if (atomicAdd(bar, 1u) + 1u == gridDim.x) {
+        if (atomicAdd(bar, 1u) + 1u == expected) {
             atomicExch(bar, 0u);
             __threadfence();
             atomicAdd(bar + 1, 1u);
         } else {
             for (uint32_t spins = 0; *vgen == gen; ++spins) {
-                if (spins >= BARRIER_SPIN) {
+                if (spins >= spin_limit) {
                     atomicExch(err, 1);
                     ok = 0;
                     break;
@@ -574,6 +576,13 @@ __device__ bool grid_barrier(unsigned *bar, int32_t *err)
     }
     __syncthreads();
     return s_ok != 0;
+}
+
+// Self-test of the barrier's time limit: the CTAs wait for one CTA more than
+// the grid has, so the wait runs out after spin_limit polls and sets *err.
+__global__ void k_barrier_probe(unsigned *bar, int32_t *err, uint32_t spin_limit)
+{
+    grid_barrier(bar, err, gridDim.x + 1u, spin_limit);
 }
 
 // Every wave of an asynchronous sweep of a single graph whose rows are all in
@@ -1387,6 +1396,15 @@ int sweep_prepare() { return prepare<false>() | prepare<true>(); }
 int sweep_launch(int bucket, const SweepArgs &a, bool multi, int num_sms, cudaStream_t st)
 {
     return multi ? launch<true>(bucket, a, num_sms, st) : launch<false>(bucket, a, num_sms, st);
+}
+
+int barrier_probe_launch(unsigned *bar, int32_t *err, uint32_t spin_limit, cudaStream_t st)
+{
+    void *args[] = {&bar, &err, &spin_limit};
+    if (cudaLaunchCooperativeKernel((const void *)k_barrier_probe, dim3(4), dim3(32), args, 0, st) !=
+        cudaSuccess)
+        return -1;
+    return 1;
 }
 
 int small_waves_launch(const SweepArgs &a, const int32_t *wlist, const int64_t *wstart,

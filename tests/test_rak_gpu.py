@@ -321,6 +321,15 @@ def test_all_waves_launch_parity(lp, waves):
     assert np.array_equal(lab, ref2)
 
 
+def test_grid_barrier_wait_is_bounded(lp):
+    """The all-waves sweep's grid barrier gives up after its poll limit: a
+    barrier that waits for a CTA that does not exist reports the timeout, and
+    the context keeps working afterwards."""
+    assert lp.lp_selftest_barrier_timeout()
+    g = gg.kmer_like(20_000, seed=1)
+    assert_async_parity(lp, g.offsets, g.indices, g.weights, 16)
+
+
 def test_async_wave_counts_of_the_benchmarks(lp):
     """The wave counts the benchmarks use keep modularity within 1e-2 of the
     sequential in-place order: 3 waves on the road grid (coprime with its
