@@ -1411,10 +1411,14 @@ int small_waves_launch(const SweepArgs &a, const int32_t *wlist, const int64_t *
                        const int64_t *wcount, int64_t max_len, unsigned *bar, int32_t *err,
                        int num_sms, cudaStream_t st)
 {
-    static int per_sm = -1;  // resident CTAs per SM (same kernel on every device here)
-    if (per_sm < 0 &&
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_small_waves, 256, 0) != cudaSuccess)
-        return -1;
+    // resident CTAs per SM (thread-safe one-time initialisation)
+    static const int per_sm = [] {
+        int n = 0;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_small_waves, 256, 0) ==
+                       cudaSuccess
+                   ? n
+                   : 0;
+    }();
     if (per_sm <= 0) return -1;
     SweepArgs b = a;
     b.tile_rows = small_tile_rows(max_len, a.small_mean_deg, num_sms);
