@@ -382,32 +382,19 @@ __global__ void k_merge_final(int32_t *lab0, const int32_t *lab1, int32_t nv,
 }
 
 // one block: hub tasks with exclusive prefixes of segments and table slots
-__global__ void __launch_bounds__(1024) k_hub_tasks(int32_t *list, int64_t len,
+__global__ void __launch_bounds__(1024) k_hub_tasks(int32_t *__restrict__ list, int64_t len,
                                                      const int32_t *off, const int32_t *vgraph,
-                                                     HubTask *tasks, int64_t *totals)
+                                                     HubTask *__restrict__ tasks, int64_t *totals)
 {
-    __shared__ int64_t s_warp[33];
     __shared__ int64_t s_scan6[33][6];
-    // rows longer than HUB_ONE_MAX
-    int64_t nbig = 0;
-    for (int64_t i0 = 0; i0 < len; i0 += 1024) {
-        const int64_t i = i0 + threadIdx.x;
-        const int64_t big = i < len && degree_of(off, vgraph, list[i]) > HUB_ONE_MAX;
-        int64_t tot;
-        block_exclusive_scan(big, s_warp, &tot);
-        nbig += tot;
-    }
-    // stable partition into tasks; segments, partitions and tables of long rows
-    int64_t big_run = 0, small_run = nbig, tab_run = 0, seg_run = 0, part_run = 0, poff_run = 0;
-    for (int64_t i0 = 0; i0 < len; i0 += 1024) {
-        const int64_t i = i0 + threadIdx.x;
-        int32_t v = 0, d = 0;
-        if (i < len) {
-            v = list[i];
-            d = degree_of(off, vgraph, v);
-        }
-        const int64_t big = i < len && d > HUB_ONE_MAX;
-        const int64_t small = i < len && !big;
+    // thread t takes a contiguous run of rows: it sums them, one block scan
+    // turns the sums into its starting positions, then it writes their tasks
+    const int64_t per = (len + blockDim.x - 1) / blockDim.x;
+    const int64_t lo = min(len, (int64_t)threadIdx.x * per), hi = min(len, lo + per);
+    // per row: long, short, fallback table slots, segments, partitions,
+    // partition offsets
+    auto shape = [](int32_t d, int64_t (&x)[6]) {
+        const bool big = d > HUB_ONE_MAX;
         int64_t tsz = 0, nseg = 0, npart = 0;
         if (big) {
             tsz = 1;
@@ -415,40 +402,51 @@ __global__ void __launch_bounds__(1024) k_hub_tasks(int32_t *list, int64_t len,
             nseg = ((int64_t)d + HUB_SEG - 1) / HUB_SEG;
             npart = nseg < HUB_PMAX ? nseg : HUB_PMAX;
         }
-        const int64_t xs[6] = {big, small, tsz, nseg, npart, nseg * (npart + 1)};
-        int64_t exs[6], ts[6];
-        block_exclusive_scan_k<6>(xs, exs, ts, s_scan6);
-        const int64_t ex_big = exs[0], ex_small = exs[1], ex_tab = exs[2], ex_seg = exs[3],
-                      ex_part = exs[4], ex_poff = exs[5];
-        const int64_t t_big = ts[0], t_small = ts[1], t_tab = ts[2], t_seg = ts[3],
-                      t_part = ts[4], t_poff = ts[5];
-        if (i < len) {
-            HubTask t;
-            t.v = v;
-            t.d = d;
-            t.nseg = (int32_t)nseg;
-            t.npart = (int32_t)npart;
-            t.seg0 = big ? (int32_t)(seg_run + ex_seg) : 0;
-            t.part0 = big ? (int32_t)(part_run + ex_part) : 0;
-            t.poff0 = big ? poff_run + ex_poff : 0;
-            t.tab = big ? tab_run + ex_tab : 0;
-            tasks[big ? big_run + ex_big : small_run + ex_small] = t;
-        }
-        big_run += t_big;
-        small_run += t_small;
-        tab_run += t_tab;
-        seg_run += t_seg;
-        part_run += t_part;
-        poff_run += t_poff;
+        x[0] = big;
+        x[1] = !big;
+        x[2] = tsz;
+        x[3] = nseg;
+        x[4] = npart;
+        x[5] = nseg * (npart + 1);
+    };
+    int64_t sums[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll 4
+    for (int64_t i = lo; i < hi; ++i) {
+        int64_t x[6];
+        shape(degree_of(off, vgraph, list[i]), x);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) sums[k] += x[k];
+    }
+    int64_t at[6], tot[6];
+    block_exclusive_scan_k<6>(sums, at, tot, s_scan6);
+    at[1] += tot[0];  // short rows follow every long row
+    for (int64_t i = lo; i < hi; ++i) {
+        const int32_t v = list[i];
+        const int32_t d = degree_of(off, vgraph, v);
+        int64_t x[6];
+        shape(d, x);
+        const bool big = x[0] != 0;
+        HubTask t;
+        t.v = v;
+        t.d = d;
+        t.nseg = (int32_t)x[3];
+        t.npart = (int32_t)x[4];
+        t.seg0 = big ? (int32_t)at[3] : 0;
+        t.part0 = big ? (int32_t)at[4] : 0;
+        t.poff0 = big ? at[5] : 0;
+        t.tab = big ? at[2] : 0;
+        tasks[big ? at[0] : at[1]] = t;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) at[k] += x[k];
     }
     __syncthreads();
-    for (int64_t i = threadIdx.x; i < len; i += 1024) list[i] = tasks[i].v;
+    for (int64_t i = threadIdx.x; i < len; i += blockDim.x) list[i] = tasks[i].v;
     if (threadIdx.x == 0) {
-        totals[0] = nbig;
-        totals[1] = tab_run;
-        totals[2] = seg_run;
-        totals[3] = part_run;
-        totals[4] = poff_run;
+        totals[0] = tot[0];
+        totals[1] = tot[2];
+        totals[2] = tot[3];
+        totals[3] = tot[4];
+        totals[4] = tot[5];
     }
 }
 
