@@ -29,6 +29,13 @@ Extra keys: ``roofline`` (dominant sweep kernel vs measured HBM bandwidth),
 
 ``--impl reference`` times the CPU oracle (the only reference this method
 has: the paper publishes no code) on the same workload and metric.
+
+``--experiment tolerance`` runs the paper's tolerance / tie-rule study
+(Sec. 3.2) on the synthetic classes instead: tolerance 0.1 down to 0.0001,
+strict and non-strict ties, synchronous and asynchronous updates, each with
+and without a self-loop on every vertex (Sec. 3.1), max_iter 100.  It prints
+one JSON line per setting (iterations, convergence, run time, GTEPS,
+modularity of the labels on the graph without self-loops).
 Multi-GPU (torchrun): every rank runs its own replica of the workload;
 ``value`` = entries traversed by all ranks / the slowest rank's time.
 """
@@ -92,6 +99,10 @@ def parse():
                     help="arrival window replayed one graph at a time")
     ap.add_argument("--per-graph-sample", type=int, default=256,
                     help="graphs of the batch timed one at a time")
+    ap.add_argument("--experiment", choices=["tolerance"], default=None,
+                    help="run the tolerance / tie-rule study instead of the benchmark")
+    ap.add_argument("--classes", default="sbm10k,rmat22,road4096,kmer8m",
+                    help="workloads of the study (comma-separated)")
     return ap.parse_args()
 
 
@@ -890,8 +901,69 @@ def run_serve(args):
     return 0
 
 
+EXPERIMENT_TOLERANCES = (0.1, 0.05, 0.01, 0.001, 0.0001)
+
+
+def run_experiment(args):
+    """Tolerance / tie-rule / update-order study (Sec. 3.2; self-loops,
+    Sec. 3.1) on the synthetic classes: one JSON line per setting."""
+    import torch
+
+    import graphgen as gg
+    import paper_2301_09125_gb300 as lp
+    from paper_2301_09125_gb300 import build
+
+    build.build()
+    lp.load()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    for name in [c for c in args.classes.split(",") if c]:
+        base = gen_graph(name)
+        waves = WORKLOADS[name]["waves"]
+        plain = [torch.from_numpy(a).to(dev) if a is not None else None
+                 for a in (base.offsets, base.indices, base.weights)]
+        h_plain = lp.lp_graph_create(*plain, borrow=True, stream=stream.cuda_stream)
+        lab = torch.empty(base.n, dtype=torch.int32, device=dev)
+        for loops in (False, True):
+            g = gg.with_self_loops(base) if loops else base
+            arrs = [torch.from_numpy(a).to(dev) if a is not None else None
+                    for a in (g.offsets, g.indices, g.weights)]
+            h = lp.lp_graph_create(*arrs, borrow=True, stream=stream.cuda_stream)
+            for mode in ("sync", "async"):
+                for strict in (True, False):
+                    for tol in EXPERIMENT_TOLERANCES:
+                        params, _ = lp.make_params(tolerance=tol, max_iter=100, mode=mode,
+                                                   strict=strict, waves=waves, seed=1)
+                        lp.lp_rak_run(h, params)  # warm-up
+                        lp.lp_rak_run(h, params)  # repeated parameters: captured as a graph
+                        torch.cuda.synchronize()
+                        e0 = torch.cuda.Event(enable_timing=True)
+                        e1 = torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        r = lp.lp_rak_run(h, params)
+                        e1.record(stream)
+                        torch.cuda.synchronize()
+                        ms = e0.elapsed_time(e1)
+                        lp.lp_labels_get(h, lab)
+                        q = lp.lp_modularity(h_plain, lab)
+                        print(json.dumps({
+                            "experiment": "tolerance", "workload": name, "n": base.n,
+                            "m": base.m, "self_loops": loops, "mode": mode,
+                            "waves": waves if mode == "async" else 1, "strict": strict,
+                            "tolerance": tol, "iterations": r.iterations,
+                            "converged": bool(r.converged), "run_ms": ms,
+                            "gteps": r.iterations * g.m / (ms * 1e-3) / 1e9,
+                            "modularity": q}), flush=True)
+            lp.lp_graph_destroy(h)
+        lp.lp_graph_destroy(h_plain)
+    return 0
+
+
 def main():
     args = parse()
+    if args.experiment:
+        return run_experiment(args)
     if args.workload == "serve":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable":

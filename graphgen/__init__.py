@@ -172,6 +172,26 @@ def workload(name: str, **override) -> CSR:
     return globals()[kind](**spec)
 
 
+def with_self_loops(g: CSR, weight: int = 1) -> CSR:
+    """The graph with a self-loop of the given weight added to every vertex
+    (Sec. 3.1 adds one to every vertex of its inputs), stored last in its row.
+    Weights become explicit when they were unit."""
+    n, m = g.n, g.m
+    deg = np.diff(g.offsets.astype(np.int64))
+    off = (g.offsets.astype(np.int64) + np.arange(n + 1)).astype(np.int32)
+    loop_at = off[1:].astype(np.int64) - 1
+    keep = np.ones(m + n, dtype=bool)
+    keep[loop_at] = False
+    idx = np.empty(m + n, dtype=np.int32)
+    idx[keep] = g.indices
+    idx[loop_at] = np.arange(n, dtype=np.int32)
+    w = np.empty(m + n, dtype=np.int32)
+    w[keep] = 1 if g.weights is None else g.weights
+    w[loop_at] = weight
+    assert int(deg.sum()) == m
+    return CSR(off, idx, w)
+
+
 def batch_sbm_params(count=4096, seed=1000, n_lo=1_000, n_hi=200_000, k_lo=5, k_hi=500,
                      d_lo=8.0, d_hi=32.0, mu=0.3):
     """Parameters of the batched-SBM workload: per graph i, n log-uniform in

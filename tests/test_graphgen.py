@@ -87,3 +87,17 @@ def test_rejects_bad_parameters():
         gg.rmat(0)
     with pytest.raises(ValueError):
         gg.sbm_planted(10, 0, 0.1, 0.1)
+
+
+def test_with_self_loops_appends_one_loop_per_row():
+    g = gg.sbm_planted(300, 3, 0.05, 0.01, seed=4)
+    s = gg.with_self_loops(g, weight=2)
+    assert s.n == g.n and s.m == g.m + g.n
+    assert np.array_equal(np.diff(s.offsets), np.diff(g.offsets) + 1)
+    for v in (0, 17, 299):
+        row = s.indices[s.offsets[v]:s.offsets[v + 1]]
+        w = s.weights[s.offsets[v]:s.offsets[v + 1]]
+        assert row[-1] == v and w[-1] == 2
+        assert np.array_equal(row[:-1], g.indices[g.offsets[v]:g.offsets[v + 1]])
+        assert (w[:-1] == 1).all()
+

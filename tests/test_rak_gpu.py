@@ -330,6 +330,16 @@ def test_grid_barrier_wait_is_bounded(lp):
     assert_async_parity(lp, g.offsets, g.indices, g.weights, 16)
 
 
+def test_self_loop_variant_parity(lp):
+    """Graphs with a self-loop on every vertex (the paper's inputs, Sec. 3.1)
+    through the same path: labels bit-exact with the oracle."""
+    g = gg.with_self_loops(gg.rmat(13, seed=6))
+    assert_sync_parity(lp, g.offsets, g.indices, g.weights, strict=False, seed=2)
+    assert_async_parity(lp, g.offsets, g.indices, g.weights, 2)
+    g = gg.with_self_loops(gg.grid_road(128, seed=3), weight=3)
+    assert_async_parity(lp, g.offsets, g.indices, g.weights, 16)
+
+
 def test_async_wave_counts_of_the_benchmarks(lp):
     """The wave counts the benchmarks use keep modularity within 1e-2 of the
     sequential in-place order: 3 waves on the road grid (coprime with its
