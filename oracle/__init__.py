@@ -59,6 +59,8 @@ def _load():
                                    ctypes.c_int32, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
                                    ctypes.c_int32, _i32p, ctypes.c_int32, _i32p, _i32p, _i32p,
                                    _i64p]
+        lib.oracle_split.restype = ctypes.c_int64
+        lib.oracle_split.argtypes = [ctypes.c_int32, _i32p, _i32p, _i32p, _i32p]
         lib.oracle_modularity.restype = ctypes.c_double
         lib.oracle_modularity.argtypes = [ctypes.c_int32, _i32p, _i32p, _i32p, _i32p, _i64p,
                                           _i64p, _u64p]
@@ -150,6 +152,24 @@ def choose_many(offsets, indices, weights, cur, verts, strict=True, seed=0, t=0)
     if rc != 0:
         raise MemoryError("oracle_choose_many")
     return out
+
+
+def split(offsets, indices, labels):
+    """Split every community of ``labels`` into its connected components
+    (only edges between two vertices of one community count); each component
+    is labelled by its smallest vertex.  Returns ``(labels, components)``.
+    The paper leaves this step out (end of Sec. 3.4)."""
+    offsets = _arr(offsets)
+    indices = _arr(indices)
+    n = _check_csr(offsets, indices, None)
+    labels = _arr(labels)
+    if labels.shape != (n,):
+        raise ValueError("labels must have one entry per vertex")
+    out = np.empty(n, dtype=np.int32)
+    k = _load().oracle_split(n, _ptr(offsets), _ptr(indices), _ptr(labels), _ptr(out))
+    if k < 0:
+        raise ValueError("oracle_split rejected its arguments")
+    return out, int(k)
 
 
 def modularity(offsets, indices, weights, labels, exact=False):

@@ -297,3 +297,42 @@ double oracle_modularity(int32_t n, const int32_t *offsets, const int32_t *indic
     double dm = (double)two_m;
     return (double)l_in / dm - (double)s / (dm * dm);
 }
+
+/*
+ * Splitting disconnected communities (the paper does not post-process its
+ * communities; it names this split as the step it leaves out, end of
+ * Sec. 3.4).  Two vertices stay together when a path of edges whose two ends
+ * both carry that community's label joins them.  Breadth-first search from
+ * every not yet reached vertex in increasing order: each component is labelled
+ * by the vertex its search started from, which is its smallest vertex (a
+ * smaller one would have started an earlier search that reached it).
+ * out[v] = that vertex; returns the number of components (-1 on bad input).
+ */
+int64_t oracle_split(int32_t n, const int32_t *offsets, const int32_t *indices,
+                     const int32_t *labels, int32_t *out)
+{
+    if (n < 0) return -1;
+    int32_t *queue = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
+    if (!queue) return -1;
+    for (int32_t v = 0; v < n; ++v) out[v] = -1;
+    int64_t components = 0;
+    for (int32_t s = 0; s < n; ++s) {
+        if (out[s] >= 0) continue;
+        ++components;
+        out[s] = s;
+        int64_t head = 0, tail = 0;
+        queue[tail++] = s;
+        while (head < tail) {
+            const int32_t v = queue[head++];
+            for (int32_t e = offsets[v]; e < offsets[v + 1]; ++e) {
+                const int32_t u = indices[e];
+                if (labels[u] == labels[v] && out[u] < 0) {
+                    out[u] = s;
+                    queue[tail++] = u;
+                }
+            }
+        }
+    }
+    free(queue);
+    return components;
+}

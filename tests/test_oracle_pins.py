@@ -310,3 +310,46 @@ def test_rejects_bad_arguments():
         oracle.rak(off, np.array([1, 5], np.int32), None)
     with pytest.raises(ValueError):
         oracle.rak(off, idx, None, mode="async", waves=-1)
+
+
+# ------------------------------------------------- splitting disconnected communities
+def test_split_hand_example():
+    # path 0-1-2 and edge 3-4 share label 7, vertex 5 is isolated, and the
+    # edge 2-6 joins two different labels
+    off, idx, _ = csr_from_adj([[1], [0, 2], [1, 6], [4], [3], [], [2]])
+    labels = np.array([7, 7, 7, 7, 7, 5, 1], np.int32)
+    out, k = oracle.split(off, idx, labels)
+    assert out.tolist() == [0, 0, 0, 3, 3, 5, 6] and k == 4
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_split_matches_library_components(seed):
+    """The split equals scipy's connected components of the graph that keeps
+    only the edges whose two ends share a label, each component named by its
+    smallest vertex."""
+    sp = pytest.importorskip("scipy.sparse")
+    csg = pytest.importorskip("scipy.sparse.csgraph")
+    off, idx, _ = random_graph(400, 0.01, seed)
+    rng = np.random.default_rng(seed)
+    labels = rng.integers(0, 6, 400).astype(np.int32)
+    rows = np.repeat(np.arange(400), np.diff(off))
+    keep = labels[rows] == labels[idx]
+    a = sp.csr_matrix((np.ones(int(keep.sum())), (rows[keep], idx[keep])), shape=(400, 400))
+    k_ref, comp = csg.connected_components(a, directed=False)
+    first = np.full(k_ref, 400)
+    np.minimum.at(first, comp, np.arange(400))
+    out, k = oracle.split(off, idx, labels)
+    assert k == k_ref
+    assert np.array_equal(out, first[comp])
+
+
+def test_split_refines_and_is_idempotent():
+    off, idx, _ = random_graph(300, 0.02, 9)
+    labels, _, _, _ = oracle.rak(off, idx, None, 0.05, 20, "sync", strict=False, seed=3)
+    out, k = oracle.split(off, idx, labels)
+    # same component => same community; every component is named by a member
+    for c in np.unique(out):
+        assert len(np.unique(labels[out == c])) == 1 and out[c] == c
+    again, k2 = oracle.split(off, idx, out)
+    assert np.array_equal(again, out) and k2 == k
+    assert k >= len(np.unique(labels))
