@@ -36,6 +36,8 @@ strict and non-strict ties, synchronous and asynchronous updates, each with
 and without a self-loop on every vertex (Sec. 3.1), max_iter 100.  It prints
 one JSON line per setting (iterations, convergence, run time, GTEPS,
 modularity of the labels on the graph without self-loops).
+``--experiment split`` times the split of disconnected communities after
+each class's benchmark run (communities and modularity before and after).
 Multi-GPU (torchrun): every rank runs its own replica of the workload;
 ``value`` = entries traversed by all ranks / the slowest rank's time.
 """
@@ -99,8 +101,9 @@ def parse():
                     help="arrival window replayed one graph at a time")
     ap.add_argument("--per-graph-sample", type=int, default=256,
                     help="graphs of the batch timed one at a time")
-    ap.add_argument("--experiment", choices=["tolerance"], default=None,
-                    help="run the tolerance / tie-rule study instead of the benchmark")
+    ap.add_argument("--experiment", choices=["tolerance", "split"], default=None,
+                    help="run the tolerance / tie-rule study, or time the split of "
+                         "disconnected communities, instead of the benchmark")
     ap.add_argument("--classes", default="sbm10k,rmat22,road4096,kmer8m",
                     help="workloads of the study (comma-separated)")
     return ap.parse_args()
@@ -960,8 +963,57 @@ def run_experiment(args):
     return 0
 
 
+def run_split_experiment(args):
+    """Split of disconnected communities after RAK (each class's benchmark
+    parameters): communities before and after, modularity before and after,
+    time of the split (CUDA events on the library's stream)."""
+    import torch
+
+    import paper_2301_09125_gb300 as lp
+    from paper_2301_09125_gb300 import build
+
+    build.build()
+    lp.load()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    for name in [c for c in args.classes.split(",") if c]:
+        g = gen_graph(name)
+        p = WORKLOADS[name]
+        params, _ = lp.make_params(tolerance=p["tolerance"], max_iter=p["max_iter"],
+                                   mode=p["mode"], strict=p["strict"], waves=p["waves"])
+        arrs = [torch.from_numpy(a).to(dev) if a is not None else None
+                for a in (g.offsets, g.indices, g.weights)]
+        times = []
+        for rep in range(4):
+            h = lp.lp_graph_create(*arrs, borrow=True, stream=stream.cuda_stream)
+            lp.lp_rak_run(h, params)
+            before = lp.lp_labels_get(h)
+            q0 = lp.lp_modularity(h)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            k = lp.lp_split_communities(h)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if rep:  # the first split pays for its scratch allocation
+                times.append(e0.elapsed_time(e1))
+            q1 = lp.lp_modularity(h)
+            lp.lp_graph_destroy(h)
+        ms = statistics.median(times)
+        print(json.dumps({"experiment": "split", "workload": name, "n": g.n, "m": g.m,
+                          "mode": p["mode"], "communities_before": int(len(np.unique(before))),
+                          "communities_after": k, "modularity_before": q0,
+                          "modularity_after": q1, "split_ms": ms,
+                          "gteps": g.m / (ms * 1e-3) / 1e9}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.experiment == "split":
+        return run_split_experiment(args)
     if args.experiment:
         return run_experiment(args)
     if args.workload == "serve":

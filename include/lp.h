@@ -377,6 +377,17 @@ lp_status lp_profile_reset(void);
  * or NULL out with capacity > 0. */
 lp_status lp_profile_read(lp_kernel_stat *out, int32_t capacity, int32_t *count);
 
+/* Split every community of the graph's current labelling into its connected
+ * components, in place: two vertices keep one label only if a path of edges
+ * whose two ends both carry that label joins them.  The paper does not
+ * post-process its communities and names this split as the step it leaves
+ * out (end of Sec. 3.4).  Each component takes the id of its smallest vertex
+ * as its label, so the result is unique; *communities (may be NULL) receives
+ * the number of components, isolated vertices included.  Runs on the graph's
+ * stream and synchronises it.  Single graphs only.
+ * Errors: LP_EINVAL on NULL g, LP_ENOMEM, LP_ECUDA. */
+lp_status lp_split_communities(lp_graph *g, int64_t *communities);
+
 /* Self-test of the time limit on the grid barrier that the all-waves sweep
  * (asynchronous runs of 8 or more waves over rows of at most 32 entries)
  * waits at: four CTAs of one cooperative launch wait for a fifth that never

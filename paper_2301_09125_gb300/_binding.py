@@ -132,6 +132,7 @@ SIGNATURES = {
     "lp_rak_sweep_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, _P, _P, _P, _P, _P,
                                             ctypes.c_int32, ctypes.c_uint64, ctypes.c_int32,
                                             ctypes.POINTER(ctypes.c_int64), _P]),
+    "lp_split_communities": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
     "lp_selftest_barrier_timeout": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int32)]),
     "lp_last_error": (ctypes.c_char_p, []),
     "lp_launch_count": (ctypes.c_int64, []),
@@ -478,6 +479,14 @@ def lp_last_error() -> str:
     return load().lp_last_error().decode(errors="replace")
 
 
+def lp_split_communities(handle: int) -> int:
+    """Split the graph's communities into connected components in place (each
+    named by its smallest vertex); returns the number of components."""
+    k = ctypes.c_int64()
+    _check(load().lp_split_communities(handle, ctypes.byref(k)))
+    return k.value
+
+
 def lp_selftest_barrier_timeout() -> bool:
     """True when a grid barrier that can never complete gave up after its
     poll limit and reported the timeout (the context stays usable)."""
@@ -501,6 +510,9 @@ class Graph:
 
     def rak(self, **kw) -> lp_rak_result:
         return lp_rak_run(self.handle, **kw)
+
+    def split(self) -> int:
+        return lp_split_communities(self.handle)
 
     def autotune(self, sweeps: int = 5, **kw) -> lp_tune_result:
         return lp_graph_autotune(self.handle, sweeps=sweeps, **kw)

@@ -316,6 +316,14 @@ int converge_launch(const int32_t *changed_it, const int32_t *g_n, int32_t *g_ac
                     cudaGraphConditionalHandle next, bool has_next, int32_t *stop, bool last,
                     cudaStream_t st);
 
+// Split the communities of lab (n vertices, m entries, one graph) into
+// connected components in place: lab[v] = smallest vertex of v's component.
+// parent: n scratch ints; *err set to 1 if a link gave up; *count +=
+// components.
+int split_launch(const int32_t *off, const int32_t *idx, int32_t *lab, int32_t n, int64_t m,
+                 int32_t *parent, int32_t *err, unsigned long long *count, int num_sms,
+                 cudaStream_t st, int64_t *launches);
+
 // Entry and square passes of the modularity of every graph of a set.
 int modularity_launch(const ModArgs &a, const int64_t *bucket_begin, const int64_t *bucket_len,
                       int64_t nslots, bool multi, int num_sms, cudaStream_t st, int64_t *launches);

@@ -679,3 +679,61 @@ def test_rmat22_full_size(lp, rmat22):
 def test_road4096_full_size(lp, road4096):
     sampled_sync_check(lp, road4096, strict=True, seed=3)
     assert_async_quality(lp, road4096.offsets, road4096.indices, road4096.weights, waves=31)
+
+
+# ------------------------------------------------- splitting disconnected communities
+def split_check(lp, g, mode, waves=None, strict=True, max_iter=20, init=None, tol=0.05):
+    kw = {} if waves is None else {"waves": waves}
+    ref, _, _, _ = oracle.rak(g.offsets, g.indices, g.weights, tol, max_iter, mode,
+                              strict=strict, seed=4, init_labels=init, **kw)
+    ref_split, k_ref = oracle.split(g.offsets, g.indices, ref)
+    with lp.Graph(g.offsets, g.indices, g.weights) as G:
+        G.rak(tolerance=tol, max_iter=max_iter, mode=mode, strict=strict, seed=4,
+              init_labels=init, **kw)
+        assert np.array_equal(G.labels(), ref)
+        k = G.split()
+        assert k == k_ref
+        assert np.array_equal(G.labels(), ref_split)
+        q = G.modularity()
+        assert abs(q - oracle.modularity(g.offsets, g.indices, g.weights, ref_split)) <= Q_SYNC_TOL
+
+
+def test_split_parity(lp):
+    """Communities split into connected components on the GPU equal the
+    oracle's split of the oracle's labels (each component named by its
+    smallest vertex), on every bucket's rows."""
+    split_check(lp, gg.rmat(14, seed=3), "sync", strict=False)
+    split_check(lp, gg.rmat(14, seed=3), "async", waves=2)
+    off, idx, w = hub_graph(5, n=20_000, hub_deg=9_000)
+    split_check(lp, gg.CSR(off, idx, w), "sync")
+    split_check(lp, gg.grid_road(256, seed=2), "async", waves=3)
+    split_check(lp, gg.sbm_planted(3000, 6, 0.02, 0.0005, seed=2), "sync", strict=False)
+
+
+def test_split_of_scattered_labels(lp):
+    """Labels v mod 3 after one sweep leave most communities in many pieces."""
+    g = gg.rmat(12, seed=9)
+    init = (np.arange(g.n) % 3).astype(np.int32)
+    split_check(lp, g, "sync", max_iter=1, init=init, tol=1.0)
+    g = gg.grid_road(64, seed=9)
+    init = (np.arange(g.n) % 3).astype(np.int32)
+    split_check(lp, g, "sync", max_iter=1, init=init, tol=1.0)
+
+
+def test_split_before_any_run_and_edge_cases(lp):
+    off, idx, w = csr_from_adj([[1], [0], [], [4], [3]])
+    with lp.Graph(off, idx, w) as G:
+        assert G.split() == 5  # unique labels: every vertex alone
+        assert G.labels().tolist() == [0, 1, 2, 3, 4]
+        G.rak(tolerance=0.0, max_iter=5, mode="async", waves=2)
+        assert G.split() == 3
+        assert G.labels().tolist() == [0, 0, 2, 3, 3]
+    empty = gg.CSR(np.zeros(1, np.int32), np.zeros(0, np.int32), None)
+    with lp.Graph(empty.offsets, empty.indices, None) as G:
+        assert G.split() == 0
+
+
+@pytest.mark.slow
+def test_split_full_size(lp, road4096, rmat22):
+    split_check(lp, road4096, "async", waves=3)
+    split_check(lp, rmat22, "async", waves=2)
