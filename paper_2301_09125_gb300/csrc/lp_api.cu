@@ -1823,20 +1823,22 @@ lp_status lp_split_communities(lp_graph *g, int64_t *communities)
     if (communities) *communities = 0;
     if (s.nv == 0) return LP_OK;
     int32_t *lab = s.lab[s.final_buf[0]];
-    // scratch: parent array, error word and component count
+    // scratch: parent array; component count, then error word, sampled root
+    // and sampling switch (int32 each)
     int32_t *parent = nullptr;
     unsigned long long *words = nullptr;
     LP_TRY(dev_alloc(&parent, s.nv, "split scratch", s.st, s.device));
-    if (dev_alloc(&words, 2, "split scratch", s.st, s.device) != LP_OK) {
+    if (dev_alloc(&words, 3, "split scratch", s.st, s.device) != LP_OK) {
         cudaFreeAsync(parent, s.st);
         return LP_ENOMEM;
     }
     unsigned long long h[2] = {0, 0};
-    cudaError_t e = cudaMemsetAsync(words, 0, 2 * sizeof(unsigned long long), s.st);
+    cudaError_t e = cudaMemsetAsync(words, 0, 3 * sizeof(unsigned long long), s.st);
     Launches L;
     if (e == cudaSuccess &&
         lp::split_launch(s.off, s.idx, lab, s.nv, s.ne, parent,
                          reinterpret_cast<int32_t *>(words + 1),
+                         reinterpret_cast<int32_t *>(words + 1) + 1,
                          words, s.num_sms, s.st, &L.n) != 0)
         e = cudaGetLastError();
     if (e == cudaSuccess)
@@ -1845,7 +1847,7 @@ lp_status lp_split_communities(lp_graph *g, int64_t *communities)
     cudaFreeAsync(parent, s.st);
     cudaFreeAsync(words, s.st);
     if (e != cudaSuccess) return fail(LP_ECUDA, cuda_msg("community split", e));
-    if (h[1]) return fail(LP_ECUDA, "community split: a union-find link gave up");
+    if ((uint32_t)h[1]) return fail(LP_ECUDA, "community split: a union-find link gave up");
     s.q_valid = false;
     if (communities) *communities = (int64_t)h[0];
     return LP_OK;

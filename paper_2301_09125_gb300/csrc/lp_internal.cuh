@@ -318,11 +318,11 @@ int converge_launch(const int32_t *changed_it, const int32_t *g_n, int32_t *g_ac
 
 // Split the communities of lab (n vertices, m entries, one graph) into
 // connected components in place: lab[v] = smallest vertex of v's component.
-// parent: n scratch ints; *err set to 1 if a link gave up; *count +=
-// components.
+// parent: n scratch ints; *err set to 1 if a link gave up; big: two scratch
+// ints; *count += components.
 int split_launch(const int32_t *off, const int32_t *idx, int32_t *lab, int32_t n, int64_t m,
-                 int32_t *parent, int32_t *err, unsigned long long *count, int num_sms,
-                 cudaStream_t st, int64_t *launches);
+                 int32_t *parent, int32_t *err, int32_t *big, unsigned long long *count,
+                 int num_sms, cudaStream_t st, int64_t *launches);
 
 // Entry and square passes of the modularity of every graph of a set.
 int modularity_launch(const ModArgs &a, const int64_t *bucket_begin, const int64_t *bucket_len,
