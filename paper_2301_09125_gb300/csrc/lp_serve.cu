@@ -57,11 +57,12 @@ struct Request {
 };
 
 // device bytes a request may hold: CSR, two label buffers, bucket and wave
-// lists, modularity scratch, hub fallback tables (at most 4 slots of 12 bytes
-// per entry) and hub segment records (at most 32 bytes per entry)
+// lists, modularity scratch, majority flags (1 byte per vertex), hub
+// fallback tables (at most 4 slots of 12 bytes per entry) and hub segment
+// records (at most 32 bytes per entry)
 int64_t footprint(int32_t n, int64_t m, bool weighted)
 {
-    return 4 * ((int64_t)n + 1) + (weighted ? 8 : 4) * m + 36 * (int64_t)n + 80 * m + (1 << 20);
+    return 4 * ((int64_t)n + 1) + (weighted ? 8 : 4) * m + 37 * (int64_t)n + 80 * m + (1 << 20);
 }
 
 }  // namespace
