@@ -6,14 +6,17 @@
 //   S   = sum_c K_c^2  (128-bit)
 //   Q   = L / 2m - S / (2m)^2   (formed in double on the host)
 //
-// The entry pass reuses the sweep's degree buckets: rows of the small bucket
+// The entry pass reuses the sweep's degree buckets: tiles of small rows of at
+// most 8 entries take one lane per row, other rows of the small bucket
 // (<= 32 entries) are read as aligned 16-byte blocks packed several rows to a
 // 32-block warp chunk, longer rows get a warp or a CTA of 128, 256 or 512
-// threads reading aligned blocks.  Each row adds k_v to K_{c_v} (per-thread
-// run aggregation, one 64-bit atomic per run); L and 2m are summed in
-// registers and flushed once per warp (one graph) or per row (graph sets).
-// The square pass adds K_c^2 into per-graph 128-bit accumulators
-// (carry-propagating 64-bit atomics).
+// threads reading aligned blocks.  Each row adds k_v to K_{c_v}: rows of one
+// community in a chunk are summed first, and every thread keeps running sums
+// for two communities (one 64-bit atomic when one is evicted).  L and 2m are
+// summed in registers and flushed once per block (one graph) or whenever a
+// thread's rows move to another graph (graph sets).  The square pass adds
+// K_c^2 into per-graph 128-bit accumulators (carry-propagating 64-bit
+// atomics).
 #include "lp_device.cuh"
 #include "lp_internal.cuh"
 
