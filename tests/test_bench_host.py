@@ -45,3 +45,24 @@ def test_reference_arm_other_ranks_exit_quietly():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
                         "--gpus", "2"], env=env, capture_output=True, text=True, timeout=120)
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_traffic_summary_is_well_formed():
+    """The committed DRAM-traffic summary carries one ratio per sweep bucket
+    and a sources hash in the form bench.py checks; bench.py returns its
+    ratio when the hash matches the current sweep sources, and None when
+    they differ."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    path = os.path.join(ROOT, "profiles", "dram_traffic_rmat21_async_w2.md")
+    lines = [ln.split() for ln in open(path)
+             if ln.strip().startswith(("traffic_ratio", "sweep_sources"))]
+    ratios = {x[1]: float(x[2]) for x in lines if x[0] == "traffic_ratio"}
+    assert set(ratios) == {"sweep_small", "sweep_warp", "sweep_cta", "sweep_cta2", "sweep_hub"}
+    assert all(0.5 < r < 10 for r in ratios.values())
+    hashes = [x[1] for x in lines if x[0] == "sweep_sources_sha256_16"]
+    assert len(hashes) == 1 and len(hashes[0]) == 16
+    current = bench.sweep_sources_hash()
+    expect = ratios["sweep_hub"] if hashes[0] == current else None
+    assert bench.traffic_ratio("sweep_hub") == expect
