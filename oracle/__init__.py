@@ -59,6 +59,14 @@ def _load():
                                    ctypes.c_int32, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
                                    ctypes.c_int32, _i32p, ctypes.c_int32, _i32p, _i32p, _i32p,
                                    _i64p]
+        lib.oracle_slpa_slot.restype = ctypes.c_int32
+        lib.oracle_slpa_slot.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64,
+                                         ctypes.c_int64]
+        lib.oracle_slpa.restype = ctypes.c_int
+        lib.oracle_slpa.argtypes = [ctypes.c_int32, _i32p, _i32p, _i32p, ctypes.c_int32,
+                                    ctypes.c_double, ctypes.c_int, ctypes.c_uint64, _i32p, _i32p,
+                                    ctypes.POINTER(ctypes.c_int32),
+                                    ctypes.POINTER(ctypes.c_int32), _i64p]
         lib.oracle_split.restype = ctypes.c_int64
         lib.oracle_split.argtypes = [ctypes.c_int32, _i32p, _i32p, _i32p, _i32p]
         lib.oracle_modularity.restype = ctypes.c_double
@@ -152,6 +160,40 @@ def choose_many(offsets, indices, weights, cur, verts, strict=True, seed=0, t=0)
     if rc != 0:
         raise MemoryError("oracle_choose_many")
     return out
+
+
+def slpa_slot(seed, t, v, pos):
+    """The memory slot (0 .. t-1) a speaker speaks in iteration t to listener
+    v through the entry at row position pos (Sec. 3.4's random speaker)."""
+    return int(_load().oracle_slpa_slot(ctypes.c_uint64(seed & (2**64 - 1)), t, v, pos))
+
+
+def slpa(offsets, indices, weights=None, memory_size=20, tolerance=0.05, strict=True, seed=0):
+    """SLPA (Sec. 3.4): every vertex remembers itself, then in each iteration
+    listens to one remembered label per neighbour and stores the heaviest.
+
+    Returns ``(labels, memory, iterations, converged, changed_per_iteration)``
+    with ``memory[t, v]`` the label v stored in iteration t (slot 0 = v).
+    """
+    offsets = _arr(offsets)
+    indices = _arr(indices)
+    weights = None if weights is None else _arr(weights)
+    n = _check_csr(offsets, indices, weights)
+    if memory_size < 1:
+        raise ValueError("memory_size must be >= 1")
+    memory = np.empty((memory_size, n), dtype=np.int32)
+    labels = np.empty(n, dtype=np.int32)
+    hist = np.zeros(max(memory_size - 1, 1), dtype=np.int64)
+    iters = ctypes.c_int32(0)
+    conv = ctypes.c_int32(0)
+    rc = _load().oracle_slpa(n, _ptr(offsets), _ptr(indices), _ptr(weights), int(memory_size),
+                             float(tolerance), 1 if strict else 0,
+                             ctypes.c_uint64(seed & (2**64 - 1)), _ptr(memory), _ptr(labels),
+                             ctypes.byref(iters), ctypes.byref(conv), _ptr(hist, _i64p))
+    if rc != 0:
+        raise ValueError("oracle_slpa rejected its arguments")
+    it = int(iters.value)
+    return labels, memory[: it + 1].copy(), it, bool(conv.value), hist[:it].copy()
 
 
 def split(offsets, indices, labels):

@@ -336,3 +336,155 @@ int64_t oracle_split(int32_t n, const int32_t *offsets, const int32_t *indices,
     free(queue);
     return components;
 }
+
+/* ------------------------------------------------------------------------- */
+/* SLPA, the speaker-listener label propagation (Sec. 3.4).                  */
+/* ------------------------------------------------------------------------- */
+/*
+ * Readings where Sec. 3.4 is open:
+ *   - the memory holds memory_size labels; slot 0 is the vertex itself and
+ *     iteration t (1 <= t < memory_size) fills slot t, so at most
+ *     memory_size - 1 iterations run;
+ *   - a speaker speaks from the slots its memory held before the iteration
+ *     (0 .. t-1), so every listener of one iteration hears the same
+ *     memories (synchronous); the slot is drawn by a counter-based SplitMix64
+ *     draw of (seed ^ SLPA_SPEAK, t, listener, position of the entry in the
+ *     listener's row), mapped to [0, t) by the high 32 bits times t;
+ *   - the listener sums the weights of the spoken labels and takes the
+ *     heaviest; strict keeps the first such label in row order, non-strict
+ *     the one with the smallest RAK tie hash of (seed, t, listener, label);
+ *   - a vertex without edges repeats its previous slot;
+ *   - converged once at most tolerance * n vertices stored a label that
+ *     differs from their previous slot;
+ *   - a vertex's community is the label it stored most often, the one first
+ *     stored on equal counts.
+ */
+#define ORACLE_SLPA_SPEAK 0x5350454Bull /* "SPEK": keeps speaker draws apart from tie hashes */
+
+/* memory slot a speaker speaks in iteration t to listener v through the entry
+ * at row position pos */
+int32_t oracle_slpa_slot(uint64_t seed, int64_t t, int64_t v, int64_t pos)
+{
+    uint64_t h = oracle_tie_hash(seed ^ ORACLE_SLPA_SPEAK, t, v, pos);
+    return (int32_t)(((h >> 32) * (uint64_t)t) >> 32);
+}
+
+/* the label listener v stores, given the labels its row's entries speak */
+static int32_t oracle_listen(oracle_map *m, int32_t v, int32_t begin, int32_t end,
+                             const int32_t *weights, const int32_t *spoken, int strict,
+                             uint64_t seed, int64_t t)
+{
+    int32_t count = 0;
+    for (int32_t e = begin; e < end; ++e) {
+        int32_t l = spoken[e - begin];
+        int64_t w = weights ? (int64_t)weights[e] : 1;
+        int32_t s = m->slot_of[l];
+        if (s < 0) {
+            s = count++;
+            m->slot_of[l] = s;
+            m->label[s] = l;
+            m->weight[s] = 0;
+            m->first[s] = e - begin;
+        }
+        m->weight[s] += w;
+    }
+    int64_t wmax = m->weight[0];
+    for (int32_t s = 1; s < count; ++s)
+        if (m->weight[s] > wmax) wmax = m->weight[s];
+    int32_t best = -1;
+    uint64_t best_hash = 0;
+    for (int32_t s = 0; s < count; ++s) {
+        if (m->weight[s] != wmax) continue;
+        if (strict) {
+            best = s;
+            break;
+        }
+        uint64_t h = oracle_tie_hash(seed, t, v, m->label[s]);
+        if (best < 0 || h < best_hash) {
+            best = s;
+            best_hash = h;
+        }
+    }
+    int32_t chosen = m->label[best];
+    for (int32_t s = 0; s < count; ++s) m->slot_of[m->label[s]] = -1;
+    return chosen;
+}
+
+/* SLPA on an n-vertex CSR.  memory (may be NULL): memory_size * n ints, slot
+ * t of vertex v at memory[t * n + v], filled for slots 0 .. *iterations.
+ * labels: the community of every vertex.  changed_hist (may be NULL,
+ * capacity memory_size - 1): vertices whose stored label differs from their
+ * previous slot, per iteration.  Returns 0, or -1 on bad input or allocation
+ * failure. */
+int oracle_slpa(int32_t n, const int32_t *offsets, const int32_t *indices, const int32_t *weights,
+                int32_t memory_size, double tolerance, int strict, uint64_t seed,
+                int32_t *memory, int32_t *labels, int32_t *iterations, int32_t *converged,
+                int64_t *changed_hist)
+{
+    if (n < 0 || memory_size < 1) return -1;
+    int32_t *mem = memory ? memory : (int32_t *)malloc((size_t)memory_size * (n > 0 ? n : 1) *
+                                                       sizeof(int32_t));
+    int64_t dmax = oracle_max_degree(n, offsets);
+    int32_t *spoken = (int32_t *)malloc((size_t)(dmax > 0 ? dmax : 1) * sizeof(int32_t));
+    oracle_map m;
+    int rc = 0;
+    if (!mem || !spoken) {
+        rc = -1;
+        goto done_alloc;
+    }
+    if (oracle_map_init(&m, n, dmax) != 0) {
+        oracle_map_free(&m);
+        rc = -1;
+        goto done_alloc;
+    }
+    for (int32_t v = 0; v < n; ++v) mem[v] = v;
+    *iterations = 0;
+    *converged = 0;
+    for (int32_t t = 1; t < memory_size; ++t) {
+        const int32_t *prev = mem + (size_t)(t - 1) * n;
+        int32_t *next = mem + (size_t)t * n;
+        int64_t changed = 0;
+        for (int32_t v = 0; v < n; ++v) {
+            int32_t begin = offsets[v], end = offsets[v + 1];
+            if (begin == end) {
+                next[v] = prev[v];
+                continue;
+            }
+            for (int32_t e = begin; e < end; ++e) {
+                int32_t u = indices[e];
+                int32_t slot = oracle_slpa_slot(seed, t, v, e - begin);
+                spoken[e - begin] = mem[(size_t)slot * n + u];
+            }
+            next[v] = oracle_listen(&m, v, begin, end, weights, spoken, strict, seed, t);
+            if (next[v] != prev[v]) ++changed;
+        }
+        if (changed_hist) changed_hist[t - 1] = changed;
+        *iterations = t;
+        if ((double)changed <= tolerance * (double)n) {
+            *converged = 1;
+            break;
+        }
+    }
+    /* community: the label stored most often, the first stored on equal counts */
+    for (int32_t v = 0; v < n; ++v) {
+        int32_t best = mem[v], best_count = 0;
+        for (int32_t a = 0; a <= *iterations; ++a) {
+            int32_t l = mem[(size_t)a * n + v], c = 0, seen_before = 0;
+            for (int32_t b = 0; b < a; ++b)
+                if (mem[(size_t)b * n + v] == l) seen_before = 1;
+            if (seen_before) continue;
+            for (int32_t b = a; b <= *iterations; ++b)
+                if (mem[(size_t)b * n + v] == l) ++c;
+            if (c > best_count) {
+                best = l;
+                best_count = c;
+            }
+        }
+        labels[v] = best;
+    }
+    oracle_map_free(&m);
+done_alloc:
+    free(spoken);
+    if (!memory) free(mem);
+    return rc;
+}

@@ -353,3 +353,64 @@ def test_split_refines_and_is_idempotent():
     again, k2 = oracle.split(off, idx, out)
     assert np.array_equal(again, out) and k2 == k
     assert k >= len(np.unique(labels))
+
+
+# ------------------------------------------------------------------------- SLPA
+def test_slpa_memory_of_one_slot_is_identity():
+    off, idx, w = random_graph(50, 0.1, 1)
+    lab, mem, it, conv, hist = oracle.slpa(off, idx, w, memory_size=1)
+    assert it == 0 and np.array_equal(lab, np.arange(50)) and mem.shape == (1, 50)
+
+
+@pytest.mark.parametrize("strict", [True, False])
+def test_slpa_first_iteration_is_a_rak_step(strict):
+    """In the first iteration every speaker can only speak its own id, so the
+    listener's choice is one synchronous RAK step from unique labels (the tie
+    hash of iteration index 1 on both sides)."""
+    off, idx, w = random_graph(300, 0.03, 5, wmax=3)
+    _, mem, it, _, _ = oracle.slpa(off, idx, w, memory_size=2, tolerance=0.0, strict=strict,
+                                   seed=7)
+    ref, _, _, _ = oracle.rak(off, idx, w, 0.0, 1, "sync", strict=strict, seed=7, iter_offset=1)
+    assert it == 1 and np.array_equal(mem[1], ref)
+
+
+def test_slpa_star_first_iteration_by_hand():
+    # centre 0 hears leaves 1..4 (one each, first is 1); every leaf hears 0
+    off, idx, w = csr_from_adj([[1, 2, 3, 4], [0], [0], [0], [0]])
+    _, mem, _, _, _ = oracle.slpa(off, idx, w, memory_size=2, tolerance=0.0)
+    assert mem[1].tolist() == [1, 0, 0, 0, 0]
+
+
+def test_slpa_slots_are_uniform():
+    t = 5
+    slots = np.array([oracle.slpa_slot(3, t, v, p) for v in range(400) for p in range(10)])
+    assert slots.min() >= 0 and slots.max() < t
+    counts = np.bincount(slots, minlength=t)
+    expected = slots.size / t
+    chi2 = float(((counts - expected) ** 2 / expected).sum())
+    assert chi2 < 20.5  # 4 degrees of freedom, p ~ 0.0004
+
+
+def test_slpa_memories_are_valid_and_stay_in_components():
+    """Every stored label was in some neighbour's memory before that
+    iteration; labels never cross components; isolated vertices repeat
+    themselves; the community is the label stored most often."""
+    off_a, idx_a, _ = random_graph(60, 0.2, 8)
+    off_b, idx_b, _ = random_graph(40, 0.25, 9)
+    off = np.concatenate([off_a, off_b[1:] + off_a[-1], [off_a[-1] + off_b[-1]]]).astype(np.int32)
+    idx = np.concatenate([idx_a, idx_b + 60]).astype(np.int32)  # vertex 100 isolated
+    lab, mem, it, _, _ = oracle.slpa(off, idx, None, memory_size=8, tolerance=0.0, seed=2)
+    assert it == 7
+    comp = np.where(np.arange(101) < 60, 0, np.where(np.arange(101) < 100, 1, 2))
+    for t in range(1, it + 1):
+        for v in range(101):
+            row = idx[off[v]:off[v + 1]]
+            if row.size == 0:
+                assert mem[t, v] == mem[t - 1, v]
+                continue
+            assert mem[t, v] in set(mem[:t, row].ravel().tolist())
+            assert comp[mem[t, v]] == comp[v]
+    for v in range(101):
+        vals, first, counts = np.unique(mem[:, v], return_index=True, return_counts=True)
+        top = counts.max()
+        assert lab[v] == vals[first == first[counts == top].min()][0]
