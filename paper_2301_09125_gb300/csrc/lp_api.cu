@@ -253,7 +253,15 @@ struct GraphSet {
     unsigned long long *hkey = nullptr;
     uint32_t *hnpos = nullptr;
     int32_t *hused = nullptr, *hdone = nullptr, *hnused = nullptr;
-    uint32_t *hmaj = nullptr;  // long rows' majority counters (2 per hub task)
+    uint32_t *hmaj = nullptr;  // long rows' majority counters (4 per hub task)
+    int2 *hvote = nullptr;     // per segment item: its majority vote
+    int32_t *cpos = nullptr;   // rows left by a pre-pass (nv) and their count, open long rows
+    int32_t *ccount = nullptr;
+    // packed rows of the run's list (lp_internal.cuh), built for one wave
+    // count at a time (pk_waves, 0 = none yet)
+    int64_t *pk_rp = nullptr, *pk_first = nullptr;
+    int32_t *pk_idx = nullptr, *pk_wts = nullptr;
+    int32_t pk_waves = 0;
     uint8_t *vmaj = nullptr;   // per vertex: settled by the majority pre-pass
     // all-waves launches of many-wave runs over small rows only: wave starts
     // of the small bucket (device) and the grid barrier's words (count,
@@ -312,6 +320,18 @@ struct GraphSet {
         f(hpoff);
         f(hpbest);
         f(hmaj);
+        f(hvote);
+        hvote = nullptr;
+        f(cpos);
+        f(ccount);
+        cpos = ccount = nullptr;
+        f(pk_rp);
+        f(pk_first);
+        f(pk_idx);
+        f(pk_wts);
+        pk_rp = pk_first = nullptr;
+        pk_idx = pk_wts = nullptr;
+        pk_waves = 0;
         f(hseg_task);
         f(hpart_task);
         f(hseg_task_w);
@@ -491,6 +511,10 @@ struct GraphSet {
         }
         if (!vmaj && bl[2] + bl[3] + bl[HUB_BUCKET] > 0)
             LP_TRY(dev_alloc(&vmaj, nv, "majority flags", st, device));
+        if (!ccount) LP_TRY(dev_alloc(&ccount, 2, "pre-pass counters", st, device));
+        if (!cpos && G == 1 && bl[2] + bl[3] + bl[HUB_BUCKET] > 0)
+            LP_TRY(dev_alloc(&cpos, std::max(bl[2], std::max(bl[3], bl[HUB_BUCKET])),
+                             "pre-pass row lists", st, device));
         // hub vertices: longest rows first, so the static CTA assignment of
         // the hub kernels balances
         if (bl[HUB_BUCKET] > 0) {
@@ -529,7 +553,8 @@ struct GraphSet {
             LP_TRY(dev_alloc(&hused, slots / 2 + 1, "hub used lists", st, device));
             LP_TRY(dev_alloc(&hdone, bl[HUB_BUCKET], "hub counters", st, device));
             LP_TRY(dev_alloc(&hnused, bl[HUB_BUCKET], "hub counters", st, device));
-            LP_TRY(dev_alloc(&hmaj, 2 * bl[HUB_BUCKET], "hub majority counters", st, device));
+            LP_TRY(dev_alloc(&hmaj, 4 * bl[HUB_BUCKET], "hub majority counters", st, device));
+            LP_TRY(dev_alloc(&hvote, tot[2] > 0 ? tot[2] : 1, "hub majority votes", st, device));
             LP_CU(cudaMemsetAsync(hkey, 0, (size_t)slots * sizeof(unsigned long long), st));
             LP_CU(cudaMemsetAsync(hnpos, 0, (size_t)slots * sizeof(uint32_t), st));
             LP_CU(cudaMemsetAsync(hdone, 0, (size_t)bl[HUB_BUCKET] * sizeof(int32_t), st));
@@ -555,6 +580,8 @@ struct GraphSet {
         f(hpoff);
         f(hpbest);
         f(hmaj);
+        f(hvote);
+        f(cpos);
         f(hkey);
         f(hnpos);
         f(hused);
@@ -571,12 +598,15 @@ struct GraphSet {
         hpoff = nullptr;
         hpbest = nullptr;
         hmaj = nullptr;
+        hvote = nullptr;
+        cpos = nullptr;
         hkey = nullptr;
         hnpos = nullptr;
         hused = hdone = hnused = nullptr;
         hseg_task = hpart_task = hseg_task_w = hpart_task_w = nullptr;
         hmulti = hsegs = hparts = 0;
         wl_waves = 0;
+        pk_waves = 0;
         drop_graph();
         gr_last = GraphKey{};
         th = t;
@@ -744,6 +774,38 @@ struct GraphSet {
         return LP_OK;
     }
 
+    // Pack the rows of the run's list (the bucket list, or the wave lists of
+    // `waves` > 1) in list order, once per wave count; hub tasks learn their
+    // packed row starts.  A captured run graph reads the packed arrays, so it
+    // is dropped whenever they are rebuilt.
+    lp_status ensure_packed(int32_t waves)
+    {
+        if (waves == pk_waves) return LP_OK;
+        drop_graph();
+        const int64_t len = bb[HUB_BUCKET] + bl[HUB_BUCKET];
+        if (!pk_rp) LP_TRY(dev_alloc(&pk_rp, len + 1, "packed row starts", st, device));
+        if (!pk_first)
+            LP_TRY(dev_alloc(&pk_first, pack_chunks(ne) + 1, "packed chunk rows", st, device));
+        if (!pk_idx) LP_TRY(dev_alloc(&pk_idx, ne, "packed rows", st, device));
+        if (wts && !pk_wts) LP_TRY(dev_alloc(&pk_wts, ne, "packed rows", st, device));
+        if (((uintptr_t)pk_idx & 15u) || ((uintptr_t)pk_wts & 15u))
+            return fail(LP_ECUDA, "device allocation is not 16-byte aligned");
+        int64_t *scratch = nullptr;
+        LP_TRY(dev_alloc(&scratch, pack_scratch_ints(len), "packing scratch", st, device));
+        Launches L;
+        int rc = pack_rows(waves > 1 ? wlist : list, len, off, idx, wts, ne, vgraph, g_vbase,
+                           g_ebase, waves, scratch, pk_rp, pk_first, pk_idx, pk_wts, st, &L.n);
+        if (rc == 0 && bl[HUB_BUCKET] > 0) {
+            const int64_t hub0 = waves > 1 ? wstart[(size_t)HUB_BUCKET * waves] : bb[HUB_BUCKET];
+            rc = hub_task_starts(waves > 1 ? htask_w : htask, bl[HUB_BUCKET], pk_rp + hub0, st,
+                                 &L.n);
+        }
+        cudaFreeAsync(scratch, st);
+        if (rc != 0) return fail(LP_ECUDA, cuda_msg("row packing", cudaGetLastError()));
+        pk_waves = waves;
+        return LP_OK;
+    }
+
     lp_status ensure_changed(int64_t entries)
     {
         if (entries <= changed_cap) return LP_OK;
@@ -794,6 +856,7 @@ struct GraphSet {
         if (multi && p->init_labels) return fail(LP_EINVAL, "batches start from unique labels");
         LP_TRY(ensure_changed((int64_t)p->max_iter * G));
         if (waves > 1) LP_TRY(ensure_waves(waves));
+        LP_TRY(ensure_packed(waves));
         if (!ev_iter) LP_CU(cudaEventCreateWithFlags(&ev_iter, cudaEventDisableTiming));
         Launches L;
 
@@ -838,9 +901,9 @@ struct GraphSet {
 
         SweepArgs &a = rs.a;
         a = SweepArgs{};
-        a.off = off;
-        a.idx = idx;
-        a.wts = wts;
+        a.rp = pk_rp;
+        a.idx = pk_idx;
+        a.wts = wts ? pk_wts : nullptr;
         a.ne = ne;
         a.vgraph = vgraph;
         a.g_vbase = g_vbase;
@@ -856,10 +919,13 @@ struct GraphSet {
         a.hpoff = hpoff;
         a.hpbest = hpbest;
         a.hmaj = hmaj;
+        a.hvote = hvote;
+        a.hopen = ccount ? ccount + 1 : nullptr;
+        a.cpos = G == 1 ? cpos : nullptr;
+        a.ccount = G == 1 ? ccount : nullptr;
         a.vmaj = vmaj;
         a.small_mean_deg = small_mean_deg();
         a.waves = (uint32_t)waves;
-        a.wave_magic = fastmod_magic((uint32_t)waves);
         return LP_OK;
     }
 
@@ -880,9 +946,9 @@ struct GraphSet {
         a.lab_out = lab[cur ^ 1];
         a.changed = changed + (int64_t)it * G;
         a.key_t = stream_at(rs.p.seed, (uint64_t)t + 1);
-        // labels read in the first two sweeps from unique labels rarely hold a
-        // majority of a row
-        a.majority = rs.p.init_labels || it >= 2;
+        // the labels read in the first sweep from unique labels never give a
+        // row a majority label
+        a.majority = rs.p.init_labels || it >= 1;
         a.changed_prev = it > 0 ? changed + (int64_t)(it - 1) * G : nullptr;
         a.g_n = g_n;
         // many waves over small rows only (one graph, not captured): one
@@ -905,6 +971,7 @@ struct GraphSet {
                 LP_CU(cudaEventRecord(prof_ev[2 * rs.prof_launch.size()], s));
             }
             LP_CU(cudaMemsetAsync(d_coop, 0, 2 * sizeof(int32_t), s));
+            a.rp = pk_rp;  // aligned with wlist; the kernel offsets it per wave
             const int nk = small_waves_launch(a, wlist, d_wstart0, d_wtot, max_len,
                                               reinterpret_cast<unsigned *>(d_coop), d_coop + 2,
                                               num_sms, s);
@@ -922,6 +989,7 @@ struct GraphSet {
             const int k = launch_i / NUM_BUCKETS, b = launch_i % NUM_BUCKETS;
             if (waves == 1) {
                 a.list = list + bb[b];
+                a.rp = pk_rp + bb[b];
                 a.len = bl[b];
                 a.htask = htask;
                 a.hmulti = hmulti;
@@ -931,6 +999,7 @@ struct GraphSet {
                 a.hpart_task = hpart_task;
             } else {
                 a.list = wlist + wstart[(size_t)b * waves + k];
+                a.rp = pk_rp + wstart[(size_t)b * waves + k];
                 a.len = wcount[(size_t)b * waves + k];
                 if (b == HUB_BUCKET) {
                     a.htask = htask_w + (wstart[(size_t)b * waves + k] - wstart[(size_t)b * waves]);
@@ -944,7 +1013,6 @@ struct GraphSet {
                 }
             }
             if (a.len == 0) continue;
-            a.wave_k = (uint32_t)k;
             // the first sweep from unique labels reads unique labels only in
             // its first wave (later waves see this sweep's new labels)
             a.identity = rows_distinct && it == 0 && !rs.p.init_labels && k == 0;
@@ -1333,20 +1401,24 @@ struct GraphSet {
         Launches L;
         if (nv > 0) LP_CU(cudaMemsetAsync(kc, 0, (size_t)nv * sizeof(unsigned long long), st));
         LP_CU(cudaMemsetAsync(macc, 0, 4 * (size_t)G * sizeof(unsigned long long), st));
+        // the entry pass reads the packed rows (those of the last run, or the
+        // bucket list's when no run has packed them yet)
+        LP_TRY(ensure_packed(pk_waves > 0 ? pk_waves : 1));
         ModArgs ma{};
-        ma.off = off;
-        ma.idx = idx;
-        ma.wts = wts;
+        ma.rp = pk_rp;
+        ma.idx = pk_idx;
+        ma.wts = wts ? pk_wts : nullptr;
         ma.lab = labels;
-        ma.list = list;
+        ma.list = pk_waves > 1 ? wlist : list;
+        ma.len = bb[HUB_BUCKET] + bl[HUB_BUCKET];
         ma.ne = ne;
+        ma.first_row = pk_first;
+        ma.ncopy = pack_chunks(ne);
         ma.vgraph = vgraph;
         ma.g_vbase = g_vbase;
-        ma.g_ebase = g_ebase;
         ma.kc = kc;
         ma.acc = macc;
-        ma.small_mean_deg = small_mean_deg();
-        if (modularity_launch(ma, bb, bl, nv, vgraph != nullptr, num_sms, st, &L.n) != 0)
+        if (modularity_launch(ma, nv, vgraph != nullptr, st, &L.n) != 0)
             return fail(LP_ECUDA, cuda_msg("modularity launch", cudaGetLastError()));
         LP_CU(cudaMemcpyAsync(h_macc, macc, 4 * (size_t)G * sizeof(unsigned long long),
                               cudaMemcpyDeviceToHost, st));

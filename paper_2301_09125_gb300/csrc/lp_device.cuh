@@ -178,5 +178,160 @@ __device__ __forceinline__ bool table_add(int32_t *key, int32_t *sum, uint32_t *
     return table_add_at(key, sum, npos, (1u << lg) - 1u, slot_hash(l, lg), limit, l, s, p);
 }
 
+// ----------------------------------------------------------------------------
+// Tables of 64-bit slots: (label + 1) << 32 | summed weight, 0 = free.  One
+// shared atomic per inserted entry (a claim or an add); the first position of
+// a label is not kept: it is recovered for the rows whose maximum is tied
+// (tie_position below).
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long slot_tag(int32_t l)
+{
+    return (unsigned long long)((uint32_t)l + 1u) << 32;
+}
+
+__device__ __forceinline__ int32_t slot_label(unsigned long long v)
+{
+    return (int32_t)((uint32_t)(v >> 32) - 1u);
+}
+
+// add weight s of label l to a table of 2^lg slots that has room for every
+// label inserted into it (at most half full).  A slot is claimed with a 64-bit
+// CAS (label and first weight at once); later weights of its label are added
+// to its low word (the sum) with a native 32-bit atomic, only after the
+// claim was seen, so the two atomics never race on a free slot (a failed CAS
+// writes nothing).  Sums stay below 2^31 and never carry into the label.
+__device__ __forceinline__ void table64_add(unsigned long long *t, int lg, int32_t l, uint32_t s)
+{
+    const uint32_t mask = (1u << lg) - 1u;
+    const unsigned long long tag = slot_tag(l);
+    volatile unsigned long long *vt = t;
+    uint32_t h = slot_hash(l, lg);
+    for (uint32_t i = 0; i <= mask; ++i) {
+        unsigned long long cur = vt[h];
+        if (cur == 0ull) {
+            cur = atomicCAS(t + h, 0ull, tag | s);
+            if (cur == 0ull) return;
+        }
+        if ((cur & 0xFFFFFFFF00000000ull) == tag) {
+            atomicAdd(reinterpret_cast<unsigned int *>(t + h), s);  // low word = sum
+            return;
+        }
+        h = (h + 1) & mask;
+    }
+}
+
+// summed weight of label l in such a table (0 if absent)
+__device__ __forceinline__ uint32_t table64_sum(const unsigned long long *t, int lg, int32_t l)
+{
+    const uint32_t mask = (1u << lg) - 1u;
+    const unsigned long long tag = slot_tag(l);
+    const volatile unsigned long long *vt = t;
+    uint32_t h = slot_hash(l, lg);
+    for (uint32_t i = 0; i <= mask; ++i) {
+        const unsigned long long cur = vt[h];
+        if (cur == 0ull) return 0u;
+        if ((cur & 0xFFFFFFFF00000000ull) == tag) return (uint32_t)cur;
+        h = (h + 1) & mask;
+    }
+    return 0u;
+}
+
+// The maximum of a table: its weight, how many labels reach it, one of those
+// labels, and (non-strict) the least tie key among them with its count.
+struct Top {
+    uint32_t sum;
+    uint32_t cnt;
+    int32_t label;
+    uint64_t h;  // non-strict: least tie key of the labels at the maximum
+};
+
+// Warp-wide combination of per-lane tops, valid in every lane: the largest
+// `key` (lanes with key 0 hold nothing), the summed counts of the lanes
+// reaching it and the largest label among them.
+__device__ __forceinline__ void warp_top(uint64_t &key, uint32_t &cnt, int32_t &label)
+{
+    uint64_t k = key;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        const uint64_t y = __shfl_xor_sync(FULL, k, o);
+        k = y > k ? y : k;
+    }
+    const bool at = key == k;
+    cnt = __reduce_add_sync(FULL, at ? cnt : 0u);
+    label = (int32_t)__reduce_max_sync(FULL, at ? (uint32_t)label + 1u : 0u) - 1;
+    key = k;
+}
+
+// The same over a block of NT threads (s: NT / 32 + 1 entries of each array),
+// valid in every thread.
+template <int NT>
+__device__ __forceinline__ void block_top(uint64_t &key, uint32_t &cnt, int32_t &label,
+                                          uint64_t *s_k, uint32_t *s_c, int32_t *s_l)
+{
+    warp_top(key, cnt, label);
+    if (NT == 32) return;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    if (lane == 0) {
+        s_k[wib] = key;
+        s_c[wib] = cnt;
+        s_l[wib] = label;
+    }
+    __syncthreads();
+    if (wib == 0) {
+        uint64_t k = lane < NT / 32 ? s_k[lane] : 0ull;
+        uint32_t c = lane < NT / 32 ? s_c[lane] : 0u;
+        int32_t l = lane < NT / 32 ? s_l[lane] : EMPTY;
+        warp_top(k, c, l);
+        if (lane == 0) {
+            s_k[NT / 32] = k;
+            s_c[NT / 32] = c;
+            s_l[NT / 32] = l;
+        }
+    }
+    __syncthreads();
+    key = s_k[NT / 32];
+    cnt = s_c[NT / 32];
+    label = s_l[NT / 32];
+}
+
+// Row of every entry of a chunk of 256 consecutive entries (one warp): rows
+// k = 1 .. nr - 1 start at chunk offsets start(k) in (0, 256] (strictly
+// increasing: every row has an entry), row 0 holds offset 0.  s_row[e]
+// receives the row of offset e: the number of row starts at or before e.
+template <typename StartOf>
+__device__ __forceinline__ void chunk_rows(StartOf start, int nr, uint16_t *s_row)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) s_row[lane + 32 * i] = 0;
+    __syncwarp();
+    for (int k = 1 + lane; k < nr; k += 32) {
+        const int e = start(k);
+        if (e < 256) s_row[e] = 1;
+    }
+    __syncwarp();
+    uint16_t m[8];
+    int sum = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        m[i] = s_row[8 * lane + i];
+        sum += m[i];
+    }
+    int inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, inc, o);
+        if (lane >= o) inc += y;
+    }
+    int run = inc - sum;
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        run += m[i];
+        s_row[8 * lane + i] = (uint16_t)run;
+    }
+    __syncwarp();
+}
+
 }  // namespace
 }  // namespace lp

@@ -10,6 +10,7 @@
 // (small / warp / cta / hub) with a stable three-pass count-scan-scatter, so
 // the vertices of a bucket stay in ascending id order (coalesced row pointer
 // and label accesses in the sweep).
+#include "lp_device.cuh"
 #include "lp_internal.cuh"
 
 namespace lp {
@@ -435,6 +436,7 @@ __global__ void __launch_bounds__(1024) k_hub_tasks(int32_t *__restrict__ list, 
         t.part0 = big ? (int32_t)at[4] : 0;
         t.poff0 = big ? at[5] : 0;
         t.tab = big ? at[2] : 0;
+        t.e0 = 0;  // set once the rows are packed (hub_task_starts)
         tasks[big ? at[0] : at[1]] = t;
 #pragma unroll
         for (int k = 0; k < 6; ++k) at[k] += x[k];
@@ -512,6 +514,134 @@ __global__ void k_hub_item_maps(const HubTask *tasks, int64_t nbig, int32_t *seg
     }
 }
 
+
+__global__ void k_hub_task_starts(HubTask *tasks, int64_t n, const int64_t *rp)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        tasks[i].e0 = rp[i];
+}
+
+// ---------------------------------------------------------------------------
+// packed rows: the rows of a list copied in list order
+// ---------------------------------------------------------------------------
+constexpr int PK_SCAN = 1024;            // list items per scan block
+constexpr int PK_T = 256, PK_PER = 8;    // copy: threads per block, entries per thread
+constexpr int PK_OUT = 32 * PK_PER;      // entries per warp chunk
+constexpr int PK_WARPS = PK_T / 32;
+static_assert(PK_OUT == PACK_CHUNK, "copy chunks are the modularity pass's chunks");
+
+// summed degree of each block of PK_SCAN list items
+__global__ void __launch_bounds__(PK_SCAN) k_pack_sum(const int32_t *list, int64_t len,
+                                                      const int32_t *off, const int32_t *vgraph,
+                                                      int64_t *bsum)
+{
+    __shared__ int64_t s_warp[33];
+    const int64_t i = (int64_t)blockIdx.x * PK_SCAN + threadIdx.x;
+    const int64_t d = i < len ? degree_of(off, vgraph, list[i]) : 0;
+    int64_t tot;
+    block_exclusive_scan(d, s_warp, &tot);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+// rp[i] = block start + prefix of the degrees within the block; rp[len] =
+// total; srcw[i] = the row's start in the original CSR | its wave class << 48.
+// Every listed row has at least one entry, so each copy block's first entry
+// (a multiple of PK_OUT) lies in exactly one row: that row records itself as
+// the block's first row (first_row[ncopy] = the last row).
+__global__ void __launch_bounds__(PK_SCAN) k_pack_rp(const int32_t *list, int64_t len,
+                                                     const int32_t *off, const int32_t *vgraph,
+                                                     const int32_t *g_vbase, const int64_t *g_ebase,
+                                                     uint32_t waves, uint64_t magic,
+                                                     const int64_t *bstart, int64_t *rp,
+                                                     int64_t *srcw, int64_t *first_row,
+                                                     int64_t ncopy)
+{
+    __shared__ int64_t s_warp[33];
+    const int64_t i = (int64_t)blockIdx.x * PK_SCAN + threadIdx.x;
+    int64_t d = 0, src = 0;
+    uint32_t wv = 0;
+    if (i < len) {
+        const int32_t v = list[i];
+        const int32_t g = vgraph ? vgraph[v] : 0;
+        const int32_t rs = off[(int64_t)v + g];
+        d = off[(int64_t)v + g + 1] - rs;
+        src = (g_ebase ? g_ebase[g] : 0) + rs;
+        const int32_t lv = v - (vgraph ? g_vbase[g] : 0);
+        wv = waves > 1 ? fastmod((uint32_t)lv, magic, waves) : 0u;
+    }
+    int64_t tot;
+    const int64_t ex = block_exclusive_scan(d, s_warp, &tot);
+    if (i < len) {
+        const int64_t start = bstart[blockIdx.x] + ex, end = start + d;
+        rp[i] = start;
+        srcw[i] = src | ((int64_t)wv << 48);
+        for (int64_t c = (start + PK_OUT - 1) / PK_OUT; c * PK_OUT < end; ++c) first_row[c] = i;
+        if (i == len - 1) {
+            rp[len] = end;
+            first_row[ncopy] = i;
+        }
+    }
+}
+
+// Entries [j_lo, j_lo + PK_OUT) of the packed arrays, one warp per chunk: rows
+// r0 (holding j_lo) to r1 (holding the next chunk's first entry, or the last
+// row), at most PK_OUT + 1 of them.  Their packed and original starts and
+// wave classes are staged in the warp's shared memory with the row of every
+// entry of the chunk; lane l copies entries l, l + 32, ..., so every load and
+// store of the warp covers 32 consecutive entries.
+__global__ void __launch_bounds__(PK_T) k_pack_rows(const int64_t *rp, const int64_t *srcw,
+                                                    const int64_t *first_row, int64_t ncopy,
+                                                    const int32_t *idx, const int32_t *wts,
+                                                    int64_t ne, uint32_t waves, uint64_t magic,
+                                                    int32_t *pidx, int32_t *pwts)
+{
+    __shared__ int64_t s_rp_all[PK_WARPS][PK_OUT + 2];
+    __shared__ int64_t s_src_all[PK_WARPS][PK_OUT + 1];
+    __shared__ uint16_t s_row_all[PK_WARPS][PK_OUT];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t chunk = (int64_t)blockIdx.x * PK_WARPS + wib;
+    if (chunk >= ncopy) return;  // warp-uniform
+    int64_t *s_rp = s_rp_all[wib];
+    int64_t *s_src = s_src_all[wib];
+    uint16_t *s_row = s_row_all[wib];
+    const int64_t j_lo = chunk * PK_OUT;
+    const int64_t j_hi = min(j_lo + (int64_t)PK_OUT, ne);
+    const int64_t r0 = first_row[chunk];
+    const int64_t r1 = first_row[chunk + 1];
+    const int nr = (int)min(r1 - r0 + 1, (int64_t)PK_OUT + 1);
+    for (int k = lane; k <= nr; k += 32) s_rp[k] = rp[r0 + k];
+    for (int k = lane; k < nr; k += 32) s_src[k] = srcw[r0 + k];
+    __syncwarp();
+    chunk_rows([&](int k) { return (int)(s_rp[k] - j_lo); }, nr, s_row);
+    int32_t c[PK_PER], w[PK_PER];
+    uint32_t wv[PK_PER];
+#pragma unroll
+    for (int q = 0; q < PK_PER; ++q) {  // every load in flight before any use
+        const int e = lane + 32 * q;
+        const int64_t j = j_lo + e;
+        c[q] = w[q] = 0;
+        wv[q] = 0u;
+        if (j < j_hi) {
+            const int k = s_row[e];
+            const int64_t sw = s_src[k];
+            const int64_t src = (sw & 0xFFFFFFFFFFFFll) + (j - s_rp[k]);
+            wv[q] = (uint32_t)(sw >> 48);
+            c[q] = __ldg(idx + src);
+            if (wts) w[q] = __ldg(wts + src);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < PK_PER; ++q) {
+        const int64_t j = j_lo + lane + 32 * q;
+        if (j >= j_hi) continue;
+        int32_t u = c[q];
+        if (waves > 1 && fastmod((uint32_t)u, magic, waves) < wv[q])
+            u = (int32_t)((uint32_t)u | 0x80000000u);
+        pidx[j] = u;
+        if (wts) pwts[j] = w[q];
+    }
+}
 
 // ---------------------------------------------------------------------------
 // wave partition (asynchronous mode)
@@ -712,6 +842,49 @@ int hub_order(const int32_t *list, int64_t len, const int32_t *off, const int32_
     if (len <= 0) return 0;
     k_hub_order<<<1, 1024, 0, st>>>(list, len, off, vgraph, out);
     ++*launches;
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int hub_task_starts(HubTask *tasks, int64_t n, const int64_t *rp, cudaStream_t st,
+                    int64_t *launches)
+{
+    if (n <= 0) return 0;
+    k_hub_task_starts<<<grid_for(n, 256, 1024), 256, 0, st>>>(tasks, n, rp);
+    ++*launches;
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int64_t pack_scratch_ints(int64_t len)
+{
+    const int64_t nblk = (len + PK_SCAN - 1) / PK_SCAN;
+    return 2 * (nblk > 0 ? nblk : 1) + len;
+}
+
+int pack_rows(const int32_t *list, int64_t len, const int32_t *off, const int32_t *idx,
+              const int32_t *wts, int64_t ne, const int32_t *vgraph, const int32_t *g_vbase,
+              const int64_t *g_ebase, int waves, int64_t *scratch, int64_t *rp,
+              int64_t *first_row, int32_t *pidx, int32_t *pwts, cudaStream_t st,
+              int64_t *launches)
+{
+    if (waves < 1) return -1;
+    if (len == 0) return cudaMemsetAsync(rp, 0, sizeof(int64_t), st) == cudaSuccess ? 0 : -1;
+    const int64_t nblk = (len + PK_SCAN - 1) / PK_SCAN;
+    const int64_t ncopy = (ne + PK_OUT - 1) / PK_OUT;
+    int64_t *bsum = scratch, *bstart = scratch + nblk, *srcw = scratch + 2 * nblk;
+    const uint64_t magic = fastmod_magic((uint32_t)waves);
+    k_pack_sum<<<(int)nblk, PK_SCAN, 0, st>>>(list, len, off, vgraph, bsum);
+    k_class_begin<<<1, 1024, 0, st>>>(bsum, nblk, bstart);
+    k_pack_rp<<<(int)nblk, PK_SCAN, 0, st>>>(list, len, off, vgraph, g_vbase, g_ebase,
+                                              (uint32_t)waves, magic, bstart, rp, srcw, first_row,
+                                              ncopy);
+    *launches += 3;
+    if (ne > 0) {
+        k_pack_rows<<<(int)((ncopy + PK_WARPS - 1) / PK_WARPS), PK_T, 0, st>>>(
+            rp, srcw, first_row, ncopy, idx, wts, ne,
+                                                  (uint32_t)waves, magic, pidx,
+                                                  wts ? pwts : nullptr);
+        ++*launches;
+    }
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

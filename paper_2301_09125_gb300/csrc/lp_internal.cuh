@@ -11,6 +11,14 @@
 //   list int32  global vertex ids sorted into degree buckets
 //               [small | warp | cta | cta2 | hub], ascending id inside a bucket
 //               except hub, which is sorted by degree, largest first
+// Packed rows (what the sweep reads): the rows of the run's list (the bucket
+// list, or the wave-partitioned list of an asynchronous run) copied in list
+// order, so that the rows of one launch lie next to each other in HBM:
+//   rp   int64  [len + 1] start of list item i's row in pidx / pwts
+//   pidx int32  neighbour ids (local), bit 31 set when the neighbour's wave
+//               comes before the row's vertex's wave (read from this
+//               iteration's labels); never set in synchronous runs
+//   pwts int32  weights aligned with pidx, or null for unit weights
 #pragma once
 
 #include <cstdint>
@@ -68,13 +76,14 @@ struct HubTask {
     int32_t part0;   // first partition item of the row in this list
     int64_t poff0;   // first entry of its partition offsets (nseg x (npart + 1))
     int64_t tab;     // first slot of its fallback table
+    int64_t e0;      // first entry of its packed row
 };
 
 // Arguments of one sweep kernel launch (one bucket).
 struct SweepArgs {
-    const int32_t *off;
-    const int32_t *idx;
-    const int32_t *wts;      // null = unit weights
+    const int64_t *rp;       // packed row starts, aligned with `list` (rp[i] .. rp[i + 1])
+    const int32_t *idx;      // packed neighbour ids (bit 31: earlier wave)
+    const int32_t *wts;      // packed weights, null = unit weights
     const int32_t *lab_in;   // labels read (== lab_out in asynchronous mode)
     int32_t *lab_out;        // labels written
     const int32_t *list;     // bucket entries (global vertex ids)
@@ -102,12 +111,10 @@ struct SweepArgs {
     // raised by the device-side tolerance test once the run is over: kernels
     // of iterations launched ahead of it return at once (null: not used)
     const int32_t *stop;
-    // asynchronous waves (Sec. 3.3): this launch runs wave `wave_k` of `waves`;
-    // a neighbour u of an earlier wave (u mod waves < wave_k) is read from
-    // lab_out (this iteration), every other one from lab_in.  waves = 1: sync.
+    // asynchronous waves (Sec. 3.3): a neighbour of an earlier wave (bit 31 of
+    // its packed id) is read from lab_out (this iteration), every other one
+    // from lab_in.  waves = 1: sync.
     uint32_t waves;
-    uint32_t wave_k;
-    uint64_t wave_magic;     // fastmod constant of `waves`
     // small-row kernel: list entries per warp tile (32, or fewer for short
     // lists of rows long enough to need several chunks; set by the launch
     // from the bucket's mean degree)
@@ -135,30 +142,41 @@ struct SweepArgs {
     int32_t *hused;
     int32_t *hdone;
     int32_t *hnused;
-    // per long-row task: own-label weight and total weight of the row (the
-    // majority test of rows longer than HUB_ONE_MAX, summed over segments)
+    // per long-row task: own-label weight, total weight, candidate weight and
+    // candidate of the row (the majority test of rows longer than HUB_ONE_MAX,
+    // summed over segments); per segment item: its weighted majority vote
+    // (candidate, surplus)
     uint32_t *hmaj;
+    int2 *hvote;
+    int32_t *hopen;   // long rows that no label holds by majority (set before the segment pass)
+    // single graphs, majority level 2: the pre-pass lists the positions of the
+    // rows it did not settle (cpos, *ccount of them) for the CTA kernel
+    int32_t *cpos;
+    int32_t *ccount;
     // per vertex: 1 if the majority pre-pass of this launch settled its row
     // (rows of the cta, cta2 and hub buckets; null = no pre-pass)
     uint8_t *vmaj;
 };
 
 // Modularity arguments (a whole graph set; graph layout as for SweepArgs).
+// The entry pass reads the packed rows in chunks of PACK_CHUNK entries;
+// first_row[c] is the list item whose row holds entry c * PACK_CHUNK
+// (first_row[ncopy] = the last item).
+constexpr int PACK_CHUNK = 256;  // one warp, eight entries per lane
 struct ModArgs {
-    const int32_t *off;
-    const int32_t *idx;
-    const int32_t *wts;        // null = unit weights
+    const int64_t *rp;         // packed row starts, aligned with list (len + 1)
+    const int32_t *idx;        // packed neighbour ids (bit 31 ignored)
+    const int32_t *wts;        // packed weights, null = unit weights
     const int32_t *lab;        // labels of every vertex (local ids)
-    const int32_t *list;       // bucket entries
+    const int32_t *list;       // list items (global vertices), len of them
     int64_t len;
     int64_t ne;                // entries in the arena
+    const int64_t *first_row;  // ncopy + 1 entries
+    int64_t ncopy;
     const int32_t *vgraph;     // null for a single graph
     const int32_t *g_vbase;
-    const int64_t *g_ebase;
     unsigned long long *kc;    // [nv] K_c of community c of graph g at vbase_g + c (zeroed)
     unsigned long long *acc;   // [4 G]: L, 2m, S high, S low per graph (zeroed)
-    int32_t tile_rows;         // small-row kernel: list entries per warp tile
-    int32_t small_mean_deg;    // mean degree of the small bucket (rounded up)
 };
 
 // Rows per warp tile of the small-row kernels: fewer than 32 while a list
@@ -233,6 +251,23 @@ int hub_order(const int32_t *list, int64_t len, const int32_t *off, const int32_
               int32_t *out, cudaStream_t st, int64_t *launches);
 int hub_tasks(int32_t *list, int64_t len, const int32_t *off, const int32_t *vgraph,
               HubTask *tasks, int64_t *totals, cudaStream_t st, int64_t *launches);
+// tasks[i].e0 = rp[i] for i < n (the packed row start of task i's row).
+int hub_task_starts(HubTask *tasks, int64_t n, const int64_t *rp, cudaStream_t st,
+                    int64_t *launches);
+// Packed rows of list[0..len) (every listed vertex has at least one entry):
+// rp[i] = entries of the rows before item i (rp[len] = their total, the
+// arena's entry count), then the rows copied in list order into pidx / pwts
+// (pwts skipped when wts is null), with bit 31 of a neighbour id set when
+// waves > 1 and the neighbour's wave (local id mod waves) comes before the
+// row's; first_row (pack_chunks(ne) + 1 entries) receives the item holding
+// each PACK_CHUNK-th entry.  scratch: pack_scratch_ints(len) int64.
+int64_t pack_scratch_ints(int64_t len);
+inline int64_t pack_chunks(int64_t ne) { return (ne + PACK_CHUNK - 1) / PACK_CHUNK; }
+int pack_rows(const int32_t *list, int64_t len, const int32_t *off, const int32_t *idx,
+              const int32_t *wts, int64_t ne, const int32_t *vgraph, const int32_t *g_vbase,
+              const int64_t *g_ebase, int waves, int64_t *scratch, int64_t *rp,
+              int64_t *first_row, int32_t *pidx, int32_t *pwts, cudaStream_t st,
+              int64_t *launches);
 // Task index of every segment item and partition item of the first nbig tasks.
 int hub_item_maps(const HubTask *tasks, int64_t nbig, int32_t *seg_task, int32_t *part_task,
                   cudaStream_t st, int64_t *launches);
@@ -324,8 +359,9 @@ int split_launch(const int32_t *off, const int32_t *idx, int32_t *lab, int32_t n
                  int32_t *parent, int32_t *err, int32_t *big, unsigned long long *count,
                  int num_sms, cudaStream_t st, int64_t *launches);
 
-// Entry and square passes of the modularity of every graph of a set.
-int modularity_launch(const ModArgs &a, const int64_t *bucket_begin, const int64_t *bucket_len,
-                      int64_t nslots, bool multi, int num_sms, cudaStream_t st, int64_t *launches);
+// Entry and square passes of the modularity of every graph of a set (nslots:
+// entries of kc).
+int modularity_launch(const ModArgs &a, int64_t nslots, bool multi, cudaStream_t st,
+                      int64_t *launches);
 
 }  // namespace lp

@@ -49,9 +49,11 @@ struct Vtx {
     int64_t e0;   // global index of the first entry
 };
 
+// List item `item` of the launch: its vertex, graph and packed row.
 template <bool MULTI>
-__device__ __forceinline__ bool load_vtx(const SweepArgs &a, int32_t v, Vtx &x)
+__device__ __forceinline__ bool load_vtx(const SweepArgs &a, int64_t item, Vtx &x)
 {
+    const int32_t v = __ldg(a.list + item);
     x.v = v;
     x.g = 0;
     x.vb = 0;
@@ -61,12 +63,29 @@ __device__ __forceinline__ bool load_vtx(const SweepArgs &a, int32_t v, Vtx &x)
         x.vb = a.g_vbase[x.g];
     }
     x.lv = v - x.vb;
-    const int64_t ob = (int64_t)x.vb + x.g + x.lv;  // graph g's offsets start at vbase_g + g
-    const int32_t rs = __ldg(a.off + ob);
-    const int32_t re = __ldg(a.off + ob + 1);
-    x.d = re - rs;
-    x.e0 = (MULTI ? a.g_ebase[x.g] : 0) + rs;
+    const int64_t rs = __ldg(a.rp + item);
+    x.d = (int32_t)(__ldg(a.rp + item + 1) - rs);
+    x.e0 = rs;
     x.own = __ldg(a.lab_in + v);
+    return true;
+}
+
+// The row of a hub task (its packed start and degree are in the task).
+template <bool MULTI>
+__device__ __forceinline__ bool load_task(const SweepArgs &a, const HubTask &t, Vtx &x)
+{
+    x.v = t.v;
+    x.g = 0;
+    x.vb = 0;
+    if (MULTI) {
+        x.g = a.vgraph[t.v];
+        if (!a.g_active[x.g]) return false;
+        x.vb = a.g_vbase[x.g];
+    }
+    x.lv = t.v - x.vb;
+    x.d = t.d;
+    x.e0 = t.e0;
+    x.own = __ldg(a.lab_in + t.v);
     return true;
 }
 
@@ -79,39 +98,69 @@ struct VtxPipe {
     uint8_t next_maj = 0;  // the majority pre-pass flag (when there is one)
     __device__ __forceinline__ void fetch(const SweepArgs &a, int64_t item)
     {
-        next_ok = item < a.len && load_vtx<MULTI>(a, a.list[item], next);
+        next_ok = item < a.len && load_vtx<MULTI>(a, item, next);
         next_maj = next_ok && a.vmaj ? a.vmaj[next.v] : 0;
     }
 };
 
 // Whether graph g's vertices try the majority test in this launch: not in
-// the first two sweeps from unique labels (the host clears a.majority; the
-// labels are still too fragmented: on R-MAT no row longer than 32 entries
-// passed the test in the second sweep and all of them in the third), and only
-// after an iteration that changed fewer than 60% of the graph's labels (a
-// synchronous run that oscillates changes nearly all of them and no row
-// passes).
-__device__ __forceinline__ bool try_majority(const SweepArgs &a, int32_t g)
+// the first sweep from unique labels (the host clears a.majority: no row
+// longer than 8 entries has a majority label then), and only after an
+// iteration that changed fewer than 60% of the graph's labels (a synchronous
+// run that oscillates changes nearly all of them and no row passes).  On
+// R-MAT the test (own label, then the weighted vote's candidate) settles
+// nearly every row longer than 32 entries from the second wave of the second
+// sweep on.
+// Level 1 (20-60% changed: labels still consolidating, many rows fail) tests
+// only rows already held in registers, where a failed test costs no memory
+// traffic; level 2 (under 20%: nearly every row passes) also runs the
+// warp-per-row pre-passes of the CTA kernels' rows and the small kernel's
+// packed majority pass.
+__device__ __forceinline__ int maj_level(const SweepArgs &a, int32_t g)
 {
-    if (!a.majority || a.identity) return false;
-    if (!a.changed_prev) return true;
-    return 5ll * __ldg(a.changed_prev + g) < 3ll * __ldg(a.g_n + g);
+    if (!a.majority || a.identity) return 0;
+    if (!a.changed_prev) return 2;
+    const long long c = __ldg(a.changed_prev + g), n = __ldg(a.g_n + g);
+    if (5 * c >= 3 * n) return 0;
+    return 5 * c < n ? 2 : 1;
 }
 
-// Label of neighbour u (local id u, global index gi) as seen by this launch.
-// Neither buffer is written at an address this launch reads: lab_in is only
-// written by the next iteration, and lab_out entries of earlier waves were
-// written by earlier launches, so both go through the read-only path.  When
-// one launch sweeps every wave (COH), earlier waves' labels were written by
-// other CTAs of the same launch before a grid barrier: they are read from L2
-// (ld.global.cg), which the barrier's fences make coherent, never through a
-// possibly stale L1 line.
-template <bool COH = false>
-__device__ __forceinline__ int32_t neighbour_label(const SweepArgs &a, int64_t gi, int32_t u)
+__device__ __forceinline__ bool try_majority(const SweepArgs &a, int32_t g)
 {
-    const bool earlier = a.waves > 1 && fastmod((uint32_t)u, a.wave_magic, a.waves) < a.wave_k;
-    if (COH && earlier) return __ldcg(a.lab_out + gi);
-    return ld_label((earlier ? a.lab_out : a.lab_in) + gi);
+    return maj_level(a, g) > 0;
+}
+
+// Whether the weighted vote's candidate c (final surplus n, row weight tw) is
+// worth a counting pass: a surplus above half the weight already proves the
+// majority (the candidate's weight is at least its surplus); a thin surplus
+// rarely ends in one, and the row's table gives the exact answer anyway.
+__device__ __forceinline__ bool vote_proven(uint32_t n, uint32_t tw)
+{
+    return 2ull * n > (unsigned long long)tw;
+}
+
+__device__ __forceinline__ bool vote_worth_counting(uint32_t n, uint32_t tw)
+{
+    return 8ull * n >= (unsigned long long)tw;
+}
+
+constexpr int32_t ID_MASK = 0x7FFFFFFF;  // packed neighbour id without its wave bit
+
+// Label of the neighbour with packed id `col` (graph's first vertex vb) as
+// seen by this launch: a neighbour of an earlier wave (bit 31) is read from
+// lab_out, every other one from lab_in.  Neither buffer is written at an
+// address this launch reads: lab_in is only written by the next iteration,
+// and lab_out entries of earlier waves were written by earlier launches, so
+// both go through the read-only path.  When one launch sweeps every wave
+// (COH), earlier waves' labels were written by other CTAs of the same launch
+// before a grid barrier: they are read from L2 (ld.global.cg), which the
+// barrier's fences make coherent, never through a possibly stale L1 line.
+template <bool COH = false>
+__device__ __forceinline__ int32_t neighbour_label(const SweepArgs &a, int32_t vb, int32_t col)
+{
+    const int64_t gi = (int64_t)vb + (col & ID_MASK);
+    if (COH && col < 0) return __ldcg(a.lab_out + gi);
+    return ld_label((col < 0 ? a.lab_out : a.lab_in) + gi);
 }
 
 
@@ -177,7 +226,7 @@ __device__ __forceinline__ Quad load_quad(const SweepArgs &a, int64_t blk, int64
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const bool in = e0 + j >= lo && e0 + j < hi;
-        q.l[j] = in ? neighbour_label<COH>(a, (int64_t)vb + u[j], u[j]) : EMPTY;
+        q.l[j] = in ? neighbour_label<COH>(a, vb, u[j]) : EMPTY;
         q.w[j] = in ? w[j] : 0;
     }
     return q;
@@ -221,6 +270,97 @@ __device__ __forceinline__ void own_weight(const Quad &q, int32_t own, uint32_t 
     }
 }
 
+// Weighted majority vote (Boyer & Moore's MJRTY with weights): the state is
+// a candidate label and its surplus weight.  If some label holds more than
+// half of the weight of the entries voted, the final candidate is that label,
+// whatever the order in which entries are added and partial states merged.
+// A label that holds more than half of a row's weight is the unique maximum
+// under either tie rule, so a verified candidate is the row's new label.
+struct Vote {
+    int32_t c = EMPTY;
+    uint32_t n = 0u;
+};
+
+__device__ __forceinline__ void vote_add(Vote &v, int32_t l, uint32_t w)
+{
+    if (l == EMPTY) return;
+    if (v.n == 0u) {
+        v.c = l;
+        v.n = w;
+    } else if (v.c == l) {
+        v.n += w;
+    } else if (v.n >= w) {
+        v.n -= w;
+    } else {
+        v.c = l;
+        v.n = w - v.n;
+    }
+}
+
+__device__ __forceinline__ Vote vote_merge(const Vote &x, const Vote &y)
+{
+    if (x.n == 0u) return y;
+    if (y.n == 0u) return x;
+    if (x.c == y.c) return Vote{x.c, x.n + y.n};
+    return x.n >= y.n ? Vote{x.c, x.n - y.n} : Vote{y.c, y.n - x.n};
+}
+
+// the warp's merged state (lane 0's, broadcast: lanes may merge in different
+// orders and disagree when there is no majority)
+__device__ __forceinline__ Vote warp_vote_state(Vote v)
+{
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        Vote y;
+        y.c = __shfl_xor_sync(FULL, v.c, o);
+        y.n = __shfl_xor_sync(FULL, v.n, o);
+        v = vote_merge(v, y);
+    }
+    v.c = __shfl_sync(FULL, v.c, 0);
+    v.n = __shfl_sync(FULL, v.n, 0);
+    return v;
+}
+
+// the warp's candidate (EMPTY when nothing is left)
+__device__ __forceinline__ int32_t warp_vote(const Vote &v)
+{
+    const Vote r = warp_vote_state(v);
+    return r.n ? r.c : EMPTY;
+}
+
+__device__ __forceinline__ void vote_quad(const Quad &q, Vote &v)
+{
+#pragma unroll
+    for (int j = 0; j < 4; ++j) vote_add(v, q.l[j], (uint32_t)q.w[j]);
+}
+
+// summed weight of the entries of q carrying label c
+__device__ __forceinline__ uint32_t label_weight(const Quad &q, int32_t c)
+{
+    uint32_t s = 0u;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) s += q.l[j] == c ? (uint32_t)q.w[j] : 0u;
+    return s;
+}
+
+// the block's merged vote, valid in every thread (s_v: NT / 32 + 1 entries)
+template <int NT>
+__device__ __forceinline__ Vote block_vote(const Vote &v, Vote *s_v)
+{
+    const Vote w = warp_vote_state(v);
+    if ((threadIdx.x & 31) == 0) s_v[threadIdx.x >> 5] = w;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        Vote m;
+        for (int k = 0; k < NT / 32; ++k) m = vote_merge(m, s_v[k]);
+        s_v[NT / 32] = m;
+    }
+    __syncthreads();
+    const Vote r = s_v[NT / 32];
+    __syncthreads();
+    return r;
+}
+
 // Identity sweep: the labels read are the initial unique labels (label of u
 // is u) and no row repeats a neighbour, so a label's summed weight is its one
 // edge weight and its first position is that entry's.  The adopted label is
@@ -239,8 +379,9 @@ __device__ __forceinline__ Cand identity_best(const SweepArgs &a, int64_t row, i
         for (int j = 0; j < 4; ++j) {
             const int64_t e = blk * 4 + j;
             if (e < lo || e >= hi || (uint32_t)w[j] < best.sum) continue;
+            const int32_t l = u[j] & ID_MASK;  // the initial label of u is u
             const Cand c{(uint32_t)w[j], 0xFFFFFFFFu - (uint32_t)(e - row),
-                         a.strict ? 0ull : stream_at(ktv, (uint64_t)u[j] + 1), u[j]};
+                         a.strict ? 0ull : stream_at(ktv, (uint64_t)l + 1), l};
             if (better(c, best)) best = c;
         }
     }
@@ -303,7 +444,7 @@ __device__ __forceinline__ void small_sweep(const SweepArgs &a)
         const int64_t i = tile * rt + lane;
         Vtx x{0, 0, 0, 0, 0, 0, 0};
         bool ok = false;
-        if (lane < rt && i < a.len) ok = load_vtx<MULTI>(a, a.list[i], x);
+        if (lane < rt && i < a.len) ok = load_vtx<MULTI>(a, i, x);
         int d = ok ? x.d : 0;
         const int32_t own = ok ? x.own : 0;
 
@@ -323,7 +464,7 @@ __device__ __forceinline__ void small_sweep(const SweepArgs &a)
                     const int64_t e = x.e0 + j;
                     const int32_t u = ld_entry(a.idx + e);
                     wt[j] = a.wts ? (uint32_t)ld_entry(a.wts + e) : 1u;
-                    lab[j] = a.identity ? u : neighbour_label<COH>(a, (int64_t)x.vb + u, u);
+                    lab[j] = a.identity ? (u & ID_MASK) : neighbour_label<COH>(a, x.vb, u);
                 }
             }
             // entries past the row are EMPTY with weight 0: their totals are 0
@@ -373,7 +514,7 @@ __device__ __forceinline__ void small_sweep(const SweepArgs &a)
             }
         }
 
-        if (__any_sync(FULL, d > 0 && try_majority(a, x.g))) {
+        if (__any_sync(FULL, d > 0 && maj_level(a, x.g) == 2)) {
             // Majority pass: rows are read as aligned 16-byte blocks, several
             // rows per 32-block chunk; a row whose own label holds more than
             // half of its weight keeps it (the unique maximum) and drops out.
@@ -471,7 +612,7 @@ __device__ __forceinline__ void small_sweep(const SweepArgs &a)
                 const long long e = o_e0 + pos;
                 const int32_t u = ld_entry(a.idx + e);
                 w = a.wts ? ld_entry(a.wts + e) : 1;
-                l = a.identity ? u : neighbour_label<COH>(a, (int64_t)o_vb + u, u);
+                l = a.identity ? (u & ID_MASK) : neighbour_label<COH>(a, o_vb, u);
             }
             // the owner's lanes (its whole row: rows fit in the chunk), then the
             // lanes of the owner with an equal label; the lowest lane of a
@@ -597,8 +738,8 @@ __global__ void __launch_bounds__(256, 6) k_small_waves(SweepArgs a, const int32
     for (uint32_t k = 0; k < a.waves; ++k) {
         SweepArgs b = a;
         b.list = wlist + wstart[k];
+        b.rp = a.rp + wstart[k];
         b.len = wcount[k];
-        b.wave_k = k;
         b.identity = a.identity && k == 0;  // later waves read this sweep's labels
         small_sweep<false, true>(b);
         if (k + 1 < a.waves && !grid_barrier(bar, err)) return;
@@ -631,31 +772,149 @@ __device__ __forceinline__ void insert_hot(const HotLabel &hot, int32_t *tk, int
 }
 
 // ----------------------------------------------------------------------------
+// 64-bit tables of the warp and CTA kernels: slot = (label + 1, summed
+// weight), one shared atomic per inserted entry.  The strict tie rule needs a
+// label's first position only when several labels reach the maximum (rows of
+// more than 128 entries rarely tie once a sweep has run); those rows take a
+// second pass over their entries that finds the earliest entry whose label
+// is at the maximum.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ void insert_quad64(const Quad &q, HotLabel &hot, unsigned long long *t,
+                                              int lg)
+{
+    hot.pick(q);
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        if (!hot.take(q.l[j], q.w[j], 0u) && q.l[j] != EMPTY)
+            table64_add(t, lg, q.l[j], (uint32_t)q.w[j]);
+}
+
+__device__ __forceinline__ void insert_hot64(const HotLabel &hot, unsigned long long *t, int lg)
+{
+    const int hs = hot.total();
+    if ((threadIdx.x & 31) == 0 && hs > 0) table64_add(t, lg, hot.label, (uint32_t)hs);
+}
+
+// Top of the slots [0, slots) of a 64-bit table, scanned by NT threads
+// (index tid), valid in every thread: the maximum, how many labels reach it
+// and one of them; with non-strict ties, the least tie key among those labels
+// (a second scan), how many share it and one of them.
+template <int NT>
+__device__ __forceinline__ Top scan64(const unsigned long long *t, int slots, int tid, int strict,
+                                      uint64_t ktv, uint64_t *s_k, uint32_t *s_c, int32_t *s_l)
+{
+    uint32_t ms = 0u, mc = 0u;
+    int32_t ml = EMPTY;
+    for (int j = tid; j < slots; j += NT) {
+        const unsigned long long v = t[j];
+        const uint32_t sw = (uint32_t)v;
+        if (v != 0ull && sw >= ms) {
+            mc = sw > ms ? 1u : mc + 1u;
+            ms = sw;
+            ml = slot_label(v);
+        }
+    }
+    uint64_t k = ms;
+    block_top<NT>(k, mc, ml, s_k, s_c, s_l);
+    Top r{(uint32_t)k, mc, ml, 0ull};
+    if (!strict && r.sum > 0u) {
+        uint64_t hk = 0ull;  // ~tie key: the largest wins
+        uint32_t hc = 0u;
+        int32_t hl = EMPTY;
+        for (int j = tid; j < slots; j += NT) {
+            const unsigned long long v = t[j];
+            if (v != 0ull && (uint32_t)v == r.sum) {
+                const int32_t l = slot_label(v);
+                const uint64_t key = ~stream_at(ktv, (uint64_t)l + 1);
+                if (hc == 0u || key > hk) {
+                    hk = key;
+                    hc = 1u;
+                    hl = l;
+                } else if (key == hk) {
+                    ++hc;
+                }
+            }
+        }
+        block_top<NT>(hk, hc, hl, s_k, s_c, s_l);
+        r.h = ~hk;
+        r.cnt = hc;
+        r.label = hl;
+    }
+    return r;
+}
+
+template <int NT>
+__device__ __forceinline__ void clear64(unsigned long long *t, int slots, int tid)
+{
+    for (int j = tid; j < slots; j += NT) t[j] = 0ull;
+}
+
+// (row position << 32 | label) of the earliest entry of q (entries 4 * blk ..
+// of a row starting at `row`) whose label is one of the tied labels of `top`,
+// ~0 if none
+__device__ __forceinline__ uint64_t tie_quad(const Quad &q, int64_t blk, int64_t row,
+                                             const unsigned long long *t, int lg, const Top &top,
+                                             int strict, uint64_t ktv)
+{
+    uint64_t best = ~0ull;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int32_t l = q.l[j];
+        if (l == EMPTY || table64_sum(t, lg, l) != top.sum) continue;
+        if (!strict && stream_at(ktv, (uint64_t)l + 1) != top.h) continue;
+        const uint64_t c = ((uint64_t)(uint32_t)(blk * 4 + j - row) << 32) | (uint32_t)l;
+        best = c < best ? c : best;
+    }
+    return best;
+}
+
+// the same over the entries [lo, hi) of a row, re-read, NT threads (index tid)
+template <int NT>
+__device__ __forceinline__ uint64_t tie_range(const SweepArgs &a, int64_t row, int64_t lo,
+                                              int64_t hi, int32_t vb, int tid,
+                                              const unsigned long long *t, int lg, const Top &top,
+                                              uint64_t ktv)
+{
+    uint64_t best = ~0ull;
+    for (int64_t blk = (lo >> 2) + tid; blk <= (hi - 1) >> 2; blk += NT) {
+        const uint64_t c = tie_quad(load_quad(a, blk, lo, hi, vb), blk, row, t, lg, top, a.strict,
+                                    ktv);
+        best = c < best ? c : best;
+    }
+    return best;
+}
+
+// Aggregate the entries [lo, hi) of a row into a 64-bit table of 2^lg slots
+// (room for every distinct label of the range), NT threads cooperating.
+template <int NT>
+__device__ __forceinline__ void accumulate_range64(const SweepArgs &a, int64_t lo, int64_t hi,
+                                                   int32_t vb, unsigned long long *t, int lg)
+{
+    const int64_t b_hi = (hi - 1) >> 2;
+    HotLabel hot;
+    for (int64_t base = lo >> 2; base <= b_hi; base += NT) {
+        const int64_t blk = base + threadIdx.x;
+        const Quad q = blk <= b_hi ? load_quad(a, blk, lo, hi, vb) : empty_quad();
+        insert_quad64(q, hot, t, lg);
+    }
+    insert_hot64(hot, t, lg);
+}
+
+// ----------------------------------------------------------------------------
 // warp bucket: one warp per vertex, private shared table
 // ----------------------------------------------------------------------------
 constexpr int WARP_LG = 8;  // log2(WARP_TABLE)
 static_assert((1 << WARP_LG) == WARP_TABLE, "warp table size");
 
 template <bool MULTI>
-__global__ void __launch_bounds__(256, MULTI ? 4 : 5) k_warp(SweepArgs a)
+__global__ void __launch_bounds__(256, 4) k_warp(SweepArgs a)
 {
     if (a.stop && *a.stop) return;  // launched past the end of the run
-    __shared__ int32_t s_key[8 * WARP_TABLE];
-    __shared__ int32_t s_sum[8 * WARP_TABLE];
-    __shared__ uint32_t s_np[8 * WARP_TABLE];
+    __shared__ unsigned long long s_tab[8 * WARP_TABLE];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    volatile int32_t *tk = s_key + wib * WARP_TABLE;
-    int32_t *tk_atomic = s_key + wib * WARP_TABLE;
-    volatile int32_t *ts = s_sum + wib * WARP_TABLE;
-    volatile uint32_t *tp = s_np + wib * WARP_TABLE;
-    int32_t *ts_atomic = s_sum + wib * WARP_TABLE;
-    uint32_t *tp_atomic = s_np + wib * WARP_TABLE;
-    for (int j = lane; j < WARP_TABLE; j += 32) {
-        tk[j] = EMPTY;
-        ts[j] = 0;
-        tp[j] = 0;
-    }
+    unsigned long long *tab = s_tab + wib * WARP_TABLE;
+    clear64<32>(tab, WARP_TABLE, lane);
     __syncwarp();
 
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -672,91 +931,82 @@ __global__ void __launch_bounds__(256, MULTI ? 4 : 5) k_warp(SweepArgs a)
         const int32_t own = x.own;
         const int64_t lo = x.e0, hi = x.e0 + x.d;
         const int64_t b_hi = (hi - 1) >> 2;
+        const uint64_t ktv = stream_at(a.key_t, (uint64_t)x.lv + 1);
+        int32_t label;
         if (a.identity) {
-            const Cand best = warp_argmax(
-                identity_best<32>(a, lo, lo, hi, stream_at(a.key_t, (uint64_t)x.lv + 1), lane),
-                a.strict);
-            if (lane == 0) {
-                a.lab_out[x.v] = best.label;
-                if (best.label != own) {
-                    if (MULTI)
-                        atomicAdd(a.changed + x.g, 1);
-                    else
-                        ++my_changed;
-                }
-            }
-            continue;
-        }
-        // a row of at most 32 quads is loaded once, one quad per lane; if the
-        // vertex's own label holds more than half of its weight it stays
-        const int64_t b0 = lo >> 2;
-        const bool one = b_hi - b0 < 32;
-        Quad q1 = empty_quad();
-        if (one) {
-            if (b0 + lane <= b_hi) q1 = load_quad(a, b0 + lane, lo, hi, x.vb);
-            if (try_majority(a, x.g)) {
-                uint32_t ow = 0, tw = 0;
-                own_weight(q1, own, ow, tw);
-                ow = __reduce_add_sync(FULL, ow);
-                tw = __reduce_add_sync(FULL, tw);
-                if (2ull * ow > (unsigned long long)tw) {
-                    if (lane == 0) a.lab_out[x.v] = own;
-                    continue;
-                }
-            }
-        }
-        // <= 128 labels in 256 slots: every insert finds its slot
-        HotLabel hot;
-        for (int64_t base = b0; base <= b_hi; base += 32) {
-            const int64_t blk = base + lane;
-            const Quad q = one ? q1 : (blk <= b_hi ? load_quad(a, blk, lo, hi, x.vb) : empty_quad());
-            insert_quad(q, blk, lo, hot, tk_atomic, ts_atomic, tp_atomic, WARP_LG);
-        }
-        insert_hot(hot, tk_atomic, ts_atomic, tp_atomic, WARP_LG);
-        __syncwarp();
-
-        Cand best{0u, 0u, 0ull, EMPTY};
-        if (a.strict) {
-            for (int j = lane; j < WARP_TABLE; j += 32) {
-                const int32_t key = tk[j];
-                if (key != EMPTY) {
-                    const Cand c{(uint32_t)ts[j], tp[j], 0ull, key};
-                    if (better(c, best)) best = c;
-                    tk[j] = EMPTY;
-                    ts[j] = 0;
-                    tp[j] = 0;
-                }
-            }
+            label = warp_argmax(identity_best<32>(a, lo, lo, hi, ktv, lane), a.strict).label;
         } else {
-            uint32_t mx = 0;
-            for (int j = lane; j < WARP_TABLE; j += 32)
-                if (tk[j] != EMPTY) mx = max(mx, (uint32_t)ts[j]);
-            mx = __reduce_max_sync(FULL, mx);
-            const uint64_t ktv = stream_at(a.key_t, (uint64_t)x.lv + 1);
-            for (int j = lane; j < WARP_TABLE; j += 32) {
-                const int32_t key = tk[j];
-                if (key != EMPTY) {
-                    if ((uint32_t)ts[j] == mx) {
-                        const Cand c{mx, tp[j], stream_at(ktv, (uint64_t)key + 1), key};
-                        if (better(c, best)) best = c;
+            // a row of at most 32 quads is loaded once, one quad per lane; if
+            // the vertex's own label holds more than half of its weight it stays
+            const int64_t b0 = lo >> 2;
+            const bool one = b_hi - b0 < 32;
+            Quad q1 = empty_quad();
+            bool settled = false;
+            if (one) {
+                if (b0 + lane <= b_hi) q1 = load_quad(a, b0 + lane, lo, hi, x.vb);
+                if (try_majority(a, x.g)) {
+                    // own label first, then the vote's candidate
+                    uint32_t ow = 0, tw = 0;
+                    own_weight(q1, own, ow, tw);
+                    ow = __reduce_add_sync(FULL, ow);
+                    tw = __reduce_add_sync(FULL, tw);
+                    label = own;
+                    settled = 2ull * ow > (unsigned long long)tw;
+                    if (!settled) {
+                        Vote vt;
+                        vote_quad(q1, vt);
+                        vt = warp_vote_state(vt);
+                        if (vt.n && vt.c != own) {
+                            label = vt.c;
+                            if (vote_proven(vt.n, tw)) {
+                                settled = true;
+                            } else if (vote_worth_counting(vt.n, tw)) {
+                                const uint32_t cw =
+                                    __reduce_add_sync(FULL, label_weight(q1, vt.c));
+                                settled = 2ull * cw > (unsigned long long)tw;
+                            }
+                        }
                     }
-                    tk[j] = EMPTY;
-                    ts[j] = 0;
-                    tp[j] = 0;
                 }
             }
+            if (!settled) {
+                // <= 128 labels in 256 slots: every insert finds its slot
+                HotLabel hot;
+                for (int64_t base = b0; base <= b_hi; base += 32) {
+                    const int64_t blk = base + lane;
+                    const Quad q =
+                        one ? q1 : (blk <= b_hi ? load_quad(a, blk, lo, hi, x.vb) : empty_quad());
+                    insert_quad64(q, hot, tab, WARP_LG);
+                }
+                insert_hot64(hot, tab, WARP_LG);
+                __syncwarp();
+                const Top top =
+                    scan64<32>(tab, WARP_TABLE, lane, a.strict, ktv, nullptr, nullptr, nullptr);
+                label = top.label;
+                if (top.cnt > 1u) {  // tied maximum: the earliest entry of a tied label
+                    uint64_t t = one ? tie_quad(q1, b0 + lane, lo, tab, WARP_LG, top, a.strict, ktv)
+                                     : tie_range<32>(a, lo, lo, hi, x.vb, lane, tab, WARP_LG, top,
+                                                     ktv);
+                    uint64_t k = ~t;
+                    uint32_t c = 0u;
+                    int32_t l = EMPTY;
+                    warp_top(k, c, l);
+                    label = (int32_t)(uint32_t)~k;
+                }
+                __syncwarp();
+                clear64<32>(tab, WARP_TABLE, lane);
+                __syncwarp();
+            }
         }
-        best = warp_argmax(best, a.strict);
         if (lane == 0) {
-            a.lab_out[x.v] = best.label;
-            if (best.label != own) {
+            a.lab_out[x.v] = label;
+            if (label != own) {
                 if (MULTI)
                     atomicAdd(a.changed + x.g, 1);
                 else
                     ++my_changed;
             }
         }
-        __syncwarp();
     }
     if (!MULTI && lane == 0 && my_changed) atomicAdd(a.changed, (int)my_changed);
 }
@@ -836,50 +1086,57 @@ __device__ __forceinline__ uint2 block_sum2(uint32_t x, uint32_t y, uint32_t *s)
 // cta bucket: one CTA per vertex, shared table
 // ----------------------------------------------------------------------------
 template <int NT, int CAP, bool MULTI>
-__global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 2048 / NT) k_cta(SweepArgs a)
+__global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 1536 / NT) k_cta(SweepArgs a)
 {
     if (a.stop && *a.stop) return;  // launched past the end of the run
-    extern __shared__ int32_t smem[];
-    int32_t *tk = smem;
-    int32_t *ts = tk + CAP;
-    uint32_t *tp = reinterpret_cast<uint32_t *>(ts + CAP);
+    extern __shared__ unsigned long long smem64[];
+    unsigned long long *tab = smem64;  // CAP 64-bit slots
     __shared__ Cand s_red[NT / 32];
-    __shared__ uint32_t s_u[NT / 32 + 1];
+    __shared__ uint64_t s_k[NT / 32 + 1];
+    __shared__ uint32_t s_c[NT / 32 + 1];
+    __shared__ int32_t s_l[NT / 32 + 1];
     __shared__ uint32_t s_u2[2 * (NT / 32)];
+    __shared__ Vote s_vote[NT / 32 + 1];
     constexpr int LG = (CAP == 1024) ? 10 : (CAP == 2048) ? 11 : (CAP == 4096) ? 12 : (CAP == 8192) ? 13 : 14;
     static_assert((1 << LG) == CAP, "table size");
     // quads per thread that hold a row of CAP / 2 entries starting 16-byte aligned
     constexpr int R = CAP / 2 / (4 * NT) > 0 ? CAP / 2 / (4 * NT) : 1;
 
-    for (int j = threadIdx.x; j < CAP; j += NT) {
-        tk[j] = EMPTY;
-        ts[j] = 0;
-        tp[j] = 0;
-    }
+    clear64<NT>(tab, CAP, threadIdx.x);
     __syncthreads();
     uint32_t my_changed = 0;
 
+    // a single graph whose pre-pass ran in this launch: only the rows it left
+    // (listed in cpos) remain
+    const bool compact = !MULTI && a.cpos && maj_level(a, 0) > 0;
+    const int64_t len = compact ? (int64_t)__ldcg(a.ccount) : a.len;
+    auto position = [&](int64_t i) -> int64_t { return compact ? (int64_t)__ldcg(a.cpos + i) : i; };
     VtxPipe<MULTI> pipe;
-    pipe.fetch(a, blockIdx.x);
-    for (int64_t item = blockIdx.x; item < a.len; item += gridDim.x) {
+    if (blockIdx.x < len) pipe.fetch(a, position(blockIdx.x));
+    for (int64_t i = blockIdx.x; i < len; i += gridDim.x) {
         const Vtx x = pipe.next;
         const bool ok = pipe.next_ok;
         const uint8_t maj = pipe.next_maj;
-        pipe.fetch(a, item + gridDim.x);
+        if (i + gridDim.x < len)
+            pipe.fetch(a, position(i + gridDim.x));
+        else
+            pipe.next_ok = false;
         if (!ok) continue;  // block-uniform
         // the pre-pass of this launch tested the row (and wrote its label if
         // it settled)
-        const bool pre = a.vmaj && try_majority(a, x.g);
-        if (pre && maj) continue;
+        const bool pre = compact || (a.vmaj && maj_level(a, x.g) > 0);
+        if (!compact && pre && maj) continue;
         // slots in use for this vertex: 2^lg >= 2d (d <= CAP / 2 in this bucket)
         const int lg = min(ilog2_ceil(2u * (uint32_t)x.d), LG);
+        const int slots = 1 << lg;
         const uint64_t ktv = stream_at(a.key_t, (uint64_t)x.lv + 1);
         const int64_t end = x.e0 + x.d;
         const int64_t b0 = x.e0 >> 2, b_hi = (end - 1) >> 2;
-        Cand best{0u, 0u, 0ull, x.own};
+        int32_t label = x.own;
         if (a.identity) {
-            best = block_argmax<NT>(identity_best<NT>(a, x.e0, x.e0, end, ktv, threadIdx.x),
-                                    a.strict, s_red);
+            label = block_argmax<NT>(identity_best<NT>(a, x.e0, x.e0, end, ktv, threadIdx.x),
+                                     a.strict, s_red)
+                        .label;  // valid in warp 0
         } else if (b_hi - b0 < (int64_t)R * NT) {
             // the row in registers, R quads per thread
             Quad q[R];
@@ -889,34 +1146,80 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 2048 / NT) k_cta(SweepArgs
                 q[r] = blk <= b_hi ? load_quad(a, blk, x.e0, end, x.vb) : empty_quad();
             }
             // a label holding more than half of the row's weight is the
-            // unique maximum: the vertex keeps its own label if it does
+            // unique maximum: the own label, else the vote's candidate
             bool settled = false;
             if (!pre && try_majority(a, x.g)) {
                 uint32_t ow = 0, tw = 0;
+                Vote vt;
 #pragma unroll
-                for (int r = 0; r < R; ++r) own_weight(q[r], x.own, ow, tw);
+                for (int r = 0; r < R; ++r) {
+                    own_weight(q[r], x.own, ow, tw);
+                    vote_quad(q[r], vt);
+                }
                 const uint2 s2 = block_sum2<NT>(ow, tw, s_u2);
                 settled = 2ull * s2.x > (unsigned long long)s2.y;
+                if (!settled) {
+                    const Vote bv = block_vote<NT>(vt, s_vote);
+                    if (bv.n && bv.c != x.own) {
+                        if (vote_proven(bv.n, s2.y)) {
+                            settled = true;
+                            label = bv.c;
+                        } else if (vote_worth_counting(bv.n, s2.y)) {
+                            uint32_t cw = 0u;
+#pragma unroll
+                            for (int r = 0; r < R; ++r) cw += label_weight(q[r], bv.c);
+                            const uint2 c2 = block_sum2<NT>(cw, 0u, s_u2);
+                            if (2ull * c2.x > (unsigned long long)s2.y) {
+                                settled = true;
+                                label = bv.c;
+                            }
+                        }
+                    }
+                }
             }
             if (!settled) {
                 HotLabel hot;
 #pragma unroll
-                for (int r = 0; r < R; ++r)
-                    insert_quad(q[r], b0 + r * NT + threadIdx.x, x.e0, hot, tk, ts, tp, lg);
-                insert_hot(hot, tk, ts, tp, lg);
+                for (int r = 0; r < R; ++r) insert_quad64(q[r], hot, tab, lg);
+                insert_hot64(hot, tab, lg);
                 __syncthreads();
-                best = block_argmax<NT>(scan_table<NT>(tk, ts, tp, 1 << lg, a.strict, ktv, s_u),
-                                        a.strict, s_red);
+                const Top top = scan64<NT>(tab, slots, threadIdx.x, a.strict, ktv, s_k, s_c, s_l);
+                label = top.label;
+                if (top.cnt > 1u) {  // tied maximum: the earliest entry of a tied label
+                    uint64_t t = ~0ull;
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const uint64_t c = tie_quad(q[r], b0 + r * NT + threadIdx.x, x.e0, tab, lg,
+                                                    top, a.strict, ktv);
+                        t = c < t ? c : t;
+                    }
+                    uint64_t k = ~t;
+                    uint32_t c = 0u;
+                    int32_t l = EMPTY;
+                    block_top<NT>(k, c, l, s_k, s_c, s_l);
+                    label = (int32_t)(uint32_t)~k;
+                }
+                __syncthreads();
+                clear64<NT>(tab, slots, threadIdx.x);
             }
         } else {
-            accumulate_range<NT>(a, x.e0, x.e0, end, x.vb, tk, ts, tp, lg);
+            accumulate_range64<NT>(a, x.e0, end, x.vb, tab, lg);
             __syncthreads();
-            best = block_argmax<NT>(scan_table<NT>(tk, ts, tp, 1 << lg, a.strict, ktv, s_u),
-                                    a.strict, s_red);
+            const Top top = scan64<NT>(tab, slots, threadIdx.x, a.strict, ktv, s_k, s_c, s_l);
+            label = top.label;
+            if (top.cnt > 1u) {
+                uint64_t k = ~tie_range<NT>(a, x.e0, x.e0, end, x.vb, threadIdx.x, tab, lg, top, ktv);
+                uint32_t c = 0u;
+                int32_t l = EMPTY;
+                block_top<NT>(k, c, l, s_k, s_c, s_l);
+                label = (int32_t)(uint32_t)~k;
+            }
+            __syncthreads();
+            clear64<NT>(tab, slots, threadIdx.x);
         }
         if (threadIdx.x == 0) {
-            a.lab_out[x.v] = best.label;
-            if (best.label != x.own) {
+            a.lab_out[x.v] = label;
+            if (label != x.own) {
                 if (MULTI)
                     atomicAdd(a.changed + x.g, 1);
                 else
@@ -931,17 +1234,19 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 2048 / NT) k_cta(SweepArgs
 // ----------------------------------------------------------------------------
 // Majority pre-pass for the rows of the CTA kernels (cta, cta2 and hub rows up
 // to HUB_ONE_MAX entries): one warp per row counts the weight of the entries
-// carrying the row's own label.  A row where that label holds more than half
-// of the weight keeps it (the unique maximum): the label is written here and
-// the row's flag tells the CTA kernel to skip it.  Once labels have settled
-// nearly every such row passes, and a warp reads a row with a fraction of
-// the instructions a CTA spends on it.
+// carrying the row's own label and runs the weighted majority vote.  A label
+// holding more than half of the row's weight is the unique maximum: the own
+// label if it passes, else the vote's candidate once a second read of the
+// row confirms its weight.  The label is written here and the row's flag
+// tells the CTA kernel to skip it.  Once labels have settled nearly every
+// such row passes, and a warp reads a row with a fraction of the
+// instructions a CTA spends on it.
 // ----------------------------------------------------------------------------
 template <bool MULTI>
 __global__ void __launch_bounds__(256) k_major_rows(SweepArgs a)
 {
     if (a.stop && *a.stop) return;  // launched past the end of the run
-    if (!MULTI && !try_majority(a, 0)) return;
+    if (!MULTI && maj_level(a, 0) == 0) return;
     const int lane = threadIdx.x & 31;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -951,18 +1256,70 @@ __global__ void __launch_bounds__(256) k_major_rows(SweepArgs a)
         const Vtx x = pipe.next;
         const bool ok = pipe.next_ok;
         pipe.fetch(a, item + nw);
-        if (!ok || (MULTI && !try_majority(a, x.g))) continue;  // warp-uniform
+        if (!ok) continue;  // warp-uniform
+        const int lvl = maj_level(a, x.g);
+        if (lvl == 0) continue;
         const int64_t lo = x.e0, hi = x.e0 + x.d;
+        const int64_t b_lo = lo >> 2, b_hi = (hi - 1) >> 2;
         uint32_t ow = 0u, tw = 0u;
+        Vote vt;
+        // the first 32 blocks (128 entries); while labels still consolidate
+        // (level 1) a row where neither the own label nor the vote's
+        // candidate leads its prefix is left to the CTA kernel unread
+        if (b_lo + lane <= b_hi) {
+            const Quad q = load_quad(a, b_lo + lane, lo, hi, x.vb);
+            own_weight(q, x.own, ow, tw);
+            vote_quad(q, vt);
+        }
+        bool hopeless = false;
+        if (lvl == 1 && b_hi - b_lo >= 32) {
+            const uint32_t pow_ = __reduce_add_sync(FULL, ow), ptw = __reduce_add_sync(FULL, tw);
+            const Vote pv = warp_vote_state(vt);
+            hopeless = 2ull * pow_ <= (unsigned long long)ptw && 4ull * pv.n < (unsigned long long)ptw;
+        }
+        bool settled = false;
+        int32_t label = x.own;
+        if (!hopeless) {
 #pragma unroll 4
-        for (int64_t blk = (lo >> 2) + lane; blk <= (hi - 1) >> 2; blk += 32)
-            own_weight(load_quad(a, blk, lo, hi, x.vb), x.own, ow, tw);
-        ow = __reduce_add_sync(FULL, ow);  // row sums < 2^31
-        tw = __reduce_add_sync(FULL, tw);
+            for (int64_t blk = b_lo + 32 + lane; blk <= b_hi; blk += 32) {
+                const Quad q = load_quad(a, blk, lo, hi, x.vb);
+                own_weight(q, x.own, ow, tw);
+                vote_quad(q, vt);
+            }
+            ow = __reduce_add_sync(FULL, ow);  // row sums < 2^31
+            tw = __reduce_add_sync(FULL, tw);
+            settled = 2ull * ow > (unsigned long long)tw;
+        }
+        if (!settled && !hopeless) {
+            // the vote's candidate, proven by its surplus or verified by a
+            // second read of the row
+            vt = warp_vote_state(vt);
+            if (vt.n && vt.c != x.own) {
+                label = vt.c;
+                if (vote_proven(vt.n, tw)) {
+                    settled = true;
+                } else if (vote_worth_counting(vt.n, tw)) {
+                    uint32_t cw = 0u;
+#pragma unroll 4
+                    for (int64_t blk = (lo >> 2) + lane; blk <= (hi - 1) >> 2; blk += 32)
+                        cw += label_weight(load_quad(a, blk, lo, hi, x.vb), vt.c);
+                    cw = __reduce_add_sync(FULL, cw);
+                    settled = 2ull * cw > (unsigned long long)tw;
+                }
+            }
+        }
         if (lane == 0) {
-            const bool settled = 2ull * ow > (unsigned long long)tw;
             a.vmaj[x.v] = settled ? 1 : 0;
-            if (settled) a.lab_out[x.v] = x.own;
+            if (!MULTI && !settled && a.cpos) a.cpos[atomicAdd(a.ccount, 1)] = (int32_t)item;
+            if (settled) {
+                a.lab_out[x.v] = label;
+                if (label != x.own) {
+                    if (MULTI)
+                        atomicAdd(a.changed + x.g, 1);
+                    else
+                        atomicAdd(a.changed, 1);
+                }
+            }
         }
     }
 }
@@ -972,6 +1329,8 @@ template <bool MULTI>
 int launch_major(const SweepArgs &a, int num_sms, cudaStream_t st)
 {
     if (!a.vmaj || !a.majority || a.identity || a.len <= 0) return 0;
+    if (!MULTI && a.ccount && cudaMemsetAsync(a.ccount, 0, sizeof(int32_t), st) != cudaSuccess)
+        return -1;
     const int64_t blocks = (a.len + 7) / 8;
     k_major_rows<MULTI><<<(int)(blocks < num_sms * 8 ? blocks : num_sms * 8), 256, 0, st>>>(a);
     return 1;
@@ -1065,41 +1424,151 @@ __device__ __forceinline__ void block_scan_counts(int32_t *c, int n, int32_t *s_
 }
 
 // Majority pre-pass over the segments of the long rows: each segment adds its
-// row's own-label weight and total weight into the row's two counters, so the
-// segment and partition passes can skip rows whose own label holds more than
-// half of the weight (that label is then the row's unique maximum).
+// row's own-label weight and total weight into the row's counters and stores
+// its weighted majority vote, so that the segment and partition passes can
+// skip rows where one label holds more than half of the weight (that label is
+// then the row's unique maximum).  Counters per long-row task (hmaj, 4
+// words): own-label weight, total weight, candidate weight, candidate.
 template <bool MULTI>
 __global__ void __launch_bounds__(HUB_THREADS) k_hub_major(SweepArgs a)
 {
     constexpr int NT = HUB_THREADS;
     if (a.stop && *a.stop) return;  // launched past the end of the run
     __shared__ uint32_t s_sum[2 * (NT / 32)];
+    __shared__ Vote s_vote[NT / 32];
     for (int64_t item = blockIdx.x; item < a.hsegs; item += gridDim.x) {
         const int64_t ti = __ldg(a.hseg_task + item);
         const HubTask t = a.htask[ti];
         Vtx x;
         // a pre-pass costs under a tenth of a high-cardinality segment pass
-        if (!load_vtx<MULTI>(a, t.v, x) || !try_majority(a, x.g)) continue;  // uniform
+        if (!load_task<MULTI>(a, t, x) || !try_majority(a, x.g)) continue;  // uniform
         const int64_t lo = x.e0 + (int64_t)(item - t.seg0) * HUB_SEG;
         const int64_t hi = min(lo + HUB_SEG, x.e0 + x.d);
         uint32_t ow = 0u, tw = 0u;
-        for (int64_t blk = (lo >> 2) + threadIdx.x; blk <= (hi - 1) >> 2; blk += NT)
-            own_weight(load_quad(a, blk, lo, hi, x.vb), x.own, ow, tw);
-        const uint2 s2 = block_sum2<NT>(ow, tw, s_sum);
+        Vote vt;
+        for (int64_t blk = (lo >> 2) + threadIdx.x; blk <= (hi - 1) >> 2; blk += NT) {
+            const Quad q = load_quad(a, blk, lo, hi, x.vb);
+            own_weight(q, x.own, ow, tw);
+            vote_quad(q, vt);
+        }
+        vt = warp_vote_state(vt);
+        if ((threadIdx.x & 31) == 0) s_vote[threadIdx.x >> 5] = vt;
+        const uint2 s2 = block_sum2<NT>(ow, tw, s_sum);  // its barriers publish s_vote
         if (threadIdx.x == 0) {
-            atomicAdd(a.hmaj + 2 * ti, s2.x);
-            atomicAdd(a.hmaj + 2 * ti + 1, s2.y);
+            Vote m;
+            for (int k = 0; k < NT / 32; ++k) m = vote_merge(m, s_vote[k]);
+            a.hvote[item] = make_int2(m.c, (int32_t)m.n);
+            atomicAdd(a.hmaj + 4 * ti, s2.x);
+            atomicAdd(a.hmaj + 4 * ti + 1, s2.y);
         }
     }
 }
 
-// whether the long row of task ti keeps its own label (pre-pass counters)
+// Second pre-pass over the segments of the long rows whose own label failed:
+// the row's candidate (its segments' votes merged in segment order, the same
+// in every segment) has its weight counted segment by segment.
 template <bool MULTI>
-__device__ __forceinline__ bool hub_settled(const SweepArgs &a, int64_t ti, int32_t g)
+__global__ void __launch_bounds__(HUB_THREADS) k_hub_candw(SweepArgs a)
 {
-    if (!a.hmaj || !try_majority(a, g)) return false;
-    const uint32_t own = __ldcg(a.hmaj + 2 * ti), tot = __ldcg(a.hmaj + 2 * ti + 1);
-    return 2ull * own > (unsigned long long)tot;
+    constexpr int NT = HUB_THREADS;
+    if (a.stop && *a.stop) return;  // launched past the end of the run
+    __shared__ uint32_t s_sum[2 * (NT / 32)];
+    __shared__ int32_t s_c;
+    for (int64_t item = blockIdx.x; item < a.hsegs; item += gridDim.x) {
+        const int64_t ti = __ldg(a.hseg_task + item);
+        const HubTask t = a.htask[ti];
+        Vtx x;
+        if (!load_task<MULTI>(a, t, x) || !try_majority(a, x.g)) continue;  // uniform
+        const uint32_t ow = __ldcg(a.hmaj + 4 * ti), tot = __ldcg(a.hmaj + 4 * ti + 1);
+        if (2ull * ow > (unsigned long long)tot) continue;  // the own label holds
+        if (threadIdx.x == 0) {
+            Vote m;
+            for (int k = 0; k < t.nseg; ++k) {
+                const int2 v = __ldcg(a.hvote + t.seg0 + k);
+                m = vote_merge(m, Vote{v.x, (uint32_t)v.y});
+            }
+            s_c = m.n && m.c != x.own && vote_worth_counting(m.n, tot) ? m.c : EMPTY;
+            if (s_c != EMPTY && vote_proven(m.n, tot)) {
+                // proven by its surplus: the first segment records it, the
+                // others count nothing
+                if (item == t.seg0) {
+                    a.hmaj[4 * ti + 2] = tot;
+                    a.hmaj[4 * ti + 3] = (uint32_t)m.c;
+                }
+                s_c = EMPTY;
+            }
+        }
+        __syncthreads();
+        const int32_t c = s_c;
+        __syncthreads();
+        if (c == EMPTY) continue;  // uniform
+        const int64_t lo = x.e0 + (int64_t)(item - t.seg0) * HUB_SEG;
+        const int64_t hi = min(lo + HUB_SEG, x.e0 + x.d);
+        uint32_t cw = 0u;
+        for (int64_t blk = (lo >> 2) + threadIdx.x; blk <= (hi - 1) >> 2; blk += NT)
+            cw += label_weight(load_quad(a, blk, lo, hi, x.vb), c);
+        const uint2 s2 = block_sum2<NT>(cw, 0u, s_sum);
+        if (threadIdx.x == 0) {
+            atomicAdd(a.hmaj + 4 * ti + 2, s2.x);
+            if (item == t.seg0) a.hmaj[4 * ti + 3] = (uint32_t)c;
+        }
+    }
+}
+
+// the label of the long row of task ti if one label holds more than half of
+// its weight (pre-pass counters), else EMPTY
+template <bool MULTI>
+__device__ __forceinline__ int32_t hub_settled(const SweepArgs &a, int64_t ti, int32_t g,
+                                               int32_t own)
+{
+    if (!a.hmaj || !try_majority(a, g)) return EMPTY;
+    const uint32_t *h = a.hmaj + 4 * ti;
+    const uint32_t ow = __ldcg(h), tot = __ldcg(h + 1);
+    if (2ull * ow > (unsigned long long)tot) return own;
+    if (2ull * __ldcg(h + 2) > (unsigned long long)tot) return (int32_t)__ldcg(h + 3);
+    return EMPTY;
+}
+
+// Long rows that one label holds by majority take that label here (and
+// count as changed if it differs); *open receives the number of the other
+// long rows, and the segment and partition passes return at once when there
+// is none.  One block.
+template <bool MULTI>
+__global__ void __launch_bounds__(1024) k_hub_open(SweepArgs a, int32_t *open)
+{
+    if (a.stop && *a.stop) return;  // launched past the end of the run
+    __shared__ int32_t s_n, s_ch;
+    if (threadIdx.x == 0) s_n = s_ch = 0;
+    __syncthreads();
+    int32_t k = 0, ch = 0;
+    for (int64_t ti = threadIdx.x; ti < a.hmulti; ti += blockDim.x) {
+        const HubTask t = a.htask[ti];
+        Vtx x;
+        if (!load_task<MULTI>(a, t, x)) continue;
+        const int32_t maj = hub_settled<MULTI>(a, ti, x.g, x.own);
+        if (maj == EMPTY) {
+            ++k;
+            continue;
+        }
+        a.lab_out[x.v] = maj;
+        if (maj != x.own) {
+            if (MULTI)
+                atomicAdd(a.changed + x.g, 1);
+            else
+                ++ch;
+        }
+    }
+    k = (int32_t)__reduce_add_sync(FULL, (uint32_t)k);
+    ch = (int32_t)__reduce_add_sync(FULL, (uint32_t)ch);
+    if ((threadIdx.x & 31) == 0) {
+        if (k) atomicAdd(&s_n, k);
+        if (ch) atomicAdd(&s_ch, ch);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (open) *open = s_n;
+        if (!MULTI && s_ch) atomicAdd(a.changed, s_ch);
+    }
 }
 
 // Segment pass: a segment's entries are aggregated in the shared table and
@@ -1110,6 +1579,7 @@ template <bool MULTI>
 __global__ void __launch_bounds__(HUB_THREADS, 2) k_hub_seg(SweepArgs a)
 {
     if (a.stop && *a.stop) return;  // launched past the end of the run
+    if (a.hmaj && a.hopen && *a.hopen == 0) return;  // every long row is settled
     constexpr int NT = HUB_THREADS;
     constexpr int LG = 13;
     static_assert((1 << LG) == HUB_TABLE && HUB_TABLE >= 2 * HUB_SEG, "hub table size");
@@ -1131,14 +1601,14 @@ __global__ void __launch_bounds__(HUB_THREADS, 2) k_hub_seg(SweepArgs a)
         const int64_t ti = __ldg(a.hseg_task + item);
         const HubTask t = a.htask[ti];
         Vtx x;
-        if (!load_vtx<MULTI>(a, t.v, x)) continue;  // block-uniform
+        if (!load_task<MULTI>(a, t, x)) continue;  // block-uniform
         const int seg = (int)(item - t.seg0);
         const int64_t lo = x.e0 + (int64_t)seg * HUB_SEG;
         const int64_t hi = min(lo + HUB_SEG, x.e0 + x.d);
         const int np = t.npart;
         int4 *out = a.hrec + item * HUB_SEG;
         int32_t *poff = a.hpoff + t.poff0 + (int64_t)seg * (np + 1);
-        if (hub_settled<MULTI>(a, ti, x.g)) {  // no records
+        if (hub_settled<MULTI>(a, ti, x.g, x.own) != EMPTY) {  // no records
             for (int q = threadIdx.x; q <= np; q += NT) poff[q] = 0;
             continue;
         }
@@ -1188,6 +1658,7 @@ template <bool MULTI>
 __global__ void __launch_bounds__(HUB_THREADS, 2) k_hub_merge(SweepArgs a)
 {
     if (a.stop && *a.stop) return;  // launched past the end of the run
+    if (a.hmaj && a.hopen && *a.hopen == 0) return;  // every long row is settled
     constexpr int NT = HUB_THREADS;
     constexpr int LG = 13;
     constexpr int PROBE = 256;
@@ -1213,13 +1684,11 @@ __global__ void __launch_bounds__(HUB_THREADS, 2) k_hub_merge(SweepArgs a)
         const int64_t ti = __ldg(a.hpart_task + item);
         const HubTask t = a.htask[ti];
         Vtx x;
-        if (!load_vtx<MULTI>(a, t.v, x)) continue;  // block-uniform
+        if (!load_task<MULTI>(a, t, x)) continue;  // block-uniform
         const int p = (int)(item - t.part0);
         const int np = t.npart;
-        if (hub_settled<MULTI>(a, ti, x.g)) {  // the row keeps its own label
-            if (p == 0 && threadIdx.x == 0) a.lab_out[x.v] = x.own;
-            continue;
-        }
+        // a row that one label holds by majority took it in k_hub_open
+        if (hub_settled<MULTI>(a, ti, x.g, x.own) != EMPTY) continue;
         const uint64_t ktv = stream_at(a.key_t, (uint64_t)x.lv + 1);
         const int glg = ilog2_ceil(2u * (uint32_t)x.d);
         unsigned long long *gk = a.hkey + t.tab;
@@ -1299,12 +1768,13 @@ __global__ void __launch_bounds__(HUB_THREADS, 2) k_hub_merge(SweepArgs a)
 template <bool MULTI>
 int launch(int bucket, const SweepArgs &a, int num_sms, cudaStream_t st)
 {
-    constexpr size_t cta_smem = (size_t)CTA_TABLE * 12;
-    constexpr size_t cta2_smem = (size_t)CTA2_TABLE * 12;
+    constexpr size_t cta_smem = (size_t)CTA_TABLE * 8;
+    constexpr size_t cta2_smem = (size_t)CTA2_TABLE * 8;
+    constexpr size_t hubcta_smem = (size_t)HUB_TABLE * 8;
     constexpr size_t hub_smem = (size_t)HUB_TABLE * 12;
     if (a.len <= 0) return 0;
     int64_t blocks = 0;
-    int n = 1;
+    int n = 1, m = 0;
     switch (bucket) {
     case 0: {
         SweepArgs b = a;
@@ -1319,13 +1789,15 @@ int launch(int bucket, const SweepArgs &a, int num_sms, cudaStream_t st)
         break;
     case 2:
         blocks = a.len;
-        n += launch_major<MULTI>(a, num_sms, st);
+        if ((m = launch_major<MULTI>(a, num_sms, st)) < 0) return -1;
+        n += m;
         k_cta<CTA_THREADS, CTA_TABLE, MULTI>
             <<<(int)(blocks < num_sms * 16 ? blocks : num_sms * 16), CTA_THREADS, cta_smem, st>>>(a);
         break;
     case 3:
         blocks = a.len;
-        n += launch_major<MULTI>(a, num_sms, st);
+        if ((m = launch_major<MULTI>(a, num_sms, st)) < 0) return -1;
+        n += m;
         k_cta<CTA2_THREADS, CTA2_TABLE, MULTI>
             <<<(int)(blocks < num_sms * 8 ? blocks : num_sms * 8), CTA2_THREADS, cta2_smem, st>>>(a);
         break;
@@ -1335,11 +1807,15 @@ int launch(int bucket, const SweepArgs &a, int num_sms, cudaStream_t st)
             const int64_t cap = (int64_t)num_sms * 2;
             SweepArgs h = a;
             if (a.majority && !a.identity && a.hmaj) {
-                if (cudaMemsetAsync(a.hmaj, 0, (size_t)a.hmulti * 2 * sizeof(uint32_t), st) !=
+                if (cudaMemsetAsync(a.hmaj, 0, (size_t)a.hmulti * 4 * sizeof(uint32_t), st) !=
                     cudaSuccess)
                     return -1;
                 k_hub_major<MULTI>
                     <<<(int)(a.hsegs < cap * 2 ? a.hsegs : cap * 2), HUB_THREADS, 0, st>>>(a);
+                k_hub_candw<MULTI>
+                    <<<(int)(a.hsegs < cap * 2 ? a.hsegs : cap * 2), HUB_THREADS, 0, st>>>(a);
+                n += 2;
+                k_hub_open<MULTI><<<1, 1024, 0, st>>>(a, a.hopen);  // writes settled labels
                 ++n;
             } else {
                 h.hmaj = nullptr;
@@ -1352,10 +1828,12 @@ int launch(int bucket, const SweepArgs &a, int num_sms, cudaStream_t st)
         if (a.len > a.hmulti) {  // the other hub rows: one CTA each
             SweepArgs b = a;
             b.list = a.list + a.hmulti;
+            b.rp = a.rp + a.hmulti;
             b.len = a.len - a.hmulti;
             blocks = b.len < (int64_t)num_sms * 2 ? b.len : (int64_t)num_sms * 2;
-            n += launch_major<MULTI>(b, num_sms, st);
-            k_cta<HUB_THREADS, HUB_TABLE, MULTI><<<(int)blocks, HUB_THREADS, hub_smem, st>>>(b);
+            if ((m = launch_major<MULTI>(b, num_sms, st)) < 0) return -1;
+            n += m;
+            k_cta<HUB_THREADS, HUB_TABLE, MULTI><<<(int)blocks, HUB_THREADS, hubcta_smem, st>>>(b);
             ++n;
         }
         break;
@@ -1369,15 +1847,15 @@ int prepare()
 {
     if (cudaFuncSetAttribute(k_cta<CTA_THREADS, CTA_TABLE, MULTI>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)((size_t)CTA_TABLE * 12)) != cudaSuccess)
+                             (int)((size_t)CTA_TABLE * 8)) != cudaSuccess)
         return -1;
     if (cudaFuncSetAttribute(k_cta<CTA2_THREADS, CTA2_TABLE, MULTI>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)((size_t)CTA2_TABLE * 12)) != cudaSuccess)
+                             (int)((size_t)CTA2_TABLE * 8)) != cudaSuccess)
         return -1;
     if (cudaFuncSetAttribute(k_cta<HUB_THREADS, HUB_TABLE, MULTI>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)((size_t)HUB_TABLE * 12)) != cudaSuccess)
+                             (int)((size_t)HUB_TABLE * 8)) != cudaSuccess)
         return -1;
     if (cudaFuncSetAttribute(k_hub_seg<MULTI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)((size_t)HUB_TABLE * 12)) != cudaSuccess)
