@@ -16,10 +16,15 @@ Workloads (synthetic stand-ins for the paper's SuiteSparse classes):
   batch     4096 planted-partition graphs (n log-uniform 1k-200k, 5-500 blocks,
             mean degree 8-32, mixing 0.3) in one arena, synchronous; metric
             graphs/s, compared with the same graphs run one at a time
-  serve     Poisson request stream (mean 200 req/s) of SBM / R-MAT / grid
-            graphs (n log-uniform 10k-2M, weights 1-8) drawn from a pool,
-            served with continuous batching; graphs/s and p50/p99 latency,
-            compared with the same arrivals served one graph at a time
+  serve     Poisson request stream (mean 200 req/s, 60 s) of SBM / R-MAT /
+            grid graphs (n log-uniform 10k-2M, weights 1-8) drawn from a pool
+            of 96 distinct graphs, served with continuous batching; graphs/s
+            and p50/p99 latency, compared with the same arrivals served one
+            graph at a time
+
+The default run (rmat22) also measures the batched and served configurations
+and adds them as the ``batch`` and ``serve`` sub-records (``--no-batch`` /
+``--no-serve`` leave them out).
 
 Extra keys: ``roofline`` (dominant sweep kernel vs measured HBM bandwidth),
 ``sweep`` (all sweep kernels of one iteration vs the same peak), ``e2e``
@@ -38,8 +43,11 @@ one JSON line per setting (iterations, convergence, run time, GTEPS,
 modularity of the labels on the graph without self-loops).
 ``--experiment split`` times the split of disconnected communities after
 each class's benchmark run (communities and modularity before and after).
-Multi-GPU (torchrun): every rank runs its own replica of the workload;
-``value`` = entries traversed by all ranks / the slowest rank's time.
+Multi-GPU (torchrun): on a single graph every rank runs its own replica;
+the batch and the serving stream shard whole graphs over the ranks
+(size-balanced; requests r, r + N, ... to rank r) with no collective on the
+data path, and per-graph results are gathered on rank 0.  ``value`` = the
+work of all ranks / the slowest rank's time.
 """
 from __future__ import annotations
 
@@ -92,13 +100,17 @@ def parse():
     ap.add_argument("--cpu-sweeps", type=int, default=4,
                     help="oracle sweeps in the CPU baseline sample")
     ap.add_argument("--batch-count", type=int, default=4096, help="graphs of the batch workload")
-    ap.add_argument("--serve-seconds", type=float, default=20.0, help="arrival window (serve)")
+    ap.add_argument("--serve-seconds", type=float, default=60.0, help="arrival window (serve)")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="mean arrivals per second")
     ap.add_argument("--serve-saturation", type=int, default=512,
                     help="requests of the burst that measures service capacity")
-    ap.add_argument("--serve-pool", type=int, default=48, help="distinct graphs in the pool")
-    ap.add_argument("--serve-baseline-seconds", type=float, default=5.0,
+    ap.add_argument("--serve-pool", type=int, default=96, help="distinct graphs in the pool")
+    ap.add_argument("--serve-baseline-seconds", type=float, default=10.0,
                     help="arrival window replayed one graph at a time")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="single-graph workloads: leave out the batch sub-record")
+    ap.add_argument("--no-serve", action="store_true",
+                    help="single-graph workloads: leave out the serve sub-record")
     ap.add_argument("--per-graph-sample", type=int, default=256,
                     help="graphs of the batch timed one at a time")
     ap.add_argument("--experiment", choices=["tolerance", "split"], default=None,
@@ -153,7 +165,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={gpu_id}", f"--query-gpu={self.QUERY}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
@@ -208,6 +220,37 @@ def reduce_across_ranks(t_ms, entries, device=None):
     return float(t.item()), float(e.item())
 
 
+def shard_graphs(sizes, rank, world):
+    """Indices of the graphs rank `rank` of `world` takes: whole graphs, in
+    decreasing size each to the rank with the least work so far (ties to the
+    lowest rank), listed in increasing index order."""
+    load = [0] * world
+    mine = []
+    for i in sorted(range(len(sizes)), key=lambda i: (-sizes[i], i)):
+        r = min(range(world), key=lambda k: (load[k], k))
+        load[r] += sizes[i]
+        if r == rank:
+            mine.append(i)
+    return sorted(mine)
+
+
+def gather_results(local, world):
+    """Per-graph results of every rank merged into one dict (index -> result),
+    on every rank; the identity without a process group."""
+    if world == 1:
+        return dict(local)
+    import torch.distributed as dist
+
+    parts = [None] * world
+    dist.all_gather_object(parts, dict(local))
+    merged = {}
+    for part in parts:
+        for k, v in part.items():
+            assert k not in merged, f"graph {k} was run on two ranks"
+            merged[k] = v
+    return merged
+
+
 def sweep_sources_hash():
     """First 16 hex digits of the SHA-256 of the sweep kernel sources."""
     import hashlib
@@ -245,12 +288,10 @@ def gen_graph(name):
 
 
 def alg_bytes_per_sweep(g):
-    """Algorithmic HBM bytes of one sweep over the whole graph: row pointer,
-    own label read and label write per non-isolated vertex, column index (and
-    weight) per entry."""
-    deg = np.diff(g.offsets)
-    nz = int(np.count_nonzero(deg))
-    return 12 * nz + (8 if g.weights is not None else 4) * g.m
+    """Algorithmic HBM bytes of one sweep over the whole graph: the row
+    pointer array (4 (n + 1)), the own label read and the label write (4 n
+    each), over every vertex, and the column index (and weight) per entry."""
+    return 4 * (g.n + 1) + 8 * g.n + (8 if g.weights is not None else 4) * g.m
 
 
 # --------------------------------------------------------------------------
@@ -515,6 +556,16 @@ def run_ours(args):
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(g, p, args.cpu_sweeps)
 
+    # the batched and served configurations, measured after the headline
+    if args.workload == "rmat22" and not (args.no_batch and args.no_serve):
+        del off, idx, w
+        torch.cuda.empty_cache()
+        ctx = Ctx(torch, lp, dev, rank, world, local)
+        if not args.no_batch:
+            line["batch"] = measure_batch(args, ctx, sub=True)
+        if not args.no_serve:
+            line["serve"] = measure_serve(args, ctx)
+
     if world > 1:
         import torch.distributed as dist
 
@@ -534,7 +585,23 @@ def batch_graphs(count):
     return gg.batch_sbm(gg.batch_sbm_params(count=count, seed=1000))
 
 
-def run_batch(args):
+class Ctx:
+    """What a measurement needs from the process set-up."""
+
+    def __init__(self, torch, lp, dev, rank, world, local):
+        self.torch, self.lp, self.dev = torch, lp, dev
+        self.rank, self.world, self.local = rank, world, local
+        self.stream = torch.cuda.current_stream(dev)
+
+    def barrier(self):
+        if self.world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+        self.torch.cuda.synchronize()
+
+
+def setup_ctx():
     import torch
 
     import paper_2301_09125_gb300 as lp
@@ -551,66 +618,83 @@ def run_batch(args):
     dev = torch.device("cuda", torch.cuda.current_device())
     build.build()
     lp.load()
-    p = workload_params(args)
+    return Ctx(torch, lp, dev, rank, world, local)
+
+
+def finish_ctx(ctx):
+    if ctx.world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def measure_batch(args, ctx, sub=False):
+    """The batch workload: graphs shard whole over the ranks (size-balanced),
+    each rank runs its share as one arena; value = graphs of all ranks / the
+    slowest rank's time.  sub: the reduced form embedded in the single-graph
+    line (3 timed steps, 128 graphs one at a time, one end-to-end step)."""
+    torch, lp = ctx.torch, ctx.lp
+    p = dict(WORKLOADS["batch"])
     count = args.batch_count
+    steps = min(args.steps, 3) if sub else args.steps
+    warmup = 1 if sub else args.warmup
+    import graphgen as gg
+
     t0 = time.perf_counter()
-    graphs = batch_graphs(count)
+    params_all = gg.batch_sbm_params(count=count, seed=1000)
+    sizes = [q["n"] * q["avg_degree"] for q in params_all]
+    mine = shard_graphs(sizes, ctx.rank, ctx.world)
+    graphs = [gg.sbm_mixing(params_all[i]["n"], params_all[i]["k"], params_all[i]["avg_degree"],
+                            params_all[i]["mu"], seed=params_all[i]["seed"]) for i in mine]
     gen_s = time.perf_counter() - t0
     n_tot = sum(g.n for g in graphs)
     m_tot = sum(g.m for g in graphs)
-    stream = torch.cuda.current_stream(dev)
+    stream = ctx.stream
     triples = [(g.offsets, g.indices, g.weights) for g in graphs]
     params, _ = lp.make_params(tolerance=p["tolerance"], max_iter=p["max_iter"], mode=p["mode"],
                                strict=p["strict"], waves=p["waves"])
-
     h = lp.lp_batch_create(triples, stream=stream.cuda_stream)
-
-    # bucket bounds picked by the autotuner (outside the timed region)
     t0 = time.perf_counter()
-    tune = lp.lp_batch_autotune(h, params, sweeps=5)
+    tune = lp.lp_batch_autotune(h, params, sweeps=5)  # outside the timed region
     tune_s = time.perf_counter() - t0
 
     def step():
-        res = lp.lp_batch_run(h, count, params)
+        res = lp.lp_batch_run(h, len(graphs), params)
         lp.lp_batch_modularity(h, 0)  # computes every graph's modularity
         return res
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
-
-    def barrier():
-        if world > 1:
-            import torch.distributed as dist
-
-            dist.barrier()
-        torch.cuda.synchronize()
-
-    clocks = ClockSampler(nvsmi_id(torch, local), enabled=not args.no_clocks)
+    clocks = ClockSampler(nvsmi_id(torch, ctx.local), enabled=not args.no_clocks)
     launches0 = lp.lp_launch_count()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    barrier()
+    ctx.barrier()
     e0.record(stream)
     iters_entries = 0
-    for _ in range(args.steps):
+    for _ in range(steps):
         res = step()  # the batch's run is one CUDA graph launch
         iters_entries += sum(r.iterations * g.m for r, g in zip(res, graphs))
     e1.record(stream)
-    barrier()
+    ctx.barrier()
     launches = lp.lp_launch_count() - launches0
     clock_info = clocks.stop()
     t_ms = e0.elapsed_time(e1)
-    # profiled step: CUDA events around every sweep launch
+    local_res = {i: (res[j].iterations, int(res[j].converged), lp.lp_batch_modularity(h, j))
+                 for j, i in enumerate(mine)}
     lp.lp_profile_reset()
     lp.lp_profile_enable(True)
     step()
     torch.cuda.synchronize()
     lp.lp_profile_enable(False)
     prof = lp.lp_profile_read()
-    t_ms, graphs_all = reduce_across_ranks(t_ms, count * args.steps, device=dev)
+    t_ms, graphs_all = reduce_across_ranks(t_ms, len(graphs) * steps, device=ctx.dev)
+    _, entries_all = reduce_across_ranks(0.0, iters_entries, device=ctx.dev)
     value = graphs_all / (t_ms * 1e-3)
-    gteps = iters_entries * world / (t_ms * 1e-3) / 1e9
+    gteps = entries_all / (t_ms * 1e-3) / 1e9
     lp.lp_batch_destroy(h)
+    assembled = gather_results(local_res, ctx.world)
 
     # e2e: every step creates the batch from pinned host buffers (host-to-device
     # copies and ingest inside the timed region), runs it, and reads every
@@ -640,45 +724,48 @@ def run_batch(args):
 
         def e2e_step():
             hb = lp.lp_batch_create(host_triples, stream=stream.cuda_stream)
-            lp.lp_batch_run(hb, count, params)
+            lp.lp_batch_run(hb, len(graphs), params)
             lp.lp_batch_modularity(hb, 0)  # every graph's, read back to the host
             lp.lp_batch_destroy(hb)
 
-        e2e_step()
-        barrier()
-        e2e_steps = min(args.steps, 3)
+        if not sub:
+            e2e_step()
+        ctx.barrier()
+        e2e_steps = 1 if sub else min(steps, 3)
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
             e2e_step()
-        barrier()
-        e2e_s = (time.perf_counter() - t0) / e2e_steps
-        e2e = {"value": count * world / e2e_s, "unit": "graphs/s",
-               "h2d_bytes_per_step": int(4 * total), "d2h_bytes_per_step": int(32 * count),
+        ctx.barrier()
+        e2e_s, _ = reduce_across_ranks((time.perf_counter() - t0) / e2e_steps, 0,
+                                       device=ctx.dev)
+        e2e = {"value": count / e2e_s, "unit": "graphs/s",
+               "h2d_bytes_per_step": int(4 * total), "d2h_bytes_per_step": int(32 * len(graphs)),
                "steps": e2e_steps,
                "how": f"lp_batch_create from {host_kind} host buffers + one run + every "
                       "graph's modularity back on the host"}
         del flat, flat_t, host_triples
 
     # the same graphs one at a time: device-resident CSR, create + run + modularity
-    sample = list(range(0, count, max(1, count // args.per_graph_sample)))
-    dev_csr = [tuple(None if a is None else torch.from_numpy(a).to(dev) for a in triples[i])
+    n_sample = 128 if sub else args.per_graph_sample
+    sample = list(range(0, len(graphs), max(1, len(graphs) // n_sample)))
+    dev_csr = [tuple(None if a is None else torch.from_numpy(a).to(ctx.dev) for a in triples[i])
                for i in sample]
-    for i in sample[:3]:
-        hh = lp.lp_graph_create(*dev_csr[sample.index(i)], borrow=True, stream=stream.cuda_stream)
+    for j in range(min(3, len(sample))):
+        hh = lp.lp_graph_create(*dev_csr[j], borrow=True, stream=stream.cuda_stream)
         lp.lp_rak_run(hh, params)
         lp.lp_graph_destroy(hh)
     torch.cuda.synchronize()
     lat = []
     t0 = time.perf_counter()
-    for j, i in enumerate(sample):
+    for j in range(len(sample)):
         s0 = time.perf_counter()
         hh = lp.lp_graph_create(*dev_csr[j], borrow=True, stream=stream.cuda_stream)
         lp.lp_rak_run(hh, params)
         lp.lp_modularity(hh)
         lp.lp_graph_destroy(hh)
         lat.append(time.perf_counter() - s0)
-    per_graph_s = time.perf_counter() - t0
-    per_graph_gps = len(sample) / per_graph_s
+    per_graph_gps = len(sample) / (time.perf_counter() - t0)
+    del dev_csr
 
     peak, peak_kind = measured_peak_gbs()
     kern = {k: v for k, v in prof.items() if v["launches"] > 0}
@@ -688,23 +775,26 @@ def run_batch(args):
     sweep_ms = sum(v["total_ms"] for v in kern.values())
     line = {
         "metric": f"batched graphs/s ({count} SBM graphs)", "value": value, "unit": "graphs/s",
-        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "n_gpus": ctx.world, "steps": steps, "warmup": warmup,
+        "ms_per_step": t_ms / steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": "batch", "graphs": count, "n_total": n_tot, "m_total": m_tot, **p,
+        "config": {"workload": "batch", "graphs": count, "graphs_this_rank": len(graphs),
+                   "n_this_rank": n_tot, "m_this_rank": m_tot, **p,
                    "step": "lp_batch_run (all graphs, per-graph convergence on the device, one "
                            "CUDA graph launch) + modularity of every graph, arena resident in "
                            "HBM",
                    "l2": "inputs larger than L2", "generation_s": round(gen_s, 1),
                    "autotune": {**tune.as_dict(), "seconds": round(tune_s, 2)},
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+                   "parallelism": (f"graph-level sharding over {ctx.world} ranks (size-balanced)"
+                                   if ctx.world > 1 else "single GPU")},
         "gteps": gteps,
+        "assembled_graphs": len(assembled),
         "per_graph_launch": {"graphs_per_s": per_graph_gps, "sample": len(sample),
                              "p50_ms": 1e3 * statistics.median(lat),
                              "p99_ms": 1e3 * float(np.percentile(lat, 99)),
                              "how": "lp_graph_create (borrowed device CSR) + lp_rak_run + "
-                                    "lp_modularity per graph, sequentially"},
-        "speedup_vs_per_graph": value / per_graph_gps,
+                                    "lp_modularity per graph, sequentially, this rank's graphs"},
+        "speedup_vs_per_graph": value / ctx.world / per_graph_gps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None, "kernel": dom_name,
                      "peak_source": peak_kind},
@@ -714,7 +804,7 @@ def run_batch(args):
         "clocks": clock_info,
         "e2e": e2e,
     }
-    if rank == 0 and not args.no_cpu_baseline:
+    if ctx.rank == 0 and not sub and not args.no_cpu_baseline:
         import oracle
 
         oracle.build()
@@ -731,12 +821,14 @@ def run_batch(args):
         line["cpu_baseline"] = {"value": done / t, "unit": "graphs/s", "cores": 1,
                                 "kind": "oracle",
                                 "sample": f"{done} graphs of the batch (every 64th), full runs"}
-    if world > 1:
-        import torch.distributed as dist
+    return line
 
-        dist.barrier()
-        dist.destroy_process_group()
-    if rank == 0:
+
+def run_batch(args):
+    ctx = setup_ctx()
+    line = measure_batch(args, ctx)
+    finish_ctx(ctx)
+    if ctx.rank == 0:
         print(json.dumps(line), flush=True)
     return 0
 
@@ -767,26 +859,23 @@ def serve_pool(count, seed=7):
     return out
 
 
-def run_serve(args):
-    import torch
-
-    import paper_2301_09125_gb300 as lp
-    from paper_2301_09125_gb300 import build
-
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local if world > 1 else 0)
-    build.build()
-    lp.load()
-    p = workload_params(args)
+def measure_serve(args, ctx):
+    """The serving workload: a Poisson stream of requests drawn from a pool of
+    distinct graphs, served with continuous batching; under torchrun rank r
+    serves the requests r, r + N, ... on its own GPU (graph-level sharding)
+    and the latencies of every rank are pooled."""
+    torch, lp = ctx.torch, ctx.lp
+    p = dict(WORKLOADS["serve"])
     t0 = time.perf_counter()
     pool = serve_pool(args.serve_pool)
     gen_s = time.perf_counter() - t0
     pinned = [tuple(torch.from_numpy(a).pin_memory() for a in (g.offsets, g.indices, g.weights))
               for g in pool]
     rng = np.random.default_rng(11)
-    n_req = int(rng.poisson(args.serve_rate * args.serve_seconds))
-    arrivals = np.sort(rng.uniform(0, args.serve_seconds, n_req))
-    picks = rng.integers(0, len(pool), n_req)
+    n_all = int(rng.poisson(args.serve_rate * args.serve_seconds))
+    arrivals_all = np.sort(rng.uniform(0, args.serve_seconds, n_all))
+    picks_all = rng.integers(0, len(pool), n_all)
+    mine = [rid for rid in range(n_all) if rid % ctx.world == ctx.rank]
     params, _ = lp.make_params(tolerance=p["tolerance"], max_iter=p["max_iter"], mode=p["mode"],
                                strict=p["strict"], waves=p["waves"])
     cfg = lp.lp_server_config_default()
@@ -801,46 +890,50 @@ def run_serve(args):
     lp.lp_server_drain(srv)
     lp.lp_server_poll(srv, capacity=len(pool))
 
+    ctx.barrier()
     launches0 = lp.lp_launch_count()
-    clocks = ClockSampler(nvsmi_id(torch, local), enabled=not args.no_clocks)
+    clocks = ClockSampler(nvsmi_id(torch, ctx.local), enabled=not args.no_clocks)
     outs, done = {}, []
     start = time.perf_counter()
-    for rid in range(n_req):
-        delay = start + arrivals[rid] - time.perf_counter()
+    for rid in mine:
+        delay = start + arrivals_all[rid] - time.perf_counter()
         if delay > 0:
             time.sleep(delay)
-        o, x, w = pinned[picks[rid]]
-        outs[rid] = np.empty(pool[picks[rid]].n, np.int32)
+        o, x, w = pinned[picks_all[rid]]
+        outs[rid] = np.empty(pool[picks_all[rid]].n, np.int32)
         lp.lp_server_submit(srv, rid, o, x, w, outs[rid])
         for r in lp.lp_server_poll(srv, capacity=256):
             done.append(r)
             outs.pop(r.request_id, None)
     lp.lp_server_drain(srv)
-    done += lp.lp_server_poll(srv, capacity=n_req + 1)
+    done += lp.lp_server_poll(srv, capacity=len(mine) + 1)
     makespan = time.perf_counter() - start
     clock_info = clocks.stop()
     launches = lp.lp_launch_count() - launches0
     lp.lp_server_destroy(srv)
-    lat = np.array([r.latency_ms for r in done])
-    queued = np.array([r.queued_ms for r in done])
-    errors = sum(1 for r in done if r.status != 0)
-    entries = sum(r.iterations * pool[picks[r.request_id]].m for r in done)
+    local = {r.request_id: (r.latency_ms, r.queued_ms, r.status, r.iterations) for r in done}
+    merged = gather_results(local, ctx.world)
+    makespan, _ = reduce_across_ranks(makespan, 0, device=ctx.dev)
+    lat = np.array([v[0] for v in merged.values()])
+    queued = np.array([v[1] for v in merged.values()])
+    errors = sum(1 for v in merged.values() if v[2] != 0)
+    entries = sum(v[3] * pool[picks_all[k]].m for k, v in merged.items())
 
-    # the same arrivals, one graph at a time (no overlap, no batching)
-    nb = int(np.searchsorted(arrivals, args.serve_baseline_seconds))
+    # the same arrivals, one graph at a time (no overlap, no batching), on rank 0
+    nb = int(np.searchsorted(arrivals_all, args.serve_baseline_seconds))
     base_lat = []
     bstart = time.perf_counter()
     for rid in range(nb):
-        delay = bstart + arrivals[rid] - time.perf_counter()
+        delay = bstart + arrivals_all[rid] - time.perf_counter()
         if delay > 0:
             time.sleep(delay)
-        o, x, w = pinned[picks[rid]]
+        o, x, w = pinned[picks_all[rid]]
         h = lp.lp_graph_create(o, x, w)
         lp.lp_rak_run(h, params)
         lp.lp_modularity(h)
         lp.lp_labels_get(h)
         lp.lp_graph_destroy(h)
-        base_lat.append(1e3 * (time.perf_counter() - bstart - arrivals[rid]))
+        base_lat.append(1e3 * (time.perf_counter() - bstart - arrivals_all[rid]))
     base_span = time.perf_counter() - bstart
     base_lat = np.array(base_lat) if base_lat else np.zeros(1)
 
@@ -867,18 +960,19 @@ def run_serve(args):
         lp.lp_labels_get(h)
         lp.lp_graph_destroy(h)
     seq_span = time.perf_counter() - sstart
-    line = {
+    return {
         "metric": f"served graphs/s (Poisson {args.serve_rate:g} req/s)",
-        "value": len(done) / makespan, "unit": "graphs/s", "n_gpus": 1, "steps": n_req,
-        "warmup": len(pool), "ms_per_step": 1e3 * makespan / max(1, len(done)),
+        "value": len(merged) / makespan, "unit": "graphs/s", "n_gpus": ctx.world,
+        "steps": n_all, "warmup": len(pool), "ms_per_step": 1e3 * makespan / max(1, len(merged)),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic",
-        "config": {"workload": "serve", **p, "requests": n_req, "window_s": args.serve_seconds,
+        "config": {"workload": "serve", **p, "requests": n_all, "window_s": args.serve_seconds,
                    "pool_graphs": len(pool), "pool_generation_s": round(gen_s, 1),
                    "max_active": cfg.max_active, "streams": cfg.streams,
                    "hbm_budget_gib": cfg.hbm_budget >> 30,
                    "l2": "graphs resident per request, no flush",
-                   "parallelism": "single GPU"},
+                   "parallelism": (f"requests sharded over {ctx.world} ranks"
+                                   if ctx.world > 1 else "single GPU")},
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                        "mean_queued": float(queued.mean())},
         "gteps": entries / makespan / 1e9,
@@ -894,13 +988,20 @@ def run_serve(args):
                               "requests one after another through lp_graph_create/lp_rak_run"},
         "gpu_launches": int(launches),
         "clocks": clock_info,
-        "e2e": {"value": len(done) / makespan, "unit": "graphs/s",
+        "e2e": {"value": len(merged) / makespan, "unit": "graphs/s",
                 "h2d_bytes_per_step": int(np.mean([pool[i].offsets.nbytes + pool[i].indices.nbytes
-                                                   + pool[i].weights.nbytes for i in picks])),
-                "d2h_bytes_per_step": int(np.mean([pool[i].n * 4 for i in picks])),
+                                                   + pool[i].weights.nbytes for i in picks_all])),
+                "d2h_bytes_per_step": int(np.mean([pool[i].n * 4 for i in picks_all])),
                 "how": "submit from pinned host CSR -> labels and modularity back on the host"},
     }
-    print(json.dumps(line), flush=True)
+
+
+def run_serve(args):
+    ctx = setup_ctx()
+    line = measure_serve(args, ctx)
+    finish_ctx(ctx)
+    if ctx.rank == 0:
+        print(json.dumps(line), flush=True)
     return 0
 
 

@@ -210,14 +210,22 @@ __global__ void __launch_bounds__(MT) k_mod_entries(ModArgs a)
             }
             rs += (uint32_t)w[q];
             const unsigned long long lw = cu[q] == s_c[kq[q]] ? (unsigned long long)w[q] : 0ull;
-            if (MULTI) {
-                run.add(a.acc, s_g[kq[q]], lw, (unsigned long long)w[q]);
+            if (MULTI && s_g[kq[q]] != s_g[0]) {
+                run.add(a.acc, s_g[kq[q]], lw, (unsigned long long)w[q]);  // rare: a graph boundary
             } else {
-                l += lw;
+                l += lw;  // single graph, or the chunk's first graph
                 w2 += (unsigned long long)w[q];
             }
         }
         if (rs) atomicAdd(&s_kv[cur], rs);
+    }
+    if (MULTI) {  // the chunk's first graph: one pair of atomics per warp
+        l = warp_sum64(l);
+        w2 = warp_sum64(w2);
+        if (have && lane == 0 && w2) {
+            atomicAdd(a.acc + 4 * (int64_t)s_g[0], l);
+            atomicAdd(a.acc + 4 * (int64_t)s_g[0] + 1, w2);
+        }
     }
     __syncthreads();  // s_kv of every warp complete, s_dom_slot set
 

@@ -13,10 +13,14 @@
 //     for labels that do not fit the CTA's shared-memory table.
 // Its size bounds the graphs it accepts: at most NA_MAX_DEGREE entries per row.
 //
-// The kernel is a variant of the hub sweep kernel: one 512-thread CTA per
-// vertex over all vertices (no degree buckets, which would need memory per
-// graph), a shared table of NA_TABLE slots, and the overflow table taken from
-// the static array instead of a library allocation.
+// The kernel needs no degree buckets (which would need memory per graph).
+// It makes two passes over the vertices.  First, each warp takes the rows
+// of at most 32 entries, one lane per entry: a lane's label total is the
+// sum over the lanes holding the same label (__match_any_sync), and the
+// lowest of those lanes is the label's first position.  Then each CTA takes
+// the longer rows: a shared table of 2^ceil(log2(2d)) slots (at most
+// NA_TABLE), probed at most NA_PROBE slots from a label's hash; a label
+// whose window is full goes to the CTA's overflow table in the static array.
 #include <mutex>
 #include <string>
 
@@ -59,6 +63,8 @@ struct NoAllocArgs {
     uint32_t *ov_npos;
 };
 
+constexpr int NA_WARP_MAX = 32;  // rows of at most this many entries: one warp each
+
 __global__ void __launch_bounds__(NA_THREADS) k_sweep_noalloc(NoAllocArgs a)
 {
     extern __shared__ int32_t smem[];
@@ -68,6 +74,48 @@ __global__ void __launch_bounds__(NA_THREADS) k_sweep_noalloc(NoAllocArgs a)
     __shared__ Cand s_red[NA_THREADS / 32];
     __shared__ uint32_t s_u[NA_THREADS / 32 + 1];
     __shared__ int s_spilled;
+    const int lane = threadIdx.x & 31;
+    uint32_t my_changed = 0;
+
+    // rows of 1 .. 32 entries: one warp each, no table
+    const int64_t wid = ((int64_t)blockIdx.x * NA_THREADS + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * NA_THREADS) >> 5;
+    for (int64_t v = wid; v < a.n; v += nw) {
+        const int32_t rs = __ldg(a.off + v), d = __ldg(a.off + v + 1) - rs;
+        if (d > NA_WARP_MAX) continue;  // warp-uniform
+        const int32_t own = __ldg(a.lab_in + v);
+        if (d == 0) {  // no neighbours: the label stays (Sec. 3.2 reading c8)
+            if (lane == 0) a.lab_out[v] = own;
+            continue;
+        }
+        const bool act = lane < d;
+        int32_t l = EMPTY;
+        uint32_t w = 0u;
+        if (act) {
+            const int32_t u = __ldg(a.idx + rs + lane);
+            w = a.wts ? (uint32_t)__ldg(a.wts + rs + lane) : 1u;
+            l = __ldg(a.lab_in + u);
+        }
+        const unsigned grp = __match_any_sync(FULL, act ? l : EMPTY);
+        const uint32_t sum = __reduce_add_sync(grp, w);  // a row's sum < 2^31
+        const bool lead = act && lane == __ffs(grp) - 1;  // the label's first position
+        Cand c{0u, 0u, 0ull, EMPTY};
+        if (lead) c = Cand{sum, 0xFFFFFFFFu - (uint32_t)lane, 0ull, l};
+        if (!a.strict) {
+            const uint32_t mx = __reduce_max_sync(FULL, c.sum);
+            if (lead && c.sum == mx)
+                c.h = stream_at(stream_at(a.key_t, (uint64_t)v + 1), (uint64_t)l + 1);
+            else
+                c = Cand{0u, 0u, 0ull, EMPTY};
+        }
+        c = warp_best(c);
+        if (lane == 0) {
+            a.lab_out[v] = c.label;
+            if (c.label != own) ++my_changed;
+        }
+    }
+
+    // longer rows: one CTA each, a table of 2^ceil(log2(2d)) slots
     for (int j = threadIdx.x; j < NA_TABLE; j += NA_THREADS) {
         tk[j] = EMPTY;
         ts[j] = 0;
@@ -78,16 +126,13 @@ __global__ void __launch_bounds__(NA_THREADS) k_sweep_noalloc(NoAllocArgs a)
     int32_t *gk = a.ov_key + (int64_t)blockIdx.x * NA_SLOTS;
     int32_t *gs = a.ov_sum + (int64_t)blockIdx.x * NA_SLOTS;
     uint32_t *gp = a.ov_npos + (int64_t)blockIdx.x * NA_SLOTS;
-    uint32_t my_changed = 0;
-
     for (int32_t v = blockIdx.x; v < a.n; v += gridDim.x) {
         const int32_t rs = __ldg(a.off + v), d = __ldg(a.off + v + 1) - rs;
+        if (d <= NA_WARP_MAX) continue;  // block-uniform
         const int32_t own = __ldg(a.lab_in + v);
-        if (d == 0) {  // no neighbours: the label stays (Sec. 3.2 reading c8)
-            if (threadIdx.x == 0) a.lab_out[v] = own;
-            continue;
-        }
         const int glg = ilog2_ceil(2u * (uint32_t)d);  // 2^glg <= NA_SLOTS (degree checked)
+        const int lg = glg < NA_TABLE_LG ? glg : NA_TABLE_LG;
+        const int probe = NA_PROBE < (1 << lg) ? NA_PROBE : (1 << lg);
         for (int k0 = 0; k0 < d; k0 += NA_THREADS) {
             const int k = k0 + threadIdx.x;
             const bool act = k < d;
@@ -98,28 +143,28 @@ __global__ void __launch_bounds__(NA_THREADS) k_sweep_noalloc(NoAllocArgs a)
                 w = a.wts ? __ldg(a.wts + rs + k) : 1;
                 l = __ldg(a.lab_in + u);
             }
-            if (act && !table_add(tk, ts, tp, NA_TABLE_LG, NA_PROBE, l, w, k)) {
+            if (act && !table_add(tk, ts, tp, lg, probe, l, w, k)) {
                 s_spilled = 1;
                 table_add(gk, gs, gp, glg, 1 << glg, l, w, k);
             }
         }
         __syncthreads();
+        const int slots = 1 << lg;
         const int gslots = s_spilled ? (1 << glg) : 0;
         Cand best{0u, 0u, 0ull, EMPTY};
         uint32_t mx = 0;
         if (!a.strict) {
-            for (int j = threadIdx.x; j < NA_TABLE + gslots; j += NA_THREADS) {
-                const int32_t key = j < NA_TABLE ? tk[j] : gk[j - NA_TABLE];
-                if (key != EMPTY)
-                    mx = max(mx, (uint32_t)(j < NA_TABLE ? ts[j] : gs[j - NA_TABLE]));
+            for (int j = threadIdx.x; j < slots + gslots; j += NA_THREADS) {
+                const int32_t key = j < slots ? tk[j] : gk[j - slots];
+                if (key != EMPTY) mx = max(mx, (uint32_t)(j < slots ? ts[j] : gs[j - slots]));
             }
             mx = block_max<NA_THREADS>(mx, s_u);
         }
         const uint64_t ktv = stream_at(a.key_t, (uint64_t)v + 1);
-        for (int j = threadIdx.x; j < NA_TABLE + gslots; j += NA_THREADS) {
-            int32_t *K = j < NA_TABLE ? tk + j : gk + (j - NA_TABLE);
-            int32_t *S = j < NA_TABLE ? ts + j : gs + (j - NA_TABLE);
-            uint32_t *Q = j < NA_TABLE ? tp + j : gp + (j - NA_TABLE);
+        for (int j = threadIdx.x; j < slots + gslots; j += NA_THREADS) {
+            int32_t *K = j < slots ? tk + j : gk + (j - slots);
+            int32_t *S = j < slots ? ts + j : gs + (j - slots);
+            uint32_t *Q = j < slots ? tp + j : gp + (j - slots);
             const int32_t key = *K;
             if (key != EMPTY) {
                 if (a.strict) {
@@ -129,7 +174,7 @@ __global__ void __launch_bounds__(NA_THREADS) k_sweep_noalloc(NoAllocArgs a)
                     const Cand c{mx, *Q, stream_at(ktv, (uint64_t)key + 1), key};
                     if (better(c, best)) best = c;
                 }
-                *K = EMPTY;
+                *K = EMPTY;  // every used slot is reset: the tables stay clean
                 *S = 0;
                 *Q = 0;
             }
@@ -142,7 +187,8 @@ __global__ void __launch_bounds__(NA_THREADS) k_sweep_noalloc(NoAllocArgs a)
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0 && my_changed) atomicAdd(a.changed, (int)my_changed);
+    my_changed = __reduce_add_sync(FULL, my_changed);
+    if (lane == 0 && my_changed) atomicAdd(a.changed, (int)my_changed);
 }
 
 // Device address of the static array, looked up once per device.

@@ -1,5 +1,7 @@
 """Host-side logic of bench.py that needs no GPU: the cross-rank reduction of
-the multi-GPU path (gloo, world size 2) and the reference arm's rank rule."""
+the multi-GPU path, the graph-level sharding of the batch and serving
+workloads and the assembly of per-graph results (gloo, world size 2), and the
+reference arm's rank rule."""
 import os
 import subprocess
 import sys
@@ -66,3 +68,48 @@ def test_traffic_summary_is_well_formed():
     current = bench.sweep_sources_hash()
     expect = ratios["sweep_hub"] if hashes[0] == current else None
     assert bench.traffic_ratio("sweep_hub") == expect
+
+
+def _shard_worker(rank, world, port, sizes, out):
+    import torch.distributed as dist
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    sys.path.insert(0, ROOT)
+    import bench
+
+    mine = bench.shard_graphs(sizes, rank, world)
+    merged = bench.gather_results({i: (rank, i * i) for i in mine}, world)
+    out[rank] = (mine, merged)
+    dist.destroy_process_group()
+
+
+def test_graph_sharding_and_assembly_gloo():
+    """Each graph runs on exactly one rank; every rank ends with every graph's
+    result."""
+    import random
+
+    sizes = [int(x) for x in (1000 * (1 + (7 * i) % 13) for i in range(37))]
+    port = random.randint(20000, 40000)
+    with mp.Manager() as mgr:
+        out = mgr.dict()
+        mp.spawn(_shard_worker, args=(2, port, sizes, out), nprocs=2, join=True)
+        shards = [out[0][0], out[1][0]]
+        assert sorted(shards[0] + shards[1]) == list(range(len(sizes)))
+        for r in (0, 1):
+            merged = out[r][1]
+            assert sorted(merged) == list(range(len(sizes)))
+            assert all(merged[i] == (0 if i in shards[0] else 1, i * i) for i in merged)
+
+
+def test_graph_sharding_balances_work():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    sizes = [int(1000 * 1.7 ** (i % 11)) for i in range(200)]
+    for world in (1, 2, 3, 8):
+        parts = [bench.shard_graphs(sizes, r, world) for r in range(world)]
+        assert sorted(i for p in parts for i in p) == list(range(len(sizes)))
+        loads = [sum(sizes[i] for i in p) for p in parts]
+        assert max(loads) - min(loads) <= max(sizes)
+    assert bench.gather_results({3: "x"}, 1) == {3: "x"}

@@ -632,31 +632,7 @@ def test_autotune_then_run_matches_oracle(lp):
 
 
 # ---------------------------------------------------------------- full-size workloads
-def sampled_sync_check(lp, g, strict, seed, samples=20_000):
-    """Two sweeps at full size; each output of the second sweep is checked at
-    sampled vertices (plus every vertex of degree > 1024) against the oracle's
-    single-vertex step; the changed counts must match the label arrays."""
-    rng = np.random.default_rng(seed)
-    deg = np.diff(g.offsets)
-    verts = np.unique(np.concatenate([rng.integers(0, g.n, samples), np.nonzero(deg > 1024)[0]]))
-    verts = verts.astype(np.int32)
-    with lp.Graph(g.offsets, g.indices, g.weights) as G:
-        r1 = G.rak(tolerance=0.0, max_iter=1, mode="sync", strict=strict, seed=seed)
-        lab1 = G.labels().copy()
-        ident = np.arange(g.n, dtype=np.int32)
-        ref1 = oracle.choose_many(g.offsets, g.indices, g.weights, ident, verts, strict=strict,
-                                  seed=seed, t=0)
-        assert np.array_equal(lab1[verts], ref1)
-        assert r1.last_changed == int(np.sum(lab1 != ident))
-        r2 = G.rak(tolerance=0.0, max_iter=1, mode="sync", strict=strict, seed=seed,
-                   iter_offset=1, init_labels=lab1)
-        lab2 = G.labels().copy()
-        ref2 = oracle.choose_many(g.offsets, g.indices, g.weights, lab1, verts, strict=strict,
-                                  seed=seed, t=1)
-        assert np.array_equal(lab2[verts], ref2)
-        assert r2.last_changed == int(np.sum(lab2 != lab1))
-
-
+# (synchronous parity and asynchronous quality at full size: test_fullsize_gpu.py)
 @pytest.fixture(scope="module")
 def rmat22():
     return gg.workload("rmat22")
@@ -665,20 +641,6 @@ def rmat22():
 @pytest.fixture(scope="module")
 def road4096():
     return gg.workload("road4096")
-
-
-@pytest.mark.slow
-def test_rmat22_full_size(lp, rmat22):
-    sampled_sync_check(lp, rmat22, strict=True, seed=1)
-    sampled_sync_check(lp, rmat22, strict=False, seed=2)
-    for waves in (2, 31):
-        assert_async_quality(lp, rmat22.offsets, rmat22.indices, rmat22.weights, waves=waves)
-
-
-@pytest.mark.slow
-def test_road4096_full_size(lp, road4096):
-    sampled_sync_check(lp, road4096, strict=True, seed=3)
-    assert_async_quality(lp, road4096.offsets, road4096.indices, road4096.weights, waves=31)
 
 
 # ------------------------------------------------- splitting disconnected communities
