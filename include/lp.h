@@ -310,6 +310,46 @@ lp_status lp_server_drain(lp_server *s);
 lp_status lp_server_destroy(lp_server *s);
 
 /* ---------------------------------------------------------------------------
+ * SLPA: speaker-listener label propagation (Sec. 3.4)
+ * ------------------------------------------------------------------------- */
+
+/* SLPA parameters. */
+typedef struct {
+    int32_t memory_size; /* labels each vertex remembers, slot 0 = the vertex itself;
+                            1 .. 64 (at most memory_size - 1 iterations run) */
+    double tolerance;    /* stop once at most tolerance * n vertices stored a label
+                            that differs from their previous slot; [0, 1] */
+    int32_t strict;      /* 1: the listener keeps the first of its heaviest spoken
+                            labels (row order), 0: the one with the smallest tie key */
+    uint64_t seed;       /* drives the speakers' slot draws and the non-strict key */
+} lp_slpa_params;
+
+/* memory_size 20, tolerance 0.05, strict 1, seed 0.  Errors: LP_EINVAL on NULL. */
+lp_status lp_slpa_params_default(lp_slpa_params *p);
+
+/* Run SLPA on a graph (Sec. 3.4): every vertex remembers its own id; in
+ * iteration t = 1, 2, ... each neighbour u of a listener v speaks one label of
+ * the slots 0 .. t-1 its memory held before the iteration, the slot drawn as
+ * floor(hi32(h) * t / 2^32) from h = the counter-based SplitMix64 draw of
+ * (seed ^ 0x5350454B, t, v, position of the entry in v's row) nested as in the
+ * non-strict tie key; v sums the spoken labels' edge weights and stores the
+ * heaviest in slot t (ties as in lp_rak_params with iteration index t).  A
+ * vertex without edges repeats its previous slot.  Afterwards the graph's
+ * labels (lp_labels_get, lp_modularity) are the communities: the label a
+ * vertex's memory holds most often, the one stored first on equal counts.
+ * out: iterations run, converged, the last iteration's changed count and the
+ * device time; lp_rak_history gives the changed counts.  The memory
+ * (memory_size x n int32) stays allocated with the graph.
+ * Errors: LP_EINVAL for NULL arguments or parameters out of range; LP_ENOMEM;
+ * LP_ECUDA. */
+lp_status lp_slpa_run(lp_graph *g, const lp_slpa_params *p, lp_rak_result *out);
+
+/* Copy memory slots 0 .. slots-1 of the last SLPA run to dst (slots x n int32,
+ * slot t of vertex v at dst[t * n + v]; host or device, by dst_on_device);
+ * slots may be at most the iterations run + 1.  Errors: LP_EINVAL; LP_ECUDA. */
+lp_status lp_slpa_memory_get(lp_graph *g, int32_t *dst, int32_t slots, int32_t dst_on_device);
+
+/* ---------------------------------------------------------------------------
  * One sweep without any allocation
  * ------------------------------------------------------------------------- */
 

@@ -86,6 +86,11 @@ class lp_tune_result(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class lp_slpa_params(ctypes.Structure):
+    _fields_ = [("memory_size", ctypes.c_int32), ("tolerance", ctypes.c_double),
+                ("strict", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+
 _lib = None
 
 # Every symbol include/lp.h declares, with its ctypes signature.
@@ -132,6 +137,10 @@ SIGNATURES = {
     "lp_rak_sweep_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, _P, _P, _P, _P, _P,
                                             ctypes.c_int32, ctypes.c_uint64, ctypes.c_int32,
                                             ctypes.POINTER(ctypes.c_int64), _P]),
+    "lp_slpa_params_default": (ctypes.c_int, [ctypes.POINTER(lp_slpa_params)]),
+    "lp_slpa_run": (ctypes.c_int, [_P, ctypes.POINTER(lp_slpa_params),
+                                   ctypes.POINTER(lp_rak_result)]),
+    "lp_slpa_memory_get": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int32]),
     "lp_split_communities": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
     "lp_selftest_barrier_timeout": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int32)]),
     "lp_last_error": (ctypes.c_char_p, []),
@@ -479,6 +488,31 @@ def lp_last_error() -> str:
     return load().lp_last_error().decode(errors="replace")
 
 
+def lp_slpa_run(handle: int, memory_size=20, tolerance=0.05, strict=True, seed=0) -> lp_rak_result:
+    """Run SLPA (Sec. 3.4) on a graph; its labels become the communities."""
+    p = lp_slpa_params()
+    _check(load().lp_slpa_params_default(ctypes.byref(p)))
+    p.memory_size = int(memory_size)
+    p.tolerance = float(tolerance)
+    p.strict = 1 if strict else 0
+    p.seed = int(seed) & (2**64 - 1)
+    r = lp_rak_result()
+    _check(load().lp_slpa_run(handle, ctypes.byref(p), ctypes.byref(r)))
+    return r
+
+
+def lp_slpa_memory_get(handle: int, slots: int, out=None):
+    """Memory slots 0 .. slots-1 of the last SLPA run as a (slots, n) array
+    (numpy, or into a contiguous int32 ``out``, host or CUDA)."""
+    n, _ = lp_graph_info(handle)
+    if out is None:
+        out = np.empty((slots, n), dtype=np.int32)
+    ptr, on_dev, keep = _int32_buffer(out, "out")
+    _check(load().lp_slpa_memory_get(handle, ptr, int(slots), 1 if on_dev else 0))
+    del keep
+    return out
+
+
 def lp_split_communities(handle: int) -> int:
     """Split the graph's communities into connected components in place (each
     named by its smallest vertex); returns the number of components."""
@@ -513,6 +547,12 @@ class Graph:
 
     def split(self) -> int:
         return lp_split_communities(self.handle)
+
+    def slpa(self, **kw) -> lp_rak_result:
+        return lp_slpa_run(self.handle, **kw)
+
+    def slpa_memory(self, slots: int, out=None):
+        return lp_slpa_memory_get(self.handle, slots, out)
 
     def autotune(self, sweeps: int = 5, **kw) -> lp_tune_result:
         return lp_graph_autotune(self.handle, sweeps=sweeps, **kw)

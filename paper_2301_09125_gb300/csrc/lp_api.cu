@@ -255,6 +255,11 @@ struct GraphSet {
     int32_t *hused = nullptr, *hdone = nullptr, *hnused = nullptr;
     uint32_t *hmaj = nullptr;  // long rows' majority counters (4 per hub task)
     int2 *hvote = nullptr;     // per segment item: its majority vote
+    // SLPA (Sec. 3.4): memory slots (slpa_slots x nv, slot t of v at t * nv + v)
+    // and the labels spoken to every packed entry in the current iteration
+    int32_t *slpa_mem = nullptr, *spoken = nullptr;
+    int32_t slpa_slots = 0, slpa_filled = 0;
+    bool slpa_on = false;
     int32_t *cpos = nullptr;   // rows left by a pre-pass (nv) and their count, open long rows
     int32_t *ccount = nullptr;
     // packed rows of the run's list (lp_internal.cuh), built for one wave
@@ -325,6 +330,10 @@ struct GraphSet {
         f(cpos);
         f(ccount);
         cpos = ccount = nullptr;
+        f(slpa_mem);
+        f(spoken);
+        slpa_mem = spoken = nullptr;
+        slpa_slots = slpa_filled = 0;
         f(pk_rp);
         f(pk_first);
         f(pk_idx);
@@ -944,6 +953,12 @@ struct GraphSet {
         // earlier waves (written by this iteration's earlier launches)
         a.lab_in = lab[cur];
         a.lab_out = lab[cur ^ 1];
+        a.spoken = nullptr;
+        if (slpa_on) {  // SLPA: memory slot it is read, slot it + 1 written
+            a.lab_in = slpa_mem + (int64_t)it * nv;
+            a.lab_out = slpa_mem + (int64_t)(it + 1) * nv;
+            a.spoken = spoken;
+        }
         a.changed = changed + (int64_t)it * G;
         a.key_t = stream_at(rs.p.seed, (uint64_t)t + 1);
         // the labels read in the first sweep from unique labels never give a
@@ -961,7 +976,7 @@ struct GraphSet {
             }
             int64_t max_len = 0;
             for (int k = 0; k < waves; ++k) max_len = std::max(max_len, wcount[(size_t)k]);
-            a.identity = rows_distinct && it == 0 && !rs.p.init_labels;  // wave 0 only
+            a.identity = rows_distinct && it == 0 && !rs.p.init_labels && !slpa_on;  // wave 0 only
             if (prof) {
                 while (prof_ev.size() < 2 * (rs.prof_launch.size() + 1)) {
                     cudaEvent_t e;
@@ -1015,7 +1030,7 @@ struct GraphSet {
             if (a.len == 0) continue;
             // the first sweep from unique labels reads unique labels only in
             // its first wave (later waves see this sweep's new labels)
-            a.identity = rows_distinct && it == 0 && !rs.p.init_labels && k == 0;
+            a.identity = rows_distinct && it == 0 && !rs.p.init_labels && k == 0 && !slpa_on;
             if (prof) {
                 while (prof_ev.size() < 2 * (rs.prof_launch.size() + 1)) {
                     cudaEvent_t e;
@@ -1364,6 +1379,97 @@ struct GraphSet {
         return run_end();
     }
 
+    // SLPA (Sec. 3.4) on a single graph: iteration t (1 <= t < memory_size)
+    // speaks one label per entry from the memories of the previous slots and
+    // runs one synchronous RAK sweep over the spoken labels into slot t; the
+    // tolerance test counts vertices whose new slot differs from the previous
+    // one.  The graph's labels become the communities (the label a memory
+    // holds most often).
+    lp_status slpa(const lp_slpa_params *p)
+    {
+        if (!p) return fail(LP_EINVAL, "params is NULL");
+        if (p->memory_size < 1 || p->memory_size > SLPA_MAX_MEMORY)
+            return fail(LP_EINVAL, "memory_size must lie in [1, 64]");
+        if (!(p->tolerance >= 0.0 && p->tolerance <= 1.0))
+            return fail(LP_EINVAL, "tolerance must lie in [0, 1]");
+        if (G != 1) return fail(LP_EINVAL, "SLPA runs on single graphs");
+        const int32_t M = p->memory_size;
+        lp_rak_params q{};
+        lp_rak_params_default(&q);
+        q.mode = LP_SYNC;
+        q.strict = p->strict ? 1 : 0;
+        q.seed = p->seed;
+        q.tolerance = p->tolerance;
+        q.max_iter = M > 1 ? M - 1 : 1;
+        q.iter_offset = 1;  // the tie key of slot t uses t
+        q.init_labels = nullptr;
+        if (slpa_slots < M) {
+            if (slpa_mem) cudaFreeAsync(slpa_mem, st);
+            slpa_mem = nullptr;
+            slpa_slots = 0;
+            LP_TRY(dev_alloc(&slpa_mem, (int64_t)M * nv, "SLPA memory", st, device));
+            slpa_slots = M;
+        }
+        if (!spoken) LP_TRY(dev_alloc(&spoken, ne, "SLPA spoken labels", st, device));
+        LP_TRY(run_begin(&q, false));
+        rs.prof = false;
+        Launches L;
+        if (nv > 0)
+            LP_CU(cudaMemcpyAsync(slpa_mem, lab[0], (size_t)nv * sizeof(int32_t),
+                                  cudaMemcpyDeviceToDevice, st));  // slot 0: the vertex itself
+        int32_t iters = 0, conv = 0;
+        int64_t last = 0;
+        history.clear();
+        slpa_on = true;
+        lp_status ls = LP_OK;
+        for (int32_t t = 1; t < M && ls == LP_OK; ++t) {
+            const int32_t it = t - 1;
+            // a vertex without edges repeats its previous slot
+            cudaError_t e = cudaMemcpyAsync(slpa_mem + (int64_t)t * nv, slpa_mem + (int64_t)it * nv,
+                                            (size_t)nv * sizeof(int32_t), cudaMemcpyDeviceToDevice,
+                                            st);
+            if (e != cudaSuccess) {
+                ls = fail(LP_ECUDA, cuda_msg("SLPA slot copy", e));
+                break;
+            }
+            if (slpa_speak(pk_rp, list, pk_first, ne, pk_idx, slpa_mem, nv, t, p->seed, spoken, st,
+                           &L.n) != 0) {
+                ls = fail(LP_ECUDA, cuda_msg("SLPA speak launch", cudaGetLastError()));
+                break;
+            }
+            if ((ls = launch_sweeps(st, it, 0, false, &L.n)) != LP_OK) break;
+            e = cudaMemcpyAsync(h_changed + it, changed + it, sizeof(int32_t),
+                                cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) {
+                ls = fail(LP_ECUDA, cuda_msg("SLPA changed count", e));
+                break;
+            }
+            iters = t;
+            last = h_changed[it];
+            history.push_back(last);
+            if ((double)last <= p->tolerance * (double)nv) {  // Sec. 3.2's tolerance test
+                conv = 1;
+                break;
+            }
+        }
+        slpa_on = false;
+        LP_TRY(ls);
+        slpa_filled = iters + 1;
+        if (slpa_community(slpa_mem, nv, iters, lab[0], st, &L.n) != 0)
+            return fail(LP_ECUDA, cuda_msg("SLPA community launch", cudaGetLastError()));
+        LP_CU(cudaEventRecord(ev1, st));
+        LP_CU(cudaEventSynchronize(ev1));
+        float ms = 0.f;
+        LP_CU(cudaEventElapsedTime(&ms, ev0, ev1));
+        std::fill(final_buf.begin(), final_buf.end(), 0);
+        q_valid = false;
+        results[0] = lp_rak_result{iters, conv, last, ms};
+        rs.it = iters;
+        rs.active_left = 0;
+        return LP_OK;
+    }
+
     // Graphs of a batch stop in different iterations, so their final labels
     // sit in either buffer; copy them all into buffer 0.
     lp_status gather_final_labels()
@@ -1619,6 +1725,41 @@ lp_status lp_rak_run(lp_graph *g, const lp_rak_params *p, lp_rak_result *out)
     DeviceGuard dg(g->s.device);
     LP_TRY(g->s.run(p, false));
     *out = g->s.results[0];
+    return LP_OK;
+}
+
+lp_status lp_slpa_params_default(lp_slpa_params *p)
+{
+    if (!p) return fail(LP_EINVAL, "params is NULL");
+    p->memory_size = 20;
+    p->tolerance = 0.05;
+    p->strict = 1;
+    p->seed = 0;
+    return LP_OK;
+}
+
+lp_status lp_slpa_run(lp_graph *g, const lp_slpa_params *p, lp_rak_result *out)
+{
+    if (!g) return fail(LP_EINVAL, "graph is NULL");
+    if (!out) return fail(LP_EINVAL, "result is NULL");
+    DeviceGuard dg(g->s.device);
+    LP_TRY(g->s.slpa(p));
+    *out = g->s.results[0];
+    return LP_OK;
+}
+
+lp_status lp_slpa_memory_get(lp_graph *g, int32_t *dst, int32_t slots, int32_t dst_on_device)
+{
+    if (!g) return fail(LP_EINVAL, "graph is NULL");
+    lp::GraphSet &s = g->s;
+    if (slots < 0 || slots > s.slpa_filled)
+        return fail(LP_EINVAL, "slots must lie in [0, the slots the last SLPA run filled]");
+    if (!dst && slots > 0 && s.nv > 0) return fail(LP_EINVAL, "dst is NULL");
+    if (slots == 0 || s.nv == 0) return LP_OK;
+    DeviceGuard dg(s.device);
+    LP_CU(cudaMemcpyAsync(dst, s.slpa_mem, (size_t)slots * s.nv * sizeof(int32_t),
+                          dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s.st));
+    LP_CU(cudaStreamSynchronize(s.st));
     return LP_OK;
 }
 

@@ -85,6 +85,9 @@ struct SweepArgs {
     const int32_t *idx;      // packed neighbour ids (bit 31: earlier wave)
     const int32_t *wts;      // packed weights, null = unit weights
     const int32_t *lab_in;   // labels read (== lab_out in asynchronous mode)
+    // SLPA (Sec. 3.4): the label each entry's speaker spoke, aligned with idx
+    // (null: an entry's label is its neighbour's current label)
+    const int32_t *spoken;
     int32_t *lab_out;        // labels written
     const int32_t *list;     // bucket entries (global vertex ids)
     int64_t len;             // bucket length
@@ -350,6 +353,22 @@ int converge_launch(const int32_t *changed_it, const int32_t *g_n, int32_t *g_ac
                     double tolerance, int32_t it, bool multi, const RunResults &res,
                     cudaGraphConditionalHandle next, bool has_next, int32_t *stop, bool last,
                     cudaStream_t st);
+
+// SLPA (Sec. 3.4), lp_slpa.cu.  Memory slot t of vertex v at mem[t * n + v].
+// SLPA_SPEAK keeps the speakers' slot draws apart from the tie keys (the
+// same seed drives both).
+constexpr int SLPA_MAX_MEMORY = 64;
+constexpr uint64_t SLPA_SPEAK = 0x5350454Bull;
+// spoken[e] for every packed entry e of a single graph's rows in iteration t
+// (1 <= t < memory_size): the speaker's label in slot draw(seed ^ SLPA_SPEAK,
+// t, listener, row position) mod t of its memory.
+int slpa_speak(const int64_t *rp, const int32_t *list, const int64_t *first_row, int64_t ne,
+               const int32_t *pidx, const int32_t *mem, int32_t n, int32_t t, uint64_t seed,
+               int32_t *spoken, cudaStream_t st, int64_t *launches);
+// out[v] = the label slots 0 .. last of v's memory hold most often, the first
+// stored on equal counts.
+int slpa_community(const int32_t *mem, int32_t n, int32_t last, int32_t *out, cudaStream_t st,
+                   int64_t *launches);
 
 // Split the communities of lab (n vertices, m entries, one graph) into
 // connected components in place: lab[v] = smallest vertex of v's component.

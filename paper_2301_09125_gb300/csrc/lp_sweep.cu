@@ -223,6 +223,26 @@ __device__ __forceinline__ Quad load_quad(const SweepArgs &a, int64_t blk, int64
     int32_t u[4], w[4];
     load_block(a, blk, u, w);
     Quad q;
+    if (a.spoken) {  // SLPA: the labels the entries' speakers spoke
+        int32_t sp[4];
+        if (e0 + 3 < a.ne) {
+            const int4 S = ld_entries4(a.spoken, blk);
+            sp[0] = S.x;
+            sp[1] = S.y;
+            sp[2] = S.z;
+            sp[3] = S.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) sp[j] = e0 + j < a.ne ? __ldg(a.spoken + e0 + j) : EMPTY;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const bool in = e0 + j >= lo && e0 + j < hi;
+            q.l[j] = in ? sp[j] : EMPTY;
+            q.w[j] = in ? w[j] : 0;
+        }
+        return q;
+    }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const bool in = e0 + j >= lo && e0 + j < hi;
@@ -464,7 +484,8 @@ __device__ __forceinline__ void small_sweep(const SweepArgs &a)
                     const int64_t e = x.e0 + j;
                     const int32_t u = ld_entry(a.idx + e);
                     wt[j] = a.wts ? (uint32_t)ld_entry(a.wts + e) : 1u;
-                    lab[j] = a.identity ? (u & ID_MASK) : neighbour_label<COH>(a, x.vb, u);
+                    lab[j] = a.spoken ? ld_entry(a.spoken + e)
+                             : a.identity ? (u & ID_MASK) : neighbour_label<COH>(a, x.vb, u);
                 }
             }
             // entries past the row are EMPTY with weight 0: their totals are 0
@@ -612,7 +633,8 @@ __device__ __forceinline__ void small_sweep(const SweepArgs &a)
                 const long long e = o_e0 + pos;
                 const int32_t u = ld_entry(a.idx + e);
                 w = a.wts ? ld_entry(a.wts + e) : 1;
-                l = a.identity ? (u & ID_MASK) : neighbour_label<COH>(a, o_vb, u);
+                l = a.spoken ? ld_entry(a.spoken + e)
+                             : a.identity ? (u & ID_MASK) : neighbour_label<COH>(a, o_vb, u);
             }
             // the owner's lanes (its whole row: rows fit in the chunk), then the
             // lanes of the owner with an equal label; the lowest lane of a
