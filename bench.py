@@ -43,6 +43,9 @@ one JSON line per setting (iterations, convergence, run time, GTEPS,
 modularity of the labels on the graph without self-loops).
 ``--experiment split`` times the split of disconnected communities after
 each class's benchmark run (communities and modularity before and after).
+``--experiment gather`` measures the ceiling of a label-gathering sweep: one
+pass streaming the rows, and one that also gathers every entry's neighbour
+label, on each class as generated and renumbered by decreasing degree.
 Multi-GPU (torchrun): on a single graph every rank runs its own replica;
 the batch and the serving stream shard whole graphs over the ranks
 (size-balanced; requests r, r + N, ... to rank r) with no collective on the
@@ -113,7 +116,7 @@ def parse():
                     help="single-graph workloads: leave out the serve sub-record")
     ap.add_argument("--per-graph-sample", type=int, default=256,
                     help="graphs of the batch timed one at a time")
-    ap.add_argument("--experiment", choices=["tolerance", "split"], default=None,
+    ap.add_argument("--experiment", choices=["tolerance", "split", "gather"], default=None,
                     help="run the tolerance / tie-rule study, or time the split of "
                          "disconnected communities, instead of the benchmark")
     ap.add_argument("--classes", default="sbm10k,rmat22,road4096,kmer8m",
@@ -1111,8 +1114,69 @@ def run_split_experiment(args):
     return 0
 
 
+def degree_renumbered(g):
+    """The graph with vertices renumbered by decreasing degree (stable), rows
+    in the new order: a layout where the most gathered labels sit together."""
+    n, m = g.n, g.m
+    deg = np.diff(g.offsets.astype(np.int64))
+    order = np.argsort(-deg, kind="stable")
+    pos = np.empty(n, dtype=np.int64)
+    pos[order] = np.arange(n)
+    d2 = deg[order]
+    off2 = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(d2, out=off2[1:])
+    rowid = np.repeat(np.arange(n), d2)
+    src = g.offsets[:-1].astype(np.int64)[order][rowid] + (np.arange(m) - off2[:-1][rowid])
+    idx2 = pos[g.indices[src]].astype(np.int32)
+    w2 = None if g.weights is None else g.weights[src]
+    return idx2, w2
+
+
+def run_gather_experiment(args):
+    """The ceiling a label-gathering sweep can reach on each class: one pass
+    streaming the column indices and weights (mode 0), and the same pass also
+    gathering every entry's neighbour label (mode 1), on the graph as given
+    and renumbered by decreasing degree.  Bytes are the sweep's algorithmic
+    HBM bytes (4 (n + 1) + 8 n + 4 or 8 per entry)."""
+    import torch
+
+    import paper_2301_09125_gb300 as lp
+    from paper_2301_09125_gb300 import build
+
+    build.build()
+    lp.load()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    peak, peak_kind = measured_peak_gbs()
+    for name in [c for c in args.classes.split(",") if c]:
+        g = gen_graph(name)
+        alg = alg_bytes_per_sweep(g)
+        for numbering in ("as generated", "by decreasing degree"):
+            if numbering == "as generated":
+                idx, w = g.indices, g.weights
+            else:
+                idx, w = degree_renumbered(g)
+            m4 = (g.m // 4) * 4
+            t_idx = torch.from_numpy(np.ascontiguousarray(idx[:m4])).to(dev)
+            t_w = None if w is None else torch.from_numpy(np.ascontiguousarray(w[:m4])).to(dev)
+            lab = torch.arange(g.n, dtype=torch.int32, device=dev)
+            for mode in (0, 1):
+                ms = lp.lp_probe_gather(g.n, t_idx, t_w, lab, mode=mode, repeats=20)
+                print(json.dumps({"experiment": "gather", "workload": name, "n": g.n, "m": g.m,
+                                  "numbering": numbering,
+                                  "pass": "stream" if mode == 0 else "stream + label gather",
+                                  "ms": ms, "g_entries_per_s": g.m / (ms * 1e-3) / 1e9,
+                                  "alg_gbs": alg / (ms * 1e-3) / 1e9,
+                                  "hbm_frac": alg / (ms * 1e-3) / 1e9 / peak,
+                                  "peak_gbs": peak, "peak_source": peak_kind}), flush=True)
+            del t_idx, t_w, lab
+    return 0
+
+
 def main():
     args = parse()
+    if args.experiment == "gather":
+        return run_gather_experiment(args)
     if args.experiment == "split":
         return run_split_experiment(args)
     if args.experiment:

@@ -417,6 +417,19 @@ lp_status lp_profile_reset(void);
  * or NULL out with capacity > 0. */
 lp_status lp_profile_read(lp_kernel_stat *out, int32_t capacity, int32_t *count);
 
+/* Measurement helper (no counterpart in the paper): the time of one pass that
+ * streams the first m / 4 16-byte blocks of indices and weights (mode 0), or
+ * also gathers labels[index] of every entry (mode 1), the data movement of a
+ * sweep without its per-row work.  indices, weights (NULL = unit), labels
+ * (n entries): device pointers, indices and weights 16-byte aligned, every
+ * index in [0, n) (checked first, LP_EINVAL otherwise).  sink: two device
+ * words, overwritten.  Runs 3 warm-up and `repeats` timed passes on
+ * cuda_stream; *ms_per_pass receives their mean (CUDA events).
+ * Errors: LP_EINVAL; LP_ECUDA. */
+lp_status lp_probe_gather(int32_t n, int64_t m, const int32_t *indices, const int32_t *weights,
+                          const int32_t *labels, int32_t mode, int32_t repeats, unsigned *sink,
+                          float *ms_per_pass, void *cuda_stream);
+
 /* Split every community of the graph's current labelling into its connected
  * components, in place: two vertices keep one label only if a path of edges
  * whose two ends both carry that label joins them.  The paper does not

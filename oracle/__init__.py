@@ -7,8 +7,8 @@ with the C file compiled here (``rak_oracle.c``).
 
 The functions are thin ctypes wrappers around the single-threaded C oracle,
 which restates Sec. 3.2 of Sahu, arXiv 2301.09125 (RAK: strict / non-strict
-tie rule, tolerance test), Sec. 3.3 (asynchronous update) and Sec. 1
-(Newman-Girvan modularity).  See the comment block at the top of
+tie rule, tolerance test), Sec. 3.3 (COPRA and the asynchronous update), Sec.
+3.4 (SLPA) and Sec. 1 (Newman-Girvan modularity).  See the comment block at the top of
 ``rak_oracle.c`` for each reading of the paper.
 """
 from __future__ import annotations
@@ -67,6 +67,13 @@ def _load():
                                     ctypes.c_double, ctypes.c_int, ctypes.c_uint64, _i32p, _i32p,
                                     ctypes.POINTER(ctypes.c_int32),
                                     ctypes.POINTER(ctypes.c_int32), _i64p]
+        lib.oracle_copra.restype = ctypes.c_int
+        lib.oracle_copra.argtypes = [ctypes.c_int32, _i32p, _i32p, _i32p, ctypes.c_int32,
+                                     ctypes.c_double, ctypes.c_int32, ctypes.c_int, ctypes.c_int32,
+                                     ctypes.c_int, ctypes.c_uint64, _i32p,
+                                     ctypes.POINTER(ctypes.c_uint32), _i32p,
+                                     ctypes.POINTER(ctypes.c_int32),
+                                     ctypes.POINTER(ctypes.c_int32), _i64p]
         lib.oracle_split.restype = ctypes.c_int64
         lib.oracle_split.argtypes = [ctypes.c_int32, _i32p, _i32p, _i32p, _i32p]
         lib.oracle_modularity.restype = ctypes.c_double
@@ -194,6 +201,44 @@ def slpa(offsets, indices, weights=None, memory_size=20, tolerance=0.05, strict=
         raise ValueError("oracle_slpa rejected its arguments")
     it = int(iters.value)
     return labels, memory[: it + 1].copy(), it, bool(conv.value), hist[:it].copy()
+
+
+COPRA_ONE = 65536  # belongings are integers in units of 2^-16 that sum to this
+
+
+def copra(offsets, indices, weights=None, max_labels=4, tolerance=0.01, max_iter=20,
+          mode="sync", waves=0, strict=True, seed=0):
+    """COPRA (Sec. 3.3): every vertex keeps at most ``max_labels`` (label,
+    belonging) pairs, belongings in units of 2^-16 summing to 2^16.
+
+    Returns ``(labels, sets_l, sets_b, iterations, converged, changed)``:
+    the best label of every vertex, the final sets as (n, max_labels) arrays
+    (belonging 0 after a set's last pair), and the per-iteration counts of
+    vertices whose best label changed.  ``waves`` as in :func:`rak`.
+    """
+    offsets = _arr(offsets)
+    indices = _arr(indices)
+    weights = None if weights is None else _arr(weights)
+    n = _check_csr(offsets, indices, weights)
+    if not 1 <= max_labels <= 64:
+        raise ValueError("max_labels must lie in [1, 64]")
+    L = int(max_labels)
+    sets_l = np.empty((max(n, 1), L), dtype=np.int32)
+    sets_b = np.empty((max(n, 1), L), dtype=np.uint32)
+    labels = np.empty(max(n, 1), dtype=np.int32)
+    hist = np.zeros(max_iter, dtype=np.int64)
+    iters = ctypes.c_int32(0)
+    conv = ctypes.c_int32(0)
+    rc = _load().oracle_copra(n, _ptr(offsets), _ptr(indices), _ptr(weights), L,
+                              float(tolerance), int(max_iter), 0 if mode == "sync" else 1,
+                              int(waves), 1 if strict else 0, ctypes.c_uint64(seed & (2**64 - 1)),
+                              _ptr(sets_l), sets_b.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+                              _ptr(labels), ctypes.byref(iters), ctypes.byref(conv),
+                              _ptr(hist, _i64p))
+    if rc != 0:
+        raise ValueError("oracle_copra rejected its arguments")
+    it = int(iters.value)
+    return labels[:n].copy(), sets_l[:n].copy(), sets_b[:n].copy(), it, bool(conv.value), hist[:it].copy()
 
 
 def split(offsets, indices, labels):

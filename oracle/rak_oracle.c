@@ -488,3 +488,220 @@ done_alloc:
     if (!memory) free(mem);
     return rc;
 }
+
+/* ------------------------------------------------------------------------- */
+/* COPRA, community overlap propagation (Sec. 3.3).                          */
+/* ------------------------------------------------------------------------- */
+/*
+ * Readings where Sec. 3.3 is open:
+ *   - a vertex holds a set of at most max_labels (label, belonging) pairs; the
+ *     belongings are integers in units of 2^-16 that sum to exactly
+ *     ORACLE_COPRA_ONE = 2^16 (the paper's real coefficients that sum to 1,
+ *     in fixed point so that every comparison is exact); the set is stored in
+ *     decreasing belonging, equal belongings by first appearance in the scan
+ *     that produced it, and its first label is the vertex's best label;
+ *   - every vertex starts as its own community: {(v, 2^16)};
+ *   - a listener v scans its row in CSR order and, for each neighbour u
+ *     (entry weight w), the pairs of u's set in stored order, summing
+ *     T(l) += w * b; its own labels are not added (only neighbours', as the
+ *     paper does); a label's first appearance is the index of its first
+ *     (entry, pair) in that scan;
+ *   - the threshold is 1/max_labels of the normalized belonging: label l is
+ *     kept iff max_labels * T(l) >= W * 2^16, W the summed weight of the row
+ *     (the sum of all T(l));
+ *   - no label above the threshold: the best label alone is kept, best =
+ *     largest T(l), ties by the RAK rule (strict: first appearance;
+ *     non-strict: smallest tie hash of (seed, iteration, v, label), then
+ *     first appearance);
+ *   - the kept labels are normalized: b(l) = floor(T(l) * 2^16 / T_kept),
+ *     and the rounding remainder goes to the best kept label;
+ *   - a vertex without edges joins its own community: {(v, 2^16)};
+ *   - changed = vertices whose best label differs from the previous
+ *     iteration's; converged iff changed <= tolerance * n (the paper's RAK
+ *     style test, which it prefers over the original one);
+ *   - synchronous and wave-ordered asynchronous updates as for RAK;
+ *   - the result is every vertex's best label (disjoint communities).
+ */
+#define ORACLE_COPRA_ONE 65536u
+
+typedef struct {
+    int32_t *slot_of; /* [n] label -> index into the lists below, -1 if absent */
+    int32_t *label;   /* [max_deg * L] labels in order of first appearance */
+    uint64_t *t;      /* summed w * b */
+    int64_t *first;   /* first appearance index */
+} oracle_cmap;
+
+/* keep 1 when candidate slot a comes before slot b as the best label */
+static int oracle_copra_better(const oracle_cmap *m, int32_t a, int32_t b, int strict,
+                               uint64_t seed, int64_t t_iter, int32_t v)
+{
+    if (m->t[a] != m->t[b]) return m->t[a] > m->t[b];
+    if (!strict) {
+        uint64_t ha = oracle_tie_hash(seed, t_iter, v, m->label[a]);
+        uint64_t hb = oracle_tie_hash(seed, t_iter, v, m->label[b]);
+        if (ha != hb) return ha < hb;
+    }
+    return m->first[a] < m->first[b];
+}
+
+/* new set of listener v from the sets `src` of its neighbours (src_l / src_b:
+ * n * L entries, b = 0 ends a set); writes L entries at out_l / out_b */
+static void oracle_copra_listen(oracle_cmap *m, int32_t v, const int32_t *offsets,
+                                const int32_t *indices, const int32_t *weights,
+                                const int32_t *const *src_l, const uint32_t *const *src_b,
+                                int32_t waves, int32_t k_wave, int32_t L, int strict, uint64_t seed,
+                                int64_t t_iter, int32_t *out_l, uint32_t *out_b)
+{
+    int32_t begin = offsets[v], end = offsets[v + 1];
+    for (int32_t s = 0; s < L; ++s) {
+        out_l[s] = -1;
+        out_b[s] = 0;
+    }
+    if (begin == end) { /* no labels: the vertex joins its own community */
+        out_l[0] = v;
+        out_b[0] = ORACLE_COPRA_ONE;
+        return;
+    }
+    int32_t count = 0;
+    int64_t k = 0;
+    uint64_t W = 0;
+    for (int32_t e = begin; e < end; ++e) {
+        int32_t u = indices[e];
+        uint64_t w = weights ? (uint64_t)weights[e] : 1u;
+        W += w;
+        int which = (u % waves) < k_wave ? 1 : 0; /* earlier wave: this iteration's set */
+        const int32_t *ul = src_l[which] + (size_t)u * L;
+        const uint32_t *ub = src_b[which] + (size_t)u * L;
+        for (int32_t p = 0; p < L && ub[p] != 0; ++p, ++k) {
+            int32_t l = ul[p];
+            int32_t s = m->slot_of[l];
+            if (s < 0) {
+                s = count++;
+                m->slot_of[l] = s;
+                m->label[s] = l;
+                m->t[s] = 0;
+                m->first[s] = k;
+            }
+            m->t[s] += w * (uint64_t)ub[p];
+        }
+    }
+    /* the kept labels: above the threshold, else the best alone */
+    int32_t kept[64], nk = 0;
+    for (int32_t s = 0; s < count; ++s)
+        if ((uint64_t)L * m->t[s] >= W * (uint64_t)ORACLE_COPRA_ONE) kept[nk++] = s;
+    if (nk == 0) {
+        int32_t best = 0;
+        for (int32_t s = 1; s < count; ++s)
+            if (oracle_copra_better(m, s, best, strict, seed, t_iter, v)) best = s;
+        kept[nk++] = best;
+    }
+    /* normalize, the remainder to the best kept label */
+    uint64_t tk = 0;
+    for (int32_t i = 0; i < nk; ++i) tk += m->t[kept[i]];
+    uint32_t bsum = 0, bval[64];
+    int32_t best_i = 0;
+    for (int32_t i = 0; i < nk; ++i) {
+        bval[i] = (uint32_t)((m->t[kept[i]] * (uint64_t)ORACLE_COPRA_ONE) / tk);
+        bsum += bval[i];
+        if (i > 0 && oracle_copra_better(m, kept[i], kept[best_i], strict, seed, t_iter, v))
+            best_i = i;
+    }
+    bval[best_i] += ORACLE_COPRA_ONE - bsum;
+    /* store by decreasing belonging, equal belongings by first appearance */
+    for (int32_t i = 0; i < nk; ++i) {
+        int32_t pick = -1;
+        for (int32_t j = 0; j < nk; ++j) {
+            if (kept[j] < 0) continue;
+            if (pick < 0 || bval[j] > bval[pick] ||
+                (bval[j] == bval[pick] && m->first[kept[j]] < m->first[kept[pick]]))
+                pick = j;
+        }
+        out_l[i] = m->label[kept[pick]];
+        out_b[i] = bval[pick];
+        kept[pick] = -1;
+    }
+    for (int32_t s = 0; s < count; ++s) m->slot_of[m->label[s]] = -1;
+}
+
+/* COPRA on an n-vertex CSR (max_labels 1 .. 64; waves as in oracle_rak, 0 or
+ * >= n = the plain in-place ascending order, mode 0 sync).  sets_l / sets_b
+ * (n * max_labels each): the final sets, b = 0 after a set's last pair.
+ * labels: the best label of every vertex.  changed_hist: capacity max_iter.
+ * Returns 0, or -1 on bad input or allocation failure. */
+int oracle_copra(int32_t n, const int32_t *offsets, const int32_t *indices, const int32_t *weights,
+                 int32_t max_labels, double tolerance, int32_t max_iter, int mode, int32_t waves,
+                 int strict, uint64_t seed, int32_t *sets_l, uint32_t *sets_b, int32_t *labels,
+                 int32_t *iterations, int32_t *converged, int64_t *changed_hist)
+{
+    if (n < 0 || max_labels < 1 || max_labels > 64 || max_iter < 1) return -1;
+    const int32_t L = max_labels;
+    const size_t cells = (size_t)(n > 0 ? n : 1) * (size_t)L;
+    int64_t dmax = oracle_max_degree(n, offsets);
+    int32_t *buf_l[2] = {(int32_t *)malloc(cells * sizeof(int32_t)),
+                         (int32_t *)malloc(cells * sizeof(int32_t))};
+    uint32_t *buf_b[2] = {(uint32_t *)malloc(cells * sizeof(uint32_t)),
+                          (uint32_t *)malloc(cells * sizeof(uint32_t))};
+    oracle_cmap m;
+    size_t lists = (size_t)(dmax > 0 ? dmax : 1) * (size_t)L;
+    m.slot_of = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    m.label = (int32_t *)malloc(sizeof(int32_t) * lists);
+    m.t = (uint64_t *)malloc(sizeof(uint64_t) * lists);
+    m.first = (int64_t *)malloc(sizeof(int64_t) * lists);
+    int rc = 0;
+    if (!buf_l[0] || !buf_l[1] || !buf_b[0] || !buf_b[1] || !m.slot_of ||
+        !m.label || !m.t || !m.first) {
+        rc = -1;
+        goto done;
+    }
+    for (int32_t v = 0; v < n; ++v) {
+        m.slot_of[v] = -1;
+        for (int32_t s = 0; s < L; ++s) {
+            buf_l[0][(size_t)v * L + s] = s == 0 ? v : -1;
+            buf_b[0][(size_t)v * L + s] = s == 0 ? ORACLE_COPRA_ONE : 0;
+        }
+    }
+    int32_t W = mode == 0 ? 1 : (waves <= 0 || waves > n ? (n > 0 ? n : 1) : waves);
+    *iterations = 0;
+    *converged = 0;
+    int cur = 0;
+    for (int32_t it = 0; it < max_iter; ++it) {
+        int nxt = cur ^ 1;
+        const int32_t *src_l[2] = {buf_l[cur], buf_l[nxt]};
+        const uint32_t *src_b[2] = {buf_b[cur], buf_b[nxt]};
+        int64_t changed = 0;
+        /* wave k reads the new sets of earlier waves, the previous ones otherwise */
+        for (int32_t k = 0; k < W; ++k) {
+            for (int32_t v = k; v < n; v += W) {
+                oracle_copra_listen(&m, v, offsets, indices, weights, src_l, src_b, W, k, L,
+                                    strict, seed, it, buf_l[nxt] + (size_t)v * L,
+                                    buf_b[nxt] + (size_t)v * L);
+                if (buf_l[nxt][(size_t)v * L] != buf_l[cur][(size_t)v * L]) ++changed;
+            }
+        }
+        cur = nxt;
+        if (changed_hist) changed_hist[it] = changed;
+        *iterations = it + 1;
+        if ((double)changed <= tolerance * (double)n) {
+            *converged = 1;
+            break;
+        }
+    }
+    for (int32_t v = 0; v < n; ++v) {
+        labels[v] = buf_l[cur][(size_t)v * L];
+        if (sets_l)
+            for (int32_t s = 0; s < L; ++s) {
+                sets_l[(size_t)v * L + s] = buf_l[cur][(size_t)v * L + s];
+                sets_b[(size_t)v * L + s] = buf_b[cur][(size_t)v * L + s];
+            }
+    }
+done:
+    free(buf_l[0]);
+    free(buf_l[1]);
+    free(buf_b[0]);
+    free(buf_b[1]);
+    free(m.slot_of);
+    free(m.label);
+    free(m.t);
+    free(m.first);
+    return rc;
+}

@@ -16,6 +16,6 @@ from ._binding import (  # noqa: F401
     lp_last_error, lp_launch_count, lp_modularity, lp_profile_enable, lp_profile_read,
     lp_profile_reset, lp_rak_history, lp_rak_params, lp_selftest_barrier_timeout,
     lp_rak_params_default, lp_rak_result, lp_rak_run, lp_rak_sweep_noalloc, lp_serve_result,
-    lp_slpa_memory_get, lp_slpa_params, lp_slpa_run, lp_split_communities,
+    lp_probe_gather, lp_slpa_memory_get, lp_slpa_params, lp_slpa_run, lp_split_communities,
     lp_server_config, lp_server_config_default, lp_server_create, lp_server_destroy,
     lp_server_drain, lp_server_poll, lp_server_submit, lp_tune_result, make_params)

@@ -141,6 +141,9 @@ SIGNATURES = {
     "lp_slpa_run": (ctypes.c_int, [_P, ctypes.POINTER(lp_slpa_params),
                                    ctypes.POINTER(lp_rak_result)]),
     "lp_slpa_memory_get": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int32]),
+    "lp_probe_gather": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, _P, _P, _P,
+                                       ctypes.c_int32, ctypes.c_int32, _P,
+                                       ctypes.POINTER(ctypes.c_float), _P]),
     "lp_split_communities": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
     "lp_selftest_barrier_timeout": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int32)]),
     "lp_last_error": (ctypes.c_char_p, []),
@@ -511,6 +514,22 @@ def lp_slpa_memory_get(handle: int, slots: int, out=None):
     _check(load().lp_slpa_memory_get(handle, ptr, int(slots), 1 if on_dev else 0))
     del keep
     return out
+
+
+def lp_probe_gather(n, indices, weights, labels, mode=1, repeats=20, stream=None) -> float:
+    """Milliseconds per pass streaming indices and weights (mode 0), or also
+    gathering labels[index] per entry (mode 1); CUDA tensors."""
+    import torch
+
+    sink = torch.zeros(2, dtype=torch.int32, device=indices.device)
+    ms = ctypes.c_float()
+    if stream is None:
+        stream = _stream_of(indices)
+    _check(load().lp_probe_gather(int(n), int(indices.shape[0]), indices.data_ptr(),
+                                  None if weights is None else weights.data_ptr(),
+                                  labels.data_ptr(), int(mode), int(repeats), sink.data_ptr(),
+                                  ctypes.byref(ms), stream))
+    return float(ms.value)
 
 
 def lp_split_communities(handle: int) -> int:

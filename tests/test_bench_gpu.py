@@ -33,3 +33,29 @@ def test_split_study_lines():
     r = rows[0]
     assert r["communities_after"] >= r["communities_before"] >= 1
     assert r["modularity_after"] >= r["modularity_before"] - 1e-9
+
+
+def test_gather_ceiling_lines():
+    rows = run_bench("--experiment", "gather", "--classes", "sbm10k")
+    assert len(rows) == 4  # numbering x (stream, stream + gather)
+    assert {r["numbering"] for r in rows} == {"as generated", "by decreasing degree"}
+    for r in rows:
+        assert r["ms"] > 0 and r["hbm_frac"] > 0
+
+
+def test_probe_rejects_out_of_range_indices():
+    import numpy as np
+    import torch
+
+    sys.path.insert(0, ROOT)
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2301_09125_gb300 as lp
+
+    dev = torch.device("cuda")
+    idx = torch.from_numpy(np.array([0, 1, 2, 3, 1, 2, 3, 9], np.int32)).to(dev)
+    lab = torch.arange(4, dtype=torch.int32, device=dev)
+    with pytest.raises(lp.LPError, match="outside"):
+        lp.lp_probe_gather(4, idx, None, lab, mode=1)
+    assert lp.lp_probe_gather(4, idx[:4].contiguous(), None, lab, mode=1, repeats=2) > 0
