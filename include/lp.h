@@ -310,6 +310,50 @@ lp_status lp_server_drain(lp_server *s);
 lp_status lp_server_destroy(lp_server *s);
 
 /* ---------------------------------------------------------------------------
+ * COPRA: community overlap propagation (Sec. 3.3)
+ * ------------------------------------------------------------------------- */
+
+/* COPRA parameters. */
+typedef struct {
+    int32_t max_labels; /* pairs a vertex keeps at most, 1 .. 64 (the paper tries 1-32) */
+    double tolerance;   /* stop once at most tolerance * n vertices changed their best
+                           label; [0, 1] (the paper suggests 0.01) */
+    int32_t max_iter;   /* >= 1 */
+    int32_t mode;       /* LP_SYNC or LP_ASYNC (waves as in lp_rak_params) */
+    int32_t waves;      /* >= 1 in LP_ASYNC */
+    int32_t strict;     /* tie rule for the best label, as in lp_rak_params */
+    uint64_t seed;      /* non-strict tie key */
+} lp_copra_params;
+
+/* max_labels 4, tolerance 0.01, max_iter 20, LP_ASYNC with 31 waves, strict,
+ * seed 0.  Errors: LP_EINVAL on NULL. */
+lp_status lp_copra_params_default(lp_copra_params *p);
+
+/* Run COPRA on a graph (Sec. 3.3).  Every vertex holds at most max_labels
+ * (label, belonging) pairs, belongings in units of 2^-16 that sum to exactly
+ * 2^16, stored by decreasing belonging (equal ones by first appearance), the
+ * first pair being the vertex's best label; it starts as {(v, 2^16)}.  In an
+ * iteration v sums T(l) = sum of w * b over its row's entries (u, w) and the
+ * pairs (l, b) of u's set (its own labels are not added), keeps the labels
+ * with max_labels * T(l) >= W * 2^16 (W: the row's summed weight), else the
+ * best label alone (largest T; ties by the strict rule on first appearance,
+ * or the non-strict tie key of iteration t), and stores the kept T divided
+ * by their sum in fixed point (floor; the remainder to the best kept).  A
+ * vertex without edges is its own community.  The run stops once at most
+ * tolerance * n best labels changed, or after max_iter iterations.  The
+ * graph's labels (lp_labels_get, lp_modularity) become the best labels; out
+ * as for lp_rak_run, lp_rak_history gives the changed counts.
+ * Errors: LP_EINVAL for NULL arguments, parameters out of range, or a row too
+ * long for max_labels (its table would exceed 2^28 slots); LP_ENOMEM; LP_ECUDA. */
+lp_status lp_copra_run(lp_graph *g, const lp_copra_params *p, lp_rak_result *out);
+
+/* The sets of the last COPRA run: n x max_labels labels and belongings
+ * (row-major, belonging 0 after a set's last pair; host or device by
+ * dst_on_device).  Errors: LP_EINVAL (NULL, or no COPRA run yet); LP_ECUDA. */
+lp_status lp_copra_sets_get(lp_graph *g, int32_t *labels, uint32_t *belongings,
+                            int32_t dst_on_device);
+
+/* ---------------------------------------------------------------------------
  * SLPA: speaker-listener label propagation (Sec. 3.4)
  * ------------------------------------------------------------------------- */
 

@@ -86,6 +86,12 @@ class lp_tune_result(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class lp_copra_params(ctypes.Structure):
+    _fields_ = [("max_labels", ctypes.c_int32), ("tolerance", ctypes.c_double),
+                ("max_iter", ctypes.c_int32), ("mode", ctypes.c_int32), ("waves", ctypes.c_int32),
+                ("strict", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+
 class lp_slpa_params(ctypes.Structure):
     _fields_ = [("memory_size", ctypes.c_int32), ("tolerance", ctypes.c_double),
                 ("strict", ctypes.c_int32), ("seed", ctypes.c_uint64)]
@@ -137,6 +143,10 @@ SIGNATURES = {
     "lp_rak_sweep_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, _P, _P, _P, _P, _P,
                                             ctypes.c_int32, ctypes.c_uint64, ctypes.c_int32,
                                             ctypes.POINTER(ctypes.c_int64), _P]),
+    "lp_copra_params_default": (ctypes.c_int, [ctypes.POINTER(lp_copra_params)]),
+    "lp_copra_run": (ctypes.c_int, [_P, ctypes.POINTER(lp_copra_params),
+                                    ctypes.POINTER(lp_rak_result)]),
+    "lp_copra_sets_get": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32]),
     "lp_slpa_params_default": (ctypes.c_int, [ctypes.POINTER(lp_slpa_params)]),
     "lp_slpa_run": (ctypes.c_int, [_P, ctypes.POINTER(lp_slpa_params),
                                    ctypes.POINTER(lp_rak_result)]),
@@ -491,6 +501,32 @@ def lp_last_error() -> str:
     return load().lp_last_error().decode(errors="replace")
 
 
+def lp_copra_run(handle: int, max_labels=4, tolerance=0.01, max_iter=20, mode="async", waves=31,
+                 strict=True, seed=0) -> lp_rak_result:
+    """Run COPRA (Sec. 3.3) on a graph; its labels become the best labels."""
+    p = lp_copra_params()
+    _check(load().lp_copra_params_default(ctypes.byref(p)))
+    p.max_labels = int(max_labels)
+    p.tolerance = float(tolerance)
+    p.max_iter = int(max_iter)
+    p.mode = {"sync": LP_SYNC, "async": LP_ASYNC}[mode] if isinstance(mode, str) else int(mode)
+    p.waves = int(waves)
+    p.strict = 1 if strict else 0
+    p.seed = int(seed) & (2**64 - 1)
+    r = lp_rak_result()
+    _check(load().lp_copra_run(handle, ctypes.byref(p), ctypes.byref(r)))
+    return r
+
+
+def lp_copra_sets_get(handle: int, max_labels: int):
+    """(labels, belongings) of the last COPRA run as (n, max_labels) arrays."""
+    n, _ = lp_graph_info(handle)
+    lab = np.empty((n, max_labels), dtype=np.int32)
+    bel = np.empty((n, max_labels), dtype=np.uint32)
+    _check(load().lp_copra_sets_get(handle, lab.ctypes.data, bel.ctypes.data, 0))
+    return lab, bel
+
+
 def lp_slpa_run(handle: int, memory_size=20, tolerance=0.05, strict=True, seed=0) -> lp_rak_result:
     """Run SLPA (Sec. 3.4) on a graph; its labels become the communities."""
     p = lp_slpa_params()
@@ -566,6 +602,13 @@ class Graph:
 
     def split(self) -> int:
         return lp_split_communities(self.handle)
+
+    def copra(self, **kw) -> lp_rak_result:
+        self._copra_labels = kw.get("max_labels", 4)
+        return lp_copra_run(self.handle, **kw)
+
+    def copra_sets(self):
+        return lp_copra_sets_get(self.handle, getattr(self, "_copra_labels", 4))
 
     def slpa(self, **kw) -> lp_rak_result:
         return lp_slpa_run(self.handle, **kw)

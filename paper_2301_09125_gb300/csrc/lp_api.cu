@@ -258,6 +258,15 @@ struct GraphSet {
     // SLPA (Sec. 3.4): memory slots (slpa_slots x nv, slot t of v at t * nv + v)
     // and the labels spoken to every packed entry in the current iteration
     int32_t *slpa_mem = nullptr, *spoken = nullptr;
+    // COPRA (Sec. 3.3): two set buffers (nv x copra_L pairs), which one holds
+    // the last run's sets, and the global tables of long rows
+    int32_t *cset_l[2] = {nullptr, nullptr};
+    uint32_t *cset_b[2] = {nullptr, nullptr};
+    int32_t copra_L = 0, copra_cur = 0, copra_cap = 0;
+    int32_t *ctab_key = nullptr;
+    unsigned long long *ctab_sum = nullptr, *ctab_first = nullptr;
+    int32_t ctab_lg = 0;
+    int32_t max_deg = 0;  // longest row (single graphs)
     int32_t slpa_slots = 0, slpa_filled = 0;
     bool slpa_on = false;
     int32_t *cpos = nullptr;   // rows left by a pre-pass (nv) and their count, open long rows
@@ -333,6 +342,19 @@ struct GraphSet {
         f(slpa_mem);
         f(spoken);
         slpa_mem = spoken = nullptr;
+        for (int b = 0; b < 2; ++b) {
+            f(cset_l[b]);
+            f(cset_b[b]);
+            cset_l[b] = nullptr;
+            cset_b[b] = nullptr;
+        }
+        copra_L = copra_cap = 0;
+        f(ctab_key);
+        f(ctab_sum);
+        f(ctab_first);
+        ctab_key = nullptr;
+        ctab_sum = ctab_first = nullptr;
+        ctab_lg = 0;
         slpa_slots = slpa_filled = 0;
         f(pk_rp);
         f(pk_first);
@@ -411,7 +433,7 @@ struct GraphSet {
         st = (cudaStream_t)stream;
         static std::atomic<uint64_t> prepared{0};
         if (device < 64 && !(prepared.load() & (1ull << device))) {
-            if (sweep_prepare() != 0 || wave_prepare() != 0)
+            if (sweep_prepare() != 0 || wave_prepare() != 0 || copra_prepare() != 0)
                 return fail(LP_ECUDA, "setting kernel attributes failed");
             prepared |= (1ull << device);
         }
@@ -473,6 +495,7 @@ struct GraphSet {
             LP_TRY(read_ingest(-1));
         }
         rows_distinct = h_ing->repeated == 0;
+        max_deg = h_ing->max_deg;
         return LP_OK;
     }
 
@@ -1470,6 +1493,118 @@ struct GraphSet {
         return LP_OK;
     }
 
+    // COPRA (Sec. 3.3) on a single graph: every vertex starts as its own
+    // community; each iteration (in waves when asynchronous) computes every
+    // vertex's set from its neighbours' sets; the tolerance test counts the
+    // vertices whose best label changed.  The graph's labels become the best
+    // labels.
+    lp_status copra(const lp_copra_params *p)
+    {
+        if (!p) return fail(LP_EINVAL, "params is NULL");
+        if (p->max_labels < 1 || p->max_labels > 64)
+            return fail(LP_EINVAL, "max_labels must lie in [1, 64]");
+        if (!(p->tolerance >= 0.0 && p->tolerance <= 1.0))
+            return fail(LP_EINVAL, "tolerance must lie in [0, 1]");
+        if (p->max_iter < 1) return fail(LP_EINVAL, "max_iter must be >= 1");
+        if (p->mode != LP_SYNC && p->mode != LP_ASYNC)
+            return fail(LP_EINVAL, "mode must be LP_SYNC or LP_ASYNC");
+        if (p->mode == LP_ASYNC && p->waves < 1) return fail(LP_EINVAL, "waves must be >= 1");
+        if (G != 1) return fail(LP_EINVAL, "COPRA runs on single graphs");
+        const int32_t L = p->max_labels;
+        const int32_t waves = p->mode == LP_ASYNC ? std::min(p->waves, std::max(nv, 1)) : 1;
+        const int glg = copra_table_lg(max_deg, L);
+        if (glg > 28) return fail(LP_EINVAL, "a row holds too many labels for max_labels");
+        if (copra_cap < L) {
+            for (int b = 0; b < 2; ++b) {
+                if (cset_l[b]) cudaFreeAsync(cset_l[b], st);
+                if (cset_b[b]) cudaFreeAsync(cset_b[b], st);
+                cset_l[b] = nullptr;
+                cset_b[b] = nullptr;
+            }
+            copra_cap = 0;
+            for (int b = 0; b < 2; ++b) {
+                LP_TRY(dev_alloc(&cset_l[b], (int64_t)nv * L, "COPRA sets", st, device));
+                LP_TRY(dev_alloc(&cset_b[b], (int64_t)nv * L, "COPRA sets", st, device));
+            }
+            copra_cap = L;
+        }
+        if (glg > ctab_lg) {
+            if (ctab_key) cudaFreeAsync(ctab_key, st);
+            if (ctab_sum) cudaFreeAsync(ctab_sum, st);
+            if (ctab_first) cudaFreeAsync(ctab_first, st);
+            ctab_key = nullptr;
+            ctab_sum = ctab_first = nullptr;
+            ctab_lg = 0;
+            const int64_t slots = (int64_t)copra_big_ctas() << glg;
+            LP_TRY(dev_alloc(&ctab_key, slots, "COPRA long-row tables", st, device));
+            LP_TRY(dev_alloc(&ctab_sum, slots, "COPRA long-row tables", st, device));
+            LP_TRY(dev_alloc(&ctab_first, slots, "COPRA long-row tables", st, device));
+            LP_CU(cudaMemsetAsync(ctab_key, 0xFF, (size_t)slots * sizeof(int32_t), st));
+            LP_CU(cudaMemsetAsync(ctab_sum, 0, (size_t)slots * sizeof(unsigned long long), st));
+            LP_CU(cudaMemsetAsync(ctab_first, 0xFF, (size_t)slots * sizeof(unsigned long long),
+                                  st));
+            ctab_lg = glg;
+        }
+        LP_TRY(ensure_changed(p->max_iter));
+        LP_CU(cudaMemsetAsync(changed, 0, (size_t)p->max_iter * sizeof(int32_t), st));
+        LP_CU(cudaEventRecord(ev0, st));
+        Launches L0;
+        if (copra_init(cset_l[0], cset_b[0], nv, L, st, &L0.n) != 0)
+            return fail(LP_ECUDA, cuda_msg("COPRA init", cudaGetLastError()));
+        int cur = 0;
+        int32_t iters = 0, conv = 0;
+        int64_t last = 0;
+        history.clear();
+        for (int32_t it = 0; it < p->max_iter; ++it) {
+            CopraStep cs{};
+            cs.off = off;
+            cs.idx = idx;
+            cs.wts = wts;
+            cs.n = nv;
+            cs.L = L;
+            cs.cur_l = cset_l[cur];
+            cs.cur_b = cset_b[cur];
+            cs.nxt_l = cset_l[cur ^ 1];
+            cs.nxt_b = cset_b[cur ^ 1];
+            cs.waves = waves;
+            cs.strict = p->strict ? 1 : 0;
+            cs.key_t = stream_at(p->seed, (uint64_t)it + 1);  // the tie key of iteration it
+            cs.changed = changed + it;
+            cs.gkey = ctab_key;
+            cs.gsum = ctab_sum;
+            cs.gfirst = ctab_first;
+            cs.glg_max = glg;
+            for (int32_t k = 0; k < waves; ++k) {
+                cs.wave_k = k;
+                if (copra_step(cs, num_sms, st, &L0.n) != 0)
+                    return fail(LP_ECUDA, cuda_msg("COPRA launch", cudaGetLastError()));
+            }
+            cur ^= 1;
+            LP_CU(cudaMemcpyAsync(h_changed + it, changed + it, sizeof(int32_t),
+                                  cudaMemcpyDeviceToHost, st));
+            LP_CU(cudaStreamSynchronize(st));
+            iters = it + 1;
+            last = h_changed[it];
+            history.push_back(last);
+            if ((double)last <= p->tolerance * (double)nv) {  // the RAK-style test
+                conv = 1;
+                break;
+            }
+        }
+        copra_L = L;
+        copra_cur = cur;
+        if (copra_best(cset_l[cur], nv, L, lab[0], st, &L0.n) != 0)
+            return fail(LP_ECUDA, cuda_msg("COPRA labels", cudaGetLastError()));
+        LP_CU(cudaEventRecord(ev1, st));
+        LP_CU(cudaEventSynchronize(ev1));
+        float ms = 0.f;
+        LP_CU(cudaEventElapsedTime(&ms, ev0, ev1));
+        std::fill(final_buf.begin(), final_buf.end(), 0);
+        q_valid = false;
+        results[0] = lp_rak_result{iters, conv, last, ms};
+        return LP_OK;
+    }
+
     // Graphs of a batch stop in different iterations, so their final labels
     // sit in either buffer; copy them all into buffer 0.
     lp_status gather_final_labels()
@@ -1725,6 +1860,46 @@ lp_status lp_rak_run(lp_graph *g, const lp_rak_params *p, lp_rak_result *out)
     DeviceGuard dg(g->s.device);
     LP_TRY(g->s.run(p, false));
     *out = g->s.results[0];
+    return LP_OK;
+}
+
+lp_status lp_copra_params_default(lp_copra_params *p)
+{
+    if (!p) return fail(LP_EINVAL, "params is NULL");
+    p->max_labels = 4;
+    p->tolerance = 0.01;
+    p->max_iter = 20;
+    p->mode = LP_ASYNC;
+    p->waves = 31;
+    p->strict = 1;
+    p->seed = 0;
+    return LP_OK;
+}
+
+lp_status lp_copra_run(lp_graph *g, const lp_copra_params *p, lp_rak_result *out)
+{
+    if (!g) return fail(LP_EINVAL, "graph is NULL");
+    if (!out) return fail(LP_EINVAL, "result is NULL");
+    DeviceGuard dg(g->s.device);
+    LP_TRY(g->s.copra(p));
+    *out = g->s.results[0];
+    return LP_OK;
+}
+
+lp_status lp_copra_sets_get(lp_graph *g, int32_t *labels, uint32_t *belongings,
+                            int32_t dst_on_device)
+{
+    if (!g) return fail(LP_EINVAL, "graph is NULL");
+    lp::GraphSet &s = g->s;
+    if (s.copra_L == 0) return fail(LP_EINVAL, "no COPRA run on this graph");
+    if ((!labels || !belongings) && s.nv > 0) return fail(LP_EINVAL, "labels or belongings is NULL");
+    if (s.nv == 0) return LP_OK;
+    DeviceGuard dg(s.device);
+    const size_t cells = (size_t)s.nv * s.copra_L;
+    const cudaMemcpyKind kind = dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    LP_CU(cudaMemcpyAsync(labels, s.cset_l[s.copra_cur], cells * sizeof(int32_t), kind, s.st));
+    LP_CU(cudaMemcpyAsync(belongings, s.cset_b[s.copra_cur], cells * sizeof(uint32_t), kind, s.st));
+    LP_CU(cudaStreamSynchronize(s.st));
     return LP_OK;
 }
 

@@ -370,6 +370,38 @@ int slpa_speak(const int64_t *rp, const int32_t *list, const int64_t *first_row,
 int slpa_community(const int32_t *mem, int32_t n, int32_t last, int32_t *out, cudaStream_t st,
                    int64_t *launches);
 
+// COPRA (Sec. 3.3), lp_copra.cu: one iteration (or one wave of it) of a
+// single graph.  Sets: L (label, belonging) pairs per vertex, belongings in
+// units of 2^-16 summing to COPRA_ONE, belonging 0 after a set's last pair.
+constexpr uint32_t COPRA_ONE = 65536u;
+struct CopraStep {
+    const int32_t *off, *idx, *wts;  // the original CSR
+    int32_t n, L;
+    const int32_t *cur_l;            // previous iteration's sets
+    const uint32_t *cur_b;
+    int32_t *nxt_l;                  // this iteration's sets
+    uint32_t *nxt_b;
+    int32_t waves, wave_k;           // wave_k of waves (1: synchronous)
+    int strict;
+    uint64_t key_t;                  // non-strict key of the iteration
+    int32_t *changed;                // += vertices whose best label changed
+    // rows of more than the shared table's pairs: copra_big_ctas() tables of
+    // 2^glg_max slots (key -1, sum 0, first ~0 when clean; left clean)
+    int32_t *gkey;
+    unsigned long long *gsum, *gfirst;
+    int32_t glg_max;                 // 0: no such row
+};
+int copra_prepare();
+int copra_init(int32_t *l, uint32_t *b, int32_t n, int32_t L, cudaStream_t st, int64_t *launches);
+// out[v] = the best (first) label of v's set
+int copra_best(const int32_t *l, int32_t n, int32_t L, int32_t *out, cudaStream_t st,
+               int64_t *launches);
+// log2 of the slots a row of max_degree entries needs in the global tables
+// (0 when every row fits the shared table)
+int copra_table_lg(int64_t max_degree, int32_t L);
+int copra_big_ctas();
+int copra_step(const CopraStep &s, int num_sms, cudaStream_t st, int64_t *launches);
+
 // Split the communities of lab (n vertices, m entries, one graph) into
 // connected components in place: lab[v] = smallest vertex of v's component.
 // parent: n scratch ints; *err set to 1 if a link gave up; big: two scratch
