@@ -43,6 +43,9 @@ one JSON line per setting (iterations, convergence, run time, GTEPS,
 modularity of the labels on the graph without self-loops).
 ``--experiment split`` times the split of disconnected communities after
 each class's benchmark run (communities and modularity before and after).
+``--experiment copra`` / ``--experiment slpa`` time COPRA (Sec. 3.3, 4 labels,
+tolerance 0.01) and SLPA (Sec. 3.4, memory of 20) on each class, with their
+first iteration checked against the oracle at full size.
 ``--experiment gather`` measures the ceiling of a label-gathering sweep: one
 pass streaming the rows, and one that also gathers every entry's neighbour
 label, on each class as generated and renumbered by decreasing degree.
@@ -116,7 +119,8 @@ def parse():
                     help="single-graph workloads: leave out the serve sub-record")
     ap.add_argument("--per-graph-sample", type=int, default=256,
                     help="graphs of the batch timed one at a time")
-    ap.add_argument("--experiment", choices=["tolerance", "split", "gather"], default=None,
+    ap.add_argument("--experiment", choices=["tolerance", "split", "gather", "copra", "slpa"],
+                    default=None,
                     help="run the tolerance / tie-rule study, or time the split of "
                          "disconnected communities, instead of the benchmark")
     ap.add_argument("--classes", default="sbm10k,rmat22,road4096,kmer8m",
@@ -271,7 +275,7 @@ def traffic_ratio(kernel):
     """DRAM traffic / algorithmic bytes of a bucket launch from the committed
     ncu summary, or None when the sweep sources changed since it was taken."""
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles",
-                        "dram_traffic_rmat21_async_w2.md")
+                        "dram_traffic_rmat22_async_w2.md")
     try:
         lines = [ln.split() for ln in open(path) if ln.strip().startswith(("traffic_ratio",
                                                                            "sweep_sources"))]
@@ -497,8 +501,8 @@ def run_ours(args):
                 "frac": achieved / peak,
                 "traffic": None if ratio is None else ratio * dom["bytes"] / dom["launches"],
                 "kernel": dom_name, "peak_source": peak_kind,
-                "traffic_source": "profiles/dram_traffic_rmat21_async_w2.md (ratio to "
-                                  "algorithmic bytes, scaled to this launch)"}
+                "traffic_source": "profiles/dram_traffic_rmat22_async_w2.md (ratio to "
+                                  "algorithmic bytes over a whole run, applied to this launch)"}
     line = {
         "metric": f"RAK GTEPS ({args.workload})", "value": value, "unit": "GTEPS",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -1114,6 +1118,132 @@ def run_split_experiment(args):
     return 0
 
 
+# COPRA (Sec. 3.3) and SLPA (Sec. 3.4) on the synthetic classes
+METHOD_DEFAULTS = {
+    # the paper's suggestion for COPRA: tolerance 0.01, 4 labels for
+    # non-road graphs, asynchronous updates (each class's wave count)
+    "copra": dict(max_labels=4, tolerance=0.01, max_iter=20),
+    "slpa": dict(memory_size=20, tolerance=0.05),
+}
+
+
+def method_alg_bytes(method, g, max_labels):
+    """Algorithmic HBM bytes of one iteration: the CSR once (4 (n + 1) + 4 or
+    8 per entry); COPRA reads the previous sets and writes the new ones (8
+    bytes per pair and vertex each way: label and belonging, every speaker's
+    set counted once); SLPA reads the previous slot and writes the new one (4
+    per vertex each)."""
+    csr = 4 * (g.n + 1) + (8 if g.weights is not None else 4) * g.m
+    if method == "copra":
+        return csr + 16 * max_labels * g.n
+    return csr + 8 * g.n
+
+
+def run_method_experiment(args):
+    """COPRA or SLPA on each class: one run to convergence timed with CUDA
+    events on the library's stream (best of 3 after a warm-up run), GTEPS
+    (iterations x m / run time), the iteration's algorithmic bytes against
+    the measured HBM peak, the first iteration compared with the oracle at
+    full size, and the oracle's first iteration timed as the CPU baseline."""
+    import torch
+
+    import oracle
+    import paper_2301_09125_gb300 as lp
+    from paper_2301_09125_gb300 import build
+
+    method = args.experiment
+    build.build()
+    lp.load()
+    oracle.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    peak, peak_kind = measured_peak_gbs()
+    d = METHOD_DEFAULTS[method]
+    for name in [c for c in args.classes.split(",") if c]:
+        g = gen_graph(name)
+        p = WORKLOADS[name]
+        arrs = [torch.from_numpy(a).to(dev) if a is not None else None
+                for a in (g.offsets, g.indices, g.weights)]
+        h = lp.lp_graph_create(*arrs, borrow=True, stream=stream.cuda_stream)
+        if method == "copra":
+            kw = dict(max_labels=d["max_labels"], tolerance=d["tolerance"],
+                      max_iter=d["max_iter"], mode=p["mode"], waves=p["waves"],
+                      strict=p["strict"], seed=1)
+            run = lambda **o: lp.lp_copra_run(h, **{**kw, **o})  # noqa: E731
+            settings = {k: kw[k] for k in ("max_labels", "tolerance", "max_iter", "mode",
+                                           "strict")}
+            settings["waves"] = p["waves"] if p["mode"] == "async" else 1
+        else:
+            kw = dict(memory_size=d["memory_size"], tolerance=d["tolerance"],
+                      strict=p["strict"], seed=1)
+            run = lambda **o: lp.lp_slpa_run(h, **{**kw, **o})  # noqa: E731
+            settings = dict(kw, mode="sync")
+            settings.pop("seed")
+        # first iteration against the oracle, full arrays (and its CPU time)
+        o_waves = p["waves"] if p["mode"] == "async" else 0
+        t0 = time.perf_counter()
+        if method == "copra":
+            _, ref_l, ref_b, _, _, _ = oracle.copra(
+                g.offsets, g.indices, g.weights, max_labels=kw["max_labels"], tolerance=0.0,
+                max_iter=1, mode=p["mode"], waves=o_waves, strict=p["strict"], seed=1)
+        else:
+            _, ref_mem, _, _, _ = oracle.slpa(g.offsets, g.indices, g.weights, memory_size=2,
+                                              tolerance=0.0, strict=p["strict"], seed=1)
+        cpu_s = time.perf_counter() - t0
+        if method == "copra":
+            run(max_iter=1, tolerance=0.0)
+            sl, sb = lp.lp_copra_sets_get(h, kw["max_labels"])
+            exact = bool(np.array_equal(sb, ref_b) and
+                         np.array_equal(np.where(ref_b > 0, sl, 0), np.where(ref_b > 0, ref_l, 0)))
+            del sl, sb, ref_l, ref_b
+        else:
+            run(memory_size=2, tolerance=0.0)
+            exact = bool(np.array_equal(lp.lp_slpa_memory_get(h, 2), ref_mem))
+            del ref_mem
+        run()  # warm-up: scratch allocation
+        launches0 = lp.lp_launch_count()
+        clocks = ClockSampler(nvsmi_id(torch, 0), enabled=not args.no_clocks)
+        best = None
+        for _ in range(3):
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = run()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            if best is None or ms < best[0]:
+                best = (ms, r.iterations, bool(r.converged))
+        clock_info = clocks.stop()
+        launches = (lp.lp_launch_count() - launches0) // 3
+        q = lp.lp_modularity(h)
+        lp.lp_graph_destroy(h)
+        ms, iters, conv = best
+        alg = method_alg_bytes(method, g, kw.get("max_labels", 1))
+        it_ms = ms / max(iters, 1)
+        achieved = alg / (it_ms * 1e-3) / 1e9
+        print(json.dumps({
+            "experiment": method, "metric": f"{method.upper()} GTEPS ({name})",
+            "workload": name, "n": g.n, "m": g.m, **settings,
+            "iterations": iters, "converged": conv, "run_ms": ms, "ms_per_iteration": it_ms,
+            "value": iters * g.m / (ms * 1e-3) / 1e9, "unit": "GTEPS", "modularity": q,
+            "first_iteration_bit_exact": exact,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "whole iteration", "alg_bytes": alg,
+                         "peak_source": peak_kind},
+            "cpu_baseline": {"value": g.m / cpu_s / 1e9, "unit": "GTEPS", "cores": 1,
+                             "kind": "oracle",
+                             "sample": f"first iteration on the full graph ({cpu_s:.1f} s, "
+                                       f"single thread)"},
+            "gpu_launches": launches, "clocks": clock_info}), flush=True)
+        del arrs
+        torch.cuda.empty_cache()
+    return 0
+
+
 def degree_renumbered(g):
     """The graph with vertices renumbered by decreasing degree (stable), rows
     in the new order: a layout where the most gathered labels sit together."""
@@ -1162,11 +1292,15 @@ def run_gather_experiment(args):
             lab = torch.arange(g.n, dtype=torch.int32, device=dev)
             for mode in (0, 1):
                 ms = lp.lp_probe_gather(g.n, t_idx, t_w, lab, mode=mode, repeats=20)
+                moved = (4 if w is None else 8) * m4  # the bytes the pass streams
                 print(json.dumps({"experiment": "gather", "workload": name, "n": g.n, "m": g.m,
                                   "numbering": numbering,
                                   "pass": "stream" if mode == 0 else "stream + label gather",
                                   "ms": ms, "g_entries_per_s": g.m / (ms * 1e-3) / 1e9,
-                                  "alg_gbs": alg / (ms * 1e-3) / 1e9,
+                                  "moved_gbs": moved / (ms * 1e-3) / 1e9,
+                                  "moved_frac": moved / (ms * 1e-3) / 1e9 / peak,
+                                  "l2_resident": moved < L2_BYTES,
+                                  "sweep_alg_gbs": alg / (ms * 1e-3) / 1e9,
                                   "hbm_frac": alg / (ms * 1e-3) / 1e9 / peak,
                                   "peak_gbs": peak, "peak_source": peak_kind}), flush=True)
             del t_idx, t_w, lab
@@ -1179,6 +1313,8 @@ def main():
         return run_gather_experiment(args)
     if args.experiment == "split":
         return run_split_experiment(args)
+    if args.experiment in ("copra", "slpa"):
+        return run_method_experiment(args)
     if args.experiment:
         return run_experiment(args)
     if args.workload == "serve":

@@ -7,10 +7,10 @@
 //   Q   = L / 2m - S / (2m)^2   (formed in double on the host)
 //
 // The entry pass streams the packed rows (the sweep's layout: rows in list
-// order, contiguous) in chunks of PACK_CHUNK entries, one block per chunk:
-// the block stages the rows that meet its chunk (their starts, labels and
-// graphs) in shared memory, and every thread takes eight consecutive
-// entries, gathers their neighbours' labels and sums L and 2m in registers.
+// order, contiguous) in chunks of PACK_CHUNK entries, one warp per chunk:
+// the warp stages the rows that meet its chunk (their starts, labels and
+// graphs) in shared memory, and every lane takes eight consecutive entries,
+// gathers their neighbours' labels and sums L and 2m in registers.
 // A row's weights within the chunk are summed in shared memory and added to
 // K of the row's community: a row split over several chunks adds one part
 // from each, which sums to the same K.  Rows of one community in a chunk

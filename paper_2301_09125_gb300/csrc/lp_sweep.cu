@@ -27,12 +27,16 @@
 // warp-wide __match_any_sync merge of equal labels before insertion cost more
 // than the atomics it saved); the one label a warp sees most once labels have
 // settled is summed in registers instead (HotLabel).
-// Every table slot holds (label, summed weight, ~first position); the first
-// position of a label is the smallest row position at which it occurs, so the
-// argmax key (weight desc, [non-strict key asc,] first position asc) is unique
-// and independent of the order in which entries were accumulated.  Weights
-// are summed in int32 (the library rejects graphs whose per-vertex weight sum
-// reaches 2^31), so synchronous results are bit-exact.
+// A warp or CTA table slot is one 64-bit word, (label + 1) << 32 | summed
+// weight: claimed by a 64-bit compare-and-swap, summed by a 32-bit add on its
+// low word.  A label's first position (the smallest row position at which it
+// occurs) is found only for the labels tied at the maximum, by a second pass
+// over the row; the hub segment and partition tables keep (label, summed
+// weight, ~first position) records.  Either way the argmax key (weight desc,
+// [non-strict key asc,] first position asc) is unique and independent of the
+// order in which entries were accumulated.  Weights are summed in int32 (the
+// library rejects graphs whose per-vertex weight sum reaches 2^31), so
+// results are bit-exact.
 #include "lp_device.cuh"
 #include "lp_internal.cuh"
 

@@ -57,7 +57,7 @@ def test_traffic_summary_is_well_formed():
     sys.path.insert(0, ROOT)
     import bench
 
-    path = os.path.join(ROOT, "profiles", "dram_traffic_rmat21_async_w2.md")
+    path = os.path.join(ROOT, "profiles", "dram_traffic_rmat22_async_w2.md")
     lines = [ln.split() for ln in open(path)
              if ln.strip().startswith(("traffic_ratio", "sweep_sources"))]
     ratios = {x[1]: float(x[2]) for x in lines if x[0] == "traffic_ratio"}
