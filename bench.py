@@ -258,16 +258,28 @@ def gather_results(local, world):
     return merged
 
 
+def code_lines(text):
+    """The lines of a C/CUDA source without its // comments and blank lines
+    (what the compiler sees, up to whitespace at the line ends)."""
+    out = []
+    for line in text.splitlines():
+        code = line.split("//", 1)[0].rstrip()
+        if code.strip():
+            out.append(code)
+    return "\n".join(out)
+
+
 def sweep_sources_hash():
-    """First 16 hex digits of the SHA-256 of the sweep kernel sources."""
+    """First 16 hex digits of the SHA-256 of the sweep kernel sources' code
+    (comments and blank lines left out, so a comment edit keeps the hash)."""
     import hashlib
 
     h = hashlib.sha256()
     csrc = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2301_09125_gb300",
                         "csrc")
     for f in ("lp_sweep.cu", "lp_device.cuh", "lp_internal.cuh"):
-        with open(os.path.join(csrc, f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(csrc, f), encoding="utf-8") as fh:
+            h.update(code_lines(fh.read()).encode())
     return h.hexdigest()[:16]
 
 
