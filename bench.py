@@ -929,6 +929,7 @@ def measure_serve(args, ctx):
     makespan = time.perf_counter() - start
     clock_info = clocks.stop()
     launches = lp.lp_launch_count() - launches0
+    cohorts = lp.lp_server_stats(srv)
     lp.lp_server_destroy(srv)
     local = {r.request_id: (r.latency_ms, r.queued_ms, r.status, r.iterations) for r in done}
     merged = gather_results(local, ctx.world)
@@ -968,6 +969,7 @@ def measure_serve(args, ctx):
     lp.lp_server_drain(srv)
     sat_span = time.perf_counter() - sstart
     sat_done = lp.lp_server_poll(srv, capacity=len(sat_picks) + 1)
+    sat_cohorts = lp.lp_server_stats(srv)
     lp.lp_server_destroy(srv)
     sat_err = sum(1 for r in sat_done if r.status != 0)
     sstart = time.perf_counter()
@@ -988,6 +990,7 @@ def measure_serve(args, ctx):
         "config": {"workload": "serve", **p, "requests": n_all, "window_s": args.serve_seconds,
                    "pool_graphs": len(pool), "pool_generation_s": round(gen_s, 1),
                    "max_active": cfg.max_active, "streams": cfg.streams,
+                   "max_cohort": cfg.max_cohort,
                    "hbm_budget_gib": cfg.hbm_budget >> 30,
                    "l2": "graphs resident per request, no flush",
                    "parallelism": (f"requests sharded over {ctx.world} ranks"
@@ -1003,8 +1006,10 @@ def measure_serve(args, ctx):
         "saturation": {"requests": len(sat_picks), "errors": sat_err,
                        "served_graphs_per_s": len(sat_picks) / sat_span,
                        "per_graph_launch_graphs_per_s": len(sat_picks) / seq_span,
+                       "cohorts": sat_cohorts,
                        "how": "all requests submitted at t=0; the per-graph arm runs the same "
                               "requests one after another through lp_graph_create/lp_rak_run"},
+        "cohorts": cohorts,
         "gpu_launches": int(launches),
         "clocks": clock_info,
         "e2e": {"value": len(merged) / makespan, "unit": "graphs/s",

@@ -249,21 +249,30 @@ lp_status lp_batch_modularity(lp_batch *b, int32_t index, double *q);
 /* ---------------------------------------------------------------------------
  * Serving: a request server with continuous batching.
  * Each request is one graph run with the server's parameters.  An admission
- * thread admits a queued request when fewer than max_active requests are on
- * the device and its estimated footprint (about 40 n + 88 m bytes) fits the
- * HBM budget still free, and ingests it on one of the server's streams; a
- * worker thread advances every admitted request one RAK iteration (Sec. 3.2)
- * at a time, interleaved with the others; a converged request is retired
- * (modularity, labels) as soon as it finishes, and queued requests take its
- * place.  A request's result is the same as that of lp_rak_run on its graph
- * alone.
+ * thread admits queued requests while fewer than max_active requests are on
+ * the device and their estimated footprints (about 40 n + 88 m bytes each)
+ * fit the HBM budget still free.  The requests it finds queued together, up
+ * to max_cohort of them, form one cohort: a lone request is ingested as a
+ * graph, several as one batch arena (lp_batch_create), on one of the
+ * server's streams.  A worker thread advances every cohort one RAK iteration
+ * (Sec. 3.2) at a time, interleaved with the other cohorts; an iteration of
+ * a cohort is one launch per degree bucket for all of its graphs, and graphs
+ * that have converged are left out of its later iterations.  When a cohort's
+ * last graph has finished, its requests are retired (modularity, labels) and
+ * queued requests take their places.  A request's result is the same as
+ * that of lp_rak_run on its graph alone.  If a cohort's batch cannot be
+ * ingested (an invalid graph), its requests are ingested one by one, so that
+ * only the invalid ones fail.
  * ------------------------------------------------------------------------- */
 typedef struct lp_server lp_server;
 
 typedef struct {
     int64_t hbm_budget; /* device bytes admitted requests may hold together (default 8 GiB) */
     int32_t max_active; /* requests on the device at once (default 64) */
-    int32_t streams;    /* CUDA streams the requests are spread over, 1..64 (default 8) */
+    int32_t streams;    /* CUDA streams the cohorts are spread over, 1..64 (default 8) */
+    int32_t max_cohort; /* requests ingested and iterated together, >= 1 (default 16;
+                           1 = every request on its own) */
+    int32_t reserved;   /* 0 */
 } lp_server_config;
 
 typedef struct {
@@ -301,6 +310,11 @@ lp_status lp_server_submit(lp_server *s, int64_t request_id, int32_t n, int64_t 
  * Returns LP_ENOTREADY when none was available.  Thread-safe. */
 lp_status lp_server_poll(lp_server *s, lp_serve_result *out, int32_t capacity, int32_t *count,
                          int32_t wait_ms);
+
+/* Cohorts formed so far, requests that ran in a cohort of two or more (one
+ * batch arena), and the largest cohort.  Thread-safe.
+ * Errors: LP_EINVAL on NULL. */
+lp_status lp_server_stats(lp_server *s, int64_t *cohorts, int64_t *batched, int64_t *largest);
 
 /* Block until every submitted request has a result.  Errors: LP_EINVAL on NULL. */
 lp_status lp_server_drain(lp_server *s);

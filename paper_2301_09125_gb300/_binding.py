@@ -57,7 +57,8 @@ class lp_graph_desc(ctypes.Structure):
 
 class lp_server_config(ctypes.Structure):
     _fields_ = [("hbm_budget", ctypes.c_int64), ("max_active", ctypes.c_int32),
-                ("streams", ctypes.c_int32)]
+                ("streams", ctypes.c_int32), ("max_cohort", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class lp_serve_result(ctypes.Structure):
@@ -135,6 +136,9 @@ SIGNATURES = {
     "lp_server_poll": (ctypes.c_int, [_P, ctypes.POINTER(lp_serve_result), ctypes.c_int32,
                                       ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]),
     "lp_server_drain": (ctypes.c_int, [_P]),
+    "lp_server_stats": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64),
+                                       ctypes.POINTER(ctypes.c_int64),
+                                       ctypes.POINTER(ctypes.c_int64)]),
     "lp_server_destroy": (ctypes.c_int, [_P]),
     "lp_profile_enable": (ctypes.c_int, [ctypes.c_int32]),
     "lp_profile_reset": (ctypes.c_int, []),
@@ -445,6 +449,14 @@ def lp_server_poll(handle: int, capacity: int = 256, wait_ms: int = 0) -> list:
     if st not in (LP_OK, LP_ENOTREADY):
         _check(st)
     return [out[i] for i in range(cnt.value)]
+
+
+def lp_server_stats(handle: int) -> dict:
+    """Cohorts formed so far, requests that ran in a cohort of two or more,
+    and the largest cohort."""
+    c, b, m = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(load().lp_server_stats(handle, ctypes.byref(c), ctypes.byref(b), ctypes.byref(m)))
+    return {"cohorts": c.value, "batched_requests": b.value, "largest_cohort": m.value}
 
 
 def lp_server_drain(handle: int) -> None:

@@ -1701,6 +1701,13 @@ bool graph_run_done(lp_graph *g);
 lp_status graph_run_launch(lp_graph *g, cudaEvent_t *done_event);
 lp_status graph_run_finish(lp_graph *g);
 lp_status graph_run_end(lp_graph *g, lp_rak_result *r);
+// The same for every graph of a batch at once (converged graphs are left out
+// of later iterations on the device; per_graph receives count results).
+lp_status batch_run_begin(lp_batch *b, const lp_rak_params *p);
+bool batch_run_done(lp_batch *b);
+lp_status batch_run_launch(lp_batch *b, cudaEvent_t *done_event);
+lp_status batch_run_finish(lp_batch *b);
+lp_status batch_run_end(lp_batch *b, lp_rak_result *per_graph);
 
 void lp_add_launches(int64_t n) { g_launches += n; }
 
@@ -1734,6 +1741,31 @@ lp_status graph_run_end(lp_graph *g, lp_rak_result *r)
     DeviceGuard dg(g->s.device);
     LP_TRY(g->s.run_end());
     *r = g->s.results[0];
+    return LP_OK;
+}
+lp_status batch_run_begin(lp_batch *b, const lp_rak_params *p)
+{
+    DeviceGuard dg(b->s.device);
+    return b->s.run_begin(p, true);
+}
+bool batch_run_done(lp_batch *b) { return b->s.run_done(); }
+lp_status batch_run_launch(lp_batch *b, cudaEvent_t *done_event)
+{
+    DeviceGuard dg(b->s.device);
+    LP_TRY(b->s.run_launch());
+    *done_event = b->s.ev_iter;
+    return LP_OK;
+}
+lp_status batch_run_finish(lp_batch *b)
+{
+    DeviceGuard dg(b->s.device);
+    return b->s.run_finish();
+}
+lp_status batch_run_end(lp_batch *b, lp_rak_result *per_graph)
+{
+    DeviceGuard dg(b->s.device);
+    LP_TRY(b->s.run_end());
+    for (int32_t i = 0; i < b->s.G; ++i) per_graph[i] = b->s.results[(size_t)i];
     return LP_OK;
 }
 }  // namespace lp

@@ -1,16 +1,20 @@
 // Continuous-batching request server (lp_server_*).
 //
 // Requests (one graph each, host CSR) queue up as they are submitted.  An
-// admission thread takes a queued request as soon as an active slot is free
-// and its estimated device footprint fits the HBM budget, and ingests it on
-// one of the server's CUDA streams.  A worker thread advances every ingested
-// request one RAK iteration at a time: whenever a request's in-flight
-// iteration has finished on the device (event query), the worker applies the
-// tolerance test and either launches its next iteration or retires it
-// (modularity, labels copied to the caller's buffer, result queued for
-// lp_server_poll).  Requests therefore join and leave between iterations while
-// the kernels of the others keep running on their streams, and ingest never
-// holds up the launches; each result is the same as a lone lp_rak_run.
+// admission thread takes the requests queued at that moment, as many as the
+// free active slots, the HBM budget and max_cohort allow, and ingests them
+// as one cohort on one of the server's CUDA streams: a lone request as a
+// graph, several as one batch arena, whose iterations sweep every graph with
+// one launch per degree bucket.  A worker thread advances every cohort one
+// RAK iteration at a time: whenever a cohort's in-flight iteration has
+// finished on the device (event query), it applies the tolerance test to
+// each of its graphs (a converged graph is left out of later iterations) and
+// either launches the next iteration or, once every graph has finished,
+// retires the cohort's requests (modularity, labels copied to the callers'
+// buffers, results queued for lp_server_poll).  Requests therefore join
+// between iterations of the running cohorts, ingest never holds up their
+// launches, and each result is the same as a lone lp_rak_run.
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -31,6 +35,11 @@ bool graph_run_done(lp_graph *g);
 lp_status graph_run_launch(lp_graph *g, cudaEvent_t *done_event);
 lp_status graph_run_finish(lp_graph *g);
 lp_status graph_run_end(lp_graph *g, lp_rak_result *r);
+lp_status batch_run_begin(lp_batch *b, const lp_rak_params *p);
+bool batch_run_done(lp_batch *b);
+lp_status batch_run_launch(lp_batch *b, cudaEvent_t *done_event);
+lp_status batch_run_finish(lp_batch *b);
+lp_status batch_run_end(lp_batch *b, lp_rak_result *per_graph);
 }  // namespace lp
 
 namespace {
@@ -50,10 +59,16 @@ struct Request {
     int32_t *labels_out = nullptr;
     int64_t footprint = 0;
     Clock::time_point t_submit, t_admit;
-    lp_graph *g = nullptr;
-    cudaEvent_t ev = nullptr;  // end of the in-flight iteration (owned by the graph)
-    bool in_flight = false;
     lp_serve_result res{};
+};
+
+// Requests ingested and iterated together: one graph, or one batch arena.
+struct Cohort {
+    std::vector<std::unique_ptr<Request>> reqs;
+    lp_graph *g = nullptr;  // a lone request
+    lp_batch *b = nullptr;  // several
+    cudaEvent_t ev = nullptr;  // end of the in-flight iteration (owned by the graph set)
+    bool in_flight = false;
 };
 
 // device bytes a request may hold: CSR, two label buffers, bucket and wave
@@ -77,25 +92,22 @@ struct lp_server {
 
     std::mutex mu;
     std::condition_variable cv_work, cv_done, cv_admit;
-    std::deque<std::unique_ptr<Request>> queue;    // submitted, not yet admitted
-    std::deque<std::unique_ptr<Request>> ready;    // ingested, not yet picked up
+    std::deque<std::unique_ptr<Request>> queue;  // submitted, not yet admitted
+    std::deque<std::unique_ptr<Cohort>> ready;   // ingested, not yet picked up
     std::deque<lp_serve_result> results;
     int64_t outstanding = 0;  // submitted, result not yet queued
     int64_t slots_used = 0;   // admitted, not yet retired
     int64_t mem_used = 0;     // footprint of the admitted requests
+    int64_t n_cohorts = 0, n_batched = 0, max_cohort_seen = 0;  // lp_server_stats
     bool stop = false;
     std::thread worker, admitter;
 
-    std::vector<std::unique_ptr<Request>> active;  // worker thread only
+    std::vector<std::unique_ptr<Cohort>> active;  // worker thread only
 
     void retire(std::unique_ptr<Request> r, lp_status st)
     {
         r->res.status = st;
         r->res.latency_ms = ms_since(r->t_submit);
-        if (r->g) {
-            lp_graph_destroy(r->g);
-            r->g = nullptr;
-        }
         std::lock_guard<std::mutex> lock(mu);
         mem_used -= r->footprint;
         --slots_used;
@@ -105,64 +117,145 @@ struct lp_server {
         cv_admit.notify_one();
     }
 
-    // ingest and start a request; false if it failed (already retired)
-    bool admit(std::unique_ptr<Request> &r)
+    // free a cohort's graph set, then retire its requests (st[i] per request)
+    void retire_cohort(std::unique_ptr<Cohort> c, const std::vector<lp_status> &st)
     {
-        r->t_admit = Clock::now();
-        r->res.queued_ms = std::chrono::duration<double, std::milli>(r->t_admit - r->t_submit).count();
-        cudaStream_t st = streams[(size_t)next_stream];
-        next_stream = (next_stream + 1) % (int)streams.size();
-        lp_status s = lp_graph_create(r->n, r->m, r->off, r->idx, r->wts, 0, st, &r->g);
-        if (s == LP_OK) s = lp::graph_run_begin(r->g, &params);
-        if (s != LP_OK) {
-            retire(std::move(r), s);
-            return false;
-        }
-        return true;
+        if (c->g) lp_graph_destroy(c->g);
+        if (c->b) lp_batch_destroy(c->b);
+        c->g = nullptr;
+        c->b = nullptr;
+        for (size_t i = 0; i < c->reqs.size(); ++i) retire(std::move(c->reqs[i]), st[i]);
+    }
+    void retire_cohort(std::unique_ptr<Cohort> c, lp_status st)
+    {
+        const std::vector<lp_status> all(c->reqs.size(), st);
+        retire_cohort(std::move(c), all);
     }
 
-    // advance one request by at most one iteration; false once retired
-    bool advance(std::unique_ptr<Request> &r, bool *progressed)
+    cudaStream_t take_stream()
+    {
+        cudaStream_t st = streams[(size_t)next_stream];
+        next_stream = (next_stream + 1) % (int)streams.size();
+        return st;
+    }
+
+    // ingest a lone request and start its run; null if it failed (retired)
+    std::unique_ptr<Cohort> admit_one(std::unique_ptr<Request> r)
+    {
+        std::unique_ptr<Cohort> c(new Cohort);
+        c->reqs.push_back(std::move(r));
+        lp_status s = lp_graph_create(c->reqs[0]->n, c->reqs[0]->m, c->reqs[0]->off,
+                                      c->reqs[0]->idx, c->reqs[0]->wts, 0, take_stream(), &c->g);
+        if (s == LP_OK) s = lp::graph_run_begin(c->g, &params);
+        if (s != LP_OK) {
+            retire_cohort(std::move(c), s);
+            return nullptr;
+        }
+        return c;
+    }
+
+    // ingest requests taken from the queue together, as one cohort when
+    // there are several and their batch ingests; otherwise one by one
+    void admit(std::vector<std::unique_ptr<Request>> take)
+    {
+        const Clock::time_point now = Clock::now();
+        for (auto &r : take) {
+            r->t_admit = now;
+            r->res.queued_ms = std::chrono::duration<double, std::milli>(now - r->t_submit).count();
+        }
+        std::vector<std::unique_ptr<Cohort>> made;
+        if (take.size() > 1) {
+            std::vector<lp_graph_desc> d(take.size());
+            for (size_t i = 0; i < take.size(); ++i)
+                d[i] = lp_graph_desc{take[i]->n, take[i]->m, take[i]->off, take[i]->idx,
+                                     take[i]->wts};
+            std::unique_ptr<Cohort> c(new Cohort);
+            lp_status s = lp_batch_create((int32_t)take.size(), d.data(), 0, take_stream(), &c->b);
+            if (s == LP_OK) s = lp::batch_run_begin(c->b, &params);
+            if (s == LP_OK) {
+                c->reqs = std::move(take);
+                take.clear();
+                made.push_back(std::move(c));
+            } else if (c->b) {
+                lp_batch_destroy(c->b);
+                c->b = nullptr;
+            }
+        }
+        for (auto &r : take)  // a lone request, or a cohort that did not ingest
+            if (r) {
+                std::unique_ptr<Cohort> c = admit_one(std::move(r));
+                if (c) made.push_back(std::move(c));
+            }
+        if (made.empty()) return;
+        std::lock_guard<std::mutex> lock(mu);
+        for (auto &c : made) {
+            const int64_t k = (int64_t)c->reqs.size();
+            ++n_cohorts;
+            if (k > 1) n_batched += k;
+            max_cohort_seen = std::max(max_cohort_seen, k);
+            ready.push_back(std::move(c));
+        }
+        cv_work.notify_one();
+    }
+
+    // advance a cohort by at most one iteration; false once retired
+    bool advance(std::unique_ptr<Cohort> &c, bool *progressed)
     {
         lp_status s = LP_OK;
-        if (r->in_flight) {
-            const cudaError_t q = cudaEventQuery(r->ev);
+        if (c->in_flight) {
+            const cudaError_t q = cudaEventQuery(c->ev);
             if (q == cudaErrorNotReady) return true;
+            c->in_flight = false;
+            *progressed = true;
             if (q != cudaSuccess) {
-                retire(std::move(r), LP_ECUDA);
+                retire_cohort(std::move(c), LP_ECUDA);
                 return false;
             }
-            r->in_flight = false;
-            *progressed = true;
-            s = lp::graph_run_finish(r->g);
+            s = c->g ? lp::graph_run_finish(c->g) : lp::batch_run_finish(c->b);
         }
-        if (s == LP_OK && !lp::graph_run_done(r->g)) {
-            s = lp::graph_run_launch(r->g, &r->ev);
+        if (s == LP_OK && !(c->g ? lp::graph_run_done(c->g) : lp::batch_run_done(c->b))) {
+            s = c->g ? lp::graph_run_launch(c->g, &c->ev) : lp::batch_run_launch(c->b, &c->ev);
             if (s == LP_OK) {
-                r->in_flight = true;
+                c->in_flight = true;
                 *progressed = true;
                 return true;
             }
         }
-        if (s == LP_OK) {
-            lp_rak_result rr{};
-            s = lp::graph_run_end(r->g, &rr);
-            r->res.iterations = rr.iterations;
-            r->res.converged = rr.converged;
-            if (s == LP_OK) s = lp_modularity(r->g, nullptr, 0, &r->res.modularity);
-            if (s == LP_OK && r->labels_out) s = lp_labels_get(r->g, r->labels_out, 0);
-        }
         *progressed = true;
-        retire(std::move(r), s);
+        std::vector<lp_status> st(c->reqs.size(), s);
+        if (s == LP_OK && c->g) {
+            lp_rak_result rr{};
+            Request &r = *c->reqs[0];
+            lp_status e = lp::graph_run_end(c->g, &rr);
+            r.res.iterations = rr.iterations;
+            r.res.converged = rr.converged;
+            if (e == LP_OK) e = lp_modularity(c->g, nullptr, 0, &r.res.modularity);
+            if (e == LP_OK && r.labels_out) e = lp_labels_get(c->g, r.labels_out, 0);
+            st[0] = e;
+        } else if (s == LP_OK) {
+            std::vector<lp_rak_result> rr(c->reqs.size());
+            lp_status e = lp::batch_run_end(c->b, rr.data());
+            for (size_t i = 0; i < c->reqs.size(); ++i) {
+                Request &r = *c->reqs[i];
+                lp_status ei = e;
+                r.res.iterations = rr[i].iterations;
+                r.res.converged = rr[i].converged;
+                if (ei == LP_OK) ei = lp_batch_modularity(c->b, (int32_t)i, &r.res.modularity);
+                if (ei == LP_OK && r.labels_out)
+                    ei = lp_batch_labels_get(c->b, (int32_t)i, r.labels_out, 0);
+                st[i] = ei;
+            }
+        }
+        retire_cohort(std::move(c), st);
         return false;
     }
 
-    // admission thread: slot and budget check, then ingest on a stream
+    // admission thread: slot and budget checks, then ingest on a stream
     void admit_loop()
     {
         cudaSetDevice(device);
         for (;;) {
-            std::unique_ptr<Request> r;
+            std::vector<std::unique_ptr<Request>> take;
             {
                 std::unique_lock<std::mutex> lock(mu);
                 cv_admit.wait(lock, [this] {
@@ -170,21 +263,25 @@ struct lp_server {
                                     mem_used + queue.front()->footprint <= cfg.hbm_budget);
                 });
                 if (stop && queue.empty()) return;
-                if (queue.empty()) continue;
-                r = std::move(queue.front());
-                queue.pop_front();
-                mem_used += r->footprint;
-                ++slots_used;
+                // the requests queued now, in order, while slots and budget last
+                // (and a batch's vertex ids stay below 2^31)
+                int64_t nv = 0;
+                while (!queue.empty() && (int64_t)take.size() < cfg.max_cohort &&
+                       slots_used < cfg.max_active &&
+                       mem_used + queue.front()->footprint <= cfg.hbm_budget &&
+                       nv + queue.front()->n + (int64_t)take.size() + 1 < 2147483647LL) {
+                    nv += queue.front()->n;
+                    mem_used += queue.front()->footprint;
+                    ++slots_used;
+                    take.push_back(std::move(queue.front()));
+                    queue.pop_front();
+                }
             }
-            if (admit(r)) {
-                std::lock_guard<std::mutex> lock(mu);
-                ready.push_back(std::move(r));
-                cv_work.notify_one();
-            }
+            if (!take.empty()) admit(std::move(take));
         }
     }
 
-    // worker thread: advance every ingested request by iterations
+    // worker thread: advance every ingested cohort by iterations
     void run()
     {
         cudaSetDevice(device);
@@ -209,7 +306,7 @@ struct lp_server {
                 }
             }
             if (!progressed && !active.empty()) {
-                // nothing finished: wait briefly for a newly ingested request
+                // nothing finished: wait briefly for a newly ingested cohort
                 std::unique_lock<std::mutex> lock(mu);
                 cv_work.wait_for(lock, std::chrono::microseconds(20),
                                  [this] { return !ready.empty(); });
@@ -226,6 +323,8 @@ lp_status lp_server_config_default(lp_server_config *cfg)
     cfg->hbm_budget = (int64_t)8 << 30;
     cfg->max_active = 64;
     cfg->streams = 8;
+    cfg->max_cohort = 16;
+    cfg->reserved = 0;
     return LP_OK;
 }
 
@@ -234,8 +333,10 @@ lp_status lp_server_create(const lp_server_config *cfg, const lp_rak_params *p, 
     if (!out) return lp::lp_fail(LP_EINVAL, "out is NULL");
     *out = nullptr;
     if (!cfg || !p) return lp::lp_fail(LP_EINVAL, "cfg or params is NULL");
-    if (cfg->hbm_budget <= 0 || cfg->max_active < 1 || cfg->streams < 1 || cfg->streams > 64)
-        return lp::lp_fail(LP_EINVAL, "hbm_budget > 0, max_active >= 1, 1 <= streams <= 64");
+    if (cfg->hbm_budget <= 0 || cfg->max_active < 1 || cfg->streams < 1 || cfg->streams > 64 ||
+        cfg->max_cohort < 1)
+        return lp::lp_fail(LP_EINVAL,
+                           "hbm_budget > 0, max_active >= 1, 1 <= streams <= 64, max_cohort >= 1");
     if (p->init_labels) return lp::lp_fail(LP_EINVAL, "served requests start from unique labels");
     if (!(p->tolerance >= 0.0 && p->tolerance <= 1.0) || p->max_iter < 1 ||
         (p->mode != LP_SYNC && p->mode != LP_ASYNC) || (p->mode == LP_ASYNC && p->waves < 1))
@@ -306,6 +407,16 @@ lp_status lp_server_poll(lp_server *s, lp_serve_result *out, int32_t capacity, i
     }
     *count = k;
     return k > 0 ? LP_OK : LP_ENOTREADY;
+}
+
+lp_status lp_server_stats(lp_server *s, int64_t *cohorts, int64_t *batched, int64_t *largest)
+{
+    if (!s || !cohorts || !batched || !largest) return lp::lp_fail(LP_EINVAL, "bad arguments");
+    std::lock_guard<std::mutex> lock(s->mu);
+    *cohorts = s->n_cohorts;
+    *batched = s->n_batched;
+    *largest = s->max_cohort_seen;
+    return LP_OK;
 }
 
 lp_status lp_server_drain(lp_server *s)
