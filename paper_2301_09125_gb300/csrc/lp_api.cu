@@ -266,6 +266,11 @@ struct GraphSet {
     int32_t *ctab_key = nullptr;
     unsigned long long *ctab_sum = nullptr, *ctab_first = nullptr;
     int32_t ctab_lg = 0;
+    // rows that take a CTA, by kind and wave (copra_rows), and the bins' starts
+    int32_t *crows = nullptr, *cbins = nullptr;
+    int64_t cbins_cap = 0;
+    std::vector<int32_t> h_cbins;
+    std::vector<int64_t> h_cstart;
     int32_t max_deg = 0;  // longest row (single graphs)
     int32_t slpa_slots = 0, slpa_filled = 0;
     bool slpa_on = false;
@@ -355,6 +360,10 @@ struct GraphSet {
         ctab_key = nullptr;
         ctab_sum = ctab_first = nullptr;
         ctab_lg = 0;
+        f(crows);
+        f(cbins);
+        crows = cbins = nullptr;
+        cbins_cap = 0;
         slpa_slots = slpa_filled = 0;
         f(pk_rp);
         f(pk_first);
@@ -1546,9 +1555,24 @@ struct GraphSet {
             ctab_lg = glg;
         }
         LP_TRY(ensure_changed(p->max_iter));
+        // the rows that take a CTA, by kind and wave
+        const int64_t nbins = copra_bins(waves);
+        if (!crows) LP_TRY(dev_alloc(&crows, std::max(nv, 1), "COPRA row lists", st, device));
+        if (cbins_cap < nbins) {
+            if (cbins) cudaFreeAsync(cbins, st);
+            cbins = nullptr;
+            cbins_cap = 0;
+            LP_TRY(dev_alloc(&cbins, nbins, "COPRA row lists", st, device));
+            cbins_cap = nbins;
+        }
+        h_cbins.resize((size_t)nbins);
+        h_cstart.resize((size_t)nbins + 1);
+        Launches L0;
+        if (copra_rows(off, nv, L, waves, cbins, h_cbins.data(), h_cstart.data(), crows, st,
+                       &L0.n) != 0)
+            return fail(LP_ECUDA, cuda_msg("COPRA row lists", cudaGetLastError()));
         LP_CU(cudaMemsetAsync(changed, 0, (size_t)p->max_iter * sizeof(int32_t), st));
         LP_CU(cudaEventRecord(ev0, st));
-        Launches L0;
         if (copra_init(cset_l[0], cset_b[0], nv, L, st, &L0.n) != 0)
             return fail(LP_ECUDA, cuda_msg("COPRA init", cudaGetLastError()));
         int cur = 0;
@@ -1576,6 +1600,10 @@ struct GraphSet {
             cs.glg_max = glg;
             for (int32_t k = 0; k < waves; ++k) {
                 cs.wave_k = k;
+                cs.rows_cta = crows + h_cstart[(size_t)k];
+                cs.n_cta = h_cstart[(size_t)k + 1] - h_cstart[(size_t)k];
+                cs.rows_big = crows + h_cstart[(size_t)waves + k];
+                cs.n_big = h_cstart[(size_t)waves + k + 1] - h_cstart[(size_t)waves + k];
                 if (copra_step(cs, num_sms, st, &L0.n) != 0)
                     return fail(LP_ECUDA, cuda_msg("COPRA launch", cudaGetLastError()));
             }

@@ -12,11 +12,18 @@
 // kept label) and stores them sorted.  A vertex without edges is its own
 // community.  Asynchronous runs go in waves as RAK's do.
 //
-// One CTA per vertex: the (label, T, first appearance) table lives in shared
-// memory for rows of at most CP_PAIRS pairs and in a per-CTA region of global
-// memory for longer rows (a second launch with fewer CTAs).  A label's first
-// appearance is encoded as row position * 64 + pair index, which orders the
-// pairs as the row scan meets them.
+// Rows of at most CPW_PAIRS pairs (with L <= 32) take one warp and a
+// 256-slot table of the warp's own in shared memory; longer rows of at most
+// CP_PAIRS pairs take one CTA and a 4096-slot shared table; longer ones one
+// CTA each with a region of a global table (a launch of copra_big_ctas()
+// CTAs).  Rows that need a CTA are listed once per run, by wave and kind, so
+// that a launch visits only its own rows.  In shared memory T(l) is summed
+// exactly in two 32-bit words (the carry out of the low word is added to the
+// high word), which keeps every shared atomic a native 32-bit one; a
+// label's first appearance, row position * 64 + pair index (which orders
+// the pairs as the row scan meets them), fits 32 bits there.
+#include <type_traits>
+
 #include "lp_device.cuh"
 #include "lp_internal.cuh"
 
@@ -27,6 +34,11 @@ constexpr int CP_T = 256;
 constexpr int CP_LG = 12;
 constexpr int CP_TAB = 1 << CP_LG;    // shared slots per CTA
 constexpr int CP_PAIRS = CP_TAB / 2;  // rows of at most this many pairs use shared memory
+constexpr int CPW_LG = 8;
+constexpr int CPW_TAB = 1 << CPW_LG;    // shared slots per warp
+constexpr int CPW_PAIRS = CPW_TAB / 2;  // rows of at most this many pairs take one warp
+constexpr int CPW_WARPS = 8;            // warps per block of the warp kernel
+constexpr int CPW_MAX_L = 32;           // the warp kernel holds a set in one lane per pair
 
 struct CopraArgs {
     const int32_t *off, *idx, *wts;  // the graph's CSR (wts null = unit weights)
@@ -41,6 +53,9 @@ struct CopraArgs {
     int strict;
     uint64_t key_t;        // non-strict key of this iteration
     int32_t *changed;
+    // the rows of this wave a CTA kernel takes (list, count)
+    const int32_t *rows;
+    int64_t nrows;
     // long rows: a table of 2^glg_max slots per CTA
     int32_t *gkey;
     unsigned long long *gsum, *gfirst;
@@ -73,28 +88,14 @@ __device__ __forceinline__ CpCand cp_shfl(const CpCand &c, int o)
     return r;
 }
 
-// add (label l, value val, first appearance f) to a table of mask + 1 slots
-// (shared or global memory) that has room for every label of the row
-__device__ __forceinline__ void cp_insert(int32_t *key, unsigned long long *sum,
-                                          unsigned long long *first, int lg, int32_t l,
-                                          unsigned long long val, unsigned long long f)
+__device__ __forceinline__ CpCand cp_warp_best(CpCand c)
 {
-    const uint32_t mask = (1u << lg) - 1u;
-    volatile int32_t *vk = key;
-    uint32_t h = slot_hash(l, lg);
-    for (uint32_t i = 0; i <= mask; ++i) {
-        int32_t cur = vk[h];
-        if (cur == EMPTY) {
-            cur = atomicCAS(key + h, EMPTY, l);
-            if (cur == EMPTY) cur = l;
-        }
-        if (cur == l) {
-            atomicAdd(sum + h, val);
-            atomicMin(first + h, f);
-            return;
-        }
-        h = (h + 1) & mask;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        const CpCand y = cp_shfl(c, o);
+        if (cp_better(y, c)) c = y;
     }
+    return c;
 }
 
 __device__ __forceinline__ unsigned long long cp_warp_sum(unsigned long long v)
@@ -104,42 +105,238 @@ __device__ __forceinline__ unsigned long long cp_warp_sum(unsigned long long v)
     return v;
 }
 
-// One COPRA step for the vertices of wave wave_k whose rows hold more pairs
-// than CP_PAIRS (BIG) or at most that many (the others).
-template <bool BIG>
-__global__ void __launch_bounds__(CP_T) k_copra(CopraArgs a)
+// Wave of vertex v (0 in synchronous runs).
+__device__ __forceinline__ uint32_t cp_wave(const CopraArgs &a, int32_t v)
 {
-    extern __shared__ unsigned long long cp_smem[];
+    return a.waves > 1 ? fastmod((uint32_t)v, a.magic, a.waves) : 0u;
+}
+
+// Shared table of 2^lg slots: label, T in two 32-bit words, first appearance.
+struct CpShared {
+    int32_t *key;
+    uint32_t *lo, *hi, *first;
+    __device__ __forceinline__ unsigned long long t(int j) const
+    {
+        return ((unsigned long long)hi[j] << 32) | lo[j];
+    }
+    __device__ __forceinline__ void clear(int j) const
+    {
+        key[j] = EMPTY;
+        lo[j] = 0u;
+        hi[j] = 0u;
+        first[j] = 0xFFFFFFFFu;
+    }
+    // add (label l, value val < 2^48, first appearance f < 2^32); the table
+    // has room for every label of the row
+    __device__ __forceinline__ void add(int lg, int32_t l, unsigned long long val,
+                                        unsigned long long f) const
+    {
+        const uint32_t mask = (1u << lg) - 1u;
+        volatile int32_t *vk = key;
+        uint32_t h = slot_hash(l, lg);
+        for (uint32_t i = 0; i <= mask; ++i) {
+            int32_t cur = vk[h];
+            if (cur == EMPTY) {
+                cur = atomicCAS(key + h, EMPTY, l);
+                if (cur == EMPTY) cur = l;
+            }
+            if (cur == l) {
+                const uint32_t vlo = (uint32_t)val, vhi = (uint32_t)(val >> 32);
+                const uint32_t old = atomicAdd(lo + h, vlo);
+                // the low word wrapped: the carry goes to the high word, so
+                // hi * 2^32 + lo is the exact sum of every value added
+                const uint32_t up = vhi + (old + vlo < old ? 1u : 0u);
+                if (up) atomicAdd(hi + h, up);
+                atomicMin(first + h, (uint32_t)f);
+                return;
+            }
+            h = (h + 1) & mask;
+        }
+    }
+};
+
+// Global table region of 2^lg slots (native 64-bit atomics).
+struct CpGlobal {
+    int32_t *key;
+    unsigned long long *sum, *first;
+    __device__ __forceinline__ unsigned long long t(int64_t j) const { return sum[j]; }
+    __device__ __forceinline__ void clear(int64_t j) const
+    {
+        key[j] = EMPTY;
+        sum[j] = 0ull;
+        first[j] = ~0ull;
+    }
+    __device__ __forceinline__ void add(int lg, int32_t l, unsigned long long val,
+                                        unsigned long long f) const
+    {
+        const uint32_t mask = (1u << lg) - 1u;
+        volatile int32_t *vk = key;
+        uint32_t h = slot_hash(l, lg);
+        for (uint32_t i = 0; i <= mask; ++i) {
+            int32_t cur = vk[h];
+            if (cur == EMPTY) {
+                cur = atomicCAS(key + h, EMPTY, l);
+                if (cur == EMPTY) cur = l;
+            }
+            if (cur == l) {
+                atomicAdd(sum + h, val);
+                atomicMin(first + h, f);
+                return;
+            }
+            h = (h + 1) & mask;
+        }
+    }
+};
+
+// One COPRA step for the rows of wave wave_k with at most CPW_PAIRS pairs
+// (rows without entries included), L <= CPW_MAX_L: one warp per vertex,
+// which keeps the kept pairs one per lane.
+__global__ void __launch_bounds__(CPW_WARPS * 32) k_copra_warp(CopraArgs a)
+{
+    __shared__ int32_t s_key[CPW_WARPS * CPW_TAB];
+    __shared__ uint32_t s_lo[CPW_WARPS * CPW_TAB];
+    __shared__ uint32_t s_hi[CPW_WARPS * CPW_TAB];
+    __shared__ uint32_t s_first[CPW_WARPS * CPW_TAB];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int o = wib * CPW_TAB;
+    const CpShared tab{s_key + o, s_lo + o, s_hi + o, s_first + o};
+    for (int j = lane; j < CPW_TAB; j += 32) tab.clear(j);
+    __syncwarp();
+
+    const uint32_t L = (uint32_t)a.L;
+    const int64_t W = a.waves;
+    const int64_t nw = (int64_t)a.n > (int64_t)a.wave_k ? ((int64_t)a.n - a.wave_k + W - 1) / W : 0;
+    const int64_t tw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    uint32_t my_changed = 0;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nw; i += tw) {
+        const int32_t v = (int32_t)(a.wave_k + i * W);
+        const int32_t rs = __ldg(a.off + v), d = __ldg(a.off + v + 1) - rs;
+        const int64_t pairs = (int64_t)d * L;
+        if (pairs > CPW_PAIRS) continue;  // a CTA kernel's row (warp-uniform)
+        const int32_t prev = a.cur_l[(int64_t)v * L];
+        int32_t *out_l = a.nxt_l + (int64_t)v * L;
+        uint32_t *out_b = a.nxt_b + (int64_t)v * L;
+        if (d == 0) {  // no labels: the vertex is its own community
+            if ((uint32_t)lane < L) {
+                out_l[lane] = lane == 0 ? v : EMPTY;
+                out_b[lane] = lane == 0 ? COPRA_ONE : 0u;
+            }
+            if (lane == 0 && prev != v) ++my_changed;
+            continue;
+        }
+        const int lg = ilog2_ceil((uint32_t)(2 * pairs));  // 2^lg >= 2 pairs
+        const int slots = 1 << lg;
+        // T(l) and first appearance over the row's entries and their speakers' pairs
+        uint32_t wsum = 0u;
+        for (int32_t e = lane; e < d; e += 32) {
+            const int32_t u = __ldg(a.idx + rs + e);
+            const uint32_t w = a.wts ? (uint32_t)__ldg(a.wts + rs + e) : 1u;
+            wsum += w;
+            const bool earlier = cp_wave(a, u) < a.wave_k;
+            const int32_t *ul = (earlier ? a.nxt_l : a.cur_l) + (int64_t)u * L;
+            const uint32_t *ub = (earlier ? a.nxt_b : a.cur_b) + (int64_t)u * L;
+            for (uint32_t p = 0; p < L; ++p) {
+                const uint32_t b = ub[p];
+                if (b == 0u) break;
+                tab.add(lg, ul[p], (unsigned long long)w * b, (uint32_t)e * 64u + p);
+            }
+        }
+        wsum = __reduce_add_sync(FULL, wsum);  // < 2^31 (checked at ingest)
+        __syncwarp();
+        // the labels above the threshold, one per lane from lane 0 on, and the best label
+        const unsigned long long wt = (unsigned long long)wsum * COPRA_ONE;
+        const uint64_t ktv = stream_at(a.key_t, (uint64_t)v + 1);
+        CpCand best{0ull, 0ull, 0ull, -1};
+        int32_t mine = -1;  // the kept slot this lane holds
+        int nk = 0;
+        for (int base = 0; base < slots; base += 32) {
+            const int j = base + lane;
+            bool kept = false;
+            if (j < slots) {
+                const int32_t l = tab.key[j];
+                if (l != EMPTY) {
+                    const unsigned long long t = tab.t(j);
+                    kept = (unsigned long long)L * t >= wt;
+                    const CpCand c{t, a.strict ? 0ull : stream_at(ktv, (uint64_t)l + 1),
+                                   (unsigned long long)tab.first[j], j};
+                    if (cp_better(c, best)) best = c;
+                }
+            }
+            const unsigned m = __ballot_sync(FULL, kept);
+            const int nm = __popc(m);
+            // lane nk + k takes the slot of the k-th kept lane of this round
+            const int k = lane - nk;
+            const int src = (k >= 0 && k < nm) ? (int)__fns(m, 0, k + 1) : 0;
+            const int js = __shfl_sync(FULL, j, src);
+            if (k >= 0 && k < nm) mine = js;
+            nk += nm;  // at most L labels reach the threshold (their T sum to W * 2^16)
+        }
+        best = cp_warp_best(best);
+        if (nk > (int)L) nk = (int)L;  // never (see above); keeps the stores inside the set
+        if (nk == 0) {  // none above the threshold: the best label alone
+            mine = lane == 0 ? best.slot : -1;
+            nk = 1;
+        }
+        // normalize in fixed point, the remainder to the best label (always kept)
+        const bool hold = lane < nk;
+        const unsigned long long ti = hold ? tab.t(mine) : 0ull;
+        const unsigned long long tk = cp_warp_sum(ti);
+        uint32_t bv = hold ? (uint32_t)((ti * COPRA_ONE) / tk) : 0u;
+        const uint32_t bsum = __reduce_add_sync(FULL, bv);
+        if (hold && mine == best.slot) bv += COPRA_ONE - bsum;
+        // store by decreasing belonging, equal belongings by first appearance
+        const uint32_t fi = hold ? tab.first[mine] : 0xFFFFFFFFu;
+        const int32_t li = hold ? tab.key[mine] : EMPTY;
+        int rank = 0;
+        for (int q = 0; q < nk; ++q) {
+            const uint32_t bq = __shfl_sync(FULL, bv, q), fq = __shfl_sync(FULL, fi, q);
+            rank += (bq > bv || (bq == bv && fq < fi)) ? 1 : 0;
+        }
+        if (hold) {
+            out_l[rank] = li;
+            out_b[rank] = bv;
+            if (rank == 0 && li != prev) ++my_changed;
+        } else if ((uint32_t)lane < L) {
+            out_l[lane] = EMPTY;
+            out_b[lane] = 0u;
+        }
+        __syncwarp();
+        for (int j = lane; j < slots; j += 32) tab.clear(j);  // leave the table clean
+        __syncwarp();
+    }
+    my_changed = __reduce_add_sync(FULL, my_changed);
+    if (lane == 0 && my_changed) atomicAdd(a.changed, (int)my_changed);
+}
+
+// One COPRA step for the listed rows of one wave (a.rows, a.nrows): one CTA
+// per vertex, its table in shared memory (BIG false: rows of at most
+// CP_PAIRS pairs) or in the CTA's region of the global tables.
+template <bool BIG>
+__global__ void __launch_bounds__(CP_T) k_copra_cta(CopraArgs a)
+{
+    extern __shared__ uint32_t cp_smem[];
     __shared__ CpCand s_red[CP_T / 32];
     __shared__ unsigned long long s_w[CP_T / 32];
     __shared__ int32_t s_kept[64];
     __shared__ int s_nk;
     const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
-    int32_t *key;
-    unsigned long long *sum, *first;
-    if (BIG) {  // this CTA's region of the global tables (clean at every row's start)
+    using Tab = typename std::conditional<BIG, CpGlobal, CpShared>::type;
+    Tab tab;
+    if constexpr (BIG) {  // this CTA's region of the global tables (clean at every row's start)
         const int64_t base = (int64_t)blockIdx.x << a.glg_max;
-        key = a.gkey + base;
-        sum = a.gsum + base;
-        first = a.gfirst + base;
+        tab = CpGlobal{a.gkey + base, a.gsum + base, a.gfirst + base};
     } else {
-        sum = cp_smem;
-        first = sum + CP_TAB;
-        key = reinterpret_cast<int32_t *>(first + CP_TAB);
-        for (int j = tid; j < CP_TAB; j += CP_T) {
-            key[j] = EMPTY;
-            sum[j] = 0ull;
-            first[j] = ~0ull;
-        }
+        tab = CpShared{reinterpret_cast<int32_t *>(cp_smem), cp_smem + CP_TAB, cp_smem + 2 * CP_TAB,
+                       cp_smem + 3 * CP_TAB};
+        for (int j = tid; j < CP_TAB; j += CP_T) tab.clear(j);
         __syncthreads();
     }
     const uint32_t L = (uint32_t)a.L;
     uint32_t my_changed = 0;
-    for (int32_t v = blockIdx.x; v < a.n; v += gridDim.x) {
-        if (a.waves > 1 && fastmod((uint32_t)v, a.magic, a.waves) != a.wave_k) continue;
+    for (int64_t i = blockIdx.x; i < a.nrows; i += gridDim.x) {
+        const int32_t v = a.rows[i];
         const int32_t rs = __ldg(a.off + v), d = __ldg(a.off + v + 1) - rs;
         const int64_t pairs = (int64_t)d * L;
-        if ((pairs > CP_PAIRS) != BIG) continue;  // block-uniform
         const int32_t prev = a.cur_l[(int64_t)v * L];
         int32_t *out_l = a.nxt_l + (int64_t)v * L;
         uint32_t *out_b = a.nxt_b + (int64_t)v * L;
@@ -159,14 +356,13 @@ __global__ void __launch_bounds__(CP_T) k_copra(CopraArgs a)
             const int32_t u = __ldg(a.idx + rs + e);
             const uint32_t w = a.wts ? (uint32_t)__ldg(a.wts + rs + e) : 1u;
             wsum += w;
-            const bool earlier = a.waves > 1 && fastmod((uint32_t)u, a.magic, a.waves) < a.wave_k;
+            const bool earlier = cp_wave(a, u) < a.wave_k;
             const int32_t *ul = (earlier ? a.nxt_l : a.cur_l) + (int64_t)u * L;
             const uint32_t *ub = (earlier ? a.nxt_b : a.cur_b) + (int64_t)u * L;
             for (uint32_t p = 0; p < L; ++p) {
                 const uint32_t b = ub[p];
                 if (b == 0u) break;
-                cp_insert(key, sum, first, lg, ul[p], (unsigned long long)w * b,
-                          (unsigned long long)e * 64ull + p);
+                tab.add(lg, ul[p], (unsigned long long)w * b, (unsigned long long)e * 64ull + p);
             }
         }
         wsum = cp_warp_sum(wsum);
@@ -180,62 +376,53 @@ __global__ void __launch_bounds__(CP_T) k_copra(CopraArgs a)
         const uint64_t ktv = stream_at(a.key_t, (uint64_t)v + 1);
         CpCand best{0ull, 0ull, 0ull, -1};
         for (int j = tid; j < slots; j += CP_T) {
-            const int32_t l = key[j];
+            const int32_t l = tab.key[j];
             if (l == EMPTY) continue;
-            const unsigned long long t = sum[j];
+            const unsigned long long t = tab.t(j);
             if ((unsigned long long)L * t >= W * (unsigned long long)COPRA_ONE) {
                 const int at = atomicAdd(&s_nk, 1);
                 if (at < 64) s_kept[at] = j;  // at most L labels pass
             }
-            const CpCand c{t, a.strict ? 0ull : stream_at(ktv, (uint64_t)l + 1), first[j], j};
+            const CpCand c{t, a.strict ? 0ull : stream_at(ktv, (uint64_t)l + 1),
+                           (unsigned long long)tab.first[j], j};
             if (cp_better(c, best)) best = c;
         }
-#pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) {
-            const CpCand y = cp_shfl(best, o);
-            if (cp_better(y, best)) best = y;
-        }
+        best = cp_warp_best(best);
         if (lane == 0) s_red[wib] = best;
         __syncthreads();
         if (tid == 0) {
             best = s_red[0];
             for (int k = 1; k < CP_T / 32; ++k)
                 if (cp_better(s_red[k], best)) best = s_red[k];
-            int nk = s_nk < 64 ? s_nk : 64;
+            int nk = s_nk < (int)L ? s_nk : (int)L;  // at most L labels pass
             if (nk == 0) {  // none above the threshold: the best label alone
                 s_kept[0] = best.slot;
                 nk = 1;
             }
-            // normalize in fixed point, the remainder to the best kept label
+            // normalize in fixed point, the remainder to the best label (always kept)
             unsigned long long tk = 0ull;
-            for (int i = 0; i < nk; ++i) tk += sum[s_kept[i]];
+            for (int q = 0; q < nk; ++q) tk += tab.t(s_kept[q]);
             uint32_t bv[64];
             uint32_t bsum = 0u;
-            int bi = 0;
-            CpCand cb{};
-            for (int i = 0; i < nk; ++i) {
-                const int j = s_kept[i];
-                bv[i] = (uint32_t)((sum[j] * (unsigned long long)COPRA_ONE) / tk);
-                bsum += bv[i];
-                const CpCand c{sum[j], a.strict ? 0ull : stream_at(ktv, (uint64_t)key[j] + 1),
-                               first[j], j};
-                if (i == 0 || cp_better(c, cb)) {
-                    cb = c;
-                    bi = i;
-                }
+            for (int q = 0; q < nk; ++q) {
+                bv[q] = (uint32_t)((tab.t(s_kept[q]) * (unsigned long long)COPRA_ONE) / tk);
+                bsum += bv[q];
             }
-            bv[bi] += COPRA_ONE - bsum;
+            for (int q = 0; q < nk; ++q)
+                if (s_kept[q] == best.slot) bv[q] += COPRA_ONE - bsum;
             // store by decreasing belonging, equal belongings by first appearance
-            for (int i = 0; i < nk; ++i) {
+            for (int r = 0; r < nk; ++r) {
                 int pick = -1;
                 for (int q = 0; q < nk; ++q) {
                     if (s_kept[q] < 0) continue;
                     if (pick < 0 || bv[q] > bv[pick] ||
-                        (bv[q] == bv[pick] && first[s_kept[q]] < first[s_kept[pick]]))
+                        (bv[q] == bv[pick] &&
+                         (unsigned long long)tab.first[s_kept[q]] <
+                             (unsigned long long)tab.first[s_kept[pick]]))
                         pick = q;
                 }
-                out_l[i] = key[s_kept[pick]];
-                out_b[i] = bv[pick];
+                out_l[r] = tab.key[s_kept[pick]];
+                out_b[r] = bv[pick];
                 s_kept[pick] = -1 - s_kept[pick];  // taken
             }
             for (uint32_t s = nk; s < L; ++s) {
@@ -245,13 +432,8 @@ __global__ void __launch_bounds__(CP_T) k_copra(CopraArgs a)
             if (out_l[0] != prev) ++my_changed;
         }
         __syncthreads();
-        for (int j = tid; j < slots; j += CP_T) {  // leave the table clean
-            if (key[j] != EMPTY) {
-                key[j] = EMPTY;
-                sum[j] = 0ull;
-                first[j] = ~0ull;
-            }
-        }
+        for (int j = tid; j < slots; j += CP_T)  // leave the table clean
+            if (tab.key[j] != EMPTY) tab.clear(j);
         __syncthreads();
     }
     if (tid == 0 && my_changed) atomicAdd(a.changed, (int)my_changed);
@@ -274,6 +456,51 @@ __global__ void k_copra_best(const int32_t *l, int32_t n, int32_t L, int32_t *ou
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
          v += (int64_t)gridDim.x * blockDim.x)
         out[v] = l[v * L];
+}
+
+// Bin of row v among the rows the CTA kernels take: kind * waves + wave
+// (kind 0: shared table, 1: global table), or -1 for a row of the warp
+// kernel.
+__device__ __forceinline__ int64_t cp_bin(const int32_t *off, int32_t v, int32_t L, int32_t waves,
+                                          uint64_t magic)
+{
+    const int64_t pairs = (int64_t)(__ldg(off + v + 1) - __ldg(off + v)) * L;
+    if (L <= CPW_MAX_L && pairs <= CPW_PAIRS) return -1;
+    const uint32_t wave = waves > 1 ? fastmod((uint32_t)v, magic, (uint32_t)waves) : 0u;
+    return (pairs > CP_PAIRS ? (int64_t)waves : 0) + wave;
+}
+
+// count[bin] += rows of each bin (one atomic per bin and warp)
+__global__ void __launch_bounds__(256) k_copra_count(const int32_t *off, int32_t n, int32_t L,
+                                                     int32_t waves, uint64_t magic, int32_t *count)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+        const int64_t v = base + threadIdx.x;
+        const int64_t bin = v < n ? cp_bin(off, (int32_t)v, L, waves, magic) : -1;
+        const unsigned peers = __match_any_sync(FULL, (unsigned long long)bin);
+        if (bin >= 0 && lane == __ffs(peers) - 1) atomicAdd(count + bin, __popc(peers));
+    }
+}
+
+// rows[cursor[bin]++] = v for every listed row (cursor: the bins' starts)
+__global__ void __launch_bounds__(256) k_copra_scatter(const int32_t *off, int32_t n, int32_t L,
+                                                       int32_t waves, uint64_t magic,
+                                                       int32_t *cursor, int32_t *rows)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+        const int64_t v = base + threadIdx.x;
+        const int64_t bin = v < n ? cp_bin(off, (int32_t)v, L, waves, magic) : -1;
+        const unsigned peers = __match_any_sync(FULL, (unsigned long long)bin);
+        const int leader = __ffs(peers) - 1;
+        int32_t at = 0;
+        if (bin >= 0 && lane == leader) at = atomicAdd(cursor + bin, __popc(peers));
+        at = __shfl_sync(FULL, at, leader);
+        if (bin >= 0) rows[at + __popc(peers & ((1u << lane) - 1u))] = (int32_t)v;
+    }
 }
 
 int cp_grid(int64_t items) { return (int)(items < 1 ? 1 : (items + 255) / 256 < 8192 ? (items + 255) / 256 : 8192); }
@@ -299,8 +526,8 @@ int copra_best(const int32_t *l, int32_t n, int32_t L, int32_t *out, cudaStream_
 
 int copra_prepare()
 {
-    const int bytes = CP_TAB * (8 + 8 + 4);
-    return cudaFuncSetAttribute(k_copra<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const int bytes = CP_TAB * 16;
+    return cudaFuncSetAttribute(k_copra_cta<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 bytes) == cudaSuccess
                ? 0
                : -1;
@@ -316,6 +543,38 @@ int copra_table_lg(int64_t max_degree, int32_t L)
 }
 
 int copra_big_ctas() { return 32; }
+
+int64_t copra_bins(int32_t waves) { return 2 * (int64_t)waves; }
+
+int copra_rows(const int32_t *off, int32_t n, int32_t L, int32_t waves, int32_t *bins,
+               int32_t *h_bins, int64_t *h_start, int32_t *rows, cudaStream_t st,
+               int64_t *launches)
+{
+    const int64_t nb = copra_bins(waves);
+    const uint64_t magic = fastmod_magic((uint32_t)waves);
+    if (cudaMemsetAsync(bins, 0, (size_t)nb * sizeof(int32_t), st) != cudaSuccess) return -1;
+    if (n > 0) {
+        k_copra_count<<<cp_grid(n), 256, 0, st>>>(off, n, L, waves, magic, bins);
+        ++*launches;
+    }
+    if (cudaMemcpyAsync(h_bins, bins, (size_t)nb * sizeof(int32_t), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return -1;
+    h_start[0] = 0;
+    for (int64_t b = 0; b < nb; ++b) h_start[b + 1] = h_start[b] + h_bins[b];
+    for (int64_t b = 0; b < nb; ++b) h_bins[b] = (int32_t)h_start[b];
+    if (h_start[nb] > 0) {
+        if (cudaMemcpyAsync(bins, h_bins, (size_t)nb * sizeof(int32_t), cudaMemcpyHostToDevice,
+                            st) != cudaSuccess)
+            return -1;
+        k_copra_scatter<<<cp_grid(n), 256, 0, st>>>(off, n, L, waves, magic, bins, rows);
+        ++*launches;
+        // h_bins is read by the copy before it is reused
+        if (cudaStreamSynchronize(st) != cudaSuccess) return -1;
+    }
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
 
 int copra_step(const CopraStep &s, int num_sms, cudaStream_t st, int64_t *launches)
 {
@@ -340,11 +599,27 @@ int copra_step(const CopraStep &s, int num_sms, cudaStream_t st, int64_t *launch
     a.gfirst = s.gfirst;
     a.glg_max = s.glg_max;
     if (s.n <= 0) return 0;
-    const int grid = s.n < num_sms * 2 ? s.n : num_sms * 2;
-    k_copra<false><<<grid, CP_T, CP_TAB * (8 + 8 + 4), st>>>(a);
-    ++*launches;
-    if (s.glg_max > 0) {
-        k_copra<true><<<copra_big_ctas(), CP_T, 0, st>>>(a);
+    if (s.L <= CPW_MAX_L) {
+        const int64_t nw = (s.n - s.wave_k + (int64_t)s.waves - 1) / s.waves;
+        int64_t blocks = (nw + CPW_WARPS - 1) / CPW_WARPS;
+        if (blocks > (int64_t)num_sms * 8) blocks = (int64_t)num_sms * 8;
+        if (blocks > 0) {
+            k_copra_warp<<<(int)blocks, CPW_WARPS * 32, 0, st>>>(a);
+            ++*launches;
+        }
+    }
+    if (s.n_cta > 0) {
+        a.rows = s.rows_cta;
+        a.nrows = s.n_cta;
+        const int64_t grid = s.n_cta < (int64_t)num_sms * 3 ? s.n_cta : (int64_t)num_sms * 3;
+        k_copra_cta<false><<<(int)grid, CP_T, CP_TAB * 16, st>>>(a);
+        ++*launches;
+    }
+    if (s.n_big > 0) {
+        a.rows = s.rows_big;
+        a.nrows = s.n_big;
+        const int64_t grid = s.n_big < copra_big_ctas() ? s.n_big : copra_big_ctas();
+        k_copra_cta<true><<<(int)grid, CP_T, 0, st>>>(a);
         ++*launches;
     }
     return cudaGetLastError() == cudaSuccess ? 0 : -1;

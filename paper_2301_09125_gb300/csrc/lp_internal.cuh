@@ -385,6 +385,10 @@ struct CopraStep {
     int strict;
     uint64_t key_t;                  // non-strict key of the iteration
     int32_t *changed;                // += vertices whose best label changed
+    // this wave's rows that take a CTA (copra_rows): with the shared table
+    // and with the global tables
+    const int32_t *rows_cta, *rows_big;
+    int64_t n_cta, n_big;
     // rows of more than the shared table's pairs: copra_big_ctas() tables of
     // 2^glg_max slots (key -1, sum 0, first ~0 when clean; left clean)
     int32_t *gkey;
@@ -400,6 +404,15 @@ int copra_best(const int32_t *l, int32_t n, int32_t L, int32_t *out, cudaStream_
 // (0 when every row fits the shared table)
 int copra_table_lg(int64_t max_degree, int32_t L);
 int copra_big_ctas();
+// The rows that take a CTA (all rows when L > 32, else those of more than
+// 128 pairs), grouped by bin = kind * waves + wave (kind 0: shared table, 1:
+// global tables): rows[h_start[bin] .. h_start[bin + 1]).  bins: device
+// scratch and h_bins host scratch of copra_bins(waves) ints; h_start:
+// copra_bins(waves) + 1; rows: n.  Waits for the stream.
+int64_t copra_bins(int32_t waves);
+int copra_rows(const int32_t *off, int32_t n, int32_t L, int32_t waves, int32_t *bins,
+               int32_t *h_bins, int64_t *h_start, int32_t *rows, cudaStream_t st,
+               int64_t *launches);
 int copra_step(const CopraStep &s, int num_sms, cudaStream_t st, int64_t *launches);
 
 // Split the communities of lab (n vertices, m entries, one graph) into

@@ -104,3 +104,12 @@ def test_copra_rmat20(lp):
     g = gg.rmat(20, seed=1)
     copra_parity(lp, g.offsets, g.indices, g.weights, max_labels=4, mode="async", waves=2,
                  tolerance=0.01, max_iter=4)
+
+
+@pytest.mark.parametrize("shape", ["small", "mixed"])
+@pytest.mark.parametrize("mode", ["sync", "async"])
+def test_copra_more_labels_than_a_warp(lp, shape, mode):
+    # max_labels above 32: every row (rows without entries included) takes a CTA
+    off, idx, w = shape_graph(shape)
+    copra_parity(lp, off, idx, w, max_labels=40, mode=mode, waves=3, max_iter=4, strict=False,
+                 seed=5)
