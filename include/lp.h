@@ -257,9 +257,10 @@ lp_status lp_batch_modularity(lp_batch *b, int32_t index, double *q);
  * server's streams.  A worker thread advances every cohort one RAK iteration
  * (Sec. 3.2) at a time, interleaved with the other cohorts; an iteration of
  * a cohort is one launch per degree bucket for all of its graphs, and graphs
- * that have converged are left out of its later iterations.  When a cohort's
- * last graph has finished, its requests are retired (modularity, labels) and
- * queued requests take their places.  A request's result is the same as
+ * that have converged are left out of its later iterations and give their
+ * active slots back (their memory stays counted until the cohort retires).
+ * When a cohort's last graph has finished, its requests are retired
+ * (modularity, labels).  A request's result is the same as
  * that of lp_rak_run on its graph alone.  If a cohort's batch cannot be
  * ingested (an invalid graph), its requests are ingested one by one, so that
  * only the invalid ones fail.

@@ -267,7 +267,7 @@ struct GraphSet {
     unsigned long long *ctab_sum = nullptr, *ctab_first = nullptr;
     int32_t ctab_lg = 0;
     // rows that take a CTA, by kind and wave (copra_rows), and the bins' starts
-    int32_t *crows = nullptr, *cbins = nullptr;
+    int32_t *crows = nullptr, *cbins = nullptr, *covf = nullptr;
     int64_t cbins_cap = 0;
     std::vector<int32_t> h_cbins;
     std::vector<int64_t> h_cstart;
@@ -362,7 +362,8 @@ struct GraphSet {
         ctab_lg = 0;
         f(crows);
         f(cbins);
-        crows = cbins = nullptr;
+        f(covf);
+        crows = cbins = covf = nullptr;
         cbins_cap = 0;
         slpa_slots = slpa_filled = 0;
         f(pk_rp);
@@ -1558,6 +1559,7 @@ struct GraphSet {
         // the rows that take a CTA, by kind and wave
         const int64_t nbins = copra_bins(waves);
         if (!crows) LP_TRY(dev_alloc(&crows, std::max(nv, 1), "COPRA row lists", st, device));
+        if (!covf) LP_TRY(dev_alloc(&covf, (int64_t)nv + 1, "COPRA row lists", st, device));
         if (cbins_cap < nbins) {
             if (cbins) cudaFreeAsync(cbins, st);
             cbins = nullptr;
@@ -1604,6 +1606,7 @@ struct GraphSet {
                 cs.n_cta = h_cstart[(size_t)k + 1] - h_cstart[(size_t)k];
                 cs.rows_big = crows + h_cstart[(size_t)waves + k];
                 cs.n_big = h_cstart[(size_t)waves + k + 1] - h_cstart[(size_t)waves + k];
+                cs.ovf = covf;
                 if (copra_step(cs, num_sms, st, &L0.n) != 0)
                     return fail(LP_ECUDA, cuda_msg("COPRA launch", cudaGetLastError()));
             }
@@ -1736,6 +1739,7 @@ bool batch_run_done(lp_batch *b);
 lp_status batch_run_launch(lp_batch *b, cudaEvent_t *done_event);
 lp_status batch_run_finish(lp_batch *b);
 lp_status batch_run_end(lp_batch *b, lp_rak_result *per_graph);
+int32_t batch_run_active(lp_batch *b);  // graphs still iterating
 
 void lp_add_launches(int64_t n) { g_launches += n; }
 
@@ -1777,6 +1781,7 @@ lp_status batch_run_begin(lp_batch *b, const lp_rak_params *p)
     return b->s.run_begin(p, true);
 }
 bool batch_run_done(lp_batch *b) { return b->s.run_done(); }
+int32_t batch_run_active(lp_batch *b) { return b->s.rs.active_left; }
 lp_status batch_run_launch(lp_batch *b, cudaEvent_t *done_event)
 {
     DeviceGuard dg(b->s.device);

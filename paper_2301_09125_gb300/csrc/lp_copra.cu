@@ -53,9 +53,14 @@ struct CopraArgs {
     int strict;
     uint64_t key_t;        // non-strict key of this iteration
     int32_t *changed;
-    // the rows of this wave a CTA kernel takes (list, count)
+    // the rows of this wave a CTA kernel takes (list, count; or the count
+    // at nrows_dev when set)
     const int32_t *rows;
     int64_t nrows;
+    const int32_t *nrows_dev;
+    // rows that outgrew the long-row kernel's shared table: count at ovf[0],
+    // the rows after it
+    int32_t *ovf;
     // long rows: a table of 2^glg_max slots per CTA
     int32_t *gkey;
     unsigned long long *gsum, *gfirst;
@@ -128,7 +133,8 @@ struct CpShared {
     }
     // add (label l, value val < 2^48, first appearance f < 2^32); the table
     // has room for every label of the row
-    __device__ __forceinline__ void add(int lg, int32_t l, unsigned long long val,
+    // true when this call claimed the label's slot
+    __device__ __forceinline__ bool add(int lg, int32_t l, unsigned long long val,
                                         unsigned long long f) const
     {
         const uint32_t mask = (1u << lg) - 1u;
@@ -136,9 +142,13 @@ struct CpShared {
         uint32_t h = slot_hash(l, lg);
         for (uint32_t i = 0; i <= mask; ++i) {
             int32_t cur = vk[h];
+            bool claimed = false;
             if (cur == EMPTY) {
                 cur = atomicCAS(key + h, EMPTY, l);
-                if (cur == EMPTY) cur = l;
+                if (cur == EMPTY) {
+                    cur = l;
+                    claimed = true;
+                }
             }
             if (cur == l) {
                 const uint32_t vlo = (uint32_t)val, vhi = (uint32_t)(val >> 32);
@@ -148,10 +158,11 @@ struct CpShared {
                 const uint32_t up = vhi + (old + vlo < old ? 1u : 0u);
                 if (up) atomicAdd(hi + h, up);
                 atomicMin(first + h, (uint32_t)f);
-                return;
+                return claimed;
             }
             h = (h + 1) & mask;
         }
+        return false;
     }
 };
 
@@ -166,7 +177,7 @@ struct CpGlobal {
         sum[j] = 0ull;
         first[j] = ~0ull;
     }
-    __device__ __forceinline__ void add(int lg, int32_t l, unsigned long long val,
+    __device__ __forceinline__ bool add(int lg, int32_t l, unsigned long long val,
                                         unsigned long long f) const
     {
         const uint32_t mask = (1u << lg) - 1u;
@@ -174,17 +185,22 @@ struct CpGlobal {
         uint32_t h = slot_hash(l, lg);
         for (uint32_t i = 0; i <= mask; ++i) {
             int32_t cur = vk[h];
+            bool claimed = false;
             if (cur == EMPTY) {
                 cur = atomicCAS(key + h, EMPTY, l);
-                if (cur == EMPTY) cur = l;
+                if (cur == EMPTY) {
+                    cur = l;
+                    claimed = true;
+                }
             }
             if (cur == l) {
                 atomicAdd(sum + h, val);
                 atomicMin(first + h, f);
-                return;
+                return claimed;
             }
             h = (h + 1) & mask;
         }
+        return false;
     }
 };
 
@@ -308,32 +324,48 @@ __global__ void __launch_bounds__(CPW_WARPS * 32) k_copra_warp(CopraArgs a)
     if (lane == 0 && my_changed) atomicAdd(a.changed, (int)my_changed);
 }
 
-// One COPRA step for the listed rows of one wave (a.rows, a.nrows): one CTA
-// per vertex, its table in shared memory (BIG false: rows of at most
-// CP_PAIRS pairs) or in the CTA's region of the global tables.
-template <bool BIG>
-__global__ void __launch_bounds__(CP_T) k_copra_cta(CopraArgs a)
+// Table modes of the CTA kernel: shared with room for every label of the
+// row (CP_SHARED), shared with a fixed 2^LG slots that a row may outgrow
+// (CP_SPILL: the row is then listed for the global tables), or this CTA's
+// region of the global tables (CP_GLOBAL).
+constexpr int CP_SHARED = 0, CP_SPILL = 1, CP_GLOBAL = 2;
+constexpr int CPL_T = 512;                  // threads of the long-row kernel
+constexpr int CPL_LG = 13;
+constexpr int CPL_TAB = 1 << CPL_LG;        // its shared slots
+constexpr int CPL_FULL = CPL_TAB / 4 * 3;   // claimed slots at which a row moves to the global tables
+constexpr int32_t CPL_MAX_D = 1 << 26;      // first appearance e * 64 + p stays below 2^32
+
+// One COPRA step for the listed rows of one wave (a.rows, a.nrows, or
+// *a.nrows_dev rows): one CTA of NT threads per vertex.
+template <int NT, int LG, int MODE>
+__global__ void __launch_bounds__(NT) k_copra_cta(CopraArgs a)
 {
     extern __shared__ uint32_t cp_smem[];
-    __shared__ CpCand s_red[CP_T / 32];
-    __shared__ unsigned long long s_w[CP_T / 32];
+    __shared__ CpCand s_red[NT / 32];
+    __shared__ unsigned long long s_w[NT / 32];
     __shared__ int32_t s_kept[64];
-    __shared__ int s_nk;
+    __shared__ int s_nk, s_claimed, s_full;
+    constexpr int TAB = 1 << LG;
     const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
-    using Tab = typename std::conditional<BIG, CpGlobal, CpShared>::type;
+    using Tab = typename std::conditional<MODE == CP_GLOBAL, CpGlobal, CpShared>::type;
     Tab tab;
-    if constexpr (BIG) {  // this CTA's region of the global tables (clean at every row's start)
+    if constexpr (MODE == CP_GLOBAL) {  // this CTA's region (clean at every row's start)
         const int64_t base = (int64_t)blockIdx.x << a.glg_max;
         tab = CpGlobal{a.gkey + base, a.gsum + base, a.gfirst + base};
     } else {
-        tab = CpShared{reinterpret_cast<int32_t *>(cp_smem), cp_smem + CP_TAB, cp_smem + 2 * CP_TAB,
-                       cp_smem + 3 * CP_TAB};
-        for (int j = tid; j < CP_TAB; j += CP_T) tab.clear(j);
-        __syncthreads();
+        tab = CpShared{reinterpret_cast<int32_t *>(cp_smem), cp_smem + TAB, cp_smem + 2 * TAB,
+                       cp_smem + 3 * TAB};
+        for (int j = tid; j < TAB; j += NT) tab.clear(j);
     }
+    if (tid == 0) {
+        s_claimed = 0;
+        s_full = 0;
+    }
+    __syncthreads();
+    const int64_t nrows = a.nrows_dev ? (int64_t)*a.nrows_dev : a.nrows;
     const uint32_t L = (uint32_t)a.L;
     uint32_t my_changed = 0;
-    for (int64_t i = blockIdx.x; i < a.nrows; i += gridDim.x) {
+    for (int64_t i = blockIdx.x; i < nrows; i += gridDim.x) {
         const int32_t v = a.rows[i];
         const int32_t rs = __ldg(a.off + v), d = __ldg(a.off + v + 1) - rs;
         const int64_t pairs = (int64_t)d * L;
@@ -341,18 +373,33 @@ __global__ void __launch_bounds__(CP_T) k_copra_cta(CopraArgs a)
         int32_t *out_l = a.nxt_l + (int64_t)v * L;
         uint32_t *out_b = a.nxt_b + (int64_t)v * L;
         if (d == 0) {  // no labels: the vertex is its own community
-            for (uint32_t s = tid; s < L; s += CP_T) {
+            for (uint32_t s = tid; s < L; s += NT) {
                 out_l[s] = s == 0 ? v : EMPTY;
                 out_b[s] = s == 0 ? COPRA_ONE : 0u;
             }
             if (tid == 0 && prev != v) ++my_changed;
             continue;
         }
-        const int lg = ilog2_ceil((uint32_t)(2 * pairs));  // 2^lg >= 2 pairs (<= 2^glg_max)
+        if (MODE == CP_SPILL && d >= CPL_MAX_D) {  // block-uniform
+            if (tid == 0) a.ovf[1 + atomicAdd(a.ovf, 1)] = v;
+            continue;
+        }
+        // 2^lg >= 2 pairs slots (<= 2^glg_max), or the whole table in CP_SPILL
+        const int lg = MODE == CP_SPILL ? LG : ilog2_ceil((uint32_t)(2 * pairs));
         const int slots = 1 << lg;
-        // T(l) and first appearance over the row's entries and their speakers' pairs
+        // T(l) and first appearance over the row's entries and their speakers'
+        // pairs; each thread sums the runs of its speakers' first (best)
+        // labels in registers, so a label most speakers share is added once
         unsigned long long wsum = 0ull;
-        for (int32_t e = tid; e < d; e += CP_T) {
+        int32_t c_l = EMPTY;
+        unsigned long long c_v = 0ull, c_f = 0ull;
+        auto put = [&](int32_t l, unsigned long long val, unsigned long long f) {
+            if (tab.add(lg, l, val, f) && MODE == CP_SPILL) {
+                if (atomicAdd(&s_claimed, 1) + 1 >= CPL_FULL) s_full = 1;
+            }
+        };
+        for (int32_t e = tid; e < d; e += NT) {
+            if (MODE == CP_SPILL && *(volatile int *)&s_full) break;
             const int32_t u = __ldg(a.idx + rs + e);
             const uint32_t w = a.wts ? (uint32_t)__ldg(a.wts + rs + e) : 1u;
             wsum += w;
@@ -362,20 +409,46 @@ __global__ void __launch_bounds__(CP_T) k_copra_cta(CopraArgs a)
             for (uint32_t p = 0; p < L; ++p) {
                 const uint32_t b = ub[p];
                 if (b == 0u) break;
-                tab.add(lg, ul[p], (unsigned long long)w * b, (unsigned long long)e * 64ull + p);
+                const int32_t l = ul[p];
+                const unsigned long long val = (unsigned long long)w * b;
+                const unsigned long long f = (unsigned long long)e * 64ull + p;
+                if (p == 0) {
+                    if (l == c_l) {
+                        c_v += val;  // its first appearance is the cached one (earlier)
+                        continue;
+                    }
+                    if (c_l != EMPTY) put(c_l, c_v, c_f);
+                    c_l = l;
+                    c_v = val;
+                    c_f = f;
+                    continue;
+                }
+                put(l, val, f);
             }
         }
+        if (c_l != EMPTY && !(MODE == CP_SPILL && *(volatile int *)&s_full)) put(c_l, c_v, c_f);
         wsum = cp_warp_sum(wsum);
         if (lane == 0) s_w[wib] = wsum;
         if (tid == 0) s_nk = 0;
         __syncthreads();
+        if (MODE == CP_SPILL && s_full) {  // too many labels: the global tables take the row
+            if (tid == 0) a.ovf[1 + atomicAdd(a.ovf, 1)] = v;
+            for (int j = tid; j < slots; j += NT)
+                if (tab.key[j] != EMPTY) tab.clear(j);
+            if (tid == 0) {
+                s_claimed = 0;
+                s_full = 0;
+            }
+            __syncthreads();
+            continue;
+        }
         unsigned long long W = 0ull;
 #pragma unroll
-        for (int k = 0; k < CP_T / 32; ++k) W += s_w[k];
+        for (int k = 0; k < NT / 32; ++k) W += s_w[k];
         // the labels above the threshold and the best label
         const uint64_t ktv = stream_at(a.key_t, (uint64_t)v + 1);
         CpCand best{0ull, 0ull, 0ull, -1};
-        for (int j = tid; j < slots; j += CP_T) {
+        for (int j = tid; j < slots; j += NT) {
             const int32_t l = tab.key[j];
             if (l == EMPTY) continue;
             const unsigned long long t = tab.t(j);
@@ -392,7 +465,7 @@ __global__ void __launch_bounds__(CP_T) k_copra_cta(CopraArgs a)
         __syncthreads();
         if (tid == 0) {
             best = s_red[0];
-            for (int k = 1; k < CP_T / 32; ++k)
+            for (int k = 1; k < NT / 32; ++k)
                 if (cp_better(s_red[k], best)) best = s_red[k];
             int nk = s_nk < (int)L ? s_nk : (int)L;  // at most L labels pass
             if (nk == 0) {  // none above the threshold: the best label alone
@@ -432,8 +505,9 @@ __global__ void __launch_bounds__(CP_T) k_copra_cta(CopraArgs a)
             if (out_l[0] != prev) ++my_changed;
         }
         __syncthreads();
-        for (int j = tid; j < slots; j += CP_T)  // leave the table clean
+        for (int j = tid; j < slots; j += NT)  // leave the table clean
             if (tab.key[j] != EMPTY) tab.clear(j);
+        if (tid == 0) s_claimed = 0;
         __syncthreads();
     }
     if (tid == 0 && my_changed) atomicAdd(a.changed, (int)my_changed);
@@ -526,11 +600,14 @@ int copra_best(const int32_t *l, int32_t n, int32_t L, int32_t *out, cudaStream_
 
 int copra_prepare()
 {
-    const int bytes = CP_TAB * 16;
-    return cudaFuncSetAttribute(k_copra_cta<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                bytes) == cudaSuccess
-               ? 0
-               : -1;
+    const bool ok =
+        cudaFuncSetAttribute(k_copra_cta<CP_T, CP_LG, CP_SHARED>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, CP_TAB * 16) ==
+            cudaSuccess &&
+        cudaFuncSetAttribute(k_copra_cta<CPL_T, CPL_LG, CP_SPILL>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, CPL_TAB * 16) ==
+            cudaSuccess;
+    return ok ? 0 : -1;
 }
 
 int copra_table_lg(int64_t max_degree, int32_t L)
@@ -612,15 +689,23 @@ int copra_step(const CopraStep &s, int num_sms, cudaStream_t st, int64_t *launch
         a.rows = s.rows_cta;
         a.nrows = s.n_cta;
         const int64_t grid = s.n_cta < (int64_t)num_sms * 3 ? s.n_cta : (int64_t)num_sms * 3;
-        k_copra_cta<false><<<(int)grid, CP_T, CP_TAB * 16, st>>>(a);
+        k_copra_cta<CP_T, CP_LG, CP_SHARED><<<(int)grid, CP_T, CP_TAB * 16, st>>>(a);
         ++*launches;
     }
     if (s.n_big > 0) {
+        // long rows in shared memory; those with too many labels, then, in the global tables
+        if (cudaMemsetAsync(s.ovf, 0, sizeof(int32_t), st) != cudaSuccess) return -1;
         a.rows = s.rows_big;
         a.nrows = s.n_big;
-        const int64_t grid = s.n_big < copra_big_ctas() ? s.n_big : copra_big_ctas();
-        k_copra_cta<true><<<(int)grid, CP_T, 0, st>>>(a);
-        ++*launches;
+        a.ovf = s.ovf;
+        const int64_t grid = s.n_big < num_sms ? s.n_big : num_sms;
+        k_copra_cta<CPL_T, CPL_LG, CP_SPILL><<<(int)grid, CPL_T, CPL_TAB * 16, st>>>(a);
+        a.rows = s.ovf + 1;
+        a.nrows = 0;
+        a.nrows_dev = s.ovf;
+        const int64_t gg = s.n_big < copra_big_ctas() ? s.n_big : copra_big_ctas();
+        k_copra_cta<CP_T, CP_LG, CP_GLOBAL><<<(int)gg, CP_T, 0, st>>>(a);
+        *launches += 2;
     }
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

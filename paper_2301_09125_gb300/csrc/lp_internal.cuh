@@ -389,6 +389,8 @@ struct CopraStep {
     // and with the global tables
     const int32_t *rows_cta, *rows_big;
     int64_t n_cta, n_big;
+    // n + 1 ints of scratch: the long rows that outgrow the shared table
+    int32_t *ovf;
     // rows of more than the shared table's pairs: copra_big_ctas() tables of
     // 2^glg_max slots (key -1, sum 0, first ~0 when clean; left clean)
     int32_t *gkey;

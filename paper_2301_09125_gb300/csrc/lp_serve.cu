@@ -40,6 +40,7 @@ bool batch_run_done(lp_batch *b);
 lp_status batch_run_launch(lp_batch *b, cudaEvent_t *done_event);
 lp_status batch_run_finish(lp_batch *b);
 lp_status batch_run_end(lp_batch *b, lp_rak_result *per_graph);
+int32_t batch_run_active(lp_batch *b);
 }  // namespace lp
 
 namespace {
@@ -69,6 +70,10 @@ struct Cohort {
     lp_batch *b = nullptr;  // several
     cudaEvent_t ev = nullptr;  // end of the in-flight iteration (owned by the graph set)
     bool in_flight = false;
+    // requests still holding an active slot: a converged graph of a batch
+    // gives its slot back at once (its memory stays counted until the cohort
+    // retires), so that queued requests need not wait for the cohort's last one
+    int64_t slots = 0;
 };
 
 // device bytes a request may hold: CSR, two label buffers, bucket and wave
@@ -96,7 +101,7 @@ struct lp_server {
     std::deque<std::unique_ptr<Cohort>> ready;   // ingested, not yet picked up
     std::deque<lp_serve_result> results;
     int64_t outstanding = 0;  // submitted, result not yet queued
-    int64_t slots_used = 0;   // admitted, not yet retired
+    int64_t slots_used = 0;   // admitted and still iterating
     int64_t mem_used = 0;     // footprint of the admitted requests
     int64_t n_cohorts = 0, n_batched = 0, max_cohort_seen = 0;  // lp_server_stats
     bool stop = false;
@@ -104,13 +109,21 @@ struct lp_server {
 
     std::vector<std::unique_ptr<Cohort>> active;  // worker thread only
 
+    // give back active slots of requests whose graphs have finished
+    void release_slots(int64_t k)
+    {
+        if (k <= 0) return;
+        std::lock_guard<std::mutex> lock(mu);
+        slots_used -= k;
+        cv_admit.notify_one();
+    }
+
     void retire(std::unique_ptr<Request> r, lp_status st)
     {
         r->res.status = st;
         r->res.latency_ms = ms_since(r->t_submit);
         std::lock_guard<std::mutex> lock(mu);
         mem_used -= r->footprint;
-        --slots_used;
         results.push_back(r->res);
         --outstanding;
         cv_done.notify_all();
@@ -124,6 +137,8 @@ struct lp_server {
         if (c->b) lp_batch_destroy(c->b);
         c->g = nullptr;
         c->b = nullptr;
+        release_slots(c->slots);
+        c->slots = 0;
         for (size_t i = 0; i < c->reqs.size(); ++i) retire(std::move(c->reqs[i]), st[i]);
     }
     void retire_cohort(std::unique_ptr<Cohort> c, lp_status st)
@@ -144,6 +159,7 @@ struct lp_server {
     {
         std::unique_ptr<Cohort> c(new Cohort);
         c->reqs.push_back(std::move(r));
+        c->slots = 1;
         lp_status s = lp_graph_create(c->reqs[0]->n, c->reqs[0]->m, c->reqs[0]->off,
                                       c->reqs[0]->idx, c->reqs[0]->wts, 0, take_stream(), &c->g);
         if (s == LP_OK) s = lp::graph_run_begin(c->g, &params);
@@ -173,6 +189,7 @@ struct lp_server {
             lp_status s = lp_batch_create((int32_t)take.size(), d.data(), 0, take_stream(), &c->b);
             if (s == LP_OK) s = lp::batch_run_begin(c->b, &params);
             if (s == LP_OK) {
+                c->slots = (int64_t)take.size();
                 c->reqs = std::move(take);
                 take.clear();
                 made.push_back(std::move(c));
@@ -212,6 +229,13 @@ struct lp_server {
                 return false;
             }
             s = c->g ? lp::graph_run_finish(c->g) : lp::batch_run_finish(c->b);
+            if (s == LP_OK && c->b) {
+                const int64_t left = lp::batch_run_active(c->b);
+                if (left < c->slots) {
+                    release_slots(c->slots - left);
+                    c->slots = left;
+                }
+            }
         }
         if (s == LP_OK && !(c->g ? lp::graph_run_done(c->g) : lp::batch_run_done(c->b))) {
             s = c->g ? lp::graph_run_launch(c->g, &c->ev) : lp::batch_run_launch(c->b, &c->ev);

@@ -48,7 +48,7 @@ def copra_parity(lp, off, idx, w, max_labels=4, tolerance=0.0, max_iter=6, mode=
     return r
 
 
-SHAPES = ["small", "warp", "cta", "hub", "mixed"]
+SHAPES = ["small", "warp", "cta", "hub", "bighub", "mixed"]
 
 
 def shape_graph(shape):
@@ -60,6 +60,8 @@ def shape_graph(shape):
         return random_graph(2000, 300 / 2000, 53, wmax=3)
     if shape == "hub":
         return hub_graph(54, n=15_000, hubs=2, hub_deg=6_000)
+    if shape == "bighub":  # rows with more labels than the long-row shared table holds
+        return hub_graph(56, n=30_000, hubs=3, hub_deg=9_000)
     g = gg.rmat(13, seed=55)
     return g.offsets, g.indices, g.weights
 
@@ -71,7 +73,7 @@ def test_copra_sync_parity(lp, shape, max_labels):
     copra_parity(lp, off, idx, w, max_labels=max_labels, mode="sync", max_iter=5)
 
 
-@pytest.mark.parametrize("shape", ["small", "cta", "mixed"])
+@pytest.mark.parametrize("shape", ["small", "cta", "bighub", "mixed"])
 @pytest.mark.parametrize("strict", [True, False])
 def test_copra_async_parity(lp, shape, strict):
     off, idx, w = shape_graph(shape)
