@@ -111,6 +111,12 @@ def parse():
     ap.add_argument("--serve-saturation", type=int, default=512,
                     help="requests of the burst that measures service capacity")
     ap.add_argument("--serve-pool", type=int, default=96, help="distinct graphs in the pool")
+    ap.add_argument("--serve-cohort", type=int, default=None,
+                    help="requests iterated together in one batch (server default if unset)")
+    ap.add_argument("--serve-admitters", type=int, default=None,
+                    help="ingest threads of the server (server default if unset)")
+    ap.add_argument("--serve-cohort-entries", type=int, default=None,
+                    help="largest graph (CSR entries) that joins a cohort")
     ap.add_argument("--serve-baseline-seconds", type=float, default=10.0,
                     help="arrival window replayed one graph at a time")
     ap.add_argument("--no-batch", action="store_true",
@@ -901,6 +907,12 @@ def measure_serve(args, ctx):
     cfg.hbm_budget = 64 << 30
     cfg.max_active = 64
     cfg.streams = 8
+    if args.serve_cohort is not None:
+        cfg.max_cohort = args.serve_cohort
+    if args.serve_admitters is not None:
+        cfg.admitters = args.serve_admitters
+    if args.serve_cohort_entries is not None:
+        cfg.cohort_max_entries = args.serve_cohort_entries
 
     # warm-up: every pool graph once through the server
     srv = lp.lp_server_create(cfg, params)
@@ -990,7 +1002,8 @@ def measure_serve(args, ctx):
         "config": {"workload": "serve", **p, "requests": n_all, "window_s": args.serve_seconds,
                    "pool_graphs": len(pool), "pool_generation_s": round(gen_s, 1),
                    "max_active": cfg.max_active, "streams": cfg.streams,
-                   "max_cohort": cfg.max_cohort,
+                   "max_cohort": cfg.max_cohort, "admitters": cfg.admitters,
+                   "cohort_max_entries": cfg.cohort_max_entries,
                    "hbm_budget_gib": cfg.hbm_budget >> 30,
                    "l2": "graphs resident per request, no flush",
                    "parallelism": (f"requests sharded over {ctx.world} ranks"

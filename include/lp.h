@@ -251,10 +251,12 @@ lp_status lp_batch_modularity(lp_batch *b, int32_t index, double *q);
  * Each request is one graph run with the server's parameters.  An admission
  * thread admits queued requests while fewer than max_active requests are on
  * the device and their estimated footprints (about 40 n + 88 m bytes each)
- * fit the HBM budget still free.  The requests it finds queued together, up
- * to max_cohort of them, form one cohort: a lone request is ingested as a
- * graph, several as one batch arena (lp_batch_create), on one of the
- * server's streams.  A worker thread advances every cohort one RAK iteration
+ * fit the HBM budget still free.  The requests of at most cohort_max_entries
+ * entries it finds queued together, up to max_cohort of them, form one
+ * cohort; a larger request forms a cohort of its own.  A lone request is
+ * ingested as a graph, several as one batch arena (lp_batch_create), on one
+ * of the server's streams, by one of `admitters` threads, so that the
+ * ingest of several cohorts overlaps.  A worker thread advances every cohort one RAK iteration
  * (Sec. 3.2) at a time, interleaved with the other cohorts; an iteration of
  * a cohort is one launch per degree bucket for all of its graphs, and graphs
  * that have converged are left out of its later iterations and give their
@@ -273,7 +275,9 @@ typedef struct {
     int32_t streams;    /* CUDA streams the cohorts are spread over, 1..64 (default 8) */
     int32_t max_cohort; /* requests ingested and iterated together, >= 1 (default 16;
                            1 = every request on its own) */
-    int32_t reserved;   /* 0 */
+    int32_t admitters;  /* threads that ingest admitted requests, 1..16 (default 4) */
+    int64_t cohort_max_entries; /* a graph with more CSR entries is admitted on its own
+                                   (default 2^22; small graphs gain from sharing launches) */
 } lp_server_config;
 
 typedef struct {

@@ -58,7 +58,7 @@ class lp_graph_desc(ctypes.Structure):
 class lp_server_config(ctypes.Structure):
     _fields_ = [("hbm_budget", ctypes.c_int64), ("max_active", ctypes.c_int32),
                 ("streams", ctypes.c_int32), ("max_cohort", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("admitters", ctypes.c_int32), ("cohort_max_entries", ctypes.c_int64)]
 
 
 class lp_serve_result(ctypes.Structure):

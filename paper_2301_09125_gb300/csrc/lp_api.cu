@@ -13,6 +13,7 @@
 #include <cstring>
 #include <memory>
 #include <mutex>
+#include <unordered_map>
 #include <string>
 #include <vector>
 
@@ -124,17 +125,86 @@ lp_status dev_alloc(T **p, int64_t count, const char *what, cudaStream_t st, int
     return LP_OK;
 }
 
+// Pinned host blocks of up to PINNED_CACHE_MAX bytes are kept for reuse in
+// power-of-two size classes: cudaMallocHost is slow, and cudaFreeHost may
+// wait for the whole device, which would stall every other stream of a
+// process that creates and destroys graph sets while others run (a server).
+constexpr size_t PINNED_CACHE_MAX = (size_t)1 << 20;
+constexpr int PINNED_CLASSES = 13;  // 256 B .. 1 MiB
+constexpr size_t PINNED_KEEP = 256; // blocks kept per class
+struct PinnedCache {
+    std::mutex mu;
+    std::vector<void *> free_[PINNED_CLASSES];
+    std::unordered_map<void *, int> cls;  // live cached-size blocks and their class
+};
+PinnedCache &pinned_cache()
+{
+    static PinnedCache *c = new PinnedCache;  // never destroyed: blocks may outlive statics
+    return *c;
+}
+int pinned_class(size_t bytes)
+{
+    int k = 0;
+    while (((size_t)256 << k) < bytes) ++k;
+    return k;
+}
+void *pinned_take(size_t bytes)
+{
+    if (bytes <= PINNED_CACHE_MAX) {
+        const int k = pinned_class(bytes);
+        PinnedCache &c = pinned_cache();
+        {
+            std::lock_guard<std::mutex> lock(c.mu);
+            if (!c.free_[k].empty()) {
+                void *q = c.free_[k].back();
+                c.free_[k].pop_back();
+                c.cls[q] = k;
+                return q;
+            }
+        }
+        void *q = nullptr;
+        if (cudaMallocHost(&q, (size_t)256 << k) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        std::lock_guard<std::mutex> lock(c.mu);
+        c.cls[q] = k;
+        return q;
+    }
+    void *q = nullptr;
+    if (cudaMallocHost(&q, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return q;
+}
+void host_free(void *p)
+{
+    if (!p) return;
+    PinnedCache &c = pinned_cache();
+    {
+        std::lock_guard<std::mutex> lock(c.mu);
+        auto it = c.cls.find(p);
+        if (it != c.cls.end()) {
+            const int k = it->second;
+            c.cls.erase(it);
+            if (c.free_[k].size() < PINNED_KEEP) {
+                c.free_[k].push_back(p);
+                return;
+            }
+        }
+    }
+    cudaFreeHost(p);
+}
+
 template <typename T>
 lp_status host_alloc(T **p, int64_t count, const char *what)
 {
     *p = nullptr;
     if (count <= 0) count = 1;
-    cudaError_t e = cudaMallocHost((void **)p, (size_t)count * sizeof(T));
-    if (e != cudaSuccess) {
-        *p = nullptr;
-        cudaGetLastError();
-        return fail(LP_ENOMEM, std::string("pinned host allocation of ") + what + " failed");
-    }
+    void *q = pinned_take((size_t)count * sizeof(T));
+    if (!q) return fail(LP_ENOMEM, std::string("pinned host allocation of ") + what + " failed");
+    *p = static_cast<T *>(q);
     return LP_OK;
 }
 
@@ -309,7 +379,7 @@ struct GraphSet {
             if (p) cudaFreeAsync(p, s0);
         };
         auto fh = [](void *p) {
-            if (p) cudaFreeHost(p);
+            if (p) host_free(p);
         };
         if (own_off) f(off);
         if (own_idx) f(idx);
@@ -424,9 +494,9 @@ struct GraphSet {
         drop_graph();
         if (gr_stream) cudaStreamDestroy(gr_stream);
         gr_stream = nullptr;
-        if (h_res) cudaFreeHost(h_res);
+        if (h_res) host_free(h_res);
         h_res = nullptr;
-        if (h_stop) cudaFreeHost(h_stop);
+        if (h_stop) host_free(h_stop);
         h_stop = nullptr;
         h_stop_cap = 0;
         for (cudaEvent_t &e : run_ev) {
@@ -852,7 +922,7 @@ struct GraphSet {
     {
         if (entries <= changed_cap) return LP_OK;
         if (changed) cudaFreeAsync(changed, st);
-        if (h_changed) cudaFreeHost(h_changed);
+        if (h_changed) host_free(h_changed);
         changed = nullptr;
         h_changed = nullptr;
         changed_cap = 0;
@@ -1356,7 +1426,7 @@ struct GraphSet {
         LP_TRY(run_begin(p, multi));
         if (!d_stop) LP_TRY(dev_alloc(&d_stop, 1, "stop flag", st, device));
         if (h_stop_cap < rs.p.max_iter) {
-            if (h_stop) cudaFreeHost(h_stop);
+            if (h_stop) host_free(h_stop);
             h_stop = nullptr;
             h_stop_cap = 0;
             LP_TRY(host_alloc(&h_stop, rs.p.max_iter, "stop flags"));

@@ -2,10 +2,11 @@
 //
 // Requests (one graph each, host CSR) queue up as they are submitted.  An
 // admission thread takes the requests queued at that moment, as many as the
-// free active slots, the HBM budget and max_cohort allow, and ingests them
-// as one cohort on one of the server's CUDA streams: a lone request as a
-// graph, several as one batch arena, whose iterations sweep every graph with
-// one launch per degree bucket.  A worker thread advances every cohort one
+// free active slots, the HBM budget and max_cohort allow (a graph of more
+// than cohort_max_entries entries alone), and ingests them as one cohort on
+// one of the server's CUDA streams: a lone request as a graph, several as
+// one batch arena, whose iterations sweep every graph with one launch per
+// degree bucket.  Several admission threads ingest cohorts side by side.  A worker thread advances every cohort one
 // RAK iteration at a time: whenever a cohort's in-flight iteration has
 // finished on the device (event query), it applies the tolerance test to
 // each of its graphs (a converged graph is left out of later iterations) and
@@ -15,6 +16,7 @@
 // between iterations of the running cohorts, ingest never holds up their
 // launches, and each result is the same as a lone lp_rak_run.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -92,7 +94,7 @@ struct lp_server {
     lp_rak_params params{};
     int device = 0;
     std::vector<cudaStream_t> streams;
-    int next_stream = 0;
+    std::atomic<int> next_stream{0};
     Clock::time_point t0 = Clock::now();
 
     std::mutex mu;
@@ -105,7 +107,8 @@ struct lp_server {
     int64_t mem_used = 0;     // footprint of the admitted requests
     int64_t n_cohorts = 0, n_batched = 0, max_cohort_seen = 0;  // lp_server_stats
     bool stop = false;
-    std::thread worker, admitter;
+    std::thread worker;
+    std::vector<std::thread> admitters;
 
     std::vector<std::unique_ptr<Cohort>> active;  // worker thread only
 
@@ -149,9 +152,7 @@ struct lp_server {
 
     cudaStream_t take_stream()
     {
-        cudaStream_t st = streams[(size_t)next_stream];
-        next_stream = (next_stream + 1) % (int)streams.size();
-        return st;
+        return streams[(size_t)(next_stream.fetch_add(1) % (int)streams.size())];
     }
 
     // ingest a lone request and start its run; null if it failed (retired)
@@ -274,7 +275,7 @@ struct lp_server {
         return false;
     }
 
-    // admission thread: slot and budget checks, then ingest on a stream
+    // admission threads: slot and budget checks, then ingest on a stream
     void admit_loop()
     {
         cudaSetDevice(device);
@@ -287,12 +288,15 @@ struct lp_server {
                                     mem_used + queue.front()->footprint <= cfg.hbm_budget);
                 });
                 if (stop && queue.empty()) return;
-                // the requests queued now, in order, while slots and budget last
-                // (and a batch's vertex ids stay below 2^31)
+                // the requests queued now, in order, while slots and budget last:
+                // a large request alone, else the small ones up to the next large
+                // one (and a batch's vertex ids stay below 2^31)
                 int64_t nv = 0;
-                while (!queue.empty() && (int64_t)take.size() < cfg.max_cohort &&
+                const bool alone = queue.front()->m > cfg.cohort_max_entries;
+                while (!queue.empty() && (int64_t)take.size() < (alone ? 1 : cfg.max_cohort) &&
                        slots_used < cfg.max_active &&
                        mem_used + queue.front()->footprint <= cfg.hbm_budget &&
+                       (alone || queue.front()->m <= cfg.cohort_max_entries) &&
                        nv + queue.front()->n + (int64_t)take.size() + 1 < 2147483647LL) {
                     nv += queue.front()->n;
                     mem_used += queue.front()->footprint;
@@ -300,6 +304,7 @@ struct lp_server {
                     take.push_back(std::move(queue.front()));
                     queue.pop_front();
                 }
+                if (!queue.empty()) cv_admit.notify_one();  // another admitter may go on
             }
             if (!take.empty()) admit(std::move(take));
         }
@@ -348,7 +353,8 @@ lp_status lp_server_config_default(lp_server_config *cfg)
     cfg->max_active = 64;
     cfg->streams = 8;
     cfg->max_cohort = 16;
-    cfg->reserved = 0;
+    cfg->admitters = 4;
+    cfg->cohort_max_entries = (int64_t)1 << 22;
     return LP_OK;
 }
 
@@ -358,9 +364,11 @@ lp_status lp_server_create(const lp_server_config *cfg, const lp_rak_params *p, 
     *out = nullptr;
     if (!cfg || !p) return lp::lp_fail(LP_EINVAL, "cfg or params is NULL");
     if (cfg->hbm_budget <= 0 || cfg->max_active < 1 || cfg->streams < 1 || cfg->streams > 64 ||
-        cfg->max_cohort < 1)
-        return lp::lp_fail(LP_EINVAL,
-                           "hbm_budget > 0, max_active >= 1, 1 <= streams <= 64, max_cohort >= 1");
+        cfg->max_cohort < 1 || cfg->admitters < 1 || cfg->admitters > 16 ||
+        cfg->cohort_max_entries < 0)
+        return lp::lp_fail(LP_EINVAL, "hbm_budget > 0, max_active >= 1, 1 <= streams <= 64, "
+                                      "max_cohort >= 1, 1 <= admitters <= 16, "
+                                      "cohort_max_entries >= 0");
     if (p->init_labels) return lp::lp_fail(LP_EINVAL, "served requests start from unique labels");
     if (!(p->tolerance >= 0.0 && p->tolerance <= 1.0) || p->max_iter < 1 ||
         (p->mode != LP_SYNC && p->mode != LP_ASYNC) || (p->mode == LP_ASYNC && p->waves < 1))
@@ -380,7 +388,8 @@ lp_status lp_server_create(const lp_server_config *cfg, const lp_rak_params *p, 
     }
     lp_server *raw = s.get();
     s->worker = std::thread([raw] { raw->run(); });
-    s->admitter = std::thread([raw] { raw->admit_loop(); });
+    for (int i = 0; i < cfg->admitters; ++i)
+        s->admitters.emplace_back([raw] { raw->admit_loop(); });
     *out = s.release();
     return LP_OK;
 }
@@ -462,7 +471,8 @@ lp_status lp_server_destroy(lp_server *s)
     }
     s->cv_work.notify_all();
     s->cv_admit.notify_all();
-    if (s->admitter.joinable()) s->admitter.join();
+    for (std::thread &t : s->admitters)
+        if (t.joinable()) t.join();
     if (s->worker.joinable()) s->worker.join();
     for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
     delete s;
