@@ -861,10 +861,10 @@ def run_batch(args):
 # --------------------------------------------------------------------------
 # serving with continuous batching against one request at a time
 # --------------------------------------------------------------------------
-def serve_pool(count, seed=7):
+def serve_pool(count, seed=7, n_lo=10_000, n_hi=2_000_000):
     """Graphs of the serving stream: type uniform over SBM (mean degree 16,
     mixing 0.3), R-MAT (edge factor 8, 2^round(log2 n) vertices) and grid
-    (side floor(sqrt n)); n log-uniform in [10k, 2M]; weights 1-8."""
+    (side floor(sqrt n)); n log-uniform in [n_lo, n_hi] (10k-2M); weights 1-8."""
     import math
 
     import graphgen as gg
@@ -872,7 +872,7 @@ def serve_pool(count, seed=7):
     rng = np.random.default_rng(seed)
     out = []
     for i in range(count):
-        n = int(math.exp(rng.uniform(math.log(10_000), math.log(2_000_000))))
+        n = int(math.exp(rng.uniform(math.log(n_lo), math.log(n_hi))))
         kind = i % 3
         if kind == 0:
             out.append(gg.sbm_mixing(n, max(2, n // 500), 16.0, 0.3, seed=seed + i, wmin=1, wmax=8))
@@ -993,6 +993,43 @@ def measure_serve(args, ctx):
         lp.lp_labels_get(h)
         lp.lp_graph_destroy(h)
     seq_span = time.perf_counter() - sstart
+
+    # a burst of small graphs (n 1k-20k), where launches dominate and
+    # cohorts share them: served against one graph at a time
+    small = serve_pool(64, seed=17, n_lo=1_000, n_hi=20_000)
+    small_pinned = [tuple(torch.from_numpy(a).pin_memory() for a in (g.offsets, g.indices,
+                                                                      g.weights))
+                    for g in small]
+    small_picks = np.random.default_rng(19).integers(0, len(small), 4 * args.serve_saturation)
+
+    def small_burst(config):
+        srv = lp.lp_server_create(config, params)
+        t = time.perf_counter()
+        for rid, k in enumerate(small_picks):
+            o, x, w = small_pinned[k]
+            lp.lp_server_submit(srv, rid, o, x, w)
+        lp.lp_server_drain(srv)
+        span = time.perf_counter() - t
+        got = lp.lp_server_poll(srv, capacity=len(small_picks) + 1)
+        st = lp.lp_server_stats(srv)
+        lp.lp_server_destroy(srv)
+        return span, sum(1 for r in got if r.status != 0), st
+
+    small_burst(cfg)  # warm-up
+    sm_span, sm_err, sm_cohorts = small_burst(cfg)
+    single = lp.lp_server_config_default()
+    single.hbm_budget, single.max_active, single.streams = cfg.hbm_budget, cfg.max_active, cfg.streams
+    single.max_cohort = 1
+    sm1_span, sm1_err, _ = small_burst(single)
+    t = time.perf_counter()
+    for k in small_picks:
+        o, x, w = small_pinned[k]
+        h = lp.lp_graph_create(o, x, w)
+        lp.lp_rak_run(h, params)
+        lp.lp_modularity(h)
+        lp.lp_labels_get(h)
+        lp.lp_graph_destroy(h)
+    sm_seq = time.perf_counter() - t
     return {
         "metric": f"served graphs/s (Poisson {args.serve_rate:g} req/s)",
         "value": len(merged) / makespan, "unit": "graphs/s", "n_gpus": ctx.world,
@@ -1022,6 +1059,12 @@ def measure_serve(args, ctx):
                        "cohorts": sat_cohorts,
                        "how": "all requests submitted at t=0; the per-graph arm runs the same "
                               "requests one after another through lp_graph_create/lp_rak_run"},
+        "saturation_small": {"requests": len(small_picks), "errors": sm_err + sm1_err,
+                             "pool": "64 graphs, n log-uniform 1k-20k, same kinds and weights",
+                             "served_graphs_per_s": len(small_picks) / sm_span,
+                             "served_without_cohorts_graphs_per_s": len(small_picks) / sm1_span,
+                             "per_graph_launch_graphs_per_s": len(small_picks) / sm_seq,
+                             "cohorts": sm_cohorts},
         "cohorts": cohorts,
         "gpu_launches": int(launches),
         "clocks": clock_info,

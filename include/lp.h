@@ -275,9 +275,10 @@ typedef struct {
     int32_t streams;    /* CUDA streams the cohorts are spread over, 1..64 (default 8) */
     int32_t max_cohort; /* requests ingested and iterated together, >= 1 (default 16;
                            1 = every request on its own) */
-    int32_t admitters;  /* threads that ingest admitted requests, 1..16 (default 4) */
+    int32_t admitters;  /* threads that ingest admitted requests, 1..16 (default 2) */
     int64_t cohort_max_entries; /* a graph with more CSR entries is admitted on its own
-                                   (default 2^22; small graphs gain from sharing launches) */
+                                   (default 2^18: launch-bound small graphs gain from
+                                   sharing launches, larger ones keep the GPU busy alone) */
 } lp_server_config;
 
 typedef struct {

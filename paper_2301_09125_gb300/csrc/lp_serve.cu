@@ -353,8 +353,8 @@ lp_status lp_server_config_default(lp_server_config *cfg)
     cfg->max_active = 64;
     cfg->streams = 8;
     cfg->max_cohort = 16;
-    cfg->admitters = 4;
-    cfg->cohort_max_entries = (int64_t)1 << 22;
+    cfg->admitters = 2;
+    cfg->cohort_max_entries = (int64_t)1 << 18;
     return LP_OK;
 }
 

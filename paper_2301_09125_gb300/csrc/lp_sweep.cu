@@ -37,6 +37,8 @@
 // order in which entries were accumulated.  Weights are summed in int32 (the
 // library rejects graphs whose per-vertex weight sum reaches 2^31), so
 // results are bit-exact.
+#include <algorithm>
+
 #include "lp_device.cuh"
 #include "lp_internal.cuh"
 
@@ -1112,7 +1114,8 @@ __device__ __forceinline__ uint2 block_sum2(uint32_t x, uint32_t y, uint32_t *s)
 // cta bucket: one CTA per vertex, shared table
 // ----------------------------------------------------------------------------
 template <int NT, int CAP, bool MULTI>
-__global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 1536 / NT) k_cta(SweepArgs a)
+__global__ void __launch_bounds__(NT, NT >= 512 ? 2 : (1536 / NT < 32 ? 1536 / NT : 32))
+    k_cta(SweepArgs a)
 {
     if (a.stop && *a.stop) return;  // launched past the end of the run
     extern __shared__ unsigned long long smem64[];
@@ -1791,6 +1794,15 @@ __global__ void __launch_bounds__(HUB_THREADS, 2) k_hub_merge(SweepArgs a)
     if (!MULTI && threadIdx.x == 0 && my_changed) atomicAdd(a.changed, (int)my_changed);
 }
 
+// CTAs of nt threads and smem bytes of dynamic shared memory that fit one SM
+// at once (at most 32 CTAs, 2048 threads and 227 KB per SM)
+constexpr int resident_ctas(int nt, size_t smem)
+{
+    const int by_threads = 2048 / nt < 32 ? 2048 / nt : 32;
+    const int by_smem = (int)((size_t)232448 / (smem + 1024));
+    return by_threads < by_smem ? by_threads : by_smem;
+}
+
 template <bool MULTI>
 int launch(int bucket, const SweepArgs &a, int num_sms, cudaStream_t st)
 {
@@ -1817,15 +1829,16 @@ int launch(int bucket, const SweepArgs &a, int num_sms, cudaStream_t st)
         blocks = a.len;
         if ((m = launch_major<MULTI>(a, num_sms, st)) < 0) return -1;
         n += m;
-        k_cta<CTA_THREADS, CTA_TABLE, MULTI>
-            <<<(int)(blocks < num_sms * 16 ? blocks : num_sms * 16), CTA_THREADS, cta_smem, st>>>(a);
+        blocks = std::min<int64_t>(blocks, (int64_t)num_sms * resident_ctas(CTA_THREADS, cta_smem));
+        k_cta<CTA_THREADS, CTA_TABLE, MULTI><<<(int)blocks, CTA_THREADS, cta_smem, st>>>(a);
         break;
     case 3:
         blocks = a.len;
         if ((m = launch_major<MULTI>(a, num_sms, st)) < 0) return -1;
         n += m;
-        k_cta<CTA2_THREADS, CTA2_TABLE, MULTI>
-            <<<(int)(blocks < num_sms * 8 ? blocks : num_sms * 8), CTA2_THREADS, cta2_smem, st>>>(a);
+        blocks =
+            std::min<int64_t>(blocks, (int64_t)num_sms * resident_ctas(CTA2_THREADS, cta2_smem));
+        k_cta<CTA2_THREADS, CTA2_TABLE, MULTI><<<(int)blocks, CTA2_THREADS, cta2_smem, st>>>(a);
         break;
     default: {
         n = 0;
