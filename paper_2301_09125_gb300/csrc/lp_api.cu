@@ -1756,6 +1756,8 @@ struct GraphSet {
         ma.ne = ne;
         ma.first_row = pk_first;
         ma.ncopy = pack_chunks(ne);
+        ma.nsmall = bl[0];  // the small bucket leads the list (and so the packed rows)
+        ma.e_lo = be[0];
         ma.vgraph = vgraph;
         ma.g_vbase = g_vbase;
         ma.kc = kc;

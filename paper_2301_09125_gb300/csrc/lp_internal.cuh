@@ -176,6 +176,11 @@ struct ModArgs {
     int64_t ne;                // entries in the arena
     const int64_t *first_row;  // ncopy + 1 entries
     int64_t ncopy;
+    // the list's first nsmall items (the small bucket) hold the entries
+    // [0, e_lo): their rows are summed one per lane, and the chunk pass
+    // counts only entries from e_lo on (chunks from e_lo / PACK_CHUNK)
+    int64_t nsmall;
+    int64_t e_lo;
     const int32_t *vgraph;     // null for a single graph
     const int32_t *g_vbase;
     unsigned long long *kc;    // [nv] K_c of community c of graph g at vbase_g + c (zeroed)

@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(MT) k_mod_entries(ModArgs a)
     __shared__ unsigned long long s_dom;  // K part of the block's first community
     __shared__ int64_t s_dom_slot;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int64_t chunk = (int64_t)blockIdx.x * MW + wib;
+    const int64_t chunk = a.e_lo / CH + (int64_t)blockIdx.x * MW + wib;
     const bool have = chunk < a.ncopy;  // warp-uniform
     int32_t *s_rp = s_rp_all[wib];
     int32_t *s_c = s_c_all[wib];
@@ -183,6 +183,12 @@ __global__ void __launch_bounds__(MT) k_mod_entries(ModArgs a)
                 u[q] = in ? a.idx[j0 + q] : 0;
                 w[q] = in ? (a.wts ? a.wts[j0 + q] : 1) : 0;
             }
+        }
+        // entries of the small rows (summed one row per lane) count as absent
+        if (j0 < a.e_lo) {
+#pragma unroll
+            for (int q = 0; q < MPER; ++q)
+                if (j0 + q < a.e_lo) w[q] = 0;
         }
         // rows of the entries (shared memory), then every label gather in flight
         int kq[MPER];
@@ -254,6 +260,57 @@ __global__ void __launch_bounds__(MT) k_mod_entries(ModArgs a)
     if (threadIdx.x == 0 && s_dom) atomicAdd(a.kc + dom, s_dom);
 }
 
+// The rows of the small bucket (the list's first nsmall items, at most 32
+// entries each), one row per lane: its weight k_v and the weight of its
+// entries whose neighbour carries its label; k_v goes to K of its community,
+// combined over the lanes of the same community.
+template <bool MULTI>
+__global__ void __launch_bounds__(256) k_mod_small(ModArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long l = 0, w2 = 0;
+    for (int64_t base = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32;
+         base < a.nsmall; base += warps * 32) {  // warp-uniform bounds
+        const int64_t i = base + lane;
+        const bool valid = i < a.nsmall;
+        int32_t c = EMPTY, g = 0;
+        int64_t vb = 0;
+        uint32_t kv = 0u, lv = 0u;
+        if (valid) {
+            const int32_t v = a.list[i];
+            if (MULTI) {
+                g = a.vgraph[v];
+                vb = a.g_vbase[g];
+            }
+            c = a.lab[v];
+            const int64_t e1 = a.rp[i + 1];
+            for (int64_t e = a.rp[i]; e < e1; ++e) {
+                const int32_t u = a.idx[e] & MOD_ID_MASK;
+                const uint32_t w = a.wts ? (uint32_t)a.wts[e] : 1u;
+                kv += w;
+                if (__ldg(a.lab + vb + u) == c) lv += w;
+            }
+        }
+        const int64_t slot = valid ? vb + c : -1;
+        const unsigned grp = __match_any_sync(FULL, (unsigned long long)slot);
+        const unsigned long long sum = group_sum(grp, kv);
+        if (valid && lane == __ffs(grp) - 1 && sum) atomicAdd(a.kc + slot, sum);
+        if (MULTI) {  // L and 2m: one pair of atomics per graph the warp's rows meet
+            const unsigned gm = __match_any_sync(FULL, valid ? g : -1);
+            const unsigned long long ls = group_sum(gm, lv), ks = group_sum(gm, kv);
+            if (valid && lane == __ffs(gm) - 1 && ks) {
+                atomicAdd(a.acc + 4 * (int64_t)g, ls);
+                atomicAdd(a.acc + 4 * (int64_t)g + 1, ks);
+            }
+        } else {
+            l += lv;
+            w2 += kv;
+        }
+    }
+    if (!MULTI) block_flush_lw(a.acc, l, w2);
+}
+
 // one graph: 128-bit sums over the warp, then the block, then one add
 __device__ __forceinline__ void sumsq_block_add(unsigned long long *s_acc, unsigned long long hi,
                                                 unsigned long long lo)
@@ -319,8 +376,18 @@ __global__ void __launch_bounds__(256) k_mod_sumsq(ModArgs a, int64_t nslots)
 int modularity_launch(const ModArgs &a, int64_t nslots, bool multi, cudaStream_t st,
                       int64_t *launches)
 {
-    if (a.ne > 0 && a.ncopy > 0) {
-        const unsigned blocks = (unsigned)((a.ncopy + MW - 1) / MW);
+    if (a.nsmall > 0) {
+        const int64_t b = (a.nsmall + 255) / 256;
+        const unsigned blocks = (unsigned)(b < 8192 ? b : 8192);
+        if (multi)
+            k_mod_small<true><<<blocks, 256, 0, st>>>(a);
+        else
+            k_mod_small<false><<<blocks, 256, 0, st>>>(a);
+        ++*launches;
+    }
+    const int64_t chunks = a.ncopy - a.e_lo / PACK_CHUNK;  // from the chunk holding e_lo
+    if (a.ne > a.e_lo && chunks > 0) {
+        const unsigned blocks = (unsigned)((chunks + MW - 1) / MW);
         if (multi)
             k_mod_entries<true><<<blocks, MT, 0, st>>>(a);
         else
