@@ -906,7 +906,7 @@ struct GraphSet {
         LP_TRY(dev_alloc(&scratch, pack_scratch_ints(len), "packing scratch", st, device));
         Launches L;
         int rc = pack_rows(waves > 1 ? wlist : list, len, off, idx, wts, ne, vgraph, g_vbase,
-                           g_ebase, waves, scratch, pk_rp, pk_first, pk_idx, pk_wts, st, &L.n);
+                           g_ebase, waves, be, scratch, pk_rp, pk_first, pk_idx, pk_wts, st, &L.n);
         if (rc == 0 && bl[HUB_BUCKET] > 0) {
             const int64_t hub0 = waves > 1 ? wstart[(size_t)HUB_BUCKET * waves] : bb[HUB_BUCKET];
             rc = hub_task_starts(waves > 1 ? htask_w : htask, bl[HUB_BUCKET], pk_rp + hub0, st,

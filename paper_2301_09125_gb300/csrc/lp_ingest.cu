@@ -590,18 +590,43 @@ __global__ void __launch_bounds__(PK_SCAN) k_pack_rp(const int32_t *list, int64_
 // wave classes are staged in the warp's shared memory with the row of every
 // entry of the chunk; lane l copies entries l, l + 32, ..., so every load and
 // store of the warp covers 32 consecutive entries.
+// Order in which the copy visits its chunks: the chunks of bucket b's region
+// [c0[b], c0[b + 1]) (its W wave segments one after another, of about q[b]
+// chunks each) are taken in turn from every segment, so that the W warps
+// copying rows of neighbouring vertices (the same source sectors) run at
+// about the same time and the sectors are read from DRAM once.  nreg = 0:
+// chunk order.
+struct PackOrder {
+    int32_t nreg;
+    uint32_t waves;
+    int64_t c0[NUM_BUCKETS + 1];
+    int64_t q[NUM_BUCKETS];
+    int64_t slot0[NUM_BUCKETS + 1];
+};
+
+__device__ __forceinline__ int64_t pack_chunk_of(const PackOrder &o, int64_t t)
+{
+    if (o.nreg == 0) return t;
+    int b = 0;
+    while (b + 1 < o.nreg && t >= o.slot0[b + 1]) ++b;
+    if (t >= o.slot0[o.nreg]) return -1;
+    const int64_t r = t - o.slot0[b];
+    const int64_t c = o.c0[b] + (r % o.waves) * o.q[b] + r / o.waves;
+    return c < o.c0[b + 1] ? c : -1;
+}
+
 __global__ void __launch_bounds__(PK_T) k_pack_rows(const int64_t *rp, const int64_t *srcw,
                                                     const int64_t *first_row, int64_t ncopy,
                                                     const int32_t *idx, const int32_t *wts,
                                                     int64_t ne, uint32_t waves, uint64_t magic,
-                                                    int32_t *pidx, int32_t *pwts)
+                                                    PackOrder order, int32_t *pidx, int32_t *pwts)
 {
     __shared__ int64_t s_rp_all[PK_WARPS][PK_OUT + 2];
     __shared__ int64_t s_src_all[PK_WARPS][PK_OUT + 1];
     __shared__ uint16_t s_row_all[PK_WARPS][PK_OUT];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int64_t chunk = (int64_t)blockIdx.x * PK_WARPS + wib;
-    if (chunk >= ncopy) return;  // warp-uniform
+    const int64_t chunk = pack_chunk_of(order, (int64_t)blockIdx.x * PK_WARPS + wib);
+    if (chunk < 0 || chunk >= ncopy) return;  // warp-uniform
     int64_t *s_rp = s_rp_all[wib];
     int64_t *s_src = s_src_all[wib];
     uint16_t *s_row = s_row_all[wib];
@@ -862,9 +887,9 @@ int64_t pack_scratch_ints(int64_t len)
 
 int pack_rows(const int32_t *list, int64_t len, const int32_t *off, const int32_t *idx,
               const int32_t *wts, int64_t ne, const int32_t *vgraph, const int32_t *g_vbase,
-              const int64_t *g_ebase, int waves, int64_t *scratch, int64_t *rp,
-              int64_t *first_row, int32_t *pidx, int32_t *pwts, cudaStream_t st,
-              int64_t *launches)
+              const int64_t *g_ebase, int waves, const int64_t *bucket_entries,
+              int64_t *scratch, int64_t *rp, int64_t *first_row, int32_t *pidx, int32_t *pwts,
+              cudaStream_t st, int64_t *launches)
 {
     if (waves < 1) return -1;
     if (len == 0) return cudaMemsetAsync(rp, 0, sizeof(int64_t), st) == cudaSuccess ? 0 : -1;
@@ -879,10 +904,28 @@ int pack_rows(const int32_t *list, int64_t len, const int32_t *off, const int32_
                                               ncopy);
     *launches += 3;
     if (ne > 0) {
-        k_pack_rows<<<(int)((ncopy + PK_WARPS - 1) / PK_WARPS), PK_T, 0, st>>>(
-            rp, srcw, first_row, ncopy, idx, wts, ne,
-                                                  (uint32_t)waves, magic, pidx,
-                                                  wts ? pwts : nullptr);
+        PackOrder order{};
+        int64_t slots = ncopy;
+        if (waves > 1 && bucket_entries) {
+            order.nreg = NUM_BUCKETS;
+            order.waves = (uint32_t)waves;
+            int64_t e = 0;
+            order.slot0[0] = 0;
+            for (int b = 0; b < NUM_BUCKETS; ++b) {
+                order.c0[b] = e / PK_OUT;
+                e += bucket_entries[b];
+            }
+            order.c0[NUM_BUCKETS] = ncopy;
+            for (int b = 0; b < NUM_BUCKETS; ++b) {
+                const int64_t nc = order.c0[b + 1] - order.c0[b];
+                order.q[b] = (nc + waves - 1) / waves;
+                order.slot0[b + 1] = order.slot0[b] + order.q[b] * waves;
+            }
+            slots = order.slot0[NUM_BUCKETS];
+        }
+        k_pack_rows<<<(int)((slots + PK_WARPS - 1) / PK_WARPS), PK_T, 0, st>>>(
+            rp, srcw, first_row, ncopy, idx, wts, ne, (uint32_t)waves, magic, order, pidx,
+            wts ? pwts : nullptr);
         ++*launches;
     }
     return cudaGetLastError() == cudaSuccess ? 0 : -1;

@@ -269,13 +269,16 @@ int hub_task_starts(HubTask *tasks, int64_t n, const int64_t *rp, cudaStream_t s
 // waves > 1 and the neighbour's wave (local id mod waves) comes before the
 // row's; first_row (pack_chunks(ne) + 1 entries) receives the item holding
 // each PACK_CHUNK-th entry.  scratch: pack_scratch_ints(len) int64.
+// bucket_entries (host, NUM_BUCKETS, or null): the entries of each bucket's
+// rows, the list being bucket-major; the copy then takes the wave segments
+// of a bucket in turn (results do not depend on it).
 int64_t pack_scratch_ints(int64_t len);
 inline int64_t pack_chunks(int64_t ne) { return (ne + PACK_CHUNK - 1) / PACK_CHUNK; }
 int pack_rows(const int32_t *list, int64_t len, const int32_t *off, const int32_t *idx,
               const int32_t *wts, int64_t ne, const int32_t *vgraph, const int32_t *g_vbase,
-              const int64_t *g_ebase, int waves, int64_t *scratch, int64_t *rp,
-              int64_t *first_row, int32_t *pidx, int32_t *pwts, cudaStream_t st,
-              int64_t *launches);
+              const int64_t *g_ebase, int waves, const int64_t *bucket_entries,
+              int64_t *scratch, int64_t *rp, int64_t *first_row, int32_t *pidx, int32_t *pwts,
+              cudaStream_t st, int64_t *launches);
 // Task index of every segment item and partition item of the first nbig tasks.
 int hub_item_maps(const HubTask *tasks, int64_t nbig, int32_t *seg_task, int32_t *part_task,
                   cudaStream_t st, int64_t *launches);
