@@ -285,11 +285,23 @@ __global__ void __launch_bounds__(256) k_mod_small(ModArgs a)
             }
             c = a.lab[v];
             const int64_t e1 = a.rp[i + 1];
-            for (int64_t e = a.rp[i]; e < e1; ++e) {
-                const int32_t u = a.idx[e] & MOD_ID_MASK;
-                const uint32_t w = a.wts ? (uint32_t)a.wts[e] : 1u;
-                kv += w;
-                if (__ldg(a.lab + vb + u) == c) lv += w;
+            for (int64_t e = a.rp[i]; e < e1; e += 4) {  // four entries, then four gathers, in flight
+                int32_t u[4];
+                uint32_t w[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const bool in = e + q < e1;
+                    u[q] = in ? a.idx[e + q] & MOD_ID_MASK : 0;
+                    w[q] = in ? (a.wts ? (uint32_t)a.wts[e + q] : 1u) : 0u;
+                }
+                int32_t cu[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) cu[q] = w[q] ? __ldg(a.lab + vb + u[q]) : EMPTY;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    kv += w[q];
+                    if (cu[q] == c) lv += w[q];
+                }
             }
         }
         const int64_t slot = valid ? vb + c : -1;
