@@ -317,7 +317,7 @@ struct GraphSet {
     std::vector<int64_t> hmulti_w, hsegs_w, hparts_w, hsegs_at_w, hparts_at_w;
     int32_t *hseg_task = nullptr, *hpart_task = nullptr;      // plain list
     int32_t *hseg_task_w = nullptr, *hpart_task_w = nullptr;  // wave lists, wave after wave
-    int4 *hrec = nullptr;
+    int32_t *hrec = nullptr;
     int32_t *hpoff = nullptr;
     uint4 *hpbest = nullptr;
     unsigned long long *hkey = nullptr;
@@ -652,7 +652,8 @@ struct GraphSet {
             hsegs = tot[2];
             hparts = tot[3];
             const int64_t slots = tot[1] > 0 ? tot[1] : 1;
-            LP_TRY(dev_alloc(&hrec, (tot[2] > 0 ? tot[2] : 1) * HUB_SEG, "hub records", st, device));
+            LP_TRY(dev_alloc(&hrec, (tot[2] > 0 ? tot[2] : 1) * (int64_t)HUB_REC * HUB_SEG,
+                             "hub records", st, device));
             LP_TRY(dev_alloc(&hpoff, tot[4] > 0 ? tot[4] : 1, "hub partition offsets", st, device));
             LP_TRY(dev_alloc(&hpbest, 2 * (tot[3] > 0 ? tot[3] : 1), "hub partition bests", st,
                              device));

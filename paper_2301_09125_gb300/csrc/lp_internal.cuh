@@ -56,6 +56,7 @@ constexpr int HUB_THREADS = 512;
 constexpr int HUB_TABLE = 8192;         // shared slots per hub CTA (>= 2 * HUB_ONE_MAX)
 constexpr int HUB_ONE_MAX = 4096;       // longest hub row swept by one CTA
 constexpr int HUB_SEG = 4096;           // entries per segment of a longer row
+constexpr int HUB_REC = 3;              // ints per segment record (label, sum, ~first position)
 constexpr int HUB_PMAX = 2048;          // most label partitions of one row
 
 // One hub of a list being swept (the hub bucket, or its part in one wave),
@@ -125,8 +126,8 @@ struct SweepArgs {
     int32_t small_mean_deg;
     // hub launches: the list's tasks (aligned with `list`), how many of them
     // are rows longer than HUB_ONE_MAX, with their segment and partition item
-    // counts; segment records (HUB_SEG int4 per segment item: label, sum,
-    // ~first position), partition offsets, partition bests (32 bytes per
+    // counts; segment records (HUB_SEG records of HUB_REC ints per segment
+    // item: label, sum, ~first position), partition offsets, partition bests (32 bytes per
     // partition item); fallback tables (slot = (label + 1) << 32 | summed
     // weight, 0 when free, plus ~first position), used-slot lists and
     // per-task counters of finished partitions and used slots (zero between
@@ -137,7 +138,7 @@ struct SweepArgs {
     int64_t hparts;
     const int32_t *hseg_task;   // task of each segment item
     const int32_t *hpart_task;  // task of each partition item
-    int4 *hrec;
+    int32_t *hrec;
     int32_t *hpoff;
     void *hpbest;
     unsigned long long *hkey;

@@ -1635,7 +1635,7 @@ __global__ void __launch_bounds__(HUB_THREADS, 2) k_hub_seg(SweepArgs a)
         const int64_t lo = x.e0 + (int64_t)seg * HUB_SEG;
         const int64_t hi = min(lo + HUB_SEG, x.e0 + x.d);
         const int np = t.npart;
-        int4 *out = a.hrec + item * HUB_SEG;
+        int32_t *out = a.hrec + item * (HUB_REC * HUB_SEG);
         int32_t *poff = a.hpoff + t.poff0 + (int64_t)seg * (np + 1);
         if (hub_settled<MULTI>(a, ti, x.g, x.own) != EMPTY) {  // no records
             for (int q = threadIdx.x; q <= np; q += NT) poff[q] = 0;
@@ -1647,7 +1647,9 @@ __global__ void __launch_bounds__(HUB_THREADS, 2) k_hub_seg(SweepArgs a)
                                                a.strict, s_red);
             if (threadIdx.x == 0) {
                 s_cnt[0] = best.sum > 0 ? (int)part_of(best.label, (uint32_t)np) : -1;
-                out[0] = make_int4(best.label, (int)best.sum, (int)best.npos, 0);
+                out[0] = best.label;
+                out[1] = (int)best.sum;
+                out[2] = (int)best.npos;
             }
             __syncthreads();
             const int bp = s_cnt[0];
@@ -1668,7 +1670,9 @@ __global__ void __launch_bounds__(HUB_THREADS, 2) k_hub_seg(SweepArgs a)
             const int32_t key = tk[j];
             if (key != EMPTY) {
                 const int at = atomicAdd(&s_cnt[part_of(key, (uint32_t)np)], 1);
-                out[at] = make_int4(key, ts[j], (int)tp[j], 0);
+                out[HUB_REC * at] = key;
+                out[HUB_REC * at + 1] = ts[j];
+                out[HUB_REC * at + 2] = (int)tp[j];
                 tk[j] = EMPTY;
                 ts[j] = 0;
                 tp[j] = 0;
@@ -1734,9 +1738,10 @@ __global__ void __launch_bounds__(HUB_THREADS, 2) k_hub_merge(SweepArgs a)
             }
             __syncthreads();
             for (int s = 0; s < ns; ++s) {
-                const int4 *rec = a.hrec + (int64_t)(t.seg0 + s0 + s) * HUB_SEG;
+                const int32_t *rec = a.hrec + (int64_t)(t.seg0 + s0 + s) * (HUB_REC * HUB_SEG);
                 for (int r = s_rb[s] + threadIdx.x; r < s_re[s]; r += NT) {
-                    const int4 R = __ldcs(rec + r);
+                    const int4 R = make_int4(__ldg(rec + HUB_REC * r), __ldg(rec + HUB_REC * r + 1),
+                                             __ldg(rec + HUB_REC * r + 2), 0);
                     if (!table_add(tk, ts, tp, LG, PROBE, R.x, R.y, 0xFFFFFFFFu - (uint32_t)R.z)) {
                         const int64_t c =
                             global_add(gk, gp, glg, R.x, (uint32_t)R.y, (uint32_t)R.z);
