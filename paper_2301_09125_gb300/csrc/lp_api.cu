@@ -1673,10 +1673,13 @@ struct GraphSet {
             cs.glg_max = glg;
             for (int32_t k = 0; k < waves; ++k) {
                 cs.wave_k = k;
-                cs.rows_cta = crows + h_cstart[(size_t)k];
-                cs.n_cta = h_cstart[(size_t)k + 1] - h_cstart[(size_t)k];
-                cs.rows_big = crows + h_cstart[(size_t)waves + k];
-                cs.n_big = h_cstart[(size_t)waves + k + 1] - h_cstart[(size_t)waves + k];
+                auto bin = [&](int kind) { return (size_t)kind * waves + k; };
+                cs.rows_warp = crows + h_cstart[bin(0)];
+                cs.n_warp = h_cstart[bin(0) + 1] - h_cstart[bin(0)];
+                cs.rows_cta = crows + h_cstart[bin(1)];
+                cs.n_cta = h_cstart[bin(1) + 1] - h_cstart[bin(1)];
+                cs.rows_big = crows + h_cstart[bin(2)];
+                cs.n_big = h_cstart[bin(2) + 1] - h_cstart[bin(2)];
                 cs.ovf = covf;
                 if (copra_step(cs, num_sms, st, &L0.n) != 0)
                     return fail(LP_ECUDA, cuda_msg("COPRA launch", cudaGetLastError()));

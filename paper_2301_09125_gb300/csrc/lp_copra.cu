@@ -12,8 +12,9 @@
 // kept label) and stores them sorted.  A vertex without edges is its own
 // community.  Asynchronous runs go in waves as RAK's do.
 //
-// Rows of at most CPW_PAIRS pairs (with L <= 32) take one warp and a
-// 256-slot table of the warp's own in shared memory; longer rows of at most
+// Rows of at most 32 pairs (with L <= 8) take 8 lanes (four rows per warp)
+// and a 64-slot table, rows of at most CPW_PAIRS pairs (with L <= 32) one warp
+// and a 256-slot table of the warp's own in shared memory; longer rows of at most
 // CP_PAIRS pairs take one CTA and a 4096-slot shared table; longer ones one
 // CTA each with a region of a global table (a launch of copra_big_ctas()
 // CTAs).  Rows that need a CTA are listed once per run, by wave and kind, so
@@ -204,47 +205,87 @@ struct CpGlobal {
     }
 };
 
-// One COPRA step for the rows of wave wave_k with at most CPW_PAIRS pairs
-// (rows without entries included), L <= CPW_MAX_L: one warp per vertex,
-// which keeps the kept pairs one per lane.
+// Best candidate and 64-bit sum over the GS lanes of a group (mask m).
+template <int GS>
+__device__ __forceinline__ CpCand cp_group_best(CpCand c, unsigned m)
+{
+#pragma unroll
+    for (int o = GS / 2; o >= 1; o >>= 1) {
+        CpCand y;
+        y.t = __shfl_xor_sync(m, c.t, o);
+        y.h = __shfl_xor_sync(m, c.h, o);
+        y.first = __shfl_xor_sync(m, c.first, o);
+        y.slot = __shfl_xor_sync(m, c.slot, o);
+        if (cp_better(y, c)) c = y;
+    }
+    return c;
+}
+
+template <int GS>
+__device__ __forceinline__ unsigned long long cp_group_sum(unsigned long long v, unsigned m)
+{
+#pragma unroll
+    for (int o = GS / 2; o >= 1; o >>= 1) v += __shfl_xor_sync(m, v, o);
+    return v;
+}
+
+// One COPRA step for the rows of wave wave_k with at most 4 GS pairs (rows
+// without entries included, L <= GS): a group of GS lanes per vertex (GS =
+// 8: four vertices per warp; GS = 32: one), which keeps the kept pairs one
+// per lane.  A table of 8 GS slots per group.  The GS = 32 launch takes the
+// rows the GS = 8 launch leaves (more than 32 pairs, or L > 8).
+template <int GS>
 __global__ void __launch_bounds__(CPW_WARPS * 32) k_copra_warp(CopraArgs a)
 {
+    constexpr int GT = 8 * GS;       // slots per group
+    constexpr int GP = 4 * GS;       // pairs per group's row at most
+    constexpr int NG = 32 / GS;      // groups per warp
     __shared__ int32_t s_key[CPW_WARPS * CPW_TAB];
     __shared__ uint32_t s_lo[CPW_WARPS * CPW_TAB];
     __shared__ uint32_t s_hi[CPW_WARPS * CPW_TAB];
     __shared__ uint32_t s_first[CPW_WARPS * CPW_TAB];
+    static_assert(NG * GT == CPW_TAB, "a warp's groups share its 256 slots");
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int o = wib * CPW_TAB;
+    const int grp = lane / GS, gl = lane % GS;
+    const unsigned gm = GS == 32 ? FULL : (((1u << GS) - 1u) << (grp * GS));
+    const int o = wib * CPW_TAB + grp * GT;
     const CpShared tab{s_key + o, s_lo + o, s_hi + o, s_first + o};
-    for (int j = lane; j < CPW_TAB; j += 32) tab.clear(j);
+    for (int j = gl; j < GT; j += GS) tab.clear(j);
     __syncwarp();
 
     const uint32_t L = (uint32_t)a.L;
     const int64_t W = a.waves;
-    const int64_t nw = (int64_t)a.n > (int64_t)a.wave_k ? ((int64_t)a.n - a.wave_k + W - 1) / W : 0;
-    const int64_t tw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    // the wave's vertices (v = wave_k + i W), or the listed rows when a.rows is set
+    const int64_t nw = a.rows ? a.nrows
+                              : ((int64_t)a.n > (int64_t)a.wave_k
+                                     ? ((int64_t)a.n - a.wave_k + W - 1) / W
+                                     : 0);
+    const int64_t ng = (((int64_t)gridDim.x * blockDim.x) >> 5) * NG;
     uint32_t my_changed = 0;
-    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nw; i += tw) {
-        const int32_t v = (int32_t)(a.wave_k + i * W);
+    for (int64_t i = ((((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * NG) + grp; i < nw;
+         i += ng) {
+        const int32_t v = a.rows ? a.rows[i] : (int32_t)(a.wave_k + i * W);
         const int32_t rs = __ldg(a.off + v), d = __ldg(a.off + v + 1) - rs;
         const int64_t pairs = (int64_t)d * L;
-        if (pairs > CPW_PAIRS) continue;  // a CTA kernel's row (warp-uniform)
+        // group-uniform: the other launch's rows
+        if (GS == 32 ? (pairs > CPW_PAIRS || (L <= 8 && pairs <= 32)) : (L > 8 || pairs > GP))
+            continue;
         const int32_t prev = a.cur_l[(int64_t)v * L];
         int32_t *out_l = a.nxt_l + (int64_t)v * L;
         uint32_t *out_b = a.nxt_b + (int64_t)v * L;
         if (d == 0) {  // no labels: the vertex is its own community
-            if ((uint32_t)lane < L) {
-                out_l[lane] = lane == 0 ? v : EMPTY;
-                out_b[lane] = lane == 0 ? COPRA_ONE : 0u;
+            for (uint32_t s = gl; s < L; s += GS) {
+                out_l[s] = s == 0 ? v : EMPTY;
+                out_b[s] = s == 0 ? COPRA_ONE : 0u;
             }
-            if (lane == 0 && prev != v) ++my_changed;
+            if (gl == 0 && prev != v) ++my_changed;
             continue;
         }
-        const int lg = ilog2_ceil((uint32_t)(2 * pairs));  // 2^lg >= 2 pairs
+        const int lg = ilog2_ceil((uint32_t)(2 * pairs));  // 2^lg >= 2 pairs (<= GT)
         const int slots = 1 << lg;
         // T(l) and first appearance over the row's entries and their speakers' pairs
         uint32_t wsum = 0u;
-        for (int32_t e = lane; e < d; e += 32) {
+        for (int32_t e = gl; e < d; e += GS) {
             const int32_t u = __ldg(a.idx + rs + e);
             const uint32_t w = a.wts ? (uint32_t)__ldg(a.wts + rs + e) : 1u;
             wsum += w;
@@ -257,16 +298,17 @@ __global__ void __launch_bounds__(CPW_WARPS * 32) k_copra_warp(CopraArgs a)
                 tab.add(lg, ul[p], (unsigned long long)w * b, (uint32_t)e * 64u + p);
             }
         }
-        wsum = __reduce_add_sync(FULL, wsum);  // < 2^31 (checked at ingest)
-        __syncwarp();
-        // the labels above the threshold, one per lane from lane 0 on, and the best label
+        wsum = __reduce_add_sync(gm, wsum);  // < 2^31 (checked at ingest)
+        __syncwarp(gm);
+        // the labels above the threshold, one per lane from the group's lane 0
+        // on, and the best label
         const unsigned long long wt = (unsigned long long)wsum * COPRA_ONE;
         const uint64_t ktv = stream_at(a.key_t, (uint64_t)v + 1);
         CpCand best{0ull, 0ull, 0ull, -1};
         int32_t mine = -1;  // the kept slot this lane holds
         int nk = 0;
-        for (int base = 0; base < slots; base += 32) {
-            const int j = base + lane;
+        for (int base = 0; base < slots; base += GS) {
+            const int j = base + gl;
             bool kept = false;
             if (j < slots) {
                 const int32_t l = tab.key[j];
@@ -278,48 +320,50 @@ __global__ void __launch_bounds__(CPW_WARPS * 32) k_copra_warp(CopraArgs a)
                     if (cp_better(c, best)) best = c;
                 }
             }
-            const unsigned m = __ballot_sync(FULL, kept);
+            const unsigned m = (__ballot_sync(gm, kept) & gm) >> (grp * GS);
             const int nm = __popc(m);
-            // lane nk + k takes the slot of the k-th kept lane of this round
-            const int k = lane - nk;
+            // lane nk + k of the group takes the slot of the k-th kept lane of this round
+            const int k = gl - nk;
             const int src = (k >= 0 && k < nm) ? (int)__fns(m, 0, k + 1) : 0;
-            const int js = __shfl_sync(FULL, j, src);
+            const int js = __shfl_sync(gm, j, src, GS);
             if (k >= 0 && k < nm) mine = js;
             nk += nm;  // at most L labels reach the threshold (their T sum to W * 2^16)
         }
-        best = cp_warp_best(best);
+        best = cp_group_best<GS>(best, gm);
         if (nk > (int)L) nk = (int)L;  // never (see above); keeps the stores inside the set
         if (nk == 0) {  // none above the threshold: the best label alone
-            mine = lane == 0 ? best.slot : -1;
+            mine = gl == 0 ? best.slot : -1;
             nk = 1;
         }
         // normalize in fixed point, the remainder to the best label (always kept)
-        const bool hold = lane < nk;
+        const bool hold = gl < nk;
         const unsigned long long ti = hold ? tab.t(mine) : 0ull;
-        const unsigned long long tk = cp_warp_sum(ti);
+        const unsigned long long tk = cp_group_sum<GS>(ti, gm);
         uint32_t bv = hold ? (uint32_t)((ti * COPRA_ONE) / tk) : 0u;
-        const uint32_t bsum = __reduce_add_sync(FULL, bv);
+        const uint32_t bsum = __reduce_add_sync(gm, bv);
         if (hold && mine == best.slot) bv += COPRA_ONE - bsum;
         // store by decreasing belonging, equal belongings by first appearance
         const uint32_t fi = hold ? tab.first[mine] : 0xFFFFFFFFu;
         const int32_t li = hold ? tab.key[mine] : EMPTY;
         int rank = 0;
         for (int q = 0; q < nk; ++q) {
-            const uint32_t bq = __shfl_sync(FULL, bv, q), fq = __shfl_sync(FULL, fi, q);
+            const uint32_t bq = __shfl_sync(gm, bv, q, GS), fq = __shfl_sync(gm, fi, q, GS);
             rank += (bq > bv || (bq == bv && fq < fi)) ? 1 : 0;
         }
         if (hold) {
             out_l[rank] = li;
             out_b[rank] = bv;
             if (rank == 0 && li != prev) ++my_changed;
-        } else if ((uint32_t)lane < L) {
-            out_l[lane] = EMPTY;
-            out_b[lane] = 0u;
         }
-        __syncwarp();
-        for (int j = lane; j < slots; j += 32) tab.clear(j);  // leave the table clean
-        __syncwarp();
+        for (uint32_t s = (uint32_t)nk + gl; s < L; s += GS) {
+            out_l[s] = EMPTY;
+            out_b[s] = 0u;
+        }
+        __syncwarp(gm);
+        for (int j = gl; j < slots; j += GS) tab.clear(j);  // leave the table clean
+        __syncwarp(gm);
     }
+    __syncwarp();
     my_changed = __reduce_add_sync(FULL, my_changed);
     if (lane == 0 && my_changed) atomicAdd(a.changed, (int)my_changed);
 }
@@ -532,16 +576,17 @@ __global__ void k_copra_best(const int32_t *l, int32_t n, int32_t L, int32_t *ou
         out[v] = l[v * L];
 }
 
-// Bin of row v among the rows the CTA kernels take: kind * waves + wave
-// (kind 0: shared table, 1: global table), or -1 for a row of the warp
-// kernel.
+// Bin of row v among the listed rows: kind * waves + wave (kind 0: a whole
+// warp, 1: a CTA with the shared table, 2: the long-row kernel), or -1 for a
+// row of the 8-lane kernel, which visits the wave's vertices directly.
 __device__ __forceinline__ int64_t cp_bin(const int32_t *off, int32_t v, int32_t L, int32_t waves,
                                           uint64_t magic)
 {
     const int64_t pairs = (int64_t)(__ldg(off + v + 1) - __ldg(off + v)) * L;
-    if (L <= CPW_MAX_L && pairs <= CPW_PAIRS) return -1;
+    if (L <= 8 && pairs <= 32) return -1;
     const uint32_t wave = waves > 1 ? fastmod((uint32_t)v, magic, (uint32_t)waves) : 0u;
-    return (pairs > CP_PAIRS ? (int64_t)waves : 0) + wave;
+    const int kind = (L <= CPW_MAX_L && pairs <= CPW_PAIRS) ? 0 : pairs > CP_PAIRS ? 2 : 1;
+    return (int64_t)kind * waves + wave;
 }
 
 // count[bin] += rows of each bin (one atomic per bin and warp)
@@ -621,7 +666,7 @@ int copra_table_lg(int64_t max_degree, int32_t L)
 
 int copra_big_ctas() { return 32; }
 
-int64_t copra_bins(int32_t waves) { return 2 * (int64_t)waves; }
+int64_t copra_bins(int32_t waves) { return 3 * (int64_t)waves; }
 
 int copra_rows(const int32_t *off, int32_t n, int32_t L, int32_t waves, int32_t *bins,
                int32_t *h_bins, int64_t *h_start, int32_t *rows, cudaStream_t st,
@@ -676,14 +721,24 @@ int copra_step(const CopraStep &s, int num_sms, cudaStream_t st, int64_t *launch
     a.gfirst = s.gfirst;
     a.glg_max = s.glg_max;
     if (s.n <= 0) return 0;
-    if (s.L <= CPW_MAX_L) {
+    if (s.L <= 8) {  // rows of at most 32 pairs: four per warp, over the wave's vertices
         const int64_t nw = (s.n - s.wave_k + (int64_t)s.waves - 1) / s.waves;
-        int64_t blocks = (nw + CPW_WARPS - 1) / CPW_WARPS;
+        int64_t blocks = (nw + 4 * CPW_WARPS - 1) / (4 * CPW_WARPS);
         if (blocks > (int64_t)num_sms * 8) blocks = (int64_t)num_sms * 8;
         if (blocks > 0) {
-            k_copra_warp<<<(int)blocks, CPW_WARPS * 32, 0, st>>>(a);
+            k_copra_warp<8><<<(int)blocks, CPW_WARPS * 32, 0, st>>>(a);
             ++*launches;
         }
+    }
+    if (s.n_warp > 0) {  // the listed rows of up to 128 pairs: one per warp
+        a.rows = s.rows_warp;
+        a.nrows = s.n_warp;
+        int64_t blocks = (s.n_warp + CPW_WARPS - 1) / CPW_WARPS;
+        if (blocks > (int64_t)num_sms * 8) blocks = (int64_t)num_sms * 8;
+        k_copra_warp<32><<<(int)blocks, CPW_WARPS * 32, 0, st>>>(a);
+        ++*launches;
+        a.rows = nullptr;
+        a.nrows = 0;
     }
     if (s.n_cta > 0) {
         a.rows = s.rows_cta;

@@ -394,10 +394,10 @@ struct CopraStep {
     int strict;
     uint64_t key_t;                  // non-strict key of the iteration
     int32_t *changed;                // += vertices whose best label changed
-    // this wave's rows that take a CTA (copra_rows): with the shared table
-    // and with the global tables
-    const int32_t *rows_cta, *rows_big;
-    int64_t n_cta, n_big;
+    // this wave's listed rows (copra_rows): those of a whole warp, of a CTA
+    // with the shared table, and of the long-row kernel
+    const int32_t *rows_warp, *rows_cta, *rows_big;
+    int64_t n_warp, n_cta, n_big;
     // n + 1 ints of scratch: the long rows that outgrow the shared table
     int32_t *ovf;
     // rows of more than the shared table's pairs: copra_big_ctas() tables of
@@ -415,9 +415,10 @@ int copra_best(const int32_t *l, int32_t n, int32_t L, int32_t *out, cudaStream_
 // (0 when every row fits the shared table)
 int copra_table_lg(int64_t max_degree, int32_t L);
 int copra_big_ctas();
-// The rows that take a CTA (all rows when L > 32, else those of more than
-// 128 pairs), grouped by bin = kind * waves + wave (kind 0: shared table, 1:
-// global tables): rows[h_start[bin] .. h_start[bin + 1]).  bins: device
+// The rows that the 8-lane kernel does not take (all rows when L > 8, else
+// those of more than 32 pairs), grouped by bin = kind * waves + wave (kind 0:
+// a whole warp, 1: a CTA with the shared table, 2: the long-row kernel):
+// rows[h_start[bin] .. h_start[bin + 1]).  bins: device
 // scratch and h_bins host scratch of copra_bins(waves) ints; h_start:
 // copra_bins(waves) + 1; rows: n.  Waits for the stream.
 int64_t copra_bins(int32_t waves);

@@ -67,7 +67,7 @@ def shape_graph(shape):
 
 
 @pytest.mark.parametrize("shape", SHAPES)
-@pytest.mark.parametrize("max_labels", [1, 4, 8])
+@pytest.mark.parametrize("max_labels", [1, 4, 8, 16])
 def test_copra_sync_parity(lp, shape, max_labels):
     off, idx, w = shape_graph(shape)
     copra_parity(lp, off, idx, w, max_labels=max_labels, mode="sync", max_iter=5)
