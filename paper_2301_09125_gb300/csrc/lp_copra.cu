@@ -205,6 +205,39 @@ struct CpGlobal {
     }
 };
 
+// f(p, label, belonging) for the pairs of a speaker's set in order, up to its
+// first empty pair (sets are prefixes).  Four pairs are loaded at a time, as
+// two 16-byte loads when L is a multiple of 4 (a set then starts 16-byte
+// aligned), so that a set costs one memory round trip instead of one per
+// pair.  The sets read are not written by the launch that reads them.
+template <typename F>
+__device__ __forceinline__ void cp_each_pair(const int32_t *ul, const uint32_t *ub, uint32_t L,
+                                             F &&f)
+{
+    for (uint32_t p0 = 0; p0 < L; p0 += 4) {
+        int32_t l[4];
+        uint32_t b[4];
+        if ((L & 3u) == 0u) {
+            const int4 l4 = __ldg(reinterpret_cast<const int4 *>(ul + p0));
+            const uint4 b4 = __ldg(reinterpret_cast<const uint4 *>(ub + p0));
+            l[0] = l4.x; l[1] = l4.y; l[2] = l4.z; l[3] = l4.w;
+            b[0] = b4.x; b[1] = b4.y; b[2] = b4.z; b[3] = b4.w;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const bool in = p0 + q < L;
+                b[q] = in ? __ldg(ub + p0 + q) : 0u;
+                l[q] = in ? __ldg(ul + p0 + q) : EMPTY;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (b[q] == 0u) return;
+            f(p0 + q, l[q], b[q]);
+        }
+    }
+}
+
 // Best candidate and 64-bit sum over the GS lanes of a group (mask m).
 template <int GS>
 __device__ __forceinline__ CpCand cp_group_best(CpCand c, unsigned m)
@@ -292,11 +325,9 @@ __global__ void __launch_bounds__(CPW_WARPS * 32) k_copra_warp(CopraArgs a)
             const bool earlier = cp_wave(a, u) < a.wave_k;
             const int32_t *ul = (earlier ? a.nxt_l : a.cur_l) + (int64_t)u * L;
             const uint32_t *ub = (earlier ? a.nxt_b : a.cur_b) + (int64_t)u * L;
-            for (uint32_t p = 0; p < L; ++p) {
-                const uint32_t b = ub[p];
-                if (b == 0u) break;
-                tab.add(lg, ul[p], (unsigned long long)w * b, (uint32_t)e * 64u + p);
-            }
+            cp_each_pair(ul, ub, L, [&](uint32_t p, int32_t l, uint32_t b) {
+                tab.add(lg, l, (unsigned long long)w * b, (uint32_t)e * 64u + p);
+            });
         }
         wsum = __reduce_add_sync(gm, wsum);  // < 2^31 (checked at ingest)
         __syncwarp(gm);
@@ -450,25 +481,22 @@ __global__ void __launch_bounds__(NT) k_copra_cta(CopraArgs a)
             const bool earlier = cp_wave(a, u) < a.wave_k;
             const int32_t *ul = (earlier ? a.nxt_l : a.cur_l) + (int64_t)u * L;
             const uint32_t *ub = (earlier ? a.nxt_b : a.cur_b) + (int64_t)u * L;
-            for (uint32_t p = 0; p < L; ++p) {
-                const uint32_t b = ub[p];
-                if (b == 0u) break;
-                const int32_t l = ul[p];
+            cp_each_pair(ul, ub, L, [&](uint32_t p, int32_t l, uint32_t b) {
                 const unsigned long long val = (unsigned long long)w * b;
                 const unsigned long long f = (unsigned long long)e * 64ull + p;
                 if (p == 0) {
                     if (l == c_l) {
                         c_v += val;  // its first appearance is the cached one (earlier)
-                        continue;
+                        return;
                     }
                     if (c_l != EMPTY) put(c_l, c_v, c_f);
                     c_l = l;
                     c_v = val;
                     c_f = f;
-                    continue;
+                    return;
                 }
                 put(l, val, f);
-            }
+            });
         }
         if (c_l != EMPTY && !(MODE == CP_SPILL && *(volatile int *)&s_full)) put(c_l, c_v, c_f);
         wsum = cp_warp_sum(wsum);
