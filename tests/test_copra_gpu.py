@@ -115,3 +115,18 @@ def test_copra_more_labels_than_a_warp(lp, shape, mode):
     off, idx, w = shape_graph(shape)
     copra_parity(lp, off, idx, w, max_labels=40, mode=mode, waves=3, max_iter=4, strict=False,
                  seed=5)
+
+
+@pytest.mark.parametrize("strict", [True, False])
+@pytest.mark.parametrize("waves", [31, 4000])
+def test_copra_all_waves_launch(lp, strict, waves):
+    # short rows only (k-mer-like paths, at most 8 pairs per label set of 4
+    # labels) and many waves: one cooperative launch sweeps every wave of an
+    # iteration, later waves reading the sets earlier waves wrote
+    g = gg.kmer_like(4000, mean_path=50, branch_frac=0.05, seed=9)
+    assert int(np.diff(g.offsets).max()) * 4 <= 32
+    copra_parity(lp, g.offsets, g.indices, g.weights, max_labels=4, mode="async", waves=waves,
+                 strict=strict, seed=3, max_iter=6)
+    # more than 8 labels: the same graph through the per-wave launches
+    copra_parity(lp, g.offsets, g.indices, g.weights, max_labels=16, mode="async", waves=waves,
+                 strict=strict, seed=3, max_iter=6)
