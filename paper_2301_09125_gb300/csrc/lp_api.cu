@@ -357,7 +357,6 @@ struct GraphSet {
     // generation, error flag)
     int64_t *d_wstart0 = nullptr;
     int32_t *d_coop = nullptr;
-    int32_t *h_coop = nullptr;  // pinned: the COPRA all-waves sweep's barrier status
     // modularity and label staging scratch
     unsigned long long *kc = nullptr, *macc = nullptr, *h_macc = nullptr;
     int64_t kc_cap = 0;
@@ -457,8 +456,6 @@ struct GraphSet {
         f(lab_tmp);
         f(d_ing);
         fh(h_ing);
-        fh(h_coop);
-        h_coop = nullptr;
         f(d_counts);
         fh(h_counts);
         f(vmaj);
@@ -1651,14 +1648,6 @@ struct GraphSet {
         LP_CU(cudaEventRecord(ev0, st));
         if (copra_init(cset_l[0], cset_b[0], nv, L, st, &L0.n) != 0)
             return fail(LP_ECUDA, cuda_msg("COPRA init", cudaGetLastError()));
-        // many waves whose rows all take the 8-lane kernel: one cooperative
-        // launch per iteration instead of one launch per wave
-        const bool coop = waves >= 8 && L <= 8 && h_cstart[(size_t)nbins] == 0;
-        if (coop) {
-            if (!d_coop) LP_TRY(dev_alloc(&d_coop, 4, "grid barrier", st, device));
-            if (!h_coop) LP_TRY(host_alloc(&h_coop, 1, "grid barrier status"));
-            LP_CU(cudaMemsetAsync(d_coop, 0, 4 * sizeof(int32_t), st));
-        }
         int cur = 0;
         int32_t iters = 0, conv = 0;
         int64_t last = 0;
@@ -1682,10 +1671,7 @@ struct GraphSet {
             cs.gsum = ctab_sum;
             cs.gfirst = ctab_first;
             cs.glg_max = glg;
-            if (coop && copra_waves(cs, reinterpret_cast<unsigned *>(d_coop), d_coop + 2, num_sms,
-                                    st, &L0.n) != 0)
-                return fail(LP_ECUDA, cuda_msg("COPRA all-waves launch", cudaGetLastError()));
-            for (int32_t k = 0; k < (coop ? 0 : waves); ++k) {
+            for (int32_t k = 0; k < waves; ++k) {
                 cs.wave_k = k;
                 auto bin = [&](int kind) { return (size_t)kind * waves + k; };
                 cs.rows_warp = crows + h_cstart[bin(0)];
@@ -1701,14 +1687,7 @@ struct GraphSet {
             cur ^= 1;
             LP_CU(cudaMemcpyAsync(h_changed + it, changed + it, sizeof(int32_t),
                                   cudaMemcpyDeviceToHost, st));
-            if (coop) LP_CU(cudaMemcpyAsync(h_coop, d_coop + 2, sizeof(int32_t),
-                                            cudaMemcpyDeviceToHost, st));
             LP_CU(cudaStreamSynchronize(st));
-            if (coop && *h_coop) {
-                LP_CU(cudaMemsetAsync(d_coop, 0, 4 * sizeof(int32_t), st));
-                LP_CU(cudaStreamSynchronize(st));
-                return fail(LP_ECUDA, "a grid barrier of the all-waves COPRA sweep timed out");
-            }
             iters = it + 1;
             last = h_changed[it];
             history.push_back(last);

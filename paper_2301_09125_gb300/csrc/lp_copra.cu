@@ -209,10 +209,8 @@ struct CpGlobal {
 // first empty pair (sets are prefixes).  Four pairs are loaded at a time, as
 // two 16-byte loads when L is a multiple of 4 (a set then starts 16-byte
 // aligned), so that a set costs one memory round trip instead of one per
-// pair.  COH: the set may have been written by other CTAs of the same
-// launch before a grid barrier, so it is read from L2 (ld.global.cg);
-// otherwise it was written by an earlier launch and the read-only path serves.
-template <bool COH, typename F>
+// pair.  The sets read are not written by the launch that reads them.
+template <typename F>
 __device__ __forceinline__ void cp_each_pair(const int32_t *ul, const uint32_t *ub, uint32_t L,
                                              F &&f)
 {
@@ -220,18 +218,16 @@ __device__ __forceinline__ void cp_each_pair(const int32_t *ul, const uint32_t *
         int32_t l[4];
         uint32_t b[4];
         if ((L & 3u) == 0u) {
-            const int4 l4 = COH ? __ldcg(reinterpret_cast<const int4 *>(ul + p0))
-                                : __ldg(reinterpret_cast<const int4 *>(ul + p0));
-            const uint4 b4 = COH ? __ldcg(reinterpret_cast<const uint4 *>(ub + p0))
-                                 : __ldg(reinterpret_cast<const uint4 *>(ub + p0));
+            const int4 l4 = __ldg(reinterpret_cast<const int4 *>(ul + p0));
+            const uint4 b4 = __ldg(reinterpret_cast<const uint4 *>(ub + p0));
             l[0] = l4.x; l[1] = l4.y; l[2] = l4.z; l[3] = l4.w;
             b[0] = b4.x; b[1] = b4.y; b[2] = b4.z; b[3] = b4.w;
         } else {
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const bool in = p0 + q < L;
-                b[q] = in ? (COH ? __ldcg(ub + p0 + q) : __ldg(ub + p0 + q)) : 0u;
-                l[q] = in ? (COH ? __ldcg(ul + p0 + q) : __ldg(ul + p0 + q)) : EMPTY;
+                b[q] = in ? __ldg(ub + p0 + q) : 0u;
+                l[q] = in ? __ldg(ul + p0 + q) : EMPTY;
             }
         }
 #pragma unroll
@@ -271,8 +267,8 @@ __device__ __forceinline__ unsigned long long cp_group_sum(unsigned long long v,
 // 8: four vertices per warp; GS = 32: one), which keeps the kept pairs one
 // per lane.  A table of 8 GS slots per group.  The GS = 32 launch takes the
 // rows the GS = 8 launch leaves (more than 32 pairs, or L > 8).
-template <int GS, bool COH>
-__device__ __forceinline__ void copra_groups(const CopraArgs &a)
+template <int GS>
+__global__ void __launch_bounds__(CPW_WARPS * 32) k_copra_warp(CopraArgs a)
 {
     constexpr int GT = 8 * GS;       // slots per group
     constexpr int GP = 4 * GS;       // pairs per group's row at most
@@ -329,13 +325,9 @@ __device__ __forceinline__ void copra_groups(const CopraArgs &a)
             const bool earlier = cp_wave(a, u) < a.wave_k;
             const int32_t *ul = (earlier ? a.nxt_l : a.cur_l) + (int64_t)u * L;
             const uint32_t *ub = (earlier ? a.nxt_b : a.cur_b) + (int64_t)u * L;
-            auto add = [&](uint32_t p, int32_t l, uint32_t b) {
+            cp_each_pair(ul, ub, L, [&](uint32_t p, int32_t l, uint32_t b) {
                 tab.add(lg, l, (unsigned long long)w * b, (uint32_t)e * 64u + p);
-            };
-            if (COH && earlier)
-                cp_each_pair<true>(ul, ub, L, add);
-            else
-                cp_each_pair<false>(ul, ub, L, add);
+            });
         }
         wsum = __reduce_add_sync(gm, wsum);  // < 2^31 (checked at ingest)
         __syncwarp(gm);
@@ -405,26 +397,6 @@ __device__ __forceinline__ void copra_groups(const CopraArgs &a)
     __syncwarp();
     my_changed = __reduce_add_sync(FULL, my_changed);
     if (lane == 0 && my_changed) atomicAdd(a.changed, (int)my_changed);
-}
-
-template <int GS>
-__global__ void __launch_bounds__(CPW_WARPS * 32) k_copra_warp(CopraArgs a)
-{
-    copra_groups<GS, false>(a);
-}
-
-// Every wave of an iteration in one cooperative launch, when every row takes
-// the 8-lane kernel (many waves of short rows): the grid sweeps wave k, then
-// meets at a grid barrier before wave k + 1, whose rows read wave k's sets
-// (from L2).  A barrier that runs out of polls sets *err and the kernel ends.
-__global__ void __launch_bounds__(CPW_WARPS * 32) k_copra_waves(CopraArgs a, unsigned *bar,
-                                                                int32_t *err)
-{
-    for (uint32_t k = 0; k < a.waves; ++k) {
-        a.wave_k = k;
-        copra_groups<8, true>(a);
-        if (k + 1 < a.waves && !grid_barrier(bar, err)) return;
-    }
 }
 
 // Table modes of the CTA kernel: shared with room for every label of the
@@ -509,7 +481,7 @@ __global__ void __launch_bounds__(NT) k_copra_cta(CopraArgs a)
             const bool earlier = cp_wave(a, u) < a.wave_k;
             const int32_t *ul = (earlier ? a.nxt_l : a.cur_l) + (int64_t)u * L;
             const uint32_t *ub = (earlier ? a.nxt_b : a.cur_b) + (int64_t)u * L;
-            cp_each_pair<false>(ul, ub, L, [&](uint32_t p, int32_t l, uint32_t b) {
+            cp_each_pair(ul, ub, L, [&](uint32_t p, int32_t l, uint32_t b) {
                 const unsigned long long val = (unsigned long long)w * b;
                 const unsigned long long f = (unsigned long long)e * 64ull + p;
                 if (p == 0) {
@@ -754,8 +726,7 @@ int copra_rows(const int32_t *off, int32_t n, int32_t L, int32_t waves, int32_t 
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-namespace {
-CopraArgs cp_args(const CopraStep &s)
+int copra_step(const CopraStep &s, int num_sms, cudaStream_t st, int64_t *launches)
 {
     CopraArgs a{};
     a.off = s.off;
@@ -777,38 +748,6 @@ CopraArgs cp_args(const CopraStep &s)
     a.gsum = s.gsum;
     a.gfirst = s.gfirst;
     a.glg_max = s.glg_max;
-    return a;
-}
-}  // namespace
-
-int copra_waves(const CopraStep &s, unsigned *bar, int32_t *err, int num_sms, cudaStream_t st,
-                int64_t *launches)
-{
-    // resident CTAs per SM (thread-safe one-time initialisation)
-    static const int per_sm = [] {
-        int n = 0;
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_copra_waves, CPW_WARPS * 32,
-                                                             0) == cudaSuccess
-                   ? n
-                   : 0;
-    }();
-    if (per_sm <= 0 || s.n <= 0 || s.L > 8) return -1;
-    CopraArgs a = cp_args(s);
-    const int64_t nw = ((int64_t)s.n + s.waves - 1) / s.waves;  // the longest wave
-    const int64_t want = (nw + 4 * CPW_WARPS - 1) / (4 * CPW_WARPS);
-    const int64_t cap = (int64_t)per_sm * num_sms;
-    const int grid = (int)(want < 1 ? 1 : (want < cap ? want : cap));
-    void *args[] = {&a, &bar, &err};
-    if (cudaLaunchCooperativeKernel((const void *)k_copra_waves, dim3(grid), dim3(CPW_WARPS * 32),
-                                    args, 0, st) != cudaSuccess)
-        return -1;
-    ++*launches;
-    return 0;
-}
-
-int copra_step(const CopraStep &s, int num_sms, cudaStream_t st, int64_t *launches)
-{
-    CopraArgs a = cp_args(s);
     if (s.n <= 0) return 0;
     if (s.L <= 8) {  // rows of at most 32 pairs: four per warp, over the wave's vertices
         const int64_t nw = (s.n - s.wave_k + (int64_t)s.waves - 1) / s.waves;

@@ -333,44 +333,5 @@ __device__ __forceinline__ void chunk_rows(StartOf start, int nr, uint16_t *s_ro
     __syncwarp();
 }
 
-// Grid-wide barrier of a cooperative launch (every CTA resident).  bar[0]
-// counts arrivals, bar[1] is the generation: the last CTA to arrive resets
-// the count and advances the generation.  A CTA that polls more than
-// BARRIER_SPIN times records *err = 1; every CTA returns false once *err is
-// set, so the kernel ends instead of waiting.
-constexpr uint32_t BARRIER_SPIN = 1u << 22;
-
-__device__ __forceinline__ bool grid_barrier(unsigned *bar, int32_t *err, unsigned expected = 0,
-                                             uint32_t spin_limit = BARRIER_SPIN)
-{
-    if (expected == 0) expected = gridDim.x;
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        volatile unsigned *vgen = bar + 1;
-        const unsigned gen = *vgen;
-        __threadfence();
-        int ok = 1;
-        if (atomicAdd(bar, 1u) + 1u == expected) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
-            for (uint32_t spins = 0; *vgen == gen; ++spins) {
-                if (spins >= spin_limit) {
-                    atomicExch(err, 1);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(64);
-            }
-        }
-        __threadfence();
-        s_ok = ok && *(volatile int32_t *)err == 0;
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
-
 }  // namespace
 }  // namespace lp

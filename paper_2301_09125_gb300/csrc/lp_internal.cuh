@@ -426,11 +426,6 @@ int copra_rows(const int32_t *off, int32_t n, int32_t L, int32_t waves, int32_t 
                int32_t *h_bins, int64_t *h_start, int32_t *rows, cudaStream_t st,
                int64_t *launches);
 int copra_step(const CopraStep &s, int num_sms, cudaStream_t st, int64_t *launches);
-// Every wave of an iteration in one cooperative launch (L <= 8 and no listed
-// rows: every row takes the 8-lane kernel); bar: two zeroed barrier words,
-// *err set if a barrier gave up.
-int copra_waves(const CopraStep &s, unsigned *bar, int32_t *err, int num_sms, cudaStream_t st,
-                int64_t *launches);
 
 // Split the communities of lab (n vertices, m entries, one graph) into
 // connected components in place: lab[v] = smallest vertex of v's component.

@@ -119,14 +119,13 @@ def test_copra_more_labels_than_a_warp(lp, shape, mode):
 
 @pytest.mark.parametrize("strict", [True, False])
 @pytest.mark.parametrize("waves", [31, 4000])
-def test_copra_all_waves_launch(lp, strict, waves):
-    # short rows only (k-mer-like paths, at most 8 pairs per label set of 4
-    # labels) and many waves: one cooperative launch sweeps every wave of an
-    # iteration, later waves reading the sets earlier waves wrote
+def test_copra_many_waves_of_short_rows(lp, strict, waves):
+    # k-mer-like paths (at most 32 pairs per row with 4 labels: the 8-lane
+    # kernel) and many waves, later waves reading the sets earlier waves wrote;
+    # with 16 labels the same rows take a listed warp each
     g = gg.kmer_like(4000, mean_path=50, branch_frac=0.05, seed=9)
     assert int(np.diff(g.offsets).max()) * 4 <= 32
     copra_parity(lp, g.offsets, g.indices, g.weights, max_labels=4, mode="async", waves=waves,
                  strict=strict, seed=3, max_iter=6)
-    # more than 8 labels: the same graph through the per-wave launches
     copra_parity(lp, g.offsets, g.indices, g.weights, max_labels=16, mode="async", waves=waves,
                  strict=strict, seed=3, max_iter=6)
