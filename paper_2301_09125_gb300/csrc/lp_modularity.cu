@@ -304,16 +304,27 @@ __global__ void __launch_bounds__(256) k_mod_small(ModArgs a)
                 }
             }
         }
+        // K: one atomic when the warp's rows share a community (a converged
+        // labelling often has a giant one), else one per row
         const int64_t slot = valid ? vb + c : -1;
-        const unsigned grp = __match_any_sync(FULL, (unsigned long long)slot);
-        const unsigned long long sum = group_sum(grp, kv);
-        if (valid && lane == __ffs(grp) - 1 && sum) atomicAdd(a.kc + slot, sum);
-        if (MULTI) {  // L and 2m: one pair of atomics per graph the warp's rows meet
-            const unsigned gm = __match_any_sync(FULL, valid ? g : -1);
-            const unsigned long long ls = group_sum(gm, lv), ks = group_sum(gm, kv);
-            if (valid && lane == __ffs(gm) - 1 && ks) {
-                atomicAdd(a.acc + 4 * (int64_t)g, ls);
-                atomicAdd(a.acc + 4 * (int64_t)g + 1, ks);
+        const int64_t slot0 = __shfl_sync(FULL, slot, 0);
+        if (__all_sync(FULL, !valid || slot == slot0)) {
+            const unsigned long long sum = group_sum(FULL, kv);
+            if (lane == 0 && sum) atomicAdd(a.kc + slot0, sum);
+        } else if (valid && kv) {
+            atomicAdd(a.kc + slot, (unsigned long long)kv);
+        }
+        if (MULTI) {  // L and 2m: one pair of atomics when the warp's rows share a graph
+            const int32_t g0 = __shfl_sync(FULL, g, 0);
+            if (__all_sync(FULL, !valid || g == g0)) {
+                const unsigned long long ls = group_sum(FULL, lv), ks = group_sum(FULL, kv);
+                if (lane == 0 && ks) {
+                    atomicAdd(a.acc + 4 * (int64_t)g0, ls);
+                    atomicAdd(a.acc + 4 * (int64_t)g0 + 1, ks);
+                }
+            } else if (valid && kv) {
+                atomicAdd(a.acc + 4 * (int64_t)g, (unsigned long long)lv);
+                atomicAdd(a.acc + 4 * (int64_t)g + 1, (unsigned long long)kv);
             }
         } else {
             l += lv;
