@@ -514,7 +514,8 @@ def run_ours(args):
     total_sweeps = sum(iters)
     sweep_bytes = alg_bytes_per_sweep(g)
     per_sweep_ms = sweep_ms / total_sweeps
-    ratio = traffic_ratio(dom_name)
+    # the ratios were measured on R-MAT-22 only: other graphs report none
+    ratio = traffic_ratio(dom_name) if args.workload == "rmat22" else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak,
                 "traffic": None if ratio is None else ratio * dom["bytes"] / dom["launches"],
