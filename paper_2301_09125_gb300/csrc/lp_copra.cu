@@ -111,6 +111,27 @@ __device__ __forceinline__ unsigned long long cp_warp_sum(unsigned long long v)
     return v;
 }
 
+// floor(t * 2^16 / tk) for 0 <= t <= tk < 2^47 (a belonging in units of
+// 2^-16, at most 2^16): a single-precision estimate, off by at most one
+// (each rounding of t, tk and their quotient is within 2^-24 relative, so
+// the estimate is within 2^16 * 3 * 2^-24 of the quotient), then corrected
+// with exact 64-bit integer arithmetic.
+__device__ __forceinline__ uint32_t cp_frac(unsigned long long t, unsigned long long tk)
+{
+    uint32_t q = (uint32_t)(((float)t * 65536.0f) / (float)tk);
+    if (q > COPRA_ONE) q = COPRA_ONE;
+    long long r = (long long)(t << 16) - (long long)q * (long long)tk;
+    while (r < 0) {
+        --q;
+        r += (long long)tk;
+    }
+    while (r >= (long long)tk) {
+        ++q;
+        r -= (long long)tk;
+    }
+    return q;
+}
+
 // Wave of vertex v (0 in synchronous runs).
 __device__ __forceinline__ uint32_t cp_wave(const CopraArgs &a, int32_t v)
 {
@@ -370,7 +391,7 @@ __global__ void __launch_bounds__(CPW_WARPS * 32) k_copra_warp(CopraArgs a)
         const bool hold = gl < nk;
         const unsigned long long ti = hold ? tab.t(mine) : 0ull;
         const unsigned long long tk = cp_group_sum<GS>(ti, gm);
-        uint32_t bv = hold ? (uint32_t)((ti * COPRA_ONE) / tk) : 0u;
+        uint32_t bv = hold ? cp_frac(ti, tk) : 0u;
         const uint32_t bsum = __reduce_add_sync(gm, bv);
         if (hold && mine == best.slot) bv += COPRA_ONE - bsum;
         // store by decreasing belonging, equal belongings by first appearance
@@ -550,7 +571,7 @@ __global__ void __launch_bounds__(NT) k_copra_cta(CopraArgs a)
             uint32_t bv[64];
             uint32_t bsum = 0u;
             for (int q = 0; q < nk; ++q) {
-                bv[q] = (uint32_t)((tab.t(s_kept[q]) * (unsigned long long)COPRA_ONE) / tk);
+                bv[q] = cp_frac(tab.t(s_kept[q]), tk);
                 bsum += bv[q];
             }
             for (int q = 0; q < nk; ++q)
