@@ -46,6 +46,7 @@ each class's benchmark run (communities and modularity before and after).
 ``--experiment copra`` / ``--experiment slpa`` time COPRA (Sec. 3.3, 4 labels,
 tolerance 0.01) and SLPA (Sec. 3.4, memory of 20) on each class, with their
 first iteration checked against the oracle at full size.
+``--experiment noalloc`` times the allocation-free sweep against lp_rak_run's.
 ``--experiment gather`` measures the ceiling of a label-gathering sweep: one
 pass streaming the rows, and one that also gathers every entry's neighbour
 label, on each class as generated and renumbered by decreasing degree.
@@ -125,7 +126,8 @@ def parse():
                     help="single-graph workloads: leave out the serve sub-record")
     ap.add_argument("--per-graph-sample", type=int, default=256,
                     help="graphs of the batch timed one at a time")
-    ap.add_argument("--experiment", choices=["tolerance", "split", "gather", "copra", "slpa"],
+    ap.add_argument("--experiment",
+                    choices=["tolerance", "split", "gather", "copra", "slpa", "noalloc"],
                     default=None,
                     help="run the tolerance / tie-rule study, or time the split of "
                          "disconnected communities, instead of the benchmark")
@@ -1318,6 +1320,71 @@ def run_method_experiment(args):
     return 0
 
 
+def run_noalloc_experiment(args):
+    """lp_rak_sweep_noalloc (one synchronous sweep, no allocation) on each
+    class whose rows fit its limit of 4096 entries: the first sweep from
+    unique labels and a second one from its result, each timed with CUDA
+    events (best of 5), against the sweeps of a 3-iteration synchronous
+    lp_rak_run of the same graph; the first sweep's labels are compared with
+    lp_rak_run's one-iteration labels."""
+    import torch
+
+    import paper_2301_09125_gb300 as lp
+    from paper_2301_09125_gb300 import build
+
+    build.build()
+    lp.load()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    for name in [c for c in args.classes.split(",") if c]:
+        g = gen_graph(name)
+        maxdeg = int(np.diff(g.offsets.astype(np.int64)).max())
+        if maxdeg > 4096:
+            print(json.dumps({"experiment": "noalloc", "workload": name, "skipped":
+                              f"longest row {maxdeg} entries, beyond the 4096 of the entry point"}),
+                  flush=True)
+            continue
+        off, idx, w = (torch.from_numpy(a).to(dev) if a is not None else None
+                       for a in (g.offsets, g.indices, g.weights))
+        lab0 = torch.arange(g.n, dtype=torch.int32, device=dev)
+        lab1 = torch.empty_like(lab0)
+        lab2 = torch.empty_like(lab0)
+
+        def timed(src, dst):
+            best = None
+            for _ in range(5):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                lp.lp_rak_sweep_noalloc(off, idx, w, src, dst, strict=True)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1)
+                best = ms if best is None else min(best, ms)
+            return best
+
+        lp.lp_rak_sweep_noalloc(off, idx, w, lab0, lab1, strict=True)  # warm-up
+        first_ms = timed(lab0, lab1)
+        second_ms = timed(lab1, lab2)
+        h = lp.lp_graph_create(off, idx, w, borrow=True, stream=stream.cuda_stream)
+        params, _ = lp.make_params(tolerance=0.0, max_iter=1, mode="sync", strict=True)
+        lp.lp_rak_run(h, params)
+        same = bool(torch.equal(lp.lp_labels_get(h, torch.empty_like(lab0)), lab1))
+        params3, _ = lp.make_params(tolerance=0.0, max_iter=3, mode="sync", strict=True)
+        lp.lp_rak_run(h, params3)
+        r = lp.lp_rak_run(h, params3)
+        lp.lp_graph_destroy(h)
+        print(json.dumps({"experiment": "noalloc", "workload": name, "n": g.n, "m": g.m,
+                          "first_sweep_ms": first_ms, "second_sweep_ms": second_ms,
+                          "noalloc_gteps": g.m / (second_ms * 1e-3) / 1e9,
+                          "lp_rak_run_ms_per_sweep": r.gpu_ms / max(r.iterations, 1),
+                          "first_sweep_equals_lp_rak_run": same}), flush=True)
+        del off, idx, w, lab0, lab1, lab2
+        torch.cuda.empty_cache()
+    return 0
+
+
 def degree_renumbered(g):
     """The graph with vertices renumbered by decreasing degree (stable), rows
     in the new order: a layout where the most gathered labels sit together."""
@@ -1389,6 +1456,8 @@ def main():
         return run_split_experiment(args)
     if args.experiment in ("copra", "slpa"):
         return run_method_experiment(args)
+    if args.experiment == "noalloc":
+        return run_noalloc_experiment(args)
     if args.experiment:
         return run_experiment(args)
     if args.workload == "serve":
