@@ -13,14 +13,16 @@
 //     for labels that do not fit the CTA's shared-memory table.
 // Its size bounds the graphs it accepts: at most NA_MAX_DEGREE entries per row.
 //
-// The kernel needs no degree buckets (which would need memory per graph).
-// It makes two passes over the vertices.  First, each warp takes the rows
-// of at most 32 entries, one lane per entry: a lane's label total is the
-// sum over the lanes holding the same label (__match_any_sync), and the
-// lowest of those lanes is the label's first position.  Then each CTA takes
-// the longer rows: a shared table of 2^ceil(log2(2d)) slots (at most
-// NA_TABLE), probed at most NA_PROBE slots from a label's hash; a label
-// whose window is full goes to the CTA's overflow table in the static array.
+// The sweep needs no degree buckets (which would need memory per graph).
+// It makes two passes over the vertices, two launches.  First, as many warps
+// as fit the GPU take the rows of at most 32 entries, one lane per entry: a
+// lane's label total is the sum over the lanes holding the same label
+// (__match_any_sync), and the lowest of those lanes is the label's first
+// position.  Then NA_CTAS CTAs take the longer rows, each looking at
+// NA_THREADS vertices at a time and listing the long ones in shared memory:
+// a shared table of 2^ceil(log2(2d)) slots (at most NA_TABLE), probed at most
+// NA_PROBE slots from a label's hash; a label whose window is full goes to
+// the CTA's overflow table in the static array.
 #include <mutex>
 #include <string>
 
@@ -65,19 +67,13 @@ struct NoAllocArgs {
 
 constexpr int NA_WARP_MAX = 32;  // rows of at most this many entries: one warp each
 
-__global__ void __launch_bounds__(NA_THREADS) k_sweep_noalloc(NoAllocArgs a)
+// Rows of 0 .. 32 entries: one warp each, no table (as many warps as fit
+// the GPU: the pass needs no scratch).
+__global__ void __launch_bounds__(NA_THREADS) k_noalloc_warp(NoAllocArgs a)
 {
-    extern __shared__ int32_t smem[];
-    int32_t *tk = smem;
-    int32_t *ts = tk + NA_TABLE;
-    uint32_t *tp = reinterpret_cast<uint32_t *>(ts + NA_TABLE);
-    __shared__ Cand s_red[NA_THREADS / 32];
-    __shared__ uint32_t s_u[NA_THREADS / 32 + 1];
-    __shared__ int s_spilled;
     const int lane = threadIdx.x & 31;
     uint32_t my_changed = 0;
 
-    // rows of 1 .. 32 entries: one warp each, no table
     const int64_t wid = ((int64_t)blockIdx.x * NA_THREADS + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * NA_THREADS) >> 5;
     for (int64_t v = wid; v < a.n; v += nw) {
@@ -114,8 +110,27 @@ __global__ void __launch_bounds__(NA_THREADS) k_sweep_noalloc(NoAllocArgs a)
             if (c.label != own) ++my_changed;
         }
     }
+    my_changed = __reduce_add_sync(FULL, my_changed);
+    if (lane == 0 && my_changed) atomicAdd(a.changed, (int)my_changed);
+}
 
-    // longer rows: one CTA each, a table of 2^ceil(log2(2d)) slots
+// Longer rows: one CTA each, a table of 2^ceil(log2(2d)) slots and the CTA's
+// overflow table in the static array (NA_CTAS CTAs).  The CTA looks at
+// NA_THREADS vertices at a time, one per thread, and lists the long ones in
+// shared memory before taking them one after another.
+__global__ void __launch_bounds__(NA_THREADS) k_noalloc_cta(NoAllocArgs a)
+{
+    extern __shared__ int32_t smem[];
+    int32_t *tk = smem;
+    int32_t *ts = tk + NA_TABLE;
+    uint32_t *tp = reinterpret_cast<uint32_t *>(ts + NA_TABLE);
+    __shared__ Cand s_red[NA_THREADS / 32];
+    __shared__ uint32_t s_u[NA_THREADS / 32 + 1];
+    __shared__ int s_spilled;
+    __shared__ int32_t s_long[NA_THREADS];
+    __shared__ int s_nlong;
+    const int lane = threadIdx.x & 31;
+    uint32_t my_changed = 0;
     for (int j = threadIdx.x; j < NA_TABLE; j += NA_THREADS) {
         tk[j] = EMPTY;
         ts[j] = 0;
@@ -126,66 +141,79 @@ __global__ void __launch_bounds__(NA_THREADS) k_sweep_noalloc(NoAllocArgs a)
     int32_t *gk = a.ov_key + (int64_t)blockIdx.x * NA_SLOTS;
     int32_t *gs = a.ov_sum + (int64_t)blockIdx.x * NA_SLOTS;
     uint32_t *gp = a.ov_npos + (int64_t)blockIdx.x * NA_SLOTS;
-    for (int32_t v = blockIdx.x; v < a.n; v += gridDim.x) {
-        const int32_t rs = __ldg(a.off + v), d = __ldg(a.off + v + 1) - rs;
-        if (d <= NA_WARP_MAX) continue;  // block-uniform
-        const int32_t own = __ldg(a.lab_in + v);
-        const int glg = ilog2_ceil(2u * (uint32_t)d);  // 2^glg <= NA_SLOTS (degree checked)
-        const int lg = glg < NA_TABLE_LG ? glg : NA_TABLE_LG;
-        const int probe = NA_PROBE < (1 << lg) ? NA_PROBE : (1 << lg);
-        for (int k0 = 0; k0 < d; k0 += NA_THREADS) {
-            const int k = k0 + threadIdx.x;
-            const bool act = k < d;
-            int w = 0;
-            int32_t l = EMPTY;
-            if (act) {
-                const int32_t u = __ldg(a.idx + rs + k);
-                w = a.wts ? __ldg(a.wts + rs + k) : 1;
-                l = __ldg(a.lab_in + u);
-            }
-            if (act && !table_add(tk, ts, tp, lg, probe, l, w, k)) {
-                s_spilled = 1;
-                table_add(gk, gs, gp, glg, 1 << glg, l, w, k);
-            }
+    for (int64_t base = (int64_t)blockIdx.x * NA_THREADS; base < a.n;
+         base += (int64_t)gridDim.x * NA_THREADS) {
+        if (threadIdx.x == 0) s_nlong = 0;
+        __syncthreads();
+        {
+            const int64_t u = base + threadIdx.x;
+            if (u < a.n && __ldg(a.off + u + 1) - __ldg(a.off + u) > NA_WARP_MAX)
+                s_long[atomicAdd(&s_nlong, 1)] = (int32_t)u;
         }
         __syncthreads();
-        const int slots = 1 << lg;
-        const int gslots = s_spilled ? (1 << glg) : 0;
-        Cand best{0u, 0u, 0ull, EMPTY};
-        uint32_t mx = 0;
-        if (!a.strict) {
-            for (int j = threadIdx.x; j < slots + gslots; j += NA_THREADS) {
-                const int32_t key = j < slots ? tk[j] : gk[j - slots];
-                if (key != EMPTY) mx = max(mx, (uint32_t)(j < slots ? ts[j] : gs[j - slots]));
-            }
-            mx = block_max<NA_THREADS>(mx, s_u);
-        }
-        const uint64_t ktv = stream_at(a.key_t, (uint64_t)v + 1);
-        for (int j = threadIdx.x; j < slots + gslots; j += NA_THREADS) {
-            int32_t *K = j < slots ? tk + j : gk + (j - slots);
-            int32_t *S = j < slots ? ts + j : gs + (j - slots);
-            uint32_t *Q = j < slots ? tp + j : gp + (j - slots);
-            const int32_t key = *K;
-            if (key != EMPTY) {
-                if (a.strict) {
-                    const Cand c{(uint32_t)*S, *Q, 0ull, key};
-                    if (better(c, best)) best = c;
-                } else if ((uint32_t)*S == mx) {
-                    const Cand c{mx, *Q, stream_at(ktv, (uint64_t)key + 1), key};
-                    if (better(c, best)) best = c;
+        const int nlong = s_nlong;
+        for (int q = 0; q < nlong; ++q) {
+            const int32_t v = s_long[q];
+            const int32_t rs = __ldg(a.off + v), d = __ldg(a.off + v + 1) - rs;
+            const int32_t own = __ldg(a.lab_in + v);
+            const int glg = ilog2_ceil(2u * (uint32_t)d);  // 2^glg <= NA_SLOTS (degree checked)
+            const int lg = glg < NA_TABLE_LG ? glg : NA_TABLE_LG;
+            const int probe = NA_PROBE < (1 << lg) ? NA_PROBE : (1 << lg);
+            for (int k0 = 0; k0 < d; k0 += NA_THREADS) {
+                const int k = k0 + threadIdx.x;
+                const bool act = k < d;
+                int w = 0;
+                int32_t l = EMPTY;
+                if (act) {
+                    const int32_t u = __ldg(a.idx + rs + k);
+                    w = a.wts ? __ldg(a.wts + rs + k) : 1;
+                    l = __ldg(a.lab_in + u);
                 }
-                *K = EMPTY;  // every used slot is reset: the tables stay clean
-                *S = 0;
-                *Q = 0;
+                if (act && !table_add(tk, ts, tp, lg, probe, l, w, k)) {
+                    s_spilled = 1;
+                    table_add(gk, gs, gp, glg, 1 << glg, l, w, k);
+                }
             }
+            __syncthreads();
+            const int slots = 1 << lg;
+            const int gslots = s_spilled ? (1 << glg) : 0;
+            Cand best{0u, 0u, 0ull, EMPTY};
+            uint32_t mx = 0;
+            if (!a.strict) {
+                for (int j = threadIdx.x; j < slots + gslots; j += NA_THREADS) {
+                    const int32_t key = j < slots ? tk[j] : gk[j - slots];
+                    if (key != EMPTY) mx = max(mx, (uint32_t)(j < slots ? ts[j] : gs[j - slots]));
+                }
+                mx = block_max<NA_THREADS>(mx, s_u);
+            }
+            const uint64_t ktv = stream_at(a.key_t, (uint64_t)v + 1);
+            for (int j = threadIdx.x; j < slots + gslots; j += NA_THREADS) {
+                int32_t *K = j < slots ? tk + j : gk + (j - slots);
+                int32_t *S = j < slots ? ts + j : gs + (j - slots);
+                uint32_t *Q = j < slots ? tp + j : gp + (j - slots);
+                const int32_t key = *K;
+                if (key != EMPTY) {
+                    if (a.strict) {
+                        const Cand c{(uint32_t)*S, *Q, 0ull, key};
+                        if (better(c, best)) best = c;
+                    } else if ((uint32_t)*S == mx) {
+                        const Cand c{mx, *Q, stream_at(ktv, (uint64_t)key + 1), key};
+                        if (better(c, best)) best = c;
+                    }
+                    *K = EMPTY;  // every used slot is reset: the tables stay clean
+                    *S = 0;
+                    *Q = 0;
+                }
+            }
+            best = block_best<NA_THREADS>(best, s_red);
+            if (threadIdx.x == 0) {
+                a.lab_out[v] = best.label;
+                if (best.label != own) ++my_changed;
+                s_spilled = 0;
+            }
+            __syncthreads();
         }
-        best = block_best<NA_THREADS>(best, s_red);
-        if (threadIdx.x == 0) {
-            a.lab_out[v] = best.label;
-            if (best.label != own) ++my_changed;
-            s_spilled = 0;
-        }
-        __syncthreads();
+        __syncthreads();  // every thread has read s_nlong before the next chunk resets it
     }
     my_changed = __reduce_add_sync(FULL, my_changed);
     if (lane == 0 && my_changed) atomicAdd(a.changed, (int)my_changed);
@@ -225,7 +253,7 @@ extern "C" lp_status lp_rak_sweep_noalloc(int32_t n, int64_t m, const int32_t *o
             cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
             if (e != cudaSuccess)
                 return lp_fail(LP_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-            e = cudaFuncSetAttribute(k_sweep_noalloc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            e = cudaFuncSetAttribute(k_noalloc_cta, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      NA_TABLE * 12);
             const size_t tab = (size_t)NA_CTAS * NA_SLOTS * sizeof(int32_t);
             int32_t *base = static_cast<int32_t *>(p);
@@ -287,8 +315,16 @@ extern "C" lp_status lp_rak_sweep_noalloc(int32_t n, int64_t m, const int32_t *o
     a.ov_sum = a.ov_key + (size_t)NA_CTAS * NA_SLOTS;
     a.ov_npos = reinterpret_cast<uint32_t *>(a.ov_sum + (size_t)NA_CTAS * NA_SLOTS);
     if (n > 0) {
-        k_sweep_noalloc<<<n < NA_CTAS ? n : NA_CTAS, NA_THREADS, NA_TABLE * 12, st>>>(a);
-        ++launches;
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return lp_fail(LP_ECUDA, "no usable CUDA device");
+        int64_t wblocks = ((int64_t)n + NA_THREADS / 32 - 1) / (NA_THREADS / 32);  // a warp per vertex
+        if (wblocks > (int64_t)sms * 4) wblocks = (int64_t)sms * 4;
+        k_noalloc_warp<<<(int)wblocks, NA_THREADS, 0, st>>>(a);
+        const int64_t cblocks = ((int64_t)n + NA_THREADS - 1) / NA_THREADS;
+        k_noalloc_cta<<<(int)(cblocks < NA_CTAS ? cblocks : NA_CTAS), NA_THREADS, NA_TABLE * 12,
+                        st>>>(a);
+        launches += 2;
         if (cudaGetLastError() != cudaSuccess) return lp_fail(LP_ECUDA, "sweep launch failed");
     }
     int32_t hc = 0;
