@@ -1091,7 +1091,7 @@ struct GraphSet {
             }
             LP_CU(cudaMemsetAsync(d_coop, 0, 2 * sizeof(int32_t), s));
             a.rp = pk_rp;  // aligned with wlist; the kernel offsets it per wave
-            const int nk = small_waves_launch(a, wlist, d_wstart0, d_wtot, max_len,
+            const int nk = small_waves_launch(a, wlist, d_wstart0, d_wtot, max_len, max_deg,
                                               reinterpret_cast<unsigned *>(d_coop), d_coop + 2,
                                               num_sms, s);
             if (nk < 0) return fail(LP_ECUDA, cuda_msg("all-waves launch", cudaGetLastError()));

@@ -239,17 +239,19 @@ int sweep_prepare();  // per-device kernel attributes; call with the device curr
 // launch the sweep kernel(s) of one degree bucket (0 small, 1 warp, 2 cta,
 // 3 cta2, 4 hub); returns the number of kernels launched, or -1
 int sweep_launch(int bucket, const SweepArgs &a, bool multi, int num_sms, cudaStream_t st);
+// Four CTAs wait at a grid barrier for a fifth that never comes: the wait
+// gives up after spin_limit polls and sets *err (bar: two zeroed words).
+int barrier_probe_launch(unsigned *bar, int32_t *err, uint32_t spin_limit, cudaStream_t st);
 // Every wave of an asynchronous single-graph sweep whose rows all lie in the
 // small bucket, as one cooperative launch (wave k's list: wlist + wstart[k],
 // wcount[k] entries, both device arrays; max_len the longest).  bar: two
 // zeroed device words (left zeroed); *err set to 1 if a grid barrier timed
 // out.  Returns the kernel count (1) or -1.
-// Four CTAs wait at a grid barrier for a fifth that never comes: the wait
-// gives up after spin_limit polls and sets *err (bar: two zeroed words).
-int barrier_probe_launch(unsigned *bar, int32_t *err, uint32_t spin_limit, cudaStream_t st);
+// (max_degree: the graph's longest row; rows of at most 8 entries take the
+// kernel that loads the next wave's rows before each barrier)
 int small_waves_launch(const SweepArgs &a, const int32_t *wlist, const int64_t *wstart,
-                       const int64_t *wcount, int64_t max_len, unsigned *bar, int32_t *err,
-                       int num_sms, cudaStream_t st);
+                       const int64_t *wcount, int64_t max_len, int32_t max_degree, unsigned *bar,
+                       int32_t *err, int num_sms, cudaStream_t st);
 // Hub tasks of list[0..len): the rows longer than HUB_ONE_MAX first, then the
 // others, each kind in list order; list is rewritten in the same order so that
 // tasks[i] belongs to list[i].  totals: [0] rows of the first kind, [1] their

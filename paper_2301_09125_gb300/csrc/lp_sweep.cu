@@ -774,6 +774,109 @@ __global__ void __launch_bounds__(256, 6) k_small_waves(SweepArgs a, const int32
     }
 }
 
+// Every wave of an asynchronous sweep of a single graph whose rows all hold
+// at most TINY entries (paths such as the k-mer graphs), in one cooperative
+// launch: 32 rows per warp tile, one per lane, counted in registers as the
+// small-row kernel counts its rows of at most TINY entries.  Before each grid
+// barrier a warp loads its first tile of the next wave (list items, packed
+// rows and own labels do not depend on labels of this iteration), so after
+// the barrier only the neighbours' labels remain to be read.
+struct TinyRow {
+    int32_t v, own, d;
+    int32_t u[TINY];
+    uint32_t w[TINY];
+};
+
+__device__ __forceinline__ void tiny_fetch(const SweepArgs &a, const int32_t *list,
+                                           const int64_t *rp, int64_t len, int64_t tile,
+                                           TinyRow &r)
+{
+    const int64_t i = tile * 32 + (threadIdx.x & 31);
+    r.d = 0;
+    r.v = 0;
+    r.own = 0;
+    if (i < len) {
+        r.v = __ldg(list + i);
+        const int64_t e0 = __ldg(rp + i);
+        r.d = (int32_t)(__ldg(rp + i + 1) - e0);
+        r.own = __ldg(a.lab_in + r.v);
+#pragma unroll
+        for (int j = 0; j < TINY; ++j) {
+            const bool in = j < r.d;
+            r.u[j] = in ? ld_entry(a.idx + e0 + j) : 0;
+            r.w[j] = in ? (a.wts ? (uint32_t)ld_entry(a.wts + e0 + j) : 1u) : 0u;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256, 2) k_tiny_waves(SweepArgs a, const int32_t *wlist,
+                                                       const int64_t *wstart, const int64_t *wcount,
+                                                       unsigned *bar, int32_t *err)
+{
+    if (a.stop && *a.stop) return;  // launched past the end of the run
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    uint32_t my_changed = 0;
+    TinyRow r;  // holds this warp's first tile of a wave before the wave starts
+    tiny_fetch(a, wlist + wstart[0], a.rp + wstart[0], wcount[0], wid, r);
+    for (uint32_t k = 0; k < a.waves; ++k) {
+        const int32_t *list = wlist + wstart[k];
+        const int64_t *rp = a.rp + wstart[k];
+        const int64_t len = wcount[k];
+        const bool identity = a.identity && k == 0;  // later waves read this sweep's labels
+        for (int64_t tile = wid; tile * 32 < len; tile += nw) {
+            if (tile != wid) tiny_fetch(a, list, rp, len, tile, r);  // the first is loaded
+            int32_t lab[TINY];
+#pragma unroll
+            for (int j = 0; j < TINY; ++j)
+                lab[j] = j < r.d ? (identity ? (r.u[j] & ID_MASK) : neighbour_label<true>(a, 0, r.u[j]))
+                                 : EMPTY;
+            // entries past the row are EMPTY with weight 0: their totals are 0
+            uint32_t bs = 0u;
+            int32_t bl = r.own;
+#pragma unroll
+            for (int j = 0; j < TINY; ++j) {
+                uint32_t t = 0u;
+#pragma unroll
+                for (int q = 0; q < TINY; ++q) t += lab[q] == lab[j] ? r.w[q] : 0u;
+                if (t > bs) {
+                    bs = t;
+                    bl = lab[j];
+                }
+            }
+            if (!a.strict && r.d > 0) {
+                // among the labels of maximum total, the least tie key (then
+                // the earliest first position)
+                uint64_t bh = ~0ull;
+#pragma unroll
+                for (int j = 0; j < TINY; ++j) {
+                    uint32_t t = 0u;
+#pragma unroll
+                    for (int q = 0; q < TINY; ++q) t += lab[q] == lab[j] ? r.w[q] : 0u;
+                    if (t == bs) {
+                        const uint64_t h = tie_key(a.key_t, r.v, lab[j]);
+                        if (h < bh) {
+                            bh = h;
+                            bl = lab[j];
+                        }
+                    }
+                }
+            }
+            if (r.d > 0) {
+                a.lab_out[r.v] = bl;
+                if (bl != r.own) ++my_changed;
+            }
+        }
+        if (k + 1 < a.waves) {
+            tiny_fetch(a, wlist + wstart[k + 1], a.rp + wstart[k + 1], wcount[k + 1], wid, r);
+            if (!grid_barrier(bar, err)) return;
+        }
+    }
+    my_changed = __reduce_add_sync(FULL, my_changed);
+    if (lane == 0 && my_changed) atomicAdd(a.changed, (int)my_changed);
+}
+
 // Insert one quad (entries 4*blk .. 4*blk+3 of a row starting at global
 // entry `row`) into a shared table of 2^lg slots: entries of the warp's hot
 // label are summed in registers, every other entry is added by its lane.
@@ -1930,8 +2033,8 @@ int barrier_probe_launch(unsigned *bar, int32_t *err, uint32_t spin_limit, cudaS
 }
 
 int small_waves_launch(const SweepArgs &a, const int32_t *wlist, const int64_t *wstart,
-                       const int64_t *wcount, int64_t max_len, unsigned *bar, int32_t *err,
-                       int num_sms, cudaStream_t st)
+                       const int64_t *wcount, int64_t max_len, int32_t max_degree, unsigned *bar,
+                       int32_t *err, int num_sms, cudaStream_t st)
 {
     // resident CTAs per SM (thread-safe one-time initialisation)
     static const int per_sm = [] {
@@ -1941,15 +2044,26 @@ int small_waves_launch(const SweepArgs &a, const int32_t *wlist, const int64_t *
                    ? n
                    : 0;
     }();
-    if (per_sm <= 0) return -1;
+    static const int per_sm_tiny = [] {
+        int n = 0;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_tiny_waves, 256, 0) ==
+                       cudaSuccess
+                   ? n
+                   : 0;
+    }();
+    // every row of at most TINY entries: the kernel that loads the next wave's
+    // rows before each barrier
+    const bool tiny = max_degree <= TINY && !a.spoken;
+    const int ps = tiny ? per_sm_tiny : per_sm;
+    if (ps <= 0) return -1;
     SweepArgs b = a;
-    b.tile_rows = small_tile_rows(max_len, a.small_mean_deg, num_sms);
+    b.tile_rows = tiny ? 32 : small_tile_rows(max_len, a.small_mean_deg, num_sms);
     const int64_t want = ((max_len + b.tile_rows - 1) / b.tile_rows + 7) / 8;
-    const int64_t cap = (int64_t)per_sm * num_sms;
+    const int64_t cap = (int64_t)ps * num_sms;
     const int grid = (int)(want < 1 ? 1 : (want < cap ? want : cap));
     void *args[] = {&b, &wlist, &wstart, &wcount, &bar, &err};
-    if (cudaLaunchCooperativeKernel((const void *)k_small_waves, dim3(grid), dim3(256), args, 0, st) !=
-        cudaSuccess)
+    const void *fn = tiny ? (const void *)k_tiny_waves : (const void *)k_small_waves;
+    if (cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(256), args, 0, st) != cudaSuccess)
         return -1;
     return 1;
 }

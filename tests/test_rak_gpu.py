@@ -304,11 +304,17 @@ def test_rmat_and_road_small(lp):
 def test_all_waves_launch_parity(lp, waves):
     """Asynchronous runs of 8 or more waves over rows of at most 32 entries
     sweep every wave of an iteration in one cooperative launch with grid
-    barriers: labels bit-exact with the oracle, also when resumed."""
+    barriers (rows of at most 8 entries: the kernel that loads the next
+    wave's rows before each barrier): labels bit-exact with the oracle, also
+    when resumed."""
     g = gg.kmer_like(120_000, seed=4)
     for strict in (True, False):
         labels, r, q = assert_async_parity(lp, g.offsets, g.indices, g.weights, waves,
                                            strict=strict, seed=3)
+    g = gg.sbm_mixing(20_000, 40, 14.0, 0.3, seed=6, wmin=1, wmax=4)  # rows of up to 32 entries
+    assert 8 < int(np.diff(g.offsets).max()) <= 32
+    for strict in (True, False):
+        assert_async_parity(lp, g.offsets, g.indices, g.weights, waves, strict=strict, seed=5)
     g = gg.grid_road(256, seed=5)
     assert_async_parity(lp, g.offsets, g.indices, g.weights, waves, strict=False, seed=2)
     # two iterations, then a resumed run from those labels
