@@ -502,6 +502,13 @@ def run_ours(args):
     prof = lp.lp_profile_read()
     prof_ms = p0.elapsed_time(p1)
 
+    # the ceiling of a label-gathering sweep on this graph: one pass streaming
+    # its entries and gathering one label per entry, with no per-row work
+    m4 = (g.m // 4) * 4
+    ceil_ms = lp.lp_probe_gather(g.n, idx[:m4], None if w is None else w[:m4],
+                                 torch.arange(g.n, dtype=torch.int32, device=dev), mode=1,
+                                 repeats=10, stream=stream.cuda_stream)
+
     t_ms, entries_all = reduce_across_ranks(t_ms, sum(iters) * g.m, device=dev)
 
     value = entries_all / (t_ms * 1e-3) / 1e9
@@ -542,6 +549,8 @@ def run_ours(args):
         "sweep": {"ms_per_sweep": per_sweep_ms, "gteps": g.m / (per_sweep_ms * 1e-3) / 1e9,
                   "alg_bytes": sweep_bytes,
                   "hbm_frac": sweep_bytes / (per_sweep_ms * 1e-3) / 1e9 / peak,
+                  "gather_ceiling_ms": ceil_ms,
+                  "of_gather_ceiling": ceil_ms / per_sweep_ms,
                   "run_ms_per_step": statistics.mean(run_ms),
                   "profiled_ms_per_step": prof_ms / args.steps,
                   "how": "steps timed with each RAK run launched from the host ahead of "
