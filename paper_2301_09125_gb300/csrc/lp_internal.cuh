@@ -245,8 +245,9 @@ int barrier_probe_launch(unsigned *bar, int32_t *err, uint32_t spin_limit, cudaS
 // Every wave of an asynchronous single-graph sweep whose rows all lie in the
 // small bucket, as one cooperative launch (wave k's list: wlist + wstart[k],
 // wcount[k] entries, both device arrays; max_len the longest).  bar: two
-// zeroed device words (left zeroed); *err set to 1 if a grid barrier timed
-// out.  Returns the kernel count (1) or -1.
+// device words, zeroed before every launch (the barriers count arrivals over
+// the launch); *err set to 1 if a grid barrier timed out.  Returns the kernel
+// count (1) or -1.
 // (max_degree: the graph's longest row; rows of at most 8 entries take the
 // kernel that loads the next wave's rows before each barrier)
 int small_waves_launch(const SweepArgs &a, const int32_t *wlist, const int64_t *wstart,

@@ -709,38 +709,35 @@ __global__ void __launch_bounds__(256, 6) k_small(SweepArgs a)
 }
 
 // Grid-wide barrier of a cooperative launch (every CTA resident).  bar[0]
-// counts arrivals, bar[1] is the generation: the last CTA to arrive resets
-// the count and advances the generation.  A CTA that polls more than
-// BARRIER_SPIN times records *err = 1; every CTA returns false once *err is
-// set, so the kernel ends instead of waiting.
+// counts arrivals over the whole launch (zeroed before it): barrier number
+// `epoch` (0, 1, ...) is passed once it has reached (epoch + 1) * expected,
+// so an arrival is one atomic and nothing has to be reset in between.  A CTA
+// that polls more than BARRIER_SPIN times records *err = 1; every CTA returns
+// false once *err is set, so the kernel ends instead of waiting.
 constexpr uint32_t BARRIER_SPIN = 1u << 22;
 
-__device__ bool grid_barrier(unsigned *bar, int32_t *err, unsigned expected = 0,
+__device__ bool grid_barrier(unsigned *bar, int32_t *err, uint32_t epoch, unsigned expected = 0,
                              uint32_t spin_limit = BARRIER_SPIN)
 {
     if (expected == 0) expected = gridDim.x;
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned *vgen = bar + 1;
-        const unsigned gen = *vgen;
-        __threadfence();
+        const unsigned target = (epoch + 1u) * expected;
+        __threadfence();  // this CTA's writes before its arrival
+        unsigned seen = atomicAdd(bar, 1u) + 1u;
+        volatile unsigned *vbar = bar;
         int ok = 1;
-        if (atomicAdd(bar, 1u) + 1u == expected) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
-            for (uint32_t spins = 0; *vgen == gen; ++spins) {
-                if (spins >= spin_limit) {
-                    atomicExch(err, 1);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(64);
+        for (uint32_t spins = 0; seen < target; ++spins) {
+            if (spins >= spin_limit) {
+                atomicExch(err, 1);
+                ok = 0;
+                break;
             }
+            __nanosleep(32);
+            seen = *vbar;
         }
-        __threadfence();
+        __threadfence();  // the other CTAs' writes before this CTA's reads
         s_ok = ok && *(volatile int32_t *)err == 0;
     }
     __syncthreads();
@@ -751,7 +748,7 @@ __device__ bool grid_barrier(unsigned *bar, int32_t *err, unsigned expected = 0,
 // the grid has, so the wait runs out after spin_limit polls and sets *err.
 __global__ void k_barrier_probe(unsigned *bar, int32_t *err, uint32_t spin_limit)
 {
-    grid_barrier(bar, err, gridDim.x + 1u, spin_limit);
+    grid_barrier(bar, err, 0u, gridDim.x + 1u, spin_limit);
 }
 
 // Every wave of an asynchronous sweep of a single graph whose rows are all in
@@ -770,7 +767,7 @@ __global__ void __launch_bounds__(256, 6) k_small_waves(SweepArgs a, const int32
         b.len = wcount[k];
         b.identity = a.identity && k == 0;  // later waves read this sweep's labels
         small_sweep<false, true>(b);
-        if (k + 1 < a.waves && !grid_barrier(bar, err)) return;
+        if (k + 1 < a.waves && !grid_barrier(bar, err, k)) return;
     }
 }
 
@@ -870,7 +867,7 @@ __global__ void __launch_bounds__(256, 2) k_tiny_waves(SweepArgs a, const int32_
         }
         if (k + 1 < a.waves) {
             tiny_fetch(a, wlist + wstart[k + 1], a.rp + wstart[k + 1], wcount[k + 1], wid, r);
-            if (!grid_barrier(bar, err)) return;
+            if (!grid_barrier(bar, err, k)) return;
         }
     }
     my_changed = __reduce_add_sync(FULL, my_changed);
