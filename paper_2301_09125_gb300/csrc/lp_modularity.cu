@@ -123,45 +123,20 @@ __global__ void __launch_bounds__(MT) k_mod_entries(ModArgs a)
     int32_t *s_vb = s_vb_all[MULTI ? wib : 0];
     int32_t *s_g = s_g_all[MULTI ? wib : 0];
     const int64_t j_lo = chunk * CH;
-    int nr = 0;
-    if (have) {
-        const int64_t r0 = a.first_row[chunk];
-        const int64_t r1 = a.first_row[chunk + 1];
-        nr = (int)min(r1 - r0 + 1, (int64_t)CH + 1);
-        for (int k = lane; k <= nr; k += 32) s_rp[k] = (int32_t)(a.rp[r0 + k] - j_lo);
-        for (int k = lane; k < nr; k += 32) {
-            const int32_t v = a.list[r0 + k];
-            if (MULTI) {
-                const int32_t g = a.vgraph[v];
-                s_g[k] = g;
-                s_vb[k] = a.g_vbase[g];
-            }
-            s_c[k] = a.lab[v];
-            s_kv[k] = 0u;
-        }
-    }
-    if (threadIdx.x == 0) {
-        s_dom = 0ull;
-        s_dom_slot = -1;
-    }
-    __syncwarp();
-    if (wib == 0 && lane == 0 && have) s_dom_slot = (MULTI ? (int64_t)s_vb[0] : 0) + s_c[0];
-
-    unsigned long long l = 0, w2 = 0;
-    AccRun run;
     const int rel0 = lane * MPER;
     const int rel_hi = have ? (int)(min(j_lo + (int64_t)CH, a.ne) - j_lo) : 0;
+    // the entries first (they depend on the chunk only) and, for a single
+    // graph, their neighbours' labels, so that these loads overlap the
+    // staging of the chunk's rows below
+    int32_t u[MPER], w[MPER], cu[MPER];
+#pragma unroll
+    for (int q = 0; q < MPER; ++q) {
+        u[q] = 0;
+        w[q] = 0;
+        cu[q] = EMPTY;
+    }
     if (rel0 < rel_hi) {
-        int lo = 0, hi = nr;  // s_rp[lo] <= rel0 < s_rp[hi]
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (s_rp[mid] <= rel0)
-                lo = mid;
-            else
-                hi = mid;
-        }
         const int64_t j0 = j_lo + rel0;
-        int32_t u[MPER], w[MPER];
         if (rel0 + MPER <= rel_hi) {  // 32-byte aligned: j_lo and rel0 are multiples of 8
             const int4 *pi = reinterpret_cast<const int4 *>(a.idx + j0);
             const int4 i0 = __ldcs(pi), i1 = __ldcs(pi + 1);
@@ -190,7 +165,48 @@ __global__ void __launch_bounds__(MT) k_mod_entries(ModArgs a)
             for (int q = 0; q < MPER; ++q)
                 if (j0 + q < a.e_lo) w[q] = 0;
         }
-        // rows of the entries (shared memory), then every label gather in flight
+    }
+    if (!MULTI) {
+#pragma unroll
+        for (int q = 0; q < MPER; ++q)
+            cu[q] = w[q] ? __ldg(a.lab + (u[q] & MOD_ID_MASK)) : EMPTY;
+    }
+    int nr = 0;
+    if (have) {
+        const int64_t r0 = a.first_row[chunk];
+        const int64_t r1 = a.first_row[chunk + 1];
+        nr = (int)min(r1 - r0 + 1, (int64_t)CH + 1);
+        for (int k = lane; k <= nr; k += 32) s_rp[k] = (int32_t)(a.rp[r0 + k] - j_lo);
+        for (int k = lane; k < nr; k += 32) {
+            const int32_t v = a.list[r0 + k];
+            if (MULTI) {
+                const int32_t g = a.vgraph[v];
+                s_g[k] = g;
+                s_vb[k] = a.g_vbase[g];
+            }
+            s_c[k] = a.lab[v];
+            s_kv[k] = 0u;
+        }
+    }
+    if (threadIdx.x == 0) {
+        s_dom = 0ull;
+        s_dom_slot = -1;
+    }
+    __syncwarp();
+    if (wib == 0 && lane == 0 && have) s_dom_slot = (MULTI ? (int64_t)s_vb[0] : 0) + s_c[0];
+
+    unsigned long long l = 0, w2 = 0;
+    AccRun run;
+    if (rel0 < rel_hi) {
+        int lo = 0, hi = nr;  // s_rp[lo] <= rel0 < s_rp[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (s_rp[mid] <= rel0)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        // rows of the entries (shared memory)
         int kq[MPER];
         int k = lo;
 #pragma unroll
@@ -198,11 +214,10 @@ __global__ void __launch_bounds__(MT) k_mod_entries(ModArgs a)
             while (k + 1 < nr && s_rp[k + 1] <= rel0 + q) ++k;
             kq[q] = k;
         }
-        int32_t cu[MPER];
+        if (MULTI) {
 #pragma unroll
-        for (int q = 0; q < MPER; ++q) {
-            const int64_t vb = MULTI ? s_vb[kq[q]] : 0;
-            cu[q] = w[q] ? __ldg(a.lab + vb + (u[q] & MOD_ID_MASK)) : EMPTY;
+            for (int q = 0; q < MPER; ++q)
+                cu[q] = w[q] ? __ldg(a.lab + (int64_t)s_vb[kq[q]] + (u[q] & MOD_ID_MASK)) : EMPTY;
         }
         int cur = kq[0];
         uint32_t rs = 0u;  // the current row's weight in this lane's entries
