@@ -1159,14 +1159,18 @@ def run_experiment(args):
 def run_split_experiment(args):
     """Split of disconnected communities after RAK (each class's benchmark
     parameters): communities before and after, modularity before and after,
-    time of the split (CUDA events on the library's stream)."""
+    time of the split (CUDA events on the library's stream), its roofline,
+    and the oracle's split of the same labels (checked equal, and timed)."""
     import torch
+
+    import oracle
 
     import paper_2301_09125_gb300 as lp
     from paper_2301_09125_gb300 import build
 
     build.build()
     lp.load()
+    oracle.build()
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
@@ -1193,13 +1197,33 @@ def run_split_experiment(args):
             if rep:  # the first split pays for its scratch allocation
                 times.append(e0.elapsed_time(e1))
             q1 = lp.lp_modularity(h)
+            after = lp.lp_labels_get(h)
             lp.lp_graph_destroy(h)
         ms = statistics.median(times)
+        # the oracle's split of the same labels, on one host core; its result
+        # is the GPU's (component ids are the smallest vertices)
+        t0 = time.perf_counter()
+        ref, ref_k = oracle.split(g.offsets, g.indices, before)
+        cpu_s = time.perf_counter() - t0
+        # algorithmic bytes: the CSR's offsets and column indices once, the
+        # labels read and the component ids written once
+        alg = 4 * (g.n + 1) + 4 * g.m + 8 * g.n
+        peak, peak_kind = measured_peak_gbs()
         print(json.dumps({"experiment": "split", "workload": name, "n": g.n, "m": g.m,
                           "mode": p["mode"], "communities_before": int(len(np.unique(before))),
                           "communities_after": k, "modularity_before": q0,
                           "modularity_after": q1, "split_ms": ms,
-                          "gteps": g.m / (ms * 1e-3) / 1e9}), flush=True)
+                          "gteps": g.m / (ms * 1e-3) / 1e9,
+                          "equals_oracle": bool(ref_k == k and np.array_equal(ref, after)),
+                          "roofline": {"bound": "hbm", "achieved": alg / (ms * 1e-3) / 1e9,
+                                       "peak": peak, "unit": "GB/s",
+                                       "frac": alg / (ms * 1e-3) / 1e9 / peak, "traffic": None,
+                                       "alg_bytes": alg, "peak_source": peak_kind},
+                          "cpu_baseline": {"value": g.m / cpu_s / 1e9, "unit": "GTEPS",
+                                           "cores": 1, "kind": "oracle",
+                                           "sample": f"the split of the same labels on the full "
+                                                     f"graph ({cpu_s:.1f} s, single thread)"}}),
+              flush=True)
     return 0
 
 
