@@ -542,21 +542,45 @@ struct GraphSet {
         return LP_OK;
     }
 
-    // validate graph g's device CSR (already in place)
-    lp_status validate(int32_t g, const int32_t *o, const int32_t *ix, const int32_t *w, int32_t n,
-                       int64_t m, int graph_index)
+    // validate every graph of a batch (device CSR in place): the checks of
+    // all graphs are launched before one read-back of their status words (a
+    // weight-sum check follows for graphs whose degrees and weights could
+    // reach 2^31); errors name the first invalid graph
+    lp_status validate_all()
     {
+        IngestOut *d_all = nullptr, *h_all = nullptr;
+        LP_TRY(dev_alloc(&d_all, G, "validation status", st, device));
+        lp_status s = host_alloc(&h_all, G, "validation status");
         Launches L;
-        if (ingest_validate(o, ix, w, n, m, d_ing, st, &L.n) != 0)
-            return fail(LP_ECUDA, cuda_msg("validation launch", cudaGetLastError()));
-        LP_TRY(read_ingest(graph_index));
-        if ((int64_t)h_ing->max_deg * (int64_t)h_ing->max_w >= 2147483648LL) {
-            if (ingest_check_wdeg(o, w, n, d_ing, st, &L.n) != 0)
-                return fail(LP_ECUDA, cuda_msg("weight-sum launch", cudaGetLastError()));
-            LP_TRY(read_ingest(graph_index));
-        }
-        (void)g;
-        return LP_OK;
+        auto launch_and_read = [&](bool wdeg) -> lp_status {
+            for (int32_t g = 0; g < G; ++g) {
+                const int64_t ob = (int64_t)h_vbase[(size_t)g] + g, e0 = h_ebase[(size_t)g];
+                const int32_t *w = wts ? wts + e0 : nullptr;
+                int rc = 0;
+                if (!wdeg)
+                    rc = ingest_validate(off + ob, idx + e0, w, h_n[(size_t)g], h_m[(size_t)g],
+                                         d_all + g, st, &L.n);
+                else if ((int64_t)h_all[g].max_deg * h_all[g].max_w >= 2147483648LL)
+                    rc = ingest_check_wdeg(off + ob, w, h_n[(size_t)g], d_all + g, st, &L.n);
+                if (rc != 0) return fail(LP_ECUDA, cuda_msg("validation launch", cudaGetLastError()));
+            }
+            LP_CU(cudaMemcpyAsync(h_all, d_all, (size_t)G * sizeof(IngestOut),
+                                  cudaMemcpyDeviceToHost, st));
+            LP_CU(cudaStreamSynchronize(st));
+            for (int32_t g = 0; g < G; ++g)
+                if (h_all[g].err != ING_OK) {
+                    char buf[256];
+                    snprintf(buf, sizeof buf, "graph %d: %s %d", g, ingest_what(h_all[g].err),
+                             h_all[g].err_at);
+                    return fail(LP_EINVAL, buf);
+                }
+            return LP_OK;
+        };
+        if (s == LP_OK) s = launch_and_read(false);
+        if (s == LP_OK) s = launch_and_read(true);
+        cudaFreeAsync(d_all, st);
+        if (h_all) host_free(h_all);
+        return s;
     }
 
     // validate a single graph's device CSR and check its row order in one pass
@@ -2195,13 +2219,7 @@ lp_status lp_batch_create(int32_t count, const lp_graph_desc *graphs, uint32_t f
             }
         }
     }
-    LP_CU(cudaStreamSynchronize(s.st));
-    for (int32_t i = 0; i < count; ++i) {
-        const int64_t ob = (int64_t)s.h_vbase[(size_t)i] + i;
-        const int64_t e0 = s.h_ebase[(size_t)i];
-        LP_TRY(s.validate(i, s.off + ob, s.idx + e0, s.wts ? s.wts + e0 : nullptr, graphs[i].n,
-                          graphs[i].m, i));
-    }
+    LP_TRY(s.validate_all());
     // graph of every global vertex, per-graph bases and sizes
     std::vector<int32_t> vg((size_t)nv);
     for (int32_t i = 0; i < count; ++i)
