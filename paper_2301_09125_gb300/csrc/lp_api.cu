@@ -610,6 +610,7 @@ struct GraphSet {
         rows_distinct = false;
         uint32_t *bits = nullptr;
         LP_TRY(dev_alloc(&bits, ne / 32 + 1, "row-start bitmap", st, device));
+        LP_CU(cudaMemsetAsync(d_ing, 0, sizeof(IngestOut), st));  // the check's status word
         Launches L;
         const int rc = ingest_row_order(off, idx, nv, ne, vgraph, g_ebase, bits, d_ing, st, &L.n);
         cudaFreeAsync(bits, st);
