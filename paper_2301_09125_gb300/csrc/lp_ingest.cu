@@ -180,16 +180,19 @@ __device__ __forceinline__ int32_t degree_of(const int32_t *off, const int32_t *
     return off[(int64_t)v + g + 1] - off[(int64_t)v + g];
 }
 
+// Per block of BK vertices: its row count (blk) and entry count (bent) in
+// every bucket, stored per bucket and block (the class scan sums them, so no
+// global atomic is shared by the blocks).
 __global__ void __launch_bounds__(BK) k_bucket_count(const int32_t *off, int32_t nv,
                                                       const int32_t *vgraph, Thresholds th,
-                                                      int32_t *blk, unsigned long long *entries)
+                                                      int32_t *blk, int64_t *bent)
 {
     __shared__ int cnt[NUM_BUCKETS];
-    __shared__ unsigned long long ent[NUM_BUCKETS];
-    if (threadIdx.x < NUM_BUCKETS) {
-        cnt[threadIdx.x] = 0;
-        ent[threadIdx.x] = 0;
-    }
+    __shared__ uint32_t ent[NUM_BUCKETS - 1];  // < BK * 1024: 32 bits suffice
+    __shared__ unsigned long long ent_last;
+    if (threadIdx.x < NUM_BUCKETS) cnt[threadIdx.x] = 0;
+    if (threadIdx.x < NUM_BUCKETS - 1) ent[threadIdx.x] = 0u;
+    if (threadIdx.x == 0) ent_last = 0ull;
     __syncthreads();
     const int64_t v = (int64_t)blockIdx.x * BK + threadIdx.x;
     const int32_t d = v < nv ? degree_of(off, vgraph, (int32_t)v) : 0;
@@ -202,19 +205,21 @@ __global__ void __launch_bounds__(BK) k_bucket_count(const int32_t *off, int32_t
         const uint32_t sum = __reduce_add_sync(FULL, b == c ? (uint32_t)d : 0u);
         if ((threadIdx.x & 31) == 0 && mask) {
             atomicAdd(&cnt[c], __popc(mask));
-            atomicAdd(&ent[c], (unsigned long long)sum);
+            atomicAdd(&ent[c], sum);
         }
     }
     if (b == NUM_BUCKETS - 1) {
         atomicAdd(&cnt[b], 1);
-        atomicAdd(&ent[b], (unsigned long long)d);
+        atomicAdd(&ent_last, (unsigned long long)d);
     }
     __syncthreads();
     if (threadIdx.x < NUM_BUCKETS) {
-        blk[(int64_t)threadIdx.x * gridDim.x + blockIdx.x] = cnt[threadIdx.x];
-        if (ent[threadIdx.x]) atomicAdd(entries + threadIdx.x, ent[threadIdx.x]);
+        const int64_t at = (int64_t)threadIdx.x * gridDim.x + blockIdx.x;
+        blk[at] = cnt[threadIdx.x];
+        bent[at] = threadIdx.x < NUM_BUCKETS - 1 ? (int64_t)ent[threadIdx.x] : (int64_t)ent_last;
     }
 }
+
 
 // exclusive block scan of one int per thread; returns the prefix, *total the sum
 __device__ int64_t block_exclusive_scan(int64_t x, int64_t *s_warp, int64_t *total)
@@ -293,6 +298,19 @@ __device__ void block_exclusive_scan_k(const int64_t (&x)[K], int64_t (&ex)[K], 
 // of class c in block b at hist[c * nblk + b].  One block per class turns its
 // counts into exclusive offsets within the class (in place) and records the
 // class size; one block then turns the sizes into class starts.
+// the entries of bucket blockIdx.x: the sum of its blocks' counts
+__global__ void __launch_bounds__(1024) k_bucket_entries(const int64_t *bent, int64_t nblk,
+                                                          int64_t *total)
+{
+    __shared__ int64_t s_warp[33];
+    const int64_t *e = bent + (int64_t)blockIdx.x * nblk;
+    int64_t part = 0;
+    for (int64_t i = threadIdx.x; i < nblk; i += 1024) part += e[i];
+    int64_t tot;
+    block_exclusive_scan(part, s_warp, &tot);
+    if (threadIdx.x == 0) total[blockIdx.x] = tot;
+}
+
 __global__ void __launch_bounds__(1024) k_class_scan(int32_t *hist, int64_t nblk,
                                                       int64_t *class_size)
 {
@@ -786,10 +804,16 @@ int ingest_check_wdeg(const int32_t *off, const int32_t *wts, int32_t n, IngestO
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
+// per block and bucket: a row count (int32), then, 8-byte aligned, an entry
+// count (int64)
+static int64_t bucket_count_words(int64_t nblk) { return (nblk * NUM_BUCKETS + 1) & ~(int64_t)1; }
+
 size_t ingest_bucket_scratch_bytes(int32_t nv_total)
 {
-    const int64_t nblk = ((int64_t)nv_total + BK - 1) / BK;
-    return (size_t)(nblk > 0 ? nblk : 1) * NUM_BUCKETS * sizeof(int32_t);
+    int64_t nblk = ((int64_t)nv_total + BK - 1) / BK;
+    if (nblk < 1) nblk = 1;
+    return (size_t)bucket_count_words(nblk) * sizeof(int32_t) +
+           (size_t)nblk * NUM_BUCKETS * sizeof(int64_t);
 }
 
 int ingest_bucket(const int32_t *off, int32_t nv, const int32_t *vgraph, const int32_t *,
@@ -800,13 +824,13 @@ int ingest_bucket(const int32_t *off, int32_t nv, const int32_t *vgraph, const i
     if (cudaMemsetAsync(d_counts, 0, 3 * NUM_BUCKETS * sizeof(int64_t), st) != cudaSuccess)
         return -1;
     if (nblk == 0) return 0;
-    k_bucket_count<<<(int)nblk, BK, 0, st>>>(
-        off, nv, vgraph, th, blk,
-        reinterpret_cast<unsigned long long *>(d_counts + 2 * NUM_BUCKETS));
+    int64_t *bent = reinterpret_cast<int64_t *>(blk + bucket_count_words(nblk));
+    k_bucket_count<<<(int)nblk, BK, 0, st>>>(off, nv, vgraph, th, blk, bent);
+    k_bucket_entries<<<NUM_BUCKETS, 1024, 0, st>>>(bent, nblk, d_counts + 2 * NUM_BUCKETS);
     k_class_scan<<<NUM_BUCKETS, 1024, 0, st>>>(blk, nblk, d_counts);
     k_class_begin<<<1, 1024, 0, st>>>(d_counts, NUM_BUCKETS, d_counts + NUM_BUCKETS);
     k_bucket_scatter<<<(int)nblk, BK, 0, st>>>(off, nv, vgraph, th, blk, d_counts, list);
-    *launches += 4;
+    *launches += 5;
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
