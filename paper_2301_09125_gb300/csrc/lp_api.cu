@@ -656,21 +656,37 @@ struct GraphSet {
         // the hub kernels balances
         if (bl[HUB_BUCKET] > 0) {
             int32_t *ordered = nullptr;
-            LP_TRY(dev_alloc(&ordered, bl[HUB_BUCKET], "hub order", st, device));
+            int64_t *hsc = nullptr;
+            LP_TRY(dev_alloc(&hsc, hub_scratch_ints(bl[HUB_BUCKET]), "hub scratch", st, device));
+            lp_status as = dev_alloc(&ordered, bl[HUB_BUCKET], "hub order", st, device);
+            if (as != LP_OK) {
+                cudaFreeAsync(hsc, st);
+                return as;
+            }
             cudaError_t e = cudaSuccess;
-            if (hub_order(list + bb[HUB_BUCKET], bl[HUB_BUCKET], off, vgraph, ordered, st, &L.n) != 0)
+            if (hub_order(list + bb[HUB_BUCKET], bl[HUB_BUCKET], off, vgraph, ordered, hsc, st,
+                          &L.n) != 0)
                 e = cudaGetLastError();
             if (e == cudaSuccess)
                 e = cudaMemcpyAsync(list + bb[HUB_BUCKET], ordered, bl[HUB_BUCKET] * sizeof(int32_t),
                                     cudaMemcpyDeviceToDevice, st);
             cudaFreeAsync(ordered, st);
-            if (e != cudaSuccess) return fail(LP_ECUDA, cuda_msg("hub order", e));
+            if (e != cudaSuccess) {
+                cudaFreeAsync(hsc, st);
+                return fail(LP_ECUDA, cuda_msg("hub order", e));
+            }
             // hub tasks, the segment / partition scratch of the long rows and
             // one fallback table per long row (zeroed; every use leaves it zeroed)
-            LP_TRY(dev_alloc(&htask, bl[HUB_BUCKET], "hub tasks", st, device));
+            as = dev_alloc(&htask, bl[HUB_BUCKET], "hub tasks", st, device);
+            if (as != LP_OK) {
+                cudaFreeAsync(hsc, st);
+                return as;
+            }
             int64_t tot[5] = {0, 0, 0, 0, 0};
-            if (hub_tasks(list + bb[HUB_BUCKET], bl[HUB_BUCKET], off, vgraph, htask, d_counts, st, &L.n) != 0)
-                return fail(LP_ECUDA, cuda_msg("hub tasks", cudaGetLastError()));
+            const int rc = hub_tasks(list + bb[HUB_BUCKET], bl[HUB_BUCKET], off, vgraph, htask,
+                                     d_counts, hsc, st, &L.n);
+            cudaFreeAsync(hsc, st);
+            if (rc != 0) return fail(LP_ECUDA, cuda_msg("hub tasks", cudaGetLastError()));
             LP_CU(cudaMemcpyAsync(tot, d_counts, sizeof tot, cudaMemcpyDeviceToHost, st));
             LP_CU(cudaStreamSynchronize(st));
             hmulti = tot[0];
@@ -697,7 +713,6 @@ struct GraphSet {
             LP_CU(cudaMemsetAsync(hnpos, 0, (size_t)slots * sizeof(uint32_t), st));
             LP_CU(cudaMemsetAsync(hdone, 0, (size_t)bl[HUB_BUCKET] * sizeof(int32_t), st));
             LP_CU(cudaMemsetAsync(hnused, 0, (size_t)bl[HUB_BUCKET] * sizeof(int32_t), st));
-            LP_CU(cudaStreamSynchronize(st));
         }
         return LP_OK;
     }
@@ -834,12 +849,19 @@ struct GraphSet {
         if (!d_wtot) LP_TRY(dev_alloc(&d_wtot, NUM_BUCKETS * WAVE_MAX, "wave sizes", st, device));
         int32_t *hist = nullptr;
         LP_TRY(dev_alloc(&hist, wave_hist_ints(len, waves), "wave histogram", st, device));
+        if (!d_wstart0) LP_TRY(dev_alloc(&d_wstart0, WAVE_MAX, "wave starts", st, device));
         Launches L;
         const int nc = NUM_BUCKETS * waves;
         std::vector<int64_t> tot((size_t)nc);
         cudaError_t e = cudaSuccess;
         if (wave_partition(list, len, bb, vgraph, g_vbase, waves, hist, d_wtot, wlist, st, &L.n) != 0)
             e = cudaGetLastError();
+        // the starts of the small bucket's waves: the partition's first class
+        // starts (its scratch begins with the class starts)
+        if (e == cudaSuccess)
+            e = len > 0 ? cudaMemcpyAsync(d_wstart0, hist, (size_t)waves * sizeof(int64_t),
+                                          cudaMemcpyDeviceToDevice, st)
+                        : cudaMemsetAsync(d_wstart0, 0, (size_t)waves * sizeof(int64_t), st);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(tot.data(), d_wtot, (size_t)nc * sizeof(int64_t),
                                 cudaMemcpyDeviceToHost, st);
@@ -853,10 +875,6 @@ struct GraphSet {
             wstart[(size_t)c] = acc;
             acc += tot[(size_t)c];
         }
-        if (!d_wstart0) LP_TRY(dev_alloc(&d_wstart0, WAVE_MAX, "wave starts", st, device));
-        LP_CU(cudaMemcpyAsync(d_wstart0, wstart.data(), (size_t)waves * sizeof(int64_t),
-                              cudaMemcpyHostToDevice, st));
-        LP_CU(cudaStreamSynchronize(st));  // wstart is host memory that may change
         // hub tasks of each wave's part of the hub bucket (contiguous classes)
         hmulti_w.assign((size_t)waves, 0);
         hsegs_w.assign((size_t)waves, 0);
@@ -867,6 +885,15 @@ struct GraphSet {
             std::vector<int64_t> tots(5 * (size_t)waves, 0);
             int64_t *d_tot = nullptr;
             LP_TRY(dev_alloc(&d_tot, 5 * (int64_t)waves, "hub totals", st, device));
+            int64_t most = 1;
+            for (int k = 0; k < waves; ++k)
+                most = std::max(most, wcount[(size_t)HUB_BUCKET * waves + k]);
+            int64_t *hsc = nullptr;
+            const lp_status as = dev_alloc(&hsc, hub_scratch_ints(most), "hub scratch", st, device);
+            if (as != LP_OK) {
+                cudaFreeAsync(d_tot, st);
+                return as;
+            }
             Launches L2;
             cudaError_t e2 = cudaMemsetAsync(d_tot, 0, tots.size() * sizeof(int64_t), st);
             for (int k = 0; k < waves && e2 == cudaSuccess; ++k) {
@@ -874,9 +901,10 @@ struct GraphSet {
                 if (c == 0) continue;
                 const int64_t st0 = wstart[(size_t)HUB_BUCKET * waves + k];
                 if (hub_tasks(wlist + st0, c, off, vgraph, htask_w + (st0 - hub0), d_tot + 5 * k,
-                              st, &L2.n) != 0)
+                              hsc, st, &L2.n) != 0)
                     e2 = cudaGetLastError();
             }
+            cudaFreeAsync(hsc, st);
             if (e2 == cudaSuccess)
                 e2 = cudaMemcpyAsync(tots.data(), d_tot, tots.size() * sizeof(int64_t),
                                      cudaMemcpyDeviceToHost, st);
@@ -1440,9 +1468,11 @@ struct GraphSet {
     // Sec. 3.2's iteration launched from the host without waiting for each
     // iteration: the tolerance test runs on the device after every iteration
     // and raises a stop flag once the run is over; the host checks the flag
-    // of the iteration RUN_LAG before the one it has just launched, so that
-    // iterations launched past the end (at most RUN_LAG) return at once.
+    // of the iteration RUN_LAG (or one, on large graphs) before the one it has
+    // just launched, so that iterations launched past the end (at most
+    // RUN_LAG) return at once.
     static constexpr int RUN_LAG = 2;
+    static constexpr int64_t LAG1_ENTRIES = (int64_t)1 << 25;
     int32_t *d_stop = nullptr, *h_stop = nullptr;
     int32_t h_stop_cap = 0;
     cudaEvent_t run_ev[RUN_LAG + 1] = {};
@@ -1481,9 +1511,14 @@ struct GraphSet {
             LP_CU(cudaMemcpyAsync(h_stop + it, d_stop, sizeof(int32_t), cudaMemcpyDeviceToHost,
                                   st));
             LP_CU(cudaEventRecord(run_ev[it % (RUN_LAG + 1)], st));
-            if (it >= RUN_LAG) {
-                LP_CU(cudaEventSynchronize(run_ev[(it - RUN_LAG) % (RUN_LAG + 1)]));
-                if (h_stop[it - RUN_LAG]) break;
+            // one iteration back when an iteration outlasts the host's
+            // launches of the next (a graph of at least LAG1_ENTRIES entries,
+            // or one all-waves launch per iteration): one fewer iteration is
+            // launched past the end
+            const int lag = (rs.coop || ne >= LAG1_ENTRIES) ? 1 : RUN_LAG;
+            if (it >= lag) {
+                LP_CU(cudaEventSynchronize(run_ev[(it - lag) % (RUN_LAG + 1)]));
+                if (h_stop[it - lag]) break;
             }
         }
         LP_CU(cudaMemcpyAsync(h_res, d_res, res_bytes, cudaMemcpyDeviceToHost, st));

@@ -400,125 +400,171 @@ __global__ void k_merge_final(int32_t *lab0, const int32_t *lab1, int32_t nv,
         if (g_sel[vgraph[v]]) lab0[v] = lab1[v];
 }
 
-// one block: hub tasks with exclusive prefixes of segments and table slots
-__global__ void __launch_bounds__(1024) k_hub_tasks(int32_t *__restrict__ list, int64_t len,
-                                                     const int32_t *off, const int32_t *vgraph,
-                                                     HubTask *__restrict__ tasks, int64_t *totals)
+// ---------------------------------------------------------------------------
+// hub rows: their order and their tasks, each as a few multi-block passes over
+// blocks of HT rows (a block-sum pass, one scan of the block sums, a write
+// pass), so that no single block walks the whole hub list
+// ---------------------------------------------------------------------------
+constexpr int HT = 1024;        // hub rows per block
+constexpr int HUB_CLASSES = 32; // degree classes of the hub order: clz(degree)
+
+// Shape of a hub row of d entries: [0] long (more than HUB_ONE_MAX entries),
+// [1] short, [2] fallback table slots, [3] segments, [4] partitions, [5]
+// partition offsets (the last four 0 for a short row).
+__device__ __forceinline__ void hub_shape(int32_t d, int64_t (&x)[6])
+{
+    const bool big = d > HUB_ONE_MAX;
+    int64_t tsz = 0, nseg = 0, npart = 0;
+    if (big) {
+        tsz = 1;
+        while (tsz < 2 * (int64_t)d) tsz <<= 1;
+        nseg = ((int64_t)d + HUB_SEG - 1) / HUB_SEG;
+        npart = nseg < HUB_PMAX ? nseg : HUB_PMAX;
+    }
+    x[0] = big;
+    x[1] = !big;
+    x[2] = tsz;
+    x[3] = nseg;
+    x[4] = npart;
+    x[5] = nseg * (npart + 1);
+}
+
+// block sums of the six shape values: bsum[blk * 6 + k]
+__global__ void __launch_bounds__(HT) k_hub_task_sums(const int32_t *list, int64_t len,
+                                                       const int32_t *off, const int32_t *vgraph,
+                                                       int64_t *bsum)
 {
     __shared__ int64_t s_scan6[33][6];
-    // thread t takes a contiguous run of rows: it sums them, one block scan
-    // turns the sums into its starting positions, then it writes their tasks
-    const int64_t per = (len + blockDim.x - 1) / blockDim.x;
-    const int64_t lo = min(len, (int64_t)threadIdx.x * per), hi = min(len, lo + per);
-    // per row: long, short, fallback table slots, segments, partitions,
-    // partition offsets
-    auto shape = [](int32_t d, int64_t (&x)[6]) {
-        const bool big = d > HUB_ONE_MAX;
-        int64_t tsz = 0, nseg = 0, npart = 0;
-        if (big) {
-            tsz = 1;
-            while (tsz < 2 * (int64_t)d) tsz <<= 1;
-            nseg = ((int64_t)d + HUB_SEG - 1) / HUB_SEG;
-            npart = nseg < HUB_PMAX ? nseg : HUB_PMAX;
-        }
-        x[0] = big;
-        x[1] = !big;
-        x[2] = tsz;
-        x[3] = nseg;
-        x[4] = npart;
-        x[5] = nseg * (npart + 1);
-    };
-    int64_t sums[6] = {0, 0, 0, 0, 0, 0};
-#pragma unroll 4
-    for (int64_t i = lo; i < hi; ++i) {
-        int64_t x[6];
-        shape(degree_of(off, vgraph, list[i]), x);
-#pragma unroll
-        for (int k = 0; k < 6; ++k) sums[k] += x[k];
-    }
-    int64_t at[6], tot[6];
-    block_exclusive_scan_k<6>(sums, at, tot, s_scan6);
-    at[1] += tot[0];  // short rows follow every long row
-    for (int64_t i = lo; i < hi; ++i) {
-        const int32_t v = list[i];
-        const int32_t d = degree_of(off, vgraph, v);
-        int64_t x[6];
-        shape(d, x);
-        const bool big = x[0] != 0;
-        HubTask t;
-        t.v = v;
-        t.d = d;
-        t.nseg = (int32_t)x[3];
-        t.npart = (int32_t)x[4];
-        t.seg0 = big ? (int32_t)at[3] : 0;
-        t.part0 = big ? (int32_t)at[4] : 0;
-        t.poff0 = big ? at[5] : 0;
-        t.tab = big ? at[2] : 0;
-        t.e0 = 0;  // set once the rows are packed (hub_task_starts)
-        tasks[big ? at[0] : at[1]] = t;
-#pragma unroll
-        for (int k = 0; k < 6; ++k) at[k] += x[k];
-    }
-    __syncthreads();
-    for (int64_t i = threadIdx.x; i < len; i += blockDim.x) list[i] = tasks[i].v;
+    const int64_t i = (int64_t)blockIdx.x * HT + threadIdx.x;
+    int64_t x[6] = {0, 0, 0, 0, 0, 0}, ex[6], tot[6];
+    if (i < len) hub_shape(degree_of(off, vgraph, list[i]), x);
+    block_exclusive_scan_k<6>(x, ex, tot, s_scan6);
     if (threadIdx.x == 0) {
-        totals[0] = tot[0];
-        totals[1] = tot[2];
-        totals[2] = tot[3];
-        totals[3] = tot[4];
-        totals[4] = tot[5];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) bsum[(int64_t)blockIdx.x * 6 + k] = tot[k];
     }
 }
 
-// Hub rows in decreasing order of floor(log2(degree)), stable within a class:
-// the longest rows come first, so the hub kernels' static CTA assignment
-// starts them first and the grid stays balanced.  One block.
-__global__ void __launch_bounds__(1024) k_hub_order(const int32_t *list, int64_t len,
-                                                     const int32_t *off, const int32_t *vgraph,
-                                                     int32_t *out)
+// one block: the block sums become exclusive block starts (in place); totals
+// as hub_tasks reports them
+__global__ void __launch_bounds__(1024) k_hub_task_scan(int64_t *bsum, int64_t nblk,
+                                                         int64_t *totals)
 {
-    __shared__ int32_t s_start[32];      // next position of each class
-    __shared__ int32_t s_wc[32][33];     // per warp and class: count, then position
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    if (threadIdx.x < 32) s_start[threadIdx.x] = 0;
-    __syncthreads();
-    // class = count of leading zero bits of the degree (degrees >= 1)
-    for (int64_t i = threadIdx.x; i < len; i += 1024)
-        atomicAdd(&s_start[__clz(degree_of(off, vgraph, list[i]))], 1);
-    __syncthreads();
+    __shared__ int64_t s_scan6[33][6];
+    int64_t running[6] = {0, 0, 0, 0, 0, 0};
+    for (int64_t i0 = 0; i0 < nblk; i0 += 1024) {
+        const int64_t i = i0 + threadIdx.x;
+        int64_t x[6], ex[6], tot[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) x[k] = i < nblk ? bsum[i * 6 + k] : 0;
+        block_exclusive_scan_k<6>(x, ex, tot, s_scan6);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            if (i < nblk) bsum[i * 6 + k] = running[k] + ex[k];
+            running[k] += tot[k];
+        }
+    }
     if (threadIdx.x == 0) {
-        int32_t run = 0;
-        for (int c = 0; c < 32; ++c) {
-            const int32_t t = s_start[c];
-            s_start[c] = run;
+        totals[0] = running[0];
+        totals[1] = running[2];
+        totals[2] = running[3];
+        totals[3] = running[4];
+        totals[4] = running[5];
+    }
+}
+
+// the tasks of a block's rows: long rows at their prefix among long rows,
+// short rows after every long row at their prefix among short rows
+__global__ void __launch_bounds__(HT) k_hub_task_write(const int32_t *list, int64_t len,
+                                                        const int32_t *off, const int32_t *vgraph,
+                                                        const int64_t *bstart,
+                                                        const int64_t *totals, HubTask *tasks)
+{
+    __shared__ int64_t s_scan6[33][6];
+    const int64_t i = (int64_t)blockIdx.x * HT + threadIdx.x;
+    int64_t x[6] = {0, 0, 0, 0, 0, 0}, ex[6], tot[6];
+    int32_t v = 0, d = 0;
+    if (i < len) {
+        v = list[i];
+        d = degree_of(off, vgraph, v);
+        hub_shape(d, x);
+    }
+    block_exclusive_scan_k<6>(x, ex, tot, s_scan6);
+    if (i >= len) return;
+    int64_t at[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) at[k] = bstart[(int64_t)blockIdx.x * 6 + k] + ex[k];
+    const bool big = x[0] != 0;
+    HubTask t;
+    t.v = v;
+    t.d = d;
+    t.nseg = (int32_t)x[3];
+    t.npart = (int32_t)x[4];
+    t.seg0 = big ? (int32_t)at[3] : 0;
+    t.part0 = big ? (int32_t)at[4] : 0;
+    t.poff0 = big ? at[5] : 0;
+    t.tab = big ? at[2] : 0;
+    t.e0 = 0;  // set once the rows are packed (hub_task_starts)
+    tasks[big ? at[0] : totals[0] + at[1]] = t;
+}
+
+__global__ void k_hub_task_list(const HubTask *tasks, int64_t len, int32_t *list)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len;
+         i += (int64_t)gridDim.x * blockDim.x)
+        list[i] = tasks[i].v;
+}
+
+// Hub order, counting sort over the classes clz(degree) (degrees >= 1, so
+// the longest rows have the smallest class).  Per block of HT rows, the count
+// of each class: hist[c * nblk + blk].
+__global__ void __launch_bounds__(HT) k_hub_class_count(const int32_t *list, int64_t len,
+                                                         const int32_t *off,
+                                                         const int32_t *vgraph, int32_t *hist)
+{
+    __shared__ int32_t s_cnt[HUB_CLASSES];
+    if (threadIdx.x < HUB_CLASSES) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * HT + threadIdx.x;
+    if (i < len) atomicAdd(&s_cnt[__clz(degree_of(off, vgraph, list[i]))], 1);
+    __syncthreads();
+    if (threadIdx.x < HUB_CLASSES)
+        hist[(int64_t)threadIdx.x * gridDim.x + blockIdx.x] = s_cnt[threadIdx.x];
+}
+
+// Each row to class start + its block's offset within the class + its rank
+// among the block's rows of the class (warp after warp, lane after lane), so
+// the order within a class is the list order.
+__global__ void __launch_bounds__(HT) k_hub_class_scatter(const int32_t *list, int64_t len,
+                                                           const int32_t *off,
+                                                           const int32_t *vgraph,
+                                                           const int32_t *hist,
+                                                           const int64_t *class_begin,
+                                                           int32_t *out)
+{
+    __shared__ int32_t s_wc[HT / 32][HUB_CLASSES + 1];  // per warp and class: count, then position
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t i = (int64_t)blockIdx.x * HT + threadIdx.x;
+    const bool have = i < len;
+    const int32_t v = have ? list[i] : 0;
+    const int c = have ? __clz(degree_of(off, vgraph, v)) : HUB_CLASSES;
+    const unsigned peers = __match_any_sync(FULL, (unsigned)c);
+    const int rank = __popc(peers & ((1u << lane) - 1u));
+    s_wc[wib][lane] = 0;
+    __syncwarp();
+    if (have && rank == 0) s_wc[wib][c] = __popc(peers);
+    __syncthreads();
+    if (threadIdx.x < HUB_CLASSES) {
+        int32_t run = (int32_t)class_begin[threadIdx.x] +
+                      hist[(int64_t)threadIdx.x * gridDim.x + blockIdx.x];
+        for (int w = 0; w < HT / 32; ++w) {
+            const int32_t t = s_wc[w][threadIdx.x];
+            s_wc[w][threadIdx.x] = run;
             run += t;
         }
     }
     __syncthreads();
-    for (int64_t i0 = 0; i0 < len; i0 += 1024) {
-        const int64_t i = i0 + threadIdx.x;
-        const bool have = i < len;
-        const int32_t v = have ? list[i] : 0;
-        const int c = have ? __clz(degree_of(off, vgraph, v)) : 32;
-        const unsigned peers = __match_any_sync(FULL, (unsigned)c);
-        const int rank = __popc(peers & ((1u << lane) - 1u));
-        s_wc[wib][lane] = 0;
-        __syncwarp();
-        if (have && rank == 0) s_wc[wib][c] = __popc(peers);
-        __syncthreads();
-        if (threadIdx.x < 32) {  // positions per class, warp after warp
-            int32_t run = s_start[threadIdx.x];
-            for (int w = 0; w < 32; ++w) {
-                const int32_t t = s_wc[w][threadIdx.x];
-                s_wc[w][threadIdx.x] = run;
-                run += t;
-            }
-            s_start[threadIdx.x] = run;
-        }
-        __syncthreads();
-        if (have) out[s_wc[wib][c] + rank] = v;
-        __syncthreads();
-    }
+    if (have) out[s_wc[wib][c] + rank] = v;
 }
 
 __global__ void k_hub_item_maps(const HubTask *tasks, int64_t nbig, int32_t *seg_task,
@@ -877,20 +923,42 @@ int wave_prepare()
     return 0;
 }
 
-int hub_tasks(int32_t *list, int64_t len, const int32_t *off, const int32_t *vgraph,
-              HubTask *tasks, int64_t *totals, cudaStream_t st, int64_t *launches)
+int64_t hub_scratch_ints(int64_t len)
 {
-    k_hub_tasks<<<1, 1024, 0, st>>>(list, len, off, vgraph, tasks, totals);
-    ++*launches;
+    const int64_t nblk = len > 0 ? (len + HT - 1) / HT : 1;
+    // the order's class counts (int32, HUB_CLASSES per block), class sizes and
+    // starts; the tasks' block sums (6 per block) fit in the same words
+    return HUB_CLASSES / 2 * nblk + 2 * HUB_CLASSES;
+}
+
+int hub_tasks(int32_t *list, int64_t len, const int32_t *off, const int32_t *vgraph,
+              HubTask *tasks, int64_t *totals, int64_t *scratch, cudaStream_t st,
+              int64_t *launches)
+{
+    if (len <= 0)
+        return cudaMemsetAsync(totals, 0, 5 * sizeof(int64_t), st) == cudaSuccess ? 0 : -1;
+    const int64_t nblk = (len + HT - 1) / HT;
+    k_hub_task_sums<<<(int)nblk, HT, 0, st>>>(list, len, off, vgraph, scratch);
+    k_hub_task_scan<<<1, 1024, 0, st>>>(scratch, nblk, totals);
+    k_hub_task_write<<<(int)nblk, HT, 0, st>>>(list, len, off, vgraph, scratch, totals, tasks);
+    k_hub_task_list<<<grid_for(len, 256, 1024), 256, 0, st>>>(tasks, len, list);
+    *launches += 4;
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 int hub_order(const int32_t *list, int64_t len, const int32_t *off, const int32_t *vgraph,
-              int32_t *out, cudaStream_t st, int64_t *launches)
+              int32_t *out, int64_t *scratch, cudaStream_t st, int64_t *launches)
 {
     if (len <= 0) return 0;
-    k_hub_order<<<1, 1024, 0, st>>>(list, len, off, vgraph, out);
-    ++*launches;
+    const int64_t nblk = (len + HT - 1) / HT;
+    int64_t *class_size = scratch, *class_begin = scratch + HUB_CLASSES;
+    int32_t *hist = reinterpret_cast<int32_t *>(scratch + 2 * HUB_CLASSES);
+    k_hub_class_count<<<(int)nblk, HT, 0, st>>>(list, len, off, vgraph, hist);
+    k_class_scan<<<HUB_CLASSES, 1024, 0, st>>>(hist, nblk, class_size);
+    k_class_begin<<<1, 1024, 0, st>>>(class_size, HUB_CLASSES, class_begin);
+    k_hub_class_scatter<<<(int)nblk, HT, 0, st>>>(list, len, off, vgraph, hist, class_begin,
+                                                    out);
+    *launches += 4;
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

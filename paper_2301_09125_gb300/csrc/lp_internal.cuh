@@ -253,16 +253,20 @@ int barrier_probe_launch(unsigned *bar, int32_t *err, uint32_t spin_limit, cudaS
 int small_waves_launch(const SweepArgs &a, const int32_t *wlist, const int64_t *wstart,
                        const int64_t *wcount, int64_t max_len, int32_t max_degree, unsigned *bar,
                        int32_t *err, int num_sms, cudaStream_t st);
+// Device scratch (int64 words) of hub_order and hub_tasks for a list of len
+// rows.
+int64_t hub_scratch_ints(int64_t len);
+// out = the hub rows of list in decreasing order of floor(log2(degree)),
+// stable within a class
+int hub_order(const int32_t *list, int64_t len, const int32_t *off, const int32_t *vgraph,
+              int32_t *out, int64_t *scratch, cudaStream_t st, int64_t *launches);
 // Hub tasks of list[0..len): the rows longer than HUB_ONE_MAX first, then the
 // others, each kind in list order; list is rewritten in the same order so that
 // tasks[i] belongs to list[i].  totals: [0] rows of the first kind, [1] their
 // fallback table slots, [2] segments, [3] partitions, [4] partition offsets.
-// out = the hub rows of list in decreasing order of floor(log2(degree)),
-// stable within a class
-int hub_order(const int32_t *list, int64_t len, const int32_t *off, const int32_t *vgraph,
-              int32_t *out, cudaStream_t st, int64_t *launches);
 int hub_tasks(int32_t *list, int64_t len, const int32_t *off, const int32_t *vgraph,
-              HubTask *tasks, int64_t *totals, cudaStream_t st, int64_t *launches);
+              HubTask *tasks, int64_t *totals, int64_t *scratch, cudaStream_t st,
+              int64_t *launches);
 // tasks[i].e0 = rp[i] for i < n (the packed row start of task i's row).
 int hub_task_starts(HubTask *tasks, int64_t n, const int64_t *rp, cudaStream_t st,
                     int64_t *launches);

@@ -97,14 +97,20 @@ constexpr int MT = 256, MPER = 8;  // threads per block, entries per lane
 constexpr int MW = MT / 32;        // warps (chunks) per block
 static_assert(32 * MPER == PACK_CHUNK, "one warp per packed chunk");
 constexpr int32_t MOD_ID_MASK = 0x7FFFFFFF;  // packed neighbour id without its wave bit
+constexpr int64_t SMALL_BLOCKS = 2048;       // blocks of the small-row pass
+constexpr int64_t ENTRY_BLOCKS = 2048;       // blocks of the entry pass
 
 // Entry pass, one warp per chunk of PACK_CHUNK entries of the packed rows
 // (entries [j_lo, j_lo + PACK_CHUNK), held by the list items r0, holding
 // j_lo, to r1, holding the next chunk's first entry or the last item: at
-// most PACK_CHUNK + 1 rows).  Warps stage their rows independently; the
-// block combines L, 2m and the K part of its first row's community at the end.
+// most PACK_CHUNK + 1 rows).  Warps stage their rows independently.  A block
+// takes groups of MW consecutive chunks in a grid-stride loop (a grid of a
+// few blocks per SM) and combines L, 2m and the K part of its first row's
+// community over all of them, so that these sums, which every block shares
+// (a converged labelling often has a giant community), take one global
+// atomic per block.
 template <bool MULTI>
-__global__ void __launch_bounds__(MT) k_mod_entries(ModArgs a)
+__global__ void __launch_bounds__(MT, MULTI ? 4 : 5) k_mod_entries(ModArgs a)
 {
     constexpr int CH = PACK_CHUNK;
     __shared__ int32_t s_rp_all[MW][CH + 2];   // row starts relative to j_lo
@@ -115,13 +121,29 @@ __global__ void __launch_bounds__(MT) k_mod_entries(ModArgs a)
     __shared__ unsigned long long s_dom;  // K part of the block's first community
     __shared__ int64_t s_dom_slot;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int64_t chunk = a.e_lo / CH + (int64_t)blockIdx.x * MW + wib;
-    const bool have = chunk < a.ncopy;  // warp-uniform
     int32_t *s_rp = s_rp_all[wib];
     int32_t *s_c = s_c_all[wib];
     uint32_t *s_kv = s_kv_all[wib];
     int32_t *s_vb = s_vb_all[MULTI ? wib : 0];
     int32_t *s_g = s_g_all[MULTI ? wib : 0];
+    const int64_t c_lo = a.e_lo / CH;
+    const int64_t groups = (a.ncopy - c_lo + MW - 1) / MW;
+    if (threadIdx.x == 0) {  // the community of the block's first row
+        s_dom = 0ull;
+        s_dom_slot = -1;
+        const int64_t c0 = c_lo + (int64_t)blockIdx.x * MW;
+        if (c0 < a.ncopy) {
+            const int32_t v = a.list[a.first_row[c0]];
+            s_dom_slot = (MULTI ? (int64_t)a.g_vbase[a.vgraph[v]] : 0) + a.lab[v];
+        }
+    }
+    __syncthreads();
+    const int64_t dom = s_dom_slot;
+    unsigned long long l = 0, w2 = 0;
+    AccRun run;
+    for (int64_t grp = blockIdx.x; grp < groups; grp += gridDim.x) {  // block-uniform
+    const int64_t chunk = c_lo + grp * MW + wib;
+    const bool have = chunk < a.ncopy;  // warp-uniform
     const int64_t j_lo = chunk * CH;
     const int rel0 = lane * MPER;
     const int rel_hi = have ? (int)(min(j_lo + (int64_t)CH, a.ne) - j_lo) : 0;
@@ -188,15 +210,7 @@ __global__ void __launch_bounds__(MT) k_mod_entries(ModArgs a)
             s_kv[k] = 0u;
         }
     }
-    if (threadIdx.x == 0) {
-        s_dom = 0ull;
-        s_dom_slot = -1;
-    }
     __syncwarp();
-    if (wib == 0 && lane == 0 && have) s_dom_slot = (MULTI ? (int64_t)s_vb[0] : 0) + s_c[0];
-
-    unsigned long long l = 0, w2 = 0;
-    AccRun run;
     if (rel0 < rel_hi) {
         int lo = 0, hi = nr;  // s_rp[lo] <= rel0 < s_rp[hi]
         while (hi - lo > 1) {
@@ -247,12 +261,12 @@ __global__ void __launch_bounds__(MT) k_mod_entries(ModArgs a)
             atomicAdd(a.acc + 4 * (int64_t)s_g[0], l);
             atomicAdd(a.acc + 4 * (int64_t)s_g[0] + 1, w2);
         }
+        l = w2 = 0;
     }
-    __syncthreads();  // s_kv of every warp complete, s_dom_slot set
+    __syncwarp();  // s_kv of the warp's rows complete
 
     // K: the rows' parts, combined per community within the warp; the block's
     // first community is combined over the block
-    const int64_t dom = s_dom_slot;
     for (int k0 = 0; k0 < nr; k0 += 32) {  // warp-uniform bounds
         const int k = k0 + lane;
         const bool valid = k < nr;
@@ -267,6 +281,8 @@ __global__ void __launch_bounds__(MT) k_mod_entries(ModArgs a)
                 atomicAdd(a.kc + slot, sum);
         }
     }
+    __syncwarp();  // the next group stages over this one's rows
+    }
     if (MULTI)
         run.flush(a.acc);
     else
@@ -278,12 +294,28 @@ __global__ void __launch_bounds__(MT) k_mod_entries(ModArgs a)
 // The rows of the small bucket (the list's first nsmall items, at most 32
 // entries each), one row per lane: its weight k_v and the weight of its
 // entries whose neighbour carries its label; k_v goes to K of its community,
-// combined over the lanes of the same community.
+// combined over the lanes of the same community.  The community of the
+// block's first row is summed in shared memory over every row the block
+// visits (a converged labelling often has a giant community, whose K would
+// otherwise take one global atomic per warp step on a single address).
 template <bool MULTI>
 __global__ void __launch_bounds__(256) k_mod_small(ModArgs a)
 {
+    __shared__ unsigned long long s_dom;  // K part of the block's first community
+    __shared__ int64_t s_dom_slot;
     const int lane = threadIdx.x & 31;
     const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    if (threadIdx.x == 0) {
+        s_dom = 0ull;
+        s_dom_slot = -1;
+        const int64_t i0 = (int64_t)blockIdx.x * blockDim.x;
+        if (i0 < a.nsmall) {
+            const int32_t v = a.list[i0];
+            s_dom_slot = (MULTI ? (int64_t)a.g_vbase[a.vgraph[v]] : 0) + a.lab[v];
+        }
+    }
+    __syncthreads();
+    const int64_t dom = s_dom_slot;
     unsigned long long l = 0, w2 = 0;
     for (int64_t base = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32;
          base < a.nsmall; base += warps * 32) {  // warp-uniform bounds
@@ -325,7 +357,12 @@ __global__ void __launch_bounds__(256) k_mod_small(ModArgs a)
         const int64_t slot0 = __shfl_sync(FULL, slot, 0);
         if (__all_sync(FULL, !valid || slot == slot0)) {
             const unsigned long long sum = group_sum(FULL, kv);
-            if (lane == 0 && sum) atomicAdd(a.kc + slot0, sum);
+            if (lane == 0 && sum) {
+                if (slot0 == dom)
+                    atomicAdd(&s_dom, sum);
+                else
+                    atomicAdd(a.kc + slot0, sum);
+            }
         } else if (valid && kv) {
             atomicAdd(a.kc + slot, (unsigned long long)kv);
         }
@@ -347,6 +384,8 @@ __global__ void __launch_bounds__(256) k_mod_small(ModArgs a)
         }
     }
     if (!MULTI) block_flush_lw(a.acc, l, w2);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_dom) atomicAdd(a.kc + dom, s_dom);
 }
 
 // one graph: 128-bit sums over the warp, then the block, then one add
@@ -415,8 +454,10 @@ int modularity_launch(const ModArgs &a, int64_t nslots, bool multi, cudaStream_t
                       int64_t *launches)
 {
     if (a.nsmall > 0) {
+        // a grid of a few blocks per SM, so that each block's shared sum of
+        // its first community covers many rows
         const int64_t b = (a.nsmall + 255) / 256;
-        const unsigned blocks = (unsigned)(b < 8192 ? b : 8192);
+        const unsigned blocks = (unsigned)(b < SMALL_BLOCKS ? b : SMALL_BLOCKS);
         if (multi)
             k_mod_small<true><<<blocks, 256, 0, st>>>(a);
         else
@@ -425,7 +466,8 @@ int modularity_launch(const ModArgs &a, int64_t nslots, bool multi, cudaStream_t
     }
     const int64_t chunks = a.ncopy - a.e_lo / PACK_CHUNK;  // from the chunk holding e_lo
     if (a.ne > a.e_lo && chunks > 0) {
-        const unsigned blocks = (unsigned)((chunks + MW - 1) / MW);
+        const int64_t groups = (chunks + MW - 1) / MW;
+        const unsigned blocks = (unsigned)(groups < ENTRY_BLOCKS ? groups : ENTRY_BLOCKS);
         if (multi)
             k_mod_entries<true><<<blocks, MT, 0, st>>>(a);
         else
