@@ -1454,14 +1454,27 @@ struct GraphSet {
         return LP_OK;
     }
 
+    // whether a run with these parameters sweeps every wave of an iteration in
+    // one cooperative launch (a single graph, many waves, small rows only),
+    // which a captured run graph cannot hold: the graph would launch every
+    // wave on its own (measured 25 % slower on 127 waves of k-mer paths)
+    bool all_waves_run(const lp_rak_params *p, bool multi) const
+    {
+        if (!p || multi || p->mode != LP_ASYNC) return false;
+        const int32_t waves = std::min(p->waves, std::max(max_n, 1));
+        return waves >= COOP_MIN_WAVES && bl[0] > 0 &&
+               bl[1] + bl[2] + bl[3] + bl[HUB_BUCKET] == 0;
+    }
+
     // Sec. 3.2 iteration over every graph of the set, to the end: one graph
-    // launch, or (while per-launch profiling is on) one host round trip per
-    // iteration with events around every sweep launch
+    // launch, or (while per-launch profiling is on, or for all-waves runs)
+    // launches from the host
     lp_status run(const lp_rak_params *p, bool multi)
     {
         // capturing a run costs about as much as a run of a mid-size graph, so
         // a graph is captured once the same parameters come back
-        if (!g_prof_on.load() && repeat_key(p, multi)) return run_graph(p, multi);
+        if (!g_prof_on.load() && !all_waves_run(p, multi) && repeat_key(p, multi))
+            return run_graph(p, multi);
         return run_host(p, multi);
     }
 

@@ -572,6 +572,17 @@ def test_graph_launch_and_host_loop_agree(lp):
                              G.labels().tolist()))
             assert all(x == runs[0] for x in runs), kw
 
+    # many waves over small rows: repeated runs stay on the host-launched
+    # all-waves sweep (no captured graph) and repeat the oracle's result
+    g = gg.kmer_like(60_000, seed=9)
+    ref, iters, _, hist = oracle.rak(g.offsets, g.indices, g.weights, 0.05, 20, "async",
+                                     seed=4, waves=31)
+    with lp.Graph(g.offsets, g.indices, g.weights) as G:
+        for _ in range(3):
+            r = G.rak(tolerance=0.05, max_iter=20, mode="async", waves=31, seed=4)
+            assert r.iterations == iters and np.array_equal(G.history(), hist)
+            assert np.array_equal(G.labels(), ref)
+
 
 @pytest.mark.parametrize("bounds", [(8, 64, 256, 1024), (16, 128, 512, 1024), (1, 1, 1, 1),
                                     (32, 32, 129, 513)])
