@@ -18,9 +18,46 @@ namespace {
 
 constexpr int BK = 1024;  // threads per bucketing block
 
+// The counting passes (buckets, wave classes, packed row starts) take their
+// items in tiles of 1024, each block a run of `per` consecutive tiles, with
+// at most TILE_BLOCKS blocks: a few waves of blocks that loop over several
+// tiles, rather than one short block per tile (which left these passes
+// bound by block scheduling on graphs of millions of vertices).  Per-block
+// counts are scanned over the blocks in order, so positions follow the
+// items' order as with one block per tile.
+constexpr int64_t TILE_BLOCKS = 1024;
+// the packing's row-start pass does more per tile (six loads, a block scan,
+// three stores): more blocks of fewer tiles each
+constexpr int64_t PACK_TILE_BLOCKS = 4096;
+struct TileGrid {
+    int64_t ntiles, per, nblk;
+};
+inline TileGrid tile_grid(int64_t items, int64_t max_blocks = TILE_BLOCKS)
+{
+    TileGrid t;
+    t.ntiles = items > 0 ? (items + BK - 1) / BK : 0;
+    t.per = t.ntiles > max_blocks ? (t.ntiles + max_blocks - 1) / max_blocks : 1;
+    t.nblk = (t.ntiles + t.per - 1) / t.per;
+    return t;
+}
+
 __device__ __forceinline__ void report(IngestOut *o, int32_t code, int64_t at)
 {
     if (atomicCAS(&o->err, 0, code) == 0) o->err_at = (int32_t)(at > 2147483647 ? 2147483647 : at);
+}
+
+// The largest of every thread's x into *dst with one global atomic per block
+// (a per-warp atomic on one address from every warp of a large grid
+// serialises in L2); every thread of the block calls this.
+__device__ __forceinline__ void block_max_into(int32_t *dst, int32_t x)
+{
+    __shared__ int32_t s_max;
+    if (threadIdx.x == 0) s_max = 0;
+    __syncthreads();
+    x = (int32_t)__reduce_max_sync(FULL, (uint32_t)(x > 0 ? x : 0));
+    if ((threadIdx.x & 31) == 0 && x) atomicMax(&s_max, x);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_max) atomicMax(dst, s_max);
 }
 
 __global__ void k_val_offsets(const int32_t *off, int32_t n, int64_t m, IngestOut *o)
@@ -39,8 +76,7 @@ __global__ void k_val_offsets(const int32_t *off, int32_t n, int64_t m, IngestOu
                 local_max = max(local_max, y - x);
         }
     }
-    local_max = (int32_t)__reduce_max_sync(FULL, (uint32_t)local_max);
-    if ((threadIdx.x & 31) == 0 && local_max) atomicMax(&o->max_deg, local_max);
+    block_max_into(&o->max_deg, local_max);
 }
 
 __global__ void k_val_entries(const int32_t *idx, const int32_t *wts, int32_t n, int64_t m,
@@ -60,8 +96,7 @@ __global__ void k_val_entries(const int32_t *idx, const int32_t *wts, int32_t n,
         }
     }
     if (!wts) wmax = m > 0 ? 1 : 0;
-    wmax = (int32_t)__reduce_max_sync(FULL, (uint32_t)wmax);
-    if ((threadIdx.x & 31) == 0 && wmax) atomicMax(&o->max_w, wmax);
+    block_max_into(&o->max_w, wmax);
 }
 
 __global__ void k_val_wdeg(const int32_t *off, const int32_t *wts, int32_t n, IngestOut *o)
@@ -144,9 +179,8 @@ __global__ void k_val_entries4(const int32_t *idx, const int32_t *wts, int32_t n
             }
         }
     }
-    wmax = (int32_t)__reduce_max_sync(FULL, (uint32_t)wmax);
-    if ((threadIdx.x & 31) == 0 && wmax) atomicMax(&o->max_w, wmax);
     if (__any_sync(FULL, unordered) && (threadIdx.x & 31) == 0) atomicExch(&o->repeated, 1);
+    block_max_into(&o->max_w, wmax);
 }
 
 // entries e, e+1 of one row must satisfy idx[e] < idx[e+1]
@@ -180,43 +214,57 @@ __device__ __forceinline__ int32_t degree_of(const int32_t *off, const int32_t *
     return off[(int64_t)v + g + 1] - off[(int64_t)v + g];
 }
 
-// Per block of BK vertices: its row count (blk) and entry count (bent) in
-// every bucket, stored per bucket and block (the class scan sums them, so no
-// global atomic is shared by the blocks).
+// Per block (a run of `per` tiles of BK vertices): its row count (blk) and
+// entry count (bent) in every bucket, stored per bucket and block (the class
+// scan sums them, so no global atomic is shared by the blocks).  Each thread
+// counts in registers; the block adds its warps' sums once at the end.
 __global__ void __launch_bounds__(BK) k_bucket_count(const int32_t *off, int32_t nv,
                                                       const int32_t *vgraph, Thresholds th,
-                                                      int32_t *blk, int64_t *bent)
+                                                      int64_t per, int32_t *blk, int64_t *bent)
 {
-    __shared__ int cnt[NUM_BUCKETS];
-    __shared__ uint32_t ent[NUM_BUCKETS - 1];  // < BK * 1024: 32 bits suffice
-    __shared__ unsigned long long ent_last;
-    if (threadIdx.x < NUM_BUCKETS) cnt[threadIdx.x] = 0;
-    if (threadIdx.x < NUM_BUCKETS - 1) ent[threadIdx.x] = 0u;
-    if (threadIdx.x == 0) ent_last = 0ull;
-    __syncthreads();
-    const int64_t v = (int64_t)blockIdx.x * BK + threadIdx.x;
-    const int32_t d = v < nv ? degree_of(off, vgraph, (int32_t)v) : 0;
-    const int b = bucket_of(d, th);
-    // one shared atomic per warp and bucket (rows of every bucket but the last
-    // are short enough for a 32-bit warp sum)
+    __shared__ unsigned long long s_c[BK / 32][NUM_BUCKETS], s_e[BK / 32][NUM_BUCKETS];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    uint32_t cnt[NUM_BUCKETS];
+    unsigned long long ent[NUM_BUCKETS];
 #pragma unroll
-    for (int c = 0; c < NUM_BUCKETS - 1; ++c) {
-        const unsigned mask = __ballot_sync(FULL, b == c);
-        const uint32_t sum = __reduce_add_sync(FULL, b == c ? (uint32_t)d : 0u);
-        if ((threadIdx.x & 31) == 0 && mask) {
-            atomicAdd(&cnt[c], __popc(mask));
-            atomicAdd(&ent[c], sum);
-        }
+    for (int c = 0; c < NUM_BUCKETS; ++c) {
+        cnt[c] = 0u;
+        ent[c] = 0ull;
     }
-    if (b == NUM_BUCKETS - 1) {
-        atomicAdd(&cnt[b], 1);
-        atomicAdd(&ent_last, (unsigned long long)d);
+    const int64_t t_lo = (int64_t)blockIdx.x * per;
+    for (int64_t t = t_lo; t < t_lo + per; ++t) {
+        const int64_t v = t * BK + threadIdx.x;
+        if (v >= nv) break;
+        const int32_t d = degree_of(off, vgraph, (int32_t)v);
+        const int b = bucket_of(d, th);
+#pragma unroll
+        for (int c = 0; c < NUM_BUCKETS; ++c)
+            if (b == c) {
+                ++cnt[c];
+                ent[c] += (unsigned long long)d;
+            }
+    }
+#pragma unroll
+    for (int c = 0; c < NUM_BUCKETS; ++c) {
+        const uint32_t wc = __reduce_add_sync(FULL, cnt[c]);
+        unsigned long long we = ent[c];
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) we += __shfl_xor_sync(FULL, we, o);
+        if (lane == 0) {
+            s_c[wib][c] = wc;
+            s_e[wib][c] = we;
+        }
     }
     __syncthreads();
     if (threadIdx.x < NUM_BUCKETS) {
+        unsigned long long tc = 0ull, te = 0ull;
+        for (int w = 0; w < BK / 32; ++w) {
+            tc += s_c[w][threadIdx.x];
+            te += s_e[w][threadIdx.x];
+        }
         const int64_t at = (int64_t)threadIdx.x * gridDim.x + blockIdx.x;
-        blk[at] = cnt[threadIdx.x];
-        bent[at] = threadIdx.x < NUM_BUCKETS - 1 ? (int64_t)ent[threadIdx.x] : (int64_t)ent_last;
+        blk[at] = (int32_t)tc;
+        bent[at] = (int64_t)te;
     }
 }
 
@@ -343,35 +391,50 @@ __global__ void __launch_bounds__(1024) k_class_begin(const int64_t *class_size,
     }
 }
 
+// Every vertex of the block's tiles to its bucket's list, in vertex order:
+// bucket start + the block's offset within the bucket + the rows of earlier
+// tiles of the block + the rank within the tile (warp after warp, lane after
+// lane).
 __global__ void __launch_bounds__(BK) k_bucket_scatter(const int32_t *off, int32_t nv,
                                                         const int32_t *vgraph, Thresholds th,
-                                                        const int32_t *blk, const int64_t *cnt,
-                                                        int32_t *list)
+                                                        int64_t per, const int32_t *blk,
+                                                        const int64_t *cnt, int32_t *list)
 {
     __shared__ int s_pre[NUM_BUCKETS][BK / 32];
+    __shared__ int64_t s_base[NUM_BUCKETS];
+    __shared__ int s_tile[NUM_BUCKETS];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int64_t v = (int64_t)blockIdx.x * BK + threadIdx.x;
-    const int b = v < nv ? bucket_of(degree_of(off, vgraph, (int32_t)v), th) : -1;
-    int rank = 0;
+    if (threadIdx.x < NUM_BUCKETS)
+        s_base[threadIdx.x] =
+            cnt[NUM_BUCKETS + threadIdx.x] + blk[(int64_t)threadIdx.x * gridDim.x + blockIdx.x];
+    const int64_t t_lo = (int64_t)blockIdx.x * per;
+    for (int64_t t = t_lo; t < t_lo + per && t * BK < nv; ++t) {  // block-uniform
+        const int64_t v = t * BK + threadIdx.x;
+        const int b = v < nv ? bucket_of(degree_of(off, vgraph, (int32_t)v), th) : -1;
+        int rank = 0;
 #pragma unroll
-    for (int c = 0; c < NUM_BUCKETS; ++c) {
-        const unsigned msk = __ballot_sync(FULL, b == c);
-        if (b == c) rank = __popc(msk & ((1u << lane) - 1u));
-        if (lane == 0) s_pre[c][wib] = __popc(msk);
-    }
-    __syncthreads();
-    if (threadIdx.x < NUM_BUCKETS) {
-        int acc = 0;
-        for (int w = 0; w < BK / 32; ++w) {
-            const int t = s_pre[threadIdx.x][w];
-            s_pre[threadIdx.x][w] = acc;
-            acc += t;
+        for (int c = 0; c < NUM_BUCKETS; ++c) {
+            const unsigned msk = __ballot_sync(FULL, b == c);
+            if (b == c) rank = __popc(msk & ((1u << lane) - 1u));
+            if (lane == 0) s_pre[c][wib] = __popc(msk);
         }
+        __syncthreads();  // s_pre of every warp (and s_base) written
+        if (wib < NUM_BUCKETS) {  // warp c scans bucket c's 32 warp counts
+            const int x = s_pre[wib][lane];
+            int inc = x;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(FULL, inc, o);
+                if (lane >= o) inc += y;
+            }
+            s_pre[wib][lane] = inc - x;
+            if (lane == 31) s_tile[wib] = inc;
+        }
+        __syncthreads();
+        if (b >= 0) list[s_base[b] + s_pre[b][wib] + rank] = (int32_t)v;
+        __syncthreads();  // every read of s_pre and s_base done
+        if (threadIdx.x < NUM_BUCKETS) s_base[threadIdx.x] += s_tile[threadIdx.x];
     }
-    __syncthreads();
-    if (b >= 0)
-        list[cnt[NUM_BUCKETS + b] + blk[(int64_t)b * gridDim.x + blockIdx.x] + s_pre[b][wib] + rank] =
-            (int32_t)v;
 }
 
 __global__ void k_iota(int32_t *lab, int32_t nv, const int32_t *vgraph, const int32_t *g_vbase)
@@ -589,62 +652,73 @@ __global__ void k_hub_task_starts(HubTask *tasks, int64_t n, const int64_t *rp)
 // ---------------------------------------------------------------------------
 // packed rows: the rows of a list copied in list order
 // ---------------------------------------------------------------------------
-constexpr int PK_SCAN = 1024;            // list items per scan block
+constexpr int PK_SCAN = 1024;            // list items per scan tile
+static_assert(PK_SCAN == BK, "the packing scans' tiles are the tile grid's");
 constexpr int PK_T = 256, PK_PER = 8;    // copy: threads per block, entries per thread
 constexpr int PK_OUT = 32 * PK_PER;      // entries per warp chunk
 constexpr int PK_WARPS = PK_T / 32;
 static_assert(PK_OUT == PACK_CHUNK, "copy chunks are the modularity pass's chunks");
 
-// summed degree of each block of PK_SCAN list items
+// summed degree of the list items of each block (a run of `per` tiles)
 __global__ void __launch_bounds__(PK_SCAN) k_pack_sum(const int32_t *list, int64_t len,
                                                       const int32_t *off, const int32_t *vgraph,
-                                                      int64_t *bsum)
+                                                      int64_t per, int64_t *bsum)
 {
     __shared__ int64_t s_warp[33];
-    const int64_t i = (int64_t)blockIdx.x * PK_SCAN + threadIdx.x;
-    const int64_t d = i < len ? degree_of(off, vgraph, list[i]) : 0;
+    int64_t d = 0;
+    const int64_t t_lo = (int64_t)blockIdx.x * per;
+    for (int64_t t = t_lo; t < t_lo + per; ++t) {
+        const int64_t i = t * PK_SCAN + threadIdx.x;
+        if (i >= len) break;
+        d += degree_of(off, vgraph, list[i]);
+    }
     int64_t tot;
     block_exclusive_scan(d, s_warp, &tot);
     if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
 }
 
-// rp[i] = block start + prefix of the degrees within the block; rp[len] =
-// total; srcw[i] = the row's start in the original CSR | its wave class << 48.
-// Every listed row has at least one entry, so each copy block's first entry
-// (a multiple of PK_OUT) lies in exactly one row: that row records itself as
-// the block's first row (first_row[ncopy] = the last row).
+// rp[i] = block start + prefix of the degrees within the block (tile after
+// tile); rp[len] = total; srcw[i] = the row's start in the original CSR | its
+// wave class << 48.  Every listed row has at least one entry, so each copy
+// block's first entry (a multiple of PK_OUT) lies in exactly one row: that row
+// records itself as the block's first row (first_row[ncopy] = the last row).
 __global__ void __launch_bounds__(PK_SCAN) k_pack_rp(const int32_t *list, int64_t len,
                                                      const int32_t *off, const int32_t *vgraph,
                                                      const int32_t *g_vbase, const int64_t *g_ebase,
-                                                     uint32_t waves, uint64_t magic,
+                                                     uint32_t waves, uint64_t magic, int64_t per,
                                                      const int64_t *bstart, int64_t *rp,
                                                      int64_t *srcw, int64_t *first_row,
                                                      int64_t ncopy)
 {
     __shared__ int64_t s_warp[33];
-    const int64_t i = (int64_t)blockIdx.x * PK_SCAN + threadIdx.x;
-    int64_t d = 0, src = 0;
-    uint32_t wv = 0;
-    if (i < len) {
-        const int32_t v = list[i];
-        const int32_t g = vgraph ? vgraph[v] : 0;
-        const int32_t rs = off[(int64_t)v + g];
-        d = off[(int64_t)v + g + 1] - rs;
-        src = (g_ebase ? g_ebase[g] : 0) + rs;
-        const int32_t lv = v - (vgraph ? g_vbase[g] : 0);
-        wv = waves > 1 ? fastmod((uint32_t)lv, magic, waves) : 0u;
-    }
-    int64_t tot;
-    const int64_t ex = block_exclusive_scan(d, s_warp, &tot);
-    if (i < len) {
-        const int64_t start = bstart[blockIdx.x] + ex, end = start + d;
-        rp[i] = start;
-        srcw[i] = src | ((int64_t)wv << 48);
-        for (int64_t c = (start + PK_OUT - 1) / PK_OUT; c * PK_OUT < end; ++c) first_row[c] = i;
-        if (i == len - 1) {
-            rp[len] = end;
-            first_row[ncopy] = i;
+    int64_t run = bstart[blockIdx.x];
+    const int64_t t_lo = (int64_t)blockIdx.x * per;
+    for (int64_t t = t_lo; t < t_lo + per && t * PK_SCAN < len; ++t) {  // block-uniform
+        const int64_t i = t * PK_SCAN + threadIdx.x;
+        int64_t d = 0, src = 0;
+        uint32_t wv = 0;
+        if (i < len) {
+            const int32_t v = list[i];
+            const int32_t g = vgraph ? vgraph[v] : 0;
+            const int32_t rs = off[(int64_t)v + g];
+            d = off[(int64_t)v + g + 1] - rs;
+            src = (g_ebase ? g_ebase[g] : 0) + rs;
+            const int32_t lv = v - (vgraph ? g_vbase[g] : 0);
+            wv = waves > 1 ? fastmod((uint32_t)lv, magic, waves) : 0u;
         }
+        int64_t tot;
+        const int64_t ex = block_exclusive_scan(d, s_warp, &tot);
+        if (i < len) {
+            const int64_t start = run + ex, end = start + d;
+            rp[i] = start;
+            srcw[i] = src | ((int64_t)wv << 48);
+            for (int64_t c = (start + PK_OUT - 1) / PK_OUT; c * PK_OUT < end; ++c) first_row[c] = i;
+            if (i == len - 1) {
+                rp[len] = end;
+                first_row[ncopy] = i;
+            }
+        }
+        run += tot;
     }
 }
 
@@ -735,7 +809,8 @@ __global__ void __launch_bounds__(PK_T) k_pack_rows(const int64_t *rp, const int
 // ---------------------------------------------------------------------------
 // wave partition (asynchronous mode)
 // ---------------------------------------------------------------------------
-constexpr int WV = 1024;  // list entries per block
+constexpr int WV = 1024;  // list entries per block tile
+static_assert(WV == BK, "the wave partition's tiles are the tile grid's");
 
 __device__ __forceinline__ int wave_class(const int32_t *list, int64_t i, const int64_t *bb,
                                           const int32_t *vgraph, const int32_t *g_vbase,
@@ -756,34 +831,53 @@ struct WaveParams {
     uint64_t magic;
 };
 
+// Per block (a run of `per` tiles of WV list items): the count of every
+// class, one shared atomic per class present in a warp.
 __global__ void __launch_bounds__(WV) k_wave_hist(const int32_t *list, int64_t len, WaveParams p,
-                                                   const int32_t *vgraph, const int32_t *g_vbase,
-                                                   int32_t *hist)
+                                                   int64_t per, const int32_t *vgraph,
+                                                   const int32_t *g_vbase, int32_t *hist)
 {
     extern __shared__ int32_t s_cnt[];  // NUM_BUCKETS * waves
+    const int lane = threadIdx.x & 31;
     const int nc = NUM_BUCKETS * (int)p.waves;
     for (int c = threadIdx.x; c < nc; c += WV) s_cnt[c] = 0;
     __syncthreads();
-    const int64_t i = (int64_t)blockIdx.x * WV + threadIdx.x;
-    if (i < len) atomicAdd(&s_cnt[wave_class(list, i, p.bb, vgraph, g_vbase, p.waves, p.magic)], 1);
+    const int64_t t_lo = (int64_t)blockIdx.x * per;
+    for (int64_t t = t_lo; t < t_lo + per && t * WV < len; ++t) {  // block-uniform
+        const int64_t i = t * WV + threadIdx.x;
+        const int c = i < len ? wave_class(list, i, p.bb, vgraph, g_vbase, p.waves, p.magic) : -1;
+        const unsigned peers = __match_any_sync(FULL, (unsigned)c);
+        if (c >= 0 && lane == __ffs(peers) - 1) atomicAdd(&s_cnt[c], __popc(peers));
+    }
     __syncthreads();
     for (int c = threadIdx.x; c < nc; c += WV) hist[(int64_t)c * gridDim.x + blockIdx.x] = s_cnt[c];
 }
 
+// Every item of the block's tiles to its class: class start + the block's
+// offset within the class + a position taken by its warp's leader for the
+// warp's items of the class (in lane order within the warp).
 __global__ void __launch_bounds__(WV) k_wave_scatter(const int32_t *list, int64_t len,
-                                                      WaveParams p, const int32_t *vgraph,
+                                                      WaveParams p, int64_t per,
+                                                      const int32_t *vgraph,
                                                       const int32_t *g_vbase, const int32_t *hist,
                                                       const int64_t *class_begin, int32_t *out)
 {
     extern __shared__ int32_t s_cur[];
+    const int lane = threadIdx.x & 31;
     const int nc = NUM_BUCKETS * (int)p.waves;
     for (int c = threadIdx.x; c < nc; c += WV)
         s_cur[c] = (int32_t)class_begin[c] + hist[(int64_t)c * gridDim.x + blockIdx.x];
     __syncthreads();
-    const int64_t i = (int64_t)blockIdx.x * WV + threadIdx.x;
-    if (i < len) {
-        const int c = wave_class(list, i, p.bb, vgraph, g_vbase, p.waves, p.magic);
-        out[atomicAdd(&s_cur[c], 1)] = list[i];
+    const int64_t t_lo = (int64_t)blockIdx.x * per;
+    for (int64_t t = t_lo; t < t_lo + per && t * WV < len; ++t) {  // block-uniform
+        const int64_t i = t * WV + threadIdx.x;
+        const int c = i < len ? wave_class(list, i, p.bb, vgraph, g_vbase, p.waves, p.magic) : -1;
+        const unsigned peers = __match_any_sync(FULL, (unsigned)c);
+        const int leader = __ffs(peers) - 1;
+        int base = 0;
+        if (c >= 0 && lane == leader) base = atomicAdd(&s_cur[c], __popc(peers));
+        base = __shfl_sync(FULL, base, leader);
+        if (c >= 0) out[base + __popc(peers & ((1u << lane) - 1u))] = list[i];
     }
 }
 
@@ -856,7 +950,7 @@ static int64_t bucket_count_words(int64_t nblk) { return (nblk * NUM_BUCKETS + 1
 
 size_t ingest_bucket_scratch_bytes(int32_t nv_total)
 {
-    int64_t nblk = ((int64_t)nv_total + BK - 1) / BK;
+    int64_t nblk = tile_grid(nv_total).nblk;
     if (nblk < 1) nblk = 1;
     return (size_t)bucket_count_words(nblk) * sizeof(int32_t) +
            (size_t)nblk * NUM_BUCKETS * sizeof(int64_t);
@@ -866,16 +960,17 @@ int ingest_bucket(const int32_t *off, int32_t nv, const int32_t *vgraph, const i
                   const Thresholds &th, int32_t *list, int32_t *blk, int64_t *d_counts,
                   cudaStream_t st, int64_t *launches)
 {
-    const int64_t nblk = ((int64_t)nv + BK - 1) / BK;
+    const TileGrid tg = tile_grid(nv);
+    const int64_t nblk = tg.nblk;
     if (cudaMemsetAsync(d_counts, 0, 3 * NUM_BUCKETS * sizeof(int64_t), st) != cudaSuccess)
         return -1;
     if (nblk == 0) return 0;
     int64_t *bent = reinterpret_cast<int64_t *>(blk + bucket_count_words(nblk));
-    k_bucket_count<<<(int)nblk, BK, 0, st>>>(off, nv, vgraph, th, blk, bent);
+    k_bucket_count<<<(int)nblk, BK, 0, st>>>(off, nv, vgraph, th, tg.per, blk, bent);
     k_bucket_entries<<<NUM_BUCKETS, 1024, 0, st>>>(bent, nblk, d_counts + 2 * NUM_BUCKETS);
     k_class_scan<<<NUM_BUCKETS, 1024, 0, st>>>(blk, nblk, d_counts);
     k_class_begin<<<1, 1024, 0, st>>>(d_counts, NUM_BUCKETS, d_counts + NUM_BUCKETS);
-    k_bucket_scatter<<<(int)nblk, BK, 0, st>>>(off, nv, vgraph, th, blk, d_counts, list);
+    k_bucket_scatter<<<(int)nblk, BK, 0, st>>>(off, nv, vgraph, th, tg.per, blk, d_counts, list);
     *launches += 5;
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
@@ -883,7 +978,7 @@ int ingest_bucket(const int32_t *off, int32_t nv, const int32_t *vgraph, const i
 // class starts (int64, first) and per-block class counts
 int64_t wave_hist_ints(int64_t list_len, int waves)
 {
-    const int64_t nblk = (list_len + WV - 1) / WV;
+    const int64_t nblk = tile_grid(list_len).nblk;
     return ((nblk > 0 ? nblk : 1) + 2) * NUM_BUCKETS * (int64_t)waves;
 }
 
@@ -899,14 +994,15 @@ int wave_partition(const int32_t *list, int64_t len, const int64_t *bucket_begin
     for (int c = 0; c < NUM_BUCKETS; ++c) p.bb[c] = bucket_begin[c];
     p.waves = (uint32_t)waves;
     p.magic = fastmod_magic((uint32_t)waves);
-    const int64_t nblk = (len + WV - 1) / WV;
+    const TileGrid tg = tile_grid(len);
+    const int64_t nblk = tg.nblk;
     const size_t smem = (size_t)nc * sizeof(int32_t);
     int64_t *class_begin = reinterpret_cast<int64_t *>(hist);
     int32_t *counts = hist + 2 * (int64_t)nc;
-    k_wave_hist<<<(int)nblk, WV, smem, st>>>(list, len, p, vgraph, g_vbase, counts);
+    k_wave_hist<<<(int)nblk, WV, smem, st>>>(list, len, p, tg.per, vgraph, g_vbase, counts);
     k_class_scan<<<nc, 1024, 0, st>>>(counts, nblk, d_totals);
     k_class_begin<<<1, 1024, 0, st>>>(d_totals, nc, class_begin);
-    k_wave_scatter<<<(int)nblk, WV, smem, st>>>(list, len, p, vgraph, g_vbase, counts,
+    k_wave_scatter<<<(int)nblk, WV, smem, st>>>(list, len, p, tg.per, vgraph, g_vbase, counts,
                                                 class_begin, out);
     *launches += 4;
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
@@ -973,7 +1069,7 @@ int hub_task_starts(HubTask *tasks, int64_t n, const int64_t *rp, cudaStream_t s
 
 int64_t pack_scratch_ints(int64_t len)
 {
-    const int64_t nblk = (len + PK_SCAN - 1) / PK_SCAN;
+    const int64_t nblk = tile_grid(len, PACK_TILE_BLOCKS).nblk;
     return 2 * (nblk > 0 ? nblk : 1) + len;
 }
 
@@ -985,15 +1081,16 @@ int pack_rows(const int32_t *list, int64_t len, const int32_t *off, const int32_
 {
     if (waves < 1) return -1;
     if (len == 0) return cudaMemsetAsync(rp, 0, sizeof(int64_t), st) == cudaSuccess ? 0 : -1;
-    const int64_t nblk = (len + PK_SCAN - 1) / PK_SCAN;
+    const TileGrid tg = tile_grid(len, PACK_TILE_BLOCKS);
+    const int64_t nblk = tg.nblk;
     const int64_t ncopy = (ne + PK_OUT - 1) / PK_OUT;
     int64_t *bsum = scratch, *bstart = scratch + nblk, *srcw = scratch + 2 * nblk;
     const uint64_t magic = fastmod_magic((uint32_t)waves);
-    k_pack_sum<<<(int)nblk, PK_SCAN, 0, st>>>(list, len, off, vgraph, bsum);
+    k_pack_sum<<<(int)nblk, PK_SCAN, 0, st>>>(list, len, off, vgraph, tg.per, bsum);
     k_class_begin<<<1, 1024, 0, st>>>(bsum, nblk, bstart);
     k_pack_rp<<<(int)nblk, PK_SCAN, 0, st>>>(list, len, off, vgraph, g_vbase, g_ebase,
-                                              (uint32_t)waves, magic, bstart, rp, srcw, first_row,
-                                              ncopy);
+                                              (uint32_t)waves, magic, tg.per, bstart, rp, srcw,
+                                              first_row, ncopy);
     *launches += 3;
     if (ne > 0) {
         PackOrder order{};
