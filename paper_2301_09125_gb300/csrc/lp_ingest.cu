@@ -753,19 +753,24 @@ __device__ __forceinline__ int64_t pack_chunk_of(const PackOrder &o, int64_t t)
     return c < o.c0[b + 1] ? c : -1;
 }
 
-__global__ void __launch_bounds__(PK_T) k_pack_rows(const int64_t *rp, const int64_t *srcw,
-                                                    const int64_t *first_row, int64_t ncopy,
-                                                    const int32_t *idx, const int32_t *wts,
-                                                    int64_t ne, uint32_t waves, uint64_t magic,
-                                                    PackOrder order, int32_t *pidx, int32_t *pwts)
+// (row starts are kept relative to the chunk's first entry in 32 bits, so
+// that seven blocks fit an SM: a row's start lies at most its length, under
+// 2^31, before the chunk; the start after the chunk's last row, which only
+// bounds it, is clamped)
+__global__ void __launch_bounds__(PK_T, 7) k_pack_rows(const int64_t *rp, const int64_t *srcw,
+                                                       const int64_t *first_row, int64_t ncopy,
+                                                       const int32_t *idx, const int32_t *wts,
+                                                       int64_t ne, uint32_t waves, uint64_t magic,
+                                                       PackOrder order, int32_t *pidx,
+                                                       int32_t *pwts)
 {
-    __shared__ int64_t s_rp_all[PK_WARPS][PK_OUT + 2];
+    __shared__ int32_t s_rp_all[PK_WARPS][PK_OUT + 2];
     __shared__ int64_t s_src_all[PK_WARPS][PK_OUT + 1];
     __shared__ uint16_t s_row_all[PK_WARPS][PK_OUT];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int64_t chunk = pack_chunk_of(order, (int64_t)blockIdx.x * PK_WARPS + wib);
     if (chunk < 0 || chunk >= ncopy) return;  // warp-uniform
-    int64_t *s_rp = s_rp_all[wib];
+    int32_t *s_rp = s_rp_all[wib];
     int64_t *s_src = s_src_all[wib];
     uint16_t *s_row = s_row_all[wib];
     const int64_t j_lo = chunk * PK_OUT;
@@ -773,34 +778,34 @@ __global__ void __launch_bounds__(PK_T) k_pack_rows(const int64_t *rp, const int
     const int64_t r0 = first_row[chunk];
     const int64_t r1 = first_row[chunk + 1];
     const int nr = (int)min(r1 - r0 + 1, (int64_t)PK_OUT + 1);
-    for (int k = lane; k <= nr; k += 32) s_rp[k] = rp[r0 + k];
+    for (int k = lane; k <= nr; k += 32)
+        s_rp[k] = (int32_t)min(rp[r0 + k] - j_lo, (int64_t)INT32_MAX);
     for (int k = lane; k < nr; k += 32) s_src[k] = srcw[r0 + k];
     __syncwarp();
-    chunk_rows([&](int k) { return (int)(s_rp[k] - j_lo); }, nr, s_row);
+    chunk_rows([&](int k) { return s_rp[k]; }, nr, s_row);
     int32_t c[PK_PER], w[PK_PER];
-    uint32_t wv[PK_PER];
 #pragma unroll
     for (int q = 0; q < PK_PER; ++q) {  // every load in flight before any use
         const int e = lane + 32 * q;
         const int64_t j = j_lo + e;
         c[q] = w[q] = 0;
-        wv[q] = 0u;
         if (j < j_hi) {
             const int k = s_row[e];
-            const int64_t sw = s_src[k];
-            const int64_t src = (sw & 0xFFFFFFFFFFFFll) + (j - s_rp[k]);
-            wv[q] = (uint32_t)(sw >> 48);
+            const int64_t src = (s_src[k] & 0xFFFFFFFFFFFFll) + (e - s_rp[k]);
             c[q] = __ldg(idx + src);
             if (wts) w[q] = __ldg(wts + src);
         }
     }
 #pragma unroll
     for (int q = 0; q < PK_PER; ++q) {
-        const int64_t j = j_lo + lane + 32 * q;
+        const int e = lane + 32 * q;
+        const int64_t j = j_lo + e;
         if (j >= j_hi) continue;
         int32_t u = c[q];
-        if (waves > 1 && fastmod((uint32_t)u, magic, waves) < wv[q])
-            u = (int32_t)((uint32_t)u | 0x80000000u);
+        if (waves > 1) {  // the row's wave class, read again from shared memory
+            const uint32_t wv = (uint32_t)(s_src[s_row[e]] >> 48);
+            if (fastmod((uint32_t)u, magic, waves) < wv) u = (int32_t)((uint32_t)u | 0x80000000u);
+        }
         pidx[j] = u;
         if (wts) pwts[j] = w[q];
     }
