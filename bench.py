@@ -335,8 +335,9 @@ def run_reference(args):
     oracle.build()
     mode = p["mode"]
     waves = p["waves"] if mode == "async" else 0
-    # one step = `sweeps` oracle sweeps from unique labels (bounded sample)
-    sweeps = max(1, args.cpu_sweeps // 2)
+    # one step = `sweeps` oracle sweeps from unique labels (bounded sample:
+    # about 60 sweeps over the whole run, so that it ends within minutes)
+    sweeps = max(1, min(args.cpu_sweeps // 2, 60 // max(1, args.steps + args.warmup)))
 
     def step():
         t0 = time.perf_counter()
