@@ -138,7 +138,12 @@ lp_status lp_graph_info(const lp_graph *g, int32_t *n, int64_t *m);
 
 /* Run RAK to convergence (Sec. 3.2; asynchronous variant Sec. 3.3).
  * The result labels stay on the device (lp_labels_get, lp_modularity).
- * Returns after the run has finished on the device.
+ * Returns after the run has finished on the device.  A run that repeats the
+ * previous run's parameters on the same graph is captured once as a CUDA
+ * graph (on its first repeat) and replayed afterwards; runs whose waves all
+ * take one cooperative launch per iteration (many waves, rows of at most 32
+ * entries) are always launched from the host.  Results are the same either
+ * way.
  * Errors: LP_EINVAL for NULL arguments, tolerance outside [0, 1],
  * max_iter < 1, mode not LP_SYNC/LP_ASYNC, waves < 1 or too large (LP_ASYNC),
  * init_labels outside [0, n);
