@@ -113,3 +113,20 @@ def test_graph_sharding_balances_work():
         loads = [sum(sizes[i] for i in p) for p in parts]
         assert max(loads) - min(loads) <= max(sizes)
     assert bench.gather_results({3: "x"}, 1) == {3: "x"}
+
+
+@pytest.mark.parametrize("steps, sweeps", [(2, 2), (40, 1)])
+def test_reference_arm_bounds_its_sample(steps, sweeps):
+    """The reference arm (the oracle on one host core) takes two sweeps per
+    step, but at most about 60 over the whole run, so a long --steps still
+    ends within minutes; its line reports the same metric as the GPU arm."""
+    import json
+
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--workload", "sbm10k", "--steps", str(steps), "--warmup", "0"],
+                       capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads([x for x in r.stdout.splitlines() if x.startswith("{")][-1])
+    assert line["impl"] == "reference" and line["steps"] == steps
+    assert line["metric"] == "RAK GTEPS (sbm10k)" and line["value"] > 0
+    assert line["cpu_baseline"]["sample"].startswith(f"{sweeps} sync sweeps")
